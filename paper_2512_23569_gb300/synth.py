@@ -1,0 +1,152 @@
+"""Seeded synthetic test images for the Haar-tSVD denoiser.
+
+This module only draws inputs: clean piecewise-constant images with gratings
+and the noise models used for evaluation.  It holds none of the denoiser's
+arithmetic, so both the CUDA path and the FP64 oracle may consume what it
+produces without sharing any method code.
+
+Recipe (one ``numpy.random.Generator(PCG64(seed))`` per image):
+
+* background: a constant drawn from U[0, 255];
+* 20 axis-aligned rectangles, corners uniform over the image, intensity U[0, 255];
+* 10 disks, centre uniform, radius U[4, min(H, W)/6], intensity U[0, 255];
+* 2 sinusoidal gratings, each confined to a random rectangle: period U[6, 20] px,
+  orientation U[0, pi), amplitude A ~ U[20, 60], mean U[A, 255 - A];
+* shapes are painted in that order, each overwriting what lies below it; the
+  result is clipped to [0, 255];
+* colour images share the geometry; every shape (and the background) gets
+  per-channel gains U[0.8, 1.2] applied before clipping.
+
+Layout is planar CHW float32 (C = 1 or 3), row-major.  Noisy images are never
+clipped.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "clean_image",
+    "awgn",
+    "poisson_gaussian",
+    "correlate_noise",
+    "make_config_image",
+    "psnr",
+]
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def clean_image(H: int, W: int, C: int, seed: int) -> np.ndarray:
+    """Seeded clean image, float32 CHW in [0, 255]."""
+    if C not in (1, 3):
+        raise ValueError("C must be 1 or 3")
+    rng = _rng(seed)
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+
+    def gains() -> np.ndarray:
+        if C == 1:
+            return np.ones(1)
+        return rng.uniform(0.8, 1.2, size=C)
+
+    img = np.empty((C, H, W), dtype=np.float64)
+    bg = rng.uniform(0.0, 255.0)
+    g = gains()
+    for c in range(C):
+        img[c] = bg * g[c]
+
+    # 20 rectangles
+    for _ in range(20):
+        y0, y1 = np.sort(rng.uniform(0, H, size=2))
+        x0, x1 = np.sort(rng.uniform(0, W, size=2))
+        val = rng.uniform(0.0, 255.0)
+        g = gains()
+        m = (yy >= y0) & (yy <= y1) & (xx >= x0) & (xx <= x1)
+        for c in range(C):
+            img[c][m] = val * g[c]
+
+    # 10 disks
+    rmax = max(4.0, min(H, W) / 6.0)
+    for _ in range(10):
+        cy = rng.uniform(0, H)
+        cx = rng.uniform(0, W)
+        r = rng.uniform(4.0, rmax)
+        val = rng.uniform(0.0, 255.0)
+        g = gains()
+        m = (yy - cy) ** 2 + (xx - cx) ** 2 <= r * r
+        for c in range(C):
+            img[c][m] = val * g[c]
+
+    # 2 gratings inside random rectangles
+    for _ in range(2):
+        y0, y1 = np.sort(rng.uniform(0, H, size=2))
+        x0, x1 = np.sort(rng.uniform(0, W, size=2))
+        period = rng.uniform(6.0, 20.0)
+        theta = rng.uniform(0.0, np.pi)
+        amp = rng.uniform(20.0, 60.0)
+        mean = rng.uniform(amp, 255.0 - amp)
+        g = gains()
+        m = (yy >= y0) & (yy <= y1) & (xx >= x0) & (xx <= x1)
+        phase = 2.0 * np.pi * (xx * np.cos(theta) + yy * np.sin(theta)) / period
+        wave = mean + amp * np.sin(phase)
+        for c in range(C):
+            img[c][m] = (wave * g[c])[m]
+
+    np.clip(img, 0.0, 255.0, out=img)
+    return img.astype(np.float32)
+
+
+def awgn(clean: np.ndarray, sigma: float, seed: int) -> np.ndarray:
+    """clean + N(0, sigma^2), float32, not clipped."""
+    rng = _rng(seed)
+    n = rng.standard_normal(clean.shape) * float(sigma)
+    return (clean.astype(np.float64) + n).astype(np.float32)
+
+
+def poisson_gaussian(clean: np.ndarray, a: float, sigma_b: float, seed: int) -> np.ndarray:
+    """a * Poisson(clean / a) + N(0, sigma_b^2) on the [0, 255] scale (float32).
+
+    ``a`` may be a scalar or an array broadcastable to ``clean`` (spatially
+    varying gain); ``a == 0`` means no shot noise.
+    """
+    rng = _rng(seed)
+    x = clean.astype(np.float64)
+    a = np.broadcast_to(np.asarray(a, dtype=np.float64), x.shape)
+    shot = np.where(a > 0, a * rng.poisson(np.where(a > 0, x / np.maximum(a, 1e-300), 0.0)), x)
+    sb = np.broadcast_to(np.asarray(sigma_b, dtype=np.float64), x.shape)
+    y = shot + rng.standard_normal(x.shape) * sb
+    return y.astype(np.float32)
+
+
+def correlate_noise(clean: np.ndarray, noisy: np.ndarray, std: float = 0.7) -> np.ndarray:
+    """Convolve the noise (noisy - clean) with a normalised 3x3 Gaussian (reflect border)."""
+    r = np.arange(-1, 2, dtype=np.float64)
+    k1 = np.exp(-0.5 * (r / std) ** 2)
+    k = np.outer(k1, k1)
+    k /= k.sum()
+    n = noisy.astype(np.float64) - clean.astype(np.float64)
+    out = np.zeros_like(n)
+    pad = np.pad(n, ((0, 0), (1, 1), (1, 1)), mode="reflect")
+    H, W = n.shape[1:]
+    for dy in range(3):
+        for dx in range(3):
+            out += k[dy, dx] * pad[:, dy:dy + H, dx:dx + W]
+    return (clean.astype(np.float64) + out).astype(np.float32)
+
+
+def make_config_image(H: int, W: int, C: int, sigma: float, seed: int):
+    """(clean, noisy) pair with AWGN of std ``sigma``; noise seed = seed + 1."""
+    clean = clean_image(H, W, C, seed)
+    noisy = awgn(clean, sigma, seed + 1)
+    return clean, noisy
+
+
+def psnr(x: np.ndarray, ref: np.ndarray) -> float:
+    """10 log10(255^2 / MSE) over all pixels and channels."""
+    d = x.astype(np.float64) - ref.astype(np.float64)
+    mse = float(np.mean(d * d))
+    if mse == 0.0:
+        return float("inf")
+    return 10.0 * np.log10(255.0 * 255.0 / mse)
