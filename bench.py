@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Haar-tSVD denoiser.
+
+Workload (one "step" = the whole hot path on one image): colour 512x512x3
+seeded synthetic image (rectangles, disks, gratings; per-channel gains) plus
+AWGN sigma = 50 that the method does not know; the step estimates the
+globally-learned t-SVD basis (Eq. 11), the noise level (Eq. 12 floor, Eq. 22-23
+vote), groups every reference patch (K = 16, 31x31 window, step 4), filters
+(Eq. 19-21) and aggregates.  Metric: Mpixel/s (H*W per second).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank denoises its own seeded image (weak scaling, no
+collective in the data path); rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s denoised on 1 GB300 at ≤0.05 dB PSNR of FP64 oracle, plain vs chosen"
+WORKLOAD = {
+    "workload": "colour 512x512x3, AWGN sigma=50 unknown (estimated), globally-learned basis, "
+                "ps=8, K=16, 31x31 window, step 4",
+    "H": 512, "W": 512, "C": 3, "sigma": 50.0, "K": 16, "win": 31, "step": 4, "seed": 2000,
+}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# ----------------------------------------------------------- algorithmic work
+
+def _grid(n, step, ps=8):
+    g = list(range(0, n - ps + 1, step))
+    if g[-1] != n - ps:
+        g.append(n - ps)
+    return g
+
+
+def algorithmic_work(H, W, C, K, win, step):
+    """Algorithmic flops / bytes per launch of the main kernels."""
+    ys, xs = _grid(H, step), _grid(W, step)
+    R = (win - 1) // 2
+    cy = [min(H - 8, y + R) - max(0, y - R) + 1 for y in ys]
+    cx = [min(W - 8, x + R) - max(0, x - R) + 1 for x in xs]
+    pairs = sum(cy) * sum(cx) - len(ys) * len(xs)  # candidates excluding self
+    nref = len(ys) * len(xs)
+    logk = int(math.log2(K))
+    if C == 3:
+        patch = 2 * 2 * 512 + 2 * 8 * 512  # real 8x8x8 pair + complex pair (8 flop / complex MAC)
+        streams = 192
+    else:
+        patch = 2 * 2 * 512
+        streams = 64
+    haar = streams * 4 * (K - 1)
+    per_group = 2 * (K * patch + haar)  # forward + inverse
+    return {
+        "k_match": {"flops": pairs * 64 * 3, "unit": "TFLOP/s", "per": "3 flop x 64 px per candidate pair",
+                    "units": pairs},
+        "k_filter": {"flops": nref * per_group, "unit": "TFLOP/s",
+                     "per": "%d flop per group (8x8 projections fwd+inv, Haar fwd+inv)" % per_group,
+                     "units": nref},
+        "k_normalize": {"bytes": H * W * C * (8 + 4) + H * W * 4, "unit": "GB/s",
+                        "per": "read int64 sums + write f32 per channel, read int32 weight", "units": H * W},
+        "nref": nref, "pairs": pairs,
+    }
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks / throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ------------------------------------------------------------------ helpers
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _image(rank):
+    from paper_2512_23569_gb300 import synth
+
+    w = WORKLOAD
+    return synth.make_config_image(w["H"], w["W"], w["C"], w["sigma"], w["seed"] + 10 * rank)
+
+
+def _oracle_params():
+    from oracle import hts_oracle as o
+
+    w = WORKLOAD
+    return o.Params(K=w["K"], win=w["win"], step=w["step"])
+
+
+def cpu_baseline(noisy, min_seconds=10.0, max_runs=3):
+    """The FP64 oracle as it stands, on the host cores, full image, >= min_seconds of work."""
+    from oracle import hts_oracle as o
+
+    p = _oracle_params()
+    runs, t0, out = 0, time.perf_counter(), None
+    while True:
+        out, _ = o.denoise(noisy, p)
+        runs += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or runs >= max_runs:
+            break
+    w = WORKLOAD
+    return {"value": runs * w["H"] * w["W"] / el / 1e6, "unit": "Mpixel/s", "cores": o.num_threads(),
+            "kind": "oracle", "sample": "%d full %dx%dx%d image(s), %.1f s" % (runs, w["H"], w["W"], w["C"], el),
+            "seconds": el}, out
+
+
+# ------------------------------------------------------------------ arms
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import hts_oracle as o
+    from paper_2512_23569_gb300 import synth
+
+    clean, noisy = _image(0)
+    crop = noisy[:, :256, :256].copy()  # bounded sample: a 256x256 crop per step
+    p = _oracle_params()
+    for _ in range(args.warmup):
+        o.denoise(crop, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        out, _ = o.denoise(crop, p)
+    el = time.perf_counter() - t0
+    val = args.steps * 256 * 256 / el / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Mpixel/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, sample="256x256x3 crop per step", l2="n/a (CPU)"),
+        "cpu_baseline": {"value": val, "unit": "Mpixel/s", "cores": o.num_threads(), "kind": "oracle",
+                         "sample": "%d steps of a 256x256x3 crop of the workload image" % args.steps},
+        "e2e": {"value": val, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "psnr_db": synth.psnr(out, clean[:, :256, :256]),
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2512_23569_gb300 import build, hts, synth
+
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build.build()
+    hts.load()
+    w = WORKLOAD
+    clean, noisy = _image(rank)
+    p = hts.params(K=w["K"], win=w["win"], step=w["step"])
+    x = torch.from_numpy(noisy).cuda()
+    out = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        hts.denoise(x, sigma=None, basis=None, p=p, out=out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = hts.launch_count()
+    hts.profile_begin()
+    for i in range(args.steps):
+        flush.zero_()  # evict the image and intermediates from L2 between steps (outside the events)
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    prof = hts.profile_end()
+    torch.cuda.synchronize()
+    launches = hts.launch_count() - l0
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = world * args.steps * w["H"] * w["W"] / (max_ms / 1e3) / 1e6
+
+    # end to end through the host-buffer C-ABI call (pinned host memory)
+    hx = torch.from_numpy(noisy).pin_memory()
+    ho = torch.empty_like(hx).pin_memory()
+    hxn, hon = hx.numpy(), ho.numpy()
+    for _ in range(2):
+        hts.denoise_host(hxn, sigma=None, p=p, out=hon)
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        hts.denoise_host(hxn, sigma=None, p=p, out=hon)
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+    e2e_val = world * args.steps * w["H"] * w["W"] / float(te.item()) / 1e6
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    den = out.cpu().numpy()
+    stats = hts.last_stats()
+    work = algorithmic_work(w["H"], w["W"], w["C"], w["K"], w["win"], w["step"])
+    kernels = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1], "share": v[0] / max(1e-9, sum(
+        u[0] for u in prof.values()))} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    dom = next(iter(kernels))
+    peaks = _peaks()
+    roof = None
+    if dom in work and "flops" in work[dom]:
+        ach = work[dom]["flops"] / (kernels[dom]["ms_per_launch"] / 1e3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2.07 GHz",
+                "algorithmic": work[dom]["per"]}
+    elif dom in work and "bytes" in work[dom]:
+        ach = work[dom]["bytes"] / (kernels[dom]["ms_per_launch"] / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    traffic = _committed_traffic(dom)
+    if roof is not None and traffic is not None:
+        roof["traffic"] = traffic
+
+    cpu = None
+    psnr_oracle = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, ref_out = cpu_baseline(noisy)
+        psnr_oracle = synth.psnr(ref_out, clean)
+        cpu["max_abs_vs_gpu"] = float(np.max(np.abs(ref_out - den.astype(np.float64))))
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(WORKLOAD, l2="flushed between steps (512 MB write outside the timed events)",
+                       parallelism="replicas: one image per rank" if world > 1 else "single GPU"),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": "Mpixel/s", "h2d_bytes_per_step": int(noisy.nbytes),
+                "d2h_bytes_per_step": int(noisy.nbytes), "call": "hts_denoise_host (pinned host buffers)"},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "kernels": kernels,
+        "psnr_db": synth.psnr(den, clean), "psnr_oracle_db": psnr_oracle,
+        "psnr_delta_db": None if psnr_oracle is None else synth.psnr(den, clean) - psnr_oracle,
+        "sigma_hat": stats["sigma"], "redo_groups": stats["filter_redo"], "exact_coefs": stats["filter_exact"],
+        "match_reranked": stats["match_reranked"], "match_fallback": stats["match_fallback"],
+    }
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _committed_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    src = vals.get(kernel + ".source")
+    if not src:
+        return None
+    h = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+    if vals.get(kernel + ".sha") != h:
+        return None
+    try:
+        return float(vals[kernel + ".dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * hts.h -- C ABI of the GB300 (sm_103a) Haar-tSVD denoiser.
+ *
+ * Haar-tSVD ("Image Denoising Using Global and Local Circulant
+ * Representation", Kong, Yang, Zhang, arXiv 2512.23569) is a one-step
+ * patch-based denoiser: every reference patch is grouped with its K nearest
+ * patches (Eq. 9, Alg. 1 step 1), the group is projected on a global t-SVD
+ * basis combined with a Haar transform along the group axis (Eq. 19), hard
+ * thresholded (Eq. 20), transformed back (Eq. 21) and averaged into the
+ * output (Alg. 1 step 3).  The noise level can be estimated from the
+ * eigenvalues of the circulant structures (Eq. 12, 22, 23).
+ *
+ * Conventions shared by every call:
+ *   - Images are planar CHW float32, row-major, contiguous, C in {1, 3}
+ *     (channel order R, G, B), values on any scale (the method's parameters
+ *     assume [0, 255]).
+ *   - Image pointers are DEVICE pointers unless the name says `host`.  The
+ *     caller owns every buffer it passes; the library never frees them.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on it unless their comment says they synchronise.
+ *   - Every call validates its arguments on the host first and returns
+ *     HTS_EINVAL / HTS_EUNSUPPORTED before launching anything.  On any
+ *     failure `hts_last_error()` returns a message (per host thread).
+ *   - The library keeps a device workspace per (device, stream), grown on
+ *     demand with cudaMalloc and released by hts_shutdown().  Two calls in
+ *     flight on the same stream are ordered by the stream; calls on different
+ *     streams use different workspaces.
+ *   - There is no CPU fallback: every step runs in the library's kernels.
+ */
+#ifndef HTS_H
+#define HTS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HTS_OK = 0,
+    HTS_EINVAL = 1,        /* bad argument (checked before any device work) */
+    HTS_ENOMEM = 2,        /* device or host allocation failed */
+    HTS_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    HTS_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+    HTS_EUNSUPPORTED = 5,  /* valid for the method, not built here (e.g. ps != 8) */
+    HTS_EINTERNAL = 6      /* a device-side consistency check failed */
+} hts_status;
+
+/* Method parameters.  Defaults (hts_params_default) follow Sec. IV-A of the
+ * paper (ps = 8, gamma = 1.2 in Eq. 9, beta = 1.2 and gamma = 13 for K = 32
+ * in Eq. 23, tau = sigma sqrt(2 ln(c K ps^2))) with K = 16, win = 21, step 4. */
+typedef struct {
+    int ps;            /* patch side; only 8 is built (else HTS_EUNSUPPORTED) */
+    int K;             /* patches per group: 2, 4, 8, 16 or 32 (Haar needs 2^n, Eq. 8) */
+    int win;           /* search window side: odd, 3..63, centred on the reference corner */
+    int step;          /* reference grid step, 1..ps; the last row/column n-ps is always added */
+    double gamma_gcp;  /* Eq. 9 green-channel weight (> 0) */
+    double beta;       /* Eq. 23 divisor (> 0) */
+    double gamma_rank; /* Eq. 23 rank threshold; <= 0 selects 13 K / 32 */
+    double tau_mult;   /* multiplier on the universal threshold (>= 0) */
+    int adjust_rank;   /* 1: apply the Eq. 22-23 vote when sigma is estimated */
+    int mp_correct;    /* 1: divide the Eq. 12 floor by the Marchenko-Pastur edge (1-1/sqrt(N_ref))^2 */
+} hts_params;
+
+/* Fills *p with the defaults above.  HTS_EINVAL if p is NULL. */
+hts_status hts_params_default(hts_params *p);
+
+/* ---------------------------------------------------------------- basis */
+
+/* Opaque global t-SVD basis (Eq. 11): for every stored Fourier slice j of
+ * mode 3 (1 slice for C = 1, 2 for C = 3; slice 3 is the conjugate of slice
+ * 2) the 8 x 8 pair (U^(j), V^(j)), kept on the device in FP64 and FP32, plus
+ * the eigenvalues it was derived from. */
+typedef struct hts_basis hts_basis;
+
+/* Globally-learned basis (Sec. III-B2, Eq. 11): eigenvectors of the row and
+ * column covariances of all reference patches of `img` (device, CHW),
+ * accumulated and eigendecomposed in FP64 on the device.  *out receives a new
+ * basis owned by the caller (free with hts_basis_free).  Synchronises on
+ * `stream` before returning. */
+hts_status hts_estimate_basis(const float *img, int H, int W, int C, const hts_params *p,
+                              hts_basis **out, void *stream);
+
+/* Builds a basis from host data (globally-reused variant, Sec. III-B2).
+ * host_basis: float64 array [ns][2][8][8][2] with ns = C/2+1; [j][0] is
+ * U^(j), [j][1] is V^(j), element [a][i] is row a of eigenvector i, last index
+ * (re, im).  host_eigvals: optional float64 [ns][2][8] (may be NULL).
+ * Slice 0 must be real (imaginary parts zero).  Matrices must be unitary to
+ * 1e-6 (checked).  Synchronous. */
+hts_status hts_basis_create(const double *host_basis, const double *host_eigvals, int C, hts_basis **out);
+
+/* Copies a basis to host arrays laid out as in hts_basis_create (either
+ * pointer may be NULL); *C_out (optional) receives the channel count. */
+hts_status hts_basis_read(const hts_basis *b, double *host_basis, double *host_eigvals, int *C_out);
+
+/* Releases a basis (NULL is a no-op). */
+hts_status hts_basis_free(hts_basis *b);
+
+/* Saves / loads a basis to / from a small binary file (magic "HTSB1"). */
+hts_status hts_basis_save(const hts_basis *b, const char *path);
+hts_status hts_basis_load(const char *path, hts_basis **out);
+
+/* ---------------------------------------------------------- noise level */
+
+typedef struct {
+    double sigma_hat;   /* final estimate (Eq. 23 applied) */
+    double sigma_est;   /* covariance floor (Eq. 12) before the vote */
+    int votes;          /* groups whose rank position of lambda_hat is <= gamma_rank */
+    int nref;           /* number of groups (reference patches) */
+    int adjusted;       /* 1 if a strict majority voted and sigma_est was divided by beta */
+    int uncertain;      /* groups whose FP32 rank test was re-evaluated in FP64 */
+} hts_sigma_info;
+
+/* Noise level of `img` (device, CHW): sigma_est from the smallest eigenvalue
+ * of the global covariances (Eq. 12: the noise adds ps * N_ref * sigma^2),
+ * then every group votes with the rank position of lambda_hat (Eq. 22) and a
+ * strict majority divides by beta (Eq. 23).  basis: the covariances'
+ * eigenvalues are taken from it when non-NULL (it must have been estimated,
+ * not created without eigenvalues), else estimated.  Writes *sigma_out (host)
+ * and *info (optional).  Synchronises on `stream`. */
+hts_status hts_estimate_sigma(const float *img, int H, int W, int C, const hts_basis *basis,
+                              const hts_params *p, double *sigma_out, hts_sigma_info *info, void *stream);
+
+/* ------------------------------------------------------------- denoise */
+
+/* Haar-tSVD (Alg. 1) of `noisy` into `out` (device, CHW, may not alias).
+ * sigma >= 0: known noise level; sigma < 0: estimated on the device as in
+ * hts_estimate_sigma (nothing is copied to the host).  basis NULL: the
+ * globally-learned basis of `noisy` is estimated on the device.  Output is
+ * the plain average of all group estimates, not clipped.  Asynchronous. */
+hts_status hts_denoise(const float *noisy, float *out, int H, int W, int C, float sigma,
+                       const hts_basis *basis, const hts_params *p, void *stream);
+
+/* hts_denoise on HOST buffers: copies noisy_host to the device, denoises and
+ * copies the result back into out_host, all on `stream`, then synchronises.
+ * Pinned host memory is fastest but not required. */
+hts_status hts_denoise_host(const float *noisy_host, float *out_host, int H, int W, int C, float sigma,
+                            const hts_basis *basis, const hts_params *p, void *stream);
+
+/* One image of a batch. */
+typedef struct {
+    const float *noisy;  /* device, CHW */
+    float *out;          /* device, CHW */
+    int H, W, C;
+    float sigma;         /* < 0: estimate */
+} hts_image;
+
+/* Denoises n independent images (mixed sizes and channel counts) on
+ * `stream`, each with its own globally-learned basis.  Asynchronous. */
+hts_status hts_denoise_batch(const hts_image *imgs, int n, const hts_params *p, void *stream);
+
+/* ------------------------------------------------- inspection / tests */
+
+/* Grouping step alone (Eq. 9, Alg. 1 step 1): idx_out (device, int32,
+ * N_ref x K) receives raster indices y*W+x of the group members' top-left
+ * corners; slot 0 is the reference, then the K-1 nearest other candidates
+ * in ascending (squared distance, raster index).  green_out (device,
+ * uint8 N_ref, may be NULL) receives the Eq. 9 flag.  N_ref = ny * nx with
+ * ny = number of grid positions 0, step, ... plus H-8.  Asynchronous. */
+hts_status hts_match(const float *img, int H, int W, int C, const hts_params *p,
+                     int32_t *idx_out, uint8_t *green_out, void *stream);
+
+/* Number of reference patches for an H x W image (0 on bad input). */
+int hts_num_refs(int H, int W, const hts_params *p);
+
+/* Counters of the last hts_denoise / hts_match / hts_estimate_sigma call on
+ * `stream` (synchronises on it). */
+typedef struct {
+    int nref;
+    int match_reranked;    /* references whose order was settled by the FP64 re-rank */
+    int match_fallback;    /* references matched by the exhaustive FP64 path */
+    int filter_redo;       /* groups with a coefficient inside the FP32 guard band */
+    int filter_exact;      /* coefficients whose threshold decision was taken in FP64 */
+    int vote_uncertain;    /* groups whose rank test was taken in FP64 */
+    double sigma;          /* noise level used */
+    double tau;            /* threshold used */
+} hts_stats;
+hts_status hts_last_stats(hts_stats *out, void *stream);
+
+/* Kernel timing: between hts_profile_begin() and hts_profile_end() every
+ * kernel launch of the library is bracketed by CUDA events recorded on its
+ * launch stream.  hts_profile_end synchronises on those events and writes up
+ * to `max` entries (one per kernel name: summed milliseconds and number of
+ * launches); *n_out receives the number written.  Process-wide. */
+typedef struct {
+    char name[48];
+    double total_ms;
+    int launches;
+} hts_kernel_time;
+hts_status hts_profile_begin(void);
+hts_status hts_profile_end(hts_kernel_time *out, int max, int *n_out);
+
+/* Thread-local message for the last failing call on this host thread. */
+const char *hts_last_error(void);
+
+/* Number of kernels this library has launched since it was loaded. */
+uint64_t hts_launch_count(void);
+
+/* Library version string. */
+const char *hts_version(void);
+
+/* Frees every workspace on every device.  No call may be in flight. */
+hts_status hts_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HTS_H */

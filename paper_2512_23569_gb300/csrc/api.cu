@@ -1,0 +1,613 @@
+// C ABI of the Haar-tSVD library (include/hts.h): argument validation,
+// per-(device, stream) workspaces and the order of the kernel launches.
+// Every step of the method runs in the kernels of match.cu, basis.cu,
+// sigma.cu and filter.cu; the host only validates and launches.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "hts_internal.h"
+
+struct hts_basis : hts::hts_basis_dev {};
+
+namespace hts {
+
+static std::atomic<unsigned long long> g_launches{0};
+static thread_local std::string g_err;
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ------------------------------------------------------------ profiling
+
+struct ProfRec {
+    const char *name;
+    cudaEvent_t e0, e1;
+};
+static std::mutex g_pmu;
+static bool g_prof = false;
+static std::vector<ProfRec> g_recs;
+static std::vector<cudaEvent_t> g_pool;
+
+static cudaEvent_t take_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+KTimer::KTimer(const char *name, cudaStream_t s) : slot(-1), stream(s) {
+    count_launch();
+    std::lock_guard<std::mutex> lk(g_pmu);
+    if (!g_prof) return;
+    ProfRec r;
+    r.name = name;
+    r.e0 = take_event();
+    r.e1 = take_event();
+    if (!r.e0 || !r.e1) return;
+    cudaEventRecord(r.e0, s);
+    slot = (int)g_recs.size();
+    g_recs.push_back(r);
+}
+
+KTimer::~KTimer() {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_pmu);
+    cudaEventRecord(g_recs[slot].e1, stream);
+}
+
+static hts_status fail(hts_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+hts_status check_launch(const char *what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(HTS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return HTS_OK;
+}
+
+static hts_status cuda_ok(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return HTS_OK;
+    if (e == cudaErrorMemoryAllocation) return fail(HTS_ENOMEM, std::string(what) + ": out of device memory");
+    return fail(HTS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define HTS_TRY(expr)                       \
+    do {                                    \
+        hts_status _s = (expr);             \
+        if (_s != HTS_OK) return _s;        \
+    } while (0)
+
+// ----------------------------------------------------------- workspace
+
+struct Workspace {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t cap_idx = 0, cap_fb = 0, cap_redo = 0, cap_green = 0, cap_hw = 0, cap_chw = 0, cap_cov = 0;
+    size_t cap_in = 0, cap_out = 0;
+    int32_t *idx = nullptr;
+    uint8_t *green = nullptr;
+    int32_t *fb = nullptr;
+    int32_t *redo = nullptr;
+    long long *acc = nullptr;
+    int *wcount = nullptr;
+    double *cov = nullptr;
+    double *b64 = nullptr;
+    float *b32 = nullptr;
+    double *eig = nullptr;
+    DevState *st = nullptr;
+    float *io_in = nullptr, *io_out = nullptr;
+};
+
+static std::mutex g_mu;
+static std::map<std::pair<int, cudaStream_t>, Workspace *> g_ws;
+
+template <typename T>
+static hts_status grow(T *&ptr, size_t &cap, size_t need, const char *what) {
+    if (need <= cap && ptr) return HTS_OK;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    cap = 0;
+    const size_t n = need + need / 4 + 64;
+    HTS_TRY(cuda_ok(cudaMalloc(reinterpret_cast<void **>(&ptr), n * sizeof(T)), what));
+    cap = n;
+    return HTS_OK;
+}
+
+static hts_status get_ws(cudaStream_t s, Workspace **out) {
+    int dev = 0;
+    HTS_TRY(cuda_ok(cudaGetDevice(&dev), "cudaGetDevice"));
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto key = std::make_pair(dev, s);
+    auto it = g_ws.find(key);
+    if (it != g_ws.end()) {
+        *out = it->second;
+        return HTS_OK;
+    }
+    Workspace *w = new Workspace();
+    w->device = dev;
+    w->stream = s;
+    hts_status st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&w->st), sizeof(DevState)), "cudaMalloc(state)");
+    if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&w->b64), 2 * 256 * sizeof(double)), "cudaMalloc");
+    if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&w->b32), 2 * 256 * sizeof(float)), "cudaMalloc");
+    if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&w->eig), 4 * 8 * sizeof(double)), "cudaMalloc");
+    if (st != HTS_OK) {
+        delete w;
+        return st;
+    }
+    g_ws[key] = w;
+    *out = w;
+    return HTS_OK;
+}
+
+static hts_status ensure(Workspace *w, const Geom &g) {
+    const size_t nref = (size_t)g.nref, hw = (size_t)g.H * g.W;
+    HTS_TRY(grow(w->idx, w->cap_idx, nref * g.K, "cudaMalloc(idx)"));
+    HTS_TRY(grow(w->fb, w->cap_fb, nref, "cudaMalloc(fallback)"));
+    HTS_TRY(grow(w->redo, w->cap_redo, nref, "cudaMalloc(redo)"));
+    HTS_TRY(grow(w->green, w->cap_green, nref, "cudaMalloc(green)"));
+    HTS_TRY(grow(w->acc, w->cap_chw, hw * g.C, "cudaMalloc(acc)"));
+    HTS_TRY(grow(w->wcount, w->cap_hw, hw, "cudaMalloc(weights)"));
+    HTS_TRY(grow(w->cov, w->cap_cov, cov_partial_count(g), "cudaMalloc(cov)"));
+    return HTS_OK;
+}
+
+// ----------------------------------------------------------- validation
+
+static hts_status validate(int H, int W, int C, const hts_params *p, Geom *g) {
+    if (!p) return fail(HTS_EINVAL, "params is NULL");
+    if (p->ps != PS) return fail(HTS_EUNSUPPORTED, "only ps = 8 is built");
+    if (C != 1 && C != 3) return fail(HTS_EINVAL, "C must be 1 or 3");
+    if (H < PS || W < PS) return fail(HTS_EINVAL, "image smaller than a patch");
+    if ((long long)H * W * C > 0x7fffffffll) return fail(HTS_EINVAL, "image too large for 32-bit indices");
+    if (p->K != 2 && p->K != 4 && p->K != 8 && p->K != 16 && p->K != 32)
+        return fail(HTS_EINVAL, "K must be a power of two in [2, 32]");
+    if (p->win < 3 || (p->win % 2) == 0) return fail(HTS_EINVAL, "win must be odd and >= 3");
+    if (p->win > MAX_WIN) return fail(HTS_EUNSUPPORTED, "win > 63 is not built");
+    if (p->step < 1 || p->step > PS) return fail(HTS_EINVAL, "step must be in [1, ps]");
+    if (!(p->gamma_gcp > 0) || !std::isfinite(p->gamma_gcp)) return fail(HTS_EINVAL, "gamma_gcp must be > 0");
+    if (!(p->beta > 0) || !std::isfinite(p->beta)) return fail(HTS_EINVAL, "beta must be > 0");
+    if (!(p->tau_mult >= 0) || !std::isfinite(p->tau_mult)) return fail(HTS_EINVAL, "tau_mult must be >= 0");
+    if (!std::isfinite(p->gamma_rank)) return fail(HTS_EINVAL, "gamma_rank must be finite");
+    const int R = (p->win - 1) / 2;
+    const long long cap = (long long)std::min(R + 1, H - PS + 1) * std::min(R + 1, W - PS + 1);
+    if (cap < p->K) return fail(HTS_EINVAL, "search window holds fewer than K patch positions");
+    g->H = H;
+    g->W = W;
+    g->C = C;
+    g->step = p->step;
+    g->R = R;
+    g->K = p->K;
+    g->ny = grid_count(H, p->step);
+    g->nx = grid_count(W, p->step);
+    g->nref = g->ny * g->nx;
+    return HTS_OK;
+}
+
+// ------------------------------------------------------------- basis
+
+// Doubles in a basis of ns stored slices: [ns][2 (U, V)][8][8][2 (re, im)].
+static inline size_t basis_doubles(int ns) { return (size_t)ns * 2 * 64 * 2; }
+// Doubles of one 8x8 complex matrix.
+constexpr int MAT_DOUBLES = 64 * 2;
+
+static hts_status alloc_basis(int C, hts_basis **out) {
+    int dev = 0;
+    HTS_TRY(cuda_ok(cudaGetDevice(&dev), "cudaGetDevice"));
+    hts_basis *b = new hts_basis();
+    b->C = C;
+    b->ns = C / 2 + 1;
+    b->has_eig = 0;
+    b->device = dev;
+    b->b64 = nullptr;
+    b->b32 = nullptr;
+    b->eig = nullptr;
+    hts_status st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&b->b64), basis_doubles(b->ns) * sizeof(double)), "cudaMalloc(basis)");
+    if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&b->b32), basis_doubles(b->ns) * sizeof(float)), "cudaMalloc(basis)");
+    if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&b->eig), b->ns * 16 * sizeof(double)), "cudaMalloc(basis)");
+    if (st != HTS_OK) {
+        cudaFree(b->b64);
+        cudaFree(b->b32);
+        cudaFree(b->eig);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return HTS_OK;
+}
+
+static void free_basis(hts_basis *b) {
+    if (!b) return;
+    cudaFree(b->b64);
+    cudaFree(b->b32);
+    cudaFree(b->eig);
+    delete b;
+}
+
+// ------------------------------------------------------------- pipeline
+
+// Basis pointers used by one call: caller's or freshly estimated.
+struct BasisRef {
+    const double *b64;
+    const float *b32;
+    const double *eig;
+};
+
+static hts_status prepare(const float *img, const Geom &g, const hts_params &p, const hts_basis *basis,
+                          bool need_sigma, Workspace *w, cudaStream_t s, BasisRef *br) {
+    HTS_TRY(cuda_ok(cudaMemsetAsync(w->st, 0, sizeof(DevState), s), "cudaMemsetAsync(state)"));
+    const bool est = (basis == nullptr) || (need_sigma && !basis->has_eig);
+    if (est) HTS_TRY(launch_basis(img, g, w->cov, w->b64, w->b32, w->eig, s));
+    br->b64 = basis ? basis->b64 : w->b64;
+    br->b32 = basis ? basis->b32 : w->b32;
+    br->eig = (basis && basis->has_eig) ? basis->eig : w->eig;
+    return HTS_OK;
+}
+
+static hts_status check_basis(const hts_basis *basis, int C) {
+    if (!basis) return HTS_OK;
+    if (basis->C != C) return fail(HTS_EINVAL, "basis was built for another channel count");
+    int dev = 0;
+    HTS_TRY(cuda_ok(cudaGetDevice(&dev), "cudaGetDevice"));
+    if (basis->device != dev) return fail(HTS_EINVAL, "basis lives on another device");
+    return HTS_OK;
+}
+
+static hts_status denoise_impl(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
+                               const hts_params &p, Workspace *w, cudaStream_t s) {
+    HTS_TRY(ensure(w, g));
+    BasisRef br;
+    HTS_TRY(prepare(noisy, g, p, basis, sigma < 0, w, s, &br));
+    const size_t hw = (size_t)g.H * g.W;
+    HTS_TRY(cuda_ok(cudaMemsetAsync(w->acc, 0, hw * g.C * sizeof(long long), s), "cudaMemsetAsync(acc)"));
+    HTS_TRY(cuda_ok(cudaMemsetAsync(w->wcount, 0, hw * sizeof(int), s), "cudaMemsetAsync(weights)"));
+    HTS_TRY(launch_match(noisy, g, p.gamma_gcp, w->idx, w->green, w->fb, w->st, s));
+    if (sigma < 0) HTS_TRY(launch_sigma(noisy, g, p, br.eig, w->idx, w->st, s));
+    else HTS_TRY(launch_set_sigma((double)sigma, g, p, w->st, s));
+    return launch_filter(noisy, g, w->idx, br.b64, br.b32, w->acc, w->wcount, w->redo, w->st, out, s);
+}
+
+}  // namespace hts
+
+using namespace hts;
+
+extern "C" {
+
+hts_status hts_params_default(hts_params *p) {
+    if (!p) return fail(HTS_EINVAL, "params is NULL");
+    p->ps = 8;
+    p->K = 16;
+    p->win = 21;
+    p->step = 4;
+    p->gamma_gcp = 1.2;
+    p->beta = 1.2;
+    p->gamma_rank = 0.0;
+    p->tau_mult = 1.0;
+    p->adjust_rank = 1;
+    p->mp_correct = 1;
+    return HTS_OK;
+}
+
+int hts_num_refs(int H, int W, const hts_params *p) {
+    if (!p || p->ps != PS || H < PS || W < PS || p->step < 1 || p->step > PS) return 0;
+    return grid_count(H, p->step) * grid_count(W, p->step);
+}
+
+hts_status hts_estimate_basis(const float *img, int H, int W, int C, const hts_params *p, hts_basis **out,
+                              void *stream) {
+    Geom g;
+    HTS_TRY(validate(H, W, C, p, &g));
+    if (!img || !out) return fail(HTS_EINVAL, "NULL pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace *w;
+    HTS_TRY(get_ws(s, &w));
+    HTS_TRY(ensure(w, g));
+    hts_basis *b;
+    HTS_TRY(alloc_basis(C, &b));
+    hts_status st = launch_basis(img, g, w->cov, b->b64, b->b32, b->eig, s);
+    if (st == HTS_OK) st = cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (st != HTS_OK) {
+        free_basis(b);
+        return st;
+    }
+    b->has_eig = 1;
+    *out = b;
+    return HTS_OK;
+}
+
+hts_status hts_basis_create(const double *host_basis, const double *host_eigvals, int C, hts_basis **out) {
+    if (!host_basis || !out) return fail(HTS_EINVAL, "NULL pointer");
+    if (C != 1 && C != 3) return fail(HTS_EINVAL, "C must be 1 or 3");
+    const int ns = C / 2 + 1;
+    for (int j = 0; j < ns; ++j)
+        for (int m = 0; m < 2; ++m) {
+            const double *M = host_basis + (size_t)(j * 2 + m) * MAT_DOUBLES;
+            for (int e = 0; e < MAT_DOUBLES; ++e)
+                if (!std::isfinite(M[e])) return fail(HTS_EINVAL, "basis holds a non-finite value");
+            if (j == 0)
+                for (int e = 0; e < 64; ++e)
+                    if (M[2 * e + 1] != 0.0) return fail(HTS_EINVAL, "slice 0 of the basis must be real");
+            for (int i1 = 0; i1 < 8; ++i1)
+                for (int i2 = 0; i2 < 8; ++i2) {
+                    double re = 0, im = 0;  // (M^H M)[i1][i2]
+                    for (int a = 0; a < 8; ++a) {
+                        const double xr = M[(a * 8 + i1) * 2], xi = M[(a * 8 + i1) * 2 + 1];
+                        const double yr = M[(a * 8 + i2) * 2], yi = M[(a * 8 + i2) * 2 + 1];
+                        re += xr * yr + xi * yi;
+                        im += xr * yi - xi * yr;
+                    }
+                    const double want = (i1 == i2) ? 1.0 : 0.0;
+                    if (std::fabs(re - want) > 1e-6 || std::fabs(im) > 1e-6)
+                        return fail(HTS_EINVAL, "basis matrices must be unitary");
+                }
+        }
+    hts_basis *b;
+    HTS_TRY(alloc_basis(C, &b));
+    float f[4 * MAT_DOUBLES];
+    const size_t nd = basis_doubles(ns);
+    for (size_t e = 0; e < nd; ++e) f[e] = (float)host_basis[e];
+    hts_status st = cuda_ok(cudaMemcpy(b->b64, host_basis, nd * sizeof(double), cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (st == HTS_OK) st = cuda_ok(cudaMemcpy(b->b32, f, nd * sizeof(float), cudaMemcpyHostToDevice), "cudaMemcpy");
+    if (st == HTS_OK && host_eigvals) {
+        st = cuda_ok(cudaMemcpy(b->eig, host_eigvals, ns * 16 * sizeof(double), cudaMemcpyHostToDevice), "cudaMemcpy");
+        b->has_eig = 1;
+    }
+    if (st != HTS_OK) {
+        free_basis(b);
+        return st;
+    }
+    *out = b;
+    return HTS_OK;
+}
+
+hts_status hts_basis_read(const hts_basis *b, double *host_basis, double *host_eigvals, int *C_out) {
+    if (!b) return fail(HTS_EINVAL, "basis is NULL");
+    if (C_out) *C_out = b->C;
+    if (host_basis) HTS_TRY(cuda_ok(cudaMemcpy(host_basis, b->b64, basis_doubles(b->ns) * sizeof(double), cudaMemcpyDeviceToHost), "cudaMemcpy"));
+    if (host_eigvals) {
+        if (!b->has_eig) return fail(HTS_EINVAL, "basis has no eigenvalues");
+        HTS_TRY(cuda_ok(cudaMemcpy(host_eigvals, b->eig, b->ns * 16 * sizeof(double), cudaMemcpyDeviceToHost), "cudaMemcpy"));
+    }
+    return HTS_OK;
+}
+
+hts_status hts_basis_free(hts_basis *b) {
+    free_basis(b);
+    return HTS_OK;
+}
+
+hts_status hts_basis_save(const hts_basis *b, const char *path) {
+    if (!b || !path) return fail(HTS_EINVAL, "NULL pointer");
+    double hb[4 * MAT_DOUBLES], he[32];
+    HTS_TRY(hts_basis_read(b, hb, nullptr, nullptr));
+    if (b->has_eig) HTS_TRY(hts_basis_read(b, nullptr, he, nullptr));
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(HTS_EINVAL, std::string("cannot open ") + path);
+    const char magic[8] = {'H', 'T', 'S', 'B', '1', 0, 0, 0};
+    const int hdr[2] = {b->C, b->has_eig};
+    bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int), 2, f) == 2 &&
+              std::fwrite(hb, sizeof(double), basis_doubles(b->ns), f) == basis_doubles(b->ns);
+    if (ok && b->has_eig) ok = std::fwrite(he, sizeof(double), b->ns * 16, f) == (size_t)b->ns * 16;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? HTS_OK : fail(HTS_EINVAL, "write failed");
+}
+
+hts_status hts_basis_load(const char *path, hts_basis **out) {
+    if (!path || !out) return fail(HTS_EINVAL, "NULL pointer");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(HTS_EINVAL, std::string("cannot open ") + path);
+    char magic[8];
+    int hdr[2];
+    double hb[4 * MAT_DOUBLES], he[32];
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "HTSB1", 5) == 0 &&
+              std::fread(hdr, sizeof(int), 2, f) == 2 && (hdr[0] == 1 || hdr[0] == 3);
+    const int ns = ok ? hdr[0] / 2 + 1 : 0;
+    if (ok) ok = std::fread(hb, sizeof(double), basis_doubles(ns), f) == basis_doubles(ns);
+    if (ok && hdr[1]) ok = std::fread(he, sizeof(double), ns * 16, f) == (size_t)ns * 16;
+    std::fclose(f);
+    if (!ok) return fail(HTS_EINVAL, "not a basis file");
+    return hts_basis_create(hb, hdr[1] ? he : nullptr, hdr[0], out);
+}
+
+hts_status hts_match(const float *img, int H, int W, int C, const hts_params *p, int32_t *idx_out,
+                     uint8_t *green_out, void *stream) {
+    Geom g;
+    HTS_TRY(validate(H, W, C, p, &g));
+    if (!img || !idx_out) return fail(HTS_EINVAL, "NULL pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace *w;
+    HTS_TRY(get_ws(s, &w));
+    HTS_TRY(ensure(w, g));
+    HTS_TRY(cuda_ok(cudaMemsetAsync(w->st, 0, sizeof(DevState), s), "cudaMemsetAsync(state)"));
+    return launch_match(img, g, p->gamma_gcp, idx_out, green_out, w->fb, w->st, s);
+}
+
+hts_status hts_estimate_sigma(const float *img, int H, int W, int C, const hts_basis *basis, const hts_params *p,
+                              double *sigma_out, hts_sigma_info *info, void *stream) {
+    Geom g;
+    HTS_TRY(validate(H, W, C, p, &g));
+    if (!img || !sigma_out) return fail(HTS_EINVAL, "NULL pointer");
+    HTS_TRY(check_basis(basis, C));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace *w;
+    HTS_TRY(get_ws(s, &w));
+    HTS_TRY(ensure(w, g));
+    BasisRef br;
+    HTS_TRY(prepare(img, g, *p, basis, true, w, s, &br));
+    if (p->adjust_rank) HTS_TRY(launch_match(img, g, p->gamma_gcp, w->idx, w->green, w->fb, w->st, s));
+    HTS_TRY(launch_sigma(img, g, *p, br.eig, w->idx, w->st, s));
+    DevState hs;
+    HTS_TRY(cuda_ok(cudaMemcpyAsync(&hs, w->st, sizeof(DevState), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync"));
+    HTS_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+    *sigma_out = hs.sigma_hat;
+    if (info) {
+        info->sigma_hat = hs.sigma_hat;
+        info->sigma_est = hs.sigma_est;
+        info->votes = hs.votes;
+        info->nref = g.nref;
+        info->adjusted = hs.adjusted;
+        info->uncertain = hs.vote_uncertain;
+    }
+    return HTS_OK;
+}
+
+hts_status hts_denoise(const float *noisy, float *out, int H, int W, int C, float sigma, const hts_basis *basis,
+                       const hts_params *p, void *stream) {
+    Geom g;
+    HTS_TRY(validate(H, W, C, p, &g));
+    if (!noisy || !out) return fail(HTS_EINVAL, "NULL pointer");
+    if (noisy == out) return fail(HTS_EINVAL, "out may not alias noisy");
+    if (std::isnan(sigma) || std::isinf(sigma)) return fail(HTS_EINVAL, "sigma must be finite");
+    HTS_TRY(check_basis(basis, C));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace *w;
+    HTS_TRY(get_ws(s, &w));
+    return denoise_impl(noisy, out, g, sigma, basis, *p, w, s);
+}
+
+hts_status hts_denoise_host(const float *noisy_host, float *out_host, int H, int W, int C, float sigma,
+                            const hts_basis *basis, const hts_params *p, void *stream) {
+    Geom g;
+    HTS_TRY(validate(H, W, C, p, &g));
+    if (!noisy_host || !out_host) return fail(HTS_EINVAL, "NULL pointer");
+    if (std::isnan(sigma) || std::isinf(sigma)) return fail(HTS_EINVAL, "sigma must be finite");
+    HTS_TRY(check_basis(basis, C));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace *w;
+    HTS_TRY(get_ws(s, &w));
+    const size_t n = (size_t)H * W * C;
+    HTS_TRY(grow(w->io_in, w->cap_in, n, "cudaMalloc(io)"));
+    HTS_TRY(grow(w->io_out, w->cap_out, n, "cudaMalloc(io)"));
+    HTS_TRY(cuda_ok(cudaMemcpyAsync(w->io_in, noisy_host, n * sizeof(float), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(H2D)"));
+    HTS_TRY(denoise_impl(w->io_in, w->io_out, g, sigma, basis, *p, w, s));
+    HTS_TRY(cuda_ok(cudaMemcpyAsync(out_host, w->io_out, n * sizeof(float), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(D2H)"));
+    return cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+}
+
+hts_status hts_denoise_batch(const hts_image *imgs, int n, const hts_params *p, void *stream) {
+    if (n < 0 || (n > 0 && !imgs)) return fail(HTS_EINVAL, "bad batch");
+    for (int i = 0; i < n; ++i) {
+        Geom g;
+        HTS_TRY(validate(imgs[i].H, imgs[i].W, imgs[i].C, p, &g));
+        if (!imgs[i].noisy || !imgs[i].out || imgs[i].noisy == imgs[i].out)
+            return fail(HTS_EINVAL, "bad image pointers in batch");
+        if (std::isnan(imgs[i].sigma) || std::isinf(imgs[i].sigma)) return fail(HTS_EINVAL, "sigma must be finite");
+    }
+    if (n == 0) return HTS_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace *w;
+    HTS_TRY(get_ws(s, &w));
+    for (int i = 0; i < n; ++i) {
+        Geom g;
+        validate(imgs[i].H, imgs[i].W, imgs[i].C, p, &g);
+        HTS_TRY(denoise_impl(imgs[i].noisy, imgs[i].out, g, imgs[i].sigma, nullptr, *p, w, s));
+    }
+    return HTS_OK;
+}
+
+hts_status hts_last_stats(hts_stats *out, void *stream) {
+    if (!out) return fail(HTS_EINVAL, "NULL pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace *w;
+    HTS_TRY(get_ws(s, &w));
+    DevState hs;
+    HTS_TRY(cuda_ok(cudaMemcpyAsync(&hs, w->st, sizeof(DevState), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync"));
+    HTS_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+    out->nref = hs.nref;
+    out->match_reranked = hs.match_reranked;
+    out->match_fallback = hs.match_fallback;
+    out->filter_redo = hs.filter_redo;
+    out->filter_exact = hs.filter_exact;
+    out->vote_uncertain = hs.vote_uncertain;
+    out->sigma = hs.sigma_hat;
+    out->tau = hs.tau;
+    return HTS_OK;
+}
+
+hts_status hts_profile_begin(void) {
+    std::lock_guard<std::mutex> lk(g_pmu);
+    for (auto &r : g_recs) {
+        g_pool.push_back(r.e0);
+        g_pool.push_back(r.e1);
+    }
+    g_recs.clear();
+    g_prof = true;
+    return HTS_OK;
+}
+
+hts_status hts_profile_end(hts_kernel_time *out, int max, int *n_out) {
+    std::lock_guard<std::mutex> lk(g_pmu);
+    g_prof = false;
+    int n = 0;
+    hts_status st = HTS_OK;
+    for (auto &r : g_recs) {
+        if (cudaEventSynchronize(r.e1) != cudaSuccess) {
+            st = fail(HTS_ECUDA, "cudaEventSynchronize");
+            break;
+        }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) {
+            st = fail(HTS_ECUDA, "cudaEventElapsedTime");
+            break;
+        }
+        int k = 0;
+        while (k < n && std::strcmp(out[k].name, r.name) != 0) ++k;
+        if (k == n) {
+            if (n >= max) continue;
+            std::memset(out[n].name, 0, sizeof(out[n].name));
+            std::strncpy(out[n].name, r.name, sizeof(out[n].name) - 1);
+            out[n].total_ms = 0.0;
+            out[n].launches = 0;
+            ++n;
+        }
+        out[k].total_ms += ms;
+        out[k].launches += 1;
+    }
+    if (n_out) *n_out = n;
+    return st;
+}
+
+const char *hts_last_error(void) { return g_err.c_str(); }
+
+uint64_t hts_launch_count(void) { return g_launches.load(); }
+
+const char *hts_version(void) { return "hts 0.1 (sm_103a)"; }
+
+hts_status hts_shutdown(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto &kv : g_ws) {
+        Workspace *w = kv.second;
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(w->device);
+        cudaFree(w->idx);
+        cudaFree(w->green);
+        cudaFree(w->fb);
+        cudaFree(w->redo);
+        cudaFree(w->acc);
+        cudaFree(w->wcount);
+        cudaFree(w->cov);
+        cudaFree(w->b64);
+        cudaFree(w->b32);
+        cudaFree(w->eig);
+        cudaFree(w->st);
+        cudaFree(w->io_in);
+        cudaFree(w->io_out);
+        cudaSetDevice(prev);
+        delete w;
+    }
+    g_ws.clear();
+    return HTS_OK;
+}
+
+}  // extern "C"

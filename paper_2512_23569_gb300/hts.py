@@ -1,0 +1,309 @@
+"""Python binding of the GB300 Haar-tSVD library (``libhts.so``, C ABI of include/hts.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides device memory and streams.  There is no CPU
+fallback -- if ``libhts.so`` is missing or cannot be loaded, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhts.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+HTS_OK = 0
+_STATUS = {0: "HTS_OK", 1: "HTS_EINVAL", 2: "HTS_ENOMEM", 3: "HTS_ECUDA", 4: "HTS_ETIMEOUT",
+           5: "HTS_EUNSUPPORTED", 6: "HTS_EINTERNAL"}
+
+# every symbol include/hts.h declares
+EXPORTS = [
+    "hts_params_default", "hts_estimate_basis", "hts_basis_create", "hts_basis_read", "hts_basis_free",
+    "hts_basis_save", "hts_basis_load", "hts_estimate_sigma", "hts_denoise", "hts_denoise_host",
+    "hts_denoise_batch", "hts_match", "hts_num_refs", "hts_last_stats", "hts_last_error",
+    "hts_launch_count", "hts_version", "hts_shutdown", "hts_profile_begin", "hts_profile_end",
+]
+
+
+class HtsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_STATUS.get(status, str(status)), msg))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("ps", ctypes.c_int), ("K", ctypes.c_int), ("win", ctypes.c_int), ("step", ctypes.c_int),
+        ("gamma_gcp", ctypes.c_double), ("beta", ctypes.c_double), ("gamma_rank", ctypes.c_double),
+        ("tau_mult", ctypes.c_double), ("adjust_rank", ctypes.c_int), ("mp_correct", ctypes.c_int),
+    ]
+
+
+class SigmaInfo(ctypes.Structure):
+    _fields_ = [("sigma_hat", ctypes.c_double), ("sigma_est", ctypes.c_double), ("votes", ctypes.c_int),
+                ("nref", ctypes.c_int), ("adjusted", ctypes.c_int), ("uncertain", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("nref", ctypes.c_int), ("match_reranked", ctypes.c_int), ("match_fallback", ctypes.c_int),
+                ("filter_redo", ctypes.c_int), ("filter_exact", ctypes.c_int), ("vote_uncertain", ctypes.c_int),
+                ("sigma", ctypes.c_double), ("tau", ctypes.c_double)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("total_ms", ctypes.c_double), ("launches", ctypes.c_int)]
+
+
+class Image(ctypes.Structure):
+    _fields_ = [("noisy", ctypes.c_void_p), ("out", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("C", ctypes.c_int), ("sigma", ctypes.c_float)]
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libhts.so (raises if it is missing: there is no fallback)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libhts.so not built (%s); run paper_2512_23569_gb300.build.build()" % path)
+        lib = ctypes.CDLL(path)
+        P, I, F, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double
+        PP = ctypes.POINTER(Params)
+        lib.hts_params_default.argtypes = [PP]
+        lib.hts_estimate_basis.argtypes = [P, I, I, I, PP, ctypes.POINTER(P), P]
+        lib.hts_basis_create.argtypes = [P, P, I, ctypes.POINTER(P)]
+        lib.hts_basis_read.argtypes = [P, P, P, ctypes.POINTER(I)]
+        lib.hts_basis_free.argtypes = [P]
+        lib.hts_basis_save.argtypes = [P, ctypes.c_char_p]
+        lib.hts_basis_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(P)]
+        lib.hts_estimate_sigma.argtypes = [P, I, I, I, P, PP, ctypes.POINTER(D), ctypes.POINTER(SigmaInfo), P]
+        lib.hts_denoise.argtypes = [P, P, I, I, I, F, P, PP, P]
+        lib.hts_denoise_host.argtypes = [P, P, I, I, I, F, P, PP, P]
+        lib.hts_denoise_batch.argtypes = [ctypes.POINTER(Image), I, PP, P]
+        lib.hts_match.argtypes = [P, I, I, I, PP, P, P, P]
+        lib.hts_num_refs.argtypes = [I, I, PP]
+        lib.hts_num_refs.restype = I
+        lib.hts_last_stats.argtypes = [ctypes.POINTER(Stats), P]
+        lib.hts_last_error.restype = ctypes.c_char_p
+        lib.hts_launch_count.restype = ctypes.c_uint64
+        lib.hts_version.restype = ctypes.c_char_p
+        lib.hts_profile_end.argtypes = [ctypes.POINTER(KernelTime), I, ctypes.POINTER(I)]
+        for name in EXPORTS:  # fail loudly on a library that lacks a declared entry point
+            getattr(lib, name)
+        _LIB = lib
+        return lib
+
+
+def _check(status: int) -> None:
+    if status != HTS_OK:
+        msg = load().hts_last_error()
+        raise HtsError(status, msg.decode() if msg else "")
+
+
+def params(**kw) -> Params:
+    """Defaults of hts_params_default with keyword overrides."""
+    p = Params()
+    _check(load().hts_params_default(ctypes.byref(p)))
+    for k, v in kw.items():
+        if k == "gamma_rank" and v is None:
+            v = 0.0
+        setattr(p, k, v)
+    return p
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _chw(t):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError("expected a CUDA float32 tensor")
+    if t.dim() == 2:
+        t = t.unsqueeze(0)
+    if t.dim() != 3 or not t.is_contiguous():
+        raise ValueError("expected a contiguous CHW tensor")
+    return t
+
+
+def num_refs(H: int, W: int, p: Params | None = None) -> int:
+    p = p or params()
+    return int(load().hts_num_refs(H, W, ctypes.byref(p)))
+
+
+class Basis:
+    """Owns an hts_basis* (global t-SVD basis, Eq. 11)."""
+
+    def __init__(self, handle: ctypes.c_void_p, C: int):
+        self._h = handle
+        self.C = C
+
+    @property
+    def handle(self):
+        return self._h
+
+    def read(self):
+        """-> (basis complex128 (ns, 2, 8, 8), eigvals (ns, 2, 8) or None)."""
+        ns = self.C // 2 + 1
+        b = np.zeros((ns, 2, 8, 8, 2))
+        e = np.zeros((ns, 2, 8))
+        lib = load()
+        _check(lib.hts_basis_read(self._h, ctypes.c_void_p(b.ctypes.data), None, None))
+        try:
+            _check(lib.hts_basis_read(self._h, None, ctypes.c_void_p(e.ctypes.data), None))
+        except HtsError:
+            e = None
+        return b[..., 0] + 1j * b[..., 1], e
+
+    def save(self, path: str) -> None:
+        _check(load().hts_basis_save(self._h, path.encode()))
+
+    @staticmethod
+    def load_file(path: str) -> "Basis":
+        h = ctypes.c_void_p()
+        _check(load().hts_basis_load(path.encode(), ctypes.byref(h)))
+        C = ctypes.c_int()
+        _check(load().hts_basis_read(h, None, None, ctypes.byref(C)))
+        return Basis(h, C.value)
+
+    @staticmethod
+    def from_array(basis: np.ndarray, eigvals: np.ndarray | None = None) -> "Basis":
+        """Basis from complex (ns, 2, 8, 8) (+ optional eigenvalues (ns, 2, 8))."""
+        b = np.asarray(basis, dtype=np.complex128)
+        ns = b.shape[0]
+        C = 1 if ns == 1 else 3
+        flat = np.ascontiguousarray(np.stack([b.real, b.imag], axis=-1))
+        ev = None if eigvals is None else np.ascontiguousarray(eigvals, dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(load().hts_basis_create(ctypes.c_void_p(flat.ctypes.data),
+                                       None if ev is None else ctypes.c_void_p(ev.ctypes.data), C, ctypes.byref(h)))
+        return Basis(h, C)
+
+    def __del__(self):
+        try:
+            if self._h and _LIB is not None:
+                _LIB.hts_basis_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+def estimate_basis(img, p: Params | None = None, stream=None) -> Basis:
+    img = _chw(img)
+    p = p or params()
+    C, H, W = img.shape
+    h = ctypes.c_void_p()
+    _check(load().hts_estimate_basis(ctypes.c_void_p(img.data_ptr()), H, W, C, ctypes.byref(p), ctypes.byref(h),
+                                     _stream(stream)))
+    return Basis(h, C)
+
+
+def estimate_sigma(img, p: Params | None = None, basis: Basis | None = None, stream=None):
+    img = _chw(img)
+    p = p or params()
+    C, H, W = img.shape
+    s = ctypes.c_double()
+    info = SigmaInfo()
+    _check(load().hts_estimate_sigma(ctypes.c_void_p(img.data_ptr()), H, W, C, basis.handle if basis else None,
+                                     ctypes.byref(p), ctypes.byref(s), ctypes.byref(info), _stream(stream)))
+    return s.value, {f: getattr(info, f) for f, _ in SigmaInfo._fields_}
+
+
+def match(img, p: Params | None = None, stream=None):
+    """Grouping step: -> (idx int32 (N_ref, K) CUDA tensor, green uint8 (N_ref,))."""
+    import torch
+
+    img = _chw(img)
+    p = p or params()
+    C, H, W = img.shape
+    n = num_refs(H, W, p)
+    idx = torch.empty((n, p.K), dtype=torch.int32, device=img.device)
+    green = torch.empty((n,), dtype=torch.uint8, device=img.device)
+    _check(load().hts_match(ctypes.c_void_p(img.data_ptr()), H, W, C, ctypes.byref(p),
+                            ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(green.data_ptr()), _stream(stream)))
+    return idx, green
+
+
+def denoise(noisy, sigma: float | None = None, basis: Basis | None = None, p: Params | None = None, out=None,
+            stream=None):
+    """Haar-tSVD of a CUDA CHW float32 tensor; sigma None -> estimated on the device."""
+    import torch
+
+    noisy = _chw(noisy)
+    p = p or params()
+    C, H, W = noisy.shape
+    if out is None:
+        out = torch.empty_like(noisy)
+    s = -1.0 if sigma is None else float(sigma)
+    _check(load().hts_denoise(ctypes.c_void_p(noisy.data_ptr()), ctypes.c_void_p(out.data_ptr()), H, W, C, s,
+                              basis.handle if basis else None, ctypes.byref(p), _stream(stream)))
+    return out
+
+
+def denoise_host(noisy: np.ndarray, sigma: float | None = None, basis: Basis | None = None,
+                 p: Params | None = None, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+    """hts_denoise_host: host (numpy) in, host out; copies happen inside the call."""
+    a = noisy if noisy.ndim == 3 else noisy[None]
+    if a.dtype != np.float32 or not a.flags.c_contiguous:
+        raise TypeError("expected a C-contiguous float32 CHW array")
+    C, H, W = a.shape
+    if out is None:
+        out = np.empty_like(a)
+    s = -1.0 if sigma is None else float(sigma)
+    p = p or params()
+    _check(load().hts_denoise_host(ctypes.c_void_p(a.ctypes.data), ctypes.c_void_p(out.ctypes.data), H, W, C, s,
+                                   basis.handle if basis else None, ctypes.byref(p), _stream(stream)))
+    return out
+
+
+def denoise_batch(noisy: list, sigmas: list, p: Params | None = None, outs: list | None = None, stream=None):
+    import torch
+
+    p = p or params()
+    imgs = (Image * max(1, len(noisy)))()
+    outs = outs or [torch.empty_like(_chw(x)) for x in noisy]
+    for i, (x, s) in enumerate(zip(noisy, sigmas)):
+        x = _chw(x)
+        C, H, W = x.shape
+        imgs[i] = Image(x.data_ptr(), outs[i].data_ptr(), H, W, C, -1.0 if s is None else float(s))
+    _check(load().hts_denoise_batch(imgs, len(noisy), ctypes.byref(p), _stream(stream)))
+    return outs
+
+
+def last_stats(stream=None) -> dict:
+    st = Stats()
+    _check(load().hts_last_stats(ctypes.byref(st), _stream(stream)))
+    return {f: getattr(st, f) for f, _ in Stats._fields_}
+
+
+def launch_count() -> int:
+    return int(load().hts_launch_count())
+
+
+def version() -> str:
+    return load().hts_version().decode()
+
+
+def profile_begin() -> None:
+    """Start bracketing every library kernel launch with CUDA events."""
+    _check(load().hts_profile_begin())
+
+
+def profile_end() -> dict:
+    """Stop profiling; -> {kernel name: (total ms, launches)} (synchronises)."""
+    arr = (KernelTime * 64)()
+    n = ctypes.c_int()
+    _check(load().hts_profile_end(arr, 64, ctypes.byref(n)))
+    return {arr[i].name.decode(): (arr[i].total_ms, arr[i].launches) for i in range(n.value)}

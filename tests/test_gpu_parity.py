@@ -1,0 +1,187 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle.
+
+Bars (from the method's statement of the problem and the build's contract):
+  * grouping: index sets and their order bit-exact (ties -> lowest index);
+  * bases: eigenvalues to 1e-10 of the largest, eigenvectors |<u, u'>| > 1 - 1e-9
+    where the eigen-gap exceeds 1e-6 (relative);
+  * noise level: sigma to 1e-9 relative, identical vote outcome;
+  * denoised pixels: max |gpu - oracle| <= 1e-3 on the [0, 255] scale and
+    |PSNR(gpu) - PSNR(oracle)| <= 0.01 dB.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2512_23569_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MAX_ABS = 1e-3
+PSNR_TOL = 0.01
+
+
+@pytest.fixture(scope="module")
+def hts():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2512_23569_gb300 import build, hts as h
+
+    build.build()
+    h.load()
+    return h
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _params(o, hts, **kw):
+    po = o.Params(**kw)
+    ph = hts.params(**{k: (0.0 if (k == "gamma_rank" and v is None) else v) for k, v in kw.items()})
+    return po, ph
+
+
+MATCH_CASES = [
+    # H, W, C, win, K, sigma, seed
+    (128, 128, 1, 21, 16, 25.0, 1000),   # grayscale 128x128 workload
+    (77, 93, 1, 21, 16, 25.0, 11),       # ragged grid (last row/column off the step)
+    (64, 80, 3, 31, 16, 50.0, 2000),     # colour, GCP switch
+    (45, 61, 3, 15, 8, 30.0, 12),
+    (40, 40, 1, 7, 4, 10.0, 13),
+    (48, 56, 3, 11, 32, 20.0, 14),
+    (16, 16, 1, 5, 2, 5.0, 15),
+    (11, 11, 1, 7, 16, 5.0, 16),         # smallest image with 16 positions in a window
+]
+
+
+@pytest.mark.parametrize("H,W,C,win,K,sigma,seed", MATCH_CASES)
+def test_match_bit_exact(oracle, hts, H, W, C, win, K, sigma, seed):
+    clean, noisy = synth.make_config_image(H, W, C, sigma, seed)
+    po, ph = _params(oracle, hts, K=K, win=win)
+    want, green_want, _ = oracle.match(noisy, po)
+    idx, green = hts.match(_dev(noisy), ph)
+    np.testing.assert_array_equal(idx.cpu().numpy(), want)
+    np.testing.assert_array_equal(green.cpu().numpy(), green_want)
+
+
+@pytest.mark.parametrize("C", [1, 3])
+def test_match_ties_and_flat(oracle, hts, C):
+    """Noiseless flat and integer images: massive exact ties resolved by index."""
+    po, ph = _params(oracle, hts, K=8, win=9)
+    flat = np.full((C, 24, 28), 7.0, dtype=np.float32)
+    idx, _ = hts.match(_dev(flat), ph)
+    np.testing.assert_array_equal(idx.cpu().numpy(), oracle.match(flat, po)[0])
+    ints = np.random.default_rng(3).integers(0, 4, size=(C, 24, 28)).astype(np.float32)
+    idx, _ = hts.match(_dev(ints), ph)
+    np.testing.assert_array_equal(idx.cpu().numpy(), oracle.match(ints, po)[0])
+
+
+@pytest.mark.parametrize("C,H,W", [(1, 64, 72), (3, 96, 80)])
+def test_basis_parity(oracle, hts, C, H, W):
+    _, noisy = synth.make_config_image(H, W, C, 20.0, 30 + C)
+    po, ph = _params(oracle, hts)
+    b_want, ev_want, _ = oracle.estimate_basis(noisy, po)
+    b, ev = hts.estimate_basis(_dev(noisy), ph).read()
+    scale = np.max(np.abs(ev_want))
+    np.testing.assert_allclose(ev, ev_want, rtol=0, atol=1e-10 * scale)
+    for j in range(b.shape[0]):
+        for m in range(2):
+            U, Uw, lam = b[j, m], b_want[j, m], ev_want[j, m]
+            np.testing.assert_allclose(U.conj().T @ U, np.eye(8), atol=1e-12)
+            for i in range(8):
+                gap = min([abs(lam[i] - lam[q]) for q in range(8) if q != i])
+                if gap > 1e-6 * scale:
+                    assert abs(np.vdot(Uw[:, i], U[:, i])) > 1 - 1e-9, (j, m, i)
+
+
+@pytest.mark.parametrize("C,H,W,sigma,win", [(1, 128, 128, 25.0, 21), (3, 128, 160, 50.0, 31), (3, 96, 96, 10.0, 15)])
+def test_sigma_parity(oracle, hts, C, H, W, sigma, win):
+    _, noisy = synth.make_config_image(H, W, C, sigma, 40 + C)
+    po, ph = _params(oracle, hts, win=win)
+    want = oracle.estimate_sigma(noisy, po)
+    s, info = hts.estimate_sigma(_dev(noisy), ph)
+    assert abs(info["sigma_est"] / want["sigma_est"] - 1) < 1e-9
+    assert abs(s / want["sigma_hat"] - 1) < 1e-9
+    assert info["votes"] == want["votes"]
+    assert bool(info["adjusted"]) == want["adjust"]
+
+
+def _compare(out, want, clean):
+    out = out.astype(np.float64)
+    err = np.max(np.abs(out - want))
+    assert err <= MAX_ABS, err
+    dp = abs(synth.psnr(out, clean) - synth.psnr(want, clean))
+    assert dp <= PSNR_TOL, dp
+    return err
+
+
+DENOISE_CASES = [
+    (128, 128, 1, 21, 16, 25.0, 1000),
+    (77, 93, 1, 21, 16, 25.0, 21),
+    (96, 112, 3, 31, 16, 50.0, 2000),
+    (45, 61, 3, 15, 8, 30.0, 22),
+    (40, 48, 1, 7, 4, 60.0, 23),
+    (48, 56, 3, 11, 32, 20.0, 24),
+    (24, 24, 3, 5, 2, 15.0, 25),
+]
+
+
+@pytest.mark.parametrize("H,W,C,win,K,sigma,seed", DENOISE_CASES)
+def test_denoise_parity_same_basis(oracle, hts, H, W, C, win, K, sigma, seed):
+    """Known sigma, the oracle's basis fed to both sides."""
+    clean, noisy = synth.make_config_image(H, W, C, sigma, seed)
+    po, ph = _params(oracle, hts, K=K, win=win)
+    basis, ev, _ = oracle.estimate_basis(noisy, po)
+    want, _ = oracle.denoise(noisy, po, sigma=sigma, basis=basis)
+    out = hts.denoise(_dev(noisy), sigma=sigma, basis=hts.Basis.from_array(basis, ev), p=ph)
+    _compare(out.cpu().numpy(), want, clean)
+
+
+@pytest.mark.parametrize("H,W,C,win,sigma,seed", [(128, 128, 1, 21, 25.0, 1001), (160, 144, 3, 31, 50.0, 2001)])
+def test_denoise_parity_end_to_end(oracle, hts, H, W, C, win, sigma, seed):
+    """Unknown sigma and globally-learned basis, each side estimating its own."""
+    clean, noisy = synth.make_config_image(H, W, C, sigma, seed)
+    po, ph = _params(oracle, hts, win=win)
+    want, info = oracle.denoise(noisy, po)
+    out = hts.denoise(_dev(noisy), sigma=None, p=ph)
+    st = hts.last_stats()
+    assert abs(st["sigma"] / info["sigma"] - 1) < 1e-9
+    _compare(out.cpu().numpy(), want, clean)
+
+
+def test_zero_threshold_reconstructs_input(hts):
+    _, noisy = synth.make_config_image(64, 72, 3, 30.0, 50)
+    out = hts.denoise(_dev(noisy), sigma=0.0, p=hts.params(win=15))
+    assert np.max(np.abs(out.cpu().numpy() - noisy)) < 1e-3
+
+
+def test_host_api_and_batch_match_device_call(hts):
+    imgs = [synth.make_config_image(64, 64, 1, 20.0, 60)[1], synth.make_config_image(48, 80, 3, 35.0, 61)[1]]
+    p = hts.params(win=15)
+    dev = [hts.denoise(_dev(x), sigma=None, p=p).cpu().numpy() for x in imgs]
+    host = [hts.denoise_host(np.ascontiguousarray(x), sigma=None, p=p) for x in imgs]
+    batch = [o.cpu().numpy() for o in hts.denoise_batch([_dev(x) for x in imgs], [None, None], p)]
+    for a, b, c in zip(dev, host, batch):
+        np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(a, c)
+
+
+def test_deterministic(hts):
+    _, noisy = synth.make_config_image(96, 96, 3, 40.0, 70)
+    x = _dev(noisy)
+    p = hts.params(win=21)
+    a = hts.denoise(x, sigma=None, p=p).cpu().numpy()
+    b = hts.denoise(x, sigma=None, p=p).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+
+
+def test_basis_save_load_roundtrip(hts, tmp_path):
+    _, noisy = synth.make_config_image(64, 64, 3, 20.0, 80)
+    b = hts.estimate_basis(_dev(noisy), hts.params())
+    path = str(tmp_path / "b.htsb")
+    b.save(path)
+    b2 = hts.Basis.load_file(path)
+    u1, e1 = b.read()
+    u2, e2 = b2.read()
+    np.testing.assert_array_equal(u1, u2)
+    np.testing.assert_array_equal(e1, e2)
