@@ -105,7 +105,8 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.5)  # let the sampler come up before the timed region
         except Exception:
             self.proc = None
 
@@ -162,7 +163,7 @@ def _oracle_params():
     return o.Params(K=w["K"], win=w["win"], step=w["step"])
 
 
-def cpu_baseline(noisy, min_seconds=10.0, max_runs=3):
+def cpu_baseline(noisy, min_seconds=10.0, max_runs=10):
     """The FP64 oracle as it stands, on the host cores, full image, >= min_seconds of work."""
     from oracle import hts_oracle as o
 
@@ -335,6 +336,7 @@ def run_ours(args):
         "psnr_delta_db": None if psnr_oracle is None else synth.psnr(den, clean) - psnr_oracle,
         "sigma_hat": stats["sigma"], "redo_groups": stats["filter_redo"], "exact_coefs": stats["filter_exact"],
         "match_reranked": stats["match_reranked"], "match_fallback": stats["match_fallback"],
+        "vote_uncertain": stats["vote_uncertain"],
     }
     print(json.dumps(line))
     if world > 1:
@@ -369,7 +371,7 @@ def _committed_traffic(kernel):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")

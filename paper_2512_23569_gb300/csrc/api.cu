@@ -14,7 +14,6 @@
 
 #include "hts_internal.h"
 
-struct hts_basis : hts::hts_basis_dev {};
 
 namespace hts {
 
@@ -69,6 +68,8 @@ static hts_status fail(hts_status s, const std::string &msg) {
     g_err = msg;
     return s;
 }
+
+hts_status report(hts_status s, const char *msg) { return fail(s, msg); }
 
 hts_status check_launch(const char *what) {
     const cudaError_t e = cudaGetLastError();
@@ -164,7 +165,7 @@ static hts_status ensure(Workspace *w, const Geom &g) {
 
 // ----------------------------------------------------------- validation
 
-static hts_status validate(int H, int W, int C, const hts_params *p, Geom *g) {
+hts_status validate(int H, int W, int C, const hts_params *p, Geom *g) {
     if (!p) return fail(HTS_EINVAL, "params is NULL");
     if (p->ps != PS) return fail(HTS_EUNSUPPORTED, "only ps = 8 is built");
     if (C != 1 && C != 3) return fail(HTS_EINVAL, "C must be 1 or 3");
@@ -254,7 +255,7 @@ static hts_status prepare(const float *img, const Geom &g, const hts_params &p, 
     return HTS_OK;
 }
 
-static hts_status check_basis(const hts_basis *basis, int C) {
+hts_status check_basis(const hts_basis *basis, int C) {
     if (!basis) return HTS_OK;
     if (basis->C != C) return fail(HTS_EINVAL, "basis was built for another channel count");
     int dev = 0;

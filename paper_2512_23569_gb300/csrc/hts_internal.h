@@ -61,6 +61,10 @@ __host__ __device__ __forceinline__ int grid_pos(int i, int n, int step) {
     return p < n - PS ? p : n - PS;
 }
 
+// Argument checks and error reporting shared by the entry points (api.cu).
+hts_status validate(int H, int W, int C, const hts_params *p, Geom *g);
+hts_status report(hts_status s, const char *msg);
+
 // Launch bookkeeping (defined in api.cu).  Every kernel launch sits inside a
 // KTimer scope: it counts the launch and, while profiling is on, records a
 // CUDA event before and after it on the launch stream.
@@ -91,4 +95,11 @@ hts_status launch_set_sigma(double sigma, const Geom &g, const hts_params &p, De
 hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, const double *b64, const float *b32,
                          long long *acc, int *wcount, int32_t *redo_list, DevState *st, float *out, cudaStream_t s);
 
+}  // namespace hts
+
+// The opaque handle of the public header.
+struct hts_basis : hts::hts_basis_dev {};
+
+namespace hts {
+hts_status check_basis(const hts_basis *basis, int C);
 }  // namespace hts
