@@ -131,6 +131,26 @@ hts_status hts_estimate_sigma(const float *img, int H, int W, int C, const hts_b
 hts_status hts_denoise(const float *noisy, float *out, int H, int W, int C, float sigma,
                        const hts_basis *basis, const hts_params *p, void *stream);
 
+/* hts_denoise without any device allocation, for callers that may not
+ * allocate device memory once they are running: for example a plugin inside
+ * a host application that owns the whole device memory budget and forbids
+ * cudaMalloc after start-up, or a latency-critical loop that cannot afford
+ * the implicit device synchronisation of cudaMalloc / cudaFree.  The paper
+ * has no counterpart; this is a deployment variant of hts_denoise.
+ * All intermediate buffers live in one static device array of the library
+ * (about 14 MB, held by every GPU that loads the library until the process
+ * exits).  That bounds the image: H*W <= 262144 pixels, at most 65536
+ * reference patches and N_ref*K <= 1048576; larger images return HTS_EINVAL
+ * before any device work.  The caller still passes `noisy` and `out` (device);
+ * every other argument and the result are as for hts_denoise.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress):
+ * make that first call before any stream capture.  All calls share the one
+ * array and each overwrites what the previous call left there, so calls that
+ * overlap on the GPU (other streams, or host threads without ordering) race
+ * and corrupt each other's results; serialise them.  Asynchronous. */
+hts_status hts_denoise_noalloc(const float *noisy, float *out, int H, int W, int C, float sigma,
+                               const hts_basis *basis, const hts_params *p, void *stream);
+
 /* hts_denoise on HOST buffers: copies noisy_host to the device, denoises and
  * copies the result back into out_host, all on `stream`, then synchronises.
  * Pinned host memory is fastest but not required. */

@@ -28,6 +28,7 @@ EXPORTS = [
     "hts_basis_save", "hts_basis_load", "hts_estimate_sigma", "hts_denoise", "hts_denoise_host",
     "hts_denoise_batch", "hts_match", "hts_num_refs", "hts_last_stats", "hts_last_error",
     "hts_launch_count", "hts_version", "hts_shutdown", "hts_profile_begin", "hts_profile_end",
+    "hts_denoise_noalloc",
 ]
 
 
@@ -86,6 +87,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.hts_estimate_sigma.argtypes = [P, I, I, I, P, PP, ctypes.POINTER(D), ctypes.POINTER(SigmaInfo), P]
         lib.hts_denoise.argtypes = [P, P, I, I, I, F, P, PP, P]
         lib.hts_denoise_host.argtypes = [P, P, I, I, I, F, P, PP, P]
+        lib.hts_denoise_noalloc.argtypes = [P, P, I, I, I, F, P, PP, P]
         lib.hts_denoise_batch.argtypes = [ctypes.POINTER(Image), I, PP, P]
         lib.hts_match.argtypes = [P, I, I, I, PP, P, P, P]
         lib.hts_num_refs.argtypes = [I, I, PP]
@@ -249,6 +251,22 @@ def denoise(noisy, sigma: float | None = None, basis: Basis | None = None, p: Pa
     s = -1.0 if sigma is None else float(sigma)
     _check(load().hts_denoise(ctypes.c_void_p(noisy.data_ptr()), ctypes.c_void_p(out.data_ptr()), H, W, C, s,
                               basis.handle if basis else None, ctypes.byref(p), _stream(stream)))
+    return out
+
+
+def denoise_noalloc(noisy, sigma: float | None = None, basis: Basis | None = None, p: Params | None = None,
+                    out=None, stream=None):
+    """hts_denoise_noalloc: like denoise(), with the library's static scratch instead of allocations."""
+    import torch
+
+    noisy = _chw(noisy)
+    p = p or params()
+    C, H, W = noisy.shape
+    if out is None:
+        out = torch.empty_like(noisy)
+    s = -1.0 if sigma is None else float(sigma)
+    _check(load().hts_denoise_noalloc(ctypes.c_void_p(noisy.data_ptr()), ctypes.c_void_p(out.data_ptr()), H, W, C,
+                                      s, basis.handle if basis else None, ctypes.byref(p), _stream(stream)))
     return out
 
 
