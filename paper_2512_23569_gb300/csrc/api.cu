@@ -108,6 +108,8 @@ struct Workspace {
     double *eig = nullptr;
     DevState *st = nullptr;
     float *io_in = nullptr, *io_out = nullptr;
+    cudaStream_t aux = nullptr;  // second stream: basis and noise floor overlap the grouping
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 static std::mutex g_mu;
@@ -142,6 +144,9 @@ static hts_status get_ws(cudaStream_t s, Workspace **out) {
     if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&w->b64), 2 * 256 * sizeof(double)), "cudaMalloc");
     if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&w->b32), 2 * 256 * sizeof(float)), "cudaMalloc");
     if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&w->eig), 4 * 8 * sizeof(double)), "cudaMalloc");
+    if (st == HTS_OK) st = cuda_ok(cudaStreamCreateWithFlags(&w->aux, cudaStreamNonBlocking), "cudaStreamCreate");
+    if (st == HTS_OK) st = cuda_ok(cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
+    if (st == HTS_OK) st = cuda_ok(cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming), "cudaEventCreate");
     if (st != HTS_OK) {
         delete w;
         return st;
@@ -264,18 +269,36 @@ hts_status check_basis(const hts_basis *basis, int C) {
     return HTS_OK;
 }
 
+// The global basis (k_cov, k_cov_sum, k_jacobi) and the noise floor depend
+// only on the reference patches, the grouping and the rank vote only on the
+// image: the first chain runs on the workspace's second stream while the
+// second runs on the caller's stream; the threshold waits for both.
 static hts_status denoise_impl(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
                                const hts_params &p, Workspace *w, cudaStream_t s) {
     HTS_TRY(ensure(w, g));
-    BasisRef br;
-    HTS_TRY(prepare(noisy, g, p, basis, sigma < 0, w, s, &br));
     const size_t hw = (size_t)g.H * g.W;
+    HTS_TRY(cuda_ok(cudaMemsetAsync(w->st, 0, sizeof(DevState), s), "cudaMemsetAsync(state)"));
     HTS_TRY(cuda_ok(cudaMemsetAsync(w->acc, 0, hw * g.C * sizeof(long long), s), "cudaMemsetAsync(acc)"));
     HTS_TRY(cuda_ok(cudaMemsetAsync(w->wcount, 0, hw * sizeof(int), s), "cudaMemsetAsync(weights)"));
+    const bool need_sigma = sigma < 0;
+    const bool est = (basis == nullptr) || (need_sigma && !basis->has_eig);
+    const double *b64 = basis ? basis->b64 : w->b64;
+    const float *b32 = basis ? basis->b32 : w->b32;
+    const double *eig = (basis && basis->has_eig) ? basis->eig : w->eig;
+    const bool fork = est || need_sigma;
+    if (fork) {
+        HTS_TRY(cuda_ok(cudaEventRecord(w->ev_fork, s), "cudaEventRecord"));
+        HTS_TRY(cuda_ok(cudaStreamWaitEvent(w->aux, w->ev_fork, 0), "cudaStreamWaitEvent"));
+        if (est) HTS_TRY(launch_basis(noisy, g, w->cov, w->b64, w->b32, w->eig, w->aux));
+        if (need_sigma) HTS_TRY(launch_sigma_floor(g, p, eig, w->st, w->aux));
+        HTS_TRY(cuda_ok(cudaEventRecord(w->ev_join, w->aux), "cudaEventRecord"));
+    }
     HTS_TRY(launch_match(noisy, g, p.gamma_gcp, w->idx, w->green, w->fb, w->st, s));
-    if (sigma < 0) HTS_TRY(launch_sigma(noisy, g, p, br.eig, w->idx, w->st, s));
+    if (need_sigma && p.adjust_rank) HTS_TRY(launch_sigma_vote(noisy, g, p, w->idx, w->redo, w->st, s));
+    if (fork) HTS_TRY(cuda_ok(cudaStreamWaitEvent(s, w->ev_join, 0), "cudaStreamWaitEvent"));
+    if (need_sigma) HTS_TRY(launch_sigma_final(g, p, w->st, s));
     else HTS_TRY(launch_set_sigma((double)sigma, g, p, w->st, s));
-    return launch_filter(noisy, g, w->idx, br.b64, br.b32, w->acc, w->wcount, w->redo, w->st, out, s);
+    return launch_filter(noisy, g, w->idx, b64, b32, w->acc, w->wcount, w->redo, w->st, out, s);
 }
 
 }  // namespace hts
@@ -446,7 +469,7 @@ hts_status hts_estimate_sigma(const float *img, int H, int W, int C, const hts_b
     BasisRef br;
     HTS_TRY(prepare(img, g, *p, basis, true, w, s, &br));
     if (p->adjust_rank) HTS_TRY(launch_match(img, g, p->gamma_gcp, w->idx, w->green, w->fb, w->st, s));
-    HTS_TRY(launch_sigma(img, g, *p, br.eig, w->idx, w->st, s));
+    HTS_TRY(launch_sigma(img, g, *p, br.eig, w->idx, w->redo, w->st, s));
     DevState hs;
     HTS_TRY(cuda_ok(cudaMemcpyAsync(&hs, w->st, sizeof(DevState), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync"));
     HTS_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
@@ -604,6 +627,9 @@ hts_status hts_shutdown(void) {
         cudaFree(w->st);
         cudaFree(w->io_in);
         cudaFree(w->io_out);
+        if (w->ev_fork) cudaEventDestroy(w->ev_fork);
+        if (w->ev_join) cudaEventDestroy(w->ev_join);
+        if (w->aux) cudaStreamDestroy(w->aux);
         cudaSetDevice(prev);
         delete w;
     }

@@ -1,22 +1,20 @@
 // Collaborative filtering and aggregation of Haar-tSVD (Eq. 19-21, Alg. 1
 // steps 2-3) on sm_103a.
 //
-// Layout of the work: a warp holds G = 32/K groups (one for K = 32); lane
-// (g, k) owns patch k of group g during the patch phases.  A group's
-// coefficients live in shared memory as [stream e][patch k] with a padded
-// row (K+1 floats) so that both the patch-major writes and the stream-major
-// reads of the Haar phase are bank-conflict free.
-//
-//   patch phase   : gather the patch (FP32), unitary DFT along channels
-//                   (c = 3), Shat^(j) = U^(j)^H Phat^(j) V^(j) per stored
-//                   Fourier slice (Eq. 19, slice 3 = conj of slice 2);
-//   stream phase  : fast Haar transform along the group axis in registers
-//                   (Eq. 8 row order), hard threshold |s| >= tau (Eq. 20;
-//                   modulus for complex coefficients), inverse Haar;
-//   patch phase   : U Shat V^H, inverse DFT (Eq. 21), and aggregation as
-//                   exact fixed-point integer sums (value * 2^24 rounded to
-//                   int64) plus an integer weight per pixel, so the result
-//                   does not depend on the order of the additions.
+// Main pass (k_filter_tile): a 512-thread block owns a tile of reference
+// patches and keeps 64 group members in flight, eight threads per patch, one
+// thread per patch row.  The separable projection Shat = U^H Phat V (Eq. 19,
+// per stored Fourier slice of mode 3; slice 3 = conj of slice 2) is split in
+// its two 8x8 factors: each thread forms its row of Phat V, the rows meet in
+// shared memory, and each thread forms its row of U^H (Phat V).  The Haar
+// transform along the group axis (Eq. 8 row order), hard thresholding
+// (Eq. 20; modulus for complex coefficients) and the inverse Haar run one
+// coefficient stream per thread from a patch-major buffer; the inverse
+// projection (Eq. 21) mirrors the forward one.  Estimates are aggregated
+// (Alg. 1 step 3) as exact fixed-point integers (value * 2^16, rounded) into
+// shared-memory accumulators that cover the tile's whole search region, and
+// flushed to the image-wide int64 sums once per tile.  Integer sums do not
+// depend on the order of the additions, so the result is deterministic.
 //
 // Threshold decisions are taken in FP64 where FP32 cannot certify them: the
 // FP32 coefficient of a group G differs from the exact one by at most
@@ -24,9 +22,11 @@
 // per-stage bounds of the DFT, the two 8x8 products with rounded bases and
 // the Haar butterflies; the stages are unitary so errors do not grow).  A
 // group with any coefficient inside that band around tau is not aggregated
-// by the main pass; a second pass recomputes it, evaluates each in-band
+// by the main pass; k_filter_exact recomputes it, evaluates each in-band
 // coefficient in FP64 from the input pixels and the FP64 basis (one warp per
 // coefficient), and takes the decision there.
+#include <algorithm>
+
 #include "hts_internal.h"
 
 namespace hts {
@@ -49,7 +49,7 @@ struct SBasis {
 
 struct FilterArgs {
     const float *img;
-    int H, W, step, nx, nref;
+    int H, W, step, R, nx, ny, nref;
     const int32_t *idx;
     const double *b64;
     const float *b32;
@@ -377,34 +377,40 @@ __device__ void exact_coef(const FilterArgs &a, const int32_t *grp, int K, int h
     im = si;
 }
 
-// ---------------------------------------------------------------- kernel
+// ---------------------------------------------------------------- kernels
 
 template <int C>
 struct Cfg {
     static constexpr int NCOEF = (C == 3) ? 192 : 64;  // real streams per patch
-    static constexpr int IPG = (C == 3) ? 128 : 64;    // stream items per group
+    static constexpr int IPG = (C == 3) ? 128 : 64;    // stream items per group (complex pairs count once)
 };
 
-template <int C, int K, bool REDO>
-__global__ void __launch_bounds__(64) k_filter(FilterArgs a) {
-    constexpr int G = REDO ? 1 : (32 / K > 0 ? 32 / K : 1);
+// Fixed-point aggregation: value * 2^16 rounded to int64 (|value| < 2^31).
+__device__ __forceinline__ long long fix16(float v) { return __float2ll_rn(v * 65536.0f); }
+
+// ---------------------------------------------------------- exact pass
+
+// One group per warp (lane k < K owns patch k), groups taken from the redo
+// list of the main pass.  FP32 forward; every coefficient inside the guard
+// band is re-evaluated in FP64 by the whole warp and decided there; FP32
+// inverse; global integer aggregation.
+template <int C, int K>
+__global__ void __launch_bounds__(64) k_filter_exact(FilterArgs a) {
     constexpr int NCOEF = Cfg<C>::NCOEF;
     constexpr int IPG = Cfg<C>::IPG;
     constexpr int ROW = K + 1;
-    constexpr int GS0 = NCOEF * ROW;
-    constexpr int GS = GS0 + ((K - GS0 % 32) % 32 + 32) % 32;  // group stride = K (mod 32)
+    constexpr int GS = NCOEF * ROW;
     constexpr int NWARPS = 2;
     constexpr int NMASK = (NCOEF * K + 31) / 32;
+    constexpr int WS = GS + 1 + NMASK + QCAP + 1;  // words per warp
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SBasis &sb = *reinterpret_cast<SBasis *>(smem_raw);
-    float *wsm = reinterpret_cast<float *>(smem_raw + sizeof(SBasis));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *coef = wsm + warp * (G * GS + 2 * G + (REDO ? NMASK + QCAP + 2 : 0));
-    float *gband = coef + G * GS;            // per-group guard band
-    int *gflag = reinterpret_cast<int *>(gband + G);
-    unsigned *mask = reinterpret_cast<unsigned *>(gflag + G);  // REDO: decided coefficients
-    int *queue = reinterpret_cast<int *>(mask + NMASK);        // REDO: in-band queue
+    float *coef = reinterpret_cast<float *>(smem_raw + sizeof(SBasis)) + warp * WS;
+    float *gband = coef + GS;
+    unsigned *mask = reinterpret_cast<unsigned *>(gband + 1);
+    int *queue = reinterpret_cast<int *>(mask + NMASK);
     int *qcount = queue + QCAP;
 
     load_basis<C>(sb, a.b32);
@@ -412,30 +418,20 @@ __global__ void __launch_bounds__(64) k_filter(FilterArgs a) {
 
     const float tau = a.st->tau32;
     const double tau64 = a.st->tau;
-    const int gl = (REDO || K >= 32) ? 0 : (lane / K);
-    const int k = lane % K;
+    const int k = lane;
+    const bool active = lane < K;
     const size_t HW = (size_t)a.H * a.W;
-
-    int nunits;
-    if (REDO) nunits = *(volatile int *)&a.st->filter_redo;
-    else nunits = (a.nref + G - 1) / G;
+    const int nunits = *(volatile int *)&a.st->filter_redo;
 
     for (int wu = blockIdx.x * NWARPS + warp; wu < nunits; wu += gridDim.x * NWARPS) {
-        int r;
-        if (REDO) r = a.redo[wu];
-        else r = wu * G + gl;
-        const bool active = REDO ? (lane < K) : (r < a.nref);
-        float *cg = coef + gl * GS;
-        const int32_t *grp = a.idx + (size_t)((REDO || active) ? r : 0) * K;
+        const int r = a.redo[wu];
+        const int32_t *grp = a.idx + (size_t)r * K;
         int py = 0, px = 0;
         float ss = 0.f;
         if (active) {
             const int pos = grp[k];
             py = pos / a.W;
             px = pos - py * a.W;
-        }
-        // ---- patch phase: forward projection per slice
-        if (active) {
             const float *base = a.img + (size_t)py * a.W + px;
             float P[64];
 #pragma unroll
@@ -457,7 +453,7 @@ __global__ void __launch_bounds__(64) k_filter(FilterArgs a) {
                 }
             fwd_real(P, sb.u0, sb.v0);
 #pragma unroll
-            for (int e = 0; e < 64; ++e) cg[e * ROW + k] = P[e];
+            for (int e = 0; e < 64; ++e) coef[e * ROW + k] = P[e];
             if (C == 3) {
                 float Pr[64], Pi[64];
 #pragma unroll
@@ -472,205 +468,136 @@ __global__ void __launch_bounds__(64) k_filter(FilterArgs a) {
                 fwd_cplx(Pr, Pi, sb);
 #pragma unroll
                 for (int e = 0; e < 64; ++e) {
-                    cg[(64 + e) * ROW + k] = Pr[e];
-                    cg[(128 + e) * ROW + k] = Pi[e];
+                    coef[(64 + e) * ROW + k] = Pr[e];
+                    coef[(128 + e) * ROW + k] = Pi[e];
                 }
             }
         }
-        // group norm -> guard band
 #pragma unroll
-        for (int o = 1; o < K && o < 32; o <<= 1) ss += __shfl_xor_sync(FULL, ss, o);
-        if (k == 0 && active) {
-            const float gb = (C == 3 ? 320.f : 160.f) * U32 * sqrtf(ss) * 1.01f + 2.f * U32 * tau;
-            gband[gl] = gb;
-            gflag[gl] = 0;
-        }
-        if (REDO && lane == 0) {
+        for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(FULL, ss, o);
+        if (lane == 0) {
+            *gband = (C == 3 ? 320.f : 160.f) * U32 * sqrtf(ss) * 1.01f + 2.f * U32 * tau;
             *qcount = 0;
             for (int q = 0; q < NMASK; ++q) mask[q] = 0u;
         }
         __syncwarp();
 
-        // ---- stream phase: Haar, threshold, inverse Haar
-        if (!REDO) {
+        // pass 1: forward Haar only; coefficients stay unthresholded
 #pragma unroll 1
-            for (int t = lane; t < G * IPG; t += 32) {
-                const int g = t / IPG, it = t - g * IPG;
-                const int rg = wu * G + g;
-                if (rg >= a.nref) continue;
-                float *cgg = coef + g * GS;
-                const float band = gband[g];
-                int flag = 0;
-                if (it < 64) {
-                    float x[K];
+        for (int t = lane; t < IPG; t += 32) {
+            if (t < 64) {
+                float x[K];
 #pragma unroll
-                    for (int q = 0; q < K; ++q) x[q] = cgg[it * ROW + q];
-                    haar_fwd<K>(x);
+                for (int q = 0; q < K; ++q) x[q] = coef[t * ROW + q];
+                haar_fwd<K>(x);
 #pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        const int d = decide(fabsf(x[q]), tau, band);
-                        flag |= (d == 2);
-                        x[q] = (d == 0) ? 0.f : x[q];
-                    }
-                    haar_inv<K>(x);
+                for (int q = 0; q < K; ++q) coef[t * ROW + q] = x[q];
+            } else {
+                const int e = t - 64;
+                float xr[K], xi[K];
 #pragma unroll
-                    for (int q = 0; q < K; ++q) cgg[it * ROW + q] = x[q];
-                } else {
-                    const int e = it - 64;
-                    float xr[K], xi[K];
-#pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        xr[q] = cgg[(64 + e) * ROW + q];
-                        xi[q] = cgg[(128 + e) * ROW + q];
-                    }
-                    haar_fwd<K>(xr);
-                    haar_fwd<K>(xi);
-#pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        const float mag = sqrtf(xr[q] * xr[q] + xi[q] * xi[q]);
-                        const int d = decide(mag, tau, band);
-                        flag |= (d == 2);
-                        if (d == 0) { xr[q] = 0.f; xi[q] = 0.f; }
-                    }
-                    haar_inv<K>(xr);
-                    haar_inv<K>(xi);
-#pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        cgg[(64 + e) * ROW + q] = xr[q];
-                        cgg[(128 + e) * ROW + q] = xi[q];
-                    }
+                for (int q = 0; q < K; ++q) {
+                    xr[q] = coef[(64 + e) * ROW + q];
+                    xi[q] = coef[(128 + e) * ROW + q];
                 }
-                if (flag) gflag[g] = 1;
-            }
-        } else {
-            // pass 1: forward Haar only; coefficients stay unthresholded
-#pragma unroll 1
-            for (int t = lane; t < IPG; t += 32) {
-                float *cgg = coef;
-                if (t < 64) {
-                    float x[K];
+                haar_fwd<K>(xr);
+                haar_fwd<K>(xi);
 #pragma unroll
-                    for (int q = 0; q < K; ++q) x[q] = cgg[t * ROW + q];
-                    haar_fwd<K>(x);
-#pragma unroll
-                    for (int q = 0; q < K; ++q) cgg[t * ROW + q] = x[q];
-                } else {
-                    const int e = t - 64;
-                    float xr[K], xi[K];
-#pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        xr[q] = cgg[(64 + e) * ROW + q];
-                        xi[q] = cgg[(128 + e) * ROW + q];
-                    }
-                    haar_fwd<K>(xr);
-                    haar_fwd<K>(xi);
-#pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        cgg[(64 + e) * ROW + q] = xr[q];
-                        cgg[(128 + e) * ROW + q] = xi[q];
-                    }
-                }
-            }
-            __syncwarp();
-            const float band = gband[0];
-            // rounds: queue undecided in-band coefficients, decide them in FP64
-            for (int round = 0; round < NCOEF * K; ++round) {
-                if (lane == 0) *qcount = 0;
-                __syncwarp();
-                for (int t = lane; t < IPG * K; t += 32) {
-                    const int it = t / K, q = t - it * K;
-                    const int bit = it * K + q;
-                    if (mask[bit >> 5] & (1u << (bit & 31))) continue;
-                    float mag;
-                    if (it < 64) mag = fabsf(coef[it * ROW + q]);
-                    else {
-                        const float xr = coef[(it) * ROW + q], xi = coef[(it + 64) * ROW + q];
-                        mag = sqrtf(xr * xr + xi * xi);
-                    }
-                    if (decide(mag, tau, band) != 2) continue;
-                    const int slot = atomicAdd(qcount, 1);
-                    if (slot < QCAP) queue[slot] = t;
-                }
-                __syncwarp();
-                const int nq = min(*qcount, QCAP);
-                if (nq == 0) break;
-                for (int s = 0; s < nq; ++s) {
-                    const int t = queue[s];
-                    const int it = t / K, q = t - it * K;
-                    const int j = it < 64 ? 0 : 1;
-                    const int e = it < 64 ? it : it - 64;
-                    double re, im;
-                    exact_coef<C>(a, grp, K, q, j, e, lane, re, im);
-                    const double mag = (j == 0) ? fabs(re) : sqrt(re * re + im * im);
-                    if (lane == 0) {
-                        const int bit = it * K + q;
-                        mask[bit >> 5] |= (1u << (bit & 31));
-                        if (!(mag >= tau64)) {
-                            if (it < 64) coef[it * ROW + q] = 0.f;
-                            else { coef[it * ROW + q] = 0.f; coef[(it + 64) * ROW + q] = 0.f; }
-                        }
-                        atomicAdd(&a.st->filter_exact, 1);
-                    }
-                    __syncwarp();
-                }
-            }
-            __syncwarp();
-            // pass 2: certain FP32 decisions for the rest, inverse Haar
-#pragma unroll 1
-            for (int t = lane; t < IPG; t += 32) {
-                if (t < 64) {
-                    float x[K];
-#pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        float v = coef[t * ROW + q];
-                        const int bit = t * K + q;
-                        const bool dec = mask[bit >> 5] & (1u << (bit & 31));
-                        if (!dec && decide(fabsf(v), tau, band) == 0) v = 0.f;
-                        x[q] = v;
-                    }
-                    haar_inv<K>(x);
-#pragma unroll
-                    for (int q = 0; q < K; ++q) coef[t * ROW + q] = x[q];
-                } else {
-                    const int e = t - 64;
-                    float xr[K], xi[K];
-#pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        float vr = coef[(64 + e) * ROW + q], vi = coef[(128 + e) * ROW + q];
-                        const int bit = t * K + q;
-                        const bool dec = mask[bit >> 5] & (1u << (bit & 31));
-                        if (!dec && decide(sqrtf(vr * vr + vi * vi), tau, band) == 0) { vr = 0.f; vi = 0.f; }
-                        xr[q] = vr;
-                        xi[q] = vi;
-                    }
-                    haar_inv<K>(xr);
-                    haar_inv<K>(xi);
-#pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        coef[(64 + e) * ROW + q] = xr[q];
-                        coef[(128 + e) * ROW + q] = xi[q];
-                    }
+                for (int q = 0; q < K; ++q) {
+                    coef[(64 + e) * ROW + q] = xr[q];
+                    coef[(128 + e) * ROW + q] = xi[q];
                 }
             }
         }
         __syncwarp();
-
-        // ---- flagged groups are finished by the exact pass
-        bool agg = active;
-        if (!REDO && active) {
-            if (gflag[gl]) {
-                agg = false;
-                if (k == 0) {
-                    const int pos = atomicAdd(&a.st->filter_redo, 1);
-                    a.redo[pos] = r;
+        const float band = *gband;
+        // rounds: queue undecided in-band coefficients, decide them in FP64
+        for (int round = 0; round < NCOEF * K; ++round) {
+            if (lane == 0) *qcount = 0;
+            __syncwarp();
+            for (int t = lane; t < IPG * K; t += 32) {
+                const int it = t / K, q = t - it * K;
+                const int bit = it * K + q;
+                if (mask[bit >> 5] & (1u << (bit & 31))) continue;
+                float mag;
+                if (it < 64) mag = fabsf(coef[it * ROW + q]);
+                else {
+                    const float xr = coef[it * ROW + q], xi = coef[(it + 64) * ROW + q];
+                    mag = sqrtf(xr * xr + xi * xi);
+                }
+                if (decide(mag, tau, band) != 2) continue;
+                const int slot = atomicAdd(qcount, 1);
+                if (slot < QCAP) queue[slot] = t;
+            }
+            __syncwarp();
+            const int nq = min(*qcount, QCAP);
+            if (nq == 0) break;
+            for (int sl = 0; sl < nq; ++sl) {
+                const int t = queue[sl];
+                const int it = t / K, q = t - it * K;
+                const int j = it < 64 ? 0 : 1;
+                const int e = it < 64 ? it : it - 64;
+                double re, im;
+                exact_coef<C>(a, grp, K, q, j, e, lane, re, im);
+                const double mag = (j == 0) ? fabs(re) : sqrt(re * re + im * im);
+                if (lane == 0) {
+                    const int bit = it * K + q;
+                    mask[bit >> 5] |= (1u << (bit & 31));
+                    if (!(mag >= tau64)) {
+                        coef[it * ROW + q] = 0.f;
+                        if (it >= 64) coef[(it + 64) * ROW + q] = 0.f;
+                    }
+                    atomicAdd(&a.st->filter_exact, 1);
+                }
+                __syncwarp();
+            }
+        }
+        __syncwarp();
+        // pass 2: certain FP32 decisions for the rest, inverse Haar
+#pragma unroll 1
+        for (int t = lane; t < IPG; t += 32) {
+            if (t < 64) {
+                float x[K];
+#pragma unroll
+                for (int q = 0; q < K; ++q) {
+                    float v = coef[t * ROW + q];
+                    const int bit = t * K + q;
+                    const bool dec = mask[bit >> 5] & (1u << (bit & 31));
+                    if (!dec && decide(fabsf(v), tau, band) == 0) v = 0.f;
+                    x[q] = v;
+                }
+                haar_inv<K>(x);
+#pragma unroll
+                for (int q = 0; q < K; ++q) coef[t * ROW + q] = x[q];
+            } else {
+                const int e = t - 64;
+                float xr[K], xi[K];
+#pragma unroll
+                for (int q = 0; q < K; ++q) {
+                    float vr = coef[(64 + e) * ROW + q], vi = coef[(128 + e) * ROW + q];
+                    const int bit = t * K + q;
+                    const bool dec = mask[bit >> 5] & (1u << (bit & 31));
+                    if (!dec && decide(sqrtf(vr * vr + vi * vi), tau, band) == 0) {
+                        vr = 0.f;
+                        vi = 0.f;
+                    }
+                    xr[q] = vr;
+                    xi[q] = vi;
+                }
+                haar_inv<K>(xr);
+                haar_inv<K>(xi);
+#pragma unroll
+                for (int q = 0; q < K; ++q) {
+                    coef[(64 + e) * ROW + q] = xr[q];
+                    coef[(128 + e) * ROW + q] = xi[q];
                 }
             }
         }
-        // ---- patch phase: inverse projection and aggregation
-        if (agg) {
+        __syncwarp();
+        if (active) {
             float P[64];
 #pragma unroll
-            for (int e = 0; e < 64; ++e) P[e] = cg[e * ROW + k];
+            for (int e = 0; e < 64; ++e) P[e] = coef[e * ROW + k];
             inv_real(P, sb.u0t, sb.v0t);
             long long *acc0 = a.acc + (size_t)py * a.W + px;
             int *wc = a.wcount + (size_t)py * a.W + px;
@@ -681,17 +608,17 @@ __global__ void __launch_bounds__(64) k_filter(FilterArgs a) {
                     for (int v = 0; v < 8; ++v) {
                         const size_t o = (size_t)u * a.W + v;
                         atomicAdd(reinterpret_cast<unsigned long long *>(acc0 + o),
-                                  (unsigned long long)__float2ll_rn(P[u * 8 + v] * FIX_SCALE));
+                                  (unsigned long long)fix16(P[u * 8 + v]));
                         atomicAdd(wc + o, 1);
                     }
             } else {
 #pragma unroll
-                for (int e = 0; e < 64; ++e) cg[e * ROW + k] = P[e];
+                for (int e = 0; e < 64; ++e) coef[e * ROW + k] = P[e];
                 float Pr[64], Pi[64];
 #pragma unroll
                 for (int e = 0; e < 64; ++e) {
-                    Pr[e] = cg[(64 + e) * ROW + k];
-                    Pi[e] = cg[(128 + e) * ROW + k];
+                    Pr[e] = coef[(64 + e) * ROW + k];
+                    Pi[e] = coef[(128 + e) * ROW + k];
                 }
                 inv_cplx(Pr, Pi, sb);
 #pragma unroll
@@ -699,17 +626,16 @@ __global__ void __launch_bounds__(64) k_filter(FilterArgs a) {
 #pragma unroll
                     for (int v = 0; v < 8; ++v) {
                         const int e = u * 8 + v;
-                        const float p0 = cg[e * ROW + k];
+                        const float p0 = coef[e * ROW + k];
                         const float R = (p0 + 2.f * Pr[e]) * K3F;
                         const float Gc = (p0 - Pr[e] - 2.f * S3H * Pi[e]) * K3F;
                         const float B = (p0 - Pr[e] + 2.f * S3H * Pi[e]) * K3F;
                         const size_t o = (size_t)u * a.W + v;
-                        atomicAdd(reinterpret_cast<unsigned long long *>(acc0 + o),
-                                  (unsigned long long)__float2ll_rn(R * FIX_SCALE));
+                        atomicAdd(reinterpret_cast<unsigned long long *>(acc0 + o), (unsigned long long)fix16(R));
                         atomicAdd(reinterpret_cast<unsigned long long *>(acc0 + HW + o),
-                                  (unsigned long long)__float2ll_rn(Gc * FIX_SCALE));
+                                  (unsigned long long)fix16(Gc));
                         atomicAdd(reinterpret_cast<unsigned long long *>(acc0 + 2 * HW + o),
-                                  (unsigned long long)__float2ll_rn(B * FIX_SCALE));
+                                  (unsigned long long)fix16(B));
                         atomicAdd(wc + o, 1);
                     }
             }
@@ -718,59 +644,510 @@ __global__ void __launch_bounds__(64) k_filter(FilterArgs a) {
     }
 }
 
-// out = sum / (2^24 * weight)
+// ------------------------------------------------------------ main pass
+
+constexpr int TPB = 512;       // threads per block
+constexpr int PPB = TPB / 8;   // patches in flight per block (8 threads per patch)
+// Coefficient e of a patch is stored at cpos(e) = e + 4 (e / 32): the 4-word
+// gap after every 32 coefficients puts the eight 8-float rows a thread block
+// writes at once into eight disjoint bank quads.  Row stride of the buffer:
+constexpr int CROW = 212;      // cpos(191) + 1 = 211, padded to a multiple of 4
+__device__ __forceinline__ int cpos(int e) { return e + 4 * (e >> 5); }
+// 8x8 basis copies indexed by a thread's own row use a 12-float row stride
+// (row r starts at bank 12 r mod 32: eight disjoint quads).
+constexpr int BROW = 12;
+
+struct TileArgs {
+    int ty, tx;          // reference patches per tile (grid units)
+    int nty, ntx, ntiles;
+    int rh_max, rw_max;  // bound of a tile's region (pixels)
+    int local;           // 1: aggregate in shared memory, 0: straight to the global sums
+};
+
+template <int C>
+struct TileCfg {
+    static constexpr int TW = (C == 3) ? 24 : 8;  // floats per row of the exchange buffer
+    static constexpr int RS = TW + 4;              // row stride (bank-shifted)
+    static constexpr int PSW = 8 * RS + 4;         // patch stride (bank-shifted)
+};
+
+// Row-indexed basis copies (row stride BROW) for the block-parallel factors.
+struct RBasis {
+    float u0[8 * BROW], u0t[8 * BROW];
+    float u1r[8 * BROW], u1i[8 * BROW], u1rt[8 * BROW], u1it[8 * BROW];
+};
+
+template <int C>
+__device__ void load_rbasis(RBasis &rb, const SBasis &sb) {
+    for (int t = threadIdx.x; t < 64; t += blockDim.x) {
+        const int r = t >> 3, c = t & 7;
+        rb.u0[r * BROW + c] = sb.u0[t];
+        rb.u0t[r * BROW + c] = sb.u0t[t];
+        if (C == 3) {
+            rb.u1r[r * BROW + c] = sb.u1r[t];
+            rb.u1i[r * BROW + c] = sb.u1i[t];
+            rb.u1rt[r * BROW + c] = sb.u1rt[t];
+            rb.u1it[r * BROW + c] = sb.u1it[t];
+        }
+    }
+}
+
+template <int C, int K>
+__global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t) {
+    constexpr int IPG = Cfg<C>::IPG;
+    constexpr int GPB = PPB / K;  // groups in flight
+    constexpr int TPG = 8 * K;    // threads per group
+    constexpr int RS = TileCfg<C>::RS;
+    constexpr int PSW = TileCfg<C>::PSW;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SBasis &sb = *reinterpret_cast<SBasis *>(smem_raw);
+    RBasis &rb = *reinterpret_cast<RBasis *>(smem_raw + sizeof(SBasis));
+    float *coef = reinterpret_cast<float *>(smem_raw + sizeof(SBasis) + sizeof(RBasis));  // [PPB][CROW]
+    float *tbuf = coef + PPB * CROW;                                                      // [PPB][PSW]
+    float *ssq = tbuf + PPB * PSW;                                                        // [TPB / 32]
+    float *gband = ssq + TPB / 32;                                        // [GPB]
+    int *gflag = reinterpret_cast<int *>(gband + GPB);                    // [GPB]
+    int *accs = gflag + GPB;                                              // hi[C][RA] lo[C][RA] w[RA]
+    const int RA = t.rh_max * t.rw_max;
+    int *acc_hi = accs, *acc_lo = accs + C * RA, *acc_w = accs + 2 * C * RA;
+
+    const int tid = threadIdx.x;
+    const int ps = tid >> 3, row = tid & 7;  // patch slot, row
+    const int gb = ps / K, k = ps - gb * K;  // group in flight, patch in group
+    const int tg = tid - gb * TPG;           // thread within group
+
+    load_basis<C>(sb, a.b32);
+    __syncthreads();
+    load_rbasis<C>(rb, sb);
+    __syncthreads();
+    const float tau = a.st->tau32;
+    const size_t HW = (size_t)a.H * a.W;
+    const int gpt = t.ty * t.tx;
+    const int nbatch = (gpt + GPB - 1) / GPB;
+
+    for (int tile = blockIdx.x; tile < t.ntiles; tile += gridDim.x) {
+        const int tyi = tile / t.ntx, txi = tile - tyi * t.ntx;
+        const int gy0 = tyi * t.ty, gx0 = txi * t.tx;
+        const int gy1 = min(a.ny, gy0 + t.ty) - 1, gx1 = min(a.nx, gx0 + t.tx) - 1;
+        const int Y0 = grid_pos(gy0, a.H, a.step), Y1 = grid_pos(gy1, a.H, a.step);
+        const int X0 = grid_pos(gx0, a.W, a.step), X1 = grid_pos(gx1, a.W, a.step);
+        const int ry0 = max(0, Y0 - a.R), ry1 = min(a.H - 1, Y1 + a.R + PS - 1);
+        const int rx0 = max(0, X0 - a.R), rx1 = min(a.W - 1, X1 + a.R + PS - 1);
+        const int rh = ry1 - ry0 + 1, rw = rx1 - rx0 + 1;
+        if (t.local) {
+            for (int e = tid; e < (2 * C + 1) * RA; e += TPB) accs[e] = 0;
+            __syncthreads();
+        }
+        for (int b = 0; b < nbatch; ++b) {
+            const int lg = b * GPB + gb;
+            const int gy = gy0 + lg / t.tx, gx = gx0 + lg % t.tx;
+            const bool valid = (lg < gpt) && gy <= gy1 && gx <= gx1;
+            const int r = valid ? gy * a.nx + gx : 0;
+            int py = 0, px = 0;
+            float ss = 0.f;
+            // ---- forward, factor 1: row `row` of Phat V
+            if (valid) {
+                const int pos = a.idx[(size_t)r * K + k];
+                py = pos / a.W;
+                px = pos - py * a.W;
+                const float *src = a.img + (size_t)(py + row) * a.W + px;
+                float P0[8], P1r[8], P1i[8];
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    if (C == 1) {
+                        const float x = __ldg(src + v);
+                        P0[v] = x;
+                        ss = fmaf(x, x, ss);
+                    } else {
+                        const float R = __ldg(src + v), Gc = __ldg(src + HW + v), B = __ldg(src + 2 * HW + v);
+                        P0[v] = ((R + Gc) + B) * K3F;
+                        P1r[v] = (R - 0.5f * (Gc + B)) * K3F;
+                        P1i[v] = (B - Gc) * 0.5f;
+                        ss = fmaf(R, R, ss);
+                        ss = fmaf(Gc, Gc, ss);
+                        ss = fmaf(B, B, ss);
+                    }
+                }
+                float t0[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int bb = 0; bb < 8; ++bb) {
+                    const float4 v0 = ld4(sb.v0 + bb * 8), v1 = ld4(sb.v0 + bb * 8 + 4);
+                    const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) t0[j] = fmaf(P0[bb], vv[j], t0[j]);
+                }
+                float *T = tbuf + ps * PSW + row * RS;
+                *reinterpret_cast<float4 *>(T) = make_float4(t0[0], t0[1], t0[2], t0[3]);
+                *reinterpret_cast<float4 *>(T + 4) = make_float4(t0[4], t0[5], t0[6], t0[7]);
+                if (C == 3) {
+                    float tr[8], ti[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) { tr[j] = 0.f; ti[j] = 0.f; }
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) {
+                        const float4 r0 = ld4(sb.v1r + bb * 8), r1 = ld4(sb.v1r + bb * 8 + 4);
+                        const float4 i0 = ld4(sb.v1i + bb * 8), i1 = ld4(sb.v1i + bb * 8 + 4);
+                        const float vr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+                        const float vi[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+                        const float pr = P1r[bb], pi = P1i[bb];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            tr[j] = fmaf(pr, vr[j], tr[j]);
+                            tr[j] = fmaf(-pi, vi[j], tr[j]);
+                            ti[j] = fmaf(pr, vi[j], ti[j]);
+                            ti[j] = fmaf(pi, vr[j], ti[j]);
+                        }
+                    }
+                    *reinterpret_cast<float4 *>(T + 8) = make_float4(tr[0], tr[1], tr[2], tr[3]);
+                    *reinterpret_cast<float4 *>(T + 12) = make_float4(tr[4], tr[5], tr[6], tr[7]);
+                    *reinterpret_cast<float4 *>(T + 16) = make_float4(ti[0], ti[1], ti[2], ti[3]);
+                    *reinterpret_cast<float4 *>(T + 20) = make_float4(ti[4], ti[5], ti[6], ti[7]);
+                }
+            }
+            // group norm (deterministic: fixed shuffle tree, then warp partials in order)
+#pragma unroll
+            for (int o = 1; o < 32 && o < TPG; o <<= 1) ss += __shfl_xor_sync(FULL, ss, o);
+            if (TPG <= 32) {
+                if (tg == 0) {
+                    gband[gb] = (C == 3 ? 320.f : 160.f) * U32 * sqrtf(ss) * 1.01f + 2.f * U32 * tau;
+                    gflag[gb] = 0;
+                }
+            } else if ((tid & 31) == 0) {
+                ssq[tid >> 5] = ss;
+            }
+            __syncthreads();
+            if (TPG > 32 && tg == 0) {
+                float s = 0.f;
+                for (int w = 0; w < TPG / 32; ++w) s += ssq[(tid >> 5) + w];
+                gband[gb] = (C == 3 ? 320.f : 160.f) * U32 * sqrtf(s) * 1.01f + 2.f * U32 * tau;
+                gflag[gb] = 0;
+            }
+            // ---- forward, factor 2: row `row` (= i) of U^H (Phat V)
+            if (valid) {
+                const float *T = tbuf + ps * PSW;
+                float s0[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                const float4 c0 = ld4(rb.u0t + row * BROW), c1 = ld4(rb.u0t + row * BROW + 4);
+                const float uc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                for (int aa = 0; aa < 8; ++aa) {
+                    const float4 x0 = ld4(T + aa * RS), x1 = ld4(T + aa * RS + 4);
+                    const float tv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) s0[j] = fmaf(uc[aa], tv[j], s0[j]);
+                }
+                float *S = coef + ps * CROW;
+                float *S0 = S + cpos(row * 8), *S1r = S + cpos(64 + row * 8), *S1i = S + cpos(128 + row * 8);
+                *reinterpret_cast<float4 *>(S0) = make_float4(s0[0], s0[1], s0[2], s0[3]);
+                *reinterpret_cast<float4 *>(S0 + 4) = make_float4(s0[4], s0[5], s0[6], s0[7]);
+                if (C == 3) {
+                    const float4 r0 = ld4(rb.u1rt + row * BROW), r1 = ld4(rb.u1rt + row * BROW + 4);
+                    const float4 i0 = ld4(rb.u1it + row * BROW), i1 = ld4(rb.u1it + row * BROW + 4);
+                    const float ur[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+                    const float ui[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+                    float sr[8], si[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) { sr[j] = 0.f; si[j] = 0.f; }
+#pragma unroll
+                    for (int aa = 0; aa < 8; ++aa) {
+                        const float4 a0 = ld4(T + aa * RS + 8), a1 = ld4(T + aa * RS + 12);
+                        const float4 b0 = ld4(T + aa * RS + 16), b1 = ld4(T + aa * RS + 20);
+                        const float trr[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                        const float tii[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {  // conj(u) * t
+                            sr[j] = fmaf(ur[aa], trr[j], sr[j]);
+                            sr[j] = fmaf(ui[aa], tii[j], sr[j]);
+                            si[j] = fmaf(ur[aa], tii[j], si[j]);
+                            si[j] = fmaf(-ui[aa], trr[j], si[j]);
+                        }
+                    }
+                    *reinterpret_cast<float4 *>(S1r) = make_float4(sr[0], sr[1], sr[2], sr[3]);
+                    *reinterpret_cast<float4 *>(S1r + 4) = make_float4(sr[4], sr[5], sr[6], sr[7]);
+                    *reinterpret_cast<float4 *>(S1i) = make_float4(si[0], si[1], si[2], si[3]);
+                    *reinterpret_cast<float4 *>(S1i + 4) = make_float4(si[4], si[5], si[6], si[7]);
+                }
+            }
+            __syncthreads();
+            // ---- Haar along the group axis, threshold, inverse Haar (one stream per thread)
+            if (valid) {
+                float *cg = coef + (gb * K) * CROW;
+                const float band = gband[gb];
+                int flag = 0;
+#pragma unroll 1
+                for (int it = tg; it < IPG; it += TPG) {
+                    if (it < 64) {
+                        const int pe = cpos(it);
+                        float x[K];
+#pragma unroll
+                        for (int q = 0; q < K; ++q) x[q] = cg[q * CROW + pe];
+                        haar_fwd<K>(x);
+#pragma unroll
+                        for (int q = 0; q < K; ++q) {
+                            const int d = decide(fabsf(x[q]), tau, band);
+                            flag |= (d == 2);
+                            x[q] = (d == 0) ? 0.f : x[q];
+                        }
+                        haar_inv<K>(x);
+#pragma unroll
+                        for (int q = 0; q < K; ++q) cg[q * CROW + pe] = x[q];
+                    } else {
+                        const int pr = cpos(it), pi = cpos(it + 64);
+                        float xr[K], xi[K];
+#pragma unroll
+                        for (int q = 0; q < K; ++q) {
+                            xr[q] = cg[q * CROW + pr];
+                            xi[q] = cg[q * CROW + pi];
+                        }
+                        haar_fwd<K>(xr);
+                        haar_fwd<K>(xi);
+#pragma unroll
+                        for (int q = 0; q < K; ++q) {
+                            const float mag = sqrtf(xr[q] * xr[q] + xi[q] * xi[q]);
+                            const int d = decide(mag, tau, band);
+                            flag |= (d == 2);
+                            if (d == 0) { xr[q] = 0.f; xi[q] = 0.f; }
+                        }
+                        haar_inv<K>(xr);
+                        haar_inv<K>(xi);
+#pragma unroll
+                        for (int q = 0; q < K; ++q) {
+                            cg[q * CROW + pr] = xr[q];
+                            cg[q * CROW + pi] = xi[q];
+                        }
+                    }
+                }
+                if (flag) gflag[gb] = 1;
+            }
+            __syncthreads();
+            const bool agg = valid && gflag[gb] == 0;
+            if (valid && !agg && tg == 0) {
+                const int pos = atomicAdd(&a.st->filter_redo, 1);
+                a.redo[pos] = r;
+            }
+            // ---- inverse, factor 1: row `row` (= i) of Shat V^H
+            if (agg) {
+                const float *S = coef + ps * CROW;
+                const float *S0 = S + cpos(row * 8), *S1r = S + cpos(64 + row * 8), *S1i = S + cpos(128 + row * 8);
+                const float4 x0 = ld4(S0), x1 = ld4(S0 + 4);
+                const float sv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                float q0[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float4 c0 = ld4(sb.v0t + j * 8), c1 = ld4(sb.v0t + j * 8 + 4);  // column j of V
+                    const float vc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) q0[bb] = fmaf(sv[j], vc[bb], q0[bb]);
+                }
+                float *T = tbuf + ps * PSW + row * RS;
+                *reinterpret_cast<float4 *>(T) = make_float4(q0[0], q0[1], q0[2], q0[3]);
+                *reinterpret_cast<float4 *>(T + 4) = make_float4(q0[4], q0[5], q0[6], q0[7]);
+                if (C == 3) {
+                    const float4 a0 = ld4(S1r), a1 = ld4(S1r + 4), b0 = ld4(S1i), b1 = ld4(S1i + 4);
+                    const float sr[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    const float si[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                    float qr[8], qi[8];
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) { qr[bb] = 0.f; qi[bb] = 0.f; }
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 r0 = ld4(sb.v1rt + j * 8), r1 = ld4(sb.v1rt + j * 8 + 4);
+                        const float4 i0 = ld4(sb.v1it + j * 8), i1 = ld4(sb.v1it + j * 8 + 4);
+                        const float vr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+                        const float vi[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+#pragma unroll
+                        for (int bb = 0; bb < 8; ++bb) {  // s * conj(v)
+                            qr[bb] = fmaf(sr[j], vr[bb], qr[bb]);
+                            qr[bb] = fmaf(si[j], vi[bb], qr[bb]);
+                            qi[bb] = fmaf(si[j], vr[bb], qi[bb]);
+                            qi[bb] = fmaf(-sr[j], vi[bb], qi[bb]);
+                        }
+                    }
+                    *reinterpret_cast<float4 *>(T + 8) = make_float4(qr[0], qr[1], qr[2], qr[3]);
+                    *reinterpret_cast<float4 *>(T + 12) = make_float4(qr[4], qr[5], qr[6], qr[7]);
+                    *reinterpret_cast<float4 *>(T + 16) = make_float4(qi[0], qi[1], qi[2], qi[3]);
+                    *reinterpret_cast<float4 *>(T + 20) = make_float4(qi[4], qi[5], qi[6], qi[7]);
+                }
+            }
+            __syncthreads();
+            // ---- inverse, factor 2: row `row` (= a) of U Q, inverse DFT, aggregation
+            if (agg) {
+                const float *Q = tbuf + ps * PSW;
+                const float4 c0 = ld4(rb.u0 + row * BROW), c1 = ld4(rb.u0 + row * BROW + 4);
+                const float ua[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+                float p0[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float4 x0 = ld4(Q + i * RS), x1 = ld4(Q + i * RS + 4);
+                    const float qv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) p0[bb] = fmaf(ua[i], qv[bb], p0[bb]);
+                }
+                float out[3][8];
+                if (C == 1) {
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) out[0][bb] = p0[bb];
+                } else {
+                    const float4 r0 = ld4(rb.u1r + row * BROW), r1 = ld4(rb.u1r + row * BROW + 4);
+                    const float4 i0 = ld4(rb.u1i + row * BROW), i1 = ld4(rb.u1i + row * BROW + 4);
+                    const float ur[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+                    const float ui[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+                    float pr[8], pi[8];
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) { pr[bb] = 0.f; pi[bb] = 0.f; }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float4 a0 = ld4(Q + i * RS + 8), a1 = ld4(Q + i * RS + 12);
+                        const float4 b0 = ld4(Q + i * RS + 16), b1 = ld4(Q + i * RS + 20);
+                        const float qr[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                        const float qi[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                        for (int bb = 0; bb < 8; ++bb) {  // u * q
+                            pr[bb] = fmaf(ur[i], qr[bb], pr[bb]);
+                            pr[bb] = fmaf(-ui[i], qi[bb], pr[bb]);
+                            pi[bb] = fmaf(ur[i], qi[bb], pi[bb]);
+                            pi[bb] = fmaf(ui[i], qr[bb], pi[bb]);
+                        }
+                    }
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) {
+                        out[0][bb] = (p0[bb] + 2.f * pr[bb]) * K3F;
+                        out[1][bb] = (p0[bb] - pr[bb] - 2.f * S3H * pi[bb]) * K3F;
+                        out[2][bb] = (p0[bb] - pr[bb] + 2.f * S3H * pi[bb]) * K3F;
+                    }
+                }
+                if (t.local) {
+                    const int ly = py + row - ry0, lx = px - rx0;
+                    if (ly >= 0 && ly < rh && lx >= 0 && lx + 7 < rw) {
+                        const int o = ly * rw + lx;
+#pragma unroll
+                        for (int bb = 0; bb < 8; ++bb) {
+#pragma unroll
+                            for (int c = 0; c < C; ++c) {
+                                const long long q = fix16(out[c][bb]);
+                                atomicAdd(acc_hi + c * RA + o + bb, (int)(q >> 16));
+                                atomicAdd(acc_lo + c * RA + o + bb, (int)(q & 0xffff));
+                            }
+                            atomicAdd(acc_w + o + bb, 1);
+                        }
+                    } else {
+                        atomicExch(&a.st->error, 1);
+                    }
+                } else {
+                    const size_t o = (size_t)(py + row) * a.W + px;
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) {
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+                            atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + c * HW + o + bb),
+                                      (unsigned long long)fix16(out[c][bb]));
+                        atomicAdd(a.wcount + o + bb, 1);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (t.local) {
+            // flush the tile's sums to the image-wide int64 sums
+            for (int e = tid; e < rh * rw; e += TPB) {
+                const int w = acc_w[e];
+                if (w == 0) continue;
+                const int yy = e / rw, xx = e - yy * rw;
+                const size_t g = (size_t)(ry0 + yy) * a.W + (rx0 + xx);
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const long long s = (long long)acc_hi[c * RA + e] * 65536ll + (long long)acc_lo[c * RA + e];
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + c * HW + g), (unsigned long long)s);
+                }
+                atomicAdd(a.wcount + g, w);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// out = sum / (2^16 * weight)
 __global__ void k_normalize(const long long *__restrict__ acc, const int *__restrict__ wcount, float *__restrict__ out,
                             size_t HW, int C) {
     const size_t n = HW * C;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const size_t p = i % HW;
         const int w = wcount[p];
-        out[i] = __ll2float_rn(acc[i]) / ((float)w * FIX_SCALE);
+        out[i] = __ll2float_rn(acc[i]) * (1.0f / 65536.0f) / (float)w;
     }
-}
-
-template <int C, int K, bool REDO>
-size_t filter_smem() {
-    constexpr int G = REDO ? 1 : (32 / K > 0 ? 32 / K : 1);
-    constexpr int NCOEF = Cfg<C>::NCOEF;
-    constexpr int ROW = K + 1;
-    constexpr int GS0 = NCOEF * ROW;
-    constexpr int GS = GS0 + ((K - GS0 % 32) % 32 + 32) % 32;
-    constexpr int NMASK = (NCOEF * K + 31) / 32;
-    return sizeof(SBasis) + (size_t)2 * (G * GS + 2 * G + (REDO ? NMASK + QCAP + 2 : 0)) * 4;
 }
 
 template <int C, int K>
-hts_status launch_ck(const FilterArgs &a, int nref, float *out, cudaStream_t s) {
-    constexpr int G = (32 / K > 0 ? 32 / K : 1);
-    const size_t sm0 = filter_smem<C, K, false>(), sm1 = filter_smem<C, K, true>();
-    static bool attr_set = false;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(k_filter<C, K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(k_filter<C, K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1) !=
-                cudaSuccess)
-            return check_launch("cudaFuncSetAttribute(k_filter)");
-        attr_set = true;
+size_t exact_smem() {
+    constexpr int NCOEF = Cfg<C>::NCOEF;
+    constexpr int GS = NCOEF * (K + 1);
+    constexpr int NMASK = (NCOEF * K + 31) / 32;
+    return sizeof(SBasis) + (size_t)2 * (GS + 1 + NMASK + QCAP + 1) * 4;
+}
+
+template <int C>
+size_t tile_fixed_smem() {
+    constexpr int GPBmax = PPB / 2;
+    return sizeof(SBasis) + sizeof(RBasis) +
+           ((size_t)PPB * CROW + (size_t)PPB * TileCfg<C>::PSW + TPB / 32 + 2 * GPBmax) * 4;
+}
+
+template <int C, int K>
+hts_status launch_ck(const FilterArgs &a, const Geom &g, float *out, cudaStream_t s) {
+    const size_t HW = (size_t)a.H * a.W;
+    // tile shape: the largest of these whose search region fits in shared memory
+    static const int shapes[][2] = {{4, 8}, {4, 4}, {2, 4}, {2, 2}, {1, 2}, {1, 1}};
+    const size_t budget = 227 * 1024;
+    const size_t fixed = tile_fixed_smem<C>();
+    TileArgs ta;
+    ta.local = 0;
+    ta.ty = 4;
+    ta.tx = 8;
+    for (auto &sh : shapes) {
+        const int rh = std::min(g.H, (sh[0] - 1) * g.step + 2 * g.R + PS);
+        const int rw = std::min(g.W, (sh[1] - 1) * g.step + 2 * g.R + PS);
+        const size_t need = fixed + (size_t)(2 * C + 1) * rh * rw * 4;
+        if (need <= budget) {
+            ta.ty = sh[0];
+            ta.tx = sh[1];
+            ta.rh_max = rh;
+            ta.rw_max = rw;
+            ta.local = 1;
+            break;
+        }
     }
-    const int units = (nref + G - 1) / G;
-    int blocks = (units + 1) / 2;
-    if (blocks < 1) blocks = 1;
+    if (!ta.local) {
+        ta.rh_max = 0;
+        ta.rw_max = 0;
+    }
+    ta.nty = (g.ny + ta.ty - 1) / ta.ty;
+    ta.ntx = (g.nx + ta.tx - 1) / ta.tx;
+    ta.ntiles = ta.nty * ta.ntx;
+    const size_t sm_tile = fixed + (size_t)(2 * C + 1) * ta.rh_max * ta.rw_max * 4;
+    const size_t sm_exact = exact_smem<C, K>();
+    if (cudaFuncSetAttribute(k_filter_tile<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tile) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_filter_exact<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_exact) !=
+            cudaSuccess)
+        return check_launch("cudaFuncSetAttribute(k_filter)");
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(ta.ntiles, nsm));
     {
         KTimer kt("k_filter", s);
-        k_filter<C, K, false><<<blocks, 64, sm0, s>>>(a);
+        k_filter_tile<C, K><<<grid, TPB, sm_tile, s>>>(a, ta);
     }
     hts_status st = check_launch("k_filter");
     if (st != HTS_OK) return st;
     {
         KTimer kt("k_filter_exact", s);
-        k_filter<C, K, true><<<152, 64, sm1, s>>>(a);
+        k_filter_exact<C, K><<<nsm, 64, sm_exact, s>>>(a);
     }
     st = check_launch("k_filter_exact");
     if (st != HTS_OK) return st;
-    const size_t HW = (size_t)a.H * a.W;
     int nb = (int)((HW * C + 255) / 256);
-    if (nb > 152 * 16) nb = 152 * 16;
+    if (nb > nsm * 16) nb = nsm * 16;
     {
         KTimer kt("k_normalize", s);
         k_normalize<<<nb, 256, 0, s>>>(a.acc, a.wcount, out, HW, C);
@@ -787,7 +1164,9 @@ hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, co
     a.H = g.H;
     a.W = g.W;
     a.step = g.step;
+    a.R = g.R;
     a.nx = g.nx;
+    a.ny = g.ny;
     a.nref = g.nref;
     a.idx = idx;
     a.b64 = b64;
@@ -797,7 +1176,7 @@ hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, co
     a.redo = redo_list;
     a.st = st;
 #define HTS_FILTER_CASE(CC, KK) \
-    if (g.C == CC && g.K == KK) return launch_ck<CC, KK>(a, g.nref, out, s);
+    if (g.C == CC && g.K == KK) return launch_ck<CC, KK>(a, g, out, s);
     HTS_FILTER_CASE(1, 2) HTS_FILTER_CASE(1, 4) HTS_FILTER_CASE(1, 8) HTS_FILTER_CASE(1, 16) HTS_FILTER_CASE(1, 32)
     HTS_FILTER_CASE(3, 2) HTS_FILTER_CASE(3, 4) HTS_FILTER_CASE(3, 8) HTS_FILTER_CASE(3, 16) HTS_FILTER_CASE(3, 32)
 #undef HTS_FILTER_CASE

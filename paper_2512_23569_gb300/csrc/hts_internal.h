@@ -12,7 +12,7 @@ namespace hts {
 constexpr int PS = 8;          // patch side (the only one built)
 constexpr int NPIX = PS * PS;  // pixels per patch
 constexpr int MAX_WIN = 63;    // largest search window side
-constexpr float FIX_SCALE = 16777216.0f;  // 2^24: fixed-point scale of the aggregation sums
+constexpr double FIX_SCALE = 65536.0;  // 2^16: fixed-point scale of the aggregation sums
 
 // Device-resident state of one call: noise level, threshold and counters.
 struct DevState {
@@ -87,9 +87,15 @@ hts_status launch_basis(const float *img, const Geom &g, double *partials, doubl
                         cudaStream_t s);
 
 // ---- noise level (sigma.cu)
+// `list`: N_ref int32 scratch for the groups whose rank test is taken in FP64
 hts_status launch_sigma(const float *img, const Geom &g, const hts_params &p, const double *eig, const int32_t *idx,
-                        DevState *st, cudaStream_t s);
+                        int32_t *list, DevState *st, cudaStream_t s);
 hts_status launch_set_sigma(double sigma, const Geom &g, const hts_params &p, DevState *st, cudaStream_t s);
+// the three parts of launch_sigma, for callers that overlap them with other work
+hts_status launch_sigma_floor(const Geom &g, const hts_params &p, const double *eig, DevState *st, cudaStream_t s);
+hts_status launch_sigma_vote(const float *img, const Geom &g, const hts_params &p, const int32_t *idx,
+                             int32_t *list, DevState *st, cudaStream_t s);
+hts_status launch_sigma_final(const Geom &g, const hts_params &p, DevState *st, cudaStream_t s);
 
 // ---- filtering and aggregation (filter.cu)
 hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, const double *b64, const float *b32,

@@ -1,11 +1,15 @@
 // Grouping step of Haar-tSVD (Eq. 9, Alg. 1 step 1) on sm_103a.
 //
-// One warp per reference patch.  The warp stages its search region of the
-// matching plane (gray image, green channel, or the channel sum R+G+B when
-// Eq. 9 rejects green) in shared memory, computes FP32 squared distances of
-// all candidates (each lane 4 horizontally adjacent candidates per item,
-// register-blocked), keeps a per-lane sorted top-(K+3) list of 64-bit keys
-// (distance bits, raster index) and merges the 32 lists.
+// A block of four warps takes a 2x2 block of reference patches and stages the
+// union of their search regions of the matching planes in shared memory
+// (gray image; for colour both the green channel and the channel sum R+G+B,
+// since Eq. 9 picks one per reference).  Each warp takes one reference:
+// lanes compute FP32 squared distances of 4 horizontally adjacent
+// candidates per item (register-blocked), store every distance in shared
+// memory and keep a sorted per-lane list of their 4 smallest keys (distance
+// bits, raster index).  The (K-1)-th smallest key of the 32 lists bounds the
+// true (K-1)-th from above; the warp then collects every candidate under the
+// certified threshold (usually K-1 plus a few) and sorts only those.
 //
 // Exactness.  The group must equal the FP64 definition bit for bit: the K-1
 // nearest candidates in ascending (distance, raster index), distances being
@@ -14,13 +18,12 @@
 // (eps covers 66 roundings of the subtract / FMA chain; beta and g0 cover the
 // rounding of the FP32 channel sum on the R+G+B plane, scaled by the largest
 // |R|+|G|+|B| of the region; g0 also absorbs subnormal flushing).  If every
-// adjacent pair among the first K FP32 entries is separated by that bound,
-// the FP32 order is the FP64 order and nothing else runs.  Otherwise every
-// entry that can still belong to the K-1 nearest is re-evaluated with the
-// FP64 expression in the same operation order as the definition and ranked
-// by (D, index); when even the list of K+3 cannot certify that it holds all
-// of them, the reference goes to an exhaustive FP64 pass (flat, noiseless
-// inputs with massive ties end up there).
+// adjacent pair among the first K sorted entries is separated by that bound,
+// the FP32 order is the FP64 order.  Otherwise every entry that can still
+// belong to the K-1 nearest is re-evaluated with the FP64 expression in the
+// same operation order as the definition and ranked by (D, index).  When the
+// candidate set exceeds what a warp handles (flat, noiseless inputs with
+// massive ties), the reference goes to an exhaustive FP64 pass.
 #include "hts_internal.h"
 
 namespace hts {
@@ -32,7 +35,7 @@ constexpr uint64_t EMPTY = ~0ull;
 
 struct MatchArgs {
     const float *img;
-    int H, W, C, step, R, nx, nref;
+    int H, W, C, step, R, nx, ny, nref;
     double gamma;
     int32_t *idx;
     uint8_t *green;
@@ -129,73 +132,118 @@ struct Bound {
     }
 };
 
-template <int K>
-__global__ void __launch_bounds__(128) k_match(MatchArgs a) {
-    constexpr int M = K + 3;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nwarps = blockDim.x >> 5;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int RW = 2 * a.R + PS;
-    uint64_t *mer = reinterpret_cast<uint64_t *>(smem_raw) + warp * M;
-    double *dex = reinterpret_cast<double *>(smem_raw) + nwarps * M + warp * M;
-    float *reg = reinterpret_cast<float *>(smem_raw + (size_t)nwarps * M * 16) + warp * RW * RW;
+constexpr int MW = 4;      // warps per block = a 2x2 block of reference patches sharing one staged region
+constexpr int LTOP = 4;    // per-lane short list that bounds the (K-1)-th distance from above
+constexpr int PMAX = 64;   // largest candidate set a warp certifies or re-ranks itself
 
-    const int r = blockIdx.x * nwarps + warp;
-    if (r >= a.nref) return;  // warp-uniform
+// Eq. 9 with FP32 channel norms (64-term sums, relative error < 40 u): the
+// decision is certain when nG^2 gamma^2 and max(nR^2, nB^2) differ by more
+// than 1e-5 relative; otherwise the FP64 sequential definition decides.
+__device__ int gcp_green_fast(const float *__restrict__ img, int W, size_t HW, int y, int x, double gamma, int lane) {
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int e = lane + 32 * q;
+        const size_t o = (size_t)(y + (e >> 3)) * W + x + (e & 7);
+        const float r = __ldg(img + o), g = __ldg(img + HW + o), b = __ldg(img + 2 * HW + o);
+        s0 = fmaf(r, r, s0);
+        s1 = fmaf(g, g, s1);
+        s2 = fmaf(b, b, s2);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        s0 += __shfl_xor_sync(FULL, s0, o);
+        s1 += __shfl_xor_sync(FULL, s1, o);
+        s2 += __shfl_xor_sync(FULL, s2, o);
+    }
+    const float lhs = s1 * (float)(gamma * gamma), rhs = fmaxf(s0, s2);
+    if (lhs > rhs * (1.f + 1e-5f) && lhs > 0.f) return 1;
+    if (lhs < rhs * (1.f - 1e-5f)) return 0;
+    return gcp_green(img, W, HW, y, x, gamma, lane);
+}
+
+template <int K>
+__global__ void __launch_bounds__(MW * 32) k_match(MatchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int RHM = a.step + 2 * a.R + PS;          // region side bound
+    const int NCM = (2 * a.R + 1) * (2 * a.R + 1);  // candidates per window bound
+    uint64_t *plist = reinterpret_cast<uint64_t *>(smem_raw) + warp * 2 * PMAX;
+    uint64_t *psort = plist + PMAX;
+    double *pd64 = reinterpret_cast<double *>(smem_raw) + MW * 2 * PMAX + warp * PMAX;
+    float *planeA = reinterpret_cast<float *>(smem_raw + (size_t)MW * 3 * PMAX * 8);
+    float *planeS = planeA + RHM * RHM;
+    float *dbuf = planeS + (a.C == 3 ? RHM * RHM : 0) + warp * NCM;
+    __shared__ unsigned s_tmax;
+
+    const int nbx = (a.nx + 1) >> 1;
+    const int by = blockIdx.x / nbx, bx = blockIdx.x - by * nbx;
+    const int gy = 2 * by + (warp >> 1), gx = 2 * bx + (warp & 1);
     const size_t HW = (size_t)a.H * a.W;
-    const int yr = grid_pos(r / a.nx, a.H, a.step), xr = grid_pos(r % a.nx, a.W, a.step);
-    const int green = (a.C == 3) ? gcp_green(a.img, a.W, HW, yr, xr, a.gamma, lane) : 1;
+    // region = union of the block's windows (plus the patch extent)
+    const int ya = grid_pos(2 * by, a.H, a.step), yb = grid_pos(min(2 * by + 1, a.ny - 1), a.H, a.step);
+    const int xa = grid_pos(2 * bx, a.W, a.step), xb = grid_pos(min(2 * bx + 1, a.nx - 1), a.W, a.step);
+    const int ry0 = max(0, ya - a.R), ry1 = min(a.H - PS, yb + a.R) + PS - 1;
+    const int rx0 = max(0, xa - a.R), rx1 = min(a.W - PS, xb + a.R) + PS - 1;
+    const int rh = ry1 - ry0 + 1, rw = rx1 - rx0 + 1;
+    if (threadIdx.x == 0) s_tmax = 0u;
+    __syncthreads();
+    float tmax = 0.f;
+    for (int e = threadIdx.x; e < rh * rw; e += blockDim.x) {
+        const int yy = e / rw, xx = e - yy * rw;
+        const size_t o = (size_t)(ry0 + yy) * a.W + (rx0 + xx);
+        if (a.C == 1) {
+            planeA[e] = __ldg(a.img + o);
+        } else {
+            const float R = __ldg(a.img + o), G = __ldg(a.img + HW + o), B = __ldg(a.img + 2 * HW + o);
+            planeA[e] = G;
+            planeS[e] = __fadd_rn(__fadd_rn(R, G), B);
+            tmax = fmaxf(tmax, fabsf(R) + fabsf(G) + fabsf(B));
+        }
+    }
+    tmax = warp_max_f(tmax);
+    if (lane == 0) atomicMax(&s_tmax, __float_as_uint(tmax));  // non-negative floats order as their bits
+    __syncthreads();
+    if (gy >= a.ny || gx >= a.nx) return;  // no block-wide barrier below
+
+    const int r = gy * a.nx + gx;
+    const int yr = grid_pos(gy, a.H, a.step), xr = grid_pos(gx, a.W, a.step);
+    const int green = (a.C == 3) ? gcp_green_fast(a.img, a.W, HW, yr, xr, a.gamma, lane) : 1;
     if (lane == 0 && a.green) a.green[r] = (uint8_t)green;
+    const bool exact_plane = (a.C == 1) || green;
+    const float *plane = exact_plane ? planeA : planeS;
+    const float T3 = exact_plane ? 0.f : __uint_as_float(s_tmax);
 
     const int cy0 = max(0, yr - a.R), cy1 = min(a.H - PS, yr + a.R);
     const int cx0 = max(0, xr - a.R), cx1 = min(a.W - PS, xr + a.R);
-    const int nrow = cy1 - cy0 + 1, ncol = cx1 - cx0 + 1;
-    const int rh = nrow + PS - 1, rw = ncol + PS - 1;
-    const bool exact_plane = (a.C == 1) || green;
-
-    float tmax = 0.f;
-    for (int e = lane; e < rh * rw; e += 32) {
-        const int yy = e / rw, xx = e - yy * rw;
-        const size_t o = (size_t)(cy0 + yy) * a.W + (cx0 + xx);
-        float v;
-        if (a.C == 1) {
-            v = __ldg(a.img + o);
-        } else if (green) {
-            v = __ldg(a.img + HW + o);
-        } else {
-            const float R = __ldg(a.img + o), G = __ldg(a.img + HW + o), B = __ldg(a.img + 2 * HW + o);
-            v = __fadd_rn(__fadd_rn(R, G), B);
-            tmax = fmaxf(tmax, fabsf(R) + fabsf(G) + fabsf(B));
-        }
-        reg[e] = v;
-    }
-    tmax = warp_max_f(tmax);
-    __syncwarp();
+    const int nrow = cy1 - cy0 + 1, ncol = cx1 - cx0 + 1, nc = nrow * ncol;
+    const int oy = cy0 - ry0, ox = cx0 - rx0;
 
     float ar[NPIX];
     {
-        const float *rp = reg + (yr - cy0) * rw + (xr - cx0);
+        const float *rp = plane + (yr - ry0) * rw + (xr - rx0);
 #pragma unroll
         for (int u = 0; u < PS; ++u)
 #pragma unroll
             for (int v = 0; v < PS; ++v) ar[u * PS + v] = rp[u * rw + v];
     }
-
-    uint64_t lst[M];
+    uint64_t lst[LTOP];
 #pragma unroll
-    for (int i = 0; i < M; ++i) lst[i] = EMPTY;
+    for (int i = 0; i < LTOP; ++i) lst[i] = EMPTY;
 
     const int nq = (ncol + 3) >> 2;
     const int nitems = nrow * nq;
     for (int it = lane; it < nitems; it += 32) {
         const int i = it / nq, cxb = (it - i * nq) * 4;
         float d[4] = {0.f, 0.f, 0.f, 0.f};
+        const float *base = plane + (oy + i) * rw + ox + cxb;
+        const int lim = rw - ox - cxb;  // columns of the region right of this quad's first candidate
 #pragma unroll
         for (int u = 0; u < PS; ++u) {
-            const float *row = reg + (i + u) * rw + cxb;
+            const float *row = base + u * rw;
             float b[PS + 3];
 #pragma unroll
-            for (int t = 0; t < PS + 3; ++t) b[t] = (cxb + t < rw) ? row[t] : 0.f;
+            for (int t = 0; t < PS + 3; ++t) b[t] = (t < lim) ? row[t] : 0.f;
 #pragma unroll
             for (int v = 0; v < PS; ++v) {
                 const float av = ar[u * PS + v];
@@ -206,75 +254,105 @@ __global__ void __launch_bounds__(128) k_match(MatchArgs a) {
                 }
             }
         }
-        const int gy = cy0 + i;
+        const int gyy = cy0 + i;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int cx = cxb + t;
             if (cx < ncol) {
-                const int gx = cx0 + cx;
-                if (gy != yr || gx != xr) topm_insert<M>(lst, make_key(d[t], gy * a.W + gx));
+                const int gxx = cx0 + cx;
+                if (gyy == yr && gxx == xr) {
+                    dbuf[i * ncol + cx] = __int_as_float(0x7f800000);  // the reference itself: never collected
+                } else {
+                    dbuf[i * ncol + cx] = d[t];
+                    topm_insert<LTOP>(lst, make_key(d[t], gyy * a.W + gxx));
+                }
             }
-        }
-    }
-
-    // merge the 32 sorted lists: M rounds of warp-wide minimum
-    for (int j = 0; j < M; ++j) {
-        const uint64_t h = lst[0];
-        const uint64_t mn = warp_min_u64(h);
-        if (lane == 0) mer[j] = mn;
-        if (h == mn && mn != EMPTY) {
-#pragma unroll
-            for (int q = 0; q < M - 1; ++q) lst[q] = lst[q + 1];
-            lst[M - 1] = EMPTY;
         }
     }
     __syncwarp();
 
+    // (K-1)-th smallest key of the union of the lane lists: an upper bound of the true one
+    uint64_t tau = EMPTY;
+    for (int j = 0; j < K - 1; ++j) {
+        const uint64_t h = lst[0];
+        const uint64_t mn = warp_min_u64(h);
+        if (h == mn && mn != EMPTY) {
+#pragma unroll
+            for (int q = 0; q < LTOP - 1; ++q) lst[q] = lst[q + 1];
+            lst[LTOP - 1] = EMPTY;
+        }
+        tau = mn;
+    }
+    int32_t *out = a.idx + (size_t)r * K;
+    if (lane == 0) out[0] = yr * a.W + xr;
     Bound bd;
     bd.eps = 100.f * U32;
-    bd.beta = exact_plane ? 0.f : 72.f * U32 * tmax;
-    bd.g0 = (exact_plane ? 0.f : 1200.f * U32 * U32 * tmax * tmax) + 1e-30f;
-
-    int32_t *out = a.idx + (size_t)r * K;
-    bool ok = true;
-    for (int i = lane; i < K - 1; i += 32) {
-        const uint64_t nx = mer[i + 1];
-        if (nx != EMPTY) ok = ok && (bd.upper(key_dist(mer[i])) < bd.lower(key_dist(nx)));
+    bd.beta = exact_plane ? 0.f : 72.f * U32 * T3;
+    bd.g0 = (exact_plane ? 0.f : 1200.f * U32 * U32 * T3 * T3) + 1e-30f;
+    bool overflow = (tau == EMPTY);
+    // collect every candidate whose distance may still matter
+    int m = 0;
+    if (!overflow) {
+        const float T = bd.upper(bd.upper(key_dist(tau)));
+        const unsigned lt = (1u << lane) - 1u;
+        for (int c0 = 0; c0 < nc; c0 += 32) {
+            const int c = c0 + lane;
+            const float dv = (c < nc) ? dbuf[c] : __int_as_float(0x7f800000);
+            const bool ok = dv <= T;
+            const unsigned msk = __ballot_sync(FULL, ok);
+            if (ok) {
+                const int pos = m + __popc(msk & lt);
+                if (pos < PMAX) {
+                    const int ci = c / ncol;
+                    plist[pos] = make_key(dv, (cy0 + ci) * a.W + cx0 + (c - ci * ncol));
+                }
+            }
+            m += __popc(msk);
+        }
+        overflow = (m > PMAX) || (m < K - 1);
     }
-    const bool certified = __all_sync(FULL, ok);
-    if (lane == 0) out[0] = yr * a.W + xr;
-    if (certified) {
-        for (int i = lane; i < K - 1; i += 32) out[1 + i] = key_idx(mer[i]);
-        return;
-    }
-    // uncertain: FP64 re-rank of every entry that may belong to the K-1 nearest
-    const float thr = bd.upper(key_dist(mer[K - 2]));
-    const uint64_t last = mer[M - 1];
-    if (last != EMPTY && bd.lower(key_dist(last)) <= thr) {
+    if (overflow) {
         if (lane == 0) {
             const int pos = atomicAdd(&a.st->match_fallback, 1);
             a.fb[pos] = r;
         }
         return;
     }
-    int m = 0;
-    for (int i = 0; i < M; ++i) {
-        const uint64_t k = mer[i];
-        if (k == EMPTY || bd.lower(key_dist(k)) > thr) break;
-        m = i + 1;
-    }
-    for (int i = lane; i < m; i += 32) {
-        const int id = key_idx(mer[i]);
-        dex[i] = exact_dist(a.img, a.W, HW, a.C, green, yr, xr, id / a.W, id % a.W);
+    __syncwarp();
+    // rank sort of the collected keys (unique: the raster index is part of the key)
+    for (int e = lane; e < m; e += 32) {
+        const uint64_t key = plist[e];
+        int rank = 0;
+        for (int j = 0; j < m; ++j) rank += (plist[j] < key) ? 1 : 0;
+        psort[rank] = key;
     }
     __syncwarp();
-    for (int i = lane; i < m; i += 32) {
-        const double di = dex[i];
-        const int ii = key_idx(mer[i]);
+    bool ok = true;
+    for (int i = lane; i < K - 1; i += 32)
+        if (i + 1 < m) ok = ok && (bd.upper(key_dist(psort[i])) < bd.lower(key_dist(psort[i + 1])));
+    if (__all_sync(FULL, ok)) {
+        for (int i = lane; i < K - 1; i += 32) out[1 + i] = key_idx(psort[i]);
+        return;
+    }
+    // uncertain order: FP64 re-rank of every entry that may belong to the K-1 nearest
+    const float thr = bd.upper(key_dist(psort[K - 2]));
+    int mp = 0;
+    for (int i = 0; i < m; ++i) {
+        if (bd.lower(key_dist(psort[i])) > thr) break;
+        mp = i + 1;
+    }
+    for (int i = lane; i < mp; i += 32) {
+        const int id = key_idx(psort[i]);
+        pd64[i] = exact_dist(a.img, a.W, HW, a.C, green, yr, xr, id / a.W, id % a.W);
+    }
+    __syncwarp();
+    for (int i = lane; i < mp; i += 32) {
+        const double di = pd64[i];
+        const int ii = key_idx(psort[i]);
         int rank = 0;
-        for (int j = 0; j < m; ++j) {
-            const double dj = dex[j];
-            const int ij = key_idx(mer[j]);
+        for (int j = 0; j < mp; ++j) {
+            const double dj = pd64[j];
+            const int ij = key_idx(psort[j]);
             rank += (dj < di || (dj == di && ij < ii)) ? 1 : 0;
         }
         if (rank < K - 1) out[1 + rank] = ii;
@@ -345,18 +423,16 @@ __global__ void __launch_bounds__(128) k_match_fallback(MatchArgs a) {
 
 template <int K>
 hts_status launch_k(const MatchArgs &a, cudaStream_t s) {
-    constexpr int M = K + 3;
-    const int nwarps = 4;
-    const int RW = 2 * a.R + PS;
-    const size_t smem = (size_t)nwarps * M * 16 + (size_t)nwarps * RW * RW * sizeof(float);
-    if (smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(k_match<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return check_launch("cudaFuncSetAttribute(k_match)");
-    }
-    const int blocks = (a.nref + nwarps - 1) / nwarps;
+    const int RHM = a.step + 2 * a.R + PS;
+    const int NCM = (2 * a.R + 1) * (2 * a.R + 1);
+    const size_t smem = (size_t)MW * 3 * PMAX * 8 + (size_t)(a.C == 3 ? 2 : 1) * RHM * RHM * sizeof(float) +
+                        (size_t)MW * NCM * sizeof(float);
+    if (cudaFuncSetAttribute(k_match<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return check_launch("cudaFuncSetAttribute(k_match)");
+    const int blocks = ((a.ny + 1) / 2) * ((a.nx + 1) / 2);
     {
         KTimer kt("k_match", s);
-        k_match<K><<<blocks, nwarps * 32, smem, s>>>(a);
+        k_match<K><<<blocks, MW * 32, smem, s>>>(a);
     }
     hts_status st = check_launch("k_match");
     if (st != HTS_OK) return st;
@@ -379,6 +455,7 @@ hts_status launch_match(const float *img, const Geom &g, double gamma_gcp, int32
     a.step = g.step;
     a.R = g.R;
     a.nx = g.nx;
+    a.ny = g.ny;
     a.nref = g.nref;
     a.gamma = gamma_gcp;
     a.idx = idx;

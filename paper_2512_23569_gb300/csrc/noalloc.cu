@@ -7,7 +7,7 @@
 // device array of this file, sized for images of at most 512 x 512 pixels
 // (any channel count the library supports), at most 65536 reference patches
 // and at most 2^20 group slots (N_ref * K).  Every GPU that loads the library
-// holds this array (about 14 MB) until the process exits.
+// holds this array (about 17 MB) until the process exits.
 #include <mutex>
 
 #include "hts_internal.h"
@@ -28,8 +28,8 @@ constexpr size_t OFF_B64 = OFF_STATE + align256(sizeof(DevState));
 constexpr size_t OFF_B32 = OFF_B64 + align256(2 * 256 * sizeof(double));
 constexpr size_t OFF_EIG = OFF_B32 + align256(2 * 256 * sizeof(float));
 constexpr size_t OFF_COV = OFF_EIG + align256(32 * sizeof(double));
-// covariance partial sums: (N_ref / 64 blocks) x 2 slices x 2 matrices x 36 entries x (re, im) + 2 x 2 x 128
-constexpr size_t COV_DOUBLES = (size_t)((NA_MAX_NREF + 63) / 64) * 2 * 2 * 36 * 2 + 2 * 2 * 64 * 2;
+// covariance sums: (N_ref / 64 blocks) x 600 channel-pair entries, then the 600 totals
+constexpr size_t COV_DOUBLES = (size_t)((NA_MAX_NREF + 63) / 64) * 600 + 600;
 constexpr size_t OFF_IDX = OFF_COV + align256(COV_DOUBLES * sizeof(double));
 constexpr size_t OFF_GREEN = OFF_IDX + align256(NA_MAX_SLOTS * sizeof(int32_t));
 constexpr size_t OFF_FB = OFF_GREEN + align256(NA_MAX_NREF);
@@ -85,6 +85,7 @@ extern "C" hts_status hts_denoise_noalloc(const float *noisy, float *out, int H,
         return report(HTS_EINVAL,
                       "image exceeds the static scratch of hts_denoise_noalloc (H*W <= 262144, N_ref <= 65536, "
                       "N_ref*K <= 1048576)");
+    if (cov_partial_count(g) > COV_DOUBLES) return report(HTS_EINTERNAL, "covariance scratch too small");
     st = check_basis(basis, C);
     if (st != HTS_OK) return st;
     unsigned char *base = nullptr;
@@ -120,7 +121,7 @@ extern "C" hts_status hts_denoise_noalloc(const float *noisy, float *out, int H,
     const double *ueig = (basis && basis->has_eig) ? basis->eig : eig;
     st = launch_match(noisy, g, p->gamma_gcp, idx, green, fb, ds, s);
     if (st != HTS_OK) return st;
-    if (sigma < 0) st = launch_sigma(noisy, g, *p, ueig, idx, ds, s);
+    if (sigma < 0) st = launch_sigma(noisy, g, *p, ueig, idx, redo, ds, s);
     else st = launch_set_sigma((double)sigma, g, *p, ds, s);
     if (st != HTS_OK) return st;
     return launch_filter(noisy, g, idx, ub64, ub32, acc, wcount, redo, ds, out, s);

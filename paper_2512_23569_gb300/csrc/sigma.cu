@@ -32,10 +32,7 @@ __global__ void k_sigma_est(const double *__restrict__ eig, int nvals, int nref,
         const double f = 1.0 - 1.0 / sqrt((double)nref);
         s2 = s2 / (f * f);
     }
-    st->sigma_est = sqrt(s2);
-    st->votes = 0;
-    st->vote_uncertain = 0;
-    st->nref = nref;
+    st->sigma_est = sqrt(s2);  // the vote counters are zeroed with the state and may be live on another stream
 }
 
 __device__ __forceinline__ void twiddle64(int j, int K, double &c, double &s) {
@@ -53,31 +50,111 @@ __device__ __forceinline__ void twiddle64(int j, int K, double &c, double &s) {
     s = -sn;
 }
 
+// exp(-2 pi i j / 32) = c_twc[j] + i c_tws[j], rounded to float (quarter turns
+// exact).  Indexed with warp-uniform j, they are read as constant operands.
+__constant__ float c_twc[32] = {
+    1.0f, 0.9807852506637573f, 0.9238795042037964f, 0.8314695954322815f,
+    0.7071067690849304f, 0.5555702447891235f, 0.3826834261417389f, 0.19509032368659973f,
+    0.0f, -0.19509032368659973f, -0.3826834261417389f, -0.5555702447891235f,
+    -0.7071067690849304f, -0.8314695954322815f, -0.9238795042037964f, -0.9807852506637573f,
+    -1.0f, -0.9807852506637573f, -0.9238795042037964f, -0.8314695954322815f,
+    -0.7071067690849304f, -0.5555702447891235f, -0.3826834261417389f, -0.19509032368659973f,
+    0.0f, 0.19509032368659973f, 0.3826834261417389f, 0.5555702447891235f,
+    0.7071067690849304f, 0.8314695954322815f, 0.9238795042037964f, 0.9807852506637573f,
+};
+__constant__ float c_tws[32] = {
+    0.0f, -0.19509032368659973f, -0.3826834261417389f, -0.5555702447891235f,
+    -0.7071067690849304f, -0.8314695954322815f, -0.9238795042037964f, -0.9807852506637573f,
+    -1.0f, -0.9807852506637573f, -0.9238795042037964f, -0.8314695954322815f,
+    -0.7071067690849304f, -0.5555702447891235f, -0.3826834261417389f, -0.19509032368659973f,
+    0.0f, 0.19509032368659973f, 0.3826834261417389f, 0.5555702447891235f,
+    0.7071067690849304f, 0.8314695954322815f, 0.9238795042037964f, 0.9807852506637573f,
+    1.0f, 0.9807852506637573f, 0.9238795042037964f, 0.8314695954322815f,
+    0.7071067690849304f, 0.5555702447891235f, 0.3826834261417389f, 0.19509032368659973f,
+};
+
+// The same twiddles in FP64 (correctly rounded cos / sin of 2 pi j / 32).
+__constant__ double c_twc64[32] = {
+    1.0, 0.9807852804032304, 0.9238795325112867, 0.8314696123025452,
+    0.7071067811865476, 0.5555702330196023, 0.38268343236508984, 0.19509032201612833,
+    0.0, -0.1950903220161282, -0.3826834323650897, -0.555570233019602,
+    -0.7071067811865475, -0.8314696123025453, -0.9238795325112867, -0.9807852804032304,
+    -1.0, -0.9807852804032304, -0.9238795325112868, -0.8314696123025455,
+    -0.7071067811865477, -0.5555702330196022, -0.38268343236509034, -0.19509032201612866,
+    0.0, 0.1950903220161283, 0.38268343236509, 0.5555702330196018,
+    0.7071067811865474, 0.8314696123025452, 0.9238795325112865, 0.9807852804032303,
+};
+__constant__ double c_tws64[32] = {
+    0.0, -0.19509032201612825, -0.3826834323650898, -0.5555702330196022,
+    -0.7071067811865475, -0.8314696123025452, -0.9238795325112867, -0.9807852804032304,
+    -1.0, -0.9807852804032304, -0.9238795325112867, -0.8314696123025455,
+    -0.7071067811865476, -0.5555702330196022, -0.3826834323650899, -0.1950903220161286,
+    0.0, 0.19509032201612836, 0.38268343236508967, 0.555570233019602,
+    0.7071067811865475, 0.8314696123025452, 0.9238795325112865, 0.9807852804032303,
+    1.0, 0.9807852804032304, 0.9238795325112866, 0.8314696123025455,
+    0.7071067811865477, 0.5555702330196022, 0.3826834323650904, 0.19509032201612872,
+};
+
+// FP64 lambda_m, m = 0..K/2 (lambda_{K-m} = lambda_m for real patches), of
+// the component range [d0, d1) of a group: one component per thread, block
+// sum in a fixed order.
+template <int C, int K>
+__device__ void lambda64_partial(const float *__restrict__ img, int H, int W, const int32_t *__restrict__ grp,
+                                 int d0, int d1, double *__restrict__ sm, double *__restrict__ out) {
+    constexpr int NM = K / 2 + 1;
+    const size_t HW = (size_t)H * W;
+    double l[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) l[m] = 0.0;
+    const int d = d0 + (int)threadIdx.x;
+    if (d < d1) {
+        const int c = d / NPIX, e = d - c * NPIX;
+        const size_t base = (size_t)c * HW + (size_t)(e >> 3) * W + (e & 7);
+        double p[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) p[k] = (double)__ldg(img + base + grp[k]);
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            double xr = 0.0, xi = 0.0;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int j = ((m * k) % K) * (32 / K);
+                xr += p[k] * c_twc64[j];
+                xi += p[k] * c_tws64[j];
+            }
+            l[m] = xr * xr + xi * xi;
+        }
+    }
+    // block sum, fixed order: warps by shuffle tree, then warp partials in order
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        double v = l[m];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+        if ((threadIdx.x & 31) == 0) sm[(threadIdx.x >> 5) * NM + m] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NM) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sm[w * NM + threadIdx.x];
+        out[threadIdx.x] = v;
+    }
+}
+
 template <int C, int K>
 __global__ void __launch_bounds__(128) k_vote(const float *__restrict__ img, int H, int W,
                                               const int32_t *__restrict__ idx, int nref, double gamma_rank,
-                                              DevState *st) {
+                                              int32_t *__restrict__ list, DevState *st) {
     constexpr int D = C * NPIX;
     constexpr int NM = K / 2 + 1;
-    __shared__ int s_votes, s_unc;
+    __shared__ int s_votes;
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        s_votes = 0;
-        s_unc = 0;
-    }
+    if (threadIdx.x == 0) s_votes = 0;
     __syncthreads();
-    float twc[K], tws[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        double c, s;
-        twiddle64(j, K, c, s);
-        twc[j] = (float)c;
-        tws[j] = (float)s;
-    }
     const size_t HW = (size_t)H * W;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    int my_votes = 0, my_unc = 0;
+    int my_votes = 0;
     for (int r = gw; r < nref; r += nw) {
         int off[K];
         {
@@ -89,6 +166,7 @@ __global__ void __launch_bounds__(128) k_vote(const float *__restrict__ img, int
 #pragma unroll
         for (int m = 0; m < NM; ++m) lam[m] = 0.f;
         float e0sq = 0.f, esq = 0.f;
+#pragma unroll 1
         for (int d = lane; d < D; d += 32) {
             const int c = d / NPIX, e = d - c * NPIX;
             const size_t base = (size_t)c * HW + (size_t)(e >> 3) * W + (e & 7);
@@ -115,9 +193,9 @@ __global__ void __launch_bounds__(128) k_vote(const float *__restrict__ img, int
                 float xr = 0.f, xi = 0.f;
 #pragma unroll
                 for (int k = 1; k < K; ++k) {
-                    const int j = (m * k) % K;
-                    xr = fmaf(q[k], twc[j], xr);
-                    xi = fmaf(q[k], tws[j], xi);
+                    const int j = ((m * k) % K) * (32 / K);
+                    xr = fmaf(q[k], c_twc[j], xr);
+                    xi = fmaf(q[k], c_tws[j], xi);
                 }
                 lam[m] = fmaf(xr, xr, fmaf(xi, xi, lam[m]));
             }
@@ -152,48 +230,42 @@ __global__ void __launch_bounds__(128) k_vote(const float *__restrict__ img, int
         if ((double)(1 + sure + unc) <= gamma_rank) vote = 1;
         else if ((double)(1 + sure) > gamma_rank) vote = 0;
         else {
-            // FP64: lambda_m for all m, rank of lambda_{K/2} (ties rank lowest)
-            double l64[K];
-#pragma unroll
-            for (int m = 0; m < K; ++m) l64[m] = 0.0;
-            for (int d = lane; d < D; d += 32) {
-                const int c = d / NPIX, e = d - c * NPIX;
-                const size_t base = (size_t)c * HW + (size_t)(e >> 3) * W + (e & 7);
-                double p[K];
-#pragma unroll
-                for (int k = 0; k < K; ++k) p[k] = (double)__ldg(img + base + off[k]);
-                for (int m = 0; m < K; ++m) {
-                    double xr = 0.0, xi = 0.0;
-                    for (int k = 0; k < K; ++k) {
-                        double cc, ss;
-                        twiddle64(m * k, K, cc, ss);
-                        xr += p[k] * cc;
-                        xi += p[k] * ss;
-                    }
-                    l64[m] += xr * xr + xi * xi;
-                }
+            vote = 0;  // decided in FP64 by k_vote_exact
+            if (lane == 0) {
+                const int pos = atomicAdd(&st->vote_uncertain, 1);
+                list[pos] = r;
             }
-#pragma unroll
-            for (int o = 16; o; o >>= 1)
-#pragma unroll
-                for (int m = 0; m < K; ++m) l64[m] += __shfl_xor_sync(FULL, l64[m], o);
-            int a = 1;
-#pragma unroll
-            for (int m = 0; m < K; ++m)
-                if (m != K / 2 && l64[m] < l64[K / 2]) ++a;
-            vote = ((double)a <= gamma_rank) ? 1 : 0;
-            ++my_unc;
         }
         my_votes += vote;
     }
-    if (lane == 0) {
-        atomicAdd(&s_votes, my_votes);
-        atomicAdd(&s_unc, my_unc);
-    }
+    if (lane == 0) atomicAdd(&s_votes, my_votes);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        atomicAdd(&st->votes, s_votes);
-        atomicAdd(&st->vote_uncertain, s_unc);
+    if (threadIdx.x == 0) atomicAdd(&st->votes, s_votes);
+}
+
+// The groups k_vote could not settle, decided in FP64: one block per listed
+// group, one thread per component (c * 64 of them), fixed-order block sum.
+template <int C, int K>
+__global__ void __launch_bounds__(C * NPIX) k_vote_exact(const float *__restrict__ img, int H, int W,
+                                                         const int32_t *__restrict__ idx, double gamma_rank,
+                                                         const int32_t *__restrict__ list, DevState *st) {
+    constexpr int NM = K / 2 + 1;
+    __shared__ double sm[(C * NPIX / 32) * NM];
+    __shared__ double lam[NM];
+    const int n = *(volatile int *)&st->vote_uncertain;
+    for (int g = blockIdx.x; g < n; g += gridDim.x) {
+        const int r = list[g];
+        lambda64_partial<C, K>(img, H, W, idx + (size_t)r * K, 0, C * NPIX, sm, lam);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int a = 1;  // rank of lambda_{K/2} among all K (m and K-m share a value)
+            for (int m = 0; m < K; ++m) {
+                const int mm = (m <= K / 2) ? m : K - m;
+                if (m != K / 2 && lam[mm] < lam[K / 2]) ++a;
+            }
+            if ((double)a <= gamma_rank) atomicAdd(&st->votes, 1);
+        }
+        __syncthreads();
     }
 }
 
@@ -226,42 +298,61 @@ double tau_scale(const Geom &g, const hts_params &p) {
 }
 
 template <int C, int K>
-hts_status launch_vote(const float *img, const Geom &g, const int32_t *idx, double gamma_rank, DevState *st,
-                       cudaStream_t s) {
+hts_status launch_vote(const float *img, const Geom &g, const int32_t *idx, double gamma_rank, int32_t *list,
+                       DevState *st, cudaStream_t s) {
     int blocks = (g.nref + 3) / 4;
     if (blocks > 152 * 8) blocks = 152 * 8;
     {
         KTimer kt("k_vote", s);
-        k_vote<C, K><<<blocks, 128, 0, s>>>(img, g.H, g.W, idx, g.nref, gamma_rank, st);
+        k_vote<C, K><<<blocks, 128, 0, s>>>(img, g.H, g.W, idx, g.nref, gamma_rank, list, st);
     }
-    return check_launch("k_vote");
+    if (hts_status e = check_launch("k_vote"); e != HTS_OK) return e;
+    {
+        KTimer kt("k_vote_exact", s);
+        k_vote_exact<C, K><<<152, C * NPIX, 0, s>>>(img, g.H, g.W, idx, gamma_rank, list, st);
+    }
+    return check_launch("k_vote_exact");
 }
 
 }  // namespace
 
-hts_status launch_sigma(const float *img, const Geom &g, const hts_params &p, const double *eig, const int32_t *idx,
-                        DevState *st, cudaStream_t s) {
+hts_status launch_sigma_floor(const Geom &g, const hts_params &p, const double *eig, DevState *st, cudaStream_t s) {
     const int ns = g.C / 2 + 1;
     {
         KTimer kt("k_sigma_est", s);
         k_sigma_est<<<1, 32, 0, s>>>(eig, ns * 2 * 8, g.nref, p.mp_correct, st);
     }
-    if (hts_status e = check_launch("k_sigma_est"); e != HTS_OK) return e;
+    return check_launch("k_sigma_est");
+}
+
+hts_status launch_sigma_vote(const float *img, const Geom &g, const hts_params &p, const int32_t *idx,
+                             int32_t *list, DevState *st, cudaStream_t s) {
     const double gamma = p.gamma_rank > 0 ? p.gamma_rank : 13.0 * g.K / 32.0;
     if (p.adjust_rank) {
         hts_status e = HTS_EUNSUPPORTED;
 #define HTS_VOTE_CASE(CC, KK) \
-    if (g.C == CC && g.K == KK) e = launch_vote<CC, KK>(img, g, idx, gamma, st, s);
+    if (g.C == CC && g.K == KK) e = launch_vote<CC, KK>(img, g, idx, gamma, list, st, s);
         HTS_VOTE_CASE(1, 2) HTS_VOTE_CASE(1, 4) HTS_VOTE_CASE(1, 8) HTS_VOTE_CASE(1, 16) HTS_VOTE_CASE(1, 32)
         HTS_VOTE_CASE(3, 2) HTS_VOTE_CASE(3, 4) HTS_VOTE_CASE(3, 8) HTS_VOTE_CASE(3, 16) HTS_VOTE_CASE(3, 32)
 #undef HTS_VOTE_CASE
         if (e != HTS_OK) return e;
     }
+    return HTS_OK;
+}
+
+hts_status launch_sigma_final(const Geom &g, const hts_params &p, DevState *st, cudaStream_t s) {
     {
         KTimer kt("k_sigma_final", s);
         k_sigma_final<<<1, 32, 0, s>>>(st, g.nref, p.adjust_rank, p.beta, tau_scale(g, p));
     }
     return check_launch("k_sigma_final");
+}
+
+hts_status launch_sigma(const float *img, const Geom &g, const hts_params &p, const double *eig, const int32_t *idx,
+                        int32_t *list, DevState *st, cudaStream_t s) {
+    if (hts_status e = launch_sigma_floor(g, p, eig, st, s); e != HTS_OK) return e;
+    if (hts_status e = launch_sigma_vote(img, g, p, idx, list, st, s); e != HTS_OK) return e;
+    return launch_sigma_final(g, p, st, s);
 }
 
 hts_status launch_set_sigma(double sigma, const Geom &g, const hts_params &p, DevState *st, cudaStream_t s) {
