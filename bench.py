@@ -143,17 +143,17 @@ class ClockSampler:
 # ------------------------------------------------------------------ helpers
 
 def _dist():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2512_23569_gb300 import dist as hd
+
+    return hd.env_rank()
 
 
 def _image(rank):
+    from paper_2512_23569_gb300 import dist as hd
     from paper_2512_23569_gb300 import synth
 
     w = WORKLOAD
-    return synth.make_config_image(w["H"], w["W"], w["C"], w["sigma"], w["seed"] + 10 * rank)
+    return synth.make_config_image(w["H"], w["W"], w["C"], w["sigma"], hd.image_seed(w["seed"], rank))
 
 
 def _oracle_params():
@@ -219,6 +219,7 @@ def run_ours(args):
     import torch
 
     from paper_2512_23569_gb300 import build, hts, synth
+    from paper_2512_23569_gb300 import dist as hd
 
     rank, world, local = _dist()
     if world > 1:
@@ -263,10 +264,7 @@ def run_ours(args):
         torch.distributed.barrier()
     clk = clocks.stop()
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    max_ms = float(t.item())
+    max_ms = hd.max_over_ranks(total_ms, device="cuda")
     value = world * args.steps * w["H"] * w["W"] / (max_ms / 1e3) / 1e6
 
     # end to end through the host-buffer C-ABI call (pinned host memory)
@@ -281,10 +279,7 @@ def run_ours(args):
     for _ in range(args.steps):
         hts.denoise_host(hxn, sigma=None, p=p, out=hon)
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-    e2e_val = world * args.steps * w["H"] * w["W"] / float(te.item()) / 1e6
+    e2e_val = world * args.steps * w["H"] * w["W"] / hd.max_over_ranks(e2e_s, device="cuda") / 1e6
 
     if rank != 0:
         if world > 1:
