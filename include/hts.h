@@ -138,7 +138,7 @@ hts_status hts_denoise(const float *noisy, float *out, int H, int W, int C, floa
  * the implicit device synchronisation of cudaMalloc / cudaFree.  The paper
  * has no counterpart; this is a deployment variant of hts_denoise.
  * All intermediate buffers live in one static device array of the library
- * (about 17 MB, held by every GPU that loads the library until the process
+ * (about 18 MB, held by every GPU that loads the library until the process
  * exits).  That bounds the image: H*W <= 262144 pixels, at most 65536
  * reference patches and N_ref*K <= 1048576; larger images return HTS_EINVAL
  * before any device work.  The caller still passes `noisy` and `out` (device);
@@ -189,11 +189,12 @@ typedef struct {
     int nref;
     int match_reranked;    /* references whose order was settled by the FP64 re-rank */
     int match_fallback;    /* references matched by the exhaustive FP64 path */
-    int filter_redo;       /* groups with a coefficient inside the FP32 guard band */
+    int filter_redo;       /* groups recomputed by the FP64 exact pass (in-band list full) */
     int filter_exact;      /* coefficients whose threshold decision was taken in FP64 */
     int vote_uncertain;    /* groups whose rank test was taken in FP64 */
     double sigma;          /* noise level used */
     double tau;            /* threshold used */
+    int filter_fixed;      /* FP64 decisions that overturned the FP32 one (contribution corrected) */
 } hts_stats;
 hts_status hts_last_stats(hts_stats *out, void *stream);
 

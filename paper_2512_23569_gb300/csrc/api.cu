@@ -100,6 +100,10 @@ struct Workspace {
     uint8_t *green = nullptr;
     int32_t *fb = nullptr;
     int32_t *redo = nullptr;
+    int4 *xlist = nullptr;
+    size_t cap_x = 0;
+    uint8_t *xskip = nullptr;
+    size_t cap_xskip = 0;
     long long *acc = nullptr;
     int *wcount = nullptr;
     double *cov = nullptr;
@@ -161,6 +165,8 @@ static hts_status ensure(Workspace *w, const Geom &g) {
     HTS_TRY(grow(w->idx, w->cap_idx, nref * g.K, "cudaMalloc(idx)"));
     HTS_TRY(grow(w->fb, w->cap_fb, nref, "cudaMalloc(fallback)"));
     HTS_TRY(grow(w->redo, w->cap_redo, nref, "cudaMalloc(redo)"));
+    HTS_TRY(grow(w->xlist, w->cap_x, nref, "cudaMalloc(xlist)"));
+    HTS_TRY(grow(w->xskip, w->cap_xskip, nref, "cudaMalloc(xskip)"));
     HTS_TRY(grow(w->green, w->cap_green, nref, "cudaMalloc(green)"));
     HTS_TRY(grow(w->acc, w->cap_chw, hw * g.C, "cudaMalloc(acc)"));
     HTS_TRY(grow(w->wcount, w->cap_hw, hw, "cudaMalloc(weights)"));
@@ -298,7 +304,7 @@ static hts_status denoise_impl(const float *noisy, float *out, const Geom &g, fl
     if (fork) HTS_TRY(cuda_ok(cudaStreamWaitEvent(s, w->ev_join, 0), "cudaStreamWaitEvent"));
     if (need_sigma) HTS_TRY(launch_sigma_final(g, p, w->st, s));
     else HTS_TRY(launch_set_sigma((double)sigma, g, p, w->st, s));
-    return launch_filter(noisy, g, w->idx, b64, b32, w->acc, w->wcount, w->redo, w->st, out, s);
+    return launch_filter(noisy, g, w->idx, b64, b32, w->acc, w->wcount, w->redo, w->xlist, w->xskip, w->st, out, s);
 }
 
 }  // namespace hts
@@ -555,6 +561,7 @@ hts_status hts_last_stats(hts_stats *out, void *stream) {
     out->vote_uncertain = hs.vote_uncertain;
     out->sigma = hs.sigma_hat;
     out->tau = hs.tau;
+    out->filter_fixed = hs.filter_fixed;
     return HTS_OK;
 }
 
@@ -618,6 +625,8 @@ hts_status hts_shutdown(void) {
         cudaFree(w->green);
         cudaFree(w->fb);
         cudaFree(w->redo);
+        cudaFree(w->xlist);
+        cudaFree(w->xskip);
         cudaFree(w->acc);
         cudaFree(w->wcount);
         cudaFree(w->cov);

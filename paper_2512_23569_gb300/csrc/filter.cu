@@ -56,6 +56,9 @@ struct FilterArgs {
     long long *acc;
     int *wcount;
     int32_t *redo;
+    int4 *xlist;  // in-band coefficients: (group, keep<<16 | row<<8 | stream, re, im)
+    int xcap;
+    uint8_t *xskip;  // [N_ref] 1 = group went to the exact pass
     DevState *st;
 };
 
@@ -671,6 +674,30 @@ struct TileCfg {
     static constexpr int PSW = 8 * RS + 4;         // patch stride (bank-shifted)
 };
 
+constexpr int NSPARSE = 32;  // groups with at most this many kept coefficients are rebuilt from the list
+
+// Entry (h, k) of the Haar matrix of Eq. 8 in FP32: row 0 is 1/sqrt(K); row
+// h >= 1 (2^l <= h < 2^(l+1)) is +-1/sqrt(L) on its support of L = K / 2^l
+// patches (first half +, second half -), 0 elsewhere.
+__device__ __forceinline__ float inv_sqrt_pow2(int L) {
+    switch (L) {
+        case 1: return 1.0f;
+        case 2: return 0.70710678118654752f;
+        case 4: return 0.5f;
+        case 8: return 0.35355339059327376f;
+        case 16: return 0.25f;
+        default: return 0.17677669529663688f;  // 32
+    }
+}
+template <int K>
+__device__ __forceinline__ float haar_entry_f32(int h, int k) {
+    if (h == 0) return inv_sqrt_pow2(K);
+    const int l = 31 - __clz(h), L = K >> l, i = h - (1 << l);
+    if (k < i * L || k >= (i + 1) * L) return 0.f;
+    const float m = inv_sqrt_pow2(L);
+    return (k < i * L + L / 2) ? m : -m;
+}
+
 // Row-indexed basis copies (row stride BROW) for the block-parallel factors.
 struct RBasis {
     float u0[8 * BROW], u0t[8 * BROW];
@@ -708,11 +735,17 @@ __global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t
     float *ssq = tbuf + PPB * PSW;                                                        // [TPB / 32]
     float *gband = ssq + TPB / 32;                                        // [GPB]
     int *gflag = reinterpret_cast<int *>(gband + GPB);                    // [GPB]
-    int *accs = gflag + GPB;                                              // hi[C][RA] lo[C][RA] w[RA]
+    int *gkept = gflag + GPB;                                             // kept coefficients per group
+    int *grefs = gkept + GPB;                                             // reference index per group
+    int *gv = grefs + GPB;                                                // group slot holds a group
+    int *glen = gv + GPB;                                                 // [GPB] kept-list lengths
+    int *klist = glen + GPB;                                              // [GPB][NSPARSE] kept (row, stream)
+    int *accs = klist + GPB * NSPARSE;                                    // hi[C][RA] lo[C][RA] w[RA]
     const int RA = t.rh_max * t.rw_max;
     int *acc_hi = accs, *acc_lo = accs + C * RA, *acc_w = accs + 2 * C * RA;
 
     const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
     const int ps = tid >> 3, row = tid & 7;  // patch slot, row
     const int gb = ps / K, k = ps - gb * K;  // group in flight, patch in group
     const int tg = tid - gb * TPG;           // thread within group
@@ -746,6 +779,12 @@ __global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t
             const int r = valid ? gy * a.nx + gx : 0;
             int py = 0, px = 0;
             float ss = 0.f;
+            if (tg == 0) {
+                gkept[gb] = 0;
+                glen[gb] = 0;
+                grefs[gb] = r;
+                gv[gb] = valid ? 1 : 0;
+            }
             // ---- forward, factor 1: row `row` of Phat V
             if (valid) {
                 const int pos = a.idx[(size_t)r * K + k];
@@ -869,11 +908,14 @@ __global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t
                 }
             }
             __syncthreads();
-            // ---- Haar along the group axis, threshold, inverse Haar (one stream per thread)
+            // ---- Haar along the group axis and threshold, one coefficient stream per
+            //      thread; the thresholded Haar-domain values stay in place.  A value
+            //      inside the guard band is decided in FP32 here and recorded; the
+            //      correction pass takes its decision in FP64.
             if (valid) {
                 float *cg = coef + (gb * K) * CROW;
                 const float band = gband[gb];
-                int flag = 0;
+                int kept = 0;
 #pragma unroll 1
                 for (int it = tg; it < IPG; it += TPG) {
                     if (it < 64) {
@@ -884,13 +926,26 @@ __global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t
                         haar_fwd<K>(x);
 #pragma unroll
                         for (int q = 0; q < K; ++q) {
-                            const int d = decide(fabsf(x[q]), tau, band);
-                            flag |= (d == 2);
-                            x[q] = (d == 0) ? 0.f : x[q];
+                            int d = decide(fabsf(x[q]), tau, band);
+                            if (d == 2) {  // FP32 decides for now; the FP64 decision may correct it
+                                const int keep = fabsf(x[q]) >= tau ? 1 : 0;
+                                const int slot = atomicAdd(&a.st->xcount, 1);
+                                if (slot < a.xcap) {
+                                    a.xlist[slot] = make_int4(r, (keep << 16) | (q << 8) | it, __float_as_int(x[q]), 0);
+                                } else {
+                                    gflag[gb] = 1;
+                                }
+                                d = keep;
+                            }
+                            if (d == 0) {
+                                x[q] = 0.f;
+                            } else {
+                                ++kept;
+                                const int slot = atomicAdd(glen + gb, 1);
+                                if (slot < NSPARSE) klist[gb * NSPARSE + slot] = (q << 8) | it;
+                            }
+                            cg[q * CROW + pe] = x[q];
                         }
-                        haar_inv<K>(x);
-#pragma unroll
-                        for (int q = 0; q < K; ++q) cg[q * CROW + pe] = x[q];
                     } else {
                         const int pr = cpos(it), pi = cpos(it + 64);
                         float xr[K], xi[K];
@@ -904,9 +959,74 @@ __global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t
 #pragma unroll
                         for (int q = 0; q < K; ++q) {
                             const float mag = sqrtf(xr[q] * xr[q] + xi[q] * xi[q]);
-                            const int d = decide(mag, tau, band);
-                            flag |= (d == 2);
-                            if (d == 0) { xr[q] = 0.f; xi[q] = 0.f; }
+                            int d = decide(mag, tau, band);
+                            if (d == 2) {  // FP32 decides for now; the FP64 decision may correct it
+                                const int keep = mag >= tau ? 1 : 0;
+                                const int slot = atomicAdd(&a.st->xcount, 1);
+                                if (slot < a.xcap) {
+                                    a.xlist[slot] = make_int4(r, (keep << 16) | (q << 8) | it, __float_as_int(xr[q]),
+                                                              __float_as_int(xi[q]));
+                                } else {
+                                    gflag[gb] = 1;
+                                }
+                                d = keep;
+                            }
+                            if (d == 0) {
+                                xr[q] = 0.f;
+                                xi[q] = 0.f;
+                            } else {
+                                ++kept;
+                                const int slot = atomicAdd(glen + gb, 1);
+                                if (slot < NSPARSE) klist[gb * NSPARSE + slot] = (q << 8) | it;
+                            }
+                            cg[q * CROW + pr] = xr[q];
+                            cg[q * CROW + pi] = xi[q];
+                        }
+                    }
+                }
+                if (kept) atomicAdd(gkept + gb, kept);
+            }
+            __syncthreads();
+            const bool agg = valid && gflag[gb] == 0;
+            const bool sparse = agg && glen[gb] <= NSPARSE;
+            if (valid && tg == 0) {
+                a.xskip[r] = agg ? 0 : 1;  // a redone group takes no corrections
+                if (!agg) {
+                    const int pos = atomicAdd(&a.st->filter_redo, 1);
+                    a.redo[pos] = r;
+                }
+            }
+            // ---- kept lists of the sparse groups, sorted by (Haar row, stream) so that
+            //      the reconstruction adds them in a fixed order
+            for (int g2 = warp; g2 < GPB; g2 += TPB / 32) {
+                if (!gv[g2] || gflag[g2] != 0 || glen[g2] > NSPARSE) continue;
+                const int n = glen[g2];
+                const int code = (lane < n) ? klist[g2 * NSPARSE + lane] : 0x7fffffff;
+                int rank = 0;
+                for (int j = 0; j < n; ++j) rank += (__shfl_sync(FULL, code, j) < code) ? 1 : 0;
+                __syncwarp();
+                if (lane < n) klist[g2 * NSPARSE + rank] = code;
+            }
+            // ---- dense groups: inverse Haar along the group axis
+            if (agg && !sparse) {
+                float *cg = coef + (gb * K) * CROW;
+#pragma unroll 1
+                for (int it = tg; it < IPG; it += TPG) {
+                    if (it < 64) {
+                        const int pe = cpos(it);
+                        float x[K];
+#pragma unroll
+                        for (int q = 0; q < K; ++q) x[q] = cg[q * CROW + pe];
+                        haar_inv<K>(x);
+#pragma unroll
+                        for (int q = 0; q < K; ++q) cg[q * CROW + pe] = x[q];
+                    } else {
+                        const int pr = cpos(it), pi = cpos(it + 64);
+                        float xr[K], xi[K];
+#pragma unroll
+                        for (int q = 0; q < K; ++q) {
+                            xr[q] = cg[q * CROW + pr];
+                            xi[q] = cg[q * CROW + pi];
                         }
                         haar_inv<K>(xr);
                         haar_inv<K>(xi);
@@ -917,16 +1037,10 @@ __global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t
                         }
                     }
                 }
-                if (flag) gflag[gb] = 1;
             }
             __syncthreads();
-            const bool agg = valid && gflag[gb] == 0;
-            if (valid && !agg && tg == 0) {
-                const int pos = atomicAdd(&a.st->filter_redo, 1);
-                a.redo[pos] = r;
-            }
-            // ---- inverse, factor 1: row `row` (= i) of Shat V^H
-            if (agg) {
+            // ---- dense groups, inverse factor 1: row `row` (= i) of Shat V^H
+            if (agg && !sparse) {
                 const float *S = coef + ps * CROW;
                 const float *S0 = S + cpos(row * 8), *S1r = S + cpos(64 + row * 8), *S1i = S + cpos(128 + row * 8);
                 const float4 x0 = ld4(S0), x1 = ld4(S0 + 4);
@@ -970,50 +1084,104 @@ __global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t
                 }
             }
             __syncthreads();
-            // ---- inverse, factor 2: row `row` (= a) of U Q, inverse DFT, aggregation
+            // ---- inverse factor 2 (dense) or the kept list (sparse): row `row` (= a)
+            //      of P_hat, inverse DFT, aggregation
             if (agg) {
-                const float *Q = tbuf + ps * PSW;
-                const float4 c0 = ld4(rb.u0 + row * BROW), c1 = ld4(rb.u0 + row * BROW + 4);
-                const float ua[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-                float p0[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float4 x0 = ld4(Q + i * RS), x1 = ld4(Q + i * RS + 4);
-                    const float qv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-#pragma unroll
-                    for (int bb = 0; bb < 8; ++bb) p0[bb] = fmaf(ua[i], qv[bb], p0[bb]);
-                }
                 float out[3][8];
-                if (C == 1) {
-#pragma unroll
-                    for (int bb = 0; bb < 8; ++bb) out[0][bb] = p0[bb];
-                } else {
-                    const float4 r0 = ld4(rb.u1r + row * BROW), r1 = ld4(rb.u1r + row * BROW + 4);
-                    const float4 i0 = ld4(rb.u1i + row * BROW), i1 = ld4(rb.u1i + row * BROW + 4);
-                    const float ur[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-                    const float ui[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
-                    float pr[8], pi[8];
-#pragma unroll
-                    for (int bb = 0; bb < 8; ++bb) { pr[bb] = 0.f; pi[bb] = 0.f; }
+                if (!sparse) {
+                    const float *Q = tbuf + ps * PSW;
+                    const float4 c0 = ld4(rb.u0 + row * BROW), c1 = ld4(rb.u0 + row * BROW + 4);
+                    const float ua[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+                    float p0[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        const float4 a0 = ld4(Q + i * RS + 8), a1 = ld4(Q + i * RS + 12);
-                        const float4 b0 = ld4(Q + i * RS + 16), b1 = ld4(Q + i * RS + 20);
-                        const float qr[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                        const float qi[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                        const float4 x0 = ld4(Q + i * RS), x1 = ld4(Q + i * RS + 4);
+                        const float qv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-                        for (int bb = 0; bb < 8; ++bb) {  // u * q
-                            pr[bb] = fmaf(ur[i], qr[bb], pr[bb]);
-                            pr[bb] = fmaf(-ui[i], qi[bb], pr[bb]);
-                            pi[bb] = fmaf(ur[i], qi[bb], pi[bb]);
-                            pi[bb] = fmaf(ui[i], qr[bb], pi[bb]);
+                        for (int bb = 0; bb < 8; ++bb) p0[bb] = fmaf(ua[i], qv[bb], p0[bb]);
+                    }
+                    if (C == 1) {
+#pragma unroll
+                        for (int bb = 0; bb < 8; ++bb) out[0][bb] = p0[bb];
+                    } else {
+                        const float4 r0 = ld4(rb.u1r + row * BROW), r1 = ld4(rb.u1r + row * BROW + 4);
+                        const float4 i0 = ld4(rb.u1i + row * BROW), i1 = ld4(rb.u1i + row * BROW + 4);
+                        const float ur[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+                        const float ui[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+                        float pr[8], pi[8];
+#pragma unroll
+                        for (int bb = 0; bb < 8; ++bb) { pr[bb] = 0.f; pi[bb] = 0.f; }
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const float4 a0 = ld4(Q + i * RS + 8), a1 = ld4(Q + i * RS + 12);
+                            const float4 b0 = ld4(Q + i * RS + 16), b1 = ld4(Q + i * RS + 20);
+                            const float qr[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                            const float qi[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                            for (int bb = 0; bb < 8; ++bb) {  // u * q
+                                pr[bb] = fmaf(ur[i], qr[bb], pr[bb]);
+                                pr[bb] = fmaf(-ui[i], qi[bb], pr[bb]);
+                                pi[bb] = fmaf(ur[i], qi[bb], pi[bb]);
+                                pi[bb] = fmaf(ui[i], qr[bb], pi[bb]);
+                            }
+                        }
+#pragma unroll
+                        for (int bb = 0; bb < 8; ++bb) {
+                            out[0][bb] = (p0[bb] + 2.f * pr[bb]) * K3F;
+                            out[1][bb] = (p0[bb] - pr[bb] - 2.f * S3H * pi[bb]) * K3F;
+                            out[2][bb] = (p0[bb] - pr[bb] + 2.f * S3H * pi[bb]) * K3F;
                         }
                     }
+
+                } else {
+                    // P_hat_k[a][b] = sum over kept (h, i, j) of H[h][k] s U[a][i] conj(V[b][j])
+                    float p0[8], pr[8], pi[8];
 #pragma unroll
-                    for (int bb = 0; bb < 8; ++bb) {
-                        out[0][bb] = (p0[bb] + 2.f * pr[bb]) * K3F;
-                        out[1][bb] = (p0[bb] - pr[bb] - 2.f * S3H * pi[bb]) * K3F;
-                        out[2][bb] = (p0[bb] - pr[bb] + 2.f * S3H * pi[bb]) * K3F;
+                    for (int bb = 0; bb < 8; ++bb) { p0[bb] = 0.f; pr[bb] = 0.f; pi[bb] = 0.f; }
+                    const int *kl = klist + gb * NSPARSE;
+                    const float *cgk = coef + (gb * K) * CROW;
+                    const int nl = glen[gb];
+                    for (int e = 0; e < nl; ++e) {
+                        const int code = kl[e];
+                        const int hq = code >> 8, it = code & 0xff;
+                        const float hv = haar_entry_f32<K>(hq, k);
+                        if (hv == 0.f) continue;
+                        // current value: zero if the FP64 decision dropped it
+                        const float vr = cgk[hq * CROW + cpos(it)] * hv;
+                        const float vi = (it >= 64) ? cgk[hq * CROW + cpos(it + 64)] * hv : 0.f;
+                        if (it < 64) {
+                            const float w = vr * rb.u0[row * BROW + (it >> 3)];
+                            const float4 c0 = ld4(sb.v0t + (it & 7) * 8), c1 = ld4(sb.v0t + (it & 7) * 8 + 4);
+                            const float vc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                            for (int bb = 0; bb < 8; ++bb) p0[bb] = fmaf(w, vc[bb], p0[bb]);
+                        } else if (C == 3) {
+                            const int e1 = it - 64, i = e1 >> 3, j = e1 & 7;
+                            const float ur = rb.u1r[row * BROW + i], ui = rb.u1i[row * BROW + i];
+                            const float wr = vr * ur - vi * ui, wi = vr * ui + vi * ur;  // s u
+                            const float4 r0 = ld4(sb.v1rt + j * 8), r1 = ld4(sb.v1rt + j * 8 + 4);
+                            const float4 i0 = ld4(sb.v1it + j * 8), i1 = ld4(sb.v1it + j * 8 + 4);
+                            const float cr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+                            const float ci[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
+#pragma unroll
+                            for (int bb = 0; bb < 8; ++bb) {  // (s u) conj(v)
+                                pr[bb] = fmaf(wr, cr[bb], pr[bb]);
+                                pr[bb] = fmaf(wi, ci[bb], pr[bb]);
+                                pi[bb] = fmaf(wi, cr[bb], pi[bb]);
+                                pi[bb] = fmaf(-wr, ci[bb], pi[bb]);
+                            }
+                        }
+                    }
+                    if (C == 1) {
+#pragma unroll
+                        for (int bb = 0; bb < 8; ++bb) out[0][bb] = p0[bb];
+                    } else {
+#pragma unroll
+                        for (int bb = 0; bb < 8; ++bb) {
+                            out[0][bb] = (p0[bb] + 2.f * pr[bb]) * K3F;
+                            out[1][bb] = (p0[bb] - pr[bb] - 2.f * S3H * pi[bb]) * K3F;
+                            out[2][bb] = (p0[bb] - pr[bb] + 2.f * S3H * pi[bb]) * K3F;
+                        }
                     }
                 }
                 if (t.local) {
@@ -1066,6 +1234,69 @@ __global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t
     }
 }
 
+// FP64 decisions of the in-band coefficients recorded by k_filter_tile, one
+// warp each.  Where FP64 disagrees with the tentative FP32 decision, the
+// coefficient's contribution to the group's estimate -- separable: Haar row h
+// over its patch support, u_i v_j^H within each patch -- is added (FP64 keeps
+// it) or subtracted (FP64 drops it), in the same fixed-point sums.
+template <int C, int K>
+__global__ void __launch_bounds__(128) k_filter_fix(FilterArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int n = min(*(volatile int *)&a.st->xcount, a.xcap);
+    const double tau64 = a.st->tau;
+    const size_t HW = (size_t)a.H * a.W;
+    for (int f = gw; f < n; f += nw) {
+        const int4 e = a.xlist[f];
+        const int r = e.x, keep32 = (e.y >> 16) & 1, h = (e.y >> 8) & 0xff, it = e.y & 0xff;
+        if (a.xskip[r]) continue;  // the exact pass recomputes this group
+        const int j = it < 64 ? 0 : 1, ei = it < 64 ? it : it - 64;
+        const int32_t *grp = a.idx + (size_t)r * K;
+        double re, im;
+        exact_coef<C>(a, grp, K, h, j, ei, lane, re, im);
+        const int keep64 = (((j == 0) ? fabs(re) : sqrt(re * re + im * im)) >= tau64) ? 1 : 0;
+        if (lane == 0) atomicAdd(&a.st->filter_exact, 1);
+        if (keep64 == keep32) continue;
+        if (lane == 0) atomicAdd(&a.st->filter_fixed, 1);
+        const float sgn = keep64 ? 1.f : -1.f;
+        const float sr = __int_as_float(e.z) * sgn, si = __int_as_float(e.w) * sgn;
+        const int i = ei >> 3, jj = ei & 7;
+        const float *U = a.b32 + (size_t)((j * 2 + 0) * 64) * 2;
+        const float *V = a.b32 + (size_t)((j * 2 + 1) * 64) * 2;
+        for (int k = 0; k < K; ++k) {
+            const float hv = haar_entry_f32<K>(h, k);
+            if (hv == 0.f) continue;
+            const int pos = grp[k];
+            const int py = pos / a.W, px = pos - py * a.W;
+            for (int pe = lane; pe < 64; pe += 32) {
+                const int aa = pe >> 3, bb = pe & 7;
+                const float ur = U[(aa * 8 + i) * 2], ui = U[(aa * 8 + i) * 2 + 1];
+                const float vr = V[(bb * 8 + jj) * 2], vi = V[(bb * 8 + jj) * 2 + 1];
+                // hv s u conj(v)
+                const float tr = hv * (sr * ur - si * ui), ti = hv * (sr * ui + si * ur);
+                const float pr = tr * vr + ti * vi, pim = ti * vr - tr * vi;
+                const size_t o = (size_t)(py + aa) * a.W + px + bb;
+                if (C == 1) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + o), (unsigned long long)fix16(pr));
+                } else if (j == 0) {
+                    const float v = pr * K3F;  // slice 0 is (R+G+B)/sqrt 3: equal share per channel
+                    for (int c = 0; c < 3; ++c)
+                        atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + c * HW + o),
+                                  (unsigned long long)fix16(v));
+                } else {
+                    const float R = 2.f * pr * K3F;
+                    const float G = (-pr - 2.f * S3H * pim) * K3F;
+                    const float B = (-pr + 2.f * S3H * pim) * K3F;
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + o), (unsigned long long)fix16(R));
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + HW + o), (unsigned long long)fix16(G));
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + 2 * HW + o), (unsigned long long)fix16(B));
+                }
+            }
+        }
+    }
+}
+
 // out = sum / (2^16 * weight)
 __global__ void k_normalize(const long long *__restrict__ acc, const int *__restrict__ wcount, float *__restrict__ out,
                             size_t HW, int C) {
@@ -1085,11 +1316,11 @@ size_t exact_smem() {
     return sizeof(SBasis) + (size_t)2 * (GS + 1 + NMASK + QCAP + 1) * 4;
 }
 
-template <int C>
+template <int C, int K>
 size_t tile_fixed_smem() {
-    constexpr int GPBmax = PPB / 2;
+    constexpr int GPB = PPB / K;
     return sizeof(SBasis) + sizeof(RBasis) +
-           ((size_t)PPB * CROW + (size_t)PPB * TileCfg<C>::PSW + TPB / 32 + 2 * GPBmax) * 4;
+           ((size_t)PPB * CROW + (size_t)PPB * TileCfg<C>::PSW + TPB / 32 + 6 * GPB + (size_t)GPB * NSPARSE) * 4;
 }
 
 template <int C, int K>
@@ -1098,7 +1329,7 @@ hts_status launch_ck(const FilterArgs &a, const Geom &g, float *out, cudaStream_
     // tile shape: the largest of these whose search region fits in shared memory
     static const int shapes[][2] = {{4, 8}, {4, 4}, {2, 4}, {2, 2}, {1, 2}, {1, 1}};
     const size_t budget = 227 * 1024;
-    const size_t fixed = tile_fixed_smem<C>();
+    const size_t fixed = tile_fixed_smem<C, K>();
     TileArgs ta;
     ta.local = 0;
     ta.ty = 4;
@@ -1146,6 +1377,12 @@ hts_status launch_ck(const FilterArgs &a, const Geom &g, float *out, cudaStream_
     }
     st = check_launch("k_filter_exact");
     if (st != HTS_OK) return st;
+    {
+        KTimer kt("k_filter_fix", s);
+        k_filter_fix<C, K><<<nsm, 128, 0, s>>>(a);
+    }
+    st = check_launch("k_filter_fix");
+    if (st != HTS_OK) return st;
     int nb = (int)((HW * C + 255) / 256);
     if (nb > nsm * 16) nb = nsm * 16;
     {
@@ -1158,7 +1395,8 @@ hts_status launch_ck(const FilterArgs &a, const Geom &g, float *out, cudaStream_
 }  // namespace
 
 hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, const double *b64, const float *b32,
-                         long long *acc, int *wcount, int32_t *redo_list, DevState *st, float *out, cudaStream_t s) {
+                         long long *acc, int *wcount, int32_t *redo_list, int4 *xlist, uint8_t *xskip,
+                         DevState *st, float *out, cudaStream_t s) {
     FilterArgs a;
     a.img = img;
     a.H = g.H;
@@ -1174,6 +1412,9 @@ hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, co
     a.acc = acc;
     a.wcount = wcount;
     a.redo = redo_list;
+    a.xlist = xlist;
+    a.xcap = g.nref;
+    a.xskip = xskip;
     a.st = st;
 #define HTS_FILTER_CASE(CC, KK) \
     if (g.C == CC && g.K == KK) return launch_ck<CC, KK>(a, g, out, s);

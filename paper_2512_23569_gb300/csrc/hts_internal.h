@@ -27,7 +27,9 @@ struct DevState {
     int match_reranked;
     int match_fallback;   // length of the fallback list
     int filter_redo;      // length of the redo list
-    int filter_exact;
+    int filter_exact;     // FP64 threshold decisions taken
+    int filter_fixed;     // of which disagreed with FP32 and were corrected
+    int xcount;           // in-band coefficients recorded by the main pass
     int error;
 };
 
@@ -98,8 +100,10 @@ hts_status launch_sigma_vote(const float *img, const Geom &g, const hts_params &
 hts_status launch_sigma_final(const Geom &g, const hts_params &p, DevState *st, cudaStream_t s);
 
 // ---- filtering and aggregation (filter.cu)
+// xlist: N_ref int4 entries for the in-band coefficients; xskip: N_ref bytes (see filter.cu)
 hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, const double *b64, const float *b32,
-                         long long *acc, int *wcount, int32_t *redo_list, DevState *st, float *out, cudaStream_t s);
+                         long long *acc, int *wcount, int32_t *redo_list, int4 *xlist, uint8_t *xskip,
+                         DevState *st, float *out, cudaStream_t s);
 
 }  // namespace hts
 

@@ -54,7 +54,7 @@ class SigmaInfo(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("nref", ctypes.c_int), ("match_reranked", ctypes.c_int), ("match_fallback", ctypes.c_int),
                 ("filter_redo", ctypes.c_int), ("filter_exact", ctypes.c_int), ("vote_uncertain", ctypes.c_int),
-                ("sigma", ctypes.c_double), ("tau", ctypes.c_double)]
+                ("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("filter_fixed", ctypes.c_int)]
 
 
 class KernelTime(ctypes.Structure):
