@@ -148,7 +148,13 @@ static hts_status get_ws(cudaStream_t s, Workspace **out) {
     if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&w->b64), 2 * 256 * sizeof(double)), "cudaMalloc");
     if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&w->b32), 2 * 256 * sizeof(float)), "cudaMalloc");
     if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&w->eig), 4 * 8 * sizeof(double)), "cudaMalloc");
-    if (st == HTS_OK) st = cuda_ok(cudaStreamCreateWithFlags(&w->aux, cudaStreamNonBlocking), "cudaStreamCreate");
+    // The basis chain ends in a few-block eigensolver that the threshold waits
+    // for: its stream gets the highest priority so that its blocks are not
+    // queued behind the grouping's.
+    int prio_lo = 0, prio_hi = 0;
+    if (st == HTS_OK) st = cuda_ok(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi), "cudaDeviceGetStreamPriorityRange");
+    if (st == HTS_OK)
+        st = cuda_ok(cudaStreamCreateWithPriority(&w->aux, cudaStreamNonBlocking, prio_hi), "cudaStreamCreate");
     if (st == HTS_OK) st = cuda_ok(cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
     if (st == HTS_OK) st = cuda_ok(cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming), "cudaEventCreate");
     if (st != HTS_OK) {

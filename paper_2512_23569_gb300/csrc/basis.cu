@@ -9,7 +9,8 @@
 //              fills the Hermitian matrices;
 // k_jacobi   : one warp per 8x8 Hermitian matrix, parallel cyclic Jacobi
 //              (4 disjoint complex rotations per round, 7 rounds per sweep),
-//              eigenvalues sorted ascending, eigenvectors as columns.
+//              first in FP32, then refined in FP64; eigenvalues sorted
+//              ascending, eigenvectors as columns.
 #include "hts_internal.h"
 
 namespace hts {
@@ -168,24 +169,190 @@ __device__ void cov_entry(const double *__restrict__ tot, int j, int m, int a, i
         }
 }
 
-// One 8x8 Hermitian eigenproblem per block (one warp), cyclic parallel Jacobi:
-// 4 disjoint rotations per round, 7 rounds per sweep.  The rotation for
-// (p, q) makes a_pq real with the phase e^{i phi} = a_pq / |a_pq| and then
-// zeroes it with the real Jacobi rotation (t = sgn(th) / (|th| + sqrt(th^2+1)),
-// th = (a_qq - a_pp) / (2 |a_pq|)).  The angle is computed in FP32 (a slightly
-// inexact angle only slows convergence); the phase and (c, s) are then
-// renormalised in FP64 by two Newton steps of 1/sqrt(x) at x ~ 1, so every
-// applied rotation is unitary to FP64 precision and the spectrum is exact to
-// FP64 rounding.  Updates are in FP64.
+// Rotation pair i (0..3) of round `round` (0..6) of the parallel cyclic
+// ordering: the 8 indices sit on a circle of 7 around a fixed index 0.
+__device__ __forceinline__ void jac_pair(int i, int round, int &p, int &q) {
+    const int L0 = (i == 0) ? 0 : 1 + ((i - 1 + round) % 7);
+    const int L1 = 1 + ((6 - i + round) % 7);
+    p = min(L0, L1);
+    q = max(L0, L1);
+}
+
+// Applies the 4 rotations of one round to A (both sides) and V (right side).
+// Rotation i acts on columns p, q (old values x, y) as p <- c x - s conj(e) y,
+// q <- s x + c conj(e) y, and by its adjoint on rows p, q.
+template <typename T>
+__device__ __forceinline__ void jac_apply(T *Ar, T *Ai, T *Vr, T *Vi, const T *pc, const T *ps_, const T *per,
+                                          const T *pei, const int *pp, const int *pq, int lane) {
+    const int i = lane >> 3, k = lane & 7;
+    const int p = pp[i], q = pq[i];
+    const T c = pc[i], s = ps_[i], er = per[i], ei = pei[i];
+    {   // columns: A <- A J
+        const T xr = Ar[k * 8 + p], xi = Ai[k * 8 + p];
+        const T yr = Ar[k * 8 + q], yi = Ai[k * 8 + q];
+        const T zr = er * yr + ei * yi, zi = er * yi - ei * yr;  // conj(e) * y
+        Ar[k * 8 + p] = c * xr - s * zr;
+        Ai[k * 8 + p] = c * xi - s * zi;
+        Ar[k * 8 + q] = s * xr + c * zr;
+        Ai[k * 8 + q] = s * xi + c * zi;
+    }
+    __syncwarp();
+    {   // rows: A <- J^H A
+        const T xr = Ar[p * 8 + k], xi = Ai[p * 8 + k];
+        const T yr = Ar[q * 8 + k], yi = Ai[q * 8 + k];
+        const T zr = er * yr - ei * yi, zi = er * yi + ei * yr;  // e * y
+        Ar[p * 8 + k] = c * xr - s * zr;
+        Ai[p * 8 + k] = c * xi - s * zi;
+        Ar[q * 8 + k] = s * xr + c * zr;
+        Ai[q * 8 + k] = s * xi + c * zi;
+    }
+    __syncwarp();
+    {   // eigenvectors: V <- V J
+        const T xr = Vr[k * 8 + p], xi = Vi[k * 8 + p];
+        const T yr = Vr[k * 8 + q], yi = Vi[k * 8 + q];
+        const T zr = er * yr + ei * yi, zi = er * yi - ei * yr;
+        Vr[k * 8 + p] = c * xr - s * zr;
+        Vi[k * 8 + p] = c * xi - s * zi;
+        Vr[k * 8 + q] = s * xr + c * zr;
+        Vi[k * 8 + q] = s * xi + c * zi;
+    }
+    __syncwarp();
+}
+
+// Rotation (phase e, cosine c, sine s) that zeroes a_pq, in FP32: a_pq is made
+// real by e = a_pq / |a_pq|, then the real Jacobi rotation
+// t = sgn(th) / (|th| + sqrt(th^2 + 1)), th = (a_qq - a_pp) / (2 |a_pq|).
+__device__ __forceinline__ bool jac_angle32(float app, float aqq, float zr, float zi, float &c, float &s, float &er,
+                                            float &ei) {
+    const float r2 = zr * zr + zi * zi;
+    c = 1.f;
+    s = 0.f;
+    er = 1.f;
+    ei = 0.f;
+    if (!(r2 > 0.f) || !(r2 > 1e-30f * (app * app + aqq * aqq))) return false;
+    const float r = sqrtf(r2);
+    er = zr / r;
+    ei = zi / r;
+    const float th = (aqq - app) / (2.f * r);
+    const float tt = copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+    c = rsqrtf(fmaf(tt, tt, 1.f));
+    s = tt * c;
+    return true;
+}
+
+// ---- double-float (float pair h + l, |l| <= ulp(h)/2) arithmetic for the
+//      refinement phase: error-free transformations (Knuth's TwoSum, TwoProd
+//      by fma) with explicit roundings so that no contraction merges steps.
+//      About 2^-48 relative per operation, on the FP32 pipes.
+struct dfl {
+    float h, l;
+};
+__device__ __forceinline__ dfl df_make(float h) { return {h, 0.f}; }
+__device__ __forceinline__ dfl df_renorm(float s, float e) {  // |s| >= |e| or s == 0
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float bv = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bv)), __fsub_rn(b.h, bv));
+    return df_renorm(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return df_renorm(p, e);
+}
+__device__ __forceinline__ dfl df_scale(dfl a, float pow2) { return {a.h * pow2, a.l * pow2}; }  // exact
+__device__ __forceinline__ double df_to_double(dfl a) { return (double)a.h + (double)a.l; }
+
+// (X^H Y)[a][b] (HX) or (X Y)[a][b] of 8x8 complex double-float matrices.
+template <bool HX>
+__device__ __forceinline__ void cmm8(const dfl *Xr, const dfl *Xi, const dfl *Yr, const dfl *Yi, int e, dfl &cr,
+                                     dfl &ci) {
+    const int a = e >> 3, b = e & 7;
+    dfl sr = df_make(0.f), si = df_make(0.f);
+#pragma unroll 2
+    for (int k = 0; k < 8; ++k) {
+        const dfl xr = HX ? Xr[k * 8 + a] : Xr[a * 8 + k];
+        const dfl xi = HX ? -Xi[k * 8 + a] : Xi[a * 8 + k];
+        const dfl yr = Yr[k * 8 + b], yi = Yi[k * 8 + b];
+        sr = sr + (xr * yr - xi * yi);
+        si = si + (xr * yi + xi * yr);
+    }
+    cr = sr;
+    ci = si;
+}
+
+// The 4 rotations of one round applied to A (both sides) and V (right side)
+// in double-float; same rotation as jac_apply.
+__device__ __forceinline__ void jac_apply_df(dfl *Ar, dfl *Ai, dfl *Vr, dfl *Vi, const dfl *pc, const dfl *ps_,
+                                             const dfl *per, const dfl *pei, const int *pp, const int *pq, int lane) {
+    const int i = lane >> 3, k = lane & 7;
+    const int p = pp[i], q = pq[i];
+    const dfl c = pc[i], s = ps_[i], er = per[i], ei = pei[i];
+    {   // columns: A <- A J
+        const dfl xr = Ar[k * 8 + p], xi = Ai[k * 8 + p];
+        const dfl yr = Ar[k * 8 + q], yi = Ai[k * 8 + q];
+        const dfl zr = er * yr + ei * yi, zi = er * yi - ei * yr;  // conj(e) * y
+        Ar[k * 8 + p] = c * xr - s * zr;
+        Ai[k * 8 + p] = c * xi - s * zi;
+        Ar[k * 8 + q] = s * xr + c * zr;
+        Ai[k * 8 + q] = s * xi + c * zi;
+    }
+    __syncwarp();
+    {   // rows: A <- J^H A
+        const dfl xr = Ar[p * 8 + k], xi = Ai[p * 8 + k];
+        const dfl yr = Ar[q * 8 + k], yi = Ai[q * 8 + k];
+        const dfl zr = er * yr - ei * yi, zi = er * yi + ei * yr;  // e * y
+        Ar[p * 8 + k] = c * xr - s * zr;
+        Ai[p * 8 + k] = c * xi - s * zi;
+        Ar[q * 8 + k] = s * xr + c * zr;
+        Ai[q * 8 + k] = s * xi + c * zi;
+    }
+    __syncwarp();
+    {   // eigenvectors: V <- V J
+        const dfl xr = Vr[k * 8 + p], xi = Vi[k * 8 + p];
+        const dfl yr = Vr[k * 8 + q], yi = Vi[k * 8 + q];
+        const dfl zr = er * yr + ei * yi, zi = er * yi - ei * yr;
+        Vr[k * 8 + p] = c * xr - s * zr;
+        Vi[k * 8 + p] = c * xi - s * zi;
+        Vr[k * 8 + q] = s * xr + c * zr;
+        Vi[k * 8 + q] = s * xi + c * zi;
+    }
+    __syncwarp();
+}
+
+// One 8x8 Hermitian eigenproblem per block (one warp), in two phases, on the
+// matrix scaled by an exact power of two (eigenvectors are unchanged).
+// Phase 1: cyclic parallel Jacobi (4 disjoint rotations per round, 7 rounds
+// per sweep) in FP32 until the off-diagonal mass is below 1e-12 of the
+// diagonal's.  Phase 2, in double-float (GB300's FP64 rate is too low for a
+// latency-bound solver): the FP32 eigenvectors are made unitary by two
+// Newton-Schulz steps V <- V (3I - V^H V) / 2, the matrix is rotated into that
+// basis (B = V^H A V, Hermitian part), and Jacobi continues on B: each angle is
+// computed in FP32 from the entries scaled so that |b_pq| ~ 1, then the phase
+// and (c, s) are renormalised by two Newton steps of 1/sqrt(x) at x ~ 1, so
+// every applied rotation is unitary to double-float precision.  B starts
+// within FP32 round-off of diagonal, so one or two sweeps bring the
+// off-diagonal mass below 1e-26 of the diagonal's.
 template <int C>
 __global__ void __launch_bounds__(32) k_jacobi(const double *__restrict__ totals, int nmat, double *__restrict__ b64,
                                                float *__restrict__ b32, double *__restrict__ eig) {
-    __shared__ double Ar[64], Ai[64], Vr[64], Vi[64];
-    __shared__ double pc[4], ps_[4], per[4], pei[4];
+    __shared__ double Ad_r[64], Ad_i[64];
+    __shared__ dfl Ar[64], Ai[64], Vr[64], Vi[64], Tr[64], Ti[64];
+    __shared__ float Fr[64], Fi[64], Gr[64], Gi[64];
+    __shared__ dfl pc[4], ps_[4], per[4], pei[4];
+    __shared__ float fc[4], fs[4], fer[4], fei[4];
     __shared__ int pp[4], pq[4];
     __shared__ int perm[8];
     const int w = blockIdx.x, lane = threadIdx.x & 31;
     if (w >= nmat) return;
+    double dmax = 0.0;
     for (int e = lane; e < 64; e += 32) {
         const int a = e >> 3, b = e & 7;
         double sr, si;
@@ -196,18 +363,30 @@ __global__ void __launch_bounds__(32) k_jacobi(const double *__restrict__ totals
             cov_entry<C>(totals, w >> 1, w & 1, b, a, sr, si);
             si = -si;  // Hermitian
         }
-        Ar[e] = sr;
-        Ai[e] = si;
-        Vr[e] = (a == b) ? 1.0 : 0.0;
-        Vi[e] = 0.0;
+        Ad_r[e] = sr;
+        Ad_i[e] = si;
+        if (a == b) dmax = fmax(dmax, fabs(sr));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, o));
+    int ex = 0;
+    if (dmax > 0.0 && dmax < 1e300) frexp(dmax, &ex);
+    __syncwarp();
+    for (int e = lane; e < 64; e += 32) {
+        const double xr = ldexp(Ad_r[e], -ex), xi = ldexp(Ad_i[e], -ex);  // exact scaling, |diag| < 1
+        Fr[e] = (float)xr;
+        Fi[e] = (float)xi;
+        Ar[e] = {(float)xr, (float)(xr - (double)(float)xr)};
+        Ai[e] = {(float)xi, (float)(xi - (double)(float)xi)};
+        Gr[e] = ((e >> 3) == (e & 7)) ? 1.f : 0.f;
+        Gi[e] = 0.f;
     }
     __syncwarp();
-    // Sweeps until the off-diagonal mass is below 1e-26 of the diagonal's
-    // (relative 3e-13 in norm, above the FP64 round-off floor); 24 at most.
-    for (int sweep = 0; sweep < 24; ++sweep) {
-        double off = 0.0, dia = 0.0;
+    // ---- phase 1, FP32
+    for (int sweep = 0; sweep < 20; ++sweep) {
+        float off = 0.f, dia = 0.f;
         for (int e = lane; e < 64; e += 32) {
-            const double m2 = Ar[e] * Ar[e] + Ai[e] * Ai[e];
+            const float m2 = Fr[e] * Fr[e] + Fi[e] * Fi[e];
             if ((e >> 3) == (e & 7)) dia += m2;
             else off += m2;
         }
@@ -216,76 +395,129 @@ __global__ void __launch_bounds__(32) k_jacobi(const double *__restrict__ totals
             off += __shfl_xor_sync(FULL, off, o);
             dia += __shfl_xor_sync(FULL, dia, o);
         }
-        if (off <= 1e-26 * dia || off == 0.0) break;
+        if (off <= 1e-12f * dia || off == 0.f) break;
         for (int round = 0; round < 7; ++round) {
             if (lane < 4) {
-                const int i = lane;
-                const int L0 = (i == 0) ? 0 : 1 + ((i - 1 + round) % 7);
-                const int L1 = 1 + ((6 - i + round) % 7);
-                const int p = min(L0, L1), q = max(L0, L1);
-                const double zr = Ar[p * 8 + q], zi = Ai[p * 8 + q];
-                const double r2 = zr * zr + zi * zi;
-                double c = 1.0, s = 0.0, er = 1.0, ei = 0.0;
-                if (r2 > 1e-300 && r2 > 1e-30 * (Ar[p * 9] * Ar[p * 9] + Ar[q * 9] * Ar[q * 9])) {
-                    const float r = sqrtf((float)r2);
-                    er = (double)((float)zr / r);
-                    ei = (double)((float)zi / r);
-                    const float th = (float)((Ar[q * 9] - Ar[p * 9]) / (2.0 * (double)r));
-                    const float tt = copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
-                    const float cf = rsqrtf(fmaf(tt, tt, 1.f));
-                    c = (double)cf;
-                    s = (double)(tt * cf);
+                int p, q;
+                jac_pair(lane, round, p, q);
+                float c, s, er, ei;
+                jac_angle32(Fr[p * 9], Fr[q * 9], Fr[p * 8 + q], Fi[p * 8 + q], c, s, er, ei);
+                fc[lane] = c;
+                fs[lane] = s;
+                fer[lane] = er;
+                fei[lane] = ei;
+                pp[lane] = p;
+                pq[lane] = q;
+            }
+            __syncwarp();
+            jac_apply<float>(Fr, Fi, Gr, Gi, fc, fs, fer, fei, pp, pq, lane);
+        }
+    }
+    // ---- phase 2, double-float: unitary V from the FP32 eigenvectors
+    for (int e = lane; e < 64; e += 32) {
+        Vr[e] = df_make(Gr[e]);
+        Vi[e] = df_make(Gi[e]);
+    }
+    __syncwarp();
+    for (int it = 0; it < 2; ++it) {
+        dfl tr0, ti0, tr1, ti1;
+        cmm8<true>(Vr, Vi, Vr, Vi, lane, tr0, ti0);
+        cmm8<true>(Vr, Vi, Vr, Vi, lane + 32, tr1, ti1);
+        // M = (3I - V^H V) / 2
+        const dfl half = df_make(0.5f), three_half = df_make(1.5f);
+        Tr[lane] = (((lane >> 3) == (lane & 7)) ? three_half : df_make(0.f)) - half * tr0;
+        Ti[lane] = -(half * ti0);
+        Tr[lane + 32] = ((((lane + 32) >> 3) == (lane & 7)) ? three_half : df_make(0.f)) - half * tr1;
+        Ti[lane + 32] = -(half * ti1);
+        __syncwarp();
+        cmm8<false>(Vr, Vi, Tr, Ti, lane, tr0, ti0);
+        cmm8<false>(Vr, Vi, Tr, Ti, lane + 32, tr1, ti1);
+        __syncwarp();
+        Vr[lane] = tr0;
+        Vi[lane] = ti0;
+        Vr[lane + 32] = tr1;
+        Vi[lane + 32] = ti1;
+        __syncwarp();
+    }
+    {   // B = V^H (A V), Hermitian part
+        dfl tr0, ti0, tr1, ti1;
+        cmm8<false>(Ar, Ai, Vr, Vi, lane, tr0, ti0);
+        cmm8<false>(Ar, Ai, Vr, Vi, lane + 32, tr1, ti1);
+        Tr[lane] = tr0;
+        Ti[lane] = ti0;
+        Tr[lane + 32] = tr1;
+        Ti[lane + 32] = ti1;
+        __syncwarp();
+        cmm8<true>(Vr, Vi, Tr, Ti, lane, tr0, ti0);
+        cmm8<true>(Vr, Vi, Tr, Ti, lane + 32, tr1, ti1);
+        __syncwarp();
+        Tr[lane] = tr0;
+        Ti[lane] = ti0;
+        Tr[lane + 32] = tr1;
+        Ti[lane + 32] = ti1;
+        __syncwarp();
+        for (int e = lane; e < 64; e += 32) {
+            const int a = e >> 3, b = e & 7, t = b * 8 + a;
+            Ar[e] = df_scale(Tr[e] + Tr[t], 0.5f);
+            Ai[e] = (a == b) ? df_make(0.f) : df_scale(Ti[e] - Ti[t], 0.5f);
+        }
+        __syncwarp();
+    }
+    // Sweeps until the off-diagonal mass is below 1e-26 of the diagonal's
+    // (relative 3e-13 in norm); 24 at most.
+    for (int sweep = 0; sweep < 24; ++sweep) {
+        float off = 0.f, dia = 0.f;
+        for (int e = lane; e < 64; e += 32) {
+            const float m2 = Ar[e].h * Ar[e].h + Ai[e].h * Ai[e].h;
+            if ((e >> 3) == (e & 7)) dia += m2;
+            else off += m2;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            off += __shfl_xor_sync(FULL, off, o);
+            dia += __shfl_xor_sync(FULL, dia, o);
+        }
+        if (off <= 1e-26f * dia || off == 0.f) break;
+        for (int round = 0; round < 7; ++round) {
+            if (lane < 4) {
+                int p, q;
+                jac_pair(lane, round, p, q);
+                const dfl zr = Ar[p * 8 + q], zi = Ai[p * 8 + q];
+                dfl c = df_make(1.f), s = df_make(0.f), er = df_make(1.f), ei = df_make(0.f);
+                const float zm = fmaxf(fabsf(zr.h), fabsf(zi.h));
+                const float app = Ar[p * 9].h, aqq = Ar[q * 9].h;
+                if (zm > 0.f && zm > 1e-15f * fmaxf(fabsf(app), fabsf(aqq))) {
+                    // FP32 angle from the entries scaled so that |b_pq| ~ 1 (exact
+                    // power-of-two scaling; the test above bounds |b_pp|, |b_qq|)
+                    int ez = 0;
+                    frexpf(zm, &ez);
+                    float cf, sf, erf_, eif;
+                    jac_angle32(ldexpf(app, -ez), ldexpf(aqq, -ez), ldexpf(zr.h, -ez), ldexpf(zi.h, -ez), cf, sf,
+                                erf_, eif);
+                    c = df_make(cf);
+                    s = df_make(sf);
+                    er = df_make(erf_);
+                    ei = df_make(eif);
+                    const dfl three_half = df_make(1.5f), half = df_make(0.5f);
 #pragma unroll
                     for (int it = 0; it < 2; ++it) {  // x -> x (3 - |x|^2) / 2
-                        const double ne = 1.5 - 0.5 * (er * er + ei * ei);
-                        er *= ne;
-                        ei *= ne;
-                        const double nc = 1.5 - 0.5 * (c * c + s * s);
-                        c *= nc;
-                        s *= nc;
+                        const dfl ne = three_half - half * (er * er + ei * ei);
+                        er = er * ne;
+                        ei = ei * ne;
+                        const dfl nc = three_half - half * (c * c + s * s);
+                        c = c * nc;
+                        s = s * nc;
                     }
                 }
-                pc[i] = c;
-                ps_[i] = s;
-                per[i] = er;
-                pei[i] = ei;
-                pp[i] = p;
-                pq[i] = q;
+                pc[lane] = c;
+                ps_[lane] = s;
+                per[lane] = er;
+                pei[lane] = ei;
+                pp[lane] = p;
+                pq[lane] = q;
             }
             __syncwarp();
-            const int i = lane >> 3, k = lane & 7;
-            const int p = pp[i], q = pq[i];
-            const double c = pc[i], s = ps_[i], er = per[i], ei = pei[i];
-            {   // columns: A <- A J
-                const double xr = Ar[k * 8 + p], xi = Ai[k * 8 + p];
-                const double yr = Ar[k * 8 + q], yi = Ai[k * 8 + q];
-                const double zr = er * yr + ei * yi, zi = er * yi - ei * yr;  // conj(e) * y
-                Ar[k * 8 + p] = c * xr - s * zr;
-                Ai[k * 8 + p] = c * xi - s * zi;
-                Ar[k * 8 + q] = s * xr + c * zr;
-                Ai[k * 8 + q] = s * xi + c * zi;
-            }
-            __syncwarp();
-            {   // rows: A <- J^H A
-                const double xr = Ar[p * 8 + k], xi = Ai[p * 8 + k];
-                const double yr = Ar[q * 8 + k], yi = Ai[q * 8 + k];
-                const double zr = er * yr - ei * yi, zi = er * yi + ei * yr;  // e * y
-                Ar[p * 8 + k] = c * xr - s * zr;
-                Ai[p * 8 + k] = c * xi - s * zi;
-                Ar[q * 8 + k] = s * xr + c * zr;
-                Ai[q * 8 + k] = s * xi + c * zi;
-            }
-            __syncwarp();
-            {   // eigenvectors: V <- V J
-                const double xr = Vr[k * 8 + p], xi = Vi[k * 8 + p];
-                const double yr = Vr[k * 8 + q], yi = Vi[k * 8 + q];
-                const double zr = er * yr + ei * yi, zi = er * yi - ei * yr;
-                Vr[k * 8 + p] = c * xr - s * zr;
-                Vi[k * 8 + p] = c * xi - s * zi;
-                Vr[k * 8 + q] = s * xr + c * zr;
-                Vi[k * 8 + q] = s * xi + c * zi;
-            }
-            __syncwarp();
+            jac_apply_df(Ar, Ai, Vr, Vi, pc, ps_, per, pei, pp, pq, lane);
         }
     }
     if (lane == 0) {
@@ -293,7 +525,7 @@ __global__ void __launch_bounds__(32) k_jacobi(const double *__restrict__ totals
         for (int i = 0; i < 8; ++i) idx[i] = i;
         for (int i = 0; i < 8; ++i)
             for (int jj = i + 1; jj < 8; ++jj)
-                if (Ar[idx[jj] * 9] < Ar[idx[i] * 9]) {
+                if (df_to_double(Ar[idx[jj] * 9]) < df_to_double(Ar[idx[i] * 9])) {
                     const int tmp = idx[i];
                     idx[i] = idx[jj];
                     idx[jj] = tmp;
@@ -304,13 +536,13 @@ __global__ void __launch_bounds__(32) k_jacobi(const double *__restrict__ totals
     for (int e = lane; e < 64; e += 32) {
         const int a = e >> 3, i = e & 7;
         const int src = a * 8 + perm[i];
-        const double vr = Vr[src], vi = Vi[src];
+        const double vr = df_to_double(Vr[src]), vi = df_to_double(Vi[src]);
         b64[((size_t)w * 64 + e) * 2] = vr;
         b64[((size_t)w * 64 + e) * 2 + 1] = vi;
         b32[((size_t)w * 64 + e) * 2] = (float)vr;
         b32[((size_t)w * 64 + e) * 2 + 1] = (float)vi;
     }
-    if (lane < 8) eig[w * 8 + lane] = Ar[perm[lane] * 9];
+    if (lane < 8) eig[w * 8 + lane] = ldexp(df_to_double(Ar[perm[lane] * 9]), ex);
 }
 
 }  // namespace

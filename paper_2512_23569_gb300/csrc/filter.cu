@@ -391,6 +391,27 @@ struct Cfg {
 // Fixed-point aggregation: value * 2^16 rounded to int64 (|value| < 2^31).
 __device__ __forceinline__ long long fix16(float v) { return __float2ll_rn(v * 65536.0f); }
 
+// The same fixed-point value split as hi * 2^16 + lo, with |lo| <= 2^15 (fast
+// path) or 0 <= lo < 2^16, for the tile's 32-bit shared sums.  For |v| < 2^22
+// it needs no 64-bit conversion: adding 1.5 * 2^23 rounds to the nearest
+// integer (ties to even) and leaves it in the low mantissa bits, for the
+// integer part and again for the 16-bit fraction; both steps are exact, so
+// hi * 2^16 + lo == fix16(v).
+__device__ __forceinline__ void fix16_split(float v, int &hi, int &lo) {
+    constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
+    constexpr int MAGIC_BITS = 0x4B400000;
+    if (fabsf(v) < 4194304.0f) {
+        const float t = v + MAGIC;
+        hi = __float_as_int(t) - MAGIC_BITS;
+        const float f = v - (t - MAGIC);  // v - round(v), exact
+        lo = __float_as_int(fmaf(f, 65536.0f, MAGIC)) - MAGIC_BITS;
+    } else {
+        const long long q = fix16(v);
+        hi = (int)(q >> 16);
+        lo = (int)(q & 0xffff);
+    }
+}
+
 // ---------------------------------------------------------- exact pass
 
 // One group per warp (lane k < K owns patch k), groups taken from the redo
@@ -1192,9 +1213,10 @@ __global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t
                         for (int bb = 0; bb < 8; ++bb) {
 #pragma unroll
                             for (int c = 0; c < C; ++c) {
-                                const long long q = fix16(out[c][bb]);
-                                atomicAdd(acc_hi + c * RA + o + bb, (int)(q >> 16));
-                                atomicAdd(acc_lo + c * RA + o + bb, (int)(q & 0xffff));
+                                int qh, ql;
+                                fix16_split(out[c][bb], qh, ql);
+                                atomicAdd(acc_hi + c * RA + o + bb, qh);
+                                atomicAdd(acc_lo + c * RA + o + bb, ql);
                             }
                             atomicAdd(acc_w + o + bb, 1);
                         }
@@ -1234,64 +1256,133 @@ __global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t
     }
 }
 
+// FP64 value of one Haar coefficient's unit (patch k of the support, row
+// arow): conj(U[:, i])^T-row arow of P_k times V[:, jj], scaled by H[h][k].
+template <int C>
+__device__ __forceinline__ void exact_unit(const FilterArgs &a, const int32_t *grp, int K, int h, int j, int i, int jj,
+                                           int k, int arow, double &sr, double &si) {
+    const size_t HW = (size_t)a.H * a.W;
+    const double *U = a.b64 + (size_t)((j * 2 + 0) * 64) * 2;
+    const double *V = a.b64 + (size_t)((j * 2 + 1) * 64) * 2;
+    const double k3 = 0.57735026918962576451;  // 1/sqrt(3)
+    const double s3h = 0.86602540378443864676; // sqrt(3)/2
+    const int pos = grp[k];
+    const int y = pos / a.W, x = pos - (pos / a.W) * a.W;
+    double tr = 0.0, ti = 0.0;
+    for (int b = 0; b < 8; ++b) {
+        const size_t o = (size_t)(y + arow) * a.W + x + b;
+        double pr, pi;
+        if (C == 1) {
+            pr = (double)__ldg(a.img + o);
+            pi = 0.0;
+        } else {
+            const double R = (double)__ldg(a.img + o), G = (double)__ldg(a.img + HW + o),
+                         B = (double)__ldg(a.img + 2 * HW + o);
+            if (j == 0) {
+                pr = ((R + G) + B) * k3;
+                pi = 0.0;
+            } else {
+                pr = (R - 0.5 * (G + B)) * k3;
+                pi = (B - G) * (s3h * k3);
+            }
+        }
+        const double vr = V[(b * 8 + jj) * 2], vi = V[(b * 8 + jj) * 2 + 1];
+        tr += pr * vr - pi * vi;
+        ti += pr * vi + pi * vr;
+    }
+    const double ur = U[(arow * 8 + i) * 2], ui = U[(arow * 8 + i) * 2 + 1];
+    const double hv = haar_entry(K, h, k);
+    sr = hv * (ur * tr + ui * ti);  // conj(u) * t
+    si = hv * (ur * ti - ui * tr);
+}
+
 // FP64 decisions of the in-band coefficients recorded by k_filter_tile, one
-// warp each.  Where FP64 disagrees with the tentative FP32 decision, the
-// coefficient's contribution to the group's estimate -- separable: Haar row h
-// over its patch support, u_i v_j^H within each patch -- is added (FP64 keeps
-// it) or subtracted (FP64 drops it), in the same fixed-point sums.
+// block of 128 threads each (one thread per (patch, row) unit of the
+// coefficient's Haar support).  Where FP64 disagrees with the tentative FP32
+// decision, the coefficient's contribution to the group's estimate --
+// separable: Haar row h over its patch support, u_i v_j^H within each patch --
+// is added (FP64 keeps it) or subtracted (FP64 drops it), in the same
+// fixed-point sums.
 template <int C, int K>
 __global__ void __launch_bounds__(128) k_filter_fix(FilterArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
+    __shared__ double red[2][4];
+    __shared__ int dec;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = min(*(volatile int *)&a.st->xcount, a.xcap);
     const double tau64 = a.st->tau;
     const size_t HW = (size_t)a.H * a.W;
-    for (int f = gw; f < n; f += nw) {
+    for (int f = blockIdx.x; f < n; f += gridDim.x) {
         const int4 e = a.xlist[f];
         const int r = e.x, keep32 = (e.y >> 16) & 1, h = (e.y >> 8) & 0xff, it = e.y & 0xff;
-        if (a.xskip[r]) continue;  // the exact pass recomputes this group
+        if (a.xskip[r]) continue;  // the exact pass recomputes this group (uniform over the block)
         const int j = it < 64 ? 0 : 1, ei = it < 64 ? it : it - 64;
-        const int32_t *grp = a.idx + (size_t)r * K;
-        double re, im;
-        exact_coef<C>(a, grp, K, h, j, ei, lane, re, im);
-        const int keep64 = (((j == 0) ? fabs(re) : sqrt(re * re + im * im)) >= tau64) ? 1 : 0;
-        if (lane == 0) atomicAdd(&a.st->filter_exact, 1);
-        if (keep64 == keep32) continue;
-        if (lane == 0) atomicAdd(&a.st->filter_fixed, 1);
-        const float sgn = keep64 ? 1.f : -1.f;
-        const float sr = __int_as_float(e.z) * sgn, si = __int_as_float(e.w) * sgn;
         const int i = ei >> 3, jj = ei & 7;
+        const int32_t *grp = a.idx + (size_t)r * K;
+        int k0 = 0, k1 = K;
+        if (h > 0) {
+            const int l = 31 - __clz(h), L = K >> l, ii = h - (1 << l);
+            k0 = ii * L;
+            k1 = k0 + L;
+        }
+        double sr = 0.0, si = 0.0;
+        for (int u = tid; u < (k1 - k0) * 8; u += 128) {
+            double ur, ui;
+            exact_unit<C>(a, grp, K, h, j, i, jj, k0 + (u >> 3), u & 7, ur, ui);
+            sr += ur;
+            si += ui;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            sr += __shfl_xor_sync(FULL, sr, o);
+            si += __shfl_xor_sync(FULL, si, o);
+        }
+        if (lane == 0) {
+            red[0][warp] = sr;
+            red[1][warp] = si;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const double re = (red[0][0] + red[0][1]) + (red[0][2] + red[0][3]);
+            const double im = (red[1][0] + red[1][1]) + (red[1][2] + red[1][3]);
+            const int keep64 = (((j == 0) ? fabs(re) : sqrt(re * re + im * im)) >= tau64) ? 1 : 0;
+            atomicAdd(&a.st->filter_exact, 1);
+            if (keep64 != keep32) atomicAdd(&a.st->filter_fixed, 1);
+            dec = keep64;
+        }
+        __syncthreads();
+        const int keep64 = dec;
+        __syncthreads();  // dec and red are reused by the next entry
+        if (keep64 == keep32) continue;
+        const float sgn = keep64 ? 1.f : -1.f;
+        const float cr = __int_as_float(e.z) * sgn, ci = __int_as_float(e.w) * sgn;
         const float *U = a.b32 + (size_t)((j * 2 + 0) * 64) * 2;
         const float *V = a.b32 + (size_t)((j * 2 + 1) * 64) * 2;
-        for (int k = 0; k < K; ++k) {
+        for (int u = tid; u < (k1 - k0) * 64; u += 128) {
+            const int k = k0 + (u >> 6), pe = u & 63;
             const float hv = haar_entry_f32<K>(h, k);
-            if (hv == 0.f) continue;
             const int pos = grp[k];
             const int py = pos / a.W, px = pos - py * a.W;
-            for (int pe = lane; pe < 64; pe += 32) {
-                const int aa = pe >> 3, bb = pe & 7;
-                const float ur = U[(aa * 8 + i) * 2], ui = U[(aa * 8 + i) * 2 + 1];
-                const float vr = V[(bb * 8 + jj) * 2], vi = V[(bb * 8 + jj) * 2 + 1];
-                // hv s u conj(v)
-                const float tr = hv * (sr * ur - si * ui), ti = hv * (sr * ui + si * ur);
-                const float pr = tr * vr + ti * vi, pim = ti * vr - tr * vi;
-                const size_t o = (size_t)(py + aa) * a.W + px + bb;
-                if (C == 1) {
-                    atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + o), (unsigned long long)fix16(pr));
-                } else if (j == 0) {
-                    const float v = pr * K3F;  // slice 0 is (R+G+B)/sqrt 3: equal share per channel
-                    for (int c = 0; c < 3; ++c)
-                        atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + c * HW + o),
-                                  (unsigned long long)fix16(v));
-                } else {
-                    const float R = 2.f * pr * K3F;
-                    const float G = (-pr - 2.f * S3H * pim) * K3F;
-                    const float B = (-pr + 2.f * S3H * pim) * K3F;
-                    atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + o), (unsigned long long)fix16(R));
-                    atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + HW + o), (unsigned long long)fix16(G));
-                    atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + 2 * HW + o), (unsigned long long)fix16(B));
-                }
+            const int aa = pe >> 3, bb = pe & 7;
+            const float ur = U[(aa * 8 + i) * 2], ui = U[(aa * 8 + i) * 2 + 1];
+            const float vr = V[(bb * 8 + jj) * 2], vi = V[(bb * 8 + jj) * 2 + 1];
+            // hv c u conj(v)
+            const float tr = hv * (cr * ur - ci * ui), ti = hv * (cr * ui + ci * ur);
+            const float pr = tr * vr + ti * vi, pim = ti * vr - tr * vi;
+            const size_t o = (size_t)(py + aa) * a.W + px + bb;
+            if (C == 1) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + o), (unsigned long long)fix16(pr));
+            } else if (j == 0) {
+                const float v = pr * K3F;  // slice 0 is (R+G+B)/sqrt 3: equal share per channel
+                for (int c = 0; c < 3; ++c)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + c * HW + o),
+                              (unsigned long long)fix16(v));
+            } else {
+                const float R = 2.f * pr * K3F;
+                const float G = (-pr - 2.f * S3H * pim) * K3F;
+                const float B = (-pr + 2.f * S3H * pim) * K3F;
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + o), (unsigned long long)fix16(R));
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + HW + o), (unsigned long long)fix16(G));
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + 2 * HW + o), (unsigned long long)fix16(B));
             }
         }
     }
