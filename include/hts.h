@@ -165,9 +165,35 @@ typedef struct {
     float sigma;         /* < 0: estimate */
 } hts_image;
 
-/* Denoises n independent images (mixed sizes and channel counts) on
- * `stream`, each with its own globally-learned basis.  Asynchronous. */
+/* Denoises n independent images (mixed sizes and channel counts, sigma known
+ * or estimated per image), each with its own globally-learned basis, as ONE
+ * CUDA-graph launch on `stream`: every image's whole pipeline is captured into
+ * a graph whose branches run concurrently on several internal streams, with
+ * all buffers in one device arena per batch signature (the list of H, W, C
+ * and sigma-estimated flags, plus *p).  The first call of a signature
+ * allocates the arena, autotunes (times every valid filter tile shape per
+ * image geometry not tuned before, and the graph on 1, 2, 4 and 8 concurrent
+ * streams) and synchronises; later calls with the same signature reuse the
+ * graph (updating it in place when pointers or sigma values change) and are
+ * asynchronous.  The output equals hts_denoise's on each image, bit for bit,
+ * whatever the tuning chose.  Up to 4 signatures are kept per process (least
+ * recently used dropped, hts_shutdown frees all).  Calls are serialised
+ * across host threads. */
 hts_status hts_denoise_batch(const hts_image *imgs, int n, const hts_params *p, void *stream);
+
+/* Schedule of the last hts_denoise_batch on a stream. */
+typedef struct {
+    int images;    /* images in the batch */
+    int lanes;     /* concurrent streams the autotuner chose */
+    int kernels;   /* kernel launches per graph launch */
+    int captures;  /* graph captures made for this signature so far */
+    int updates;   /* in-place graph updates (new pointers / sigma) so far */
+} hts_batch_info;
+
+/* Filter tile shape chosen by the autotuner for this geometry (*ty x *tx
+ * reference positions per tile; 0 x 0 = the non-local mode) or -1 x -1 if the
+ * geometry has not been tuned in this process. */
+hts_status hts_tuned_tile(int H, int W, int C, const hts_params *p, int *ty, int *tx);
 
 /* ------------------------------------------------- inspection / tests */
 
@@ -197,6 +223,11 @@ typedef struct {
     int filter_fixed;      /* FP64 decisions that overturned the FP32 one (contribution corrected) */
 } hts_stats;
 hts_status hts_last_stats(hts_stats *out, void *stream);
+
+/* Per-image counters (out[0..n-1], as hts_last_stats) and, if info is not
+ * NULL, the schedule of the last hts_denoise_batch on `stream`.  HTS_EINVAL if
+ * no batch ran there.  Synchronises. */
+hts_status hts_last_batch_stats(hts_stats *out, int n, hts_batch_info *info, void *stream);
 
 /* Kernel timing: between hts_profile_begin() and hts_profile_end() every
  * kernel launch of the library is bracketed by CUDA events recorded on its

@@ -19,8 +19,57 @@ namespace hts {
 
 static std::atomic<unsigned long long> g_launches{0};
 static thread_local std::string g_err;
+static thread_local unsigned long long g_captured = 0;
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long captured_launches() { return g_captured; }
+void reset_captured_launches() { g_captured = 0; }
+
+static bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return false;
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+hts_status allow_smem(const void *func, size_t need) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> lim;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int optin = smem_optin();
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(func, dev);
+    auto it = lim.find(key);
+    int L = 0;
+    if (it == lim.end()) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, func) != cudaSuccess) return check_launch("cudaFuncGetAttributes");
+        L = optin - (int)fa.sharedSizeBytes;
+        if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, L) != cudaSuccess)
+            return check_launch("cudaFuncSetAttribute");
+        lim[key] = L;
+    } else {
+        L = it->second;
+    }
+    if (need > (size_t)L) return report(HTS_EUNSUPPORTED, "kernel shared memory exceeds the device limit");
+    return HTS_OK;
+}
+
+int smem_optin() {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+        v = 48 * 1024;
+    cache[dev] = v;
+    return v;
+}
 
 // ------------------------------------------------------------ profiling
 
@@ -45,6 +94,10 @@ static cudaEvent_t take_event() {
 }
 
 KTimer::KTimer(const char *name, cudaStream_t s) : slot(-1), stream(s) {
+    if (capturing(s)) {  // counted when the graph launches; no profiling events in graphs
+        ++g_captured;
+        return;
+    }
     count_launch();
     std::lock_guard<std::mutex> lk(g_pmu);
     if (!g_prof) return;
@@ -91,29 +144,15 @@ static hts_status cuda_ok(cudaError_t e, const char *what) {
 
 // ----------------------------------------------------------- workspace
 
-struct Workspace {
+// Buffers grown on demand; aux is the second stream on which the basis and
+// the noise floor overlap the grouping.
+struct Workspace : Bufs {
     int device = 0;
     cudaStream_t stream = nullptr;
     size_t cap_idx = 0, cap_fb = 0, cap_redo = 0, cap_green = 0, cap_hw = 0, cap_chw = 0, cap_cov = 0;
+    size_t cap_x = 0, cap_xskip = 0;
     size_t cap_in = 0, cap_out = 0;
-    int32_t *idx = nullptr;
-    uint8_t *green = nullptr;
-    int32_t *fb = nullptr;
-    int32_t *redo = nullptr;
-    int4 *xlist = nullptr;
-    size_t cap_x = 0;
-    uint8_t *xskip = nullptr;
-    size_t cap_xskip = 0;
-    long long *acc = nullptr;
-    int *wcount = nullptr;
-    double *cov = nullptr;
-    double *b64 = nullptr;
-    float *b32 = nullptr;
-    double *eig = nullptr;
-    DevState *st = nullptr;
     float *io_in = nullptr, *io_out = nullptr;
-    cudaStream_t aux = nullptr;  // second stream: basis and noise floor overlap the grouping
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 static std::mutex g_mu;
@@ -285,9 +324,9 @@ hts_status check_basis(const hts_basis *basis, int C) {
 // only on the reference patches, the grouping and the rank vote only on the
 // image: the first chain runs on the workspace's second stream while the
 // second runs on the caller's stream; the threshold waits for both.
-static hts_status denoise_impl(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
-                               const hts_params &p, Workspace *w, cudaStream_t s) {
-    HTS_TRY(ensure(w, g));
+hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
+                       const hts_params &p, const Bufs &b, cudaStream_t s) {
+    const Bufs *w = &b;
     const size_t hw = (size_t)g.H * g.W;
     HTS_TRY(cuda_ok(cudaMemsetAsync(w->st, 0, sizeof(DevState), s), "cudaMemsetAsync(state)"));
     HTS_TRY(cuda_ok(cudaMemsetAsync(w->acc, 0, hw * g.C * sizeof(long long), s), "cudaMemsetAsync(acc)"));
@@ -311,6 +350,46 @@ static hts_status denoise_impl(const float *noisy, float *out, const Geom &g, fl
     if (need_sigma) HTS_TRY(launch_sigma_final(g, p, w->st, s));
     else HTS_TRY(launch_set_sigma((double)sigma, g, p, w->st, s));
     return launch_filter(noisy, g, w->idx, b64, b32, w->acc, w->wcount, w->redo, w->xlist, w->xskip, w->st, out, s);
+}
+
+static hts_status denoise_impl(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
+                               const hts_params &p, Workspace *w, cudaStream_t s) {
+    HTS_TRY(ensure(w, g));
+    return denoise_run(noisy, out, g, sigma, basis, p, *w, s);
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+size_t bufs_bytes(const Geom &g) {
+    const size_t nref = (size_t)g.nref, hw = (size_t)g.H * g.W;
+    return align256(sizeof(DevState)) + align256(2 * 256 * sizeof(double)) + align256(2 * 256 * sizeof(float)) +
+           align256(32 * sizeof(double)) + align256(nref * g.K * sizeof(int32_t)) + align256(nref) +
+           2 * align256(nref * sizeof(int32_t)) + align256(nref * sizeof(int4)) + align256(nref) +
+           align256(hw * g.C * sizeof(long long)) + align256(hw * sizeof(int)) +
+           align256(cov_partial_count(g) * sizeof(double));
+}
+
+void bufs_carve(const Geom &g, unsigned char *base, Bufs *b) {
+    const size_t nref = (size_t)g.nref, hw = (size_t)g.H * g.W;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        unsigned char *p = base + o;
+        o += align256(bytes);
+        return p;
+    };
+    b->st = reinterpret_cast<DevState *>(take(sizeof(DevState)));
+    b->b64 = reinterpret_cast<double *>(take(2 * 256 * sizeof(double)));
+    b->b32 = reinterpret_cast<float *>(take(2 * 256 * sizeof(float)));
+    b->eig = reinterpret_cast<double *>(take(32 * sizeof(double)));
+    b->idx = reinterpret_cast<int32_t *>(take(nref * g.K * sizeof(int32_t)));
+    b->green = reinterpret_cast<uint8_t *>(take(nref));
+    b->fb = reinterpret_cast<int32_t *>(take(nref * sizeof(int32_t)));
+    b->redo = reinterpret_cast<int32_t *>(take(nref * sizeof(int32_t)));
+    b->xlist = reinterpret_cast<int4 *>(take(nref * sizeof(int4)));
+    b->xskip = reinterpret_cast<uint8_t *>(take(nref));
+    b->acc = reinterpret_cast<long long *>(take(hw * g.C * sizeof(long long)));
+    b->wcount = reinterpret_cast<int *>(take(hw * sizeof(int)));
+    b->cov = reinterpret_cast<double *>(take(cov_partial_count(g) * sizeof(double)));
 }
 
 }  // namespace hts
@@ -530,27 +609,6 @@ hts_status hts_denoise_host(const float *noisy_host, float *out_host, int H, int
     return cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize");
 }
 
-hts_status hts_denoise_batch(const hts_image *imgs, int n, const hts_params *p, void *stream) {
-    if (n < 0 || (n > 0 && !imgs)) return fail(HTS_EINVAL, "bad batch");
-    for (int i = 0; i < n; ++i) {
-        Geom g;
-        HTS_TRY(validate(imgs[i].H, imgs[i].W, imgs[i].C, p, &g));
-        if (!imgs[i].noisy || !imgs[i].out || imgs[i].noisy == imgs[i].out)
-            return fail(HTS_EINVAL, "bad image pointers in batch");
-        if (std::isnan(imgs[i].sigma) || std::isinf(imgs[i].sigma)) return fail(HTS_EINVAL, "sigma must be finite");
-    }
-    if (n == 0) return HTS_OK;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    Workspace *w;
-    HTS_TRY(get_ws(s, &w));
-    for (int i = 0; i < n; ++i) {
-        Geom g;
-        validate(imgs[i].H, imgs[i].W, imgs[i].C, p, &g);
-        HTS_TRY(denoise_impl(imgs[i].noisy, imgs[i].out, g, imgs[i].sigma, nullptr, *p, w, s));
-    }
-    return HTS_OK;
-}
-
 hts_status hts_last_stats(hts_stats *out, void *stream) {
     if (!out) return fail(HTS_EINVAL, "NULL pointer");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -621,6 +679,7 @@ uint64_t hts_launch_count(void) { return g_launches.load(); }
 const char *hts_version(void) { return "hts 0.1 (sm_103a)"; }
 
 hts_status hts_shutdown(void) {
+    batch_shutdown();
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto &kv : g_ws) {
         Workspace *w = kv.second;

@@ -1,0 +1,436 @@
+// Batched Haar-tSVD (hts_denoise_batch): many independent images of mixed
+// sizes and channel counts denoised by ONE CUDA-graph launch.
+//
+// The full pipeline of every image (basis, grouping, noise level, filter) is
+// captured once per batch signature (sizes, channel counts, which noise
+// levels are estimated, parameters) into a graph whose branches run on
+// several streams ("lanes") at once, each image with its own slot of one
+// device arena, so that the graph neither allocates nor synchronises.  A
+// later call with the same signature but other image pointers or noise levels
+// re-captures and updates the instantiated graph in place.
+//
+// An autotuner runs on the first call of a signature: for every image
+// geometry not tuned before it times each valid tile shape of the filter
+// (k_filter_tile) on that geometry's first image, and for the batch it times
+// the graph built for 1, 2, 4 and 8 lanes (images are dealt to lanes largest
+// first, each to the least-loaded lane).  Every choice gives bit-identical
+// output (the aggregation is exact integer arithmetic and every group is
+// computed independently), so tuning changes only the speed.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "hts_internal.h"
+
+namespace hts {
+namespace {
+
+#define HTS_TRY(expr)                \
+    do {                             \
+        hts_status _s = (expr);      \
+        if (_s != HTS_OK) return _s; \
+    } while (0)
+
+hts_status cu(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return HTS_OK;
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return report(e == cudaErrorMemoryAllocation ? HTS_ENOMEM : HTS_ECUDA, m.c_str());
+}
+
+constexpr int MAX_LANES = 8;
+
+struct Sig {
+    int device = 0;
+    std::vector<int> dims;  // per image: H, W, C, estimated sigma (0/1)
+    hts_params p;
+    bool operator<(const Sig &o) const {
+        if (device != o.device) return device < o.device;
+        if (dims != o.dims) return dims < o.dims;
+        return std::memcmp(&p, &o.p, sizeof(p)) < 0;
+    }
+};
+
+struct Plan {
+    Sig sig;
+    std::vector<Geom> geo;
+    std::vector<double> work;  // relative cost per image, for the lane assignment
+    unsigned char *arena = nullptr;
+    std::vector<Bufs> bufs;
+    cudaStream_t origin = nullptr;
+    cudaStream_t lanes[MAX_LANES] = {};
+    cudaStream_t auxs[MAX_LANES] = {};
+    cudaEvent_t ev_lane[MAX_LANES] = {};
+    std::vector<cudaEvent_t> ev_img;  // fork and join of every image
+    cudaEvent_t ev_start = nullptr, ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    int nlanes = 0;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long kernels = 0;
+    std::vector<hts_image> bound;  // pointers and noise levels the graph was captured with
+    int captures = 0, updates = 0;
+    unsigned long long last_use = 0;
+};
+
+std::mutex g_bmu;
+std::map<Sig, Plan *> g_plans;
+std::map<std::pair<int, cudaStream_t>, Plan *> g_last;  // most recent plan per (device, caller stream)
+unsigned long long g_tick = 0;
+constexpr size_t MAX_PLANS = 4;
+
+void destroy_plan(Plan *P) {
+    if (!P) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(P->sig.device);
+    if (P->origin) cudaStreamSynchronize(P->origin);
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    for (int l = 0; l < MAX_LANES; ++l) {
+        if (P->lanes[l]) cudaStreamDestroy(P->lanes[l]);
+        if (P->auxs[l]) cudaStreamDestroy(P->auxs[l]);
+        if (P->ev_lane[l]) cudaEventDestroy(P->ev_lane[l]);
+    }
+    for (cudaEvent_t e : P->ev_img) cudaEventDestroy(e);
+    for (cudaEvent_t e : {P->ev_start, P->ev_in, P->ev_out, P->ev_t0, P->ev_t1})
+        if (e) cudaEventDestroy(e);
+    if (P->origin) cudaStreamDestroy(P->origin);
+    cudaFree(P->arena);
+    cudaSetDevice(prev);
+    delete P;
+}
+
+hts_status create_plan(const Sig &sig, const std::vector<Geom> &geo, Plan **out) {
+    Plan *P = new Plan();
+    P->sig = sig;
+    P->geo = geo;
+    const int n = (int)geo.size();
+    std::vector<size_t> off(n + 1, 0);
+    for (int i = 0; i < n; ++i) off[i + 1] = off[i] + bufs_bytes(geo[i]);
+    hts_status st = cu(cudaMalloc(reinterpret_cast<void **>(&P->arena), std::max<size_t>(off[n], 256)),
+                       "cudaMalloc(batch arena)");
+    int lo = 0, hi = 0;
+    if (st == HTS_OK) st = cu(cudaDeviceGetStreamPriorityRange(&lo, &hi), "cudaDeviceGetStreamPriorityRange");
+    if (st == HTS_OK) st = cu(cudaStreamCreateWithFlags(&P->origin, cudaStreamNonBlocking), "cudaStreamCreate");
+    for (int l = 0; l < MAX_LANES && st == HTS_OK; ++l) {
+        st = cu(cudaStreamCreateWithFlags(&P->lanes[l], cudaStreamNonBlocking), "cudaStreamCreate");
+        if (st == HTS_OK)
+            st = cu(cudaStreamCreateWithPriority(&P->auxs[l], cudaStreamNonBlocking, hi), "cudaStreamCreate");
+        if (st == HTS_OK)
+            st = cu(cudaEventCreateWithFlags(&P->ev_lane[l], cudaEventDisableTiming), "cudaEventCreate");
+    }
+    for (int i = 0; i < 2 * n && st == HTS_OK; ++i) {
+        cudaEvent_t e = nullptr;
+        st = cu(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+        if (st == HTS_OK) P->ev_img.push_back(e);
+    }
+    for (cudaEvent_t *e : {&P->ev_start, &P->ev_in, &P->ev_out})
+        if (st == HTS_OK) st = cu(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "cudaEventCreate");
+    for (cudaEvent_t *e : {&P->ev_t0, &P->ev_t1})
+        if (st == HTS_OK) st = cu(cudaEventCreate(e), "cudaEventCreate");
+    if (st != HTS_OK) {
+        destroy_plan(P);
+        return st;
+    }
+    P->bufs.resize(n);
+    P->work.resize(n);
+    for (int i = 0; i < n; ++i) {
+        bufs_carve(geo[i], P->arena + off[i], &P->bufs[i]);
+        P->work[i] = (double)geo[i].nref * (geo[i].C == 3 ? 4.0 : 1.0) * geo[i].K;
+    }
+    *out = P;
+    return HTS_OK;
+}
+
+// Lane of every image: largest first, each to the least-loaded lane.
+std::vector<int> assign_lanes(const Plan &P, int nl) {
+    const int n = (int)P.geo.size();
+    std::vector<int> order(n), lane(n, 0);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P.work[a] > P.work[b]; });
+    std::vector<double> load(nl, 0.0);
+    for (int i : order) {
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lane[i] = l;
+        load[l] += P.work[i];
+    }
+    return lane;
+}
+
+// Buffers of image i when it runs on lane l.
+Bufs slot(const Plan &P, int i, int l) {
+    Bufs b = P.bufs[i];
+    b.aux = P.auxs[l];
+    b.ev_fork = P.ev_img[2 * i];
+    b.ev_join = P.ev_img[2 * i + 1];
+    return b;
+}
+
+// Records the whole batch on nl lanes into a new graph.
+hts_status capture(Plan &P, const hts_image *imgs, const hts_params &p, int nl, cudaGraph_t *out,
+                   unsigned long long *kernels) {
+    const int n = (int)P.geo.size();
+    const std::vector<int> lane = assign_lanes(P, nl);
+    reset_captured_launches();
+    HTS_TRY(cu(cudaStreamBeginCapture(P.origin, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture"));
+    hts_status st = cu(cudaEventRecord(P.ev_start, P.origin), "cudaEventRecord");
+    for (int l = 0; l < nl && st == HTS_OK; ++l) st = cu(cudaStreamWaitEvent(P.lanes[l], P.ev_start, 0), "cudaStreamWaitEvent");
+    for (int i = 0; i < n && st == HTS_OK; ++i)
+        st = denoise_run(imgs[i].noisy, imgs[i].out, P.geo[i], imgs[i].sigma, nullptr, p, slot(P, i, lane[i]),
+                         P.lanes[lane[i]]);
+    for (int l = 0; l < nl && st == HTS_OK; ++l) {
+        st = cu(cudaEventRecord(P.ev_lane[l], P.lanes[l]), "cudaEventRecord");
+        if (st == HTS_OK) st = cu(cudaStreamWaitEvent(P.origin, P.ev_lane[l], 0), "cudaStreamWaitEvent");
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(P.origin, &g);
+    if (st != HTS_OK) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st;
+    }
+    HTS_TRY(cu(e, "cudaStreamEndCapture"));
+    *out = g;
+    *kernels = captured_launches();
+    return HTS_OK;
+}
+
+hts_status instantiate(cudaGraph_t g, cudaGraphExec_t *exec) {
+    return cu(cudaGraphInstantiate(exec, g, 0), "cudaGraphInstantiate");
+}
+
+// Milliseconds of one launch of exec on the plan's stream (after one warm-up launch).
+hts_status time_exec(Plan &P, cudaGraphExec_t exec, float *ms) {
+    HTS_TRY(cu(cudaGraphLaunch(exec, P.origin), "cudaGraphLaunch"));
+    HTS_TRY(cu(cudaEventRecord(P.ev_t0, P.origin), "cudaEventRecord"));
+    HTS_TRY(cu(cudaGraphLaunch(exec, P.origin), "cudaGraphLaunch"));
+    HTS_TRY(cu(cudaEventRecord(P.ev_t1, P.origin), "cudaEventRecord"));
+    HTS_TRY(cu(cudaEventSynchronize(P.ev_t1), "cudaEventSynchronize"));
+    return cu(cudaEventElapsedTime(ms, P.ev_t0, P.ev_t1), "cudaEventElapsedTime");
+}
+
+// Tile shape of every geometry of the batch that has none yet.
+hts_status tune_tiles(Plan &P, const hts_image *imgs, const hts_params &p) {
+    const int n = (int)P.geo.size();
+    std::vector<std::vector<int>> done;
+    for (int i = 0; i < n; ++i) {
+        const Geom &g = P.geo[i];
+        TileChoice have;
+        if (tuned_tile(g, &have)) continue;
+        const std::vector<int> key = {g.H, g.W, g.C};
+        if (std::find(done.begin(), done.end(), key) != done.end()) continue;
+        done.push_back(key);
+        TileChoice cands[8];
+        const int nc = tile_candidates(g, cands, 8);
+        TileChoice best = cands[0];
+        float best_ms = 1e30f;
+        for (int c = 0; c < nc && nc > 1; ++c) {
+            force_tile(&cands[c]);
+            float total = 0.f;
+            hts_status st = HTS_OK;
+            for (int rep = 0; rep < 3 && st == HTS_OK; ++rep) {  // rep 0 warms up
+                if (rep == 1) st = cu(cudaEventRecord(P.ev_t0, P.origin), "cudaEventRecord");
+                if (st == HTS_OK)
+                    st = denoise_run(imgs[i].noisy, imgs[i].out, g, imgs[i].sigma, nullptr, p, slot(P, i, 0), P.origin);
+            }
+            if (st == HTS_OK) st = cu(cudaEventRecord(P.ev_t1, P.origin), "cudaEventRecord");
+            if (st == HTS_OK) st = cu(cudaEventSynchronize(P.ev_t1), "cudaEventSynchronize");
+            if (st == HTS_OK) st = cu(cudaEventElapsedTime(&total, P.ev_t0, P.ev_t1), "cudaEventElapsedTime");
+            force_tile(nullptr);
+            HTS_TRY(st);
+            if (total < best_ms) {
+                best_ms = total;
+                best = cands[c];
+            }
+        }
+        set_tuned_tile(g, best);
+    }
+    return HTS_OK;
+}
+
+// First call of a signature: tile shapes, then the lane count, keeping the fastest graph.
+hts_status build(Plan &P, const hts_image *imgs, const hts_params &p) {
+    HTS_TRY(tune_tiles(P, imgs, p));
+    const int n = (int)P.geo.size();
+    float best_ms = 1e30f;
+    for (int nl : {1, 2, 4, 8}) {
+        if (nl > 1 && nl > n) break;
+        cudaGraph_t g = nullptr;
+        unsigned long long k = 0;
+        HTS_TRY(capture(P, imgs, p, nl, &g, &k));
+        cudaGraphExec_t ex = nullptr;
+        hts_status st = instantiate(g, &ex);
+        cudaGraphDestroy(g);
+        HTS_TRY(st);
+        ++P.captures;
+        float ms = 0.f;
+        st = time_exec(P, ex, &ms);
+        if (st != HTS_OK) {
+            cudaGraphExecDestroy(ex);
+            return st;
+        }
+        count_launches(2 * k);
+        if (ms < best_ms) {
+            best_ms = ms;
+            if (P.exec) cudaGraphExecDestroy(P.exec);
+            P.exec = ex;
+            P.nlanes = nl;
+            P.kernels = k;
+        } else {
+            cudaGraphExecDestroy(ex);
+        }
+    }
+    P.bound.assign(imgs, imgs + n);
+    return HTS_OK;
+}
+
+bool same_binding(const Plan &P, const hts_image *imgs) {
+    for (size_t i = 0; i < P.bound.size(); ++i) {
+        const hts_image &a = P.bound[i], &b = imgs[i];
+        if (a.noisy != b.noisy || a.out != b.out || std::memcmp(&a.sigma, &b.sigma, sizeof(float)) != 0) return false;
+    }
+    return true;
+}
+
+// Same signature, new pointers or noise levels: capture again and update the
+// instantiated graph (re-instantiate if the update is refused).
+hts_status rebind(Plan &P, const hts_image *imgs, const hts_params &p) {
+    cudaGraph_t g = nullptr;
+    unsigned long long k = 0;
+    HTS_TRY(capture(P, imgs, p, P.nlanes, &g, &k));
+    ++P.captures;
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(P.exec, g, &info) == cudaSuccess) {
+        ++P.updates;
+    } else {
+        cudaGetLastError();
+        cudaGraphExecDestroy(P.exec);
+        P.exec = nullptr;
+        hts_status st = instantiate(g, &P.exec);
+        if (st != HTS_OK) {
+            cudaGraphDestroy(g);
+            return st;
+        }
+    }
+    cudaGraphDestroy(g);
+    P.kernels = k;
+    P.bound.assign(imgs, imgs + P.geo.size());
+    return HTS_OK;
+}
+
+}  // namespace
+
+void batch_shutdown() {
+    std::lock_guard<std::mutex> lk(g_bmu);
+    for (auto &kv : g_plans) destroy_plan(kv.second);
+    g_plans.clear();
+    g_last.clear();
+}
+
+}  // namespace hts
+
+using namespace hts;
+
+extern "C" hts_status hts_denoise_batch(const hts_image *imgs, int n, const hts_params *p, void *stream) {
+    if (n < 0 || (n > 0 && !imgs)) return report(HTS_EINVAL, "bad batch");
+    if (!p) return report(HTS_EINVAL, "params is NULL");
+    std::vector<Geom> geo(n);
+    Sig sig;
+    std::memset(&sig.p, 0, sizeof(sig.p));
+    sig.p = *p;
+    for (int i = 0; i < n; ++i) {
+        HTS_TRY(validate(imgs[i].H, imgs[i].W, imgs[i].C, p, &geo[i]));
+        if (!imgs[i].noisy || !imgs[i].out || imgs[i].noisy == imgs[i].out)
+            return report(HTS_EINVAL, "bad image pointers in batch");
+        if (imgs[i].sigma != imgs[i].sigma || imgs[i].sigma == __builtin_inff() || imgs[i].sigma == -__builtin_inff())
+            return report(HTS_EINVAL, "sigma must be finite");
+        sig.dims.insert(sig.dims.end(), {imgs[i].H, imgs[i].W, imgs[i].C, imgs[i].sigma < 0 ? 1 : 0});
+    }
+    if (n == 0) return HTS_OK;
+    HTS_TRY(cu(cudaGetDevice(&sig.device), "cudaGetDevice"));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    std::lock_guard<std::mutex> lk(g_bmu);
+    Plan *P = nullptr;
+    auto it = g_plans.find(sig);
+    bool fresh = false;
+    if (it != g_plans.end()) {
+        P = it->second;
+    } else {
+        if (g_plans.size() >= MAX_PLANS) {  // drop the least recently used plan
+            auto lru = std::min_element(g_plans.begin(), g_plans.end(), [](const auto &a, const auto &b) {
+                return a.second->last_use < b.second->last_use;
+            });
+            for (auto l = g_last.begin(); l != g_last.end();) l = (l->second == lru->second) ? g_last.erase(l) : std::next(l);
+            destroy_plan(lru->second);
+            g_plans.erase(lru);
+        }
+        HTS_TRY(create_plan(sig, geo, &P));
+        g_plans[sig] = P;
+        fresh = true;
+    }
+    P->last_use = ++g_tick;
+    // the caller's stream hands over to the plan's stream and back
+    HTS_TRY(cu(cudaEventRecord(P->ev_in, s), "cudaEventRecord"));
+    HTS_TRY(cu(cudaStreamWaitEvent(P->origin, P->ev_in, 0), "cudaStreamWaitEvent"));
+    if (fresh) HTS_TRY(build(*P, imgs, *p));
+    else if (!same_binding(*P, imgs)) HTS_TRY(rebind(*P, imgs, *p));
+    HTS_TRY(cu(cudaGraphLaunch(P->exec, P->origin), "cudaGraphLaunch"));
+    count_launches(P->kernels);
+    HTS_TRY(cu(cudaEventRecord(P->ev_out, P->origin), "cudaEventRecord"));
+    HTS_TRY(cu(cudaStreamWaitEvent(s, P->ev_out, 0), "cudaStreamWaitEvent"));
+    g_last[std::make_pair(sig.device, s)] = P;
+    return HTS_OK;
+}
+
+extern "C" hts_status hts_last_batch_stats(hts_stats *out, int n, hts_batch_info *info, void *stream) {
+    if (n < 0 || (n > 0 && !out)) return report(HTS_EINVAL, "bad arguments");
+    int dev = 0;
+    HTS_TRY(cu(cudaGetDevice(&dev), "cudaGetDevice"));
+    std::lock_guard<std::mutex> lk(g_bmu);
+    auto it = g_last.find(std::make_pair(dev, static_cast<cudaStream_t>(stream)));
+    if (it == g_last.end()) return report(HTS_EINVAL, "no batch has run on this stream");
+    Plan *P = it->second;
+    const int m = std::min(n, (int)P->geo.size());
+    HTS_TRY(cu(cudaStreamSynchronize(P->origin), "cudaStreamSynchronize"));
+    for (int i = 0; i < m; ++i) {
+        DevState hs;
+        HTS_TRY(cu(cudaMemcpy(&hs, P->bufs[i].st, sizeof(DevState), cudaMemcpyDeviceToHost), "cudaMemcpy"));
+        hts_stats &o = out[i];
+        std::memset(&o, 0, sizeof(o));
+        o.nref = hs.nref;
+        o.match_reranked = hs.match_reranked;
+        o.match_fallback = hs.match_fallback;
+        o.filter_redo = hs.filter_redo;
+        o.filter_exact = hs.filter_exact;
+        o.vote_uncertain = hs.vote_uncertain;
+        o.sigma = hs.sigma_hat;
+        o.tau = hs.tau;
+        o.filter_fixed = hs.filter_fixed;
+    }
+    if (info) {
+        info->images = (int)P->geo.size();
+        info->lanes = P->nlanes;
+        info->kernels = (int)P->kernels;
+        info->captures = P->captures;
+        info->updates = P->updates;
+    }
+    return HTS_OK;
+}
+
+extern "C" hts_status hts_tuned_tile(int H, int W, int C, const hts_params *p, int *ty, int *tx) {
+    if (!ty || !tx) return report(HTS_EINVAL, "NULL pointer");
+    Geom g;
+    HTS_TRY(validate(H, W, C, p, &g));
+    TileChoice c;
+    if (!tuned_tile(g, &c)) {
+        *ty = -1;
+        *tx = -1;
+    } else {
+        *ty = c.ty;
+        *tx = c.tx;
+    }
+    return HTS_OK;
+}

@@ -26,6 +26,9 @@
 // coefficient in FP64 from the input pixels and the FP64 basis (one warp per
 // coefficient), and takes the decision there.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <vector>
 
 #include "hts_internal.h"
 
@@ -1414,44 +1417,68 @@ size_t tile_fixed_smem() {
            ((size_t)PPB * CROW + (size_t)PPB * TileCfg<C>::PSW + TPB / 32 + 6 * GPB + (size_t)GPB * NSPARSE) * 4;
 }
 
+constexpr int NSHAPES = 6;
+constexpr int SHAPES[NSHAPES][2] = {{4, 8}, {4, 4}, {2, 4}, {2, 2}, {1, 2}, {1, 1}};
+
+size_t tile_fixed_bytes(int C, int K) {
+#define HTS_FIXED_CASE(CC, KK) \
+    if (C == CC && K == KK) return tile_fixed_smem<CC, KK>();
+    HTS_FIXED_CASE(1, 2) HTS_FIXED_CASE(1, 4) HTS_FIXED_CASE(1, 8) HTS_FIXED_CASE(1, 16) HTS_FIXED_CASE(1, 32)
+    HTS_FIXED_CASE(3, 2) HTS_FIXED_CASE(3, 4) HTS_FIXED_CASE(3, 8) HTS_FIXED_CASE(3, 16) HTS_FIXED_CASE(3, 32)
+#undef HTS_FIXED_CASE
+    return ~size_t(0);
+}
+
+// Shared memory of a tile of ty x tx references (0 for the non-local mode's tile part).
+size_t tile_bytes(const Geom &g, int ty, int tx, int *rh_out = nullptr, int *rw_out = nullptr) {
+    const int rh = ty ? std::min(g.H, (ty - 1) * g.step + 2 * g.R + PS) : 0;
+    const int rw = tx ? std::min(g.W, (tx - 1) * g.step + 2 * g.R + PS) : 0;
+    if (rh_out) *rh_out = rh;
+    if (rw_out) *rw_out = rw;
+    return tile_fixed_bytes(g.C, g.K) + (size_t)(2 * g.C + 1) * rh * rw * 4;
+}
+
+size_t tile_budget() { return std::min((size_t)smem_optin(), (size_t)227 * 1024); }
+
+thread_local const TileChoice *t_forced = nullptr;
+thread_local TileChoice t_forced_val;
+std::mutex g_tune_mu;
+std::map<std::vector<int>, TileChoice> g_tuned;
+
+std::vector<int> tune_key(const Geom &g) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return {dev, g.H, g.W, g.C, g.K, g.R, g.step};
+}
+
 template <int C, int K>
 hts_status launch_ck(const FilterArgs &a, const Geom &g, float *out, cudaStream_t s) {
     const size_t HW = (size_t)a.H * a.W;
-    // tile shape: the largest of these whose search region fits in shared memory
-    static const int shapes[][2] = {{4, 8}, {4, 4}, {2, 4}, {2, 2}, {1, 2}, {1, 1}};
-    const size_t budget = 227 * 1024;
+    // tile shape: forced (autotuning), tuned, or the largest that fits
+    TileChoice ch;
+    TileChoice cands[NSHAPES + 1];
+    tile_candidates(g, cands, NSHAPES + 1);
+    if (t_forced) ch = *t_forced;
+    else if (!tuned_tile(g, &ch)) ch = cands[0];
+    if (ch.ty > 0 && tile_bytes(g, ch.ty, ch.tx) > tile_budget()) ch = cands[0];
     const size_t fixed = tile_fixed_smem<C, K>();
     TileArgs ta;
-    ta.local = 0;
-    ta.ty = 4;
-    ta.tx = 8;
-    for (auto &sh : shapes) {
-        const int rh = std::min(g.H, (sh[0] - 1) * g.step + 2 * g.R + PS);
-        const int rw = std::min(g.W, (sh[1] - 1) * g.step + 2 * g.R + PS);
-        const size_t need = fixed + (size_t)(2 * C + 1) * rh * rw * 4;
-        if (need <= budget) {
-            ta.ty = sh[0];
-            ta.tx = sh[1];
-            ta.rh_max = rh;
-            ta.rw_max = rw;
-            ta.local = 1;
-            break;
-        }
-    }
-    if (!ta.local) {
-        ta.rh_max = 0;
-        ta.rw_max = 0;
-    }
+    ta.local = ch.ty > 0 ? 1 : 0;
+    ta.ty = ch.ty > 0 ? ch.ty : 4;
+    ta.tx = ch.ty > 0 ? ch.tx : 8;
+    ta.rh_max = 0;
+    ta.rw_max = 0;
+    if (ta.local) tile_bytes(g, ta.ty, ta.tx, &ta.rh_max, &ta.rw_max);
     ta.nty = (g.ny + ta.ty - 1) / ta.ty;
     ta.ntx = (g.nx + ta.tx - 1) / ta.tx;
     ta.ntiles = ta.nty * ta.ntx;
     const size_t sm_tile = fixed + (size_t)(2 * C + 1) * ta.rh_max * ta.rw_max * 4;
     const size_t sm_exact = exact_smem<C, K>();
-    if (cudaFuncSetAttribute(k_filter_tile<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_tile) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_filter_exact<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_exact) !=
-            cudaSuccess)
-        return check_launch("cudaFuncSetAttribute(k_filter)");
+    {
+        hts_status st0 = allow_smem(reinterpret_cast<const void *>(k_filter_tile<C, K>), sm_tile);
+        if (st0 == HTS_OK) st0 = allow_smem(reinterpret_cast<const void *>(k_filter_exact<C, K>), sm_exact);
+        if (st0 != HTS_OK) return st0;
+    }
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1484,6 +1511,36 @@ hts_status launch_ck(const FilterArgs &a, const Geom &g, float *out, cudaStream_
 }
 
 }  // namespace
+
+int tile_candidates(const Geom &g, TileChoice *out, int max) {
+    int n = 0;
+    for (int i = 0; i < NSHAPES && n < max; ++i)
+        if (tile_bytes(g, SHAPES[i][0], SHAPES[i][1]) <= tile_budget()) out[n++] = {SHAPES[i][0], SHAPES[i][1]};
+    if (n < max) out[n++] = {0, 0};  // non-local mode: always valid
+    return n;
+}
+
+void force_tile(const TileChoice *c) {
+    if (c) {
+        t_forced_val = *c;
+        t_forced = &t_forced_val;
+    } else {
+        t_forced = nullptr;
+    }
+}
+
+bool tuned_tile(const Geom &g, TileChoice *out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(tune_key(g));
+    if (it == g_tuned.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+void set_tuned_tile(const Geom &g, TileChoice c) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[tune_key(g)] = c;
+}
 
 hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, const double *b64, const float *b32,
                          long long *acc, int *wcount, int32_t *redo_list, int4 *xlist, uint8_t *xskip,

@@ -71,7 +71,18 @@ hts_status report(hts_status s, const char *msg);
 // KTimer scope: it counts the launch and, while profiling is on, records a
 // CUDA event before and after it on the launch stream.
 void count_launch();
+void count_launches(unsigned long long n);
 hts_status check_launch(const char *what);
+// Launches recorded by this host thread into stream captures since the last
+// reset (a captured launch is counted when its graph is launched).
+unsigned long long captured_launches();
+void reset_captured_launches();
+
+// Largest shared memory a block may opt in to on the current device.
+int smem_optin();
+// Sets, once per kernel and device, the kernel's dynamic shared memory
+// attribute to the largest allowed value, and checks `need` against it.
+hts_status allow_smem(const void *func, size_t need);
 struct KTimer {
     int slot;
     cudaStream_t stream;
@@ -104,6 +115,46 @@ hts_status launch_sigma_final(const Geom &g, const hts_params &p, DevState *st, 
 hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, const double *b64, const float *b32,
                          long long *acc, int *wcount, int32_t *redo_list, int4 *xlist, uint8_t *xskip,
                          DevState *st, float *out, cudaStream_t s);
+
+// Filter tile shape (k_filter_tile): ty x tx reference positions per tile,
+// ty = 0 for the non-local mode (no tile accumulators).  The launch uses, in
+// this order: the thread's forced shape (set while autotuning), the tuned
+// shape of the geometry, the largest listed shape that fits.
+struct TileChoice {
+    int ty, tx;
+};
+int tile_candidates(const Geom &g, TileChoice *out, int max);  // shapes valid for g, largest first
+void force_tile(const TileChoice *c);                          // nullptr: off (per host thread)
+bool tuned_tile(const Geom &g, TileChoice *out);
+void set_tuned_tile(const Geom &g, TileChoice c);
+
+// Device buffers of one image's pipeline: a stream's workspace, or one slot
+// of a batch arena.  aux / ev_fork / ev_join: the second stream and the two
+// events of the basis chain's fork and join.
+struct Bufs {
+    int32_t *idx = nullptr;
+    uint8_t *green = nullptr;
+    int32_t *fb = nullptr;
+    int32_t *redo = nullptr;
+    int4 *xlist = nullptr;
+    uint8_t *xskip = nullptr;
+    long long *acc = nullptr;
+    int *wcount = nullptr;
+    double *cov = nullptr;
+    double *b64 = nullptr;
+    float *b32 = nullptr;
+    double *eig = nullptr;
+    DevState *st = nullptr;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+};
+size_t bufs_bytes(const Geom &g);                              // arena bytes of one image
+void bufs_carve(const Geom &g, unsigned char *base, Bufs *b);  // device pointers (not aux / events)
+// Releases every batch plan (batch.cu).
+void batch_shutdown();
+// The whole method for one image on stream s with the buffers of b (api.cu).
+hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
+                       const hts_params &p, const Bufs &b, cudaStream_t s);
 
 }  // namespace hts
 

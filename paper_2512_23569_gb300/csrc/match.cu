@@ -427,8 +427,10 @@ hts_status launch_k(const MatchArgs &a, cudaStream_t s) {
     const int NCM = (2 * a.R + 1) * (2 * a.R + 1);
     const size_t smem = (size_t)MW * 3 * PMAX * 8 + (size_t)(a.C == 3 ? 2 : 1) * RHM * RHM * sizeof(float) +
                         (size_t)MW * NCM * sizeof(float);
-    if (cudaFuncSetAttribute(k_match<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return check_launch("cudaFuncSetAttribute(k_match)");
+    {
+        const hts_status st0 = allow_smem(reinterpret_cast<const void *>(k_match<K>), smem);
+        if (st0 != HTS_OK) return st0;
+    }
     const int blocks = ((a.ny + 1) / 2) * ((a.nx + 1) / 2);
     {
         KTimer kt("k_match", s);

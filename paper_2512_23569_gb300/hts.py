@@ -28,7 +28,7 @@ EXPORTS = [
     "hts_basis_save", "hts_basis_load", "hts_estimate_sigma", "hts_denoise", "hts_denoise_host",
     "hts_denoise_batch", "hts_match", "hts_num_refs", "hts_last_stats", "hts_last_error",
     "hts_launch_count", "hts_version", "hts_shutdown", "hts_profile_begin", "hts_profile_end",
-    "hts_denoise_noalloc",
+    "hts_denoise_noalloc", "hts_last_batch_stats", "hts_tuned_tile",
 ]
 
 
@@ -55,6 +55,11 @@ class Stats(ctypes.Structure):
     _fields_ = [("nref", ctypes.c_int), ("match_reranked", ctypes.c_int), ("match_fallback", ctypes.c_int),
                 ("filter_redo", ctypes.c_int), ("filter_exact", ctypes.c_int), ("vote_uncertain", ctypes.c_int),
                 ("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("filter_fixed", ctypes.c_int)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("images", ctypes.c_int), ("lanes", ctypes.c_int), ("kernels", ctypes.c_int),
+                ("captures", ctypes.c_int), ("updates", ctypes.c_int)]
 
 
 class KernelTime(ctypes.Structure):
@@ -89,6 +94,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.hts_denoise_host.argtypes = [P, P, I, I, I, F, P, PP, P]
         lib.hts_denoise_noalloc.argtypes = [P, P, I, I, I, F, P, PP, P]
         lib.hts_denoise_batch.argtypes = [ctypes.POINTER(Image), I, PP, P]
+        lib.hts_last_batch_stats.argtypes = [ctypes.POINTER(Stats), I, ctypes.POINTER(BatchInfo), P]
+        lib.hts_tuned_tile.argtypes = [I, I, I, PP, ctypes.POINTER(I), ctypes.POINTER(I)]
         lib.hts_match.argtypes = [P, I, I, I, PP, P, P, P]
         lib.hts_num_refs.argtypes = [I, I, PP]
         lib.hts_num_refs.restype = I
@@ -298,6 +305,23 @@ def denoise_batch(noisy: list, sigmas: list, p: Params | None = None, outs: list
         imgs[i] = Image(x.data_ptr(), outs[i].data_ptr(), H, W, C, -1.0 if s is None else float(s))
     _check(load().hts_denoise_batch(imgs, len(noisy), ctypes.byref(p), _stream(stream)))
     return outs
+
+
+def last_batch_stats(n: int, stream=None):
+    """-> (per-image counters as in last_stats, schedule dict) of the last denoise_batch on stream."""
+    arr = (Stats * max(1, n))()
+    info = BatchInfo()
+    _check(load().hts_last_batch_stats(arr, n, ctypes.byref(info), _stream(stream)))
+    per = [{f: getattr(arr[i], f) for f, _ in Stats._fields_} for i in range(n)]
+    return per, {f: getattr(info, f) for f, _ in BatchInfo._fields_}
+
+
+def tuned_tile(H: int, W: int, C: int, p: Params | None = None):
+    """Filter tile shape the autotuner chose for this geometry, (0, 0) = non-local, None = not tuned."""
+    p = p or params()
+    ty, tx = ctypes.c_int(), ctypes.c_int()
+    _check(load().hts_tuned_tile(H, W, C, ctypes.byref(p), ctypes.byref(ty), ctypes.byref(tx)))
+    return None if ty.value < 0 else (ty.value, tx.value)
 
 
 def last_stats(stream=None) -> dict:
