@@ -159,18 +159,19 @@ hts_status hts_denoise_host(const float *noisy_host, float *out_host, int H, int
 
 /* One image of a batch. */
 typedef struct {
-    const float *noisy;  /* device, CHW */
-    float *out;          /* device, CHW */
+    const float *noisy;       /* device, CHW */
+    float *out;               /* device, CHW */
     int H, W, C;
-    float sigma;         /* < 0: estimate */
+    float sigma;              /* < 0: estimate */
+    const hts_params *params; /* NULL: the batch's parameters (read at the call, not kept) */
 } hts_image;
 
 /* Denoises n independent images (mixed sizes and channel counts, sigma known
  * or estimated per image), each with its own globally-learned basis, as ONE
  * CUDA-graph launch on `stream`: every image's whole pipeline is captured into
  * a graph whose branches run concurrently on several internal streams, with
- * all buffers in one device arena per batch signature (the list of H, W, C
- * and sigma-estimated flags, plus *p).  The first call of a signature
+ * all buffers in one device arena per batch signature (the list of H, W, C,
+ * sigma-estimated flags and parameters of every image).  The first call of a signature
  * allocates the arena, autotunes (times every valid filter tile shape per
  * image geometry not tuned before, and the graph on 1, 2, 4 and 8 concurrent
  * streams) and synchronises; later calls with the same signature reuse the

@@ -46,18 +46,19 @@ constexpr int MAX_LANES = 8;
 
 struct Sig {
     int device = 0;
-    std::vector<int> dims;  // per image: H, W, C, estimated sigma (0/1)
-    hts_params p;
+    std::vector<int> dims;          // per image: H, W, C, estimated sigma (0/1)
+    std::vector<unsigned char> par;  // per image: the bytes of its parameters
     bool operator<(const Sig &o) const {
         if (device != o.device) return device < o.device;
         if (dims != o.dims) return dims < o.dims;
-        return std::memcmp(&p, &o.p, sizeof(p)) < 0;
+        return par < o.par;
     }
 };
 
 struct Plan {
     Sig sig;
     std::vector<Geom> geo;
+    std::vector<hts_params> par;  // per image
     std::vector<double> work;  // relative cost per image, for the lane assignment
     unsigned char *arena = nullptr;
     std::vector<Bufs> bufs;
@@ -102,10 +103,12 @@ void destroy_plan(Plan *P) {
     delete P;
 }
 
-hts_status create_plan(const Sig &sig, const std::vector<Geom> &geo, Plan **out) {
+hts_status create_plan(const Sig &sig, const std::vector<Geom> &geo, const std::vector<hts_params> &par,
+                       Plan **out) {
     Plan *P = new Plan();
     P->sig = sig;
     P->geo = geo;
+    P->par = par;
     const int n = (int)geo.size();
     std::vector<size_t> off(n + 1, 0);
     for (int i = 0; i < n; ++i) off[i + 1] = off[i] + bufs_bytes(geo[i]);
@@ -169,8 +172,7 @@ Bufs slot(const Plan &P, int i, int l) {
 }
 
 // Records the whole batch on nl lanes into a new graph.
-hts_status capture(Plan &P, const hts_image *imgs, const hts_params &p, int nl, cudaGraph_t *out,
-                   unsigned long long *kernels) {
+hts_status capture(Plan &P, const hts_image *imgs, int nl, cudaGraph_t *out, unsigned long long *kernels) {
     const int n = (int)P.geo.size();
     const std::vector<int> lane = assign_lanes(P, nl);
     reset_captured_launches();
@@ -178,8 +180,8 @@ hts_status capture(Plan &P, const hts_image *imgs, const hts_params &p, int nl, 
     hts_status st = cu(cudaEventRecord(P.ev_start, P.origin), "cudaEventRecord");
     for (int l = 0; l < nl && st == HTS_OK; ++l) st = cu(cudaStreamWaitEvent(P.lanes[l], P.ev_start, 0), "cudaStreamWaitEvent");
     for (int i = 0; i < n && st == HTS_OK; ++i)
-        st = denoise_run(imgs[i].noisy, imgs[i].out, P.geo[i], imgs[i].sigma, nullptr, p, slot(P, i, lane[i]),
-                         P.lanes[lane[i]]);
+        st = denoise_run(imgs[i].noisy, imgs[i].out, P.geo[i], imgs[i].sigma, nullptr, P.par[i],
+                         slot(P, i, lane[i]), P.lanes[lane[i]]);
     for (int l = 0; l < nl && st == HTS_OK; ++l) {
         st = cu(cudaEventRecord(P.ev_lane[l], P.lanes[l]), "cudaEventRecord");
         if (st == HTS_OK) st = cu(cudaStreamWaitEvent(P.origin, P.ev_lane[l], 0), "cudaStreamWaitEvent");
@@ -212,14 +214,14 @@ hts_status time_exec(Plan &P, cudaGraphExec_t exec, float *ms) {
 }
 
 // Tile shape of every geometry of the batch that has none yet.
-hts_status tune_tiles(Plan &P, const hts_image *imgs, const hts_params &p) {
+hts_status tune_tiles(Plan &P, const hts_image *imgs) {
     const int n = (int)P.geo.size();
     std::vector<std::vector<int>> done;
     for (int i = 0; i < n; ++i) {
         const Geom &g = P.geo[i];
         TileChoice have;
         if (tuned_tile(g, &have)) continue;
-        const std::vector<int> key = {g.H, g.W, g.C};
+        const std::vector<int> key = {g.H, g.W, g.C, g.K, g.R, g.step};
         if (std::find(done.begin(), done.end(), key) != done.end()) continue;
         done.push_back(key);
         TileChoice cands[8];
@@ -233,7 +235,8 @@ hts_status tune_tiles(Plan &P, const hts_image *imgs, const hts_params &p) {
             for (int rep = 0; rep < 3 && st == HTS_OK; ++rep) {  // rep 0 warms up
                 if (rep == 1) st = cu(cudaEventRecord(P.ev_t0, P.origin), "cudaEventRecord");
                 if (st == HTS_OK)
-                    st = denoise_run(imgs[i].noisy, imgs[i].out, g, imgs[i].sigma, nullptr, p, slot(P, i, 0), P.origin);
+                    st = denoise_run(imgs[i].noisy, imgs[i].out, g, imgs[i].sigma, nullptr, P.par[i], slot(P, i, 0),
+                                     P.origin);
             }
             if (st == HTS_OK) st = cu(cudaEventRecord(P.ev_t1, P.origin), "cudaEventRecord");
             if (st == HTS_OK) st = cu(cudaEventSynchronize(P.ev_t1), "cudaEventSynchronize");
@@ -251,15 +254,15 @@ hts_status tune_tiles(Plan &P, const hts_image *imgs, const hts_params &p) {
 }
 
 // First call of a signature: tile shapes, then the lane count, keeping the fastest graph.
-hts_status build(Plan &P, const hts_image *imgs, const hts_params &p) {
-    HTS_TRY(tune_tiles(P, imgs, p));
+hts_status build(Plan &P, const hts_image *imgs) {
+    HTS_TRY(tune_tiles(P, imgs));
     const int n = (int)P.geo.size();
     float best_ms = 1e30f;
     for (int nl : {1, 2, 4, 8}) {
         if (nl > 1 && nl > n) break;
         cudaGraph_t g = nullptr;
         unsigned long long k = 0;
-        HTS_TRY(capture(P, imgs, p, nl, &g, &k));
+        HTS_TRY(capture(P, imgs, nl, &g, &k));
         cudaGraphExec_t ex = nullptr;
         hts_status st = instantiate(g, &ex);
         cudaGraphDestroy(g);
@@ -296,10 +299,10 @@ bool same_binding(const Plan &P, const hts_image *imgs) {
 
 // Same signature, new pointers or noise levels: capture again and update the
 // instantiated graph (re-instantiate if the update is refused).
-hts_status rebind(Plan &P, const hts_image *imgs, const hts_params &p) {
+hts_status rebind(Plan &P, const hts_image *imgs) {
     cudaGraph_t g = nullptr;
     unsigned long long k = 0;
-    HTS_TRY(capture(P, imgs, p, P.nlanes, &g, &k));
+    HTS_TRY(capture(P, imgs, P.nlanes, &g, &k));
     ++P.captures;
     cudaGraphExecUpdateResultInfo info;
     if (cudaGraphExecUpdate(P.exec, g, &info) == cudaSuccess) {
@@ -337,11 +340,15 @@ extern "C" hts_status hts_denoise_batch(const hts_image *imgs, int n, const hts_
     if (n < 0 || (n > 0 && !imgs)) return report(HTS_EINVAL, "bad batch");
     if (!p) return report(HTS_EINVAL, "params is NULL");
     std::vector<Geom> geo(n);
+    std::vector<hts_params> par(n);
     Sig sig;
-    std::memset(&sig.p, 0, sizeof(sig.p));
-    sig.p = *p;
     for (int i = 0; i < n; ++i) {
-        HTS_TRY(validate(imgs[i].H, imgs[i].W, imgs[i].C, p, &geo[i]));
+        const hts_params *pi = imgs[i].params ? imgs[i].params : p;
+        HTS_TRY(validate(imgs[i].H, imgs[i].W, imgs[i].C, pi, &geo[i]));
+        std::memset(&par[i], 0, sizeof(hts_params));
+        par[i] = *pi;
+        const unsigned char *pb = reinterpret_cast<const unsigned char *>(&par[i]);
+        sig.par.insert(sig.par.end(), pb, pb + sizeof(hts_params));
         if (!imgs[i].noisy || !imgs[i].out || imgs[i].noisy == imgs[i].out)
             return report(HTS_EINVAL, "bad image pointers in batch");
         if (imgs[i].sigma != imgs[i].sigma || imgs[i].sigma == __builtin_inff() || imgs[i].sigma == -__builtin_inff())
@@ -367,7 +374,7 @@ extern "C" hts_status hts_denoise_batch(const hts_image *imgs, int n, const hts_
             destroy_plan(lru->second);
             g_plans.erase(lru);
         }
-        HTS_TRY(create_plan(sig, geo, &P));
+        HTS_TRY(create_plan(sig, geo, par, &P));
         g_plans[sig] = P;
         fresh = true;
     }
@@ -375,8 +382,8 @@ extern "C" hts_status hts_denoise_batch(const hts_image *imgs, int n, const hts_
     // the caller's stream hands over to the plan's stream and back
     HTS_TRY(cu(cudaEventRecord(P->ev_in, s), "cudaEventRecord"));
     HTS_TRY(cu(cudaStreamWaitEvent(P->origin, P->ev_in, 0), "cudaStreamWaitEvent"));
-    if (fresh) HTS_TRY(build(*P, imgs, *p));
-    else if (!same_binding(*P, imgs)) HTS_TRY(rebind(*P, imgs, *p));
+    if (fresh) HTS_TRY(build(*P, imgs));
+    else if (!same_binding(*P, imgs)) HTS_TRY(rebind(*P, imgs));
     HTS_TRY(cu(cudaGraphLaunch(P->exec, P->origin), "cudaGraphLaunch"));
     count_launches(P->kernels);
     HTS_TRY(cu(cudaEventRecord(P->ev_out, P->origin), "cudaEventRecord"));

@@ -68,7 +68,7 @@ class KernelTime(ctypes.Structure):
 
 class Image(ctypes.Structure):
     _fields_ = [("noisy", ctypes.c_void_p), ("out", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
-                ("C", ctypes.c_int), ("sigma", ctypes.c_float)]
+                ("C", ctypes.c_int), ("sigma", ctypes.c_float), ("params", ctypes.c_void_p)]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -293,16 +293,23 @@ def denoise_host(noisy: np.ndarray, sigma: float | None = None, basis: Basis | N
     return out
 
 
-def denoise_batch(noisy: list, sigmas: list, p: Params | None = None, outs: list | None = None, stream=None):
+def denoise_batch(noisy: list, sigmas: list, p: Params | None = None, outs: list | None = None, stream=None,
+                  per_image: list | None = None):
+    """One graph launch over CUDA CHW tensors; sigma None -> estimated; per_image: Params or None each."""
     import torch
 
     p = p or params()
     imgs = (Image * max(1, len(noisy)))()
     outs = outs or [torch.empty_like(_chw(x)) for x in noisy]
+    keep = []  # per-image parameter structs stay alive through the call
     for i, (x, s) in enumerate(zip(noisy, sigmas)):
         x = _chw(x)
         C, H, W = x.shape
-        imgs[i] = Image(x.data_ptr(), outs[i].data_ptr(), H, W, C, -1.0 if s is None else float(s))
+        pi = per_image[i] if per_image else None
+        if pi is not None:
+            keep.append(pi)
+        imgs[i] = Image(x.data_ptr(), outs[i].data_ptr(), H, W, C, -1.0 if s is None else float(s),
+                        ctypes.addressof(pi) if pi is not None else None)
     _check(load().hts_denoise_batch(imgs, len(noisy), ctypes.byref(p), _stream(stream)))
     return outs
 

@@ -123,3 +123,15 @@ def test_batch_rejects_bad_input_before_work(hts):
         hts.denoise_batch([x, x[:, :4, :4].contiguous()], [10.0, 10.0], p)  # 4x4 is smaller than a patch
     assert hts.launch_count() == n0
     assert hts.denoise_batch([], [], p) == []
+
+
+def test_per_image_parameters(hts):
+    # gray images with a 11x11 window and K=8, colour with 15x15 and K=16, in one graph
+    pg, pc = hts.params(win=11, K=8), hts.params(win=15)
+    imgs = _images()
+    xs = [_dev(n) for _, n, _ in imgs]
+    sig = [s for _, _, s in imgs]
+    per = [pg if C == 1 else pc for (_, _, C, _, _) in BATCH]
+    outs = hts.denoise_batch(xs, sig, hts.params(), per_image=per)
+    for x, s, pi, o in zip(xs, sig, per, outs):
+        np.testing.assert_array_equal(hts.denoise(x, sigma=s, p=pi).cpu().numpy(), o.cpu().numpy())
