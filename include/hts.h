@@ -48,7 +48,8 @@ typedef enum {
 
 /* Method parameters.  Defaults (hts_params_default) follow Sec. IV-A of the
  * paper (ps = 8, gamma = 1.2 in Eq. 9, beta = 1.2 and gamma = 13 for K = 32
- * in Eq. 23, tau = sigma sqrt(2 ln(c K ps^2))) with K = 16, win = 21, step 4. */
+ * in Eq. 23, tau = sigma sqrt(2 ln(c K ps^2))) with K = 16, win = 21, step 4,
+ * precision 0. */
 typedef struct {
     int ps;            /* patch side; only 8 is built (else HTS_EUNSUPPORTED) */
     int K;             /* patches per group: 2, 4, 8, 16 or 32 (Haar needs 2^n, Eq. 8) */
@@ -60,6 +61,13 @@ typedef struct {
     double tau_mult;   /* multiplier on the universal threshold (>= 0) */
     int adjust_rank;   /* 1: apply the Eq. 22-23 vote when sigma is estimated */
     int mp_correct;    /* 1: divide the Eq. 12 floor by the Marchenko-Pastur edge (1-1/sqrt(N_ref))^2 */
+    int precision;     /* grouping arithmetic.  0: FP32 distances certified against FP64 (the
+                        * groups equal the FP64 definition's, ties to the lower index).
+                        * 1: precision form: BF16 distances on the tensor cores (FP32
+                        * accumulation), the 2K nearest re-ranked with FP32 distances; groups
+                        * may differ from the FP64 definition's where BF16 rounding reorders
+                        * near neighbours.  Windows too large for on-chip staging give
+                        * HTS_EUNSUPPORTED. */
 } hts_params;
 
 /* Fills *p with the defaults above.  HTS_EINVAL if p is NULL. */

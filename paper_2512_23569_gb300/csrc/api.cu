@@ -236,6 +236,7 @@ hts_status validate(int H, int W, int C, const hts_params *p, Geom *g) {
     if (!(p->beta > 0) || !std::isfinite(p->beta)) return fail(HTS_EINVAL, "beta must be > 0");
     if (!(p->tau_mult >= 0) || !std::isfinite(p->tau_mult)) return fail(HTS_EINVAL, "tau_mult must be >= 0");
     if (!std::isfinite(p->gamma_rank)) return fail(HTS_EINVAL, "gamma_rank must be finite");
+    if (p->precision != 0 && p->precision != 1) return fail(HTS_EINVAL, "precision must be 0 or 1");
     const int R = (p->win - 1) / 2;
     const long long cap = (long long)std::min(R + 1, H - PS + 1) * std::min(R + 1, W - PS + 1);
     if (cap < p->K) return fail(HTS_EINVAL, "search window holds fewer than K patch positions");
@@ -324,6 +325,13 @@ hts_status check_basis(const hts_basis *basis, int C) {
 // only on the reference patches, the grouping and the rank vote only on the
 // image: the first chain runs on the workspace's second stream while the
 // second runs on the caller's stream; the threshold waits for both.
+hts_status launch_grouping(const float *img, const Geom &g, const hts_params &p, int32_t *idx, uint8_t *green,
+                           int32_t *fb, DevState *st, cudaStream_t s) {
+    if (p.precision == 0) return launch_match(img, g, p.gamma_gcp, idx, green, fb, st, s);
+    if (g.C == 3) HTS_TRY(launch_gcp_flags(img, g, p.gamma_gcp, green, s));
+    return launch_match_tc(img, g, idx, green, st, s);
+}
+
 hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
                        const hts_params &p, const Bufs &b, cudaStream_t s) {
     const Bufs *w = &b;
@@ -344,7 +352,7 @@ hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigm
         if (need_sigma) HTS_TRY(launch_sigma_floor(g, p, eig, w->st, w->aux));
         HTS_TRY(cuda_ok(cudaEventRecord(w->ev_join, w->aux), "cudaEventRecord"));
     }
-    HTS_TRY(launch_match(noisy, g, p.gamma_gcp, w->idx, w->green, w->fb, w->st, s));
+    HTS_TRY(launch_grouping(noisy, g, p, w->idx, w->green, w->fb, w->st, s));
     if (need_sigma && p.adjust_rank) HTS_TRY(launch_sigma_vote(noisy, g, p, w->idx, w->redo, w->st, s));
     if (fork) HTS_TRY(cuda_ok(cudaStreamWaitEvent(s, w->ev_join, 0), "cudaStreamWaitEvent"));
     if (need_sigma) HTS_TRY(launch_sigma_final(g, p, w->st, s));
@@ -410,6 +418,7 @@ hts_status hts_params_default(hts_params *p) {
     p->tau_mult = 1.0;
     p->adjust_rank = 1;
     p->mp_correct = 1;
+    p->precision = 0;
     return HTS_OK;
 }
 
@@ -544,7 +553,7 @@ hts_status hts_match(const float *img, int H, int W, int C, const hts_params *p,
     HTS_TRY(get_ws(s, &w));
     HTS_TRY(ensure(w, g));
     HTS_TRY(cuda_ok(cudaMemsetAsync(w->st, 0, sizeof(DevState), s), "cudaMemsetAsync(state)"));
-    return launch_match(img, g, p->gamma_gcp, idx_out, green_out, w->fb, w->st, s);
+    return launch_grouping(img, g, *p, idx_out, green_out, w->fb, w->st, s);
 }
 
 hts_status hts_estimate_sigma(const float *img, int H, int W, int C, const hts_basis *basis, const hts_params *p,
@@ -559,7 +568,7 @@ hts_status hts_estimate_sigma(const float *img, int H, int W, int C, const hts_b
     HTS_TRY(ensure(w, g));
     BasisRef br;
     HTS_TRY(prepare(img, g, *p, basis, true, w, s, &br));
-    if (p->adjust_rank) HTS_TRY(launch_match(img, g, p->gamma_gcp, w->idx, w->green, w->fb, w->st, s));
+    if (p->adjust_rank) HTS_TRY(launch_grouping(img, g, *p, w->idx, w->green, w->fb, w->st, s));
     HTS_TRY(launch_sigma(img, g, *p, br.eig, w->idx, w->redo, w->st, s));
     DevState hs;
     HTS_TRY(cuda_ok(cudaMemcpyAsync(&hs, w->st, sizeof(DevState), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync"));

@@ -345,8 +345,18 @@ extern "C" hts_status hts_denoise_batch(const hts_image *imgs, int n, const hts_
     for (int i = 0; i < n; ++i) {
         const hts_params *pi = imgs[i].params ? imgs[i].params : p;
         HTS_TRY(validate(imgs[i].H, imgs[i].W, imgs[i].C, pi, &geo[i]));
-        std::memset(&par[i], 0, sizeof(hts_params));
-        par[i] = *pi;
+        std::memset(&par[i], 0, sizeof(hts_params));  // field by field: padding stays zero
+        par[i].ps = pi->ps;
+        par[i].K = pi->K;
+        par[i].win = pi->win;
+        par[i].step = pi->step;
+        par[i].gamma_gcp = pi->gamma_gcp;
+        par[i].beta = pi->beta;
+        par[i].gamma_rank = pi->gamma_rank;
+        par[i].tau_mult = pi->tau_mult;
+        par[i].adjust_rank = pi->adjust_rank;
+        par[i].mp_correct = pi->mp_correct;
+        par[i].precision = pi->precision;
         const unsigned char *pb = reinterpret_cast<const unsigned char *>(&par[i]);
         sig.par.insert(sig.par.end(), pb, pb + sizeof(hts_params));
         if (!imgs[i].noisy || !imgs[i].out || imgs[i].noisy == imgs[i].out)

@@ -94,6 +94,18 @@ struct KTimer {
 hts_status launch_match(const float *img, const Geom &g, double gamma_gcp, int32_t *idx, uint8_t *green,
                         int32_t *fallback_list, DevState *st, cudaStream_t s);
 
+// Eq. 9 flag per reference (colour images; match.cu).
+hts_status launch_gcp_flags(const float *img, const Geom &g, double gamma_gcp, uint8_t *green, cudaStream_t s);
+// Precision form of the grouping (match_tc.cu): BF16 distances on the tensor
+// cores, top-2K per reference, FP32 re-rank.  `green` must hold the Eq. 9
+// flags (colour).  HTS_EUNSUPPORTED when the window does not fit on chip.
+hts_status launch_match_tc(const float *img, const Geom &g, int32_t *idx, const uint8_t *green, DevState *st,
+                           cudaStream_t s);
+
+// The grouping step in the arithmetic p.precision selects (api.cu).
+hts_status launch_grouping(const float *img, const Geom &g, const hts_params &p, int32_t *idx, uint8_t *green,
+                           int32_t *fb, DevState *st, cudaStream_t s);
+
 // ---- global basis (basis.cu)
 size_t cov_partial_count(const Geom &g);  // doubles needed for partial sums
 hts_status launch_basis(const float *img, const Geom &g, double *partials, double *b64, float *b32, double *eig,

@@ -445,7 +445,31 @@ hts_status launch_k(const MatchArgs &a, cudaStream_t s) {
     return check_launch("k_match_fallback");
 }
 
+// Eq. 9 flag of every reference patch (one warp each), for the tensor-core
+// matching path, which reads the flags instead of deciding them itself.
+__global__ void __launch_bounds__(128) k_gcp_flags(const float *__restrict__ img, int H, int W, int step, int nx,
+                                                   int nref, double gamma, uint8_t *__restrict__ green) {
+    const int lane = threadIdx.x & 31;
+    const size_t HW = (size_t)H * W;
+    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nref; r += (gridDim.x * blockDim.x) >> 5) {
+        const int gy = r / nx, gx = r - gy * nx;
+        const int yr = grid_pos(gy, H, step), xr = grid_pos(gx, W, step);
+        const int gflag = gcp_green_fast(img, W, HW, yr, xr, gamma, lane);
+        if (lane == 0) green[r] = (uint8_t)gflag;
+    }
+}
+
 }  // namespace
+
+hts_status launch_gcp_flags(const float *img, const Geom &g, double gamma_gcp, uint8_t *green, cudaStream_t s) {
+    int blocks = (g.nref + 3) / 4;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    {
+        KTimer kt("k_gcp_flags", s);
+        k_gcp_flags<<<blocks, 128, 0, s>>>(img, g.H, g.W, g.step, g.nx, g.nref, gamma_gcp, green);
+    }
+    return check_launch("k_gcp_flags");
+}
 
 hts_status launch_match(const float *img, const Geom &g, double gamma_gcp, int32_t *idx, uint8_t *green,
                         int32_t *fallback_list, DevState *st, cudaStream_t s) {

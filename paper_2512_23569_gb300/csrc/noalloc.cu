@@ -123,7 +123,7 @@ extern "C" hts_status hts_denoise_noalloc(const float *noisy, float *out, int H,
     const double *ub64 = basis ? basis->b64 : b64;
     const float *ub32 = basis ? basis->b32 : b32;
     const double *ueig = (basis && basis->has_eig) ? basis->eig : eig;
-    st = launch_match(noisy, g, p->gamma_gcp, idx, green, fb, ds, s);
+    st = launch_grouping(noisy, g, *p, idx, green, fb, ds, s);
     if (st != HTS_OK) return st;
     if (sigma < 0) st = launch_sigma(noisy, g, *p, ueig, idx, redo, ds, s);
     else st = launch_set_sigma((double)sigma, g, *p, ds, s);

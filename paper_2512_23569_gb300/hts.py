@@ -43,6 +43,7 @@ class Params(ctypes.Structure):
         ("ps", ctypes.c_int), ("K", ctypes.c_int), ("win", ctypes.c_int), ("step", ctypes.c_int),
         ("gamma_gcp", ctypes.c_double), ("beta", ctypes.c_double), ("gamma_rank", ctypes.c_double),
         ("tau_mult", ctypes.c_double), ("adjust_rank", ctypes.c_int), ("mp_correct", ctypes.c_int),
+        ("precision", ctypes.c_int),
     ]
 
 

@@ -150,3 +150,12 @@ def psnr(x: np.ndarray, ref: np.ndarray) -> float:
     if mse == 0.0:
         return float("inf")
     return 10.0 * np.log10(255.0 * 255.0 / mse)
+
+
+def make_pg_correlated_image(H: int, W: int, C: int, seed: int, a: float = 0.01, sigma_b: float = 5.0,
+                             std: float = 0.7):
+    """(clean, noisy): Poisson-Gaussian noise (gain a, read noise sigma_b), then spatially correlated
+    by a normalised 3x3 Gaussian of std ``std``; noise seed = seed + 1."""
+    clean = clean_image(H, W, C, seed)
+    noisy = correlate_noise(clean, poisson_gaussian(clean, a, sigma_b, seed + 1), std)
+    return clean, noisy

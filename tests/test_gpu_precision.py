@@ -1,0 +1,103 @@
+"""Precision form of the grouping (BF16 tensor-core distances, FP32 re-rank of the 2K nearest).
+
+Its groups are not bit-exact by design: BF16 rounding may reorder near
+neighbours.  What is checked: every group is valid (the reference first, K
+distinct members inside its search window, the K-1 others in ascending FP32
+distance), nearly all groups equal the FP64 definition's, and the denoised
+image is within 0.05 dB PSNR of the FP64 oracle, on AWGN and on
+spatially correlated Poisson-Gaussian noise.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2512_23569_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hts():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2512_23569_gb300 import build, hts as h
+
+    build.build()
+    h.load()
+    return h
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _plane(noisy, green):
+    if noisy.shape[0] == 1:
+        return noisy[0].astype(np.float64)
+    return noisy[1].astype(np.float64) if green else (noisy[0].astype(np.float64) + noisy[1] + noisy[2])
+
+
+CASES = [
+    # H, W, C, win, K, sigma, seed
+    (128, 128, 1, 21, 16, 25.0, 1000),
+    (77, 93, 1, 21, 16, 25.0, 11),
+    (96, 112, 3, 31, 16, 50.0, 2000),
+    (45, 61, 3, 15, 8, 30.0, 12),
+    (48, 56, 3, 11, 32, 20.0, 14),
+    (40, 40, 1, 7, 4, 10.0, 13),
+]
+
+
+@pytest.mark.parametrize("H,W,C,win,K,sigma,seed", CASES)
+def test_groups_valid_and_close_to_exact(oracle, hts, H, W, C, win, K, sigma, seed):
+    _, noisy = synth.make_config_image(H, W, C, sigma, seed)
+    p1 = hts.params(K=K, win=win, precision=1)
+    idx, green = hts.match(_dev(noisy), p1)
+    idx, green = idx.cpu().numpy(), green.cpu().numpy()
+    want, green_o, _ = oracle.match(noisy, oracle.Params(K=K, win=win))
+    if C == 3:
+        np.testing.assert_array_equal(green, green_o)
+    R = (win - 1) // 2
+    ys = oracle.grid(H, 8, 4)
+    xs = oracle.grid(W, 8, 4)
+    same = 0
+    for r in range(idx.shape[0]):
+        yr, xr = ys[r // len(xs)], xs[r % len(xs)]
+        g = idx[r]
+        assert g[0] == yr * W + xr
+        assert len(set(g.tolist())) == K
+        pl = _plane(noisy, green[r] if C == 3 else 1)
+        a = pl[yr:yr + 8, xr:xr + 8]
+        d = []
+        for q in g[1:]:
+            y, x = divmod(int(q), W)
+            assert abs(y - yr) <= R and abs(x - xr) <= R and 0 <= y <= H - 8 and 0 <= x <= W - 8
+            d.append(np.sum((a - pl[y:y + 8, x:x + 8]) ** 2))
+        d = np.array(d)
+        assert np.all(np.diff(d) >= -1e-4 * (1.0 + d[1:]))  # ascending up to FP32 rounding
+        same += int(set(g.tolist()) == set(want[r].tolist()))
+    assert same >= 0.9 * idx.shape[0]
+
+
+@pytest.mark.parametrize("H,W,C,win,K,sigma,seed", CASES[:4])
+def test_denoise_within_005_db_of_oracle(oracle, hts, H, W, C, win, K, sigma, seed):
+    clean, noisy = synth.make_config_image(H, W, C, sigma, seed)
+    out = hts.denoise(_dev(noisy), sigma=sigma, p=hts.params(K=K, win=win, precision=1)).cpu().numpy()
+    want, _ = oracle.denoise(noisy, oracle.Params(K=K, win=win), sigma=sigma)
+    assert abs(synth.psnr(out, clean) - synth.psnr(want, clean)) <= 0.05
+
+
+def test_correlated_poisson_gaussian_256(oracle, hts):
+    # the precision-form workload's noise on a 256x256 colour image, sigma estimated on both sides
+    clean, noisy = synth.make_pg_correlated_image(256, 256, 3, 3000)
+    out = hts.denoise(_dev(noisy), sigma=None, p=hts.params(win=31, precision=1)).cpu().numpy()
+    want, info = oracle.denoise(noisy, oracle.Params(win=31))
+    assert abs(synth.psnr(out, clean) - synth.psnr(want, clean)) <= 0.05
+
+
+def test_precision_validation(hts):
+    x = _dev(synth.make_config_image(256, 256, 1, 10.0, 5)[1])
+    with pytest.raises(hts.HtsError):
+        hts.denoise(x, sigma=10.0, p=hts.params(precision=2))
+    with pytest.raises(hts.HtsError):  # 63x63 window: the staged search region does not fit on chip
+        hts.denoise(x, sigma=10.0, p=hts.params(win=63, precision=1))
