@@ -291,6 +291,113 @@ def run_batch(args):
     return 0
 
 
+# ------------------------------------------------------------------ precision-form workload
+
+def tc_issued_flops(H, W, K, win, step, green, C):
+    """Tensor-core flops k_match_tc issues: per tile and plane pass, ceil(Hc*Wc/256) MMA groups of
+    128 x 256 x 64 (BF16, 2 flop per MAC)."""
+    import numpy as np
+
+    R = (win - 1) // 2
+    ys, xs = _grid(H, step), _grid(W, step)
+    ny, nx = len(ys), len(xs)
+    g = np.asarray(green).reshape(ny, nx) if C == 3 else None
+    total = 0
+    for gy0 in range(0, ny, 16):
+        for gx0 in range(0, nx, 8):
+            gy1, gx1 = min(ny, gy0 + 16) - 1, min(nx, gx0 + 8) - 1
+            cy0, cy1 = max(0, ys[gy0] - R), min(H - 8, ys[gy1] + R)
+            cx0, cx1 = max(0, xs[gx0] - R), min(W - 8, xs[gx1] + R)
+            nch = ((cy1 - cy0 + 1) * (cx1 - cx0 + 1) + 255) // 256
+            passes = 1
+            if C == 3:
+                blk = g[gy0:gy1 + 1, gx0:gx1 + 1]
+                passes = int(blk.any()) + int((blk == 0).any())
+            total += passes * nch * 2 * 128 * 256 * 64
+    return total
+
+
+def run_precision(args):
+    """Colour 1024x1024x3, Poisson-Gaussian noise (a = 0.01, sigma_b = 5) spatially correlated by a 3x3
+    Gaussian (std 0.7), sigma estimated, K = 16, 31x31 window: the precision form (BF16 tensor-core
+    matching) timed against the plain FP32 path, both against the FP64 oracle."""
+    import numpy as np
+    import torch
+
+    from oracle import hts_oracle as o
+    from paper_2512_23569_gb300 import build, hts, synth
+
+    build.build()
+    hts.load()
+    H = W = 1024
+    clean, noisy = synth.make_pg_correlated_image(H, W, 3, 3000)
+    x = torch.from_numpy(noisy).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    res = {}
+    for prec in (1, 0):
+        p = hts.params(win=31, precision=prec)
+        out = torch.empty_like(x)
+        for _ in range(max(args.warmup, 3)):
+            hts.denoise(x, sigma=None, p=p, out=out)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        clocks = ClockSampler(0)
+        clocks.start()
+        hts.profile_begin()
+        for i in range(args.steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            hts.denoise(x, sigma=None, p=p, out=out)
+            evs[i][1].record(stream)
+        prof = hts.profile_end()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+        st = hts.last_stats()
+        idx, green = hts.match(x, p)
+        res[prec] = {"ms": ms, "value": H * W / (ms / 1e3) / 1e6, "out": out.cpu().numpy(), "stats": st,
+                     "idx": idx.cpu().numpy(), "green": green.cpu().numpy(), "clocks": clk,
+                     "kernels": {k: v[0] / max(v[1], 1) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
+    want, info = o.denoise(noisy, o.Params(win=31))
+    ps_o = synth.psnr(want, clean)
+    same = float(np.mean([set(a) == set(b) for a, b in zip(res[1]["idx"].tolist(), res[0]["idx"].tolist())]))
+    tc_ms = res[1]["kernels"].get("k_match_tc")
+    flops = tc_issued_flops(H, W, 16, 31, 4, res[1]["green"], 3)
+    peaks = _peaks()
+    roof = None
+    if tc_ms:
+        ach = flops / (tc_ms / 1e3) / 1e12
+        roof = {"kernel": "k_match_tc", "bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"],
+                "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"], "traffic": None,
+                "algorithmic": "issued BF16 MMA flops (window-union tiles, %.2f GFLOP per launch)" % (flops / 1e9),
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)"}
+    line = {
+        "metric": "Mpixel/s denoised on 1 GB300, precision form (BF16 tensor-core matching)",
+        "value": res[1]["value"], "unit": "Mpixel/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": res[1]["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 matching / f32 transform", "data": "synthetic",
+        "config": {"workload": "colour 1024x1024x3, Poisson-Gaussian a=0.01 sigma_b=5, 3x3 Gaussian-correlated "
+                               "(std 0.7), sigma estimated, K=16, 31x31 window, step 4", "seed": 3000,
+                   "l2": "flushed between steps (512 MB write outside the timed events)"},
+        "roofline": roof,
+        "plain_fp32": {"value": res[0]["value"], "ms": res[0]["ms"], "psnr_db": synth.psnr(res[0]["out"], clean)},
+        "speedup_vs_plain": res[0]["ms"] / res[1]["ms"],
+        "psnr_db": synth.psnr(res[1]["out"], clean), "psnr_oracle_db": ps_o,
+        "psnr_delta_db": synth.psnr(res[1]["out"], clean) - ps_o,
+        "plain_psnr_delta_db": synth.psnr(res[0]["out"], clean) - ps_o,
+        "groups_equal_to_plain": same,
+        "sigma_hat": res[1]["stats"]["sigma"], "sigma_hat_plain": res[0]["stats"]["sigma"],
+        "sigma_hat_oracle": info.get("sigma_hat"),
+        "kernels_us": {k: 1e3 * v for k, v in res[1]["kernels"].items()},
+        "kernels_us_plain": {k: 1e3 * v for k, v in res[0]["kernels"].items()},
+        "clocks": res[1]["clocks"],
+    }
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------------ arms
 
 def run_reference(args):
@@ -480,13 +587,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["colour512", "batch64"], default="colour512",
-                    help="batch64: the 64-image batched form (one JSON line of its own)")
+    ap.add_argument("--workload", choices=["colour512", "batch64", "precision1024"], default="colour512",
+                    help="batch64: the 64-image batched form; precision1024: the BF16 precision form "
+                         "(each prints one JSON line of its own)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "precision1024":
+        return run_precision(args)
     return run_ours(args)
 
 

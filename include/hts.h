@@ -146,7 +146,7 @@ hts_status hts_denoise(const float *noisy, float *out, int H, int W, int C, floa
  * the implicit device synchronisation of cudaMalloc / cudaFree.  The paper
  * has no counterpart; this is a deployment variant of hts_denoise.
  * All intermediate buffers live in one static device array of the library
- * (about 18 MB, held by every GPU that loads the library until the process
+ * (about 21 MB, held by every GPU that loads the library until the process
  * exits).  That bounds the image: H*W <= 262144 pixels, at most 65536
  * reference patches and N_ref*K <= 1048576; larger images return HTS_EINVAL
  * before any device work.  The caller still passes `noisy` and `out` (device);

@@ -210,7 +210,7 @@ static hts_status ensure(Workspace *w, const Geom &g) {
     HTS_TRY(grow(w->idx, w->cap_idx, nref * g.K, "cudaMalloc(idx)"));
     HTS_TRY(grow(w->fb, w->cap_fb, nref, "cudaMalloc(fallback)"));
     HTS_TRY(grow(w->redo, w->cap_redo, nref, "cudaMalloc(redo)"));
-    HTS_TRY(grow(w->xlist, w->cap_x, nref, "cudaMalloc(xlist)"));
+    HTS_TRY(grow(w->xlist, w->cap_x, nref * XLIST_PER_REF, "cudaMalloc(xlist)"));
     HTS_TRY(grow(w->xskip, w->cap_xskip, nref, "cudaMalloc(xskip)"));
     HTS_TRY(grow(w->green, w->cap_green, nref, "cudaMalloc(green)"));
     HTS_TRY(grow(w->acc, w->cap_chw, hw * g.C, "cudaMalloc(acc)"));
@@ -357,7 +357,8 @@ hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigm
     if (fork) HTS_TRY(cuda_ok(cudaStreamWaitEvent(s, w->ev_join, 0), "cudaStreamWaitEvent"));
     if (need_sigma) HTS_TRY(launch_sigma_final(g, p, w->st, s));
     else HTS_TRY(launch_set_sigma((double)sigma, g, p, w->st, s));
-    return launch_filter(noisy, g, w->idx, b64, b32, w->acc, w->wcount, w->redo, w->xlist, w->xskip, w->st, out, s);
+    return launch_filter(noisy, g, w->idx, b64, b32, w->acc, w->wcount, w->redo, w->xlist, w->xskip, w->st, out,
+                         p.precision == 0 ? 1 : 0, s);
 }
 
 static hts_status denoise_impl(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
@@ -372,7 +373,7 @@ size_t bufs_bytes(const Geom &g) {
     const size_t nref = (size_t)g.nref, hw = (size_t)g.H * g.W;
     return align256(sizeof(DevState)) + align256(2 * 256 * sizeof(double)) + align256(2 * 256 * sizeof(float)) +
            align256(32 * sizeof(double)) + align256(nref * g.K * sizeof(int32_t)) + align256(nref) +
-           2 * align256(nref * sizeof(int32_t)) + align256(nref * sizeof(int4)) + align256(nref) +
+           2 * align256(nref * sizeof(int32_t)) + align256(nref * XLIST_PER_REF * sizeof(int4)) + align256(nref) +
            align256(hw * g.C * sizeof(long long)) + align256(hw * sizeof(int)) +
            align256(cov_partial_count(g) * sizeof(double));
 }
@@ -393,7 +394,7 @@ void bufs_carve(const Geom &g, unsigned char *base, Bufs *b) {
     b->green = reinterpret_cast<uint8_t *>(take(nref));
     b->fb = reinterpret_cast<int32_t *>(take(nref * sizeof(int32_t)));
     b->redo = reinterpret_cast<int32_t *>(take(nref * sizeof(int32_t)));
-    b->xlist = reinterpret_cast<int4 *>(take(nref * sizeof(int4)));
+    b->xlist = reinterpret_cast<int4 *>(take(nref * XLIST_PER_REF * sizeof(int4)));
     b->xskip = reinterpret_cast<uint8_t *>(take(nref));
     b->acc = reinterpret_cast<long long *>(take(hw * g.C * sizeof(long long)));
     b->wcount = reinterpret_cast<int *>(take(hw * sizeof(int)));

@@ -61,6 +61,7 @@ struct FilterArgs {
     int32_t *redo;
     int4 *xlist;  // in-band coefficients: (group, keep<<16 | row<<8 | stream, re, im)
     int xcap;
+    int exact;       // 0: FP32 threshold decisions only (precision form)
     uint8_t *xskip;  // [N_ref] 1 = group went to the exact pass
     DevState *st;
 };
@@ -953,11 +954,14 @@ __global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t
                             int d = decide(fabsf(x[q]), tau, band);
                             if (d == 2) {  // FP32 decides for now; the FP64 decision may correct it
                                 const int keep = fabsf(x[q]) >= tau ? 1 : 0;
-                                const int slot = atomicAdd(&a.st->xcount, 1);
-                                if (slot < a.xcap) {
-                                    a.xlist[slot] = make_int4(r, (keep << 16) | (q << 8) | it, __float_as_int(x[q]), 0);
-                                } else {
-                                    gflag[gb] = 1;
+                                if (a.exact) {
+                                    const int slot = atomicAdd(&a.st->xcount, 1);
+                                    if (slot < a.xcap) {
+                                        a.xlist[slot] =
+                                            make_int4(r, (keep << 16) | (q << 8) | it, __float_as_int(x[q]), 0);
+                                    } else {
+                                        gflag[gb] = 1;
+                                    }
                                 }
                                 d = keep;
                             }
@@ -986,12 +990,14 @@ __global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t
                             int d = decide(mag, tau, band);
                             if (d == 2) {  // FP32 decides for now; the FP64 decision may correct it
                                 const int keep = mag >= tau ? 1 : 0;
-                                const int slot = atomicAdd(&a.st->xcount, 1);
-                                if (slot < a.xcap) {
-                                    a.xlist[slot] = make_int4(r, (keep << 16) | (q << 8) | it, __float_as_int(xr[q]),
-                                                              __float_as_int(xi[q]));
-                                } else {
-                                    gflag[gb] = 1;
+                                if (a.exact) {
+                                    const int slot = atomicAdd(&a.st->xcount, 1);
+                                    if (slot < a.xcap) {
+                                        a.xlist[slot] = make_int4(r, (keep << 16) | (q << 8) | it,
+                                                                  __float_as_int(xr[q]), __float_as_int(xi[q]));
+                                    } else {
+                                        gflag[gb] = 1;
+                                    }
                                 }
                                 d = keep;
                             }
@@ -1489,18 +1495,20 @@ hts_status launch_ck(const FilterArgs &a, const Geom &g, float *out, cudaStream_
     }
     hts_status st = check_launch("k_filter");
     if (st != HTS_OK) return st;
-    {
-        KTimer kt("k_filter_exact", s);
-        k_filter_exact<C, K><<<nsm, 64, sm_exact, s>>>(a);
+    if (a.exact) {
+        {
+            KTimer kt("k_filter_exact", s);
+            k_filter_exact<C, K><<<nsm, 64, sm_exact, s>>>(a);
+        }
+        st = check_launch("k_filter_exact");
+        if (st != HTS_OK) return st;
+        {
+            KTimer kt("k_filter_fix", s);
+            k_filter_fix<C, K><<<nsm, 128, 0, s>>>(a);
+        }
+        st = check_launch("k_filter_fix");
+        if (st != HTS_OK) return st;
     }
-    st = check_launch("k_filter_exact");
-    if (st != HTS_OK) return st;
-    {
-        KTimer kt("k_filter_fix", s);
-        k_filter_fix<C, K><<<nsm, 128, 0, s>>>(a);
-    }
-    st = check_launch("k_filter_fix");
-    if (st != HTS_OK) return st;
     int nb = (int)((HW * C + 255) / 256);
     if (nb > nsm * 16) nb = nsm * 16;
     {
@@ -1544,7 +1552,7 @@ void set_tuned_tile(const Geom &g, TileChoice c) {
 
 hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, const double *b64, const float *b32,
                          long long *acc, int *wcount, int32_t *redo_list, int4 *xlist, uint8_t *xskip,
-                         DevState *st, float *out, cudaStream_t s) {
+                         DevState *st, float *out, int exact, cudaStream_t s) {
     FilterArgs a;
     a.img = img;
     a.H = g.H;
@@ -1561,7 +1569,8 @@ hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, co
     a.wcount = wcount;
     a.redo = redo_list;
     a.xlist = xlist;
-    a.xcap = g.nref;
+    a.xcap = XLIST_PER_REF * g.nref;
+    a.exact = exact;
     a.xskip = xskip;
     a.st = st;
 #define HTS_FILTER_CASE(CC, KK) \

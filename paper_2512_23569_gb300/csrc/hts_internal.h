@@ -123,10 +123,12 @@ hts_status launch_sigma_vote(const float *img, const Geom &g, const hts_params &
 hts_status launch_sigma_final(const Geom &g, const hts_params &p, DevState *st, cudaStream_t s);
 
 // ---- filtering and aggregation (filter.cu)
-// xlist: N_ref int4 entries for the in-band coefficients; xskip: N_ref bytes (see filter.cu)
+// xlist: XLIST_PER_REF * N_ref int4 entries for the in-band coefficients; xskip: N_ref
+// bytes (see filter.cu).  exact = 0 (precision form): threshold decisions in FP32 only.
+constexpr int XLIST_PER_REF = 4;
 hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, const double *b64, const float *b32,
                          long long *acc, int *wcount, int32_t *redo_list, int4 *xlist, uint8_t *xskip,
-                         DevState *st, float *out, cudaStream_t s);
+                         DevState *st, float *out, int exact, cudaStream_t s);
 
 // Filter tile shape (k_filter_tile): ty x tx reference positions per tile,
 // ty = 0 for the non-local mode (no tile accumulators).  The launch uses, in

@@ -17,9 +17,9 @@
 // while the four warps read chunk c.  Each thread owns one reference (TMEM
 // lane), forms the approximate distance of every candidate inside its
 // search window from the accumulator and the BF16 squared norms, and keeps
-// the 2K smallest; those are re-ranked with FP32 distances of the FP32
-// plane, and the K-1 smallest (ties to the lower raster index) follow the
-// reference in its group.  Eq. 9 picks the plane per reference: a colour
+// the 2K smallest (48 for K = 32); those are re-ranked with FP32 distances of
+// the FP32 plane, and the K-1 smallest (ties to the lower raster index)
+// follow the reference in its group.  Eq. 9 picks the plane per reference: a colour
 // tile runs once per plane that one of its references uses.
 //
 // Every mbarrier wait is bounded; a wait that gives up records error code 2
@@ -40,6 +40,17 @@ constexpr uint32_t TMEM_COLS = 512;
 constexpr long long SPIN = 1ll << 24;
 constexpr unsigned FULLM = 0xffffffffu;
 
+// Offsets (dy, dx) of the positions around a reference whose distances seed
+// its threshold, nearest first (the 7 x 7 square without its centre); the
+// first 24 fill the 5 x 5 square.
+constexpr int NSEED = 48;
+__constant__ signed char c_seed[NSEED][2] = {
+    {0, 1},  {1, 0},   {0, -1},  {-1, 0},  {1, 1},   {1, -1},  {-1, 1},  {-1, -1}, {0, 2},   {2, 0},
+    {0, -2}, {-2, 0},  {1, 2},   {2, 1},   {-1, 2},  {2, -1},  {1, -2},  {-2, 1},  {-1, -2}, {-2, -1},
+    {2, 2},  {2, -2},  {-2, 2},  {-2, -2}, {0, 3},   {3, 0},   {0, -3},  {-3, 0},  {1, 3},   {3, 1},
+    {-1, 3}, {3, -1},  {1, -3},  {-3, 1},  {-1, -3}, {-3, -1}, {2, 3},   {3, 2},   {-2, 3},  {3, -2},
+    {2, -3}, {-3, 2},  {-2, -3}, {-3, -2}, {3, 3},   {3, -3},  {-3, 3},  {-3, -3}};
+
 struct TcArgs {
     const float *img;
     int H, W, C, step, R, nx, ny, nref;
@@ -51,12 +62,25 @@ struct TcArgs {
 };
 
 struct TcLayout {
-    size_t r0, a, e, ps, bd, bp, bar, total;
+    size_t r0, a, e, ps, rn, bd, bp, bar, total;
 };
 
 __host__ __device__ inline size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-template <int BUF>
+// Candidates kept per reference (the "2K" of the re-rank; 48 for K = 32 to
+// fit on chip) and the list capacity: a 32-candidate group is appended
+// without checks and the list is cut back to BUF when it might overflow.
+template <int K>
+struct ListCfg {
+    static constexpr int BUF = (2 * K < 8) ? 8 : (2 * K > 48 ? 48 : 2 * K);
+    static constexpr int CAP = BUF + 32;
+    static constexpr bool KEEP_PLANE = K <= 16;  // FP32 plane stays on chip for the re-rank
+};
+
+// Shared memory: Q (row-8 vectors), A, E (squared norms), the FP32 plane Ps,
+// then the lists, which overlay the row norms rn (only needed before the
+// MMAs) -- and, for K = 32, Ps too (the re-rank then reads global memory).
+template <int K>
 __host__ __device__ inline TcLayout tc_layout(int hc_max, int wc_max) {
     TcLayout L;
     const size_t nch = ((size_t)hc_max * wc_max + NCH - 1) / NCH;
@@ -65,9 +89,12 @@ __host__ __device__ inline TcLayout tc_layout(int hc_max, int wc_max) {
     L.a = up(L.r0 + nr0 * 16, 1024);
     L.e = L.a + 128 * 64 * 2;
     L.ps = up(L.e + nch * NCH * 4, 16);
-    L.bd = up(L.ps + (size_t)(hc_max + 7) * (wc_max + 7) * 4, 16);
-    L.bp = L.bd + (size_t)BUF * 128 * 4;
-    L.bar = up(L.bp + (size_t)BUF * 128 * 4, 16);
+    L.rn = up(L.ps + (size_t)(hc_max + 7) * (wc_max + 7) * 4, 16);  // row norms, after the plane
+    L.bd = ListCfg<K>::KEEP_PLANE ? L.rn : L.ps;
+    L.bp = L.bd + (size_t)ListCfg<K>::CAP * 128 * 4;
+    const size_t lists_end = L.bp + (size_t)ListCfg<K>::CAP * 128 * 4;
+    const size_t ps_end = L.rn + nr0 * 4;
+    L.bar = up(lists_end > ps_end ? lists_end : ps_end, 16);
     L.total = L.bar + 64;
     if (L.total < 120 * 1024) L.total = 120 * 1024;  // one block per SM: it holds all 512 TMEM columns
     return L;
@@ -122,47 +149,44 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) {
     return false;
 }
 
-// Per-thread list of the BUF smallest approximate distances (slots s * 128 +
-// tid of bd / bp), with the maximum of every group of 8 slots so that a
-// replacement rescans one group.
-template <int BUF>
-struct TopList {
-    static constexpr int NG = BUF / 8;
-    int cnt = 0, worst = 0;
-    float thr = __builtin_huge_valf();  // +inf until full
-    float gmax[NG];
-    __device__ __forceinline__ void insert(float *bd, int *bp, int tid, float d, int rast) {
-        const int slot = (cnt < BUF) ? cnt++ : worst;
-        bd[slot * 128 + tid] = d;
-        bp[slot * 128 + tid] = rast;
-        if (cnt < BUF) return;
-        const int g8 = slot >> 3;
-        const bool all = (slot == BUF - 1) && (thr == __builtin_huge_valf());  // just filled
-#pragma unroll
-        for (int gi = 0; gi < NG; ++gi) {
-            if (all || gi == g8) {
-                float m = -__builtin_huge_valf();
-#pragma unroll
-                for (int t = 0; t < 8; ++t) m = fmaxf(m, bd[(gi * 8 + t) * 128 + tid]);
-                gmax[gi] = m;
-            }
+// Cuts this thread's list (slots i * 128 + tid, i < cnt) back to `keep`
+// entries that include every entry below the returned value T (T is the
+// smallest value, to a bisection of 24 steps, with at least `keep` entries
+// <= T); later candidates are kept only if below T.  Every lane runs the same
+// instruction sequence (loops over CAP slots with predicates), so lanes of a
+// warp that cut together do not serialise.
+template <int CAP>
+__device__ float cut_list(float *bd, int *bp, int tid, int &cnt, int keep) {
+    float lo = __builtin_huge_valf(), hi = -__builtin_huge_valf();
+#pragma unroll 4
+    for (int i = 0; i < CAP; ++i) {
+        const float d = bd[i * 128 + tid];
+        if (i < cnt) {
+            lo = fminf(lo, d);
+            hi = fmaxf(hi, d);
         }
-        int wg = 0;
-        float wm = gmax[0];
-#pragma unroll
-        for (int gi = 1; gi < NG; ++gi)
-            if (gmax[gi] > wm) {
-                wm = gmax[gi];
-                wg = gi;
-            }
-        thr = wm;
-        int ws = wg * 8;
-#pragma unroll
-        for (int t = 7; t >= 0; --t)
-            if (bd[(wg * 8 + t) * 128 + tid] == wm) ws = wg * 8 + t;
-        worst = ws;
     }
-};
+    for (int it = 0; it < 24; ++it) {  // invariant: count(<= hi) >= keep
+        const float mid = 0.5f * (lo + hi);
+        int c = 0;
+#pragma unroll 8
+        for (int i = 0; i < CAP; ++i) c += (i < cnt && bd[i * 128 + tid] <= mid) ? 1 : 0;
+        if (c >= keep) hi = mid;
+        else lo = mid;
+    }
+    int w = 0;
+    for (int i = 0; i < CAP; ++i) {  // stable compaction: entries < hi, then entries == hi up to `keep`
+        const float d = bd[i * 128 + tid];
+        const int pv = bp[i * 128 + tid];
+        if (i < cnt && d <= hi && w < keep) {
+            bd[w * 128 + tid] = d;
+            bp[w * 128 + tid] = pv;
+            ++w;
+        }
+    }
+    cnt = w;
+    return hi;
+}
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -189,13 +213,14 @@ __device__ __forceinline__ float bf_round(float a) { return __bfloat162float(__f
 
 template <int K>
 __global__ void __launch_bounds__(128, 1) k_match_tc(TcArgs a) {
-    constexpr int BUF = (2 * K < 8) ? 8 : 2 * K;  // candidates kept per reference
+    constexpr int BUF = ListCfg<K>::BUF, CAP = ListCfg<K>::CAP;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const TcLayout L = tc_layout<BUF>(a.hc_max, a.wc_max);
+    const TcLayout L = tc_layout<K>(a.hc_max, a.wc_max);
     uint4 *Q = reinterpret_cast<uint4 *>(smem_raw + L.r0);
     unsigned char *Abuf = smem_raw + L.a;
     float *E = reinterpret_cast<float *>(smem_raw + L.e);
     float *Ps = reinterpret_cast<float *>(smem_raw + L.ps);
+    float *rn = reinterpret_cast<float *>(smem_raw + L.rn);
     float *bd = reinterpret_cast<float *>(smem_raw + L.bd);
     int *bp = reinterpret_cast<int *>(smem_raw + L.bp);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + L.bar);  // [2]
@@ -264,22 +289,26 @@ __global__ void __launch_bounds__(128, 1) k_match_tc(TcArgs a) {
             for (int q = tid; q < nq; q += 128) {
                 const int y = q / Wc, x = q - y * Wc;
                 uint4 w = make_uint4(0, 0, 0, 0);
+                float n2 = 0.f;
                 if (y < Hc + 7) {
                     const float *s = Ps + y * PSW + x;
+#pragma unroll
+                    for (int v = 0; v < PS; ++v) {
+                        const float b = bf_round(s[v]);
+                        n2 = fmaf(b, b, n2);
+                    }
                     w = make_uint4(pack_bf16(s[0], s[1]), pack_bf16(s[2], s[3]), pack_bf16(s[4], s[5]),
                                    pack_bf16(s[6], s[7]));
                 }
                 Q[q] = w;
+                rn[q] = n2;  // squared norm of the BF16 row-8 vector
             }
+            __syncthreads();
             for (int p = tid; p < nch * NCH; p += 128) {
                 float e2 = 0.f;
                 if (p < ncand) {
-                    const int y = p / Wc, x = p - y * Wc;
-                    for (int u = 0; u < PS; ++u)
-                        for (int v = 0; v < PS; ++v) {
-                            const float b = bf_round(Ps[(y + u) * PSW + x + v]);
-                            e2 = fmaf(b, b, e2);
-                        }
+#pragma unroll
+                    for (int u = 0; u < PS; ++u) e2 += rn[p + u * Wc];
                 }
                 E[p] = e2;
             }
@@ -321,52 +350,129 @@ __global__ void __launch_bounds__(128, 1) k_match_tc(TcArgs a) {
                 *issued_hi = g0 + (nch > 1 ? 2 : 1);
             }
             __syncwarp();
-            TopList<BUF> top;
-            long long consumed = g0;  // chunks whose accumulator this block has waited for
+            // threshold seed: the (K-1)-th smallest BF16 distance from the reference to the
+            // positions around it bounds the (K-1)-th nearest candidate from above, so every
+            // candidate that can be among the K-1 nearest passes the filter below it, while
+            // few others do (a factor 1.5 and an absolute margin cover the different FP32
+            // rounding of the tensor-core form and keep, for the FP32 re-rank, the candidates
+            // that BF16 rounding ranks slightly too far)
+            int cnt = 0;
+            float thr = __builtin_huge_valf();
+            if (mine) {
+                constexpr int NS = (K + 8 > 24) ? ((K + 8 > NSEED) ? NSEED : K + 8) : 24;
+                const int ay = yr - cy0, ax = xr - cx0;
+                float ab[64];
+#pragma unroll
+                for (int e = 0; e < 64; ++e) ab[e] = bf_round(Ps[(ay + (e >> 3)) * PSW + ax + (e & 7)]);
+                float best[K - 1];
+#pragma unroll
+                for (int i = 0; i < K - 1; ++i) best[i] = __builtin_huge_valf();
+                for (int sidx = 0; sidx < NS; ++sidx) {
+                    const int y = yr + c_seed[sidx][0], x = xr + c_seed[sidx][1];
+                    const bool in = y >= max(0, yr - a.R) && y <= min(a.H - PS, yr + a.R) &&
+                                    x >= max(0, xr - a.R) && x <= min(a.W - PS, xr + a.R);
+                    const float *q = Ps + (in ? (y - cy0) * PSW + (x - cx0) : ay * PSW + ax);
+                    float d = 0.f;
+#pragma unroll
+                    for (int e = 0; e < 64; ++e) {
+                        const float df = ab[e] - bf_round(q[(e >> 3) * PSW + (e & 7)]);
+                        d = fmaf(df, df, d);
+                    }
+                    if (!in) d = __builtin_huge_valf();
+#pragma unroll
+                    for (int i = 0; i < K - 1; ++i) {  // branch-free insertion into the sorted seeds
+                        const float lo = fminf(best[i], d);
+                        d = fmaxf(best[i], d);
+                        best[i] = lo;
+                    }
+                }
+                const float t = best[K - 2];
+                if (t < __builtin_huge_valf()) thr = t * 1.5f + 1e-6f * (4.f * a2 + 1.f);
+            }
+            long long consumed = g0;  // chunks whose accumulator this thread has waited for
+            const int ylo = __reduce_min_sync(FULLM, mine ? wy0 : 1 << 30);
+            const int yhi = __reduce_max_sync(FULLM, mine ? wy1 : -1);
+            const int xlo = __reduce_min_sync(FULLM, mine ? wx0 : 1 << 30);
+            const int xhi = __reduce_max_sync(FULLM, mine ? wx1 : -1);
             for (int c = 0; c < nch; ++c) {
                 const long long g = g0 + c;
                 const uint32_t b = (uint32_t)(g & 1);
-                if (!bar_wait(&full[b], (uint32_t)((g >> 1) & 1))) {
-                    ok = false;
-                    atomicExch(&a.st->error, 2);
-                } else {
-                    consumed = g + 1;
+                if (bar_wait(&full[b], (uint32_t)((g >> 1) & 1))) consumed = g + 1;
+                else ok = false;
+                ok = __all_sync(FULLM, ok);
+                if (!ok) {
+                    if (lane == 0) atomicExch(&a.st->error, 2);
+                    break;
                 }
                 tc_fence_after();
-                if (ok) {
-                    const int p0 = c * NCH;
-                    // warp-uniform skip of 32-column groups outside every window of the warp
-                    const int ylo = __reduce_min_sync(FULLM, mine ? wy0 : 1 << 30);
-                    const int yhi = __reduce_max_sync(FULLM, mine ? wy1 : -1);
+                const int p0 = c * NCH;
 #pragma unroll 1
-                    for (int grp = 0; grp < NCH / 32; ++grp) {
-                        const int pg = p0 + grp * 32;
-                        if (pg >= ncand) break;
-                        const int rlo = pg / Wc, rhi = min(pg + 31, ncand - 1) / Wc;
-                        if (rhi < ylo || rlo > yhi) continue;
-                        uint32_t v[32];
-                        tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + b * NCH + grp * 32, v);
-                        if (!mine) continue;
-                        int row = rlo, col = pg - rlo * Wc;
+                for (int grp = 0; grp < NCH / 32; ++grp) {
+                    const int pg = p0 + grp * 32;
+                    if (pg >= ncand) break;
+                    // warp-uniform skip of 32-column groups outside every window of the warp
+                    const int rlo = pg / Wc, rhi = min(pg + 31, ncand - 1) / Wc;
+                    if (rhi < ylo || rlo > yhi) continue;
+                    if (rlo == rhi && (pg - rlo * Wc > xhi || pg - rlo * Wc + 31 < xlo)) continue;
+                    uint32_t v[32];
+                    tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + b * NCH + grp * 32, v);
+                    // candidates of this group inside this reference's window, as a bit mask
+                    uint32_t mask = 0;
+                    if (mine) {
+                        int j = 0, row = rlo, col = pg - rlo * Wc;
+                        while (j < 32) {
+                            const int seg = min(32 - j, Wc - col);
+                            if (row >= wy0 && row <= wy1) {
+                                const int c0 = max(col, wx0), c1 = min(col + seg - 1, wx1);
+                                if (c0 <= c1) {
+                                    const int n = c1 - c0 + 1;
+                                    mask |= (n == 32 ? 0xffffffffu : ((1u << n) - 1u)) << (j + c0 - col);
+                                }
+                            }
+                            j += seg;
+                            ++row;
+                            col = 0;
+                        }
+                        if (ncand - pg < 32) mask &= (1u << (ncand - pg)) - 1u;
+                        if (pself >= pg && pself < pg + 32) mask &= ~(1u << (pself - pg));
+                    }
+                    if (!__any_sync(FULLM, mask != 0)) continue;
+                    const float4 *e4 = reinterpret_cast<const float4 *>(E + pg);
+                    float dd[32];
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int p = pg + j;
-                            if (row >= wy0 && row <= wy1 && col >= wx0 && col <= wx1 && p != pself && p < ncand) {
-                                const float d = E[p] + a2 - 2.f * __uint_as_float(v[j]);
-                                if (d < top.thr) top.insert(bd, bp, tid, d, (cy0 + row) * a.W + cx0 + col);
-                            }
-                            if (++col == Wc) {
-                                col = 0;
-                                ++row;
-                            }
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 ev = e4[q];
+                        dd[4 * q + 0] = ev.x + a2 - 2.f * __uint_as_float(v[4 * q + 0]);
+                        dd[4 * q + 1] = ev.y + a2 - 2.f * __uint_as_float(v[4 * q + 1]);
+                        dd[4 * q + 2] = ev.z + a2 - 2.f * __uint_as_float(v[4 * q + 2]);
+                        dd[4 * q + 3] = ev.w + a2 - 2.f * __uint_as_float(v[4 * q + 3]);
+                    }
+                    uint32_t acc = 0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) acc |= (dd[j] < thr ? 1u : 0u) << j;
+                    acc &= mask;
+                    // lists are cut back together: when one lane must, every lane above BUF does
+                    if (__any_sync(FULLM, cnt + __popc(acc) > CAP) && cnt > BUF) {
+                        thr = fminf(thr, cut_list<CAP>(bd, bp, tid, cnt, BUF));
+                        uint32_t a2m = 0;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) a2m |= (dd[j] < thr ? 1u : 0u) << j;
+                        acc &= a2m;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        if ((acc >> j) & 1u) {
+                            bd[cnt * 128 + tid] = dd[j];
+                            bp[cnt * 128 + tid] = pg + j;  // region position; raster index at the re-rank
+                            ++cnt;
                         }
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) bar_arrive(&empty[b]);
-                if (warp == 0 && c + 2 < nch && ok) {
-                    const bool got = bar_wait(&empty[b], (uint32_t)((g >> 1) & 1));
+                if (warp == 0 && c + 2 < nch) {
+                    const bool got = __all_sync(FULLM, bar_wait(&empty[b], (uint32_t)((g >> 1) & 1)));
                     tc_fence_after();
                     if (lane == 0) {
                         if (got) {
@@ -376,31 +482,47 @@ __global__ void __launch_bounds__(128, 1) k_match_tc(TcArgs a) {
                             atomicExch(&a.st->error, 2);
                         }
                     }
-                    if (!got) ok = false;
                     __syncwarp();
+                    if (!got) {
+                        ok = false;
+                        break;
+                    }
                 }
-                ok = !__syncthreads_or(!ok);
-                if (!ok) break;
             }
+            ok = !__syncthreads_or(!ok);
             if (!ok) {  // drain: wait (bounded) for the MMAs already issued before the memory is released
                 for (long long g = consumed; g < *issued_hi; ++g) bar_wait(&full[g & 1], (uint32_t)((g >> 1) & 1));
                 break;
             }
-            const int cnt = top.cnt;
             gc = g0 + nch;
 
-            // ---- FP32 re-rank of the kept candidates, then the K-1 nearest (ties: lower raster index)
+            // ---- FP32 re-rank of the kept candidates (plane read from global memory: the staging
+            //      area now holds the lists), then the K-1 nearest (ties: lower raster index)
             if (mine) {
+                if (cnt > BUF) cut_list<CAP>(bd, bp, tid, cnt, BUF);
+                const float *c0 = a.img, *c1 = a.img + HW, *c2 = a.img + 2 * HW;
+                // plane value at region row y, column x (on chip when kept, else from global memory)
+                auto plane = [&](int y, int x) -> float {
+                    if (ListCfg<K>::KEEP_PLANE) return Ps[y * PSW + x];
+                    const size_t o = (size_t)(cy0 + y) * a.W + cx0 + x;
+                    if (a.C == 1) return __ldg(c0 + o);
+                    if (pass == 0) return __ldg(c1 + o);
+                    return (__ldg(c0 + o) + __ldg(c1 + o)) + __ldg(c2 + o);
+                };
                 const int ay = yr - cy0, ax = xr - cx0;
+                float ar[64];
+#pragma unroll
+                for (int e = 0; e < 64; ++e) ar[e] = plane(ay + (e >> 3), ax + (e & 7));
                 for (int t = 0; t < cnt; ++t) {
-                    const int rast = bp[t * 128 + tid];
-                    const int by = rast / a.W - cy0, bx = rast % a.W - cx0;
+                    const int pq = bp[t * 128 + tid];
+                    const int by = pq / Wc, bx = pq - by * Wc;
+                    bp[t * 128 + tid] = (cy0 + by) * a.W + cx0 + bx;
                     float d = 0.f;
-                    for (int u = 0; u < PS; ++u)
-                        for (int v = 0; v < PS; ++v) {
-                            const float df = Ps[(ay + u) * PSW + ax + v] - Ps[(by + u) * PSW + bx + v];
-                            d = fmaf(df, df, d);
-                        }
+#pragma unroll
+                    for (int e = 0; e < 64; ++e) {
+                        const float df = ar[e] - plane(by + (e >> 3), bx + (e & 7));
+                        d = fmaf(df, df, d);
+                    }
                     bd[t * 128 + tid] = d;
                 }
                 int32_t *out = a.idx + (size_t)r * K;
@@ -436,8 +558,7 @@ __global__ void __launch_bounds__(128, 1) k_match_tc(TcArgs a) {
 
 template <int K>
 hts_status launch_tc(const TcArgs &a, cudaStream_t s) {
-    constexpr int BUF = (2 * K < 8) ? 8 : 2 * K;
-    const TcLayout L = tc_layout<BUF>(a.hc_max, a.wc_max);
+    const TcLayout L = tc_layout<K>(a.hc_max, a.wc_max);
     const hts_status st0 = allow_smem(reinterpret_cast<const void *>(k_match_tc<K>), L.total);
     if (st0 != HTS_OK) return st0;
     int dev = 0, nsm = 152;

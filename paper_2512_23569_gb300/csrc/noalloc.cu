@@ -7,7 +7,7 @@
 // device array of this file, sized for images of at most 512 x 512 pixels
 // (any channel count the library supports), at most 65536 reference patches
 // and at most 2^20 group slots (N_ref * K).  Every GPU that loads the library
-// holds this array (about 18 MB) until the process exits.
+// holds this array (about 21 MB) until the process exits.
 #include <mutex>
 
 #include "hts_internal.h"
@@ -35,7 +35,7 @@ constexpr size_t OFF_GREEN = OFF_IDX + align256(NA_MAX_SLOTS * sizeof(int32_t));
 constexpr size_t OFF_FB = OFF_GREEN + align256(NA_MAX_NREF);
 constexpr size_t OFF_REDO = OFF_FB + align256(NA_MAX_NREF * sizeof(int32_t));
 constexpr size_t OFF_XLIST = OFF_REDO + align256(NA_MAX_NREF * sizeof(int32_t));
-constexpr size_t OFF_XSKIP = OFF_XLIST + align256(NA_MAX_NREF * 16);
+constexpr size_t OFF_XSKIP = OFF_XLIST + align256((size_t)NA_MAX_NREF * XLIST_PER_REF * 16);
 constexpr size_t OFF_ACC = OFF_XSKIP + align256(NA_MAX_NREF);
 constexpr size_t OFF_W = OFF_ACC + align256(3 * NA_MAX_PIXELS * sizeof(long long));
 constexpr size_t NA_BYTES = OFF_W + align256(NA_MAX_PIXELS * sizeof(int));
@@ -128,5 +128,6 @@ extern "C" hts_status hts_denoise_noalloc(const float *noisy, float *out, int H,
     if (sigma < 0) st = launch_sigma(noisy, g, *p, ueig, idx, redo, ds, s);
     else st = launch_set_sigma((double)sigma, g, *p, ds, s);
     if (st != HTS_OK) return st;
-    return launch_filter(noisy, g, idx, ub64, ub32, acc, wcount, redo, xlist, xskip, ds, out, s);
+    return launch_filter(noisy, g, idx, ub64, ub32, acc, wcount, redo, xlist, xskip, ds, out,
+                         p->precision == 0 ? 1 : 0, s);
 }
