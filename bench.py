@@ -294,8 +294,8 @@ def run_batch(args):
 # ------------------------------------------------------------------ precision-form workload
 
 def tc_issued_flops(H, W, K, win, step, green, C):
-    """Tensor-core flops k_match_tc issues: per tile and plane pass, ceil(Hc*Wc/256) MMA groups of
-    128 x 256 x 64 (BF16, 2 flop per MAC)."""
+    """Tensor-core flops k_match_tc issues: per 8 x 8-reference tile and plane pass, ceil(Hc*Wc/128)
+    MMA groups of 128 candidates x 64 references x 64 (BF16, 2 flop per MAC)."""
     import numpy as np
 
     R = (win - 1) // 2
@@ -303,17 +303,17 @@ def tc_issued_flops(H, W, K, win, step, green, C):
     ny, nx = len(ys), len(xs)
     g = np.asarray(green).reshape(ny, nx) if C == 3 else None
     total = 0
-    for gy0 in range(0, ny, 16):
+    for gy0 in range(0, ny, 8):
         for gx0 in range(0, nx, 8):
-            gy1, gx1 = min(ny, gy0 + 16) - 1, min(nx, gx0 + 8) - 1
+            gy1, gx1 = min(ny, gy0 + 8) - 1, min(nx, gx0 + 8) - 1
             cy0, cy1 = max(0, ys[gy0] - R), min(H - 8, ys[gy1] + R)
             cx0, cx1 = max(0, xs[gx0] - R), min(W - 8, xs[gx1] + R)
-            nch = ((cy1 - cy0 + 1) * (cx1 - cx0 + 1) + 255) // 256
+            nch = ((cy1 - cy0 + 1) * (cx1 - cx0 + 1) + 127) // 128
             passes = 1
             if C == 3:
                 blk = g[gy0:gy1 + 1, gx0:gx1 + 1]
                 passes = int(blk.any()) + int((blk == 0).any())
-            total += passes * nch * 2 * 128 * 256 * 64
+            total += passes * nch * 2 * 128 * 64 * 64
     return total
 
 

@@ -3,24 +3,33 @@
 //
 // For a reference a and a candidate b of the same matching plane,
 //   ||a - b||^2 = ||a||^2 + ||b||^2 - 2 a.b,
-// and the cross terms of a tile of 128 references (16 x 8 grid positions)
-// against every candidate position of the tile's search region form one
-// BF16 GEMM with FP32 accumulation (tcgen05.mma, accumulator in TMEM):
-//   D[r][p] = sum_{u<8, v<8} A[r][8u+v] * plane[y_p + u][x_p + v].
+// and the cross terms of every candidate position of a tile's search region
+// against the tile's 64 references (8 x 8 grid positions) form one BF16 GEMM
+// with FP32 accumulation (tcgen05.mma, accumulator in TMEM):
+//   D[p][r] = sum_{u<8, v<8} plane[y_p + u][x_p + v] * A[r][8u+v].
 // No candidate matrix is materialised: the region is staged once as
 // "row-8 vectors" Q[p] = plane[y_p][x_p .. x_p+7] (16 bytes, one core-matrix
 // row), candidates are numbered p = y * Wc + x in the region, and the K slice
-// of patch rows (u, u+1) of the N = 256 candidates p0 .. p0+255 is the
+// of patch rows (u, u+1) of the M = 128 candidates p0 .. p0+127 is the
 // shared-memory matrix starting at Q[p0 + u Wc] with core matrices 8 rows
-// (128 bytes) apart along N and Wc rows (16 Wc bytes) apart along K.
-// Two TMEM accumulators of 256 columns alternate: the MMAs of chunk c+1 run
-// while the four warps read chunk c.  Each thread owns one reference (TMEM
-// lane), forms the approximate distance of every candidate inside its
-// search window from the accumulator and the BF16 squared norms, and keeps
-// the 2K smallest (48 for K = 32); those are re-ranked with FP32 distances of
-// the FP32 plane, and the K-1 smallest (ties to the lower raster index)
-// follow the reference in its group.  Eq. 9 picks the plane per reference: a colour
-// tile runs once per plane that one of its references uses.
+// (128 bytes) apart along M and Wc rows (16 Wc bytes) apart along K.
+//
+// The candidates are the MMA's M dimension, so a warp reading 32 TMEM lanes
+// (eight warps: two per lane quarter, each taking 32 of the reference
+// columns) holds, for each reference, 32 candidates side by side: the
+// filter "inside the reference's search window and below its threshold" is a
+// warp ballot, and the passing candidates are appended to the reference's
+// list at a prefix-sum position (one shared atomic per reference and warp).
+// Four TMEM accumulators of 64 columns let the MMAs run up to three chunks
+// ahead of the warps.  A reference's threshold starts at 1.5 times the
+// (K-1)-th smallest BF16 distance to the positions around it (so its K-1
+// nearest candidates always pass) and drops to its list's 2K-th smallest
+// when the list is cut back (warp-cooperative bisection, between chunks).
+// At the end every reference's kept candidates are re-ranked with FP32
+// distances of the FP32 plane and the K-1 smallest (ties to the lower raster
+// index) follow the reference in its group.  Eq. 9 picks the plane per
+// reference: a colour tile runs once per plane that one of its references
+// uses.
 //
 // Every mbarrier wait is bounded; a wait that gives up records error code 2
 // in the call's state, and the block waits (bounded) for the MMAs it has
@@ -34,11 +43,15 @@
 namespace hts {
 namespace {
 
-constexpr int TTY = 16, TTX = 8;  // reference tile (grid rows x grid columns) = 128 = MMA M
-constexpr int NCH = 256;          // candidates per MMA (N) and per TMEM accumulator
-constexpr uint32_t TMEM_COLS = 512;
+constexpr int TTY = 8, TTX = 8;  // reference tile (grid rows x grid columns)
+constexpr int NR = TTY * TTX;    // references per tile = MMA N
+constexpr int MC = 128;          // candidates per chunk = MMA M
+constexpr int NBUF = 4;          // TMEM accumulators (NR columns each)
+constexpr uint32_t TMEM_COLS = 256;
 constexpr long long SPIN = 1ll << 24;
 constexpr unsigned FULLM = 0xffffffffu;
+constexpr int NT = 256;  // threads: warp w reads TMEM lanes 32 (w % 4) .. +31 (its candidates) and the
+                         // columns of references 32 (w / 4) .. +31
 
 // Offsets (dy, dx) of the positions around a reference whose distances seed
 // its threshold, nearest first (the 7 x 7 square without its centre); the
@@ -61,42 +74,49 @@ struct TcArgs {
     int hc_max, wc_max;  // bounds of the candidate region over all tiles
 };
 
+// Candidates kept per reference for the FP32 re-rank (the "2K"; 48 for K =
+// 32) and the list capacity: a list is cut back to BUF once fewer than MC
+// free slots (a whole chunk) remain, so cuts are rarer the larger CAP is.
+template <int K>
+struct ListCfg {
+    static constexpr int BUF = (2 * K < 8) ? 8 : (2 * K > 48 ? 48 : 2 * K);
+    static constexpr int CAP = BUF + MC + 48;
+};
+
 struct TcLayout {
-    size_t r0, a, e, ps, rn, bd, bp, bar, total;
+    size_t q, a, e, ps, rn, bd, bp, ref, bar, total;
 };
 
 __host__ __device__ inline size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Candidates kept per reference (the "2K" of the re-rank; 48 for K = 32 to
-// fit on chip) and the list capacity: a 32-candidate group is appended
-// without checks and the list is cut back to BUF when it might overflow.
-template <int K>
-struct ListCfg {
-    static constexpr int BUF = (2 * K < 8) ? 8 : (2 * K > 48 ? 48 : 2 * K);
-    static constexpr int CAP = BUF + 32;
-    static constexpr bool KEEP_PLANE = K <= 16;  // FP32 plane stays on chip for the re-rank
+// Per-reference record in shared memory.
+struct RefRec {
+    int wy0, wy1, wx0, wx1;  // search window, region coordinates
+    int pself, mine, cnt, pad;
+    float a2, thr, pad1, pad2;
 };
 
-// Shared memory: Q (row-8 vectors), A, E (squared norms), the FP32 plane Ps,
-// then the lists, which overlay the row norms rn (only needed before the
-// MMAs) -- and, for K = 32, Ps too (the re-rank then reads global memory).
+// Shared memory: Q (row-8 vectors), A (references), E (squared norms), the
+// FP32 plane Ps, the row norms rn (only needed while E is formed), the lists
+// (overlaying rn), per-reference records, barriers.
 template <int K>
 __host__ __device__ inline TcLayout tc_layout(int hc_max, int wc_max) {
     TcLayout L;
-    const size_t nch = ((size_t)hc_max * wc_max + NCH - 1) / NCH;
-    const size_t nr0 = nch * NCH + 7 * (size_t)wc_max;
-    L.r0 = 0;
-    L.a = up(L.r0 + nr0 * 16, 1024);
-    L.e = L.a + 128 * 64 * 2;
-    L.ps = up(L.e + nch * NCH * 4, 16);
-    L.rn = up(L.ps + (size_t)(hc_max + 7) * (wc_max + 7) * 4, 16);  // row norms, after the plane
-    L.bd = ListCfg<K>::KEEP_PLANE ? L.rn : L.ps;
-    L.bp = L.bd + (size_t)ListCfg<K>::CAP * 128 * 4;
-    const size_t lists_end = L.bp + (size_t)ListCfg<K>::CAP * 128 * 4;
-    const size_t ps_end = L.rn + nr0 * 4;
-    L.bar = up(lists_end > ps_end ? lists_end : ps_end, 16);
-    L.total = L.bar + 64;
-    if (L.total < 120 * 1024) L.total = 120 * 1024;  // one block per SM: it holds all 512 TMEM columns
+    const size_t nch = ((size_t)hc_max * wc_max + MC - 1) / MC;
+    const size_t nq = nch * MC + 7 * (size_t)wc_max;
+    L.q = 0;
+    L.a = up(L.q + nq * 16, 1024);
+    L.e = L.a + (size_t)NR * 64 * 2;
+    L.ps = up(L.e + nch * MC * 4, 16);
+    L.rn = up(L.ps + (size_t)(hc_max + 7) * (wc_max + 7) * 4, 16);
+    L.bd = L.rn;
+    L.bp = L.bd + (size_t)NR * ListCfg<K>::CAP * 4;
+    const size_t lists_end = L.bp + (size_t)NR * ListCfg<K>::CAP * 4;
+    const size_t rn_end = L.rn + nq * 4;
+    L.ref = up(lists_end > rn_end ? lists_end : rn_end, 16);
+    L.bar = up(L.ref + (size_t)NR * sizeof(RefRec), 16);
+    L.total = L.bar + 128;
+    if (L.total < 120 * 1024) L.total = 120 * 1024;  // one block per SM
     return L;
 }
 
@@ -129,10 +149,6 @@ __device__ __forceinline__ void bar_init(uint64_t *bar, int count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count));
 }
 
-__device__ __forceinline__ void bar_arrive(uint64_t *bar) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n" ::"r"(su32(bar)));
-}
-
 // Bounded wait (non-blocking polls) for the completion of the phase with this
 // parity; false on giving up.
 __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) {
@@ -149,45 +165,6 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) {
     return false;
 }
 
-// Cuts this thread's list (slots i * 128 + tid, i < cnt) back to `keep`
-// entries that include every entry below the returned value T (T is the
-// smallest value, to a bisection of 24 steps, with at least `keep` entries
-// <= T); later candidates are kept only if below T.  Every lane runs the same
-// instruction sequence (loops over CAP slots with predicates), so lanes of a
-// warp that cut together do not serialise.
-template <int CAP>
-__device__ float cut_list(float *bd, int *bp, int tid, int &cnt, int keep) {
-    float lo = __builtin_huge_valf(), hi = -__builtin_huge_valf();
-#pragma unroll 4
-    for (int i = 0; i < CAP; ++i) {
-        const float d = bd[i * 128 + tid];
-        if (i < cnt) {
-            lo = fminf(lo, d);
-            hi = fmaxf(hi, d);
-        }
-    }
-    for (int it = 0; it < 24; ++it) {  // invariant: count(<= hi) >= keep
-        const float mid = 0.5f * (lo + hi);
-        int c = 0;
-#pragma unroll 8
-        for (int i = 0; i < CAP; ++i) c += (i < cnt && bd[i * 128 + tid] <= mid) ? 1 : 0;
-        if (c >= keep) hi = mid;
-        else lo = mid;
-    }
-    int w = 0;
-    for (int i = 0; i < CAP; ++i) {  // stable compaction: entries < hi, then entries == hi up to `keep`
-        const float d = bd[i * 128 + tid];
-        const int pv = bp[i * 128 + tid];
-        if (i < cnt && d <= hi && w < keep) {
-            bd[w * 128 + tid] = d;
-            bp[w * 128 + tid] = pv;
-            ++w;
-        }
-    }
-    cnt = w;
-    return hi;
-}
-
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -201,8 +178,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
           "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half)
@@ -211,30 +188,93 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 
 __device__ __forceinline__ float bf_round(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
 
+// Squared distance of two row-8 BF16 vectors added to acc, in FP32.
+__device__ __forceinline__ float row_dist2(uint4 x, uint4 y, float acc) {
+    const uint32_t xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&xs[i]));
+        const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&ys[i]));
+        const float d0 = fa.x - fb.x, d1 = fa.y - fb.y;
+        acc = fmaf(d0, d0, acc);
+        acc = fmaf(d1, d1, acc);
+    }
+    return acc;
+}
+
+// Warp-cooperative cut of reference j's list (n entries at j * CAP) back to
+// `keep` entries containing every entry below the returned T (the smallest
+// value, to a 12-step bisection of the list's range, with at least `keep`
+// entries <= T); the kept entries stay in list order.
+template <int CAP>
+__device__ float cut_list_warp(float *bd, int *bp, int j, int n, int keep, int lane, int *n_out) {
+    constexpr int PER = (CAP + 31) / 32;
+    float dv[PER];
+    int pv[PER];
+    float lo = __builtin_huge_valf(), hi = -__builtin_huge_valf();
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+        const int i = t * 32 + lane;
+        dv[t] = (i < n) ? bd[j * CAP + i] : __builtin_huge_valf();
+        pv[t] = (i < n) ? bp[j * CAP + i] : 0;
+        if (i < n) {
+            lo = fminf(lo, dv[t]);
+            hi = fmaxf(hi, dv[t]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(FULLM, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(FULLM, hi, o));
+    }
+    for (int it = 0; it < 12; ++it) {  // invariant: count(<= hi) >= keep
+        const float mid = 0.5f * (lo + hi);
+        int c = 0;
+#pragma unroll
+        for (int t = 0; t < PER; ++t) c += __popc(__ballot_sync(FULLM, dv[t] <= mid));
+        if (c >= keep) hi = mid;
+        else lo = mid;
+    }
+    __syncwarp();
+    int w = 0;
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {  // stable compaction: entries <= hi, at most `keep`
+        const bool k = dv[t] <= hi;
+        const uint32_t m = __ballot_sync(FULLM, k);
+        const int pos = w + __popc(m & ((1u << lane) - 1u));
+        if (k && pos < keep) {
+            bd[j * CAP + pos] = dv[t];
+            bp[j * CAP + pos] = pv[t];
+        }
+        w += __popc(m);
+    }
+    __syncwarp();
+    *n_out = w < keep ? w : keep;
+    return hi;
+}
+
 template <int K>
-__global__ void __launch_bounds__(128, 1) k_match_tc(TcArgs a) {
+__global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
     constexpr int BUF = ListCfg<K>::BUF, CAP = ListCfg<K>::CAP;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const TcLayout L = tc_layout<K>(a.hc_max, a.wc_max);
-    uint4 *Q = reinterpret_cast<uint4 *>(smem_raw + L.r0);
+    uint4 *Q = reinterpret_cast<uint4 *>(smem_raw + L.q);
     unsigned char *Abuf = smem_raw + L.a;
     float *E = reinterpret_cast<float *>(smem_raw + L.e);
     float *Ps = reinterpret_cast<float *>(smem_raw + L.ps);
     float *rn = reinterpret_cast<float *>(smem_raw + L.rn);
     float *bd = reinterpret_cast<float *>(smem_raw + L.bd);
     int *bp = reinterpret_cast<int *>(smem_raw + L.bp);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + L.bar);  // [2]
-    uint64_t *empty = full + 2;                                         // [2]
-    long long *issued_hi = reinterpret_cast<long long *>(empty + 2);  // one past the last chunk issued
+    RefRec *rec = reinterpret_cast<RefRec *>(smem_raw + L.ref);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + L.bar);  // [NBUF]
+    long long *issued_hi = reinterpret_cast<long long *>(full + NBUF);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(issued_hi + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wq4 = warp & 3, wcol = (warp >> 2) * 32;  // TMEM lane quarter, first reference column
     const size_t HW = (size_t)a.H * a.W;
     if (tid == 0) {
-        bar_init(&full[0], 1);
-        bar_init(&full[1], 1);
-        bar_init(&empty[0], 4);
-        bar_init(&empty[1], 4);
+        for (int b = 0; b < NBUF; ++b) bar_init(&full[b], 1);
         *issued_hi = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -247,8 +287,8 @@ __global__ void __launch_bounds__(128, 1) k_match_tc(TcArgs a) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tmem_slot;
-    const uint32_t idesc = idesc_bf16(128, NCH);
-    long long gc = 0;  // chunks issued by this block so far (buffer = gc & 1, use = gc >> 1)
+    const uint32_t idesc = idesc_bf16(MC, NR);
+    long long gc = 0;  // chunks issued by this block so far (buffer = gc % NBUF, use = gc / NBUF)
     bool ok = true;
 
     for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
@@ -261,22 +301,36 @@ __global__ void __launch_bounds__(128, 1) k_match_tc(TcArgs a) {
         const int cx1 = min(a.W - PS, grid_pos(gx1, a.W, a.step) + a.R);
         const int Hc = cy1 - cy0 + 1, Wc = cx1 - cx0 + 1, PSW = Wc + 7;
         const int ncand = Hc * Wc;
-        const int nch = (ncand + NCH - 1) / NCH;
-        const int nq = nch * NCH + 7 * Wc;
-        // this thread's reference
-        const int ry = gy0 + warp * 4 + (lane >> 3), rx = gx0 + (lane & 7);
-        const bool rvalid = ry <= gy1 && rx <= gx1;
-        const int r = rvalid ? ry * a.nx + rx : 0;
-        const int yr = grid_pos(ry, a.H, a.step), xr = grid_pos(rx, a.W, a.step);
-        const int wy0 = max(0, yr - a.R) - cy0, wy1 = min(a.H - PS, yr + a.R) - cy0;  // window, region coords
-        const int wx0 = max(0, xr - a.R) - cx0, wx1 = min(a.W - PS, xr + a.R) - cx0;
-        const int pself = (yr - cy0) * Wc + (xr - cx0);
+        const int nch = (ncand + MC - 1) / MC;
+        const int nq = nch * MC + 7 * Wc;
 
         for (int pass = 0; pass < (a.C == 3 ? 2 : 1) && ok; ++pass) {
-            const bool mine = rvalid && (a.C == 1 || (int)a.green[r] == (pass == 0 ? 1 : 0));
-            if (!__syncthreads_or(mine)) continue;
-            // ---- stage the plane (FP32), then the row-8 vectors, A and the squared norms
-            for (int e = tid; e < (Hc + 7) * PSW; e += 128) {
+            // ---- per-reference records (thread j < NR: reference j = row j/8, column j%8 of the tile)
+            bool any = false;
+            if (tid < NR) {
+                const int ry = gy0 + (tid >> 3), rx = gx0 + (tid & 7);
+                const bool valid = ry <= gy1 && rx <= gx1;
+                const int r = valid ? ry * a.nx + rx : 0;
+                const bool mine = valid && (a.C == 1 || (int)a.green[r] == (pass == 0 ? 1 : 0));
+                const int yr = grid_pos(min(ry, gy1), a.H, a.step), xr = grid_pos(min(rx, gx1), a.W, a.step);
+                RefRec q;
+                q.wy0 = max(0, yr - a.R) - cy0;
+                q.wy1 = min(a.H - PS, yr + a.R) - cy0;
+                q.wx0 = max(0, xr - a.R) - cx0;
+                q.wx1 = min(a.W - PS, xr + a.R) - cx0;
+                q.pself = (yr - cy0) * Wc + (xr - cx0);
+                q.mine = mine ? 1 : 0;
+                q.cnt = 0;
+                q.pad = 0;
+                q.a2 = 0.f;
+                q.thr = __builtin_huge_valf();
+                q.pad1 = q.pad2 = 0.f;
+                rec[tid] = q;
+                any = mine;
+            }
+            if (!__syncthreads_or(any)) continue;
+            // ---- stage the plane (FP32), the row-8 vectors and their norms, E, A
+            for (int e = tid; e < (Hc + 7) * PSW; e += NT) {
                 const int y = e / PSW, x = e - y * PSW;
                 const size_t o = (size_t)(cy0 + y) * a.W + cx0 + x;
                 float v;
@@ -286,7 +340,7 @@ __global__ void __launch_bounds__(128, 1) k_match_tc(TcArgs a) {
                 Ps[e] = v;
             }
             __syncthreads();
-            for (int q = tid; q < nq; q += 128) {
+            for (int q = tid; q < nq; q += NT) {
                 const int y = q / Wc, x = q - y * Wc;
                 uint4 w = make_uint4(0, 0, 0, 0);
                 float n2 = 0.f;
@@ -304,7 +358,7 @@ __global__ void __launch_bounds__(128, 1) k_match_tc(TcArgs a) {
                 rn[q] = n2;  // squared norm of the BF16 row-8 vector
             }
             __syncthreads();
-            for (int p = tid; p < nch * NCH; p += 128) {
+            for (int p = tid; p < nch * MC; p += NT) {
                 float e2 = 0.f;
                 if (p < ncand) {
 #pragma unroll
@@ -312,72 +366,33 @@ __global__ void __launch_bounds__(128, 1) k_match_tc(TcArgs a) {
                 }
                 E[p] = e2;
             }
-            // A: row t = this block's reference t, element 8u+v; core matrix (t/8, u) at (t/8)*1024 + u*128
-            for (int e = tid; e < 128 * PS; e += 128) {
-                const int t = e >> 3, u = e & 7;
-                const int tw = t >> 5, tl = t & 31;
-                const int ty_ = gy0 + tw * 4 + (tl >> 3), tx_ = gx0 + (tl & 7);
+            // A: row j = reference j, element 8u+v; core matrix (j/8, u) at (j/8)*1024 + u*128
+            for (int e = tid; e < NR * PS; e += NT) {
+                const int j = e >> 3, u = e & 7;
+                const int ty_ = gy0 + (j >> 3), tx_ = gx0 + (j & 7);
                 uint4 w = make_uint4(0, 0, 0, 0);
-                if (ty_ <= gy1 && tx_ <= gx1) {
-                    const int py = grid_pos(ty_, a.H, a.step) - cy0 + u, px = grid_pos(tx_, a.W, a.step) - cx0;
-                    const float *s = Ps + py * PSW + px;
-                    w = make_uint4(pack_bf16(s[0], s[1]), pack_bf16(s[2], s[3]), pack_bf16(s[4], s[5]),
-                                   pack_bf16(s[6], s[7]));
-                }
-                *reinterpret_cast<uint4 *>(Abuf + (t >> 3) * 1024 + u * 128 + (t & 7) * 16) = w;
+                if (ty_ <= gy1 && tx_ <= gx1) w = Q[rec[j].pself + u * Wc];
+                *reinterpret_cast<uint4 *>(Abuf + (j >> 3) * 1024 + u * 128 + (j & 7) * 16) = w;
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            const float a2 = rvalid ? E[min(pself, nch * NCH - 1)] : 0.f;
-
-            // ---- chunks: MMAs (warp 0, one elected lane) and the per-reference scan
-            auto issue = [&](int c, long long g) {
-                const uint32_t b = (uint32_t)(g & 1);
-                const uint32_t d = tbase + b * NCH;
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint64_t ad = sdesc(su32(Abuf) + kk * 256, 128, 1024);
-                    const uint64_t bdsc = sdesc(su32(Q + (size_t)c * NCH + (size_t)2 * kk * Wc), 16u * Wc, 128);
-                    mma_bf16(d, ad, bdsc, idesc, kk > 0 ? 1u : 0u);
-                }
-                mma_commit(&full[b]);
-            };
-            const long long g0 = gc;
-            if (warp == 0 && lane == 0) {
-                tc_fence_after();
-                issue(0, g0);
-                if (nch > 1) issue(1, g0 + 1);
-                *issued_hi = g0 + (nch > 1 ? 2 : 1);
-            }
-            __syncwarp();
-            // threshold seed: the (K-1)-th smallest BF16 distance from the reference to the
-            // positions around it bounds the (K-1)-th nearest candidate from above, so every
-            // candidate that can be among the K-1 nearest passes the filter below it, while
-            // few others do (a factor 1.5 and an absolute margin cover the different FP32
-            // rounding of the tensor-core form and keep, for the FP32 re-rank, the candidates
-            // that BF16 rounding ranks slightly too far)
-            int cnt = 0;
-            float thr = __builtin_huge_valf();
-            if (mine) {
+            __syncthreads();  // rn is dead from here: the lists overlay it
+            // ---- thresholds: 1.5 x the (K-1)-th smallest BF16 distance from the reference to the
+            //      positions around it (an upper bound of its (K-1)-th nearest candidate, so those
+            //      always pass), plus a margin for the different FP32 rounding of the MMA form
+            if (tid < NR && rec[tid].mine) {
                 constexpr int NS = (K + 8 > 24) ? ((K + 8 > NSEED) ? NSEED : K + 8) : 24;
-                const int ay = yr - cy0, ax = xr - cx0;
-                float ab[64];
-#pragma unroll
-                for (int e = 0; e < 64; ++e) ab[e] = bf_round(Ps[(ay + (e >> 3)) * PSW + ax + (e & 7)]);
+                const RefRec q = rec[tid];
+                const int ay = q.pself / Wc, ax = q.pself - ay * Wc;
+                const float a2 = E[q.pself];
                 float best[K - 1];
 #pragma unroll
                 for (int i = 0; i < K - 1; ++i) best[i] = __builtin_huge_valf();
                 for (int sidx = 0; sidx < NS; ++sidx) {
-                    const int y = yr + c_seed[sidx][0], x = xr + c_seed[sidx][1];
-                    const bool in = y >= max(0, yr - a.R) && y <= min(a.H - PS, yr + a.R) &&
-                                    x >= max(0, xr - a.R) && x <= min(a.W - PS, xr + a.R);
-                    const float *q = Ps + (in ? (y - cy0) * PSW + (x - cx0) : ay * PSW + ax);
+                    const int y = ay + c_seed[sidx][0], x = ax + c_seed[sidx][1];
+                    const bool in = y >= q.wy0 && y <= q.wy1 && x >= q.wx0 && x <= q.wx1;
+                    const int pq = in ? y * Wc + x : q.pself;
                     float d = 0.f;
 #pragma unroll
-                    for (int e = 0; e < 64; ++e) {
-                        const float df = ab[e] - bf_round(q[(e >> 3) * PSW + (e & 7)]);
-                        d = fmaf(df, df, d);
-                    }
+                    for (int u = 0; u < PS; ++u) d = row_dist2(Q[q.pself + u * Wc], Q[pq + u * Wc], d);
                     if (!in) d = __builtin_huge_valf();
 #pragma unroll
                     for (int i = 0; i < K - 1; ++i) {  // branch-free insertion into the sorted seeds
@@ -387,162 +402,165 @@ __global__ void __launch_bounds__(128, 1) k_match_tc(TcArgs a) {
                     }
                 }
                 const float t = best[K - 2];
-                if (t < __builtin_huge_valf()) thr = t * 1.5f + 1e-6f * (4.f * a2 + 1.f);
+                rec[tid].a2 = a2;
+                rec[tid].thr = (t < __builtin_huge_valf()) ? t * 1.5f + 1e-6f * (4.f * a2 + 1.f)
+                                                           : __builtin_huge_valf();
             }
-            long long consumed = g0;  // chunks whose accumulator this thread has waited for
-            const int ylo = __reduce_min_sync(FULLM, mine ? wy0 : 1 << 30);
-            const int yhi = __reduce_max_sync(FULLM, mine ? wy1 : -1);
-            const int xlo = __reduce_min_sync(FULLM, mine ? wx0 : 1 << 30);
-            const int xhi = __reduce_max_sync(FULLM, mine ? wx1 : -1);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+
+            // ---- chunks of MC candidates: MMAs (thread 0), then every warp's 32 lanes
+            auto issue = [&](int c, long long g) {
+                const uint32_t b = (uint32_t)(g % NBUF);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t cd = sdesc(su32(Q + (size_t)c * MC + (size_t)2 * kk * Wc), 16u * Wc, 128);
+                    const uint64_t rd = sdesc(su32(Abuf) + kk * 256, 128, 1024);
+                    mma_bf16(tbase + b * NR, cd, rd, idesc, kk > 0 ? 1u : 0u);
+                }
+                mma_commit(&full[b]);
+            };
+            const long long g0 = gc;
+            if (tid == 0) {
+                tc_fence_after();
+                for (int c = 0; c < nch && c < NBUF; ++c) issue(c, g0 + c);
+                *issued_hi = g0 + min(nch, NBUF);
+            }
+            long long consumed = g0;
             for (int c = 0; c < nch; ++c) {
                 const long long g = g0 + c;
-                const uint32_t b = (uint32_t)(g & 1);
-                if (bar_wait(&full[b], (uint32_t)((g >> 1) & 1))) consumed = g + 1;
+                const uint32_t b = (uint32_t)(g % NBUF);
+                if (bar_wait(&full[b], (uint32_t)((g / NBUF) & 1))) consumed = g + 1;
                 else ok = false;
                 ok = __all_sync(FULLM, ok);
-                if (!ok) {
-                    if (lane == 0) atomicExch(&a.st->error, 2);
-                    break;
-                }
-                tc_fence_after();
-                const int p0 = c * NCH;
-#pragma unroll 1
-                for (int grp = 0; grp < NCH / 32; ++grp) {
-                    const int pg = p0 + grp * 32;
-                    if (pg >= ncand) break;
-                    // warp-uniform skip of 32-column groups outside every window of the warp
-                    const int rlo = pg / Wc, rhi = min(pg + 31, ncand - 1) / Wc;
-                    if (rhi < ylo || rlo > yhi) continue;
-                    if (rlo == rhi && (pg - rlo * Wc > xhi || pg - rlo * Wc + 31 < xlo)) continue;
-                    uint32_t v[32];
-                    tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + b * NCH + grp * 32, v);
-                    // candidates of this group inside this reference's window, as a bit mask
-                    uint32_t mask = 0;
-                    if (mine) {
-                        int j = 0, row = rlo, col = pg - rlo * Wc;
-                        while (j < 32) {
-                            const int seg = min(32 - j, Wc - col);
-                            if (row >= wy0 && row <= wy1) {
-                                const int c0 = max(col, wx0), c1 = min(col + seg - 1, wx1);
-                                if (c0 <= c1) {
-                                    const int n = c1 - c0 + 1;
-                                    mask |= (n == 32 ? 0xffffffffu : ((1u << n) - 1u)) << (j + c0 - col);
-                                }
-                            }
-                            j += seg;
-                            ++row;
-                            col = 0;
+                if (ok) {
+                    tc_fence_after();
+                    uint32_t v0[32];
+                    tmem_ld32(tbase + ((uint32_t)(wq4 * 32) << 16) + b * NR + wcol, v0);
+                    tmem_wait_ld();
+                    // this lane's candidate
+                    const int pw = c * MC + wq4 * 32;
+                    const int p = pw + lane;
+                    const bool cval = p < ncand;
+                    const int prow = p / Wc, pcol = p - prow * Wc;
+                    const float e = cval ? E[p] : 0.f;
+                    const int rlo = pw / Wc, rhi = min(pw + 31, ncand - 1) / Wc;
+                    (void)rlo;
+                    (void)rhi;
+                    auto scan = [&](int j, uint32_t raw) {
+                        // no branch before the ballot, so the loads of consecutive references overlap
+                        const int4 wq = *reinterpret_cast<const int4 *>(&rec[j].wy0);
+                        const int4 wm = *reinterpret_cast<const int4 *>(&rec[j].pself);
+                        const float2 at = *reinterpret_cast<const float2 *>(&rec[j].a2);
+                        const float d = e + at.x - 2.f * __uint_as_float(raw);
+                        const bool pass = wm.y && cval && prow >= wq.x && prow <= wq.y && pcol >= wq.z &&
+                                          pcol <= wq.w && p != wm.x && d < at.y;
+                        const uint32_t m = __ballot_sync(FULLM, pass);
+                        if (!m) return;
+                        int base = 0;
+                        if (lane == 0) base = atomicAdd(&rec[j].cnt, __popc(m));
+                        base = __shfl_sync(FULLM, base, 0);
+                        const int pos = base + __popc(m & ((1u << lane) - 1u));
+                        if (pass && pos < CAP) {
+                            bd[j * CAP + pos] = d;
+                            bp[j * CAP + pos] = p;
                         }
-                        if (ncand - pg < 32) mask &= (1u << (ncand - pg)) - 1u;
-                        if (pself >= pg && pself < pg + 32) mask &= ~(1u << (pself - pg));
-                    }
-                    if (!__any_sync(FULLM, mask != 0)) continue;
-                    const float4 *e4 = reinterpret_cast<const float4 *>(E + pg);
-                    float dd[32];
+                    };
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 ev = e4[q];
-                        dd[4 * q + 0] = ev.x + a2 - 2.f * __uint_as_float(v[4 * q + 0]);
-                        dd[4 * q + 1] = ev.y + a2 - 2.f * __uint_as_float(v[4 * q + 1]);
-                        dd[4 * q + 2] = ev.z + a2 - 2.f * __uint_as_float(v[4 * q + 2]);
-                        dd[4 * q + 3] = ev.w + a2 - 2.f * __uint_as_float(v[4 * q + 3]);
-                    }
-                    uint32_t acc = 0;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) acc |= (dd[j] < thr ? 1u : 0u) << j;
-                    acc &= mask;
-                    // lists are cut back together: when one lane must, every lane above BUF does
-                    if (__any_sync(FULLM, cnt + __popc(acc) > CAP) && cnt > BUF) {
-                        thr = fminf(thr, cut_list<CAP>(bd, bp, tid, cnt, BUF));
-                        uint32_t a2m = 0;
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) a2m |= (dd[j] < thr ? 1u : 0u) << j;
-                        acc &= a2m;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        if ((acc >> j) & 1u) {
-                            bd[cnt * 128 + tid] = dd[j];
-                            bp[cnt * 128 + tid] = pg + j;  // region position; raster index at the re-rank
-                            ++cnt;
-                        }
-                    }
+                    for (int j = 0; j < 32; ++j) scan(wcol + j, v0[j]);
                 }
                 tc_fence_before();
-                __syncwarp();
-                if (lane == 0) bar_arrive(&empty[b]);
-                if (warp == 0 && c + 2 < nch) {
-                    const bool got = __all_sync(FULLM, bar_wait(&empty[b], (uint32_t)((g >> 1) & 1)));
-                    tc_fence_after();
-                    if (lane == 0) {
-                        if (got) {
-                            issue(c + 2, g + 2);
-                            *issued_hi = g + 3;
-                        } else {
-                            atomicExch(&a.st->error, 2);
+                ok = !__syncthreads_or(!ok);
+                if (!ok) break;
+                // lists that the next chunk could overflow are cut back (reference j by warp j mod 4)
+                if (c + 1 < nch) {
+                    for (int j = warp; j < NR; j += NT / 32) {
+                        const int n = rec[j].cnt;
+                        if (n > CAP - MC) {
+                            int n2 = 0;
+                            const float t = cut_list_warp<CAP>(bd, bp, j, n < CAP ? n : CAP, BUF, lane, &n2);
+                            if (lane == 0) {
+                                rec[j].cnt = n2;
+                                rec[j].thr = fminf(rec[j].thr, t);
+                            }
                         }
                     }
-                    __syncwarp();
-                    if (!got) {
-                        ok = false;
-                        break;
-                    }
+                }
+                __syncthreads();
+                if (tid == 0 && c + NBUF < nch) {  // the buffer of chunk c is free: chunk c + NBUF goes there
+                    tc_fence_after();
+                    issue(c + NBUF, g + NBUF);
+                    *issued_hi = g + NBUF + 1;
                 }
             }
-            ok = !__syncthreads_or(!ok);
             if (!ok) {  // drain: wait (bounded) for the MMAs already issued before the memory is released
-                for (long long g = consumed; g < *issued_hi; ++g) bar_wait(&full[g & 1], (uint32_t)((g >> 1) & 1));
+                for (long long g = consumed; g < *issued_hi; ++g)
+                    bar_wait(&full[g % NBUF], (uint32_t)((g / NBUF) & 1));
                 break;
             }
             gc = g0 + nch;
 
-            // ---- FP32 re-rank of the kept candidates (plane read from global memory: the staging
-            //      area now holds the lists), then the K-1 nearest (ties: lower raster index)
-            if (mine) {
-                if (cnt > BUF) cut_list<CAP>(bd, bp, tid, cnt, BUF);
-                const float *c0 = a.img, *c1 = a.img + HW, *c2 = a.img + 2 * HW;
-                // plane value at region row y, column x (on chip when kept, else from global memory)
-                auto plane = [&](int y, int x) -> float {
-                    if (ListCfg<K>::KEEP_PLANE) return Ps[y * PSW + x];
-                    const size_t o = (size_t)(cy0 + y) * a.W + cx0 + x;
-                    if (a.C == 1) return __ldg(c0 + o);
-                    if (pass == 0) return __ldg(c1 + o);
-                    return (__ldg(c0 + o) + __ldg(c1 + o)) + __ldg(c2 + o);
-                };
-                const int ay = yr - cy0, ax = xr - cx0;
-                float ar[64];
+            // ---- per reference (one warp each): cut back to BUF, FP32 re-rank of the kept
+            //      candidates, the K-1 nearest by (distance, raster index)
+            for (int j = warp; j < NR; j += NT / 32) {
+                if (!rec[j].mine) continue;
+                int n = min(rec[j].cnt, CAP);
+                if (n > BUF) cut_list_warp<CAP>(bd, bp, j, n, BUF, lane, &n);
+                const int pself = rec[j].pself;
+                const int ay = pself / Wc, ax = pself - ay * Wc;
+                constexpr int PER = (BUF + 31) / 32;
+                float dk[PER];
+                int rk[PER];
 #pragma unroll
-                for (int e = 0; e < 64; ++e) ar[e] = plane(ay + (e >> 3), ax + (e & 7));
-                for (int t = 0; t < cnt; ++t) {
-                    const int pq = bp[t * 128 + tid];
-                    const int by = pq / Wc, bx = pq - by * Wc;
-                    bp[t * 128 + tid] = (cy0 + by) * a.W + cx0 + bx;
-                    float d = 0.f;
+                for (int t = 0; t < PER; ++t) {
+                    const int i = t * 32 + lane;
+                    dk[t] = __builtin_huge_valf();
+                    rk[t] = 0x7fffffff;
+                    if (i < n) {
+                        const int pq = bp[j * CAP + i];
+                        const int by = pq / Wc, bx = pq - by * Wc;
+                        float d = 0.f;
+                        for (int u = 0; u < PS; ++u) {
+                            const float *ra = Ps + (ay + u) * PSW + ax, *rb = Ps + (by + u) * PSW + bx;
 #pragma unroll
-                    for (int e = 0; e < 64; ++e) {
-                        const float df = ar[e] - plane(by + (e >> 3), bx + (e & 7));
-                        d = fmaf(df, df, d);
+                            for (int v = 0; v < PS; ++v) {
+                                const float df = ra[v] - rb[v];
+                                d = fmaf(df, df, d);
+                            }
+                        }
+                        dk[t] = d;
+                        rk[t] = (cy0 + by) * a.W + cx0 + bx;
                     }
-                    bd[t * 128 + tid] = d;
                 }
+                const int r = (gy0 + (j >> 3)) * a.nx + gx0 + (j & 7);
                 int32_t *out = a.idx + (size_t)r * K;
-                out[0] = yr * a.W + xr;
-                for (int k = 1; k < K; ++k) {
-                    int best = -1;
-                    float bdv = 0.f;
-                    int bpv = 0;
-                    for (int t = 0; t < cnt; ++t) {
-                        const int pv = bp[t * 128 + tid];
-                        if (pv < 0) continue;
-                        const float dv = bd[t * 128 + tid];
-                        if (best < 0 || dv < bdv || (dv == bdv && pv < bpv)) {
-                            best = t;
-                            bdv = dv;
-                            bpv = pv;
+                const int self = (cy0 + ay) * a.W + cx0 + ax;
+                if (lane == 0) out[0] = self;
+                for (int k = 1; k < K; ++k) {  // K-1 rounds of a warp arg-min on (distance, raster)
+                    float bdv = dk[0];
+                    int brv = rk[0];
+#pragma unroll
+                    for (int t = 1; t < PER; ++t)
+                        if (dk[t] < bdv || (dk[t] == bdv && rk[t] < brv)) {
+                            bdv = dk[t];
+                            brv = rk[t];
+                        }
+#pragma unroll
+                    for (int o = 16; o; o >>= 1) {
+                        const float od = __shfl_xor_sync(FULLM, bdv, o);
+                        const int orr = __shfl_xor_sync(FULLM, brv, o);
+                        if (od < bdv || (od == bdv && orr < brv)) {
+                            bdv = od;
+                            brv = orr;
                         }
                     }
-                    out[k] = best >= 0 ? bpv : out[0];
-                    if (best >= 0) bp[best * 128 + tid] = -1;
+                    if (lane == 0) out[k] = (brv == 0x7fffffff) ? self : brv;
+#pragma unroll
+                    for (int t = 0; t < PER; ++t)
+                        if (rk[t] == brv) {
+                            dk[t] = __builtin_huge_valf();
+                            rk[t] = 0x7fffffff;
+                        }
                 }
             }
             tc_fence_before();
@@ -567,7 +585,7 @@ hts_status launch_tc(const TcArgs &a, cudaStream_t s) {
     const int grid = std::max(1, std::min(a.ntiles, nsm));
     {
         KTimer kt("k_match_tc", s);
-        k_match_tc<K><<<grid, 128, L.total, s>>>(a);
+        k_match_tc<K><<<grid, NT, L.total, s>>>(a);
     }
     return check_launch("k_match_tc");
 }
