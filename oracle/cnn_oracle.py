@@ -1,0 +1,149 @@
+"""FP64 CPU oracle of the learned noise-level map -- TEST INFRASTRUCTURE ONLY.
+
+Only the test-suite and the benchmark may import this module; the CUDA
+library never calls it and shares no code with it.
+
+The network (the learned sigma estimate that replaces Eq. 12-23 in the
+paper's adaptive variant, Sec. III-C) maps the noisy image, scaled by 1/255,
+through five 3x3 convolutions with zero padding (widths C -> 32 -> 32 -> 32
+-> 32 -> 1, ReLU after the first four) to a map of log(sigma) on the [0, 255]
+scale; a reference patch with top-left corner (y, x) reads the map at
+(y + 4, x + 4).  Weights are held in FP16 for the forward pass (the values
+here are the FP16-rounded ones, computed in FP64); training minimises the
+mean squared error of log(sigma) over the reference patches with Adam.
+
+Parameter vector layout (shared with the library's host interface): for
+every layer l, W_l[co][ci][ky][kx] then b_l[co].
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+WIDTH = 32
+DEPTH = 5
+ADAM_B1, ADAM_B2, ADAM_EPS = 0.9, 0.999, 1e-8
+
+
+def layer_shapes(C: int):
+    """[(cout, cin)] of the five layers."""
+    widths = [C] + [WIDTH] * (DEPTH - 1) + [1]
+    return [(widths[i + 1], widths[i]) for i in range(DEPTH)]
+
+
+def num_params(C: int) -> int:
+    return sum(co * ci * 9 + co for co, ci in layer_shapes(C))
+
+
+def unpack(theta: np.ndarray, C: int):
+    """Parameter vector -> [(W (co, ci, 3, 3), b (co,))]."""
+    out, o = [], 0
+    for co, ci in layer_shapes(C):
+        w = theta[o:o + co * ci * 9].reshape(co, ci, 3, 3)
+        o += co * ci * 9
+        b = theta[o:o + co]
+        o += co
+        out.append((w, b))
+    return out
+
+
+def fp16(theta: np.ndarray) -> np.ndarray:
+    return np.asarray(theta, dtype=np.float64).astype(np.float16).astype(np.float64)
+
+
+def conv3x3(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """out[co, y, x] = b[co] + sum_ci sum_ky,kx w[co, ci, ky, kx] * xpad[ci, y + ky, x + kx]."""
+    ci, H, W = x.shape
+    xp = np.zeros((ci, H + 2, W + 2))
+    xp[:, 1:-1, 1:-1] = x
+    out = np.empty((w.shape[0], H, W))
+    for co in range(w.shape[0]):
+        acc = np.full((H, W), float(b[co]))
+        for c in range(ci):
+            for ky in range(3):
+                for kx in range(3):
+                    acc += w[co, c, ky, kx] * xp[c, ky:ky + H, kx:kx + W]
+        out[co] = acc
+    return out
+
+
+def forward(theta: np.ndarray, img: np.ndarray):
+    """Returns (log-sigma map (H, W), cache for backward).  theta: FP16-rounded values."""
+    C = img.shape[0]
+    layers = unpack(theta, C)
+    a = np.asarray(img, dtype=np.float64) / 255.0
+    cache = [a]
+    for li, (w, b) in enumerate(layers):
+        z = conv3x3(a, w, b)
+        a = np.maximum(z, 0.0) if li < DEPTH - 1 else z
+        cache.append(a)
+    return a[0], cache
+
+
+def backward(theta: np.ndarray, cache, dout: np.ndarray) -> np.ndarray:
+    """Gradient of sum(dout * out) with respect to the parameter vector."""
+    C = cache[0].shape[0]
+    layers = unpack(theta, C)
+    grads = []
+    d = dout[None, :, :].astype(np.float64)
+    for li in range(DEPTH - 1, -1, -1):
+        w, b = layers[li]
+        x = cache[li]
+        if li < DEPTH - 1:
+            d = d * (cache[li + 1] > 0)  # ReLU of this layer's output
+        ci, H, W = x.shape
+        xp = np.zeros((ci, H + 2, W + 2))
+        xp[:, 1:-1, 1:-1] = x
+        dw = np.empty_like(w)
+        for co in range(w.shape[0]):
+            for c in range(ci):
+                for ky in range(3):
+                    for kx in range(3):
+                        dw[co, c, ky, kx] = np.sum(d[co] * xp[c, ky:ky + H, kx:kx + W])
+        db = d.sum(axis=(1, 2))
+        grads.append((dw, db))
+        if li > 0:  # gradient of the layer input: correlation with the flipped kernels
+            dp = np.zeros((w.shape[0], H + 2, W + 2))
+            dp[:, 1:-1, 1:-1] = d
+            dx = np.zeros((ci, H, W))
+            for c in range(ci):
+                for co in range(w.shape[0]):
+                    for ky in range(3):
+                        for kx in range(3):
+                            dx[c] += w[co, c, ky, kx] * dp[co, 2 - ky:2 - ky + H, 2 - kx:2 - kx + W]
+            d = dx
+    out = []
+    for dw, db in reversed(grads):
+        out.append(dw.reshape(-1))
+        out.append(db)
+    return np.concatenate(out)
+
+
+def ref_centres(H: int, W: int, ps: int = 8, step: int = 4):
+    """(y + 4, x + 4) of every reference patch, raster order (Alg. 1 grid)."""
+    def grid(n):
+        g = list(range(0, n - ps + 1, step))
+        if g[-1] != n - ps:
+            g.append(n - ps)
+        return g
+    ys, xs = grid(H), grid(W)
+    return np.array([(y + ps // 2, x + ps // 2) for y in ys for x in xs], dtype=np.int64)
+
+
+def loss_and_dout(out: np.ndarray, centres: np.ndarray, target_log_sigma: np.ndarray):
+    """Mean squared error over the reference patches and its gradient map."""
+    pred = out[centres[:, 0], centres[:, 1]]
+    diff = pred - np.asarray(target_log_sigma, dtype=np.float64)
+    n = len(diff)
+    dout = np.zeros_like(out)
+    np.add.at(dout, (centres[:, 0], centres[:, 1]), 2.0 * diff / n)
+    return float(np.mean(diff * diff)), dout
+
+
+def adam_step(theta, m, v, g, t: int, lr: float):
+    """One Adam update (bias-corrected), returns (theta, m, v)."""
+    m = ADAM_B1 * m + (1 - ADAM_B1) * g
+    v = ADAM_B2 * v + (1 - ADAM_B2) * g * g
+    mh = m / (1 - ADAM_B1 ** t)
+    vh = v / (1 - ADAM_B2 ** t)
+    return theta - lr * mh / (np.sqrt(vh) + ADAM_EPS), m, v

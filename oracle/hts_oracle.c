@@ -489,8 +489,26 @@ static void gather_group(const float *img, int H, int W, int C, int ps, int K, c
  * out: C x H x W doubles (plain average of all estimates; not clipped).
  * stats (optional, 3 entries): coefficients kept, groups, max imaginary
  * residue x 1e18 (rounded).  Returns 0, or -1 on bad input. */
+static int denoise_groups_impl(const float *noisy, int H, int W, int C, const htso_params *p, const double *basis,
+                               double tau, const double *taus, const int32_t *idx, double *out, double *stats);
+
 int htso_denoise_groups(const float *noisy, int H, int W, int C, const htso_params *p,
                         const double *basis, double tau, const int32_t *idx, double *out, double *stats)
+{
+    return denoise_groups_impl(noisy, H, W, C, p, basis, tau, NULL, idx, out, stats);
+}
+
+/* The same with a threshold per group (taus[r] for reference r), for a
+ * spatially varying noise level. */
+int htso_denoise_groups_taus(const float *noisy, int H, int W, int C, const htso_params *p,
+                             const double *basis, const double *taus, const int32_t *idx, double *out,
+                             double *stats)
+{
+    return denoise_groups_impl(noisy, H, W, C, p, basis, 0.0, taus, idx, out, stats);
+}
+
+static int denoise_groups_impl(const float *noisy, int H, int W, int C, const htso_params *p, const double *basis,
+                               double tau, const double *taus, const int32_t *idx, double *out, double *stats)
 {
     int ps = p->ps, K = p->K, n = ps * ps, m = C * n;
     int ny = htso_grid(H, ps, p->step, NULL), nx = htso_grid(W, ps, p->step, NULL);
@@ -512,7 +530,7 @@ int htso_denoise_groups(const float *noisy, int H, int W, int C, const htso_para
             double *S = (double *)malloc(sizeof(double) * 2 * (size_t)K * m);
             gather_group(noisy, H, W, C, ps, K, idx + (size_t)r * K, G);
             htso_group_forward(G, K, C, ps, basis, S);            /* Eq. 19 */
-            kept_chunk += htso_threshold(S, (long)K * m, tau);     /* Eq. 20 */
+            kept_chunk += htso_threshold(S, (long)K * m, taus ? taus[r] : tau); /* Eq. 20 */
             double im = htso_group_inverse(S, K, C, ps, basis, est + (size_t)(r - r0) * K * m); /* Eq. 21 */
             if (im > im_chunk) im_chunk = im;
             free(G);

@@ -90,6 +90,8 @@ def _lib():
             lib.htso_threshold.restype = ctypes.c_long
             lib.htso_denoise_groups.argtypes = [P, i, i, i, P, P, d, P, P, P]
             lib.htso_denoise_groups.restype = i
+            lib.htso_denoise_groups_taus.argtypes = [P, i, i, i, P, P, P, P, P, P]
+            lib.htso_denoise_groups_taus.restype = i
             lib.htso_group_lambdas.argtypes = [P, i, i, P]
             lib.htso_group_lambdas.restype = None
             lib.htso_rank_of_hat.argtypes = [P, i]
@@ -348,8 +350,10 @@ def rank_of_hat(lam: np.ndarray) -> int:
     return int(_lib().htso_rank_of_hat(_ptr(lam), lam.shape[0]))
 
 
-def denoise_groups(noisy: np.ndarray, p: Params, basis: np.ndarray, tau_value: float, idx: np.ndarray):
-    """Alg. 1 steps 2-3 for given groups; returns (out CHW float64, stats dict)."""
+def denoise_groups(noisy: np.ndarray, p: Params, basis: np.ndarray, tau_value, idx: np.ndarray):
+    """Alg. 1 steps 2-3 for given groups; returns (out CHW float64, stats dict).
+
+    tau_value: one threshold, or an array with one threshold per reference patch."""
     a = _img(noisy)
     C, H, W = a.shape
     idx = np.ascontiguousarray(idx, dtype=np.int32)
@@ -357,18 +361,27 @@ def denoise_groups(noisy: np.ndarray, p: Params, basis: np.ndarray, tau_value: f
     st = np.zeros(3)
     bf = basis_to_flat(basis)
     ps = p.c_struct()
-    r = _lib().htso_denoise_groups(_ptr(a), H, W, C, ctypes.byref(ps), _ptr(bf), float(tau_value),
-                                   _ptr(idx), _ptr(out), _ptr(st))
+    if np.ndim(tau_value) == 0:
+        r = _lib().htso_denoise_groups(_ptr(a), H, W, C, ctypes.byref(ps), _ptr(bf), float(tau_value),
+                                       _ptr(idx), _ptr(out), _ptr(st))
+    else:
+        taus = np.ascontiguousarray(tau_value, dtype=np.float64).reshape(-1)
+        if taus.shape[0] != idx.shape[0]:
+            raise ValueError("one threshold per reference patch")
+        r = _lib().htso_denoise_groups_taus(_ptr(a), H, W, C, ctypes.byref(ps), _ptr(bf), _ptr(taus),
+                                            _ptr(idx), _ptr(out), _ptr(st))
     if r < 0:
         raise ValueError("bad input")
     return out, {"kept": int(st[0]), "groups": int(st[1]), "max_imag": float(st[2])}
 
 
-def denoise(noisy: np.ndarray, p: Params, sigma: float | None = None, basis: np.ndarray | None = None):
+def denoise(noisy: np.ndarray, p: Params, sigma=None, basis: np.ndarray | None = None):
     """Whole Haar-tSVD: grouping, (basis), (sigma), filtering, aggregation.
 
-    sigma None -> estimated (Eq. 12 floor + Eq. 23 vote); basis None ->
-    globally-learned from the noisy image (Eq. 11).  Returns (out, info).
+    sigma None -> estimated (Eq. 12 floor + Eq. 23 vote); a number -> one
+    noise level; an array with one value per reference patch -> a threshold
+    per group (spatially varying noise).  basis None -> globally-learned from
+    the noisy image (Eq. 11).  Returns (out, info).
     """
     a = _img(noisy)
     C = a.shape[0]
@@ -383,7 +396,10 @@ def denoise(noisy: np.ndarray, p: Params, sigma: float | None = None, basis: np.
         s = estimate_sigma(a, p, eigvals=ev, nref=nref, idx=idx)
         info.update(s)
         sigma = s["sigma_hat"]
-    t = tau(sigma, C, p)
+    if np.ndim(sigma) == 0:
+        t = tau(sigma, C, p)
+    else:
+        t = np.array([tau(float(sv), C, p) for sv in np.asarray(sigma, dtype=np.float64).reshape(-1)])
     out, st = denoise_groups(a, p, basis, t, idx)
     info.update(st)
     info.update({"sigma": sigma, "tau": t, "idx": idx, "green": green, "basis": basis})

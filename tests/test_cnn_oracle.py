@@ -1,0 +1,78 @@
+"""Pins of the learned noise-level map's FP64 oracle (oracle/cnn_oracle.py).
+
+The convolution is pinned to scipy's 2-D correlation, the backward pass to
+central finite differences of the forward pass (every layer, weights and
+biases), the loss gradient to finite differences, and the first Adam step to
+its closed form lr * g / (|g| + eps).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import cnn_oracle as co
+
+scipy_signal = pytest.importorskip("scipy.signal")
+
+
+def test_conv3x3_is_2d_correlation():
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((3, 9, 11))
+    w = rng.standard_normal((4, 3, 3, 3))
+    b = rng.standard_normal(4)
+    got = co.conv3x3(x, w, b)
+    for o in range(4):
+        want = b[o] + sum(scipy_signal.correlate2d(x[c], w[o, c], mode="same", boundary="fill") for c in range(3))
+        np.testing.assert_allclose(got[o], want, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("C", [1, 3])
+def test_backward_matches_finite_differences(C):
+    rng = np.random.default_rng(10 + C)
+    theta = rng.standard_normal(co.num_params(C)) * 0.3
+    img = rng.uniform(0, 255, size=(C, 6, 7))
+    dout = rng.standard_normal((6, 7))
+    out, cache = co.forward(theta, img)
+    g = co.backward(theta, cache, dout)
+    # a sample of parameters from every layer (weights and biases)
+    offs, o = [], 0
+    for cout, cin in co.layer_shapes(C):
+        offs += [o, o + cout * cin * 9 - 1, o + cout * cin * 9 + cout - 1]
+        o += cout * cin * 9 + cout
+    offs += list(rng.choice(co.num_params(C), 20, replace=False))
+    eps = 1e-6
+    for i in offs:
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += eps
+        tm[i] -= eps
+        fp = np.sum(co.forward(tp, img)[0] * dout)
+        fm = np.sum(co.forward(tm, img)[0] * dout)
+        fd = (fp - fm) / (2 * eps)
+        assert abs(fd - g[i]) <= 1e-6 * (1.0 + abs(fd)), (i, fd, g[i])
+
+
+def test_loss_gradient():
+    rng = np.random.default_rng(3)
+    out = rng.standard_normal((20, 24))
+    cen = co.ref_centres(20, 24)
+    tgt = rng.standard_normal(len(cen))
+    L, d = co.loss_and_dout(out, cen, tgt)
+    eps = 1e-7
+    for (y, x) in cen[:5]:
+        op, om = out.copy(), out.copy()
+        op[y, x] += eps
+        om[y, x] -= eps
+        fd = (co.loss_and_dout(op, cen, tgt)[0] - co.loss_and_dout(om, cen, tgt)[0]) / (2 * eps)
+        assert abs(fd - d[y, x]) <= 1e-6
+
+
+def test_first_adam_step_closed_form():
+    g = np.array([0.5, -2.0, 1e-3])
+    th, m, v = co.adam_step(np.zeros(3), np.zeros(3), np.zeros(3), g, 1, 0.01)
+    np.testing.assert_allclose(th, -0.01 * g / (np.abs(g) + co.ADAM_EPS), rtol=1e-12)
+
+
+def test_reference_centres_follow_the_grid():
+    c = co.ref_centres(21, 17)
+    # grid {0, 4, 8, 12, 13} x {0, 4, 8, 9}: centres shifted by 4
+    assert c[0].tolist() == [4, 4] and c[-1].tolist() == [13 + 4, 9 + 4]
+    assert len(c) == 5 * 4

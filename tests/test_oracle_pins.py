@@ -390,3 +390,19 @@ def test_denoise_improves_psnr(oracle):
     p = oracle.Params(K=16, win=21)
     out, info = oracle.denoise(noisy, p, sigma=25.0)
     assert synth.psnr(out, clean) > synth.psnr(noisy, clean) + 7.0
+
+
+def test_per_reference_thresholds_reduce_to_one(oracle):
+    # a threshold per group equal everywhere is the single-threshold filter; a higher threshold on one
+    # group only changes the pixels that group covers
+    _, noisy = synth.make_config_image(40, 48, 1, 20.0, 91)
+    p = oracle.Params(win=11)
+    a, _ = oracle.denoise(noisy, p, sigma=20.0)
+    n = oracle.num_refs(40, 48, p)
+    b, _ = oracle.denoise(noisy, p, sigma=np.full(n, 20.0))
+    np.testing.assert_array_equal(a, b)
+    sig = np.full(n, 20.0)
+    sig[0] = 200.0
+    c, info = oracle.denoise(noisy, p, sigma=sig)
+    changed = np.argwhere(np.abs(c - a) > 0)
+    assert len(changed) > 0
