@@ -204,6 +204,59 @@ typedef struct {
  * geometry has not been tuned in this process. */
 hts_status hts_tuned_tile(int H, int W, int C, const hts_params *p, int *ty, int *tx);
 
+/* ------------------------------------------- spatially varying noise */
+
+/* hts_denoise with a noise level per reference patch: group r is thresholded
+ * at tau_mult * sigma_ref[r] * sqrt(2 ln(c K ps^2)) (Eq. 20 with a local
+ * sigma).  sigma_ref: device float array of N_ref values (hts_num_refs),
+ * raster order of the reference grid.  Asynchronous. */
+hts_status hts_denoise_sigma_map(const float *noisy, float *out, int H, int W, int C, const float *sigma_ref,
+                                 const hts_basis *basis, const hts_params *p, void *stream);
+
+/* Learned noise-level map: the convolutional estimate that the adaptive
+ * variant of the paper (Sec. III-C) uses in place of one global level.  Five
+ * 3x3 convolutions (C -> 32 -> 32 -> 32 -> 32 -> 1, ReLU between, zero
+ * padding) map the image / 255 to log(sigma); reference patch (y, x) reads
+ * the map at (y + 4, x + 4).  FP16 weights, FP32 accumulation, trained by
+ * the library's own kernels (mean squared error of log sigma over the
+ * reference patches, Adam).  A network is not thread-safe. */
+typedef struct hts_cnn hts_cnn;
+int hts_cnn_num_params(int C); /* 0 for C not in {1, 3} */
+int hts_cnn_channels(const hts_cnn *net); /* C of the network, 0 for NULL */
+/* New network for C channels, He-initialised from `seed`; synchronous. */
+hts_status hts_cnn_create(int C, uint64_t seed, hts_cnn **out);
+hts_status hts_cnn_free(hts_cnn *net);
+/* FP32 master parameters, per layer W[co][ci][3][3] then b[co] (host arrays of
+ * hts_cnn_num_params(C) floats); set also resets the optimiser state.  Synchronous. */
+hts_status hts_cnn_get_params(const hts_cnn *net, float *host_params);
+hts_status hts_cnn_set_params(hts_cnn *net, const float *host_params);
+/* Forward pass: log-sigma map (device, H x W) of a device CHW image. */
+hts_status hts_cnn_log_sigma_map(hts_cnn *net, const float *img, int H, int W, float *map_out, void *stream);
+/* sigma at every reference patch (device, N_ref). */
+hts_status hts_cnn_sigma_refs(hts_cnn *net, const float *img, int H, int W, const hts_params *p,
+                              float *sigma_ref, void *stream);
+/* Training: gradients accumulate over images until hts_cnn_zero_grad; the
+ * loss (mean squared error of log sigma against target_log_sigma, device,
+ * N_ref) accumulates until hts_cnn_take_loss (synchronises). */
+hts_status hts_cnn_zero_grad(hts_cnn *net, void *stream);
+hts_status hts_cnn_accumulate_grad(hts_cnn *net, const float *img, int H, int W, const hts_params *p,
+                                   const float *target_log_sigma, void *stream);
+hts_status hts_cnn_take_loss(hts_cnn *net, double *loss_sum, void *stream);
+hts_status hts_cnn_get_grad(const hts_cnn *net, float *host_grad, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the accumulated gradient. */
+hts_status hts_cnn_adam_step(hts_cnn *net, float lr, void *stream);
+/* Parameters to / from a small binary file (magic "HTSCNN1"). */
+hts_status hts_cnn_save(const hts_cnn *net, const char *path);
+hts_status hts_cnn_load(const char *path, hts_cnn **out);
+
+/* Denoising with the learned map checked against the eigenvalue estimate of
+ * hts_estimate_sigma: if the geometric mean of learned / estimated sigma lies
+ * outside [1/fallback_factor, fallback_factor] (or the map is not finite and
+ * positive), every group falls back to the estimate; hts_last_stats reports
+ * which was used and the ratio.  fallback_factor > 1.  Asynchronous. */
+hts_status hts_denoise_learned(const float *noisy, float *out, int H, int W, int C, hts_cnn *net,
+                               const hts_basis *basis, const hts_params *p, double fallback_factor, void *stream);
+
 /* ------------------------------------------------- inspection / tests */
 
 /* Grouping step alone (Eq. 9, Alg. 1 step 1): idx_out (device, int32,
@@ -230,6 +283,8 @@ typedef struct {
     double sigma;          /* noise level used */
     double tau;            /* threshold used */
     int filter_fixed;      /* FP64 decisions that overturned the FP32 one (contribution corrected) */
+    int learned;           /* hts_denoise_learned: 1 = learned noise map used, 0 = fell back */
+    double learned_ratio;  /* hts_denoise_learned: geometric mean of learned / estimated sigma */
 } hts_stats;
 hts_status hts_last_stats(hts_stats *out, void *stream);
 

@@ -151,8 +151,9 @@ struct Workspace : Bufs {
     cudaStream_t stream = nullptr;
     size_t cap_idx = 0, cap_fb = 0, cap_redo = 0, cap_green = 0, cap_hw = 0, cap_chw = 0, cap_cov = 0;
     size_t cap_x = 0, cap_xskip = 0;
-    size_t cap_in = 0, cap_out = 0;
+    size_t cap_in = 0, cap_out = 0, cap_sref = 0;
     float *io_in = nullptr, *io_out = nullptr;
+    float *sref = nullptr;  // learned noise level per reference patch
 };
 
 static std::mutex g_mu;
@@ -333,13 +334,14 @@ hts_status launch_grouping(const float *img, const Geom &g, const hts_params &p,
 }
 
 hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
-                       const hts_params &p, const Bufs &b, cudaStream_t s) {
+                       const hts_params &p, const Bufs &b, cudaStream_t s, float *sigma_ref, double fallback_factor) {
     const Bufs *w = &b;
     const size_t hw = (size_t)g.H * g.W;
     HTS_TRY(cuda_ok(cudaMemsetAsync(w->st, 0, sizeof(DevState), s), "cudaMemsetAsync(state)"));
     HTS_TRY(cuda_ok(cudaMemsetAsync(w->acc, 0, hw * g.C * sizeof(long long), s), "cudaMemsetAsync(acc)"));
     HTS_TRY(cuda_ok(cudaMemsetAsync(w->wcount, 0, hw * sizeof(int), s), "cudaMemsetAsync(weights)"));
-    const bool need_sigma = sigma < 0;
+    // a noise map without a check needs no estimate; a checked map is compared with the estimate
+    const bool need_sigma = sigma < 0 && (sigma_ref == nullptr || fallback_factor > 0);
     const bool est = (basis == nullptr) || (need_sigma && !basis->has_eig);
     const double *b64 = basis ? basis->b64 : w->b64;
     const float *b32 = basis ? basis->b32 : w->b32;
@@ -356,9 +358,10 @@ hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigm
     if (need_sigma && p.adjust_rank) HTS_TRY(launch_sigma_vote(noisy, g, p, w->idx, w->redo, w->st, s));
     if (fork) HTS_TRY(cuda_ok(cudaStreamWaitEvent(s, w->ev_join, 0), "cudaStreamWaitEvent"));
     if (need_sigma) HTS_TRY(launch_sigma_final(g, p, w->st, s));
-    else HTS_TRY(launch_set_sigma((double)sigma, g, p, w->st, s));
+    else HTS_TRY(launch_set_sigma(sigma > 0 ? (double)sigma : 0.0, g, p, w->st, s));
+    if (sigma_ref && fallback_factor > 0) HTS_TRY(launch_learned_check(sigma_ref, g.nref, fallback_factor, w->st, s));
     return launch_filter(noisy, g, w->idx, b64, b32, w->acc, w->wcount, w->redo, w->xlist, w->xskip, w->st, out,
-                         p.precision == 0 ? 1 : 0, s);
+                         p.precision == 0 ? 1 : 0, sigma_ref, tau_scale(g, p), s);
 }
 
 static hts_status denoise_impl(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
@@ -619,6 +622,39 @@ hts_status hts_denoise_host(const float *noisy_host, float *out_host, int H, int
     return cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize");
 }
 
+hts_status hts_denoise_sigma_map(const float *noisy, float *out, int H, int W, int C, const float *sigma_ref,
+                                 const hts_basis *basis, const hts_params *p, void *stream) {
+    Geom g;
+    HTS_TRY(validate(H, W, C, p, &g));
+    if (!noisy || !out || !sigma_ref) return fail(HTS_EINVAL, "NULL pointer");
+    if (noisy == out) return fail(HTS_EINVAL, "out may not alias noisy");
+    HTS_TRY(check_basis(basis, C));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace *w;
+    HTS_TRY(get_ws(s, &w));
+    HTS_TRY(ensure(w, g));
+    return denoise_run(noisy, out, g, -1.f, basis, *p, *w, s, const_cast<float *>(sigma_ref), 0.0);
+}
+
+hts_status hts_denoise_learned(const float *noisy, float *out, int H, int W, int C, hts_cnn *net,
+                               const hts_basis *basis, const hts_params *p, double fallback_factor, void *stream) {
+    Geom g;
+    HTS_TRY(validate(H, W, C, p, &g));
+    if (!noisy || !out || !net) return fail(HTS_EINVAL, "NULL pointer");
+    if (noisy == out) return fail(HTS_EINVAL, "out may not alias noisy");
+    if (!(fallback_factor > 1.0) || !std::isfinite(fallback_factor))
+        return fail(HTS_EINVAL, "fallback_factor must be > 1");
+    if (hts_cnn_channels(net) != C) return fail(HTS_EINVAL, "network built for another channel count");
+    HTS_TRY(check_basis(basis, C));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace *w;
+    HTS_TRY(get_ws(s, &w));
+    HTS_TRY(ensure(w, g));
+    HTS_TRY(grow(w->sref, w->cap_sref, (size_t)g.nref, "cudaMalloc(sigma map)"));
+    HTS_TRY(cnn_sigma_refs(net, noisy, g, w->sref, s));
+    return denoise_run(noisy, out, g, -1.f, basis, *p, *w, s, w->sref, fallback_factor);
+}
+
 hts_status hts_last_stats(hts_stats *out, void *stream) {
     if (!out) return fail(HTS_EINVAL, "NULL pointer");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -636,6 +672,8 @@ hts_status hts_last_stats(hts_stats *out, void *stream) {
     out->sigma = hs.sigma_hat;
     out->tau = hs.tau;
     out->filter_fixed = hs.filter_fixed;
+    out->learned = hs.learned;
+    out->learned_ratio = hs.learned_ratio;
     return HTS_OK;
 }
 
@@ -711,6 +749,7 @@ hts_status hts_shutdown(void) {
         cudaFree(w->st);
         cudaFree(w->io_in);
         cudaFree(w->io_out);
+        cudaFree(w->sref);
         if (w->ev_fork) cudaEventDestroy(w->ev_fork);
         if (w->ev_join) cudaEventDestroy(w->ev_join);
         if (w->aux) cudaStreamDestroy(w->aux);

@@ -62,6 +62,8 @@ struct FilterArgs {
     int4 *xlist;  // in-band coefficients: (group, keep<<16 | row<<8 | stream, re, im)
     int xcap;
     int exact;       // 0: FP32 threshold decisions only (precision form)
+    const float *sigma_ref;  // [N_ref] noise level per group (nullptr: the call's one level)
+    double tau_scale;        // tau = tau_scale * sigma
     uint8_t *xskip;  // [N_ref] 1 = group went to the exact pass
     DevState *st;
 };
@@ -314,6 +316,16 @@ __device__ __forceinline__ double haar_entry(int K, int h, int k) {
 
 // --------------------------------------------------- threshold decision
 
+// Threshold of group r: tau_scale * sigma_r in FP64 when the noise level is
+// given per group, else the call's threshold; the FP32 copy is the FP64 one
+// rounded, so every pass decides against the same value.
+__device__ __forceinline__ double group_tau64(const FilterArgs &a, int r) {
+    return a.sigma_ref ? a.tau_scale * (double)a.sigma_ref[r] : a.st->tau;
+}
+__device__ __forceinline__ float group_tau32(const FilterArgs &a, int r) {
+    return a.sigma_ref ? (float)(a.tau_scale * (double)a.sigma_ref[r]) : a.st->tau32;
+}
+
 // 0 = drop, 1 = keep, 2 = undecided in FP32 (inside the guard band).
 __device__ __forceinline__ int decide(float mag, float tau, float band) {
     if (tau <= 0.f) return 1;
@@ -444,8 +456,6 @@ __global__ void __launch_bounds__(64) k_filter_exact(FilterArgs a) {
     load_basis<C>(sb, a.b32);
     __syncthreads();
 
-    const float tau = a.st->tau32;
-    const double tau64 = a.st->tau;
     const int k = lane;
     const bool active = lane < K;
     const size_t HW = (size_t)a.H * a.W;
@@ -453,6 +463,8 @@ __global__ void __launch_bounds__(64) k_filter_exact(FilterArgs a) {
 
     for (int wu = blockIdx.x * NWARPS + warp; wu < nunits; wu += gridDim.x * NWARPS) {
         const int r = a.redo[wu];
+        const float tau = group_tau32(a, r);
+        const double tau64 = group_tau64(a, r);
         const int32_t *grp = a.idx + (size_t)r * K;
         int py = 0, px = 0;
         float ss = 0.f;
@@ -779,7 +791,6 @@ __global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t
     __syncthreads();
     load_rbasis<C>(rb, sb);
     __syncthreads();
-    const float tau = a.st->tau32;
     const size_t HW = (size_t)a.H * a.W;
     const int gpt = t.ty * t.tx;
     const int nbatch = (gpt + GPB - 1) / GPB;
@@ -802,6 +813,7 @@ __global__ void __launch_bounds__(TPB, 1) k_filter_tile(FilterArgs a, TileArgs t
             const int gy = gy0 + lg / t.tx, gx = gx0 + lg % t.tx;
             const bool valid = (lg < gpt) && gy <= gy1 && gx <= gx1;
             const int r = valid ? gy * a.nx + gx : 0;
+            const float tau = group_tau32(a, r);  // this thread's group
             int py = 0, px = 0;
             float ss = 0.f;
             if (tg == 0) {
@@ -1318,7 +1330,6 @@ __global__ void __launch_bounds__(128) k_filter_fix(FilterArgs a) {
     __shared__ int dec;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = min(*(volatile int *)&a.st->xcount, a.xcap);
-    const double tau64 = a.st->tau;
     const size_t HW = (size_t)a.H * a.W;
     for (int f = blockIdx.x; f < n; f += gridDim.x) {
         const int4 e = a.xlist[f];
@@ -1353,7 +1364,7 @@ __global__ void __launch_bounds__(128) k_filter_fix(FilterArgs a) {
         if (tid == 0) {
             const double re = (red[0][0] + red[0][1]) + (red[0][2] + red[0][3]);
             const double im = (red[1][0] + red[1][1]) + (red[1][2] + red[1][3]);
-            const int keep64 = (((j == 0) ? fabs(re) : sqrt(re * re + im * im)) >= tau64) ? 1 : 0;
+            const int keep64 = (((j == 0) ? fabs(re) : sqrt(re * re + im * im)) >= group_tau64(a, r)) ? 1 : 0;
             atomicAdd(&a.st->filter_exact, 1);
             if (keep64 != keep32) atomicAdd(&a.st->filter_fixed, 1);
             dec = keep64;
@@ -1552,7 +1563,8 @@ void set_tuned_tile(const Geom &g, TileChoice c) {
 
 hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, const double *b64, const float *b32,
                          long long *acc, int *wcount, int32_t *redo_list, int4 *xlist, uint8_t *xskip,
-                         DevState *st, float *out, int exact, cudaStream_t s) {
+                         DevState *st, float *out, int exact, const float *sigma_ref, double tau_scale,
+                         cudaStream_t s) {
     FilterArgs a;
     a.img = img;
     a.H = g.H;
@@ -1571,6 +1583,8 @@ hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, co
     a.xlist = xlist;
     a.xcap = XLIST_PER_REF * g.nref;
     a.exact = exact;
+    a.sigma_ref = sigma_ref;
+    a.tau_scale = tau_scale;
     a.xskip = xskip;
     a.st = st;
 #define HTS_FILTER_CASE(CC, KK) \

@@ -293,9 +293,6 @@ __global__ void k_set_sigma(DevState *st, double sigma, int nref, double tau_sca
     st->nref = nref;
 }
 
-double tau_scale(const Geom &g, const hts_params &p) {
-    return p.tau_mult * sqrt(2.0 * log((double)g.C * g.K * PS * PS));
-}
 
 template <int C, int K>
 hts_status launch_vote(const float *img, const Geom &g, const int32_t *idx, double gamma_rank, int32_t *list,
@@ -315,6 +312,10 @@ hts_status launch_vote(const float *img, const Geom &g, const int32_t *idx, doub
 }
 
 }  // namespace
+
+double tau_scale(const Geom &g, const hts_params &p) {
+    return p.tau_mult * sqrt(2.0 * log((double)g.C * g.K * PS * PS));
+}
 
 hts_status launch_sigma_floor(const Geom &g, const hts_params &p, const double *eig, DevState *st, cudaStream_t s) {
     const int ns = g.C / 2 + 1;

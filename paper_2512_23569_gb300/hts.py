@@ -29,6 +29,10 @@ EXPORTS = [
     "hts_denoise_batch", "hts_match", "hts_num_refs", "hts_last_stats", "hts_last_error",
     "hts_launch_count", "hts_version", "hts_shutdown", "hts_profile_begin", "hts_profile_end",
     "hts_denoise_noalloc", "hts_last_batch_stats", "hts_tuned_tile",
+    "hts_denoise_sigma_map", "hts_denoise_learned", "hts_cnn_num_params", "hts_cnn_channels", "hts_cnn_create",
+    "hts_cnn_free", "hts_cnn_get_params", "hts_cnn_set_params", "hts_cnn_log_sigma_map", "hts_cnn_sigma_refs",
+    "hts_cnn_zero_grad", "hts_cnn_accumulate_grad", "hts_cnn_take_loss", "hts_cnn_get_grad", "hts_cnn_adam_step",
+    "hts_cnn_save", "hts_cnn_load",
 ]
 
 
@@ -55,7 +59,8 @@ class SigmaInfo(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("nref", ctypes.c_int), ("match_reranked", ctypes.c_int), ("match_fallback", ctypes.c_int),
                 ("filter_redo", ctypes.c_int), ("filter_exact", ctypes.c_int), ("vote_uncertain", ctypes.c_int),
-                ("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("filter_fixed", ctypes.c_int)]
+                ("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("filter_fixed", ctypes.c_int),
+                ("learned", ctypes.c_int), ("learned_ratio", ctypes.c_double)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -105,6 +110,25 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.hts_launch_count.restype = ctypes.c_uint64
         lib.hts_version.restype = ctypes.c_char_p
         lib.hts_profile_end.argtypes = [ctypes.POINTER(KernelTime), I, ctypes.POINTER(I)]
+        lib.hts_denoise_sigma_map.argtypes = [P, P, I, I, I, P, P, PP, P]
+        lib.hts_denoise_learned.argtypes = [P, P, I, I, I, P, P, PP, D, P]
+        lib.hts_cnn_num_params.argtypes = [I]
+        lib.hts_cnn_num_params.restype = I
+        lib.hts_cnn_channels.argtypes = [P]
+        lib.hts_cnn_channels.restype = I
+        lib.hts_cnn_create.argtypes = [I, ctypes.c_uint64, ctypes.POINTER(P)]
+        lib.hts_cnn_free.argtypes = [P]
+        lib.hts_cnn_get_params.argtypes = [P, P]
+        lib.hts_cnn_set_params.argtypes = [P, P]
+        lib.hts_cnn_log_sigma_map.argtypes = [P, P, I, I, P, P]
+        lib.hts_cnn_sigma_refs.argtypes = [P, P, I, I, PP, P, P]
+        lib.hts_cnn_zero_grad.argtypes = [P, P]
+        lib.hts_cnn_accumulate_grad.argtypes = [P, P, I, I, PP, P, P]
+        lib.hts_cnn_take_loss.argtypes = [P, ctypes.POINTER(D), P]
+        lib.hts_cnn_get_grad.argtypes = [P, P, P]
+        lib.hts_cnn_adam_step.argtypes = [P, F, P]
+        lib.hts_cnn_save.argtypes = [P, ctypes.c_char_p]
+        lib.hts_cnn_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(P)]
         for name in EXPORTS:  # fail loudly on a library that lacks a declared entry point
             getattr(lib, name)
         _LIB = lib
@@ -275,6 +299,142 @@ def denoise_noalloc(noisy, sigma: float | None = None, basis: Basis | None = Non
     s = -1.0 if sigma is None else float(sigma)
     _check(load().hts_denoise_noalloc(ctypes.c_void_p(noisy.data_ptr()), ctypes.c_void_p(out.data_ptr()), H, W, C,
                                       s, basis.handle if basis else None, ctypes.byref(p), _stream(stream)))
+    return out
+
+
+def denoise_sigma_map(noisy, sigma_ref, basis: Basis | None = None, p: Params | None = None, out=None,
+                      stream=None):
+    """hts_denoise_sigma_map: one noise level per reference patch (CUDA float32 tensor of N_ref)."""
+    import torch
+
+    noisy = _chw(noisy)
+    p = p or params()
+    C, H, W = noisy.shape
+    if not isinstance(sigma_ref, torch.Tensor) or not sigma_ref.is_cuda or sigma_ref.dtype != torch.float32:
+        raise TypeError("sigma_ref: expected a CUDA float32 tensor")
+    if sigma_ref.numel() != num_refs(H, W, p) or not sigma_ref.is_contiguous():
+        raise ValueError("sigma_ref: expected a contiguous tensor of N_ref values")
+    if out is None:
+        out = torch.empty_like(noisy)
+    _check(load().hts_denoise_sigma_map(ctypes.c_void_p(noisy.data_ptr()), ctypes.c_void_p(out.data_ptr()), H, W, C,
+                                        ctypes.c_void_p(sigma_ref.data_ptr()), basis.handle if basis else None,
+                                        ctypes.byref(p), _stream(stream)))
+    return out
+
+
+class Cnn:
+    """Owns an hts_cnn* (learned noise-level map: five 3x3 convolutions, output log sigma)."""
+
+    def __init__(self, C: int = 1, seed: int = 1, handle: ctypes.c_void_p | None = None):
+        lib = load()
+        if handle is None:
+            handle = ctypes.c_void_p()
+            _check(lib.hts_cnn_create(C, seed, ctypes.byref(handle)))
+        self._h = handle
+        self.C = int(lib.hts_cnn_channels(self._h))
+        self.nparams = int(lib.hts_cnn_num_params(self.C))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.nparams, dtype=np.float32)
+        _check(load().hts_cnn_get_params(self._h, ctypes.c_void_p(a.ctypes.data)))
+        return a
+
+    def set_params(self, theta) -> None:
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        if a.size != self.nparams:
+            raise ValueError("expected %d parameters" % self.nparams)
+        _check(load().hts_cnn_set_params(self._h, ctypes.c_void_p(a.ctypes.data)))
+
+    def log_sigma_map(self, img, stream=None):
+        """Full-resolution log(sigma) map (H, W) of a CUDA CHW image."""
+        import torch
+
+        img = _chw(img)
+        C, H, W = img.shape
+        out = torch.empty((H, W), dtype=torch.float32, device=img.device)
+        _check(load().hts_cnn_log_sigma_map(self._h, ctypes.c_void_p(img.data_ptr()), H, W,
+                                            ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def sigma_refs(self, img, p: Params | None = None, stream=None):
+        """sigma of every reference patch (N_ref,)."""
+        import torch
+
+        img = _chw(img)
+        p = p or params()
+        C, H, W = img.shape
+        out = torch.empty((num_refs(H, W, p),), dtype=torch.float32, device=img.device)
+        _check(load().hts_cnn_sigma_refs(self._h, ctypes.c_void_p(img.data_ptr()), H, W, ctypes.byref(p),
+                                         ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def zero_grad(self, stream=None) -> None:
+        _check(load().hts_cnn_zero_grad(self._h, _stream(stream)))
+
+    def accumulate_grad(self, img, target_log_sigma, p: Params | None = None, stream=None) -> None:
+        """Adds the gradient of the mean squared log-sigma error over the reference patches."""
+        import torch
+
+        img = _chw(img)
+        p = p or params()
+        C, H, W = img.shape
+        t = target_log_sigma
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+            raise TypeError("target: expected a contiguous CUDA float32 tensor")
+        if t.numel() != num_refs(H, W, p):
+            raise ValueError("target: expected N_ref values")
+        _check(load().hts_cnn_accumulate_grad(self._h, ctypes.c_void_p(img.data_ptr()), H, W, ctypes.byref(p),
+                                              ctypes.c_void_p(t.data_ptr()), _stream(stream)))
+
+    def take_loss(self, stream=None) -> float:
+        """Sum of the per-image losses accumulated since the last call (synchronises; resets it)."""
+        v = ctypes.c_double()
+        _check(load().hts_cnn_take_loss(self._h, ctypes.byref(v), _stream(stream)))
+        return v.value
+
+    def get_grad(self, stream=None) -> np.ndarray:
+        a = np.empty(self.nparams, dtype=np.float32)
+        _check(load().hts_cnn_get_grad(self._h, ctypes.c_void_p(a.ctypes.data), _stream(stream)))
+        return a
+
+    def adam_step(self, lr: float, stream=None) -> None:
+        _check(load().hts_cnn_adam_step(self._h, float(lr), _stream(stream)))
+
+    def save(self, path: str) -> None:
+        _check(load().hts_cnn_save(self._h, path.encode()))
+
+    @staticmethod
+    def load_file(path: str) -> "Cnn":
+        h = ctypes.c_void_p()
+        _check(load().hts_cnn_load(path.encode(), ctypes.byref(h)))
+        return Cnn(handle=h)
+
+    def __del__(self):
+        try:
+            if self._h and _LIB is not None:
+                _LIB.hts_cnn_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+def denoise_learned(noisy, net: Cnn, p: Params | None = None, basis: Basis | None = None,
+                    fallback_factor: float = 2.0, out=None, stream=None):
+    """hts_denoise_learned: noise level of each reference patch from the network, checked against the estimate."""
+    import torch
+
+    noisy = _chw(noisy)
+    p = p or params()
+    C, H, W = noisy.shape
+    if out is None:
+        out = torch.empty_like(noisy)
+    _check(load().hts_denoise_learned(ctypes.c_void_p(noisy.data_ptr()), ctypes.c_void_p(out.data_ptr()), H, W, C,
+                                      net.handle, basis.handle if basis else None, ctypes.byref(p),
+                                      float(fallback_factor), _stream(stream)))
     return out
 
 

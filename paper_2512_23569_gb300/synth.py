@@ -32,6 +32,9 @@ __all__ = [
     "correlate_noise",
     "make_config_image",
     "psnr",
+    "make_pg_correlated_image",
+    "make_varying_noise_image",
+    "ref_log_sigma",
 ]
 
 
@@ -159,3 +162,44 @@ def make_pg_correlated_image(H: int, W: int, C: int, seed: int, a: float = 0.01,
     clean = clean_image(H, W, C, seed)
     noisy = correlate_noise(clean, poisson_gaussian(clean, a, sigma_b, seed + 1), std)
     return clean, noisy
+
+
+def make_varying_noise_image(H: int, W: int, C: int, seed: int, a_max: float = 0.02, sb_max: float = 30.0,
+                             sb_min: float = 0.0):
+    """(clean, noisy, sigma_px): Poisson-Gaussian noise whose read-noise level varies across the image.
+
+    Gain a ~ U[0, a_max]; sigma_b ramps linearly between two levels drawn from
+    U[sb_min, sb_max] along a random direction (both drawn from seed + 1's
+    generator, before the noise itself); noise seed = seed + 2.  sigma_px
+    (H, W) is the true per-pixel standard deviation, the root mean over
+    channels of a * clean + sigma_b^2.
+    """
+    clean = clean_image(H, W, C, seed)
+    rng = _rng(seed + 1)
+    a = float(rng.uniform(0.0, a_max))
+    s0, s1 = rng.uniform(sb_min, sb_max, size=2)
+    th = rng.uniform(0.0, 2.0 * np.pi)
+    yy, xx = np.meshgrid(np.arange(H, dtype=np.float64), np.arange(W, dtype=np.float64), indexing="ij")
+    proj = np.cos(th) * yy + np.sin(th) * xx
+    t = (proj - proj.min()) / max(proj.max() - proj.min(), 1e-12)
+    sb = s0 + (s1 - s0) * t
+    noisy = poisson_gaussian(clean, a, sb[None], seed + 2)
+    var = a * clean.astype(np.float64) + sb[None] ** 2
+    sigma_px = np.sqrt(var.mean(axis=0))
+    return clean, noisy, sigma_px
+
+
+def ref_log_sigma(sigma_px: np.ndarray, ps: int = 8, step: int = 4) -> np.ndarray:
+    """log of the RMS noise level over every reference patch (row-major over the reference grid:
+    0, step, 2 step, ... plus the last position n - ps), float32."""
+    H, W = sigma_px.shape
+
+    def grid(n):
+        g = list(range(0, n - ps + 1, step))
+        if g[-1] != n - ps:
+            g.append(n - ps)
+        return g
+
+    v = sigma_px.astype(np.float64) ** 2
+    out = [np.log(np.sqrt(v[y:y + ps, x:x + ps].mean())) for y in grid(H) for x in grid(W)]
+    return np.asarray(out, dtype=np.float32)

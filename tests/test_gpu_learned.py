@@ -1,0 +1,168 @@
+"""Spatially varying noise: per-reference thresholds and the learned noise-level map.
+
+* hts_denoise_sigma_map with one sigma per reference patch against the FP64
+  oracle fed the same sigmas (same tolerances as the global-sigma parity);
+* the network's forward map, loss, gradient and Adam step against the FP64
+  oracle of cnn_oracle.py, from the same (FP16-rounded) parameters;
+* training on images whose noise level varies across the frame brings the
+  map closer to the true level than one global estimate, and denoising with it
+  beats one global sigma;
+* a map far from the estimate falls back to the estimate.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2512_23569_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hts():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2512_23569_gb300 import build, hts as h
+
+    build.build()
+    h.load()
+    return h
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("H,W,C,seed", [(64, 72, 1, 41), (64, 56, 3, 42), (45, 61, 3, 43)])
+def test_sigma_map_matches_oracle(oracle, hts, H, W, C, seed):
+    p = hts.params(win=11)
+    po = oracle.Params(win=11)
+    clean, noisy = synth.make_config_image(H, W, C, 20.0, seed)
+    n = hts.num_refs(H, W, p)
+    smap = np.random.default_rng(seed).uniform(8.0, 40.0, size=n).astype(np.float32)
+    got = hts.denoise_sigma_map(_dev(noisy), _dev(smap), p=p).cpu().numpy().astype(np.float64)
+    want, _ = oracle.denoise(noisy, po, sigma=smap.astype(np.float64))
+    assert np.max(np.abs(got - want)) <= 1e-3
+    assert abs(synth.psnr(got, clean) - synth.psnr(want, clean)) <= 0.01
+    # a constant map is the global-sigma call, bit for bit
+    const = hts.denoise_sigma_map(_dev(noisy), _dev(np.full(n, 20.0, np.float32)), p=p).cpu().numpy()
+    np.testing.assert_array_equal(const, hts.denoise(_dev(noisy), sigma=20.0, p=p).cpu().numpy())
+
+
+def _layer_slices(co, C):
+    out, o = [], 0
+    for cout, cin in co.layer_shapes(C):
+        out.append(slice(o, o + cout * cin * 9))
+        out.append(slice(o + cout * cin * 9, o + cout * cin * 9 + cout))
+        o += cout * cin * 9 + cout
+    return out
+
+
+@pytest.mark.parametrize("C", [1, 3])
+def test_network_matches_oracle(hts, C):
+    from oracle import cnn_oracle as co
+
+    H, W = 24, 28
+    p = hts.params()
+    net = hts.Cnn(C, seed=5)
+    rng = np.random.default_rng(100 + C)
+    theta = (rng.standard_normal(co.num_params(C)) * 0.2).astype(np.float32)
+    net.set_params(theta)
+    np.testing.assert_array_equal(net.get_params(), theta)
+    img = rng.uniform(0, 255, size=(C, H, W)).astype(np.float32)
+    th16 = co.fp16(theta)
+    out, cache = co.forward(th16, img)
+    got = net.log_sigma_map(_dev(img)).cpu().numpy()
+    assert np.max(np.abs(got - out)) <= 1e-4 * (1.0 + np.max(np.abs(out)))
+    # sigma of every reference = exp(map at its centre)
+    cen = co.ref_centres(H, W)
+    np.testing.assert_allclose(net.sigma_refs(_dev(img), p).cpu().numpy(), np.exp(got[cen[:, 0], cen[:, 1]]),
+                               rtol=1e-6)
+    # loss and gradient
+    tgt = rng.uniform(1.0, 3.5, size=len(cen)).astype(np.float32)
+    L, dout = co.loss_and_dout(out, cen, tgt)
+    g = co.backward(th16, cache, dout)
+    net.zero_grad()
+    net.accumulate_grad(_dev(img), _dev(tgt), p)
+    assert net.take_loss() == pytest.approx(L, rel=1e-4)
+    gg = net.get_grad()
+    for sl in _layer_slices(co, C):
+        ref = g[sl]
+        assert np.linalg.norm(gg[sl] - ref) <= 1e-3 * np.linalg.norm(ref) + 1e-9
+    # Adam from the library's own gradient (first step: closed form of the oracle)
+    net.adam_step(1e-2)
+    want, _, _ = co.adam_step(theta.astype(np.float64), 0.0, 0.0, gg.astype(np.float64), 1, 1e-2)
+    np.testing.assert_allclose(net.get_params(), want, rtol=1e-5, atol=1e-7)
+
+
+def _train_set(n, size, seed):
+    out = []
+    for i in range(n):
+        clean, noisy, spx = synth.make_varying_noise_image(size, size, 1, seed + 7 * i, sb_min=2.0)
+        out.append((clean, noisy, spx))
+    return out
+
+
+def _train(hts, net, data, p, steps, batch, lr0):
+    xs = [_dev(n) for _, n, _ in data]
+    ts = [_dev(synth.ref_log_sigma(s)) for _, _, s in data]
+    rng = np.random.default_rng(0)
+    hist = []
+    for it in range(steps):
+        lr = lr0 * (0.1 ** (it / steps))  # exponential decay to lr0 / 10
+        net.zero_grad()
+        pick = rng.choice(len(xs), batch, replace=False)
+        for i in pick:
+            net.accumulate_grad(xs[i], ts[i], p)
+        net.adam_step(lr / batch)
+        if it % 50 == 49:
+            hist.append(net.take_loss() / (50 * batch))
+    return hist
+
+
+def test_training_beats_one_global_sigma(hts):
+    p = hts.params(win=15)
+    net = hts.Cnn(1, seed=3)
+    hist = _train(hts, net, _train_set(48, 96, 1000), p, steps=600, batch=8, lr0=2e-3)
+    assert hist[-1] < 0.5 * hist[0], hist
+    gains, err_l, err_g = [], [], []
+    for clean, noisy, spx in _train_set(3, 160, 9000):
+        x = _dev(noisy)
+        truth = synth.ref_log_sigma(spx)
+        est, _ = hts.estimate_sigma(x, p)
+        lmap = np.log(net.sigma_refs(x, p).cpu().numpy())
+        err_l.append(np.sqrt(np.mean((lmap - truth) ** 2)))
+        err_g.append(np.sqrt(np.mean((np.log(est) - truth) ** 2)))
+        a = hts.denoise_learned(x, net, p, fallback_factor=4.0).cpu().numpy()
+        assert hts.last_stats()["learned"] == 1
+        b = hts.denoise(x, p=p).cpu().numpy()
+        gains.append(synth.psnr(a, clean) - synth.psnr(b, clean))
+    assert np.mean(err_l) < np.mean(err_g), (err_l, err_g)
+    assert np.mean(gains) > 0.0, gains
+
+
+def test_far_map_falls_back_to_the_estimate(hts):
+    from oracle import cnn_oracle as co
+
+    p = hts.params(win=11)
+    net = hts.Cnn(1, seed=2)
+    theta = net.get_params()
+    theta[-1] = 9.0  # output bias: sigma ~ e^9, far from any estimate
+    net.set_params(theta)
+    clean, noisy = synth.make_config_image(64, 64, 1, 20.0, 77)
+    x = _dev(noisy)
+    got = hts.denoise_learned(x, net, p, fallback_factor=2.0).cpu().numpy()
+    st = hts.last_stats()
+    assert st["learned"] == 0 and st["learned_ratio"] > 2.0
+    want = hts.denoise(x, p=p).cpu().numpy()
+    assert np.max(np.abs(got - want)) <= 1e-3
+    assert co.num_params(1) == net.nparams
+
+
+def test_network_save_load_roundtrip(hts, tmp_path):
+    net = hts.Cnn(3, seed=11)
+    path = str(tmp_path / "net.bin")
+    net.save(path)
+    back = hts.Cnn.load_file(path)
+    assert back.C == 3
+    np.testing.assert_array_equal(back.get_params(), net.get_params())
