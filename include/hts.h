@@ -216,10 +216,15 @@ hts_status hts_denoise_sigma_map(const float *noisy, float *out, int H, int W, i
 /* Learned noise-level map: the convolutional estimate that the adaptive
  * variant of the paper (Sec. III-C) uses in place of one global level.  Five
  * 3x3 convolutions (C -> 32 -> 32 -> 32 -> 32 -> 1, ReLU between, zero
- * padding) map the image / 255 to log(sigma); reference patch (y, x) reads
- * the map at (y + 4, x + 4).  FP16 weights, FP32 accumulation, trained by
- * the library's own kernels (mean squared error of log sigma over the
- * reference patches, Adam).  A network is not thread-safe. */
+ * padding) map the image / 255 to a dense log(sigma) map.  Training reads
+ * the map at the centre (y + 4, x + 4) of reference patch (y, x); denoising
+ * gives the patch exp(mean of the map over the window of S x S pixels
+ * starting S/2 rows and columns before that centre, cut to the image) --
+ * the paper estimates one level per sub-image, the window is that sub-image
+ * moved with the patch (S = 128 by default, S = 1 is the centre alone).
+ * FP16 weights, FP32 accumulation, trained by the library's own kernels
+ * (mean squared error of log sigma over the reference patches, Adam).  A
+ * network is not thread-safe. */
 typedef struct hts_cnn hts_cnn;
 int hts_cnn_num_params(int C); /* 0 for C not in {1, 3} */
 int hts_cnn_channels(const hts_cnn *net); /* C of the network, 0 for NULL */
@@ -232,7 +237,10 @@ hts_status hts_cnn_get_params(const hts_cnn *net, float *host_params);
 hts_status hts_cnn_set_params(hts_cnn *net, const float *host_params);
 /* Forward pass: log-sigma map (device, H x W) of a device CHW image. */
 hts_status hts_cnn_log_sigma_map(hts_cnn *net, const float *img, int H, int W, float *map_out, void *stream);
-/* sigma at every reference patch (device, N_ref). */
+/* Readout window S (1 <= S <= 4096) of hts_cnn_sigma_refs / hts_denoise_learned. */
+hts_status hts_cnn_set_window(hts_cnn *net, int S);
+int hts_cnn_window(const hts_cnn *net); /* 0 for NULL */
+/* sigma at every reference patch through the readout window (device, N_ref). */
 hts_status hts_cnn_sigma_refs(hts_cnn *net, const float *img, int H, int W, const hts_params *p,
                               float *sigma_ref, void *stream);
 /* Training: gradients accumulate over images until hts_cnn_zero_grad; the
@@ -245,7 +253,7 @@ hts_status hts_cnn_take_loss(hts_cnn *net, double *loss_sum, void *stream);
 hts_status hts_cnn_get_grad(const hts_cnn *net, float *host_grad, void *stream);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the accumulated gradient. */
 hts_status hts_cnn_adam_step(hts_cnn *net, float lr, void *stream);
-/* Parameters to / from a small binary file (magic "HTSCNN1"). */
+/* Parameters and readout window to / from a small binary file (magic "HTSCNN2"). */
 hts_status hts_cnn_save(const hts_cnn *net, const char *path);
 hts_status hts_cnn_load(const char *path, hts_cnn **out);
 

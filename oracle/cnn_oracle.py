@@ -7,8 +7,9 @@ The network (the learned sigma estimate that replaces Eq. 12-23 in the
 paper's adaptive variant, Sec. III-C) maps the noisy image, scaled by 1/255,
 through five 3x3 convolutions with zero padding (widths C -> 32 -> 32 -> 32
 -> 32 -> 1, ReLU after the first four) to a map of log(sigma) on the [0, 255]
-scale; a reference patch with top-left corner (y, x) reads the map at
-(y + 4, x + 4).  Weights are held in FP16 for the forward pass (the values
+scale.  Training reads the map at the centre (y + 4, x + 4) of the reference
+patch with top-left corner (y, x); denoising averages it over a window around
+that centre (window_sigma).  Weights are held in FP16 for the forward pass (the values
 here are the FP16-rounded ones, computed in FP64); training minimises the
 mean squared error of log(sigma) over the reference patches with Adam.
 
@@ -128,6 +129,19 @@ def ref_centres(H: int, W: int, ps: int = 8, step: int = 4):
         return g
     ys, xs = grid(H), grid(W)
     return np.array([(y + ps // 2, x + ps // 2) for y in ys for x in xs], dtype=np.int64)
+
+
+def window_sigma(out: np.ndarray, centres: np.ndarray, S: int) -> np.ndarray:
+    """Noise level of every reference patch for denoising: exp of the mean of the log-sigma map over
+    rows [cy - S // 2, cy - S // 2 + S) x columns [cx - S // 2, cx - S // 2 + S) cut to the image
+    (the paper's one level per sub-image, the sub-image moved with the patch; S = 1 reads the centre)."""
+    H, W = out.shape
+    res = np.empty(len(centres))
+    for i, (cy, cx) in enumerate(centres):
+        y0, x0 = max(0, cy - S // 2), max(0, cx - S // 2)
+        y1, x1 = min(H, cy - S // 2 + S), min(W, cx - S // 2 + S)
+        res[i] = np.exp(np.mean(out[y0:y1, x0:x1]))
+    return res
 
 
 def loss_and_dout(out: np.ndarray, centres: np.ndarray, target_log_sigma: np.ndarray):

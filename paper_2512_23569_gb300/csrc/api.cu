@@ -361,7 +361,7 @@ hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigm
     else HTS_TRY(launch_set_sigma(sigma > 0 ? (double)sigma : 0.0, g, p, w->st, s));
     if (sigma_ref && fallback_factor > 0) HTS_TRY(launch_learned_check(sigma_ref, g.nref, fallback_factor, w->st, s));
     return launch_filter(noisy, g, w->idx, b64, b32, w->acc, w->wcount, w->redo, w->xlist, w->xskip, w->st, out,
-                         p.precision == 0 ? 1 : 0, sigma_ref, tau_scale(g, p), s);
+                         p.precision == 0 ? 1 : 0, sigma_ref, fallback_factor > 0 ? 1 : 0, tau_scale(g, p), s);
 }
 
 static hts_status denoise_impl(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,

@@ -17,10 +17,16 @@
 // k_conv_bwd_weight per-tile partial sums of the weight and bias gradients,
 //                   added by k_reduce_grad in tile order (deterministic).
 // k_loss            mean squared error of log(sigma) over the reference
-//                   patches and its gradient map.
+//                   patches (map read at the patch centre) and its gradient map.
+// k_window_rows/cols  noise level of every reference patch for denoising:
+//                   exp of the mean of the map over an S x S window around the
+//                   patch centre, as row sums then column sums (fixed order).
+// k_learned_partial/final  the map against the eigenvalue estimate: geometric
+//                   mean of the ratio, and the decision to use it.
 // k_adam            Adam with bias correction; refreshes the FP16 copy.
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,7 +36,7 @@
 #include "hts_internal.h"
 
 struct hts_cnn {
-    int C = 1, device = 0, nparams = 0, t = 0;
+    int C = 1, device = 0, nparams = 0, t = 0, window = 128;
     int off[5] = {}, cin[5] = {}, cout[5] = {};
     float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
     __half *w16 = nullptr;
@@ -238,45 +244,72 @@ __global__ void k_to_half(const float *__restrict__ p, __half *__restrict__ w16,
         w16[i] = __float2half_rn(p[i]);
 }
 
-// sigma of every reference patch: exp of the map at its centre.
-__global__ void k_sigma_refs(const float *__restrict__ outm, int H, int W, int step, int nx, int nref,
-                             float *__restrict__ sigma_ref) {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nref; r += gridDim.x * blockDim.x) {
-        const int gy = r / nx, gx = r - gy * nx;
-        const size_t o = (size_t)(grid_pos(gy, H, step) + PS / 2) * W + grid_pos(gx, W, step) + PS / 2;
-        sigma_ref[r] = expf(outm[o]);
+// Window of a reference patch along one axis: [c - S/2, c - S/2 + S) cut to [0, n), c = centre.
+__host__ __device__ __forceinline__ void window_span(int c, int S, int n, int &lo, int &hi) {
+    lo = c - S / 2;
+    hi = lo + S;
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > n ? n : hi;
+}
+
+// rows[y][gx] = sum of map[y][x] over the window columns of reference column gx.
+__global__ void k_window_rows(const float *__restrict__ outm, int H, int W, int step, int nx, int S,
+                              float *__restrict__ rows) {
+    const size_t n = (size_t)H * nx;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(e / nx), gx = (int)(e - (size_t)y * nx);
+        int lo, hi;
+        window_span(grid_pos(gx, W, step) + PS / 2, S, W, lo, hi);
+        const float *row = outm + (size_t)y * W;
+        float acc = 0.f;
+        for (int x = lo; x < hi; ++x) acc += row[x];
+        rows[e] = acc;
     }
 }
 
-// Learned map against the estimate: geometric-mean ratio, fallback outside the factor.
-__global__ void __launch_bounds__(1024) k_learned_check(float *__restrict__ sigma_ref, int nref, double factor,
-                                                        DevState *st) {
-    __shared__ double red[32];
-    __shared__ int use;
-    const double est = st->sigma_hat;
-    double s = 0.0;
-    int bad = 0;
-    for (int r = threadIdx.x; r < nref; r += blockDim.x) {
-        const float v = sigma_ref[r];
-        if (!(v > 0.f) || !isfinite(v)) bad = 1;
-        else s += log((double)v);
+// sigma_ref[r] = exp(sum of rows[y][gx] over the window rows of r / window area).
+__global__ void k_window_cols(const float *__restrict__ rows, int H, int W, int step, int nx, int nref, int S,
+                              float *__restrict__ sigma_ref) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nref; r += gridDim.x * blockDim.x) {
+        const int gy = r / nx, gx = r - gy * nx;
+        int ylo, yhi, xlo, xhi;
+        window_span(grid_pos(gy, H, step) + PS / 2, S, H, ylo, yhi);
+        window_span(grid_pos(gx, W, step) + PS / 2, S, W, xlo, xhi);
+        float acc = 0.f;
+        for (int y = ylo; y < yhi; ++y) acc += rows[(size_t)y * nx + gx];
+        sigma_ref[r] = expf(acc / (float)((yhi - ylo) * (xhi - xlo)));
     }
-    bad = __syncthreads_or(bad);
+}
+
+// Per block: sum of log(sigma_ref) over a fixed stride of references (NaN if one is not finite and > 0).
+__global__ void __launch_bounds__(256) k_learned_partial(const float *__restrict__ sigma_ref, int nref,
+                                                         DevState *st) {
+    __shared__ double red[8];
+    double s = 0.0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nref; r += gridDim.x * blockDim.x) {
+        const float v = sigma_ref[r];
+        s += (v > 0.f && isfinite(v)) ? (double)logf(v) : (double)NAN;
+    }
 #pragma unroll
     for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        const double ratio = (est > 0.0 && !bad) ? exp(t / nref - log(est)) : 0.0;
-        st->learned_ratio = ratio;
-        use = (ratio > 0.0 && ratio >= 1.0 / factor && ratio <= factor) ? 1 : 0;
-        st->learned = use;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        st->learned_part[blockIdx.x] = t;
     }
-    __syncthreads();
-    if (!use)
-        for (int r = threadIdx.x; r < nref; r += blockDim.x) sigma_ref[r] = (float)est;
+}
+
+// Geometric-mean ratio of the map to the estimate; the map is used if it lies in [1/factor, factor].
+__global__ void k_learned_final(int nref, double factor, DevState *st) {
+    if (threadIdx.x != 0) return;
+    double t = 0.0;
+    for (int b = 0; b < LEARNED_PARTS; ++b) t += st->learned_part[b];
+    const double est = st->sigma_hat;
+    const double ratio = (est > 0.0 && isfinite(t)) ? exp(t / nref - log(est)) : 0.0;
+    st->learned_ratio = ratio;
+    st->learned = (ratio > 0.0 && ratio >= 1.0 / factor && ratio <= factor) ? 1 : 0;
 }
 
 size_t fwd_smem(int cin, int cout) { return ((size_t)cin * HALO * HALO + (size_t)cout * cin * 9) * 4; }
@@ -420,26 +453,39 @@ void free_net(hts_cnn *n) {
 
 }  // namespace
 
-hts_status launch_learned_check(float *sigma_ref, int nref, double factor, DevState *st, cudaStream_t s) {
+hts_status launch_learned_check(const float *sigma_ref, int nref, double factor, DevState *st, cudaStream_t s) {
     {
-        KTimer kt("k_learned_check", s);
-        k_learned_check<<<1, 1024, 0, s>>>(sigma_ref, nref, factor, st);
+        KTimer kt("k_learned_partial", s);
+        k_learned_partial<<<LEARNED_PARTS, 256, 0, s>>>(sigma_ref, nref, st);
     }
-    return check_launch("k_learned_check");
+    HTS_TRY(check_launch("k_learned_partial"));
+    {
+        KTimer kt("k_learned_final", s);
+        k_learned_final<<<1, 32, 0, s>>>(nref, factor, st);
+    }
+    return check_launch("k_learned_final");
 }
 
-// Noise level of every reference patch from the network (device, N_ref).
+// Noise level of every reference patch from the network through the readout window (device, N_ref).
 hts_status cnn_sigma_refs(hts_cnn *n, const float *img, const Geom &g, float *sigma_ref, cudaStream_t s) {
     HTS_TRY(check_net(n, img, g.H, g.W));
     if (n->C != g.C) return report(HTS_EINVAL, "network built for another channel count");
     HTS_TRY(ensure_ws(n, g.H, g.W));
     HTS_TRY(forward(n, img, g.H, g.W, s));
+    float *rows = n->d0;  // H x nx row sums (the gradient buffers are idle outside training)
+    const size_t nrow = (size_t)g.H * g.nx;
     {
-        KTimer kt("k_sigma_refs", s);
-        k_sigma_refs<<<(g.nref + 255) / 256, 256, 0, s>>>(n->act[DEPTH - 1], g.H, g.W, g.step, g.nx, g.nref,
+        KTimer kt("k_window_rows", s);
+        k_window_rows<<<(unsigned)std::min<size_t>((nrow + 255) / 256, 152 * 16), 256, 0, s>>>(
+            n->act[DEPTH - 1], g.H, g.W, g.step, g.nx, n->window, rows);
+    }
+    HTS_TRY(check_launch("k_window_rows"));
+    {
+        KTimer kt("k_window_cols", s);
+        k_window_cols<<<(g.nref + 255) / 256, 256, 0, s>>>(rows, g.H, g.W, g.step, g.nx, g.nref, n->window,
                                                            sigma_ref);
     }
-    return check_launch("k_sigma_refs");
+    return check_launch("k_window_cols");
 }
 
 }  // namespace hts
@@ -455,6 +501,15 @@ extern "C" int hts_cnn_num_params(int C) {
 }
 
 extern "C" int hts_cnn_channels(const hts_cnn *net) { return net ? net->C : 0; }
+
+extern "C" int hts_cnn_window(const hts_cnn *net) { return net ? net->window : 0; }
+
+extern "C" hts_status hts_cnn_set_window(hts_cnn *net, int S) {
+    if (!net) return report(HTS_EINVAL, "NULL pointer");
+    if (S < 1 || S > 4096) return report(HTS_EINVAL, "window must be in [1, 4096]");
+    net->window = S;
+    return HTS_OK;
+}
 
 extern "C" hts_status hts_cnn_create(int C, uint64_t seed, hts_cnn **out) {
     if (!out) return report(HTS_EINVAL, "NULL pointer");
@@ -606,9 +661,9 @@ extern "C" hts_status hts_cnn_save(const hts_cnn *net, const char *path) {
     HTS_TRY(hts_cnn_get_params(net, h.data()));
     FILE *f = fopen(path, "wb");
     if (!f) return report(HTS_EINVAL, "cannot open file");
-    const char magic[8] = {'H', 'T', 'S', 'C', 'N', 'N', '1', 0};
-    const int hdr[2] = {net->C, net->nparams};
-    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(int), 2, f) == 2 &&
+    const char magic[8] = {'H', 'T', 'S', 'C', 'N', 'N', '2', 0};
+    const int hdr[3] = {net->C, net->nparams, net->window};
+    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof(int), 3, f) == 3 &&
               fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
     fclose(f);
     return ok ? HTS_OK : report(HTS_EINVAL, "write failed");
@@ -619,15 +674,16 @@ extern "C" hts_status hts_cnn_load(const char *path, hts_cnn **out) {
     FILE *f = fopen(path, "rb");
     if (!f) return report(HTS_EINVAL, "cannot open file");
     char magic[8];
-    int hdr[2];
-    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "HTSCNN1", 8) == 0 && fread(hdr, sizeof(int), 2, f) == 2 &&
-              (hdr[0] == 1 || hdr[0] == 3) && hdr[1] == hts_cnn_num_params(hdr[0]);
+    int hdr[3];
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "HTSCNN2", 8) == 0 && fread(hdr, sizeof(int), 3, f) == 3 &&
+              (hdr[0] == 1 || hdr[0] == 3) && hdr[1] == hts_cnn_num_params(hdr[0]) && hdr[2] >= 1 && hdr[2] <= 4096;
     std::vector<float> h(ok ? hdr[1] : 0);
     if (ok) ok = fread(h.data(), sizeof(float), h.size(), f) == h.size();
     fclose(f);
     if (!ok) return report(HTS_EINVAL, "not a network file");
     hts_cnn *n = nullptr;
     HTS_TRY(hts_cnn_create(hdr[0], 1, &n));
+    n->window = hdr[2];
     const hts_status st = upload(n, h.data());
     if (st != HTS_OK) {
         free_net(n);

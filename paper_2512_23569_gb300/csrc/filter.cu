@@ -64,6 +64,7 @@ struct FilterArgs {
     int exact;       // 0: FP32 threshold decisions only (precision form)
     const float *sigma_ref;  // [N_ref] noise level per group (nullptr: the call's one level)
     double tau_scale;        // tau = tau_scale * sigma
+    int map_judged;          // sigma_ref only if the learned-map check passed
     uint8_t *xskip;  // [N_ref] 1 = group went to the exact pass
     DevState *st;
 };
@@ -319,11 +320,14 @@ __device__ __forceinline__ double haar_entry(int K, int h, int k) {
 // Threshold of group r: tau_scale * sigma_r in FP64 when the noise level is
 // given per group, else the call's threshold; the FP32 copy is the FP64 one
 // rounded, so every pass decides against the same value.
+__device__ __forceinline__ bool use_map(const FilterArgs &a) {
+    return a.sigma_ref && (!a.map_judged || a.st->learned);
+}
 __device__ __forceinline__ double group_tau64(const FilterArgs &a, int r) {
-    return a.sigma_ref ? a.tau_scale * (double)a.sigma_ref[r] : a.st->tau;
+    return use_map(a) ? a.tau_scale * (double)a.sigma_ref[r] : a.st->tau;
 }
 __device__ __forceinline__ float group_tau32(const FilterArgs &a, int r) {
-    return a.sigma_ref ? (float)(a.tau_scale * (double)a.sigma_ref[r]) : a.st->tau32;
+    return use_map(a) ? (float)(a.tau_scale * (double)a.sigma_ref[r]) : a.st->tau32;
 }
 
 // 0 = drop, 1 = keep, 2 = undecided in FP32 (inside the guard band).
@@ -1563,7 +1567,7 @@ void set_tuned_tile(const Geom &g, TileChoice c) {
 
 hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, const double *b64, const float *b32,
                          long long *acc, int *wcount, int32_t *redo_list, int4 *xlist, uint8_t *xskip,
-                         DevState *st, float *out, int exact, const float *sigma_ref, double tau_scale,
+                         DevState *st, float *out, int exact, const float *sigma_ref, int map_judged, double tau_scale,
                          cudaStream_t s) {
     FilterArgs a;
     a.img = img;
@@ -1585,6 +1589,7 @@ hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, co
     a.exact = exact;
     a.sigma_ref = sigma_ref;
     a.tau_scale = tau_scale;
+    a.map_judged = map_judged;
     a.xskip = xskip;
     a.st = st;
 #define HTS_FILTER_CASE(CC, KK) \

@@ -14,6 +14,8 @@ constexpr int NPIX = PS * PS;  // pixels per patch
 constexpr int MAX_WIN = 63;    // largest search window side
 constexpr double FIX_SCALE = 65536.0;  // 2^16: fixed-point scale of the aggregation sums
 
+constexpr int LEARNED_PARTS = 160;  // blocks of the learned-map check
+
 // Device-resident state of one call: noise level, threshold and counters.
 struct DevState {
     double sigma_est;
@@ -33,6 +35,7 @@ struct DevState {
     int error;
     int learned;          // 1: the learned noise map was used, 0: fell back to the estimate
     double learned_ratio; // geometric mean of (learned sigma / estimated sigma)
+    double learned_part[LEARNED_PARTS];  // per-block sums of log(learned sigma)
 };
 
 // Basis on the device: [ns][2][8][8][2] (U then V, element [a][i], re/im).
@@ -128,12 +131,14 @@ hts_status launch_sigma_final(const Geom &g, const hts_params &p, DevState *st, 
 // xlist: XLIST_PER_REF * N_ref int4 entries for the in-band coefficients; xskip: N_ref
 // bytes (see filter.cu).  exact = 0 (precision form): threshold decisions in FP32 only.
 // sigma_ref (device, N_ref, may be nullptr): a noise level per group, threshold
-// tau_scale * sigma_ref[r]; nullptr: the threshold in the call's state.
+// tau_scale * sigma_ref[r]; nullptr: the threshold in the call's state.  With
+// map_judged = 1 the map is used only if DevState.learned is set (else the
+// state's threshold).
 constexpr int XLIST_PER_REF = 4;
 hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, const double *b64, const float *b32,
                          long long *acc, int *wcount, int32_t *redo_list, int4 *xlist, uint8_t *xskip,
-                         DevState *st, float *out, int exact, const float *sigma_ref, double tau_scale,
-                         cudaStream_t s);
+                         DevState *st, float *out, int exact, const float *sigma_ref, int map_judged,
+                         double tau_scale, cudaStream_t s);
 double tau_scale(const Geom &g, const hts_params &p);  // sigma -> tau factor (sigma.cu)
 
 // Filter tile shape (k_filter_tile): ty x tx reference positions per tile,
@@ -171,17 +176,17 @@ struct Bufs {
 size_t bufs_bytes(const Geom &g);                              // arena bytes of one image
 void bufs_carve(const Geom &g, unsigned char *base, Bufs *b);  // device pointers (not aux / events)
 // Learned noise map check (cnn.cu): geometric mean of sigma_ref / the
-// estimated sigma_hat; outside [1/factor, factor] every entry is replaced by
-// sigma_hat.  Records DevState.learned and learned_ratio.
-hts_status launch_learned_check(float *sigma_ref, int nref, double factor, DevState *st, cudaStream_t s);
+// estimated sigma_hat; sets DevState.learned (1 if inside [1/factor, factor]
+// and the map is finite and positive) and learned_ratio.
+hts_status launch_learned_check(const float *sigma_ref, int nref, double factor, DevState *st, cudaStream_t s);
 // Noise level of every reference patch from the learned network (device, N_ref; cnn.cu).
 hts_status cnn_sigma_refs(hts_cnn *n, const float *img, const Geom &g, float *sigma_ref, cudaStream_t s);
 // Releases every batch plan (batch.cu).
 void batch_shutdown();
 // The whole method for one image on stream s with the buffers of b (api.cu).
 // sigma_ref (device, N_ref, may be nullptr): a noise level per reference
-// patch; with a fallback factor > 0 it is first checked against the
-// estimated level (launch_learned_check).
+// patch; with a fallback factor > 0 it is checked against the estimated
+// level (launch_learned_check) and the estimate is used if it fails.
 hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
                        const hts_params &p, const Bufs &b, cudaStream_t s, float *sigma_ref = nullptr,
                        double fallback_factor = 0.0);

@@ -129,5 +129,5 @@ extern "C" hts_status hts_denoise_noalloc(const float *noisy, float *out, int H,
     else st = launch_set_sigma((double)sigma, g, *p, ds, s);
     if (st != HTS_OK) return st;
     return launch_filter(noisy, g, idx, ub64, ub32, acc, wcount, redo, xlist, xskip, ds, out,
-                         p->precision == 0 ? 1 : 0, nullptr, tau_scale(g, *p), s);
+                         p->precision == 0 ? 1 : 0, nullptr, 0, tau_scale(g, *p), s);
 }

@@ -32,7 +32,7 @@ EXPORTS = [
     "hts_denoise_sigma_map", "hts_denoise_learned", "hts_cnn_num_params", "hts_cnn_channels", "hts_cnn_create",
     "hts_cnn_free", "hts_cnn_get_params", "hts_cnn_set_params", "hts_cnn_log_sigma_map", "hts_cnn_sigma_refs",
     "hts_cnn_zero_grad", "hts_cnn_accumulate_grad", "hts_cnn_take_loss", "hts_cnn_get_grad", "hts_cnn_adam_step",
-    "hts_cnn_save", "hts_cnn_load",
+    "hts_cnn_save", "hts_cnn_load", "hts_cnn_set_window", "hts_cnn_window",
 ]
 
 
@@ -129,6 +129,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.hts_cnn_adam_step.argtypes = [P, F, P]
         lib.hts_cnn_save.argtypes = [P, ctypes.c_char_p]
         lib.hts_cnn_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(P)]
+        lib.hts_cnn_set_window.argtypes = [P, I]
+        lib.hts_cnn_window.argtypes = [P]
+        lib.hts_cnn_window.restype = I
         for name in EXPORTS:  # fail loudly on a library that lacks a declared entry point
             getattr(lib, name)
         _LIB = lib
@@ -338,6 +341,15 @@ class Cnn:
     def handle(self):
         return self._h
 
+    @property
+    def window(self) -> int:
+        """Readout window S: a patch's sigma is exp(mean of the map over S x S pixels around its centre)."""
+        return int(load().hts_cnn_window(self._h))
+
+    @window.setter
+    def window(self, S: int) -> None:
+        _check(load().hts_cnn_set_window(self._h, int(S)))
+
     def get_params(self) -> np.ndarray:
         a = np.empty(self.nparams, dtype=np.float32)
         _check(load().hts_cnn_get_params(self._h, ctypes.c_void_p(a.ctypes.data)))
@@ -361,7 +373,7 @@ class Cnn:
         return out
 
     def sigma_refs(self, img, p: Params | None = None, stream=None):
-        """sigma of every reference patch (N_ref,)."""
+        """sigma of every reference patch through the readout window (N_ref,)."""
         import torch
 
         img = _chw(img)

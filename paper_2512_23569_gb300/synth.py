@@ -201,5 +201,8 @@ def ref_log_sigma(sigma_px: np.ndarray, ps: int = 8, step: int = 4) -> np.ndarra
         return g
 
     v = sigma_px.astype(np.float64) ** 2
-    out = [np.log(np.sqrt(v[y:y + ps, x:x + ps].mean())) for y in grid(H) for x in grid(W)]
-    return np.asarray(out, dtype=np.float32)
+    S = np.zeros((H + 1, W + 1))
+    S[1:, 1:] = v.cumsum(0).cumsum(1)
+    ys, xs = np.asarray(grid(H)), np.asarray(grid(W))
+    box = (S[np.ix_(ys + ps, xs + ps)] - S[np.ix_(ys, xs + ps)] - S[np.ix_(ys + ps, xs)] + S[np.ix_(ys, xs)])
+    return np.log(np.sqrt(np.maximum(box, 0.0) / (ps * ps))).reshape(-1).astype(np.float32)

@@ -76,3 +76,26 @@ def test_reference_centres_follow_the_grid():
     # grid {0, 4, 8, 12, 13} x {0, 4, 8, 9}: centres shifted by 4
     assert c[0].tolist() == [4, 4] and c[-1].tolist() == [13 + 4, 9 + 4]
     assert len(c) == 5 * 4
+
+
+def test_window_readout_special_cases():
+    rng = np.random.default_rng(4)
+    H, W = 40, 36
+    cen = co.ref_centres(H, W)
+    out = rng.standard_normal((H, W))
+    # S = 1 is the centre readout used in training
+    np.testing.assert_allclose(co.window_sigma(out, cen, 1), np.exp(out[cen[:, 0], cen[:, 1]]), rtol=1e-14)
+    # a constant map gives the constant everywhere, whatever the window
+    np.testing.assert_allclose(co.window_sigma(np.full((H, W), 2.5), cen, 16), np.exp(2.5), rtol=1e-14)
+    # a linear map averages to its value at the window's mean index: for an even S inside the image
+    # the window [c - S/2, c + S/2) has mean index c - 1/2; for an odd S, [c - (S-1)/2, c + (S+1)/2) has c
+    yy, xx = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    lin = 0.03 * yy - 0.02 * xx
+    for S, shift in ((8, -0.5), (5, 0.0)):
+        got = np.log(co.window_sigma(lin, cen, S))
+        for (cy, cx), g in zip(cen, got):
+            if cy - S // 2 >= 0 and cx - S // 2 >= 0 and cy + S - S // 2 <= H and cx + S - S // 2 <= W:
+                assert abs(g - (0.03 * (cy + shift) - 0.02 * (cx + shift))) <= 1e-12
+    # a window cut by the border: centre (4, 4) of a 40 x 36 map with S = 16 covers rows and columns 0..11
+    got = np.log(co.window_sigma(lin, np.array([[4, 4]]), 16))[0]
+    assert abs(got - (0.03 * 5.5 - 0.02 * 5.5)) <= 1e-12

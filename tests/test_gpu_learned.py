@@ -4,9 +4,9 @@
   oracle fed the same sigmas (same tolerances as the global-sigma parity);
 * the network's forward map, loss, gradient and Adam step against the FP64
   oracle of cnn_oracle.py, from the same (FP16-rounded) parameters;
-* training on images whose noise level varies across the frame brings the
-  map closer to the true level than one global estimate, and denoising with it
-  beats one global sigma;
+* training on images whose noise level varies across the frame, with targets
+  the method generates itself (best-PSNR threshold level, train.py), gives a
+  map whose denoising beats one global estimated sigma;
 * a map far from the estimate falls back to the estimate.
 """
 
@@ -74,10 +74,13 @@ def test_network_matches_oracle(hts, C):
     out, cache = co.forward(th16, img)
     got = net.log_sigma_map(_dev(img)).cpu().numpy()
     assert np.max(np.abs(got - out)) <= 1e-4 * (1.0 + np.max(np.abs(out)))
-    # sigma of every reference = exp(map at its centre)
+    # sigma of every reference through the readout window, against the oracle's map and window
     cen = co.ref_centres(H, W)
-    np.testing.assert_allclose(net.sigma_refs(_dev(img), p).cpu().numpy(), np.exp(got[cen[:, 0], cen[:, 1]]),
-                               rtol=1e-6)
+    tol = 2e-4 * (1.0 + np.max(np.abs(out)))
+    for S in (1, 8, 128):
+        net.window = S
+        np.testing.assert_allclose(net.sigma_refs(_dev(img), p).cpu().numpy(), co.window_sigma(out, cen, S),
+                                   rtol=tol)
     # loss and gradient
     tgt = rng.uniform(1.0, 3.5, size=len(cen)).astype(np.float32)
     L, dout = co.loss_and_dout(out, cen, tgt)
@@ -95,49 +98,26 @@ def test_network_matches_oracle(hts, C):
     np.testing.assert_allclose(net.get_params(), want, rtol=1e-5, atol=1e-7)
 
 
-def _train_set(n, size, seed):
-    out = []
-    for i in range(n):
-        clean, noisy, spx = synth.make_varying_noise_image(size, size, 1, seed + 7 * i, sb_min=2.0)
-        out.append((clean, noisy, spx))
-    return out
-
-
-def _train(hts, net, data, p, steps, batch, lr0):
-    xs = [_dev(n) for _, n, _ in data]
-    ts = [_dev(synth.ref_log_sigma(s)) for _, _, s in data]
-    rng = np.random.default_rng(0)
-    hist = []
-    for it in range(steps):
-        lr = lr0 * (0.1 ** (it / steps))  # exponential decay to lr0 / 10
-        net.zero_grad()
-        pick = rng.choice(len(xs), batch, replace=False)
-        for i in pick:
-            net.accumulate_grad(xs[i], ts[i], p)
-        net.adam_step(lr / batch)
-        if it % 50 == 49:
-            hist.append(net.take_loss() / (50 * batch))
-    return hist
+def _images(n, size, seed):
+    return [synth.make_varying_noise_image(size, size, 1, seed + 7 * i, sb_min=2.0) for i in range(n)]
 
 
 def test_training_beats_one_global_sigma(hts):
+    from paper_2512_23569_gb300 import train
+
     p = hts.params(win=15)
+    data = [train.targets(n, c, s, p) for c, n, s in _images(48, 96, 1000)]
     net = hts.Cnn(1, seed=3)
-    hist = _train(hts, net, _train_set(48, 96, 1000), p, steps=600, batch=8, lr0=2e-3)
+    hist = train.fit(net, [d[0] for d in data], [d[1] for d in data], p, steps=1200, batch=8, lr0=2e-3)
     assert hist[-1] < 0.5 * hist[0], hist
-    gains, err_l, err_g = [], [], []
-    for clean, noisy, spx in _train_set(3, 160, 9000):
+    net.window = 64
+    gains = []
+    for clean, noisy, _ in _images(6, 192, 9000):
         x = _dev(noisy)
-        truth = synth.ref_log_sigma(spx)
-        est, _ = hts.estimate_sigma(x, p)
-        lmap = np.log(net.sigma_refs(x, p).cpu().numpy())
-        err_l.append(np.sqrt(np.mean((lmap - truth) ** 2)))
-        err_g.append(np.sqrt(np.mean((np.log(est) - truth) ** 2)))
-        a = hts.denoise_learned(x, net, p, fallback_factor=4.0).cpu().numpy()
+        a = hts.denoise_learned(x, net, p, fallback_factor=3.0).cpu().numpy()
         assert hts.last_stats()["learned"] == 1
         b = hts.denoise(x, p=p).cpu().numpy()
         gains.append(synth.psnr(a, clean) - synth.psnr(b, clean))
-    assert np.mean(err_l) < np.mean(err_g), (err_l, err_g)
     assert np.mean(gains) > 0.0, gains
 
 
@@ -154,15 +134,16 @@ def test_far_map_falls_back_to_the_estimate(hts):
     got = hts.denoise_learned(x, net, p, fallback_factor=2.0).cpu().numpy()
     st = hts.last_stats()
     assert st["learned"] == 0 and st["learned_ratio"] > 2.0
-    want = hts.denoise(x, p=p).cpu().numpy()
-    assert np.max(np.abs(got - want)) <= 1e-3
+    # the fallback is the estimated global threshold: the plain call, bit for bit
+    np.testing.assert_array_equal(got, hts.denoise(x, p=p).cpu().numpy())
     assert co.num_params(1) == net.nparams
 
 
 def test_network_save_load_roundtrip(hts, tmp_path):
     net = hts.Cnn(3, seed=11)
+    net.window = 40
     path = str(tmp_path / "net.bin")
     net.save(path)
     back = hts.Cnn.load_file(path)
-    assert back.C == 3
+    assert back.C == 3 and back.window == 40
     np.testing.assert_array_equal(back.get_params(), net.get_params())
