@@ -235,7 +235,9 @@ hts_status hts_cnn_free(hts_cnn *net);
  * hts_cnn_num_params(C) floats); set also resets the optimiser state.  Synchronous. */
 hts_status hts_cnn_get_params(const hts_cnn *net, float *host_params);
 hts_status hts_cnn_set_params(hts_cnn *net, const float *host_params);
-/* Forward pass: log-sigma map (device, H x W) of a device CHW image. */
+/* Forward pass used for denoising: log-sigma map (device, H x W) of a device
+ * CHW image, on the tensor cores with the network input and the hidden
+ * activations rounded to FP16 (training's forward keeps them in FP32). */
 hts_status hts_cnn_log_sigma_map(hts_cnn *net, const float *img, int H, int W, float *map_out, void *stream);
 /* Readout window S (1 <= S <= 4096) of hts_cnn_sigma_refs / hts_denoise_learned. */
 hts_status hts_cnn_set_window(hts_cnn *net, int S);

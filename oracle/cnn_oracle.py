@@ -81,6 +81,18 @@ def forward(theta: np.ndarray, img: np.ndarray):
     return a[0], cache
 
 
+def forward_act16(theta: np.ndarray, img: np.ndarray) -> np.ndarray:
+    """The forward pass used for denoising: as forward(), with the network input x / 255 and every
+    hidden activation (after ReLU) rounded to FP16 (round to nearest even).  Returns the map (H, W)."""
+    C = img.shape[0]
+    layers = unpack(theta, C)
+    a = fp16(np.asarray(img, dtype=np.float64) / 255.0)
+    for li, (w, b) in enumerate(layers):
+        z = conv3x3(a, w, b)
+        a = fp16(np.maximum(z, 0.0)) if li < DEPTH - 1 else z
+    return a[0]
+
+
 def backward(theta: np.ndarray, cache, dout: np.ndarray) -> np.ndarray:
     """Gradient of sum(dout * out) with respect to the parameter vector."""
     C = cache[0].shape[0]

@@ -1,6 +1,9 @@
 // Learned noise-level map on sm_103a: the convolutional estimate of the
 // noise level that the paper's adaptive variant uses in place of a single
 // global value (Sec. III-C), trained here by the library's own kernels.
+// This file holds the FP32 training path (forward with FP32 activations,
+// backward, Adam), the readout and the host interface; the forward pass used
+// for denoising runs on the tensor cores (cnn_tc.cu).
 //
 // Network: the noisy image scaled by 1/255 goes through five 3x3
 // convolutions with zero padding (widths C -> 32 -> 32 -> 32 -> 32 -> 1,
@@ -33,20 +36,8 @@
 #include <utility>
 #include <vector>
 
+#include "cnn_internal.h"
 #include "hts_internal.h"
-
-struct hts_cnn {
-    int C = 1, device = 0, nparams = 0, t = 0, window = 128;
-    int off[5] = {}, cin[5] = {}, cout[5] = {};
-    float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
-    __half *w16 = nullptr;
-    size_t cap_px = 0;
-    float *act[5] = {};
-    float *d0 = nullptr, *d1 = nullptr;
-    size_t cap_part = 0;
-    float *part = nullptr;
-    double *loss = nullptr;
-};
 
 namespace hts {
 namespace {
@@ -448,6 +439,11 @@ void free_net(hts_cnn *n) {
     cudaFree(n->d1);
     cudaFree(n->part);
     cudaFree(n->loss);
+    cudaFree(n->h16[0]);
+    cudaFree(n->h16[1]);
+    cudaFree(n->map);
+    cudaFree(n->rows);
+    cudaFree(n->err);
     delete n;
 }
 
@@ -470,14 +466,14 @@ hts_status launch_learned_check(const float *sigma_ref, int nref, double factor,
 hts_status cnn_sigma_refs(hts_cnn *n, const float *img, const Geom &g, float *sigma_ref, cudaStream_t s) {
     HTS_TRY(check_net(n, img, g.H, g.W));
     if (n->C != g.C) return report(HTS_EINVAL, "network built for another channel count");
-    HTS_TRY(ensure_ws(n, g.H, g.W));
-    HTS_TRY(forward(n, img, g.H, g.W, s));
-    float *rows = n->d0;  // H x nx row sums (the gradient buffers are idle outside training)
+    HTS_TRY(cnn_ensure_infer(n, g.H, g.W, g.nx));
+    HTS_TRY(cnn_forward_tc(n, img, g.H, g.W, s));
+    float *rows = n->rows;  // H x nx row sums
     const size_t nrow = (size_t)g.H * g.nx;
     {
         KTimer kt("k_window_rows", s);
         k_window_rows<<<(unsigned)std::min<size_t>((nrow + 255) / 256, 152 * 16), 256, 0, s>>>(
-            n->act[DEPTH - 1], g.H, g.W, g.step, g.nx, n->window, rows);
+            n->map, g.H, g.W, g.step, g.nx, n->window, rows);
     }
     HTS_TRY(check_launch("k_window_rows"));
     {
@@ -524,6 +520,8 @@ extern "C" hts_status hts_cnn_create(int C, uint64_t seed, hts_cnn **out) {
     if (st == HTS_OK) st = cu(cudaMalloc(&n->w16, n->nparams * sizeof(__half)), "cudaMalloc(cnn)");
     if (st == HTS_OK) st = cu(cudaMalloc(&n->loss, sizeof(double)), "cudaMalloc(cnn)");
     if (st == HTS_OK) st = cu(cudaMemset(n->loss, 0, sizeof(double)), "cudaMemset");
+    if (st == HTS_OK) st = cu(cudaMalloc(&n->err, sizeof(int)), "cudaMalloc(cnn)");
+    if (st == HTS_OK) st = cu(cudaMemset(n->err, 0, sizeof(int)), "cudaMemset");
     if (st != HTS_OK) {
         free_net(n);
         return st;
@@ -571,10 +569,9 @@ extern "C" hts_status hts_cnn_log_sigma_map(hts_cnn *net, const float *img, int 
     HTS_TRY(check_net(net, img, H, W));
     if (!map_out) return report(HTS_EINVAL, "NULL pointer");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    HTS_TRY(ensure_ws(net, H, W));
-    HTS_TRY(forward(net, img, H, W, s));
-    return cu(cudaMemcpyAsync(map_out, net->act[DEPTH - 1], (size_t)H * W * sizeof(float), cudaMemcpyDeviceToDevice,
-                              s),
+    HTS_TRY(cnn_ensure_infer(net, H, W, 1));
+    HTS_TRY(cnn_forward_tc(net, img, H, W, s));
+    return cu(cudaMemcpyAsync(map_out, net->map, (size_t)H * W * sizeof(float), cudaMemcpyDeviceToDevice, s),
               "cudaMemcpyAsync");
 }
 

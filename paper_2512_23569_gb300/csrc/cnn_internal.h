@@ -1,0 +1,40 @@
+// The learned noise-level network's handle and the entry points shared by its
+// two translation units: cnn.cu (FP32 forward and backward for training,
+// Adam, readout, host interface) and cnn_tc.cu (the tensor-core forward pass
+// used for denoising).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "../../include/hts.h"
+
+struct hts_cnn {
+    int C = 1, device = 0, nparams = 0, t = 0, window = 128;
+    int off[5] = {}, cin[5] = {}, cout[5] = {};  // per layer: parameter offset, input / output channels
+    float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;  // FP32 parameters, Adam state
+    __half *w16 = nullptr;                                                  // FP16 copy used by the kernels
+    size_t cap_px = 0;
+    float *act[5] = {};                   // FP32 activations (planar CHW) of the training forward
+    float *d0 = nullptr, *d1 = nullptr;   // gradient maps; d0 also holds the readout's row sums
+    size_t cap_part = 0;
+    float *part = nullptr;                // per-tile partial weight gradients
+    double *loss = nullptr;
+    size_t cap_h16 = 0, cap_map = 0, cap_rows = 0;
+    __half *h16[2] = {};    // FP16 activations of the tensor-core forward, 4 planes of 8 channels
+    float *map = nullptr;   // its log-sigma map (H x W)
+    float *rows = nullptr;  // row sums of the readout window (H x reference columns)
+    int *err = nullptr;     // set by a tensor-core forward whose wait gave up (the map is then NaN)
+};
+
+namespace hts {
+
+// Tensor-core forward pass (cnn_tc.cu): the log-sigma map of img (device,
+// planar C x H x W, [0, 255]) in net->map (H x W, FP32).  Hidden
+// activations are rounded to FP16 (8-channel planes, net->h16), the network
+// input x / 255 too; FP16 weights, FP32 accumulation in tensor memory.
+// cnn_ensure_infer sizes net->h16, net->map and net->rows first.
+hts_status cnn_forward_tc(hts_cnn *net, const float *img, int H, int W, cudaStream_t s);
+hts_status cnn_ensure_infer(hts_cnn *net, int H, int W, int nx);
+
+}  // namespace hts

@@ -33,6 +33,7 @@ __all__ = [
     "make_config_image",
     "psnr",
     "make_pg_correlated_image",
+    "add_varying_noise",
     "make_varying_noise_image",
     "ref_log_sigma",
 ]
@@ -164,18 +165,18 @@ def make_pg_correlated_image(H: int, W: int, C: int, seed: int, a: float = 0.01,
     return clean, noisy
 
 
-def make_varying_noise_image(H: int, W: int, C: int, seed: int, a_max: float = 0.02, sb_max: float = 30.0,
-                             sb_min: float = 0.0):
-    """(clean, noisy, sigma_px): Poisson-Gaussian noise whose read-noise level varies across the image.
+def add_varying_noise(clean: np.ndarray, seed: int, a_max: float = 0.02, sb_max: float = 30.0,
+                      sb_min: float = 0.0):
+    """(noisy, sigma_px): Poisson-Gaussian noise on `clean` whose read-noise level varies across it.
 
     Gain a ~ U[0, a_max]; sigma_b ramps linearly between two levels drawn from
-    U[sb_min, sb_max] along a random direction (both drawn from seed + 1's
-    generator, before the noise itself); noise seed = seed + 2.  sigma_px
-    (H, W) is the true per-pixel standard deviation, the root mean over
-    channels of a * clean + sigma_b^2.
+    U[sb_min, sb_max] along a direction drawn from U[0, 2 pi) (all from seed's
+    generator); the noise itself uses seed + 1.  sigma_px (H, W) is the true
+    per-pixel standard deviation, the root mean over channels of
+    a * clean + sigma_b^2.
     """
-    clean = clean_image(H, W, C, seed)
-    rng = _rng(seed + 1)
+    C, H, W = clean.shape
+    rng = _rng(seed)
     a = float(rng.uniform(0.0, a_max))
     s0, s1 = rng.uniform(sb_min, sb_max, size=2)
     th = rng.uniform(0.0, 2.0 * np.pi)
@@ -183,9 +184,16 @@ def make_varying_noise_image(H: int, W: int, C: int, seed: int, a_max: float = 0
     proj = np.cos(th) * yy + np.sin(th) * xx
     t = (proj - proj.min()) / max(proj.max() - proj.min(), 1e-12)
     sb = s0 + (s1 - s0) * t
-    noisy = poisson_gaussian(clean, a, sb[None], seed + 2)
+    noisy = poisson_gaussian(clean, a, sb[None], seed + 1)
     var = a * clean.astype(np.float64) + sb[None] ** 2
-    sigma_px = np.sqrt(var.mean(axis=0))
+    return noisy, np.sqrt(var.mean(axis=0))
+
+
+def make_varying_noise_image(H: int, W: int, C: int, seed: int, a_max: float = 0.02, sb_max: float = 30.0,
+                             sb_min: float = 0.0):
+    """(clean, noisy, sigma_px): clean_image(seed) with add_varying_noise(clean, seed + 1)."""
+    clean = clean_image(H, W, C, seed)
+    noisy, sigma_px = add_varying_noise(clean, seed + 1, a_max, sb_max, sb_min)
     return clean, noisy, sigma_px
 
 

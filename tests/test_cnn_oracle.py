@@ -99,3 +99,29 @@ def test_window_readout_special_cases():
     # a window cut by the border: centre (4, 4) of a 40 x 36 map with S = 16 covers rows and columns 0..11
     got = np.log(co.window_sigma(lin, np.array([[4, 4]]), 16))[0]
     assert abs(got - (0.03 * 5.5 - 0.02 * 5.5)) <= 1e-12
+
+
+def test_fp16_activation_forward():
+    # exact case: input k * 255 / 256 (x / 255 = k / 256), centre-tap weights +-1 from one input
+    # channel each and biases in multiples of 1/256: every activation is a small multiple of 1/256,
+    # exactly representable in FP16, so both forwards agree exactly
+    rng = np.random.default_rng(8)
+    C = 3
+    theta = np.zeros(co.num_params(C))
+    o = 0
+    for cout, cin in co.layer_shapes(C):
+        w = np.zeros((cout, cin, 3, 3))
+        for c in range(cout):
+            w[c, c % cin, 1, 1] = rng.choice([-1.0, 1.0])
+        theta[o:o + w.size] = w.reshape(-1)
+        theta[o + w.size:o + w.size + cout] = rng.integers(-4, 5, size=cout) / 256.0
+        o += w.size + cout
+    img = rng.integers(0, 256, size=(C, 7, 9)) * (255.0 / 256.0)
+    np.testing.assert_array_equal(co.forward_act16(theta, img), co.forward(theta, img)[0])
+    # generic case: rounding happens (results differ) but stays within a small multiple of the FP16
+    # unit roundoff 2^-11 relative to the activations' scale
+    theta = co.fp16(rng.standard_normal(co.num_params(C)) * 0.2)
+    img = rng.uniform(0, 255, size=(C, 12, 10))
+    a, b = co.forward_act16(theta, img), co.forward(theta, img)[0]
+    assert np.max(np.abs(a - b)) > 0
+    assert np.max(np.abs(a - b)) <= 50 * 2.0 ** -11 * (1.0 + np.max(np.abs(b)))
