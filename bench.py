@@ -581,6 +581,84 @@ def run_learned(args):
     return 0
 
 
+# ------------------------------------------------------------------ noise-level network forward alone
+
+def conv_tc_bytes(H, W, C):
+    """Algorithmic DRAM bytes of one tensor-core forward: layer 0 reads the FP32 image (4C B/px) and writes
+    32 FP16 channels (64 B/px); layers 1-3 read and write 64 B/px; layer 4 reads 64 B/px and writes the
+    FP32 map (4 B/px)."""
+    return (4 * C + 64 + 3 * 128 + 68) * H * W
+
+
+def run_cnn(args):
+    """The learned map's denoising forward (five tcgen05 convolutions) on a colour 3840x2160x3 image,
+    alone: its HBM roofline."""
+    import numpy as np
+    import torch
+
+    from paper_2512_23569_gb300 import build, hts, synth
+
+    build.build()
+    hts.load()
+    H, W, C = 2160, 3840, 3
+    _, noisy, _ = synth.make_varying_noise_image(H, W, C, 6500)
+    x = torch.from_numpy(noisy).cuda()
+    net = hts.Cnn(C, seed=1)
+    out = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    lib = hts.load()
+    import ctypes
+
+    def step():
+        hts._check(lib.hts_cnn_log_sigma_map(net.handle, ctypes.c_void_p(x.data_ptr()), H, W,
+                                             ctypes.c_void_p(out.data_ptr()), hts._stream(stream)))
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = hts.launch_count()
+    hts.profile_begin()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    prof = hts.profile_end()
+    torch.cuda.synchronize()
+    launches = hts.launch_count() - l0
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    conv_ms = prof["k_conv_tc"][0] / args.steps
+    peaks = _peaks()
+    nbytes = conv_tc_bytes(H, W, C)
+    ach = nbytes / (conv_ms / 1e3) / 1e9
+    line = {
+        "metric": "Mpixel/s of the noise-level network's denoising forward on 1 GB300",
+        "value": H * W / (ms / 1e3) / 1e6, "unit": "Mpixel/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16 operands / f32 accumulate", "data": "synthetic",
+        "config": {"workload": "colour 3840x2160x3 (Poisson-Gaussian, varying sigma_b), 5-layer 3x3 network "
+                               "(32 channels), random He-initialised weights", "seed": 6500,
+                   "l2": "flushed between steps (512 MB write outside the timed events)"},
+        "roofline": {"kernel": "k_conv_tc", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                     "algorithmic": "%d B/px over the 5 layers (%.2f GB per forward), over their summed time"
+                                    % (nbytes // (H * W), nbytes / 1e9),
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+        "tensor_flops": {"issued_tflops": 2 * 9 * H * W * (16 * 32 + 3 * 32 * 32 + 32 * 16)
+                         / (conv_ms / 1e3) / 1e12, "note": "MMA flops issued (K padded to 16, N to 16 in the last layer)"},
+        "clocks": clk, "gpu_launches": int(launches),
+        "kernels": {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1] // args.steps}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------------ arms
 
 def run_reference(args):
@@ -770,9 +848,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["colour512", "batch64", "precision1024", "learned"], default="colour512",
+    ap.add_argument("--workload", choices=["colour512", "batch64", "precision1024", "learned", "cnn"],
+                    default="colour512",
                     help="batch64: the 64-image batched form; precision1024: the BF16 precision form; learned: "
-                         "the learned noise-level map on 3840x2160x3 (each prints one JSON line of its own)")
+                         "the learned noise-level map on 3840x2160x3; cnn: its network forward alone "
+                         "(each prints one JSON line of its own)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -782,6 +862,8 @@ def main():
         return run_precision(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "cnn":
+        return run_cnn(args)
     return run_ours(args)
 
 
