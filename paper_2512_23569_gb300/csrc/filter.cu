@@ -30,16 +30,22 @@
 #include <mutex>
 #include <vector>
 
+#include "filter_common.h"
 #include "hts_internal.h"
 
 namespace hts {
 namespace {
 
+using fc::fix16;
+using fc::fix16_split;
+using fc::haar_fwd;
+using fc::haar_inv;
+using fc::K3F;
+using fc::R2F;
+using fc::S3H;
+
 constexpr float U32 = 5.9604644775390625e-08f;  // 2^-24
 constexpr unsigned FULL = 0xffffffffu;
-constexpr float R2F = 0.70710678118654752f;     // 1/sqrt(2)
-constexpr float K3F = 0.57735026918962576f;     // 1/sqrt(3)
-constexpr float S3H = 0.86602540378443865f;     // sqrt(3)/2
 constexpr int QCAP = 64;                        // in-band queue of the exact pass
 
 // Basis in shared memory, float32: for slice 0 U, V, U^T, V^T (row-major
@@ -270,40 +276,6 @@ __device__ __forceinline__ void inv_cplx(float (&Sr)[64], float (&Si)[64], const
     }
 }
 
-// --------------------------------------------------------- Haar (Eq. 8)
-
-// Forward: output row order of Eq. 8 (row 0 = sum / sqrt K, then the
-// coarse-to-fine difference rows, the finest K/2 differences last).
-template <int K>
-__device__ __forceinline__ void haar_fwd(float (&x)[K]) {
-#pragma unroll
-    for (int n = K; n >= 2; n >>= 1) {
-        float t[K];
-#pragma unroll
-        for (int i = 0; i < n / 2; ++i) {
-            t[i] = (x[2 * i] + x[2 * i + 1]) * R2F;
-            t[n / 2 + i] = (x[2 * i] - x[2 * i + 1]) * R2F;
-        }
-#pragma unroll
-        for (int i = 0; i < n; ++i) x[i] = t[i];
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void haar_inv(float (&x)[K]) {
-#pragma unroll
-    for (int n = 2; n <= K; n <<= 1) {
-        float t[K];
-#pragma unroll
-        for (int i = 0; i < n / 2; ++i) {
-            t[2 * i] = (x[i] + x[n / 2 + i]) * R2F;
-            t[2 * i + 1] = (x[i] - x[n / 2 + i]) * R2F;
-        }
-#pragma unroll
-        for (int i = 0; i < n; ++i) x[i] = t[i];
-    }
-}
-
 // Entry (h, k) of the Haar matrix of Eq. 8, in FP64.
 __device__ __forceinline__ double haar_entry(int K, int h, int k) {
     if (h == 0) return rsqrt((double)K);
@@ -407,30 +379,6 @@ struct Cfg {
     static constexpr int NCOEF = (C == 3) ? 192 : 64;  // real streams per patch
     static constexpr int IPG = (C == 3) ? 128 : 64;    // stream items per group (complex pairs count once)
 };
-
-// Fixed-point aggregation: value * 2^16 rounded to int64 (|value| < 2^31).
-__device__ __forceinline__ long long fix16(float v) { return __float2ll_rn(v * 65536.0f); }
-
-// The same fixed-point value split as hi * 2^16 + lo, with |lo| <= 2^15 (fast
-// path) or 0 <= lo < 2^16, for the tile's 32-bit shared sums.  For |v| < 2^22
-// it needs no 64-bit conversion: adding 1.5 * 2^23 rounds to the nearest
-// integer (ties to even) and leaves it in the low mantissa bits, for the
-// integer part and again for the 16-bit fraction; both steps are exact, so
-// hi * 2^16 + lo == fix16(v).
-__device__ __forceinline__ void fix16_split(float v, int &hi, int &lo) {
-    constexpr float MAGIC = 12582912.0f;  // 1.5 * 2^23
-    constexpr int MAGIC_BITS = 0x4B400000;
-    if (fabsf(v) < 4194304.0f) {
-        const float t = v + MAGIC;
-        hi = __float_as_int(t) - MAGIC_BITS;
-        const float f = v - (t - MAGIC);  // v - round(v), exact
-        lo = __float_as_int(fmaf(f, 65536.0f, MAGIC)) - MAGIC_BITS;
-    } else {
-        const long long q = fix16(v);
-        hi = (int)(q >> 16);
-        lo = (int)(q & 0xffff);
-    }
-}
 
 // ---------------------------------------------------------- exact pass
 
@@ -1472,6 +1420,17 @@ std::vector<int> tune_key(const Geom &g) {
     return {dev, g.H, g.W, g.C, g.K, g.R, g.step};
 }
 
+hts_status launch_normalize(const long long *acc, const int *wcount, float *out, size_t HW, int C, int nsm,
+                            cudaStream_t s) {
+    int nb = (int)((HW * C + 255) / 256);
+    if (nb > nsm * 16) nb = nsm * 16;
+    {
+        KTimer kt("k_normalize", s);
+        k_normalize<<<nb, 256, 0, s>>>(acc, wcount, out, HW, C);
+    }
+    return check_launch("k_normalize");
+}
+
 template <int C, int K>
 hts_status launch_ck(const FilterArgs &a, const Geom &g, float *out, cudaStream_t s) {
     const size_t HW = (size_t)a.H * a.W;
@@ -1524,13 +1483,7 @@ hts_status launch_ck(const FilterArgs &a, const Geom &g, float *out, cudaStream_
         st = check_launch("k_filter_fix");
         if (st != HTS_OK) return st;
     }
-    int nb = (int)((HW * C + 255) / 256);
-    if (nb > nsm * 16) nb = nsm * 16;
-    {
-        KTimer kt("k_normalize", s);
-        k_normalize<<<nb, 256, 0, s>>>(a.acc, a.wcount, out, HW, C);
-    }
-    return check_launch("k_normalize");
+    return launch_normalize(a.acc, a.wcount, out, HW, C, nsm, s);
 }
 
 }  // namespace
@@ -1592,6 +1545,18 @@ hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, co
     a.map_judged = map_judged;
     a.xskip = xskip;
     a.st = st;
+    if (!exact) {  // precision form: the tensor-core filter where a tile fits
+        bool used = false;
+        const hts_status st0 =
+            launch_filter_tc(img, g, idx, b32, acc, wcount, st, sigma_ref, map_judged, tau_scale, s, &used);
+        if (st0 != HTS_OK) return st0;
+        if (used) {
+            int dev = 0, nsm = 152;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            return launch_normalize(acc, wcount, out, (size_t)g.H * g.W, g.C, nsm, s);
+        }
+    }
 #define HTS_FILTER_CASE(CC, KK) \
     if (g.C == CC && g.K == KK) return launch_ck<CC, KK>(a, g, out, s);
     HTS_FILTER_CASE(1, 2) HTS_FILTER_CASE(1, 4) HTS_FILTER_CASE(1, 8) HTS_FILTER_CASE(1, 16) HTS_FILTER_CASE(1, 32)

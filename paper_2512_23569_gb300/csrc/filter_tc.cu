@@ -1,0 +1,518 @@
+// Collaborative filtering of the precision form on the sm_103a tensor cores
+// (Eq. 19-21, Alg. 1 steps 2-3), FP32 threshold decisions.
+//
+// The separable projection Shat = U^H Phat V of one Fourier slice (Eq. 19) is
+// one 64 x 64 matrix applied to the patch read as a vector:
+//   vec(S)[(a,b)] = sum_(i,j) conj(U[i][a]) V[j][b] vec(Phat)[(i,j)],
+// so a batch of 128 group members (8 groups of K = 16) is one GEMM per slice
+// with the members as the MMA's M = 128 rows: D[m][coefficient] =
+// sum_pixel A[m][pixel] B[coefficient][pixel], FP16 operands, FP32
+// accumulation in tensor memory (tcgen05.mma kind::f16).  Slice 0 is real
+// (N = 64); slice 1 is complex and runs as two real GEMMs with N = 128,
+// [Re S | Im S] = Re Phat [Mr | Mi]^T + Im Phat [-Mi | Mr]^T.  The inverse
+// (Eq. 21) is the conjugate transpose, the same shape of GEMM.  Between the
+// two, the coefficients go through shared memory (transposed, FP32) so that
+// one thread holds a coefficient stream of a group: Haar along the group axis
+// (Eq. 8), hard threshold (Eq. 20, modulus for the complex slice, the group's
+// tau), inverse Haar; then FP16 again as the inverse GEMM's A operand.  The
+// channel DFT (before) and its inverse (after, with the aggregation) run on
+// the CUDA cores.
+//
+// FP16 rather than BF16: pixels lie in a bounded range and the bases are
+// orthonormal, so FP16's 11-bit significand fits the data, where BF16's 8
+// bits would put a rounding error of up to one grey level on the input.
+//
+// Aggregation as in the SIMT filter: exact fixed-point integer sums of the
+// estimates in shared-memory accumulators over the tile's region, flushed
+// to the image-wide int64 sums once per tile (deterministic).  The MMA waits
+// are bounded: a wait that gives up records DevState.error = 2, waits
+// (bounded) for the MMAs, frees the tensor memory and leaves.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "filter_common.h"
+#include "hts_internal.h"
+#include "tc_ptx.h"
+
+namespace hts {
+namespace {
+
+using fc::fix16_split;
+using fc::haar_fwd;
+using fc::haar_inv;
+using fc::K3F;
+using fc::S3H;
+
+constexpr int NT = 256;   // 8 warps: warp w reads tensor-memory lanes 32 (w % 4) .. + 31
+constexpr int MB = 128;   // group members per batch = MMA M
+constexpr int TS = MB + 4;  // row stride (floats) of the transpose buffer: conflict-free float4 reads
+constexpr long long SPIN = 1ll << 24;
+
+// Offset (in halves) of element (r, k) of a K-major FP16 operand block of 64
+// columns, no swizzle: core matrices of 8 rows x 8 columns (128 B), 8-column
+// groups 128 B apart (LBO), 8-row groups 1024 B apart (SBO).
+__device__ __forceinline__ int cm_off(int r, int k) { return (((r >> 3) << 3) + (k >> 3)) * 64 + ((r & 7) << 3) + (k & 7); }
+
+template <int C>
+struct FtcLayout {
+    static constexpr int NBLK = (C == 3) ? 3 : 1;  // 64-column blocks of the member operand
+    // FP16 Kronecker matrices (halves): C == 3: B0 [64][64], B1 [128][64], B2 [128][64] (forward),
+    // B0i [64][64], B3 [128][64], B4 [128][64] (inverse); C == 1: B0, B0i
+    static constexpr int B0 = 0;
+    static constexpr int B1 = 64 * 64;
+    static constexpr int B2 = B1 + 128 * 64;
+    static constexpr int B0I = (C == 3) ? B2 + 128 * 64 : 64 * 64;
+    static constexpr int B3 = B0I + 64 * 64;
+    static constexpr int B4 = B3 + 128 * 64;
+    static constexpr int B_HALVES = (C == 3) ? B4 + 128 * 64 : 2 * 64 * 64;
+    static constexpr size_t a_off = 0;                               // [NBLK][128][64] FP16
+    static constexpr size_t b_off = a_off + (size_t)NBLK * MB * 64 * 2;
+    static constexpr size_t t_off = b_off + (size_t)B_HALVES * 2;    // [32][TS] FP32
+    static constexpr size_t basis_off = t_off + (size_t)32 * TS * 4;  // 6 x 64 FP32
+    static constexpr size_t misc_off = basis_off + (size_t)6 * 64 * 4;
+    // misc: pos[MB] int, ref[32] int, tau[32] float, 2 mbarrier words, tensor-memory slot
+    static constexpr size_t acc_off = misc_off + (size_t)MB * 4 + 32 * 4 + 32 * 4 + 16 + 16;
+    static constexpr uint32_t tcols = (C == 3) ? 256 : 64;
+};
+
+struct FtcArgs {
+    const float *img;
+    int H, W, step, R, nx, ny;
+    const int32_t *idx;
+    const float *b32;
+    long long *acc;
+    int *wcount;
+    const float *sigma_ref;
+    int map_judged;
+    double tau_scale;
+    DevState *st;
+    int ty, tx, nty, ntx, ntiles, rh_max, rw_max;
+};
+
+template <int C, int K>
+__global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
+    using L = FtcLayout<C>;
+    constexpr int GPB = MB / K;  // groups per batch
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __half *sA = reinterpret_cast<__half *>(smem + L::a_off);
+    __half *sB = reinterpret_cast<__half *>(smem + L::b_off);
+    float *sT = reinterpret_cast<float *>(smem + L::t_off);
+    float *sBas = reinterpret_cast<float *>(smem + L::basis_off);
+    int *sPos = reinterpret_cast<int *>(smem + L::misc_off);
+    int *sRef = sPos + MB;
+    float *sTau = reinterpret_cast<float *>(sRef + 32);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sTau + 32);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
+    int *accs = reinterpret_cast<int *>(smem + L::acc_off);
+    const int RA = a.rh_max * a.rw_max;
+    int *acc_hi = accs, *acc_lo = accs + C * RA, *acc_w = accs + 2 * C * RA;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const size_t HW = (size_t)a.H * a.W;
+    const bool use_map = a.sigma_ref && (!a.map_judged || a.st->learned);
+
+    // ---- bases (row-major 8x8, element (r, c) at r * 8 + c) and the Kronecker matrices
+    for (int t = tid; t < 64; t += NT) {
+        sBas[t] = a.b32[(0 * 64 + t) * 2];        // U0
+        sBas[64 + t] = a.b32[(1 * 64 + t) * 2];   // V0
+        if (C == 3) {
+            sBas[128 + t] = a.b32[(2 * 64 + t) * 2];      // U1 re
+            sBas[192 + t] = a.b32[(2 * 64 + t) * 2 + 1];  // U1 im
+            sBas[256 + t] = a.b32[(3 * 64 + t) * 2];      // V1 re
+            sBas[320 + t] = a.b32[(3 * 64 + t) * 2 + 1];  // V1 im
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < 64 * 64; e += NT) {
+        const int n = e >> 6, k = e & 63;  // n = coefficient (a, b), k = pixel (i, j)
+        const int ia = (k >> 3) * 8 + (n >> 3), jb = (k & 7) * 8 + (n & 7);
+        const float m0 = sBas[ia] * sBas[64 + jb];  // U0[i][a] V0[j][b]
+        sB[L::B0 + cm_off(n, k)] = __float2half_rn(m0);
+        sB[L::B0I + cm_off(k, n)] = __float2half_rn(m0);
+        if (C == 3) {
+            const float ur = sBas[128 + ia], ui = sBas[192 + ia], vr = sBas[256 + jb], vi = sBas[320 + jb];
+            const float mr = ur * vr + ui * vi, mi = ur * vi - ui * vr;  // conj(U1[i][a]) V1[j][b]
+            sB[L::B1 + cm_off(n, k)] = __float2half_rn(mr);
+            sB[L::B1 + cm_off(64 + n, k)] = __float2half_rn(mi);
+            sB[L::B2 + cm_off(n, k)] = __float2half_rn(-mi);
+            sB[L::B2 + cm_off(64 + n, k)] = __float2half_rn(mr);
+            sB[L::B3 + cm_off(k, n)] = __float2half_rn(mr);
+            sB[L::B3 + cm_off(64 + k, n)] = __float2half_rn(-mi);
+            sB[L::B4 + cm_off(k, n)] = __float2half_rn(mi);
+            sB[L::B4 + cm_off(64 + k, n)] = __float2half_rn(mr);
+        }
+    }
+    if (tid == 0) {
+        tc::bar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) tc::tmem_alloc(slot, L::tcols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = *slot;
+    const uint32_t id64 = tc::idesc_f16(MB, 64, false), id128 = tc::idesc_f16(MB, 128, false);
+    const int q = warp & 3, hh = warp >> 2;  // tensor-memory lane quarter, column half
+    const uint32_t tlane = (uint32_t)(32 * q) << 16;
+    uint32_t phase = 0;
+    bool ok = true;
+
+    // issue the MMAs of one GEMM stage and wait for them; false if the wait gave up
+    auto run_stage = [&](bool inverse) -> bool {
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after();
+            const uint32_t a0 = tc::su32(sA), b0 = tc::su32(sB);
+            const int bs = inverse ? L::B0I : L::B0;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                tc::mma_f16(tbase, tc::sdesc(a0 + kk * 256, 128, 1024), tc::sdesc(b0 + bs * 2 + kk * 256, 128, 1024),
+                            id64, kk > 0 ? 1u : 0u);
+            if (C == 3) {
+                const int b1 = inverse ? L::B3 : L::B1, b2 = inverse ? L::B4 : L::B2;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    tc::mma_f16(tbase + 64, tc::sdesc(a0 + MB * 64 * 2 + kk * 256, 128, 1024),
+                                tc::sdesc(b0 + b1 * 2 + kk * 256, 128, 1024), id128, kk > 0 ? 1u : 0u);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    tc::mma_f16(tbase + 64, tc::sdesc(a0 + 2 * MB * 64 * 2 + kk * 256, 128, 1024),
+                                tc::sdesc(b0 + b2 * 2 + kk * 256, 128, 1024), id128, 1u);
+            }
+            tc::mma_commit(bar);
+        }
+        const bool done = tc::bar_wait(bar, phase, SPIN);
+        if (__syncthreads_or(!done)) {
+            if (tid == 0) {
+                tc::bar_wait(bar, phase, SPIN);  // the MMAs must end before the memory is released
+                atomicExch(&a.st->error, 2);
+            }
+            return false;
+        }
+        phase ^= 1u;
+        tc::fence_after();
+        return true;
+    };
+
+    const int gpt = a.ty * a.tx;
+    const int nbatch = (gpt + GPB - 1) / GPB;
+    for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+        const int tyi = tile / a.ntx, txi = tile - tyi * a.ntx;
+        const int gy0 = tyi * a.ty, gx0 = txi * a.tx;
+        const int gy1 = min(a.ny, gy0 + a.ty) - 1, gx1 = min(a.nx, gx0 + a.tx) - 1;
+        const int Y0 = grid_pos(gy0, a.H, a.step), Y1 = grid_pos(gy1, a.H, a.step);
+        const int X0 = grid_pos(gx0, a.W, a.step), X1 = grid_pos(gx1, a.W, a.step);
+        const int ry0 = max(0, Y0 - a.R), ry1 = min(a.H - 1, Y1 + a.R + PS - 1);
+        const int rx0 = max(0, X0 - a.R), rx1 = min(a.W - 1, X1 + a.R + PS - 1);
+        const int rh = ry1 - ry0 + 1, rw = rx1 - rx0 + 1;
+        for (int e = tid; e < (2 * C + 1) * RA; e += NT) accs[e] = 0;
+        __syncthreads();
+        for (int b = 0; b < nbatch; ++b) {
+            // ---- the batch's groups and members
+            if (tid < GPB) {
+                const int lg = b * GPB + tid;
+                const int gy = gy0 + lg / a.tx, gx = gx0 + lg % a.tx;
+                const bool valid = lg < gpt && gy <= gy1 && gx <= gx1;
+                const int r = valid ? gy * a.nx + gx : -1;
+                sRef[tid] = r;
+                sTau[tid] = !valid ? 0.f
+                            : use_map ? (float)(a.tau_scale * (double)a.sigma_ref[r])
+                                      : a.st->tau32;
+            }
+            __syncthreads();
+            // ---- gather: member m = tid / 2, patch rows 4 (tid & 1) .. + 3; Fourier slices of the
+            //      channel axis (unitary DFT), FP16, into the operand's row m
+            {
+                const int m = tid >> 1, h = tid & 1;
+                const int g = m / K, k = m - g * K;
+                const int r = sRef[g];
+                const int pos = r >= 0 ? a.idx[(size_t)r * K + k] : -1;
+                if (h == 0) sPos[m] = pos;
+                const int py = pos >= 0 ? pos / a.W : 0, px = pos >= 0 ? pos - py * a.W : 0;
+#pragma unroll
+                for (int rr = 0; rr < 4; ++rr) {
+                    const int row = 4 * h + rr;
+                    __align__(16) __half v0[8], v1[8], v2[8];
+                    const float *src = a.img + (size_t)(py + row) * a.W + px;
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) {
+                        if constexpr (C == 1) {
+                            v0[v] = __float2half_rn(pos >= 0 ? __ldg(src + v) : 0.f);
+                        } else {
+                            float R = 0.f, G = 0.f, B = 0.f;
+                            if (pos >= 0) {
+                                R = __ldg(src + v);
+                                G = __ldg(src + HW + v);
+                                B = __ldg(src + 2 * HW + v);
+                            }
+                            v0[v] = __float2half_rn(((R + G) + B) * K3F);
+                            v1[v] = __float2half_rn((R - 0.5f * (G + B)) * K3F);
+                            v2[v] = __float2half_rn((B - G) * 0.5f);
+                        }
+                    }
+                    *reinterpret_cast<uint4 *>(sA + cm_off(m, row * 8)) = *reinterpret_cast<const uint4 *>(v0);
+                    if constexpr (C == 3) {
+                        *reinterpret_cast<uint4 *>(sA + MB * 64 + cm_off(m, row * 8)) =
+                            *reinterpret_cast<const uint4 *>(v1);
+                        *reinterpret_cast<uint4 *>(sA + 2 * MB * 64 + cm_off(m, row * 8)) =
+                            *reinterpret_cast<const uint4 *>(v2);
+                    }
+                }
+            }
+            // ---- forward projection (Eq. 19): D[m] = [S0 | Re S1 | Im S1]
+            if (!run_stage(false)) {
+                ok = false;
+                break;
+            }
+            // ---- per 32-column chunk: tensor memory -> transposed FP32 buffer, Haar + threshold +
+            //      inverse Haar per (group, coefficient) stream, FP16 into the inverse's operand.
+            //      Chunks 0, 1: S0 columns [32 ch, + 32); chunks 2..5: complex coefficients
+            //      c0 = 16 (ch - 2) .. + 15, real parts (columns 64 + c) as local columns 0..15,
+            //      imaginary parts (128 + c) as 16..31.
+            constexpr int NCHUNK = (C == 3) ? 6 : 2;
+#pragma unroll 1
+            for (int ch = 0; ch < NCHUNK; ++ch) {
+                const bool cplx = ch >= 2;
+                const int c0 = 16 * (ch - 2);
+                const int col0 = !cplx ? 32 * ch + 16 * hh : (hh == 0 ? 64 + c0 : 128 + c0);
+                {
+                    uint32_t v[16];
+                    tc::tmem_ld16(tbase + tlane + (uint32_t)col0, v);
+                    tc::tmem_wait_ld();
+                    const int m = 32 * q + lane;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) sT[(16 * hh + j) * TS + m] = __uint_as_float(v[j]);
+                }
+                __syncthreads();
+                if (!cplx) {  // real streams: 32 coefficients x GPB groups
+                    for (int s = tid; s < 32 * GPB; s += NT) {
+                        const int c = s & 31, g = s >> 5;
+                        if (sRef[g] < 0) continue;
+                        const float tau = sTau[g];
+                        float *p = sT + c * TS + g * K;
+                        float x[K];
+#pragma unroll
+                        for (int k = 0; k < K; k += 4) {
+                            const float4 t4 = *reinterpret_cast<const float4 *>(p + k);
+                            x[k] = t4.x;
+                            x[k + 1] = t4.y;
+                            x[k + 2] = t4.z;
+                            x[k + 3] = t4.w;
+                        }
+                        haar_fwd<K>(x);
+#pragma unroll
+                        for (int k = 0; k < K; ++k)
+                            if (!(fabsf(x[k]) >= tau)) x[k] = 0.f;
+                        haar_inv<K>(x);
+#pragma unroll
+                        for (int k = 0; k < K; k += 4)
+                            *reinterpret_cast<float4 *>(p + k) = make_float4(x[k], x[k + 1], x[k + 2], x[k + 3]);
+                    }
+                } else {  // complex streams: 16 coefficients x GPB groups (real part c, imaginary c + 16)
+                    for (int s = tid; s < 16 * GPB; s += NT) {
+                        const int c = s & 15, g = s >> 4;
+                        if (sRef[g] < 0) continue;
+                        const float tau = sTau[g];
+                        float *pr = sT + c * TS + g * K, *pi = sT + (c + 16) * TS + g * K;
+                        float xr[K], xi[K];
+#pragma unroll
+                        for (int k = 0; k < K; k += 4) {
+                            const float4 r4 = *reinterpret_cast<const float4 *>(pr + k);
+                            const float4 i4 = *reinterpret_cast<const float4 *>(pi + k);
+                            xr[k] = r4.x;
+                            xr[k + 1] = r4.y;
+                            xr[k + 2] = r4.z;
+                            xr[k + 3] = r4.w;
+                            xi[k] = i4.x;
+                            xi[k + 1] = i4.y;
+                            xi[k + 2] = i4.z;
+                            xi[k + 3] = i4.w;
+                        }
+                        haar_fwd<K>(xr);
+                        haar_fwd<K>(xi);
+#pragma unroll
+                        for (int k = 0; k < K; ++k)
+                            if (!(sqrtf(xr[k] * xr[k] + xi[k] * xi[k]) >= tau)) {
+                                xr[k] = 0.f;
+                                xi[k] = 0.f;
+                            }
+                        haar_inv<K>(xr);
+                        haar_inv<K>(xi);
+#pragma unroll
+                        for (int k = 0; k < K; k += 4) {
+                            *reinterpret_cast<float4 *>(pr + k) = make_float4(xr[k], xr[k + 1], xr[k + 2], xr[k + 3]);
+                            *reinterpret_cast<float4 *>(pi + k) = make_float4(xi[k], xi[k + 1], xi[k + 2], xi[k + 3]);
+                        }
+                    }
+                }
+                __syncthreads();
+                // FP16 into the inverse GEMM's operand: member m, 8 consecutive local columns 8 jg ..
+                for (int it = tid; it < MB * 4; it += NT) {
+                    const int m = it & (MB - 1), jg = it >> 7;
+                    const int gc = !cplx ? 32 * ch + 8 * jg : (jg < 2 ? 64 + c0 + 8 * jg : 128 + c0 + 8 * (jg - 2));
+                    __align__(16) __half hv[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) hv[e] = __float2half_rn(sT[(8 * jg + e) * TS + m]);
+                    *reinterpret_cast<uint4 *>(sA + (gc >> 6) * (MB * 64) + cm_off(m, gc & 63)) =
+                        *reinterpret_cast<const uint4 *>(hv);
+                }
+                tc::fence_before();
+                __syncthreads();
+            }
+            // ---- inverse projection (Eq. 21): D[m] = [Phat0 | Re Phat1 | Im Phat1]
+            if (!run_stage(true)) {
+                ok = false;
+                break;
+            }
+            // ---- inverse DFT along the channels and aggregation: member m = 32 q + lane, patch rows
+            //      4 hh .. 4 hh + 3
+            {
+                const int m = 32 * q + lane;
+                const int pos = sPos[m];
+                const int py = pos >= 0 ? pos / a.W : 0, px = pos >= 0 ? pos - py * a.W : 0;
+#pragma unroll 1
+                for (int rr = 0; rr < 4; ++rr) {
+                    const int row = 4 * hh + rr;
+                    uint32_t p0[8], p1[8] = {}, p2[8] = {};
+                    tc::tmem_ld8(tbase + tlane + (uint32_t)(row * 8), p0);
+                    if constexpr (C == 3) {
+                        tc::tmem_ld8(tbase + tlane + (uint32_t)(64 + row * 8), p1);
+                        tc::tmem_ld8(tbase + tlane + (uint32_t)(128 + row * 8), p2);
+                    }
+                    tc::tmem_wait_ld();
+                    if (pos < 0) continue;
+                    float out[C][8];
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) {
+                        const float f0 = __uint_as_float(p0[v]);
+                        if constexpr (C == 1) {
+                            out[0][v] = f0;
+                        } else {
+                            const float fr = __uint_as_float(p1[v]), fi = __uint_as_float(p2[v]);
+                            out[0][v] = (f0 + 2.f * fr) * K3F;
+                            out[1][v] = (f0 - fr - 2.f * S3H * fi) * K3F;
+                            out[2][v] = (f0 - fr + 2.f * S3H * fi) * K3F;
+                        }
+                    }
+                    const int ly = py + row - ry0, lx = px - rx0;
+                    if (ly >= 0 && ly < rh && lx >= 0 && lx + 7 < rw) {
+                        const int o = ly * rw + lx;
+#pragma unroll
+                        for (int v = 0; v < 8; ++v) {
+#pragma unroll
+                            for (int c = 0; c < C; ++c) {
+                                int qh, ql;
+                                fix16_split(out[c][v], qh, ql);
+                                atomicAdd(acc_hi + c * RA + o + v, qh);
+                                atomicAdd(acc_lo + c * RA + o + v, ql);
+                            }
+                            atomicAdd(acc_w + o + v, 1);
+                        }
+                    } else {
+                        atomicExch(&a.st->error, 1);
+                    }
+                }
+            }
+            tc::fence_before();
+            __syncthreads();
+        }
+        if (!ok) break;
+        // flush the tile's sums to the image-wide int64 sums
+        for (int e = tid; e < rh * rw; e += NT) {
+            const int w = acc_w[e];
+            if (w == 0) continue;
+            const int yy = e / rw, xx = e - yy * rw;
+            const size_t gpix = (size_t)(ry0 + yy) * a.W + (rx0 + xx);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const long long s = (long long)acc_hi[c * RA + e] * 65536ll + (long long)acc_lo[c * RA + e];
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + c * HW + gpix), (unsigned long long)s);
+            }
+            atomicAdd(a.wcount + gpix, w);
+        }
+        __syncthreads();
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, L::tcols);
+}
+
+constexpr int NSHAPES_TC = 7;
+constexpr int SHAPES_TC[NSHAPES_TC][2] = {{8, 8}, {4, 8}, {4, 4}, {2, 4}, {2, 2}, {1, 2}, {1, 1}};
+
+template <int C, int K>
+hts_status launch_ftc(FtcArgs a, const Geom &g, cudaStream_t s, bool *used) {
+    using L = FtcLayout<C>;
+    const size_t budget = std::min((size_t)smem_optin(), (size_t)227 * 1024);
+    size_t need = 0;
+    int ty = 0, tx = 0, rh = 0, rw = 0;
+    for (int i = 0; i < NSHAPES_TC; ++i) {
+        const int h = std::min(g.H, (SHAPES_TC[i][0] - 1) * g.step + 2 * g.R + PS);
+        const int w = std::min(g.W, (SHAPES_TC[i][1] - 1) * g.step + 2 * g.R + PS);
+        const size_t n = L::acc_off + (size_t)(2 * C + 1) * h * w * 4;
+        if (n <= budget) {
+            ty = SHAPES_TC[i][0];
+            tx = SHAPES_TC[i][1];
+            rh = h;
+            rw = w;
+            need = n;
+            break;
+        }
+    }
+    *used = false;
+    if (ty == 0) return HTS_OK;  // the window is too large for a tile: the SIMT filter takes it
+    const void *k = reinterpret_cast<const void *>(k_filter_tc<C, K>);
+    const hts_status st = allow_smem(k, need);
+    if (st != HTS_OK) return st;
+    a.ty = ty;
+    a.tx = tx;
+    a.nty = (g.ny + ty - 1) / ty;
+    a.ntx = (g.nx + tx - 1) / tx;
+    a.ntiles = a.nty * a.ntx;
+    a.rh_max = rh;
+    a.rw_max = rw;
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(a.ntiles, nsm));
+    {
+        KTimer kt("k_filter_tc", s);
+        k_filter_tc<C, K><<<grid, NT, need, s>>>(a);
+    }
+    *used = true;
+    return check_launch("k_filter_tc");
+}
+
+}  // namespace
+
+hts_status launch_filter_tc(const float *img, const Geom &g, const int32_t *idx, const float *b32, long long *acc,
+                            int *wcount, DevState *st, const float *sigma_ref, int map_judged, double tau_scale,
+                            cudaStream_t s, bool *used) {
+    *used = false;
+    FtcArgs a{};
+    a.img = img;
+    a.H = g.H;
+    a.W = g.W;
+    a.step = g.step;
+    a.R = g.R;
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.idx = idx;
+    a.b32 = b32;
+    a.acc = acc;
+    a.wcount = wcount;
+    a.sigma_ref = sigma_ref;
+    a.map_judged = map_judged;
+    a.tau_scale = tau_scale;
+    a.st = st;
+#define HTS_FTC_CASE(CC, KK) \
+    if (g.C == CC && g.K == KK) return launch_ftc<CC, KK>(a, g, s, used);
+    HTS_FTC_CASE(1, 8) HTS_FTC_CASE(1, 16) HTS_FTC_CASE(1, 32) HTS_FTC_CASE(3, 8) HTS_FTC_CASE(3, 16)
+    HTS_FTC_CASE(3, 32)
+#undef HTS_FTC_CASE
+    return HTS_OK;  // other group sizes: the SIMT filter
+}
+
+}  // namespace hts

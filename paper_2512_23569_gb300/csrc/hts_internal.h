@@ -140,6 +140,13 @@ hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, co
                          DevState *st, float *out, int exact, const float *sigma_ref, int map_judged,
                          double tau_scale, cudaStream_t s);
 double tau_scale(const Geom &g, const hts_params &p);  // sigma -> tau factor (sigma.cu)
+// Tensor-core filter of the precision form (filter_tc.cu): FP16 Kronecker
+// projections on tcgen05, FP32 decisions, tile aggregation into acc / wcount
+// (no normalisation).  *used = false (and nothing launched) where the group
+// size or the window does not fit it.
+hts_status launch_filter_tc(const float *img, const Geom &g, const int32_t *idx, const float *b32, long long *acc,
+                            int *wcount, DevState *st, const float *sigma_ref, int map_judged, double tau_scale,
+                            cudaStream_t s, bool *used);
 
 // Filter tile shape (k_filter_tile): ty x tx reference positions per tile,
 // ty = 0 for the non-local mode (no tile accumulators).  The launch uses, in

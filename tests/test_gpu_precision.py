@@ -1,11 +1,13 @@
-"""Precision form of the grouping (BF16 tensor-core distances, FP32 re-rank of the 2K nearest).
+"""Precision form: grouping by BF16 tensor-core distances with an FP32 re-rank of the 2K nearest,
+filtering with FP16 tensor-core projections and FP32 threshold decisions.
 
 Its groups are not bit-exact by design: BF16 rounding may reorder near
 neighbours.  What is checked: every group is valid (the reference first, K
 distinct members inside its search window, the K-1 others in ascending FP32
-distance), nearly all groups equal the FP64 definition's, and the denoised
+distance), nearly all groups equal the FP64 definition's, the denoised
 image is within 0.05 dB PSNR of the FP64 oracle, on AWGN and on
-spatially correlated Poisson-Gaussian noise.
+spatially correlated Poisson-Gaussian noise, and the tensor-core filter
+gives the image back at a zero threshold and zero at a huge one.
 """
 
 import numpy as np
@@ -101,3 +103,20 @@ def test_precision_validation(hts):
         hts.denoise(x, sigma=10.0, p=hts.params(precision=2))
     with pytest.raises(hts.HtsError):  # 63x63 window: the staged search region does not fit on chip
         hts.denoise(x, sigma=10.0, p=hts.params(win=63, precision=1))
+
+
+@pytest.mark.parametrize("C,K,win", [(1, 16, 21), (3, 16, 31), (3, 8, 15), (1, 32, 11), (3, 32, 11)])
+def test_tensor_core_filter_reconstructs_and_thresholds(hts, C, K, win):
+    # sigma = 0 keeps every coefficient: the FP16 forward and inverse projections must give the noisy
+    # image back up to their rounding (FP16 input: half a unit in the last place, 0.125 at 256, plus the
+    # FP16 coefficients); a huge sigma drops every coefficient: the output is exactly zero
+    clean, noisy = synth.make_config_image(70, 83, C, 20.0, 31 + C + K)
+    x = _dev(noisy)
+    p = hts.params(K=K, win=win, precision=1)
+    out = hts.denoise(x, sigma=0.0, p=p).cpu().numpy()
+    err = np.abs(out.astype(np.float64) - noisy.astype(np.float64))
+    assert np.max(err) <= 0.5
+    assert np.mean(err) <= 0.05
+    assert hts.last_stats()["tau"] == 0.0
+    zero = hts.denoise(x, sigma=1e6, p=p).cpu().numpy()
+    assert np.all(zero == 0.0)
