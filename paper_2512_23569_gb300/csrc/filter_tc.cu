@@ -22,9 +22,11 @@
 // orthonormal, so FP16's 11-bit significand fits the data, where BF16's 8
 // bits would put a rounding error of up to one grey level on the input.
 //
-// Aggregation as in the SIMT filter: exact fixed-point integer sums of the
-// estimates in shared-memory accumulators over the tile's region, flushed
-// to the image-wide int64 sums once per tile (deterministic).  The MMA waits
+// Aggregation: fixed-point integer sums (value * 2^8, rounded) of the
+// estimates in 32-bit shared-memory accumulators over the tile's region
+// (at most 2^10 members of a tile cover a pixel: no overflow), flushed to
+// the image-wide int64 sums (2^16 scale) once per tile; integer sums do not
+// depend on the order of the additions, so the result is deterministic.  The MMA waits
 // are bounded: a wait that gives up records DevState.error = 2, waits
 // (bounded) for the MMAs, frees the tensor memory and leaves.
 #include <cuda_fp16.h>
@@ -38,7 +40,6 @@
 namespace hts {
 namespace {
 
-using fc::fix16_split;
 using fc::haar_fwd;
 using fc::haar_inv;
 using fc::K3F;
@@ -71,8 +72,8 @@ struct FtcLayout {
     static constexpr size_t t_off = b_off + (size_t)B_HALVES * 2;    // [32][TS] FP32
     static constexpr size_t basis_off = t_off + (size_t)32 * TS * 4;  // 6 x 64 FP32
     static constexpr size_t misc_off = basis_off + (size_t)6 * 64 * 4;
-    // misc: pos[MB] int, ref[32] int, tau[32] float, 2 mbarrier words, tensor-memory slot
-    static constexpr size_t acc_off = misc_off + (size_t)MB * 4 + 32 * 4 + 32 * 4 + 16 + 16;
+    // misc, two buffers each: pos[MB] int, ref[32] int, tau[32] float; 2 mbarrier words, tensor-memory slot
+    static constexpr size_t acc_off = misc_off + (size_t)2 * (MB * 4 + 32 * 4 + 32 * 4) + 16 + 16;
     static constexpr uint32_t tcols = (C == 3) ? 256 : 64;
 };
 
@@ -99,14 +100,14 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
     __half *sB = reinterpret_cast<__half *>(smem + L::b_off);
     float *sT = reinterpret_cast<float *>(smem + L::t_off);
     float *sBas = reinterpret_cast<float *>(smem + L::basis_off);
-    int *sPos = reinterpret_cast<int *>(smem + L::misc_off);
-    int *sRef = sPos + MB;
-    float *sTau = reinterpret_cast<float *>(sRef + 32);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sTau + 32);
+    int *sPos = reinterpret_cast<int *>(smem + L::misc_off);  // [2][MB]
+    int *sRef = sPos + 2 * MB;                                 // [2][32]
+    float *sTau = reinterpret_cast<float *>(sRef + 64);        // [2][32]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sTau + 64);
     uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
     int *accs = reinterpret_cast<int *>(smem + L::acc_off);
     const int RA = a.rh_max * a.rw_max;
-    int *acc_hi = accs, *acc_lo = accs + C * RA, *acc_w = accs + 2 * C * RA;
+    int *acc_v = accs, *acc_w = accs + C * RA;  // [C][RA] sums of value * 2^8, [RA] counts
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t HW = (size_t)a.H * a.W;
     const bool use_map = a.sigma_ref && (!a.map_judged || a.st->learned);
@@ -207,64 +208,85 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
         const int ry0 = max(0, Y0 - a.R), ry1 = min(a.H - 1, Y1 + a.R + PS - 1);
         const int rx0 = max(0, X0 - a.R), rx1 = min(a.W - 1, X1 + a.R + PS - 1);
         const int rh = ry1 - ry0 + 1, rw = rx1 - rx0 + 1;
-        for (int e = tid; e < (2 * C + 1) * RA; e += NT) accs[e] = 0;
+        for (int e = tid; e < (C + 1) * RA; e += NT) accs[e] = 0;
         __syncthreads();
-        for (int b = 0; b < nbatch; ++b) {
-            // ---- the batch's groups and members
+        // ---- the groups and members of batch bb into buffer buf (sRef/sTau/sPos), then this thread's
+        //      member pixels into registers: the loads stay in flight while the previous batch is
+        //      filtered (member m = tid / 2, patch rows 4 (tid & 1) .. + 3)
+        float pf[C][4][8];
+        int pf_pos = -1;
+        auto setup = [&](int bb, int buf) {
             if (tid < GPB) {
-                const int lg = b * GPB + tid;
+                const int lg = bb * GPB + tid;
                 const int gy = gy0 + lg / a.tx, gx = gx0 + lg % a.tx;
                 const bool valid = lg < gpt && gy <= gy1 && gx <= gx1;
                 const int r = valid ? gy * a.nx + gx : -1;
-                sRef[tid] = r;
-                sTau[tid] = !valid ? 0.f
-                            : use_map ? (float)(a.tau_scale * (double)a.sigma_ref[r])
-                                      : a.st->tau32;
+                sRef[32 * buf + tid] = r;
+                sTau[32 * buf + tid] = !valid ? 0.f
+                                       : use_map ? (float)(a.tau_scale * (double)a.sigma_ref[r])
+                                                 : a.st->tau32;
             }
-            __syncthreads();
-            // ---- gather: member m = tid / 2, patch rows 4 (tid & 1) .. + 3; Fourier slices of the
-            //      channel axis (unitary DFT), FP16, into the operand's row m
-            {
-                const int m = tid >> 1, h = tid & 1;
-                const int g = m / K, k = m - g * K;
-                const int r = sRef[g];
-                const int pos = r >= 0 ? a.idx[(size_t)r * K + k] : -1;
-                if (h == 0) sPos[m] = pos;
-                const int py = pos >= 0 ? pos / a.W : 0, px = pos >= 0 ? pos - py * a.W : 0;
+        };
+        auto prefetch = [&](int buf) {
+            const int m = tid >> 1, h = tid & 1;
+            const int g = m / K, k = m - g * K;
+            const int r = sRef[32 * buf + g];
+            pf_pos = r >= 0 ? __ldg(a.idx + (size_t)r * K + k) : -1;
+            if (h == 0) sPos[MB * buf + m] = pf_pos;
+            const int py = pf_pos >= 0 ? pf_pos / a.W : 0, px = pf_pos >= 0 ? pf_pos - py * a.W : 0;
+#pragma unroll
+            for (int c = 0; c < C; ++c)
 #pragma unroll
                 for (int rr = 0; rr < 4; ++rr) {
-                    const int row = 4 * h + rr;
-                    __align__(16) __half v0[8], v1[8], v2[8];
-                    const float *src = a.img + (size_t)(py + row) * a.W + px;
+                    const float *src = a.img + c * HW + (size_t)(py + 4 * h + rr) * a.W + px;
 #pragma unroll
-                    for (int v = 0; v < 8; ++v) {
-                        if constexpr (C == 1) {
-                            v0[v] = __float2half_rn(pos >= 0 ? __ldg(src + v) : 0.f);
-                        } else {
-                            float R = 0.f, G = 0.f, B = 0.f;
-                            if (pos >= 0) {
-                                R = __ldg(src + v);
-                                G = __ldg(src + HW + v);
-                                B = __ldg(src + 2 * HW + v);
-                            }
-                            v0[v] = __float2half_rn(((R + G) + B) * K3F);
-                            v1[v] = __float2half_rn((R - 0.5f * (G + B)) * K3F);
-                            v2[v] = __float2half_rn((B - G) * 0.5f);
-                        }
-                    }
-                    *reinterpret_cast<uint4 *>(sA + cm_off(m, row * 8)) = *reinterpret_cast<const uint4 *>(v0);
-                    if constexpr (C == 3) {
-                        *reinterpret_cast<uint4 *>(sA + MB * 64 + cm_off(m, row * 8)) =
-                            *reinterpret_cast<const uint4 *>(v1);
-                        *reinterpret_cast<uint4 *>(sA + 2 * MB * 64 + cm_off(m, row * 8)) =
-                            *reinterpret_cast<const uint4 *>(v2);
+                    for (int v = 0; v < 8; ++v) pf[c][rr][v] = pf_pos >= 0 ? __ldg(src + v) : 0.f;
+                }
+        };
+        // the registers -> Fourier slices of the channel axis (unitary DFT), FP16, operand row m
+        auto commit = [&]() {
+            const int m = tid >> 1, h = tid & 1;
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+                const int row = 4 * h + rr;
+                __align__(16) __half v0[8], v1[8], v2[8];
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    if constexpr (C == 1) {
+                        v0[v] = __float2half_rn(pf[0][rr][v]);
+                    } else {
+                        const float R = pf[0][rr][v], G = pf[C - 2][rr][v], B = pf[C - 1][rr][v];
+                        v0[v] = __float2half_rn(((R + G) + B) * K3F);
+                        v1[v] = __float2half_rn((R - 0.5f * (G + B)) * K3F);
+                        v2[v] = __float2half_rn((B - G) * 0.5f);
                     }
                 }
+                *reinterpret_cast<uint4 *>(sA + cm_off(m, row * 8)) = *reinterpret_cast<const uint4 *>(v0);
+                if constexpr (C == 3) {
+                    *reinterpret_cast<uint4 *>(sA + MB * 64 + cm_off(m, row * 8)) = *reinterpret_cast<const uint4 *>(v1);
+                    *reinterpret_cast<uint4 *>(sA + 2 * MB * 64 + cm_off(m, row * 8)) =
+                        *reinterpret_cast<const uint4 *>(v2);
+                }
             }
+        };
+        setup(0, 0);
+        __syncthreads();
+        prefetch(0);
+        for (int b = 0; b < nbatch; ++b) {
+            const int cur = b & 1;
+            const int *bRef = sRef + 32 * cur;
+            const float *bTau = sTau + 32 * cur;
+            const int *bPos = sPos + MB * cur;
+            commit();
             // ---- forward projection (Eq. 19): D[m] = [S0 | Re S1 | Im S1]
             if (!run_stage(false)) {
                 ok = false;
                 break;
+            }
+            if (b + 1 < nbatch) {  // the next batch's loads go out now
+                setup(b + 1, cur ^ 1);
+                __syncthreads();
+                prefetch(cur ^ 1);
             }
             // ---- per 32-column chunk: tensor memory -> transposed FP32 buffer, Haar + threshold +
             //      inverse Haar per (group, coefficient) stream, FP16 into the inverse's operand.
@@ -289,8 +311,8 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
                 if (!cplx) {  // real streams: 32 coefficients x GPB groups
                     for (int s = tid; s < 32 * GPB; s += NT) {
                         const int c = s & 31, g = s >> 5;
-                        if (sRef[g] < 0) continue;
-                        const float tau = sTau[g];
+                        if (bRef[g] < 0) continue;
+                        const float tau = bTau[g];
                         float *p = sT + c * TS + g * K;
                         float x[K];
 #pragma unroll
@@ -310,41 +332,33 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
                         for (int k = 0; k < K; k += 4)
                             *reinterpret_cast<float4 *>(p + k) = make_float4(x[k], x[k + 1], x[k + 2], x[k + 3]);
                     }
-                } else {  // complex streams: 16 coefficients x GPB groups (real part c, imaginary c + 16)
-                    for (int s = tid; s < 16 * GPB; s += NT) {
-                        const int c = s & 15, g = s >> 4;
-                        if (sRef[g] < 0) continue;
-                        const float tau = sTau[g];
-                        float *pr = sT + c * TS + g * K, *pi = sT + (c + 16) * TS + g * K;
-                        float xr[K], xi[K];
+                } else {  // complex streams: 16 coefficients x GPB groups; lanes 2i (real part, column c)
+                          // and 2i + 1 (imaginary part, column c + 16) share one and exchange squares
+                    for (int s = tid; s < 32 * GPB; s += NT) {  // whole warps take part (32 GPB is a multiple of 32)
+                        const int part = s & 1, c = (s >> 1) & 15, g = s >> 5;
+                        const float tau = bTau[g];  // 0 for an empty slot: its zeros stay zeros
+                        float *p = sT + (c + 16 * part) * TS + g * K;
+                        float x[K];
 #pragma unroll
                         for (int k = 0; k < K; k += 4) {
-                            const float4 r4 = *reinterpret_cast<const float4 *>(pr + k);
-                            const float4 i4 = *reinterpret_cast<const float4 *>(pi + k);
-                            xr[k] = r4.x;
-                            xr[k + 1] = r4.y;
-                            xr[k + 2] = r4.z;
-                            xr[k + 3] = r4.w;
-                            xi[k] = i4.x;
-                            xi[k + 1] = i4.y;
-                            xi[k + 2] = i4.z;
-                            xi[k + 3] = i4.w;
+                            const float4 t4 = *reinterpret_cast<const float4 *>(p + k);
+                            x[k] = t4.x;
+                            x[k + 1] = t4.y;
+                            x[k + 2] = t4.z;
+                            x[k + 3] = t4.w;
                         }
-                        haar_fwd<K>(xr);
-                        haar_fwd<K>(xi);
+                        haar_fwd<K>(x);
 #pragma unroll
-                        for (int k = 0; k < K; ++k)
-                            if (!(sqrtf(xr[k] * xr[k] + xi[k] * xi[k]) >= tau)) {
-                                xr[k] = 0.f;
-                                xi[k] = 0.f;
-                            }
-                        haar_inv<K>(xr);
-                        haar_inv<K>(xi);
-#pragma unroll
-                        for (int k = 0; k < K; k += 4) {
-                            *reinterpret_cast<float4 *>(pr + k) = make_float4(xr[k], xr[k + 1], xr[k + 2], xr[k + 3]);
-                            *reinterpret_cast<float4 *>(pi + k) = make_float4(xi[k], xi[k + 1], xi[k + 2], xi[k + 3]);
+                        for (int k = 0; k < K; ++k) {
+                            const float sq = x[k] * x[k];
+                            const float other = __shfl_xor_sync(0xffffffffu, sq, 1);
+                            const float mag = part ? sqrtf(other + sq) : sqrtf(sq + other);  // re^2 + im^2 in one order
+                            if (!(mag >= tau)) x[k] = 0.f;
                         }
+                        haar_inv<K>(x);
+#pragma unroll
+                        for (int k = 0; k < K; k += 4)
+                            *reinterpret_cast<float4 *>(p + k) = make_float4(x[k], x[k + 1], x[k + 2], x[k + 3]);
                     }
                 }
                 __syncthreads();
@@ -370,7 +384,7 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
             //      4 hh .. 4 hh + 3
             {
                 const int m = 32 * q + lane;
-                const int pos = sPos[m];
+                const int pos = bPos[m];
                 const int py = pos >= 0 ? pos / a.W : 0, px = pos >= 0 ? pos - py * a.W : 0;
 #pragma unroll 1
                 for (int rr = 0; rr < 4; ++rr) {
@@ -402,12 +416,7 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
 #pragma unroll
                         for (int v = 0; v < 8; ++v) {
 #pragma unroll
-                            for (int c = 0; c < C; ++c) {
-                                int qh, ql;
-                                fix16_split(out[c][v], qh, ql);
-                                atomicAdd(acc_hi + c * RA + o + v, qh);
-                                atomicAdd(acc_lo + c * RA + o + v, ql);
-                            }
+                            for (int c = 0; c < C; ++c) atomicAdd(acc_v + c * RA + o + v, __float2int_rn(out[c][v] * 256.f));
                             atomicAdd(acc_w + o + v, 1);
                         }
                     } else {
@@ -427,7 +436,7 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
             const size_t gpix = (size_t)(ry0 + yy) * a.W + (rx0 + xx);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                const long long s = (long long)acc_hi[c * RA + e] * 65536ll + (long long)acc_lo[c * RA + e];
+                const long long s = (long long)acc_v[c * RA + e] * 256ll;  // to the image-wide 2^16 scale
                 atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + c * HW + gpix), (unsigned long long)s);
             }
             atomicAdd(a.wcount + gpix, w);
@@ -451,7 +460,7 @@ hts_status launch_ftc(FtcArgs a, const Geom &g, cudaStream_t s, bool *used) {
     for (int i = 0; i < NSHAPES_TC; ++i) {
         const int h = std::min(g.H, (SHAPES_TC[i][0] - 1) * g.step + 2 * g.R + PS);
         const int w = std::min(g.W, (SHAPES_TC[i][1] - 1) * g.step + 2 * g.R + PS);
-        const size_t n = L::acc_off + (size_t)(2 * C + 1) * h * w * 4;
+        const size_t n = L::acc_off + (size_t)(C + 1) * h * w * 4;
         if (n <= budget) {
             ty = SHAPES_TC[i][0];
             tx = SHAPES_TC[i][1];
