@@ -45,7 +45,7 @@ using fc::haar_inv;
 using fc::K3F;
 using fc::S3H;
 
-constexpr int NT = 256;   // 8 warps: warp w reads tensor-memory lanes 32 (w % 4) .. + 31
+constexpr int NT = 512;   // 16 warps: warp w reads tensor-memory lanes 32 (w % 4) .. + 31, column quarter w / 4
 constexpr int MB = 128;   // group members per batch = MMA M
 constexpr int TS = MB + 4;  // row stride (floats) of the transpose buffer: conflict-free float4 reads
 constexpr long long SPIN = 1ll << 24;
@@ -58,22 +58,21 @@ __device__ __forceinline__ int cm_off(int r, int k) { return (((r >> 3) << 3) + 
 template <int C>
 struct FtcLayout {
     static constexpr int NBLK = (C == 3) ? 3 : 1;  // 64-column blocks of the member operand
-    // FP16 Kronecker matrices (halves): C == 3: B0 [64][64], B1 [128][64], B2 [128][64] (forward),
-    // B0i [64][64], B3 [128][64], B4 [128][64] (inverse); C == 1: B0, B0i
+    // FP16 Kronecker matrices (halves): B0 [coefficient][pixel] and B0I [pixel][coefficient] of slice 0;
+    // C == 3: BF = [Mr; Mi; -Mi] [coefficient][pixel] and BI = [Mr^T; Mi^T; -Mi^T] [pixel][coefficient]
+    // of slice 1 (192 rows each)
     static constexpr int B0 = 0;
-    static constexpr int B1 = 64 * 64;
-    static constexpr int B2 = B1 + 128 * 64;
-    static constexpr int B0I = (C == 3) ? B2 + 128 * 64 : 64 * 64;
-    static constexpr int B3 = B0I + 64 * 64;
-    static constexpr int B4 = B3 + 128 * 64;
-    static constexpr int B_HALVES = (C == 3) ? B4 + 128 * 64 : 2 * 64 * 64;
+    static constexpr int BF = 64 * 64;
+    static constexpr int B0I = (C == 3) ? BF + 192 * 64 : 64 * 64;
+    static constexpr int BI = B0I + 64 * 64;
+    static constexpr int B_HALVES = (C == 3) ? BI + 192 * 64 : 2 * 64 * 64;
     static constexpr size_t a_off = 0;                               // [NBLK][128][64] FP16
     static constexpr size_t b_off = a_off + (size_t)NBLK * MB * 64 * 2;
-    static constexpr size_t t_off = b_off + (size_t)B_HALVES * 2;    // [32][TS] FP32
-    static constexpr size_t basis_off = t_off + (size_t)32 * TS * 4;  // 6 x 64 FP32
+    static constexpr size_t t_off = b_off + (size_t)B_HALVES * 2;    // [64][TS] FP32
+    static constexpr size_t basis_off = t_off + (size_t)64 * TS * 4;  // 6 x 64 FP32
     static constexpr size_t misc_off = basis_off + (size_t)6 * 64 * 4;
-    // misc, two buffers each: pos[MB] int, ref[32] int, tau[32] float; 2 mbarrier words, tensor-memory slot
-    static constexpr size_t acc_off = misc_off + (size_t)2 * (MB * 4 + 32 * 4 + 32 * 4) + 16 + 16;
+    // misc, two buffers each: pos[MB] int, tau[32] float; 2 mbarrier words, tensor-memory slot
+    static constexpr size_t acc_off = misc_off + (size_t)2 * (MB * 4 + 32 * 4) + 16 + 16;
     static constexpr uint32_t tcols = (C == 3) ? 256 : 64;
 };
 
@@ -100,10 +99,9 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
     __half *sB = reinterpret_cast<__half *>(smem + L::b_off);
     float *sT = reinterpret_cast<float *>(smem + L::t_off);
     float *sBas = reinterpret_cast<float *>(smem + L::basis_off);
-    int *sPos = reinterpret_cast<int *>(smem + L::misc_off);  // [2][MB]
-    int *sRef = sPos + 2 * MB;                                 // [2][32]
-    float *sTau = reinterpret_cast<float *>(sRef + 64);        // [2][32]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sTau + 64);
+    int *sPos = reinterpret_cast<int *>(smem + L::misc_off);  // [2][MB] members' top-left pixels
+    float *sTau = reinterpret_cast<float *>(sPos + 2 * MB);    // [2][32] groups' thresholds
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sTau + 64);  // 8-byte aligned: misc_off + 1280
     uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
     int *accs = reinterpret_cast<int *>(smem + L::acc_off);
     const int RA = a.rh_max * a.rw_max;
@@ -133,14 +131,12 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
         if (C == 3) {
             const float ur = sBas[128 + ia], ui = sBas[192 + ia], vr = sBas[256 + jb], vi = sBas[320 + jb];
             const float mr = ur * vr + ui * vi, mi = ur * vi - ui * vr;  // conj(U1[i][a]) V1[j][b]
-            sB[L::B1 + cm_off(n, k)] = __float2half_rn(mr);
-            sB[L::B1 + cm_off(64 + n, k)] = __float2half_rn(mi);
-            sB[L::B2 + cm_off(n, k)] = __float2half_rn(-mi);
-            sB[L::B2 + cm_off(64 + n, k)] = __float2half_rn(mr);
-            sB[L::B3 + cm_off(k, n)] = __float2half_rn(mr);
-            sB[L::B3 + cm_off(64 + k, n)] = __float2half_rn(-mi);
-            sB[L::B4 + cm_off(k, n)] = __float2half_rn(mi);
-            sB[L::B4 + cm_off(64 + k, n)] = __float2half_rn(mr);
+            sB[L::BF + cm_off(n, k)] = __float2half_rn(mr);
+            sB[L::BF + cm_off(64 + n, k)] = __float2half_rn(mi);
+            sB[L::BF + cm_off(128 + n, k)] = __float2half_rn(-mi);
+            sB[L::BI + cm_off(k, n)] = __float2half_rn(mr);
+            sB[L::BI + cm_off(64 + k, n)] = __float2half_rn(mi);
+            sB[L::BI + cm_off(128 + k, n)] = __float2half_rn(-mi);
         }
     }
     if (tid == 0) {
@@ -152,8 +148,8 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = *slot;
-    const uint32_t id64 = tc::idesc_f16(MB, 64, false), id128 = tc::idesc_f16(MB, 128, false);
-    const int q = warp & 3, hh = warp >> 2;  // tensor-memory lane quarter, column half
+    const uint32_t id64 = tc::idesc_f16(MB, 64, false);
+    const int q = warp & 3, wq = warp >> 2;  // tensor-memory lane quarter, column quarter
     const uint32_t tlane = (uint32_t)(32 * q) << 16;
     uint32_t phase = 0;
     bool ok = true;
@@ -172,15 +168,24 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
                 tc::mma_f16(tbase, tc::sdesc(a0 + kk * 256, 128, 1024), tc::sdesc(b0 + bs * 2 + kk * 256, 128, 1024),
                             id64, kk > 0 ? 1u : 0u);
             if (C == 3) {
-                const int b1 = inverse ? L::B3 : L::B1, b2 = inverse ? L::B4 : L::B2;
+                // rows 0, 64, 128 of BF / BI hold Mr, Mi, -Mi (resp. their transposes); A blocks 1 and 2 hold
+                // Re, Im of slice 1 (pixels forward, coefficients inverse).  Forward:
+                //   Re S = Re P Mr^T + Im P (-Mi)^T,  Im S = Re P Mi^T + Im P Mr^T;
+                // inverse: Re P = Re S Mr + Im S Mi,  Im P = Re S (-Mi) + Im S Mr.
+                const int bb = inverse ? L::BI : L::BF;
+                const int re_a = 0, re_b = inverse ? 64 : 128, im_a = inverse ? 128 : 64, im_b = 0;
+                auto chain = [&](uint32_t dcol, int r1, int r2) {
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    tc::mma_f16(tbase + 64, tc::sdesc(a0 + MB * 64 * 2 + kk * 256, 128, 1024),
-                                tc::sdesc(b0 + b1 * 2 + kk * 256, 128, 1024), id128, kk > 0 ? 1u : 0u);
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc::mma_f16(tbase + dcol, tc::sdesc(a0 + MB * 64 * 2 + kk * 256, 128, 1024),
+                                    tc::sdesc(b0 + (bb + r1 * 64) * 2 + kk * 256, 128, 1024), id64, kk > 0 ? 1u : 0u);
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    tc::mma_f16(tbase + 64, tc::sdesc(a0 + 2 * MB * 64 * 2 + kk * 256, 128, 1024),
-                                tc::sdesc(b0 + b2 * 2 + kk * 256, 128, 1024), id128, 1u);
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc::mma_f16(tbase + dcol, tc::sdesc(a0 + 2 * MB * 64 * 2 + kk * 256, 128, 1024),
+                                    tc::sdesc(b0 + (bb + r2 * 64) * 2 + kk * 256, 128, 1024), id64, 1u);
+                };
+                chain(64, re_a, re_b);
+                chain(128, im_a, im_b);
             }
             tc::mma_commit(bar);
         }
@@ -199,6 +204,10 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
 
     const int gpt = a.ty * a.tx;
     const int nbatch = (gpt + GPB - 1) / GPB;
+    // gather mapping: per step it, thread tid loads pixel (row, px) of member m(it); a warp covers one
+    // patch row of 4 consecutive members (4 coalesced 32-byte segments)
+    const int g_px = tid & 7, g_ml = (tid >> 3) & 3, g_row = (tid >> 5) & 7, g_mh = tid >> 8;
+    constexpr int NPF = MB * 64 / NT;  // pixels per thread per batch
     for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
         const int tyi = tile / a.ntx, txi = tile - tyi * a.ntx;
         const int gy0 = tyi * a.ty, gx0 = txi * a.tx;
@@ -209,163 +218,146 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
         const int rx0 = max(0, X0 - a.R), rx1 = min(a.W - 1, X1 + a.R + PS - 1);
         const int rh = ry1 - ry0 + 1, rw = rx1 - rx0 + 1;
         for (int e = tid; e < (C + 1) * RA; e += NT) accs[e] = 0;
-        __syncthreads();
-        // ---- the groups and members of batch bb into buffer buf (sRef/sTau/sPos), then this thread's
-        //      member pixels into registers: the loads stay in flight while the previous batch is
-        //      filtered (member m = tid / 2, patch rows 4 (tid & 1) .. + 3)
-        float pf[C][4][8];
-        int pf_pos = -1;
+        // the thresholds of batch bb's groups into buffer buf
         auto setup = [&](int bb, int buf) {
             if (tid < GPB) {
                 const int lg = bb * GPB + tid;
                 const int gy = gy0 + lg / a.tx, gx = gx0 + lg % a.tx;
                 const bool valid = lg < gpt && gy <= gy1 && gx <= gx1;
-                const int r = valid ? gy * a.nx + gx : -1;
-                sRef[32 * buf + tid] = r;
                 sTau[32 * buf + tid] = !valid ? 0.f
-                                       : use_map ? (float)(a.tau_scale * (double)a.sigma_ref[r])
+                                       : use_map ? (float)(a.tau_scale * (double)a.sigma_ref[gy * a.nx + gx])
                                                  : a.st->tau32;
             }
         };
-        auto prefetch = [&](int buf) {
-            const int m = tid >> 1, h = tid & 1;
-            const int g = m / K, k = m - g * K;
-            const int r = sRef[32 * buf + g];
-            pf_pos = r >= 0 ? __ldg(a.idx + (size_t)r * K + k) : -1;
-            if (h == 0) sPos[MB * buf + m] = pf_pos;
-            const int py = pf_pos >= 0 ? pf_pos / a.W : 0, px = pf_pos >= 0 ? pf_pos - py * a.W : 0;
-#pragma unroll
-            for (int c = 0; c < C; ++c)
-#pragma unroll
-                for (int rr = 0; rr < 4; ++rr) {
-                    const float *src = a.img + c * HW + (size_t)(py + 4 * h + rr) * a.W + px;
-#pragma unroll
-                    for (int v = 0; v < 8; ++v) pf[c][rr][v] = pf_pos >= 0 ? __ldg(src + v) : 0.f;
-                }
+        // member m (= tid < MB) of batch bb: its patch's top-left pixel, -1 for an empty group slot
+        auto member_pos = [&](int bb) -> int {
+            const int g = tid / K, k = tid - g * K;
+            const int lg = bb * GPB + g;
+            const int gy = gy0 + lg / a.tx, gx = gx0 + lg % a.tx;
+            const bool valid = lg < gpt && gy <= gy1 && gx <= gx1;
+            return valid ? __ldg(a.idx + (size_t)(gy * a.nx + gx) * K + k) : -1;
         };
-        // the registers -> Fourier slices of the channel axis (unitary DFT), FP16, operand row m
+        // this thread's pixels of the batch whose positions are in buffer buf, into registers
+        float pf[NPF][C];
+        auto prefetch = [&](int buf) {
+#pragma unroll
+            for (int it = 0; it < NPF; ++it) {
+                const int m = 4 * (2 * it + g_mh) + g_ml;
+                const int pos = sPos[MB * buf + m];
+                const float *src = a.img + (pos >= 0 ? pos : 0) + g_row * a.W + g_px;  // a valid address either way
+#pragma unroll
+                for (int c = 0; c < C; ++c) pf[it][c] = pos >= 0 ? __ldg(src + c * HW) : 0.f;
+            }
+        };
+        // registers -> Fourier slices of the channel axis (unitary DFT), FP16, member rows of the operand
         auto commit = [&]() {
-            const int m = tid >> 1, h = tid & 1;
 #pragma unroll
-            for (int rr = 0; rr < 4; ++rr) {
-                const int row = 4 * h + rr;
-                __align__(16) __half v0[8], v1[8], v2[8];
-#pragma unroll
-                for (int v = 0; v < 8; ++v) {
-                    if constexpr (C == 1) {
-                        v0[v] = __float2half_rn(pf[0][rr][v]);
-                    } else {
-                        const float R = pf[0][rr][v], G = pf[C - 2][rr][v], B = pf[C - 1][rr][v];
-                        v0[v] = __float2half_rn(((R + G) + B) * K3F);
-                        v1[v] = __float2half_rn((R - 0.5f * (G + B)) * K3F);
-                        v2[v] = __float2half_rn((B - G) * 0.5f);
-                    }
-                }
-                *reinterpret_cast<uint4 *>(sA + cm_off(m, row * 8)) = *reinterpret_cast<const uint4 *>(v0);
-                if constexpr (C == 3) {
-                    *reinterpret_cast<uint4 *>(sA + MB * 64 + cm_off(m, row * 8)) = *reinterpret_cast<const uint4 *>(v1);
-                    *reinterpret_cast<uint4 *>(sA + 2 * MB * 64 + cm_off(m, row * 8)) =
-                        *reinterpret_cast<const uint4 *>(v2);
+            for (int it = 0; it < NPF; ++it) {
+                const int m = 4 * (2 * it + g_mh) + g_ml;
+                const int o = cm_off(m, g_row * 8 + g_px);
+                if constexpr (C == 1) {
+                    sA[o] = __float2half_rn(pf[it][0]);
+                } else {
+                    const float R = pf[it][0], G = pf[it][C - 2], B = pf[it][C - 1];
+                    sA[o] = __float2half_rn(((R + G) + B) * K3F);
+                    sA[MB * 64 + o] = __float2half_rn((R - 0.5f * (G + B)) * K3F);
+                    sA[2 * MB * 64 + o] = __float2half_rn((B - G) * 0.5f);
                 }
             }
         };
         setup(0, 0);
+        int posreg = -1;
+        if (tid < MB) {
+            sPos[tid] = member_pos(0);
+            sPos[MB + tid] = nbatch > 1 ? member_pos(1) : -1;
+            posreg = nbatch > 2 ? member_pos(2) : -1;
+        }
         __syncthreads();
         prefetch(0);
         for (int b = 0; b < nbatch; ++b) {
             const int cur = b & 1;
-            const int *bRef = sRef + 32 * cur;
             const float *bTau = sTau + 32 * cur;
             const int *bPos = sPos + MB * cur;
             commit();
+            if (b + 1 < nbatch) setup(b + 1, cur ^ 1);  // read after the next batch's first barrier
+            if (b >= 1 && b + 1 < nbatch && tid < MB) sPos[MB * (cur ^ 1) + tid] = posreg;  // batch b + 1
             // ---- forward projection (Eq. 19): D[m] = [S0 | Re S1 | Im S1]
             if (!run_stage(false)) {
                 ok = false;
                 break;
             }
-            if (b + 1 < nbatch) {  // the next batch's loads go out now
-                setup(b + 1, cur ^ 1);
-                __syncthreads();
+            if (b + 1 < nbatch) {  // the next batch's pixel loads go out now, and the positions of the one after
                 prefetch(cur ^ 1);
+                if (tid < MB && b + 2 < nbatch) posreg = member_pos(b + 2);
             }
-            // ---- per 32-column chunk: tensor memory -> transposed FP32 buffer, Haar + threshold +
+            // ---- per 64-column chunk: tensor memory -> transposed FP32 buffer, Haar + threshold +
             //      inverse Haar per (group, coefficient) stream, FP16 into the inverse's operand.
-            //      Chunks 0, 1: S0 columns [32 ch, + 32); chunks 2..5: complex coefficients
-            //      c0 = 16 (ch - 2) .. + 15, real parts (columns 64 + c) as local columns 0..15,
-            //      imaginary parts (128 + c) as 16..31.
-            constexpr int NCHUNK = (C == 3) ? 6 : 2;
+            //      Chunk 0: S0 (columns 0..63); chunks 1, 2: complex coefficients c0 = 32 (ch - 1) .. + 31,
+            //      real parts (columns 64 + c) as local columns 0..31, imaginary parts (128 + c) as 32..63.
+            constexpr int NCHUNK = (C == 3) ? 3 : 1;
 #pragma unroll 1
             for (int ch = 0; ch < NCHUNK; ++ch) {
-                const bool cplx = ch >= 2;
-                const int c0 = 16 * (ch - 2);
-                const int col0 = !cplx ? 32 * ch + 16 * hh : (hh == 0 ? 64 + c0 : 128 + c0);
+                const bool cplx = ch >= 1;
+                const int c0 = 32 * (ch - 1);
+                const int col0 = !cplx ? 16 * wq : (wq < 2 ? 64 + c0 + 16 * wq : 128 + c0 + 16 * (wq - 2));
                 {
                     uint32_t v[16];
                     tc::tmem_ld16(tbase + tlane + (uint32_t)col0, v);
                     tc::tmem_wait_ld();
                     const int m = 32 * q + lane;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) sT[(16 * hh + j) * TS + m] = __uint_as_float(v[j]);
+                    for (int j = 0; j < 16; ++j) sT[(16 * wq + j) * TS + m] = __uint_as_float(v[j]);
                 }
                 __syncthreads();
-                if (!cplx) {  // real streams: 32 coefficients x GPB groups
-                    for (int s = tid; s < 32 * GPB; s += NT) {
-                        const int c = s & 31, g = s >> 5;
-                        if (bRef[g] < 0) continue;
-                        const float tau = bTau[g];
-                        float *p = sT + c * TS + g * K;
-                        float x[K];
+                // 64 GPB streams (real) or half-streams (complex: lanes 2i, 2i + 1 hold the real and
+                // imaginary part of one coefficient and exchange squares); whole warps take part
+                for (int s2 = tid; s2 < 64 * GPB; s2 += NT) {
+                    int col, g;
+                    if (!cplx) {
+                        col = s2 & 63;
+                        g = s2 >> 6;
+                    } else {
+                        col = ((s2 >> 1) & 31) + 32 * (s2 & 1);
+                        g = s2 >> 6;
+                    }
+                    const float tau = bTau[g];  // 0 for an empty slot: its zeros stay zeros
+                    float *p = sT + col * TS + g * K;
+                    float x[K];
 #pragma unroll
-                        for (int k = 0; k < K; k += 4) {
-                            const float4 t4 = *reinterpret_cast<const float4 *>(p + k);
-                            x[k] = t4.x;
-                            x[k + 1] = t4.y;
-                            x[k + 2] = t4.z;
-                            x[k + 3] = t4.w;
-                        }
-                        haar_fwd<K>(x);
+                    for (int k = 0; k < K; k += 4) {
+                        const float4 t4 = *reinterpret_cast<const float4 *>(p + k);
+                        x[k] = t4.x;
+                        x[k + 1] = t4.y;
+                        x[k + 2] = t4.z;
+                        x[k + 3] = t4.w;
+                    }
+                    haar_fwd<K>(x);
+                    if (!cplx) {
 #pragma unroll
                         for (int k = 0; k < K; ++k)
                             if (!(fabsf(x[k]) >= tau)) x[k] = 0.f;
-                        haar_inv<K>(x);
-#pragma unroll
-                        for (int k = 0; k < K; k += 4)
-                            *reinterpret_cast<float4 *>(p + k) = make_float4(x[k], x[k + 1], x[k + 2], x[k + 3]);
-                    }
-                } else {  // complex streams: 16 coefficients x GPB groups; lanes 2i (real part, column c)
-                          // and 2i + 1 (imaginary part, column c + 16) share one and exchange squares
-                    for (int s = tid; s < 32 * GPB; s += NT) {  // whole warps take part (32 GPB is a multiple of 32)
-                        const int part = s & 1, c = (s >> 1) & 15, g = s >> 5;
-                        const float tau = bTau[g];  // 0 for an empty slot: its zeros stay zeros
-                        float *p = sT + (c + 16 * part) * TS + g * K;
-                        float x[K];
-#pragma unroll
-                        for (int k = 0; k < K; k += 4) {
-                            const float4 t4 = *reinterpret_cast<const float4 *>(p + k);
-                            x[k] = t4.x;
-                            x[k + 1] = t4.y;
-                            x[k + 2] = t4.z;
-                            x[k + 3] = t4.w;
-                        }
-                        haar_fwd<K>(x);
+                    } else {
+                        const bool im = s2 & 1;
 #pragma unroll
                         for (int k = 0; k < K; ++k) {
                             const float sq = x[k] * x[k];
                             const float other = __shfl_xor_sync(0xffffffffu, sq, 1);
-                            const float mag = part ? sqrtf(other + sq) : sqrtf(sq + other);  // re^2 + im^2 in one order
+                            const float mag = im ? sqrtf(other + sq) : sqrtf(sq + other);  // re^2 + im^2, one order
                             if (!(mag >= tau)) x[k] = 0.f;
                         }
-                        haar_inv<K>(x);
-#pragma unroll
-                        for (int k = 0; k < K; k += 4)
-                            *reinterpret_cast<float4 *>(p + k) = make_float4(x[k], x[k + 1], x[k + 2], x[k + 3]);
                     }
+                    haar_inv<K>(x);
+#pragma unroll
+                    for (int k = 0; k < K; k += 4)
+                        *reinterpret_cast<float4 *>(p + k) = make_float4(x[k], x[k + 1], x[k + 2], x[k + 3]);
                 }
                 __syncthreads();
                 // FP16 into the inverse GEMM's operand: member m, 8 consecutive local columns 8 jg ..
-                for (int it = tid; it < MB * 4; it += NT) {
-                    const int m = it & (MB - 1), jg = it >> 7;
-                    const int gc = !cplx ? 32 * ch + 8 * jg : (jg < 2 ? 64 + c0 + 8 * jg : 128 + c0 + 8 * (jg - 2));
+#pragma unroll
+                for (int it = 0; it < MB * 8 / NT; ++it) {
+                    const int e2 = it * NT + tid;
+                    const int m = e2 & (MB - 1), jg = e2 >> 7;
+                    const int gc = !cplx ? 8 * jg : (jg < 4 ? 64 + c0 + 8 * jg : 128 + c0 + 8 * (jg - 4));
                     __align__(16) __half hv[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) hv[e] = __float2half_rn(sT[(8 * jg + e) * TS + m]);
@@ -381,14 +373,14 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
                 break;
             }
             // ---- inverse DFT along the channels and aggregation: member m = 32 q + lane, patch rows
-            //      4 hh .. 4 hh + 3
+            //      2 wq, 2 wq + 1
             {
                 const int m = 32 * q + lane;
                 const int pos = bPos[m];
                 const int py = pos >= 0 ? pos / a.W : 0, px = pos >= 0 ? pos - py * a.W : 0;
 #pragma unroll 1
-                for (int rr = 0; rr < 4; ++rr) {
-                    const int row = 4 * hh + rr;
+                for (int rr = 0; rr < 2; ++rr) {
+                    const int row = 2 * wq + rr;
                     uint32_t p0[8], p1[8] = {}, p2[8] = {};
                     tc::tmem_ld8(tbase + tlane + (uint32_t)(row * 8), p0);
                     if constexpr (C == 3) {
