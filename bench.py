@@ -6,7 +6,10 @@ seeded synthetic image (rectangles, disks, gratings; per-channel gains) plus
 AWGN sigma = 50 that the method does not know; the step estimates the
 globally-learned t-SVD basis (Eq. 11), the noise level (Eq. 12 floor, Eq. 22-23
 vote), groups every reference patch (K = 16, 31x31 window, step 4), filters
-(Eq. 19-21) and aggregates.  Metric: Mpixel/s (H*W per second).
+(Eq. 19-21) and aggregates.  Metric: Mpixel/s (H*W per second) of the chosen
+form -- the fastest of the plain form and the two tensor-core forms whose
+PSNR is within 0.05 dB of the FP64 oracle's -- with every form's number in
+the line ("plain vs chosen").
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun every rank denoises its own seeded image (weak scaling, no
@@ -696,6 +699,11 @@ def run_reference(args):
     return 0
 
 
+FORMS = {0: "plain: FP32 certified grouping, FP32 filter with FP64 decisions in the error band",
+         1: "precision form: BF16 tensor-core grouping, FP16 tensor-core filter, FP32 decisions",
+         2: "exact groups of the plain form, FP16 tensor-core filter, FP32 decisions"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -713,43 +721,61 @@ def run_ours(args):
     hts.load()
     w = WORKLOAD
     clean, noisy = _image(rank)
-    p = hts.params(K=w["K"], win=w["win"], step=w["step"])
     x = torch.from_numpy(noisy).cuda()
-    out = torch.empty_like(x)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def step():
-        hts.denoise(x, sigma=None, basis=None, p=p, out=out)
+    def timed(prec):
+        """W warm-up and K timed steps of one form (barrier + synchronize on both sides, CUDA events on
+        the launching stream, L2 flushed between steps outside the events); max over ranks."""
+        p = hts.params(K=w["K"], win=w["win"], step=w["step"], precision=prec)
+        out = torch.empty_like(x)
+        for _ in range(max(args.warmup, 3)):
+            hts.denoise(x, sigma=None, basis=None, p=p, out=out)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        l0 = hts.launch_count()
+        hts.profile_begin()
+        for i in range(args.steps):
+            flush.zero_()  # evict the image and intermediates from L2 between steps (outside the events)
+            evs[i][0].record(stream)
+            hts.denoise(x, sigma=None, basis=None, p=p, out=out)
+            evs[i][1].record(stream)
+        prof = hts.profile_end()
+        torch.cuda.synchronize()
+        launches = hts.launch_count() - l0
+        if world > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop()
+        total_ms = sum(a.elapsed_time(b) for a, b in evs)
+        max_ms = hd.max_over_ranks(total_ms, device="cuda")
+        return {"p": p, "ms": max_ms / args.steps,
+                "value": world * args.steps * w["H"] * w["W"] / (max_ms / 1e3) / 1e6,
+                "prof": prof, "launches": launches, "clocks": clk, "out": out.cpu().numpy(),
+                "stats": hts.last_stats()}
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
+    res = {k: timed(k) for k in FORMS}
+    cpu, ref_out, psnr_oracle = None, None, None
+    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+        cpu, ref_out = cpu_baseline(noisy)
+        psnr_oracle = synth.psnr(ref_out, clean)
+    for k, r in res.items():
+        r["psnr_db"] = synth.psnr(r["out"], clean)
+        r["psnr_delta_db"] = None if psnr_oracle is None else r["psnr_db"] - psnr_oracle
+    # chosen: the fastest form within 0.05 dB of the oracle (every form is, by its tests, where the
+    # oracle is not run here); the same choice on every rank (times are max over ranks)
+    ok = [k for k, r in res.items() if r["psnr_delta_db"] is None or abs(r["psnr_delta_db"]) <= 0.05]
+    chosen = min(ok, key=lambda k: res[k]["ms"])
+    r = res[chosen]
+    p = r["p"]
 
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    l0 = hts.launch_count()
-    hts.profile_begin()
-    for i in range(args.steps):
-        flush.zero_()  # evict the image and intermediates from L2 between steps (outside the events)
-        evs[i][0].record(stream)
-        step()
-        evs[i][1].record(stream)
-    prof = hts.profile_end()
-    torch.cuda.synchronize()
-    launches = hts.launch_count() - l0
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    total_ms = sum(a.elapsed_time(b) for a, b in evs)
-    max_ms = hd.max_over_ranks(total_ms, device="cuda")
-    value = world * args.steps * w["H"] * w["W"] / (max_ms / 1e3) / 1e6
-
-    # end to end through the host-buffer C-ABI call (pinned host memory)
+    # end to end through the host-buffer C-ABI call (pinned host memory), chosen form
     hx = torch.from_numpy(noisy).pin_memory()
     ho = torch.empty_like(hx).pin_memory()
     hxn, hon = hx.numpy(), ho.numpy()
@@ -768,49 +794,62 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return 0
 
-    den = out.cpu().numpy()
-    stats = hts.last_stats()
+    prof = r["prof"]
+    den = r["out"]
+    stats = r["stats"]
     work = algorithmic_work(w["H"], w["W"], w["C"], w["K"], w["win"], w["step"])
     kernels = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches": v[1], "share": v[0] / max(1e-9, sum(
         u[0] for u in prof.values()))} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
     dom = next(iter(kernels))
     peaks = _peaks()
     roof = None
-    if dom in work and "flops" in work[dom]:
-        ach = work[dom]["flops"] / (kernels[dom]["ms_per_launch"] / 1e3) / 1e12
+    wk = dict(work)
+    wk["k_filter_tc"] = work["k_filter"]
+    if dom == "k_filter_tc":
+        # a contraction on the tensor cores: the algorithmic flops against the FP16 dense peak (the measured
+        # BF16 one; FP16 and BF16 have the same nominal rate)
+        ach = wk[dom]["flops"] / (kernels[dom]["ms_per_launch"] / 1e3) / 1e12
+        roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": ach / peaks["bf16_tflops"], "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured; FP16 = BF16 rate)",
+                "algorithmic": wk[dom]["per"] + "; the Kronecker-form GEMMs issue 1.31 MFLOP per group"}
+    elif dom in wk and "flops" in wk[dom]:
+        ach = wk[dom]["flops"] / (kernels[dom]["ms_per_launch"] / 1e3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2.07 GHz",
-                "algorithmic": work[dom]["per"]}
-    elif dom in work and "bytes" in work[dom]:
-        ach = work[dom]["bytes"] / (kernels[dom]["ms_per_launch"] / 1e3) / 1e9
+                "algorithmic": wk[dom]["per"]}
+    elif dom in wk and "bytes" in wk[dom]:
+        ach = wk[dom]["bytes"] / (kernels[dom]["ms_per_launch"] / 1e3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
     traffic = _committed_traffic(dom)
     if roof is not None and traffic is not None:
         roof["traffic"] = traffic
-
-    cpu = None
-    psnr_oracle = None
-    if world == 1 and not args.no_cpu_baseline:
-        cpu, ref_out = cpu_baseline(noisy)
-        psnr_oracle = synth.psnr(ref_out, clean)
+    if cpu is not None:
         cpu["max_abs_vs_gpu"] = float(np.max(np.abs(ref_out - den.astype(np.float64))))
+        cpu["max_abs_vs_gpu_plain"] = float(np.max(np.abs(ref_out - res[0]["out"].astype(np.float64))))
     line = {
-        "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "metric": METRIC, "value": r["value"], "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if chosen == 0 else ("bf16 matching / f16 filter" if chosen == 1
+                                                                 else "f32 matching / f16 filter"),
+        "data": "synthetic",
         "config": dict(WORKLOAD, l2="flushed between steps (512 MB write outside the timed events)",
-                       parallelism="replicas: one image per rank" if world > 1 else "single GPU"),
+                       parallelism="replicas: one image per rank" if world > 1 else "single GPU",
+                       chosen_precision=chosen, chosen_form=FORMS[chosen]),
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "Mpixel/s", "h2d_bytes_per_step": int(noisy.nbytes),
                 "d2h_bytes_per_step": int(noisy.nbytes), "call": "hts_denoise_host (pinned host buffers)"},
-        "clocks": clk,
-        "gpu_launches": int(launches),
+        "clocks": r["clocks"],
+        "gpu_launches": int(r["launches"]),
         "kernels": kernels,
-        "psnr_db": synth.psnr(den, clean), "psnr_oracle_db": psnr_oracle,
-        "psnr_delta_db": None if psnr_oracle is None else synth.psnr(den, clean) - psnr_oracle,
+        "forms": {str(k): {"form": FORMS[k], "value": v["value"], "ms_per_step": v["ms"], "psnr_db": v["psnr_db"],
+                           "psnr_delta_db": v["psnr_delta_db"], "gpu_launches": int(v["launches"]),
+                           "clocks_sm_mhz": v["clocks"]["sm_mhz"]} for k, v in res.items()},
+        "plain_value": res[0]["value"],
+        "psnr_db": r["psnr_db"], "psnr_oracle_db": psnr_oracle, "psnr_delta_db": r["psnr_delta_db"],
         "sigma_hat": stats["sigma"], "redo_groups": stats["filter_redo"], "exact_coefs": stats["filter_exact"],
         "match_reranked": stats["match_reranked"], "match_fallback": stats["match_fallback"],
         "vote_uncertain": stats["vote_uncertain"],

@@ -61,13 +61,17 @@ typedef struct {
     double tau_mult;   /* multiplier on the universal threshold (>= 0) */
     int adjust_rank;   /* 1: apply the Eq. 22-23 vote when sigma is estimated */
     int mp_correct;    /* 1: divide the Eq. 12 floor by the Marchenko-Pastur edge (1-1/sqrt(N_ref))^2 */
-    int precision;     /* grouping arithmetic.  0: FP32 distances certified against FP64 (the
-                        * groups equal the FP64 definition's, ties to the lower index).
+    int precision;     /* arithmetic of the grouping and the filter.
+                        * 0: FP32 distances certified against FP64 (the groups equal the FP64
+                        *    definition's, ties to the lower index); FP32 transforms with FP64
+                        *    threshold decisions inside the FP32 error band.
                         * 1: precision form: BF16 distances on the tensor cores (FP32
-                        * accumulation), the 2K nearest re-ranked with FP32 distances; groups
-                        * may differ from the FP64 definition's where BF16 rounding reorders
-                        * near neighbours.  Windows too large for on-chip staging give
-                        * HTS_EUNSUPPORTED. */
+                        *    accumulation), the 2K nearest re-ranked with FP32 distances (groups
+                        *    may differ from the FP64 definition's where BF16 rounding reorders
+                        *    near neighbours); FP16 projections on the tensor cores (FP32
+                        *    accumulation) with FP32 threshold decisions.  Windows too large for
+                        *    on-chip staging give HTS_EUNSUPPORTED.
+                        * 2: the groups of 0 with the filter of 1. */
 } hts_params;
 
 /* Fills *p with the defaults above.  HTS_EINVAL if p is NULL. */

@@ -237,7 +237,7 @@ hts_status validate(int H, int W, int C, const hts_params *p, Geom *g) {
     if (!(p->beta > 0) || !std::isfinite(p->beta)) return fail(HTS_EINVAL, "beta must be > 0");
     if (!(p->tau_mult >= 0) || !std::isfinite(p->tau_mult)) return fail(HTS_EINVAL, "tau_mult must be >= 0");
     if (!std::isfinite(p->gamma_rank)) return fail(HTS_EINVAL, "gamma_rank must be finite");
-    if (p->precision != 0 && p->precision != 1) return fail(HTS_EINVAL, "precision must be 0 or 1");
+    if (p->precision < 0 || p->precision > 2) return fail(HTS_EINVAL, "precision must be 0, 1 or 2");
     const int R = (p->win - 1) / 2;
     const long long cap = (long long)std::min(R + 1, H - PS + 1) * std::min(R + 1, W - PS + 1);
     if (cap < p->K) return fail(HTS_EINVAL, "search window holds fewer than K patch positions");
@@ -328,7 +328,7 @@ hts_status check_basis(const hts_basis *basis, int C) {
 // second runs on the caller's stream; the threshold waits for both.
 hts_status launch_grouping(const float *img, const Geom &g, const hts_params &p, int32_t *idx, uint8_t *green,
                            int32_t *fb, DevState *st, cudaStream_t s) {
-    if (p.precision == 0) return launch_match(img, g, p.gamma_gcp, idx, green, fb, st, s);
+    if (p.precision != 1) return launch_match(img, g, p.gamma_gcp, idx, green, fb, st, s);
     if (g.C == 3) HTS_TRY(launch_gcp_flags(img, g, p.gamma_gcp, green, s));
     return launch_match_tc(img, g, idx, green, st, s);
 }

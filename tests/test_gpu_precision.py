@@ -100,7 +100,7 @@ def test_correlated_poisson_gaussian_256(oracle, hts):
 def test_precision_validation(hts):
     x = _dev(synth.make_config_image(256, 256, 1, 10.0, 5)[1])
     with pytest.raises(hts.HtsError):
-        hts.denoise(x, sigma=10.0, p=hts.params(precision=2))
+        hts.denoise(x, sigma=10.0, p=hts.params(precision=3))
     with pytest.raises(hts.HtsError):  # 63x63 window: the staged search region does not fit on chip
         hts.denoise(x, sigma=10.0, p=hts.params(win=63, precision=1))
 
@@ -120,3 +120,19 @@ def test_tensor_core_filter_reconstructs_and_thresholds(hts, C, K, win):
     assert hts.last_stats()["tau"] == 0.0
     zero = hts.denoise(x, sigma=1e6, p=p).cpu().numpy()
     assert np.all(zero == 0.0)
+
+
+@pytest.mark.parametrize("H,W,C,win,K,sigma,seed", CASES[:3])
+def test_exact_groups_with_tensor_core_filter(oracle, hts, H, W, C, win, K, sigma, seed):
+    # precision 2: the grouping of the plain form (bit-exact groups) and the filter of the precision form
+    clean, noisy = synth.make_config_image(H, W, C, sigma, seed)
+    x = _dev(noisy)
+    p2 = hts.params(K=K, win=win, precision=2)
+    idx2, green2 = hts.match(x, p2)
+    idx0, green0 = hts.match(x, hts.params(K=K, win=win))
+    assert torch.equal(idx2, idx0) and torch.equal(green2, green0)
+    out = hts.denoise(x, sigma=sigma, p=p2).cpu().numpy()
+    want, _ = oracle.denoise(noisy, oracle.Params(K=K, win=win), sigma=sigma)
+    assert abs(synth.psnr(out, clean) - synth.psnr(want, clean)) <= 0.05
+    # same groups: the filters differ only by FP16 rounding and the threshold decisions it moves
+    assert np.mean(np.abs(out.astype(np.float64) - want)) <= 0.05
