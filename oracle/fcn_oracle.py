@@ -1,0 +1,110 @@
+"""FP64 CPU oracle of the enhancement strategy's network -- TEST INFRASTRUCTURE ONLY.
+
+Only the test-suite and the benchmark may import this module; the CUDA
+library never calls it and shares no code with it.
+
+RA-Haar-tSVD (Eq. 24-25) refines the mean patch of every group with a plain
+fully connected network trained by residual learning.  Here: the input is
+the group's noisy mean patch scaled by 1/255 (C * 64 values, channel-major:
+t * 64 + u * 8 + v) followed by the noise level sigma / 255, zero-padded to a
+multiple of 16 features; two hidden layers of 128 units with ReLU; a linear
+output of C * 64 values, the residual: refined mean = noisy mean + 255 *
+output.  Training minimises the mean squared error of the scaled refined mean
+against the scaled clean mean (over samples and values) with Adam.
+
+Parameter vector layout (shared with the library's host interface): for
+every layer l, W_l[out][in] then b_l[out].
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+HIDDEN = 128
+ADAM_B1, ADAM_B2, ADAM_EPS = 0.9, 0.999, 1e-8
+
+
+def in_dim(C: int) -> int:
+    """C * 64 mean-patch values + sigma, padded to a multiple of 16."""
+    return (C * 64 + 1 + 15) // 16 * 16
+
+
+def layer_shapes(C: int):
+    """[(out, in)] of the three layers."""
+    return [(HIDDEN, in_dim(C)), (HIDDEN, HIDDEN), (C * 64, HIDDEN)]
+
+
+def num_params(C: int) -> int:
+    return sum(o * i + o for o, i in layer_shapes(C))
+
+
+def unpack(theta: np.ndarray, C: int):
+    out, o = [], 0
+    for n_out, n_in in layer_shapes(C):
+        w = np.asarray(theta[o:o + n_out * n_in], dtype=np.float64).reshape(n_out, n_in)
+        o += n_out * n_in
+        b = np.asarray(theta[o:o + n_out], dtype=np.float64)
+        o += n_out
+        out.append((w, b))
+    return out
+
+
+def features(means: np.ndarray, sigma, C: int) -> np.ndarray:
+    """Network input (n, in_dim): means / 255, then sigma / 255 (one value or one per sample), zeros."""
+    m = np.asarray(means, dtype=np.float64)
+    X = np.zeros((m.shape[0], in_dim(C)))
+    X[:, :C * 64] = m / 255.0
+    X[:, C * 64] = np.broadcast_to(np.asarray(sigma, dtype=np.float64), (m.shape[0],)) / 255.0
+    return X
+
+
+def forward(theta: np.ndarray, X: np.ndarray, C: int):
+    """Output (n, C * 64) and the cache for backward."""
+    layers = unpack(theta, C)
+    a = np.asarray(X, dtype=np.float64)
+    cache = [a]
+    for li, (w, b) in enumerate(layers):
+        z = a @ w.T + b
+        a = np.maximum(z, 0.0) if li < len(layers) - 1 else z
+        cache.append(a)
+    return a, cache
+
+
+def refine(theta: np.ndarray, means: np.ndarray, sigma, C: int) -> np.ndarray:
+    """Eq. 25: the refined mean patches, noisy mean + 255 * network output."""
+    out, _ = forward(theta, features(means, sigma, C), C)
+    return np.asarray(means, dtype=np.float64) + 255.0 * out
+
+
+def loss_and_dout(out: np.ndarray, noisy_means: np.ndarray, clean_means: np.ndarray):
+    """Mean squared error of (noisy + 255 out) / 255 against clean / 255, and d loss / d out."""
+    target = (np.asarray(clean_means, dtype=np.float64) - np.asarray(noisy_means, dtype=np.float64)) / 255.0
+    d = out - target
+    return float(np.mean(d * d)), 2.0 * d / d.size
+
+
+def backward(theta: np.ndarray, cache, dout: np.ndarray, C: int) -> np.ndarray:
+    """Gradient of sum(dout * out) with respect to the parameter vector."""
+    layers = unpack(theta, C)
+    d = np.asarray(dout, dtype=np.float64)
+    grads = []
+    for li in range(len(layers) - 1, -1, -1):
+        w, _ = layers[li]
+        if li < len(layers) - 1:
+            d = d * (cache[li + 1] > 0)
+        grads.append((d.T @ cache[li], d.sum(axis=0)))
+        d = d @ w
+    out = []
+    for dw, db in reversed(grads):
+        out.append(dw.reshape(-1))
+        out.append(db)
+    return np.concatenate(out)
+
+
+def adam_step(theta, m, v, g, t: int, lr: float):
+    """One Adam update (bias-corrected), returns (theta, m, v)."""
+    m = ADAM_B1 * m + (1 - ADAM_B1) * g
+    v = ADAM_B2 * v + (1 - ADAM_B2) * g * g
+    mh = m / (1 - ADAM_B1 ** t)
+    vh = v / (1 - ADAM_B2 ** t)
+    return theta - lr * mh / (np.sqrt(vh) + ADAM_EPS), m, v

@@ -490,12 +490,13 @@ static void gather_group(const float *img, int H, int W, int C, int ps, int K, c
  * stats (optional, 3 entries): coefficients kept, groups, max imaginary
  * residue x 1e18 (rounded).  Returns 0, or -1 on bad input. */
 static int denoise_groups_impl(const float *noisy, int H, int W, int C, const htso_params *p, const double *basis,
-                               double tau, const double *taus, const int32_t *idx, double *out, double *stats);
+                               double tau, const double *taus, const int32_t *idx, const double *mean_est,
+                               double *out, double *stats);
 
 int htso_denoise_groups(const float *noisy, int H, int W, int C, const htso_params *p,
                         const double *basis, double tau, const int32_t *idx, double *out, double *stats)
 {
-    return denoise_groups_impl(noisy, H, W, C, p, basis, tau, NULL, idx, out, stats);
+    return denoise_groups_impl(noisy, H, W, C, p, basis, tau, NULL, idx, NULL, out, stats);
 }
 
 /* The same with a threshold per group (taus[r] for reference r), for a
@@ -504,11 +505,26 @@ int htso_denoise_groups_taus(const float *noisy, int H, int W, int C, const htso
                              const double *basis, const double *taus, const int32_t *idx, double *out,
                              double *stats)
 {
-    return denoise_groups_impl(noisy, H, W, C, p, basis, 0.0, taus, idx, out, stats);
+    return denoise_groups_impl(noisy, H, W, C, p, basis, 0.0, taus, idx, NULL, out, stats);
+}
+
+/* RA-Haar-tSVD (the enhancement strategy, Eq. 24-25): as
+ * htso_denoise_groups_taus (taus NULL: one tau), with the first Haar row of
+ * every group (Eq. 24: sqrt(K) times the group's mean patch in the
+ * transform domain) replaced by sqrt(K) times the transform of a refined
+ * mean patch mean_est[r] (C x ps x ps doubles per reference, Eq. 25) and
+ * kept whole (not thresholded). */
+int htso_denoise_groups_ra(const float *noisy, int H, int W, int C, const htso_params *p, const double *basis,
+                           double tau, const double *taus, const int32_t *idx, const double *mean_est, double *out,
+                           double *stats)
+{
+    if (!mean_est) return -1;
+    return denoise_groups_impl(noisy, H, W, C, p, basis, tau, taus, idx, mean_est, out, stats);
 }
 
 static int denoise_groups_impl(const float *noisy, int H, int W, int C, const htso_params *p, const double *basis,
-                               double tau, const double *taus, const int32_t *idx, double *out, double *stats)
+                               double tau, const double *taus, const int32_t *idx, const double *mean_est,
+                               double *out, double *stats)
 {
     int ps = p->ps, K = p->K, n = ps * ps, m = C * n;
     int ny = htso_grid(H, ps, p->step, NULL), nx = htso_grid(W, ps, p->step, NULL);
@@ -531,6 +547,10 @@ static int denoise_groups_impl(const float *noisy, int H, int W, int C, const ht
             gather_group(noisy, H, W, C, ps, K, idx + (size_t)r * K, G);
             htso_group_forward(G, K, C, ps, basis, S);            /* Eq. 19 */
             kept_chunk += htso_threshold(S, (long)K * m, taus ? taus[r] : tau); /* Eq. 20 */
+            if (mean_est) { /* Eq. 24-25: Haar row 0 := sqrt(K) x transform of the refined mean patch */
+                htso_patch_forward(mean_est + (size_t)r * m, C, ps, basis, S);
+                for (long e = 0; e < 2 * (long)m; e++) S[e] = S[e] * sqrt((double)K);
+            }
             double im = htso_group_inverse(S, K, C, ps, basis, est + (size_t)(r - r0) * K * m); /* Eq. 21 */
             if (im > im_chunk) im_chunk = im;
             free(G);

@@ -92,6 +92,8 @@ def _lib():
             lib.htso_denoise_groups.restype = i
             lib.htso_denoise_groups_taus.argtypes = [P, i, i, i, P, P, P, P, P, P]
             lib.htso_denoise_groups_taus.restype = i
+            lib.htso_denoise_groups_ra.argtypes = [P, i, i, i, P, P, d, P, P, P, P, P]
+            lib.htso_denoise_groups_ra.restype = i
             lib.htso_group_lambdas.argtypes = [P, i, i, P]
             lib.htso_group_lambdas.restype = None
             lib.htso_rank_of_hat.argtypes = [P, i]
@@ -403,4 +405,72 @@ def denoise(noisy: np.ndarray, p: Params, sigma=None, basis: np.ndarray | None =
     out, st = denoise_groups(a, p, basis, t, idx)
     info.update(st)
     info.update({"sigma": sigma, "tau": t, "idx": idx, "green": green, "basis": basis})
+    return out, info
+
+
+# ------------------------------------------------ enhancement strategy (RA)
+
+def group_means(img: np.ndarray, idx: np.ndarray, ps: int = 8) -> np.ndarray:
+    """Mean patch of every group (Eq. 24 up to the sqrt(K) factor): (N_ref, C * ps * ps) FP64, entry
+    t * ps^2 + u * ps + v = mean over the group's members of pixel (u, v) of channel t."""
+    a = _img(img).astype(np.float64)
+    C, H, W = a.shape
+    idx = np.asarray(idx)
+    out = np.zeros((idx.shape[0], C, ps, ps))
+    for k in range(idx.shape[1]):
+        y, x = idx[:, k] // W, idx[:, k] % W
+        for u in range(ps):
+            for v in range(ps):
+                out[:, :, u, v] += a[:, y + u, x + v].T
+    return (out / idx.shape[1]).reshape(idx.shape[0], -1)
+
+
+def denoise_groups_ra(noisy: np.ndarray, p: Params, basis: np.ndarray, tau_value, idx: np.ndarray,
+                      mean_est: np.ndarray):
+    """Alg. 1 steps 2-3 with the enhancement strategy: the first Haar row of every group replaced by
+    sqrt(K) times the transform of mean_est[r] (N_ref, C * ps * ps) and kept whole (Eq. 24-25)."""
+    a = _img(noisy)
+    C, H, W = a.shape
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    me = np.ascontiguousarray(mean_est, dtype=np.float64)
+    if me.shape != (idx.shape[0], C * p.ps * p.ps):
+        raise ValueError("one refined mean patch per reference patch")
+    out = np.zeros((C, H, W))
+    st = np.zeros(3)
+    bf = basis_to_flat(basis)
+    ps = p.c_struct()
+    taus = None
+    if np.ndim(tau_value) != 0:
+        taus = np.ascontiguousarray(tau_value, dtype=np.float64).reshape(-1)
+    r = _lib().htso_denoise_groups_ra(_ptr(a), H, W, C, ctypes.byref(ps), _ptr(bf),
+                                      0.0 if taus is not None else float(tau_value),
+                                      None if taus is None else _ptr(taus), _ptr(idx), _ptr(me), _ptr(out), _ptr(st))
+    if r < 0:
+        raise ValueError("bad input")
+    return out, {"kept": int(st[0]), "groups": int(st[1]), "max_imag": float(st[2])}
+
+
+def denoise_ra(noisy: np.ndarray, p: Params, theta: np.ndarray, sigma=None, basis: np.ndarray | None = None):
+    """RA-Haar-tSVD: grouping, basis, noise level as denoise(); the mean patch of every group refined by
+    the fully connected network (fcn_oracle.refine, Eq. 25) replaces the group's first Haar row."""
+    from . import fcn_oracle
+
+    a = _img(noisy)
+    C = a.shape[0]
+    info: dict = {}
+    ev = nref = None
+    if basis is None or sigma is None:
+        b, ev, nref = estimate_basis(a, p)
+        if basis is None:
+            basis = b
+    idx, green, _ = match(a, p)
+    if sigma is None:
+        s = estimate_sigma(a, p, eigvals=ev, nref=nref, idx=idx)
+        info.update(s)
+        sigma = s["sigma_hat"]
+    means = group_means(a, idx, p.ps)
+    est = fcn_oracle.refine(theta, means, float(sigma), C)
+    out, st = denoise_groups_ra(a, p, basis, tau(float(sigma), C, p), idx, est)
+    info.update(st)
+    info.update({"sigma": sigma, "idx": idx, "basis": basis, "means": means, "mean_est": est})
     return out, info
