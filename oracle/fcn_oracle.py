@@ -4,13 +4,15 @@ Only the test-suite and the benchmark may import this module; the CUDA
 library never calls it and shares no code with it.
 
 RA-Haar-tSVD (Eq. 24-25) refines the mean patch of every group with a plain
-fully connected network trained by residual learning.  Here: the input is
-the group's noisy mean patch scaled by 1/255 (C * 64 values, channel-major:
-t * 64 + u * 8 + v) followed by the noise level sigma / 255, zero-padded to a
-multiple of 16 features; two hidden layers of 128 units with ReLU; a linear
-output of C * 64 values, the residual: refined mean = noisy mean + 255 *
-output.  Training minimises the mean squared error of the scaled refined mean
-against the scaled clean mean (over samples and values) with Adam.
+fully connected network trained by residual learning.  The mean patch enters
+in the image's transform (hts_oracle.mean_coefs: the orthonormal coordinates
+of Eq. 19 without the Haar factor, C * 64 values), where it is sparse.  The
+input is that vector divided by SCALE = 8 * 255 followed by sigma / 255,
+zero-padded to a multiple of 16 features; two hidden layers of 128 units
+with ReLU; a linear output of C * 64 values, the residual: refined =
+noisy + SCALE * output.  Training minimises the mean squared error of the
+scaled refined vector against the scaled clean one (over samples and values)
+with Adam.
 
 Parameter vector layout (shared with the library's host interface): for
 every layer l, W_l[out][in] then b_l[out].
@@ -21,6 +23,7 @@ from __future__ import annotations
 import numpy as np
 
 HIDDEN = 128
+SCALE = 8.0 * 255.0  # coefficient scale: a flat patch of value v has a largest coefficient of about 8 v (gray)
 ADAM_B1, ADAM_B2, ADAM_EPS = 0.9, 0.999, 1e-8
 
 
@@ -49,11 +52,11 @@ def unpack(theta: np.ndarray, C: int):
     return out
 
 
-def features(means: np.ndarray, sigma, C: int) -> np.ndarray:
-    """Network input (n, in_dim): means / 255, then sigma / 255 (one value or one per sample), zeros."""
-    m = np.asarray(means, dtype=np.float64)
+def features(coefs: np.ndarray, sigma, C: int) -> np.ndarray:
+    """Network input (n, in_dim): coefs / SCALE, then sigma / 255 (one value or one per sample), zeros."""
+    m = np.asarray(coefs, dtype=np.float64)
     X = np.zeros((m.shape[0], in_dim(C)))
-    X[:, :C * 64] = m / 255.0
+    X[:, :C * 64] = m / SCALE
     X[:, C * 64] = np.broadcast_to(np.asarray(sigma, dtype=np.float64), (m.shape[0],)) / 255.0
     return X
 
@@ -70,15 +73,15 @@ def forward(theta: np.ndarray, X: np.ndarray, C: int):
     return a, cache
 
 
-def refine(theta: np.ndarray, means: np.ndarray, sigma, C: int) -> np.ndarray:
-    """Eq. 25: the refined mean patches, noisy mean + 255 * network output."""
-    out, _ = forward(theta, features(means, sigma, C), C)
-    return np.asarray(means, dtype=np.float64) + 255.0 * out
+def refine(theta: np.ndarray, coefs: np.ndarray, sigma, C: int) -> np.ndarray:
+    """Eq. 25: the refined mean patches (transform coordinates), noisy + SCALE * network output."""
+    out, _ = forward(theta, features(coefs, sigma, C), C)
+    return np.asarray(coefs, dtype=np.float64) + SCALE * out
 
 
-def loss_and_dout(out: np.ndarray, noisy_means: np.ndarray, clean_means: np.ndarray):
-    """Mean squared error of (noisy + 255 out) / 255 against clean / 255, and d loss / d out."""
-    target = (np.asarray(clean_means, dtype=np.float64) - np.asarray(noisy_means, dtype=np.float64)) / 255.0
+def loss_and_dout(out: np.ndarray, noisy: np.ndarray, clean: np.ndarray):
+    """Mean squared error of (noisy + SCALE out) / SCALE against clean / SCALE, and d loss / d out."""
+    target = (np.asarray(clean, dtype=np.float64) - np.asarray(noisy, dtype=np.float64)) / SCALE
     d = out - target
     return float(np.mean(d * d)), 2.0 * d / d.size
 

@@ -425,6 +425,43 @@ def group_means(img: np.ndarray, idx: np.ndarray, ps: int = 8) -> np.ndarray:
     return (out / idx.shape[1]).reshape(idx.shape[0], -1)
 
 
+def mean_coefs(means: np.ndarray, basis: np.ndarray, C: int, ps: int = 8) -> np.ndarray:
+    """Mean patches (n, C ps^2) in the image's transform (Eq. 19 without the Haar factor, one patch): the
+    real vector [S^(1), sqrt(2) Re S^(2), sqrt(2) Im S^(2)] (C = 3; slice 3 is the conjugate of slice 2,
+    so the vector has the patch's norm) or S^(1) (C = 1), each slice row-major."""
+    m = np.ascontiguousarray(means, dtype=np.float64)
+    n2 = ps * ps
+    bf = basis_to_flat(basis)
+    S = np.zeros(2 * C * n2)
+    out = np.zeros((m.shape[0], C * n2))
+    for r in range(m.shape[0]):
+        _lib().htso_patch_forward(_ptr(np.ascontiguousarray(m[r])), C, ps, _ptr(bf), _ptr(S))
+        out[r, :n2] = S[0:2 * n2:2]
+        if C == 3:
+            out[r, n2:2 * n2] = math.sqrt(2.0) * S[2 * n2:4 * n2:2]
+            out[r, 2 * n2:] = math.sqrt(2.0) * S[2 * n2 + 1:4 * n2:2]
+    return out
+
+
+def coefs_to_patch(coefs: np.ndarray, basis: np.ndarray, C: int, ps: int = 8) -> np.ndarray:
+    """Inverse of mean_coefs (Eq. 21 without the Haar factor): (n, C ps^2) pixel-domain patches."""
+    c = np.asarray(coefs, dtype=np.float64)
+    n2 = ps * ps
+    bf = basis_to_flat(basis)
+    out = np.zeros((c.shape[0], C * n2))
+    P = np.zeros(C * n2)
+    for r in range(c.shape[0]):
+        S = np.zeros(2 * C * n2)
+        S[0:2 * n2:2] = c[r, :n2]
+        if C == 3:
+            re, im = c[r, n2:2 * n2] / math.sqrt(2.0), c[r, 2 * n2:] / math.sqrt(2.0)
+            S[2 * n2:4 * n2:2], S[2 * n2 + 1:4 * n2:2] = re, im
+            S[4 * n2::2], S[4 * n2 + 1::2] = re, -im
+        _lib().htso_patch_inverse(_ptr(S), C, ps, _ptr(bf), _ptr(P))
+        out[r] = P
+    return out
+
+
 def denoise_groups_ra(noisy: np.ndarray, p: Params, basis: np.ndarray, tau_value, idx: np.ndarray,
                       mean_est: np.ndarray):
     """Alg. 1 steps 2-3 with the enhancement strategy: the first Haar row of every group replaced by
@@ -451,8 +488,9 @@ def denoise_groups_ra(noisy: np.ndarray, p: Params, basis: np.ndarray, tau_value
 
 
 def denoise_ra(noisy: np.ndarray, p: Params, theta: np.ndarray, sigma=None, basis: np.ndarray | None = None):
-    """RA-Haar-tSVD: grouping, basis, noise level as denoise(); the mean patch of every group refined by
-    the fully connected network (fcn_oracle.refine, Eq. 25) replaces the group's first Haar row."""
+    """RA-Haar-tSVD: grouping, basis, noise level as denoise(); the mean patch of every group, in the
+    image's transform (mean_coefs), refined by the fully connected network (fcn_oracle.refine, Eq. 25),
+    replaces the group's first Haar row."""
     from . import fcn_oracle
 
     a = _img(noisy)
@@ -469,8 +507,9 @@ def denoise_ra(noisy: np.ndarray, p: Params, theta: np.ndarray, sigma=None, basi
         info.update(s)
         sigma = s["sigma_hat"]
     means = group_means(a, idx, p.ps)
-    est = fcn_oracle.refine(theta, means, float(sigma), C)
+    coefs = mean_coefs(means, basis, C, p.ps)
+    est = coefs_to_patch(fcn_oracle.refine(theta, coefs, float(sigma), C), basis, C, p.ps)
     out, st = denoise_groups_ra(a, p, basis, tau(float(sigma), C, p), idx, est)
     info.update(st)
-    info.update({"sigma": sigma, "idx": idx, "basis": basis, "means": means, "mean_est": est})
+    info.update({"sigma": sigma, "idx": idx, "basis": basis, "means": means, "coefs": coefs, "mean_est": est})
     return out, info

@@ -54,7 +54,7 @@ def test_loss_gradient_and_layout():
     # features: the means scaled, then sigma, then zeros up to a multiple of 16
     X = fo.features(noisy, 51.0, 3)
     assert X.shape == (3, 208)
-    np.testing.assert_array_equal(X[:, :192], noisy / 255.0)
+    np.testing.assert_array_equal(X[:, :192], noisy / fo.SCALE)
     assert np.all(X[:, 192] == 51.0 / 255.0) and np.all(X[:, 193:] == 0.0)
 
 
@@ -101,3 +101,16 @@ def test_group_means_brute_force(oracle):
     for r in range(2):
         want = np.mean([noisy[:, q // 21:q // 21 + 8, q % 21:q % 21 + 8].astype(np.float64) for q in idx[r]], axis=0)
         np.testing.assert_allclose(m[r], want.reshape(-1), rtol=1e-12)
+
+
+@pytest.mark.parametrize("C", [1, 3])
+def test_mean_coefs_orthonormal_round_trip(oracle, C):
+    # the coordinates keep the norm (Parseval: unitary DFT along the channels, orthonormal bases, the
+    # conjugate slice counted by sqrt(2)) and the inverse gives the patches back
+    clean, noisy = synth.make_config_image(30, 35, C, 30.0, 80 + C)
+    p = oracle.Params(K=8, win=9)
+    basis, _, _ = oracle.estimate_basis(noisy, p)
+    x = np.random.default_rng(C).uniform(0, 255, size=(6, C * 64))
+    c = oracle.mean_coefs(x, basis, C)
+    np.testing.assert_allclose(np.linalg.norm(c, axis=1), np.linalg.norm(x, axis=1), rtol=1e-12)
+    np.testing.assert_allclose(oracle.coefs_to_patch(c, basis, C), x, rtol=1e-12, atol=1e-9)
