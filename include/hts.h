@@ -271,6 +271,62 @@ hts_status hts_cnn_load(const char *path, hts_cnn **out);
 hts_status hts_denoise_learned(const float *noisy, float *out, int H, int W, int C, hts_cnn *net,
                                const hts_basis *basis, const hts_params *p, double fallback_factor, void *stream);
 
+/* -------------------------------------- enhancement strategy (RA-Haar-tSVD) */
+
+/* RA-Haar-tSVD (Eq. 24-25): the first Haar row of every group -- sqrt(K)
+ * times its mean patch in the transform domain -- is replaced by sqrt(K)
+ * times the transform of the mean patch refined by a plain fully connected
+ * network, and kept whole (not thresholded); the other rows are filtered as
+ * usual.  The network sees the mean patch c in the image's transform
+ * coordinates (hts_mean_coefs; pixels channel-major, t * 64 + u * 8 + v) in
+ * units of its noise level s = sigma / sqrt(K): input g(c / s), g(x) = x /
+ * (1 + |x| / 16), then sigma / 255, zero-padded to a multiple of 16; two
+ * hidden layers of 128 ReLU units; linear output r of C x 64 values;
+ * refined = c + s r (residual learning).  FP32 weights and arithmetic,
+ * trained by the library's own kernels (mean squared error of r against
+ * (clean - noisy) / s, Adam).  Not thread-safe. */
+typedef struct hts_fcn hts_fcn;
+int hts_fcn_num_params(int C); /* 0 for C not in {1, 3} */
+int hts_fcn_channels(const hts_fcn *fcn);
+int hts_fcn_group_size(const hts_fcn *fcn); /* K of the network, 0 for NULL */
+/* New network for C channels and groups of K patches (He initialisation from
+ * `seed`, output layer scaled by 0.1, zero biases); synchronous. */
+hts_status hts_fcn_create(int C, int K, uint64_t seed, hts_fcn **out);
+hts_status hts_fcn_free(hts_fcn *fcn);
+/* Parameters, per layer W[out][in] then b[out] (host, hts_fcn_num_params(C)
+ * floats); set resets the optimiser state.  Synchronous. */
+hts_status hts_fcn_get_params(const hts_fcn *fcn, float *host_params);
+hts_status hts_fcn_set_params(hts_fcn *fcn, const float *host_params);
+/* Mean patch of every group (device: idx N_ref x K from hts_match, means out
+ * N_ref x C x 64). */
+hts_status hts_group_means(const float *img, int H, int W, int C, const hts_params *p, const int32_t *idx,
+                           float *means, void *stream);
+/* The image transform of n patches (Eq. 19 without the Haar factor; device,
+ * n x C x 64 in and out): [S^(1), sqrt 2 Re S^(2), sqrt 2 Im S^(2)] (C = 3,
+ * orthonormal) or S^(1) (C = 1), with the given basis; inverse != 0 maps
+ * coordinates back to pixels.  The network reads and refines these. */
+hts_status hts_mean_coefs(const float *in, int n, int C, const hts_basis *basis, int inverse, float *out,
+                          void *stream);
+/* Refined coordinates of n mean patches (device: coords n x C x 64, sigma n
+ * values, refined out n x C x 64). */
+hts_status hts_fcn_refine(hts_fcn *fcn, const float *means, const float *sigma, int n, float *refined, void *stream);
+/* Training on n pairs (device: noisy and clean mean-patch coordinates
+ * n x C x 64, the noise level of each); gradients add up until
+ * hts_fcn_zero_grad, the loss (mean over the n x C x 64 values) until
+ * hts_fcn_take_loss (synchronises). */
+hts_status hts_fcn_zero_grad(hts_fcn *fcn, void *stream);
+hts_status hts_fcn_accumulate_grad(hts_fcn *fcn, const float *noisy_means, const float *clean_means,
+                                   const float *sigma, int n, void *stream);
+hts_status hts_fcn_take_loss(hts_fcn *fcn, double *loss_sum, void *stream);
+hts_status hts_fcn_get_grad(const hts_fcn *fcn, float *host_grad, void *stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected). */
+hts_status hts_fcn_adam_step(hts_fcn *fcn, float lr, void *stream);
+/* hts_denoise with the enhancement strategy; the network sees the call's
+ * sigma (given, or estimated as in hts_denoise).  Needs the tensor-core
+ * filter: p->precision 1 or 2 (else HTS_EUNSUPPORTED).  Asynchronous. */
+hts_status hts_denoise_ra(const float *noisy, float *out, int H, int W, int C, float sigma, hts_fcn *fcn,
+                          const hts_basis *basis, const hts_params *p, void *stream);
+
 /* ------------------------------------------------- inspection / tests */
 
 /* Grouping step alone (Eq. 9, Alg. 1 step 1): idx_out (device, int32,

@@ -6,13 +6,14 @@ library never calls it and shares no code with it.
 RA-Haar-tSVD (Eq. 24-25) refines the mean patch of every group with a plain
 fully connected network trained by residual learning.  The mean patch enters
 in the image's transform (hts_oracle.mean_coefs: the orthonormal coordinates
-of Eq. 19 without the Haar factor, C * 64 values), where it is sparse.  The
-input is that vector divided by SCALE = 8 * 255 followed by sigma / 255,
-zero-padded to a multiple of 16 features; two hidden layers of 128 units
-with ReLU; a linear output of C * 64 values, the residual: refined =
-noisy + SCALE * output.  Training minimises the mean squared error of the
-scaled refined vector against the scaled clean one (over samples and values)
-with Adam.
+of Eq. 19 without the Haar factor, C * 64 values), where it is sparse, and in
+units of its noise level s = sigma / sqrt(K) (the mean of K patches): the
+input is g(c / s) with g(x) = x / (1 + |x| / 16) (noise-only coordinates
+stay near x, strong ones saturate), then sigma / 255, zero-padded to a
+multiple of 16 features; two hidden layers of 128 units with ReLU; a linear
+output of C * 64 values, the residual in noise units: refined = c + s *
+output.  Training minimises the mean squared error of the output against
+(clean - noisy) / s over samples and values with Adam.
 
 Parameter vector layout (shared with the library's host interface): for
 every layer l, W_l[out][in] then b_l[out].
@@ -23,7 +24,7 @@ from __future__ import annotations
 import numpy as np
 
 HIDDEN = 128
-SCALE = 8.0 * 255.0  # coefficient scale: a flat patch of value v has a largest coefficient of about 8 v (gray)
+SAT = 16.0  # saturation of the input compression g
 ADAM_B1, ADAM_B2, ADAM_EPS = 0.9, 0.999, 1e-8
 
 
@@ -52,11 +53,18 @@ def unpack(theta: np.ndarray, C: int):
     return out
 
 
-def features(coefs: np.ndarray, sigma, C: int) -> np.ndarray:
-    """Network input (n, in_dim): coefs / SCALE, then sigma / 255 (one value or one per sample), zeros."""
+def noise_unit(sigma, K: int, n: int) -> np.ndarray:
+    """s = sigma / sqrt(K) per sample (n,)."""
+    return np.broadcast_to(np.asarray(sigma, dtype=np.float64), (n,)) / np.sqrt(K)
+
+
+def features(coefs: np.ndarray, sigma, C: int, K: int) -> np.ndarray:
+    """Network input (n, in_dim): g(coefs / s), then sigma / 255 (one value or one per sample), zeros."""
     m = np.asarray(coefs, dtype=np.float64)
+    s = noise_unit(sigma, K, m.shape[0])[:, None]
+    x = m / s
     X = np.zeros((m.shape[0], in_dim(C)))
-    X[:, :C * 64] = m / SCALE
+    X[:, :C * 64] = x / (1.0 + np.abs(x) / SAT)
     X[:, C * 64] = np.broadcast_to(np.asarray(sigma, dtype=np.float64), (m.shape[0],)) / 255.0
     return X
 
@@ -73,15 +81,17 @@ def forward(theta: np.ndarray, X: np.ndarray, C: int):
     return a, cache
 
 
-def refine(theta: np.ndarray, coefs: np.ndarray, sigma, C: int) -> np.ndarray:
-    """Eq. 25: the refined mean patches (transform coordinates), noisy + SCALE * network output."""
-    out, _ = forward(theta, features(coefs, sigma, C), C)
-    return np.asarray(coefs, dtype=np.float64) + SCALE * out
+def refine(theta: np.ndarray, coefs: np.ndarray, sigma, C: int, K: int) -> np.ndarray:
+    """Eq. 25: the refined mean patches (transform coordinates), c + s * network output."""
+    c = np.asarray(coefs, dtype=np.float64)
+    out, _ = forward(theta, features(c, sigma, C, K), C)
+    return c + noise_unit(sigma, K, c.shape[0])[:, None] * out
 
 
-def loss_and_dout(out: np.ndarray, noisy: np.ndarray, clean: np.ndarray):
-    """Mean squared error of (noisy + SCALE out) / SCALE against clean / SCALE, and d loss / d out."""
-    target = (np.asarray(clean, dtype=np.float64) - np.asarray(noisy, dtype=np.float64)) / SCALE
+def loss_and_dout(out: np.ndarray, noisy: np.ndarray, clean: np.ndarray, sigma, K: int):
+    """Mean squared error of the output against (clean - noisy) / s, and d loss / d out."""
+    n = np.asarray(noisy, dtype=np.float64)
+    target = (np.asarray(clean, dtype=np.float64) - n) / noise_unit(sigma, K, n.shape[0])[:, None]
     d = out - target
     return float(np.mean(d * d)), 2.0 * d / d.size
 

@@ -425,13 +425,27 @@ def group_means(img: np.ndarray, idx: np.ndarray, ps: int = 8) -> np.ndarray:
     return (out / idx.shape[1]).reshape(idx.shape[0], -1)
 
 
+def canonical_basis(basis: np.ndarray) -> np.ndarray:
+    """Every eigenvector (column i of U^(j), V^(j)) multiplied by the conjugate phase of its largest-
+    magnitude entry (ties to the lower row), which becomes real positive: eigenvectors are defined up to
+    that phase (the filter is invariant to it), the network's coordinates need one fixed choice."""
+    b = np.array(basis, dtype=np.complex128)
+    for j in range(b.shape[0]):
+        for m in range(2):
+            for i in range(b.shape[3]):
+                col = b[j, m, :, i]
+                a = int(np.argmax(np.abs(col) ** 2))  # first maximum
+                b[j, m, :, i] = col * np.conj(col[a]) / abs(col[a])
+    return b
+
+
 def mean_coefs(means: np.ndarray, basis: np.ndarray, C: int, ps: int = 8) -> np.ndarray:
-    """Mean patches (n, C ps^2) in the image's transform (Eq. 19 without the Haar factor, one patch): the
-    real vector [S^(1), sqrt(2) Re S^(2), sqrt(2) Im S^(2)] (C = 3; slice 3 is the conjugate of slice 2,
-    so the vector has the patch's norm) or S^(1) (C = 1), each slice row-major."""
+    """Mean patches (n, C ps^2) in the image's transform (Eq. 19 without the Haar factor, one patch) with
+    the canonical basis: the real vector [S^(1), sqrt(2) Re S^(2), sqrt(2) Im S^(2)] (C = 3; slice 3 is the
+    conjugate of slice 2, so the vector has the patch's norm) or S^(1) (C = 1), each slice row-major."""
     m = np.ascontiguousarray(means, dtype=np.float64)
     n2 = ps * ps
-    bf = basis_to_flat(basis)
+    bf = basis_to_flat(canonical_basis(basis))
     S = np.zeros(2 * C * n2)
     out = np.zeros((m.shape[0], C * n2))
     for r in range(m.shape[0]):
@@ -447,7 +461,7 @@ def coefs_to_patch(coefs: np.ndarray, basis: np.ndarray, C: int, ps: int = 8) ->
     """Inverse of mean_coefs (Eq. 21 without the Haar factor): (n, C ps^2) pixel-domain patches."""
     c = np.asarray(coefs, dtype=np.float64)
     n2 = ps * ps
-    bf = basis_to_flat(basis)
+    bf = basis_to_flat(canonical_basis(basis))
     out = np.zeros((c.shape[0], C * n2))
     P = np.zeros(C * n2)
     for r in range(c.shape[0]):
@@ -508,7 +522,7 @@ def denoise_ra(noisy: np.ndarray, p: Params, theta: np.ndarray, sigma=None, basi
         sigma = s["sigma_hat"]
     means = group_means(a, idx, p.ps)
     coefs = mean_coefs(means, basis, C, p.ps)
-    est = coefs_to_patch(fcn_oracle.refine(theta, coefs, float(sigma), C), basis, C, p.ps)
+    est = coefs_to_patch(fcn_oracle.refine(theta, coefs, float(sigma), C, p.K), basis, C, p.ps)
     out, st = denoise_groups_ra(a, p, basis, tau(float(sigma), C, p), idx, est)
     info.update(st)
     info.update({"sigma": sigma, "idx": idx, "basis": basis, "means": means, "coefs": coefs, "mean_est": est})

@@ -151,9 +151,10 @@ struct Workspace : Bufs {
     cudaStream_t stream = nullptr;
     size_t cap_idx = 0, cap_fb = 0, cap_redo = 0, cap_green = 0, cap_hw = 0, cap_chw = 0, cap_cov = 0;
     size_t cap_x = 0, cap_xskip = 0;
-    size_t cap_in = 0, cap_out = 0, cap_sref = 0;
+    size_t cap_in = 0, cap_out = 0, cap_sref = 0, cap_ra = 0;
     float *io_in = nullptr, *io_out = nullptr;
     float *sref = nullptr;  // learned noise level per reference patch
+    float *ra = nullptr;    // enhancement strategy: mean patches and refined ones
 };
 
 static std::mutex g_mu;
@@ -334,7 +335,8 @@ hts_status launch_grouping(const float *img, const Geom &g, const hts_params &p,
 }
 
 hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
-                       const hts_params &p, const Bufs &b, cudaStream_t s, float *sigma_ref, double fallback_factor) {
+                       const hts_params &p, const Bufs &b, cudaStream_t s, float *sigma_ref, double fallback_factor,
+                       hts_fcn *fcn, float *ra_buf) {
     const Bufs *w = &b;
     const size_t hw = (size_t)g.H * g.W;
     HTS_TRY(cuda_ok(cudaMemsetAsync(w->st, 0, sizeof(DevState), s), "cudaMemsetAsync(state)"));
@@ -360,8 +362,16 @@ hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigm
     if (need_sigma) HTS_TRY(launch_sigma_final(g, p, w->st, s));
     else HTS_TRY(launch_set_sigma(sigma > 0 ? (double)sigma : 0.0, g, p, w->st, s));
     if (sigma_ref && fallback_factor > 0) HTS_TRY(launch_learned_check(sigma_ref, g.nref, fallback_factor, w->st, s));
+    float *mean_est = nullptr;
+    if (fcn) {  // enhancement strategy: refined mean patch of every group (Eq. 24-25)
+        float *means = ra_buf, *refined = ra_buf + (size_t)g.nref * g.C * 64;
+        HTS_TRY(launch_group_means(noisy, g, w->idx, means, s));
+        HTS_TRY(fcn_refine_state(fcn, means, g.nref, w->st, b32, refined, s));
+        mean_est = refined;
+    }
     return launch_filter(noisy, g, w->idx, b64, b32, w->acc, w->wcount, w->redo, w->xlist, w->xskip, w->st, out,
-                         p.precision == 0 ? 1 : 0, sigma_ref, fallback_factor > 0 ? 1 : 0, tau_scale(g, p), s);
+                         p.precision == 0 ? 1 : 0, sigma_ref, fallback_factor > 0 ? 1 : 0, tau_scale(g, p), s,
+                         mean_est);
 }
 
 static hts_status denoise_impl(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
@@ -655,6 +665,25 @@ hts_status hts_denoise_learned(const float *noisy, float *out, int H, int W, int
     return denoise_run(noisy, out, g, -1.f, basis, *p, *w, s, w->sref, fallback_factor);
 }
 
+hts_status hts_denoise_ra(const float *noisy, float *out, int H, int W, int C, float sigma, hts_fcn *fcn,
+                          const hts_basis *basis, const hts_params *p, void *stream) {
+    Geom g;
+    HTS_TRY(validate(H, W, C, p, &g));
+    if (!noisy || !out || !fcn) return fail(HTS_EINVAL, "NULL pointer");
+    if (noisy == out) return fail(HTS_EINVAL, "out may not alias noisy");
+    if (!std::isfinite(sigma)) return fail(HTS_EINVAL, "sigma must be finite");
+    if (p->precision == 0) return fail(HTS_EUNSUPPORTED, "the enhancement strategy needs precision 1 or 2");
+    if (hts_fcn_channels(fcn) != C) return fail(HTS_EINVAL, "network built for another channel count");
+    if (hts_fcn_group_size(fcn) != p->K) return fail(HTS_EINVAL, "network built for another group size");
+    HTS_TRY(check_basis(basis, C));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace *w;
+    HTS_TRY(get_ws(s, &w));
+    HTS_TRY(ensure(w, g));
+    HTS_TRY(grow(w->ra, w->cap_ra, (size_t)2 * g.nref * C * 64, "cudaMalloc(enhancement)"));
+    return denoise_run(noisy, out, g, sigma, basis, *p, *w, s, nullptr, 0.0, fcn, w->ra);
+}
+
 hts_status hts_last_stats(hts_stats *out, void *stream) {
     if (!out) return fail(HTS_EINVAL, "NULL pointer");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -750,6 +779,7 @@ hts_status hts_shutdown(void) {
         cudaFree(w->io_in);
         cudaFree(w->io_out);
         cudaFree(w->sref);
+        cudaFree(w->ra);
         if (w->ev_fork) cudaEventDestroy(w->ev_fork);
         if (w->ev_join) cudaEventDestroy(w->ev_join);
         if (w->aux) cudaStreamDestroy(w->aux);

@@ -1521,7 +1521,7 @@ void set_tuned_tile(const Geom &g, TileChoice c) {
 hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, const double *b64, const float *b32,
                          long long *acc, int *wcount, int32_t *redo_list, int4 *xlist, uint8_t *xskip,
                          DevState *st, float *out, int exact, const float *sigma_ref, int map_judged, double tau_scale,
-                         cudaStream_t s) {
+                         cudaStream_t s, const float *mean_est) {
     FilterArgs a;
     a.img = img;
     a.H = g.H;
@@ -1545,11 +1545,13 @@ hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, co
     a.map_judged = map_judged;
     a.xskip = xskip;
     a.st = st;
+    if (mean_est && exact) return report(HTS_EUNSUPPORTED, "the enhancement strategy needs the tensor-core filter");
     if (!exact) {  // precision form: the tensor-core filter where a tile fits
         bool used = false;
         const hts_status st0 =
-            launch_filter_tc(img, g, idx, b32, acc, wcount, st, sigma_ref, map_judged, tau_scale, s, &used);
+            launch_filter_tc(img, g, idx, b32, acc, wcount, st, sigma_ref, map_judged, tau_scale, mean_est, s, &used);
         if (st0 != HTS_OK) return st0;
+        if (!used && mean_est) return report(HTS_EUNSUPPORTED, "the enhancement strategy needs the tensor-core filter");
         if (used) {
             int dev = 0, nsm = 152;
             cudaGetDevice(&dev);

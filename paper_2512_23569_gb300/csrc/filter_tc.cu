@@ -86,6 +86,7 @@ struct FtcArgs {
     const float *sigma_ref;
     int map_judged;
     double tau_scale;
+    const float *mean_est;  // [N_ref][C][64] refined mean patches (enhancement strategy) or nullptr
     DevState *st;
     int ty, tx, nty, ntx, ntiles, rh_max, rw_max;
 };
@@ -109,6 +110,7 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t HW = (size_t)a.H * a.W;
     const bool use_map = a.sigma_ref && (!a.map_judged || a.st->learned);
+    const bool ra = a.mean_est != nullptr;
 
     // ---- bases (row-major 8x8, element (r, c) at r * 8 + c) and the Kronecker matrices
     for (int t = tid; t < 64; t += NT) {
@@ -346,6 +348,7 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
                             if (!(mag >= tau)) x[k] = 0.f;
                         }
                     }
+                    if (ra) x[0] = 0.f;  // Haar row 0 (Eq. 8 order): its refined value is added after the inverse
                     haar_inv<K>(x);
 #pragma unroll
                     for (int k = 0; k < K; k += 4)
@@ -378,6 +381,11 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
                 const int m = 32 * q + lane;
                 const int pos = bPos[m];
                 const int py = pos >= 0 ? pos / a.W : 0, px = pos >= 0 ? pos - py * a.W : 0;
+                const float *mrow = nullptr;  // the member's group's refined mean patch (enhancement strategy)
+                if (ra && pos >= 0) {
+                    const int lg = b * GPB + m / K;
+                    mrow = a.mean_est + (size_t)((gy0 + lg / a.tx) * a.nx + gx0 + lg % a.tx) * (C * 64);
+                }
 #pragma unroll 1
                 for (int rr = 0; rr < 2; ++rr) {
                     const int row = 2 * wq + rr;
@@ -401,6 +409,12 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
                             out[1][v] = (f0 - fr - 2.f * S3H * fi) * K3F;
                             out[2][v] = (f0 - fr + 2.f * S3H * fi) * K3F;
                         }
+                    }
+                    if (mrow) {  // first Haar row replaced (Eq. 24-25): the refined mean joins every member
+#pragma unroll
+                        for (int c = 0; c < C; ++c)
+#pragma unroll
+                            for (int v = 0; v < 8; ++v) out[c][v] += __ldg(mrow + c * 64 + row * 8 + v);
                     }
                     const int ly = py + row - ry0, lx = px - rx0;
                     if (ly >= 0 && ly < rh && lx >= 0 && lx + 7 < rw) {
@@ -490,7 +504,7 @@ hts_status launch_ftc(FtcArgs a, const Geom &g, cudaStream_t s, bool *used) {
 
 hts_status launch_filter_tc(const float *img, const Geom &g, const int32_t *idx, const float *b32, long long *acc,
                             int *wcount, DevState *st, const float *sigma_ref, int map_judged, double tau_scale,
-                            cudaStream_t s, bool *used) {
+                            const float *mean_est, cudaStream_t s, bool *used) {
     *used = false;
     FtcArgs a{};
     a.img = img;
@@ -507,6 +521,7 @@ hts_status launch_filter_tc(const float *img, const Geom &g, const int32_t *idx,
     a.sigma_ref = sigma_ref;
     a.map_judged = map_judged;
     a.tau_scale = tau_scale;
+    a.mean_est = mean_est;
     a.st = st;
 #define HTS_FTC_CASE(CC, KK) \
     if (g.C == CC && g.K == KK) return launch_ftc<CC, KK>(a, g, s, used);

@@ -135,10 +135,13 @@ hts_status launch_sigma_final(const Geom &g, const hts_params &p, DevState *st, 
 // map_judged = 1 the map is used only if DevState.learned is set (else the
 // state's threshold).
 constexpr int XLIST_PER_REF = 4;
+// mean_est (device, N_ref x C x 64, may be nullptr; tensor-core filter only): the
+// enhancement strategy's refined mean patch of every group, which replaces the
+// group's first Haar row (Eq. 24-25).
 hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, const double *b64, const float *b32,
                          long long *acc, int *wcount, int32_t *redo_list, int4 *xlist, uint8_t *xskip,
                          DevState *st, float *out, int exact, const float *sigma_ref, int map_judged,
-                         double tau_scale, cudaStream_t s);
+                         double tau_scale, cudaStream_t s, const float *mean_est = nullptr);
 double tau_scale(const Geom &g, const hts_params &p);  // sigma -> tau factor (sigma.cu)
 // Tensor-core filter of the precision form (filter_tc.cu): FP16 Kronecker
 // projections on tcgen05, FP32 decisions, tile aggregation into acc / wcount
@@ -146,7 +149,14 @@ double tau_scale(const Geom &g, const hts_params &p);  // sigma -> tau factor (s
 // size or the window does not fit it.
 hts_status launch_filter_tc(const float *img, const Geom &g, const int32_t *idx, const float *b32, long long *acc,
                             int *wcount, DevState *st, const float *sigma_ref, int map_judged, double tau_scale,
-                            cudaStream_t s, bool *used);
+                            const float *mean_est, cudaStream_t s, bool *used);
+// Enhancement strategy (fcn.cu): mean patch of every group (N_ref x C x 64,
+// channel-major) and its refinement by the network with the state's sigma in
+// the basis b32's coordinates (buf is overwritten; the refined patch in
+// pixels lands in out).
+hts_status launch_group_means(const float *img, const Geom &g, const int32_t *idx, float *means, cudaStream_t s);
+hts_status fcn_refine_state(hts_fcn *f, float *buf, int n, const DevState *st, const float *b32, float *out,
+                            cudaStream_t s);
 
 // Filter tile shape (k_filter_tile): ty x tx reference positions per tile,
 // ty = 0 for the non-local mode (no tile accumulators).  The launch uses, in
@@ -194,9 +204,10 @@ void batch_shutdown();
 // sigma_ref (device, N_ref, may be nullptr): a noise level per reference
 // patch; with a fallback factor > 0 it is checked against the estimated
 // level (launch_learned_check) and the estimate is used if it fails.
+// fcn (may be nullptr) with ra_buf (2 N_ref C 64 floats): the enhancement strategy.
 hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
                        const hts_params &p, const Bufs &b, cudaStream_t s, float *sigma_ref = nullptr,
-                       double fallback_factor = 0.0);
+                       double fallback_factor = 0.0, hts_fcn *fcn = nullptr, float *ra_buf = nullptr);
 
 }  // namespace hts
 

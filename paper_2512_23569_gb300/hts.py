@@ -33,6 +33,10 @@ EXPORTS = [
     "hts_cnn_free", "hts_cnn_get_params", "hts_cnn_set_params", "hts_cnn_log_sigma_map", "hts_cnn_sigma_refs",
     "hts_cnn_zero_grad", "hts_cnn_accumulate_grad", "hts_cnn_take_loss", "hts_cnn_get_grad", "hts_cnn_adam_step",
     "hts_cnn_save", "hts_cnn_load", "hts_cnn_set_window", "hts_cnn_window",
+    "hts_fcn_num_params", "hts_fcn_channels", "hts_fcn_create", "hts_fcn_free", "hts_fcn_get_params",
+    "hts_fcn_set_params", "hts_group_means", "hts_fcn_refine", "hts_fcn_zero_grad", "hts_fcn_accumulate_grad",
+    "hts_fcn_take_loss", "hts_fcn_get_grad", "hts_fcn_adam_step", "hts_denoise_ra", "hts_mean_coefs",
+    "hts_fcn_group_size",
 ]
 
 
@@ -132,6 +136,25 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.hts_cnn_set_window.argtypes = [P, I]
         lib.hts_cnn_window.argtypes = [P]
         lib.hts_cnn_window.restype = I
+        lib.hts_fcn_num_params.argtypes = [I]
+        lib.hts_fcn_num_params.restype = I
+        lib.hts_fcn_channels.argtypes = [P]
+        lib.hts_fcn_channels.restype = I
+        lib.hts_fcn_create.argtypes = [I, I, ctypes.c_uint64, ctypes.POINTER(P)]
+        lib.hts_fcn_group_size.argtypes = [P]
+        lib.hts_fcn_group_size.restype = I
+        lib.hts_fcn_free.argtypes = [P]
+        lib.hts_fcn_get_params.argtypes = [P, P]
+        lib.hts_fcn_set_params.argtypes = [P, P]
+        lib.hts_group_means.argtypes = [P, I, I, I, PP, P, P, P]
+        lib.hts_fcn_refine.argtypes = [P, P, P, I, P, P]
+        lib.hts_fcn_zero_grad.argtypes = [P, P]
+        lib.hts_fcn_accumulate_grad.argtypes = [P, P, P, P, I, P]
+        lib.hts_fcn_take_loss.argtypes = [P, ctypes.POINTER(D), P]
+        lib.hts_fcn_get_grad.argtypes = [P, P, P]
+        lib.hts_fcn_adam_step.argtypes = [P, F, P]
+        lib.hts_denoise_ra.argtypes = [P, P, I, I, I, F, P, P, PP, P]
+        lib.hts_mean_coefs.argtypes = [P, I, I, P, I, P, P]
         for name in EXPORTS:  # fail loudly on a library that lacks a declared entry point
             getattr(lib, name)
         _LIB = lib
@@ -447,6 +470,126 @@ def denoise_learned(noisy, net: Cnn, p: Params | None = None, basis: Basis | Non
     _check(load().hts_denoise_learned(ctypes.c_void_p(noisy.data_ptr()), ctypes.c_void_p(out.data_ptr()), H, W, C,
                                       net.handle, basis.handle if basis else None, ctypes.byref(p),
                                       float(fallback_factor), _stream(stream)))
+    return out
+
+
+def _cuda_f32(t, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("%s: expected a contiguous CUDA float32 tensor" % name)
+    return t
+
+
+class Fcn:
+    """Owns an hts_fcn* (the enhancement strategy's network: mean patch -> refined mean patch)."""
+
+    def __init__(self, C: int = 1, K: int = 16, seed: int = 1):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.hts_fcn_create(C, K, seed, ctypes.byref(h)))
+        self._h = h
+        self.C = C
+        self.K = K
+        self.nparams = int(lib.hts_fcn_num_params(C))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.nparams, dtype=np.float32)
+        _check(load().hts_fcn_get_params(self._h, ctypes.c_void_p(a.ctypes.data)))
+        return a
+
+    def set_params(self, theta) -> None:
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        if a.size != self.nparams:
+            raise ValueError("expected %d parameters" % self.nparams)
+        _check(load().hts_fcn_set_params(self._h, ctypes.c_void_p(a.ctypes.data)))
+
+    def refine(self, means, sigma, stream=None):
+        """Refined mean-patch coordinates (n, C * 64) of coordinates (n, C * 64), noise level of each (n,)."""
+        import torch
+
+        _cuda_f32(means, "means")
+        _cuda_f32(sigma, "sigma")
+        n = means.shape[0]
+        out = torch.empty_like(means)
+        _check(load().hts_fcn_refine(self._h, ctypes.c_void_p(means.data_ptr()), ctypes.c_void_p(sigma.data_ptr()),
+                                     n, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def zero_grad(self, stream=None) -> None:
+        _check(load().hts_fcn_zero_grad(self._h, _stream(stream)))
+
+    def accumulate_grad(self, noisy_means, clean_means, sigma, stream=None) -> None:
+        for t, nm in ((noisy_means, "noisy_means"), (clean_means, "clean_means"), (sigma, "sigma")):
+            _cuda_f32(t, nm)
+        _check(load().hts_fcn_accumulate_grad(self._h, ctypes.c_void_p(noisy_means.data_ptr()),
+                                              ctypes.c_void_p(clean_means.data_ptr()),
+                                              ctypes.c_void_p(sigma.data_ptr()), noisy_means.shape[0],
+                                              _stream(stream)))
+
+    def take_loss(self, stream=None) -> float:
+        v = ctypes.c_double()
+        _check(load().hts_fcn_take_loss(self._h, ctypes.byref(v), _stream(stream)))
+        return v.value
+
+    def get_grad(self, stream=None) -> np.ndarray:
+        a = np.empty(self.nparams, dtype=np.float32)
+        _check(load().hts_fcn_get_grad(self._h, ctypes.c_void_p(a.ctypes.data), _stream(stream)))
+        return a
+
+    def adam_step(self, lr: float, stream=None) -> None:
+        _check(load().hts_fcn_adam_step(self._h, float(lr), _stream(stream)))
+
+    def __del__(self):
+        try:
+            if self._h and _LIB is not None:
+                _LIB.hts_fcn_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+def group_means(img, idx, p: Params | None = None, stream=None):
+    """Mean patch of every group (N_ref, C * 64) for the groups idx (N_ref, K) of hts_match."""
+    import torch
+
+    img = _chw(img)
+    p = p or params()
+    C, H, W = img.shape
+    out = torch.empty((idx.shape[0], C * 64), dtype=torch.float32, device=img.device)
+    _check(load().hts_group_means(ctypes.c_void_p(img.data_ptr()), H, W, C, ctypes.byref(p),
+                                  ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def mean_coefs(x, basis: Basis, inverse: bool = False, stream=None):
+    """Image-transform coordinates of patches (n, C * 64) with the basis (inverse: back to pixels)."""
+    import torch
+
+    _cuda_f32(x, "x")
+    out = torch.empty_like(x)
+    _check(load().hts_mean_coefs(ctypes.c_void_p(x.data_ptr()), x.shape[0], basis.C, basis.handle,
+                                 1 if inverse else 0, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def denoise_ra(noisy, fcn: Fcn, sigma: float | None = None, p: Params | None = None, basis: Basis | None = None,
+               out=None, stream=None):
+    """hts_denoise_ra: RA-Haar-tSVD (the groups' first Haar rows from the network's refined mean patches)."""
+    import torch
+
+    noisy = _chw(noisy)
+    p = p or params(precision=2)
+    C, H, W = noisy.shape
+    if out is None:
+        out = torch.empty_like(noisy)
+    s = -1.0 if sigma is None else float(sigma)
+    _check(load().hts_denoise_ra(ctypes.c_void_p(noisy.data_ptr()), ctypes.c_void_p(out.data_ptr()), H, W, C, s,
+                                 fcn.handle, basis.handle if basis else None, ctypes.byref(p), _stream(stream)))
     return out
 
 

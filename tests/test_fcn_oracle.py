@@ -21,7 +21,7 @@ from paper_2512_23569_gb300 import synth
 def test_backward_matches_finite_differences(C):
     rng = np.random.default_rng(20 + C)
     theta = rng.standard_normal(fo.num_params(C)) * 0.1
-    X = fo.features(rng.uniform(0, 255, size=(5, C * 64)), rng.uniform(30, 80, size=5), C)
+    X = fo.features(rng.uniform(-255, 255, size=(5, C * 64)), rng.uniform(30, 80, size=5), C, 16)
     dout = rng.standard_normal((5, C * 64))
     out, cache = fo.forward(theta, X, C)
     g = fo.backward(theta, cache, dout, C)
@@ -43,19 +43,22 @@ def test_loss_gradient_and_layout():
     rng = np.random.default_rng(4)
     noisy, clean = rng.uniform(0, 255, size=(3, 192)), rng.uniform(0, 255, size=(3, 192))
     out = rng.standard_normal((3, 192)) * 0.1
-    L, d = fo.loss_and_dout(out, noisy, clean)
+    sig = np.array([30.0, 50.0, 70.0])
+    L, d = fo.loss_and_dout(out, noisy, clean, sig, 16)
     eps = 1e-7
     for (i, j) in ((0, 0), (2, 191), (1, 77)):
         op, om = out.copy(), out.copy()
         op[i, j] += eps
         om[i, j] -= eps
-        fd = (fo.loss_and_dout(op, noisy, clean)[0] - fo.loss_and_dout(om, noisy, clean)[0]) / (2 * eps)
-        assert abs(fd - d[i, j]) <= 1e-6
-    # features: the means scaled, then sigma, then zeros up to a multiple of 16
-    X = fo.features(noisy, 51.0, 3)
-    assert X.shape == (3, 208)
-    np.testing.assert_array_equal(X[:, :192], noisy / fo.SCALE)
-    assert np.all(X[:, 192] == 51.0 / 255.0) and np.all(X[:, 193:] == 0.0)
+        fd = (fo.loss_and_dout(op, noisy, clean, sig, 16)[0] - fo.loss_and_dout(om, noisy, clean, sig, 16)[0]) / (2 * eps)
+        assert abs(fd - d[i, j]) <= 1e-6 * (1 + abs(fd))
+    # features: g(c / s) with s = sigma / sqrt(K), then sigma, then zeros up to a multiple of 16;
+    # g is odd, g(16) = 8, g(x) -> 16 for large x
+    X = fo.features(np.array([[16 * 12.5, -16 * 12.5, 0.0] + [1e9] * 189]), 50.0, 3, 16)
+    assert X.shape == (1, 208)
+    np.testing.assert_allclose(X[0, :3], [8.0, -8.0, 0.0], rtol=1e-12)
+    assert abs(X[0, 3] - 16.0) < 1e-5
+    assert X[0, 192] == 50.0 / 255.0 and np.all(X[:, 193:] == 0.0)
 
 
 def test_zero_output_layer_refines_to_the_input_and_adam():
@@ -64,7 +67,7 @@ def test_zero_output_layer_refines_to_the_input_and_adam():
     n_last = 64 * fo.HIDDEN + 64
     theta[-n_last:] = 0.0
     means = rng.uniform(0, 255, size=(4, 64))
-    np.testing.assert_array_equal(fo.refine(theta, means, 40.0, 1), means)
+    np.testing.assert_array_equal(fo.refine(theta, means, 40.0, 1, 16), means)
     g = np.array([0.5, -2.0, 1e-3])
     th, _, _ = fo.adam_step(np.zeros(3), np.zeros(3), np.zeros(3), g, 1, 0.01)
     np.testing.assert_allclose(th, -0.01 * g / (np.abs(g) + fo.ADAM_EPS), rtol=1e-12)
@@ -114,3 +117,15 @@ def test_mean_coefs_orthonormal_round_trip(oracle, C):
     c = oracle.mean_coefs(x, basis, C)
     np.testing.assert_allclose(np.linalg.norm(c, axis=1), np.linalg.norm(x, axis=1), rtol=1e-12)
     np.testing.assert_allclose(oracle.coefs_to_patch(c, basis, C), x, rtol=1e-12, atol=1e-9)
+
+
+def test_coordinates_do_not_depend_on_eigenvector_phases(oracle):
+    # multiplying eigenvectors by arbitrary phases (signs for the real slice) leaves the coordinates unchanged
+    clean, noisy = synth.make_config_image(30, 35, 3, 30.0, 85)
+    basis, _, _ = oracle.estimate_basis(noisy, oracle.Params(K=8, win=9))
+    rng = np.random.default_rng(8)
+    b2 = np.array(basis)
+    b2[0] *= rng.choice([-1.0, 1.0], size=(2, 1, 8))
+    b2[1] *= np.exp(1j * rng.uniform(0, 2 * np.pi, size=(2, 1, 8)))
+    x = rng.uniform(0, 255, size=(4, 192))
+    np.testing.assert_allclose(oracle.mean_coefs(x, b2, 3), oracle.mean_coefs(x, basis, 3), rtol=1e-10, atol=1e-9)
