@@ -40,6 +40,9 @@ WORKLOAD = {
 }
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 L2_FLUSH_BYTES = 512 << 20
+FORMS = {0: "plain: FP32 certified grouping, FP32 filter with FP64 decisions in the error band",
+         1: "precision form: BF16 tensor-core grouping, FP16 tensor-core filter, FP32 decisions",
+         2: "exact groups of the plain form, FP16 tensor-core filter, FP32 decisions"}
 
 
 def _peaks():
@@ -209,7 +212,9 @@ def batch_images(n=64, seed=4000):
 
 
 def run_batch(args):
-    """One step = one hts_denoise_batch call (one graph launch) over the 64-image batch."""
+    """One step = one hts_denoise_batch call (one graph launch) over the 64-image batch, for the plain form
+    and the exact-group tensor-core form (precision 2); the line reports the faster one within 0.05 dB of
+    the oracle on the checked images ("plain vs chosen")."""
     import numpy as np
     import torch
 
@@ -220,75 +225,91 @@ def run_batch(args):
     hts.load()
     imgs = batch_images()
     xs = [torch.from_numpy(n).cuda() for _, n, _ in imgs]
-    outs = [torch.empty_like(x) for x in xs]
     sig = [s for _, _, s in imgs]
-    pg, pc = hts.params(win=21), hts.params(win=31)
-    per = [pc if n.shape[0] == 3 else pg for _, n, _ in imgs]
     mpx = sum(n.shape[1] * n.shape[2] for _, n, _ in imgs) / 1e6
     stream = torch.cuda.current_stream()
-    t0 = time.perf_counter()
-    hts.denoise_batch(xs, sig, hts.params(), outs=outs, per_image=per)  # builds, autotunes
-    torch.cuda.synchronize()
-    build_s = time.perf_counter() - t0
-    for _ in range(max(args.warmup, 3)):
-        hts.denoise_batch(xs, sig, hts.params(), outs=outs, per_image=per)
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(0)
-    clocks.start()
-    l0 = hts.launch_count()
-    for i in range(args.steps):
-        evs[i][0].record(stream)
-        hts.denoise_batch(xs, sig, hts.params(), outs=outs, per_image=per)
-        evs[i][1].record(stream)
-    torch.cuda.synchronize()
-    launches = hts.launch_count() - l0
-    clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
-    per_stats, info = hts.last_batch_stats(len(xs))
-    # the same images one hts_denoise call after another (plain path)
-    plain = [torch.empty_like(x) for x in xs]
-    for x, s, pi, y in zip(xs, sig, per, plain):
-        hts.denoise(x, sigma=s, p=pi, out=y)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for x, s, pi, y in zip(xs, sig, per, plain):
-        hts.denoise(x, sigma=s, p=pi, out=y)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    plain_ms = e0.elapsed_time(e1)
-    same = all(torch.equal(a, b) for a, b in zip(outs, plain))
+
+    def timed(prec):
+        outs = [torch.empty_like(x) for x in xs]
+        pg, pc = hts.params(win=21, precision=prec), hts.params(win=31, precision=prec)
+        per = [pc if n.shape[0] == 3 else pg for _, n, _ in imgs]
+        t0 = time.perf_counter()
+        hts.denoise_batch(xs, sig, hts.params(), outs=outs, per_image=per)  # builds, autotunes
+        torch.cuda.synchronize()
+        build_s = time.perf_counter() - t0
+        for _ in range(max(args.warmup, 3)):
+            hts.denoise_batch(xs, sig, hts.params(), outs=outs, per_image=per)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        clocks = ClockSampler(0)
+        clocks.start()
+        l0 = hts.launch_count()
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            hts.denoise_batch(xs, sig, hts.params(), outs=outs, per_image=per)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        launches = hts.launch_count() - l0
+        clk = clocks.stop()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+        per_stats, info = hts.last_batch_stats(len(xs))
+        # the same images one hts_denoise call after another
+        single = [torch.empty_like(x) for x in xs]
+        for x, s_, pi, y in zip(xs, sig, per, single):
+            hts.denoise(x, sigma=s_, p=pi, out=y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for x, s_, pi, y in zip(xs, sig, per, single):
+            hts.denoise(x, sigma=s_, p=pi, out=y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms = e0.elapsed_time(e1)
+        same = all(torch.equal(a_, b_) for a_, b_ in zip(outs, single))
+        return {"ms": ms, "value": mpx / (ms / 1e3), "outs": outs, "info": info, "stats": per_stats,
+                "build_s": build_s, "launches": launches, "clocks": clk, "seq_ms": seq_ms, "same": same}
+
+    res = {0: timed(0), 2: timed(2)}
     # per-image error against the oracle on a bounded sample (the smallest images, ~20 s of CPU)
-    worst_abs, worst_dpsnr, checked, t0 = 0.0, 0.0, 0, time.perf_counter()
+    worst = {k: [0.0, 0.0] for k in res}
+    checked, t0 = 0, time.perf_counter()
     order = sorted(range(len(imgs)), key=lambda i: imgs[i][1].size)
     for i in order:
         if time.perf_counter() - t0 > 20.0:
             break
-        clean, noisy, s = imgs[i]
+        clean, noisy, s_ = imgs[i]
         po = o.Params(win=31 if noisy.shape[0] == 3 else 21)
-        want, _ = o.denoise(noisy, po, sigma=s)
-        got = outs[i].cpu().numpy().astype(np.float64)
-        worst_abs = max(worst_abs, float(np.max(np.abs(got - want))))
-        worst_dpsnr = max(worst_dpsnr, abs(synth.psnr(got, clean) - synth.psnr(want, clean)))
+        want, _ = o.denoise(noisy, po, sigma=s_)
+        for k, r in res.items():
+            got = r["outs"][i].cpu().numpy().astype(np.float64)
+            worst[k][0] = max(worst[k][0], float(np.max(np.abs(got - want))))
+            worst[k][1] = max(worst[k][1], abs(synth.psnr(got, clean) - synth.psnr(want, clean)))
         checked += 1
+    ok = [k for k in res if worst[k][1] <= 0.05]
+    chosen = min(ok, key=lambda k: res[k]["ms"]) if ok else 0
+    r = res[chosen]
     line = {
         "metric": "Mpixel/s denoised on 1 GB300, batched form (one graph launch per batch)",
-        "value": mpx / (ms / 1e3), "unit": "Mpixel/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
+        "value": r["value"], "unit": "Mpixel/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if chosen == 0 else "f32 matching / f16 filter", "data": "synthetic",
         "config": {"workload": "64 images, H x W uniform over 256x256, 384x512, 768x1024, 1536x2048, half gray "
                                "(21x21 window) half colour (31x31), AWGN sigma ~ U[10,75] known, K=16, step 4",
-                   "megapixels": mpx, "seed": 4000,
+                   "megapixels": mpx, "seed": 4000, "chosen_precision": chosen, "chosen_form": FORMS[chosen],
                    "l2": "inputs and outputs (%.0f MB) exceed L2; no flush" % (
                        sum(x.numel() for x in xs) * 8 / 1e6)},
-        "batch": info, "first_call_s": build_s,
-        "plain_sequential": {"ms": plain_ms, "value": mpx / (plain_ms / 1e3), "bitwise_equal": same},
-        "speedup_vs_plain": plain_ms / ms,
-        "oracle_check": {"images": checked, "max_abs": worst_abs, "max_psnr_delta_db": worst_dpsnr},
-        "clocks": clk, "gpu_launches": int(launches),
-        "redo_groups": sum(st["filter_redo"] for st in per_stats),
-        "exact_coefs": sum(st["filter_exact"] for st in per_stats),
+        "batch": r["info"], "first_call_s": r["build_s"],
+        "sequential_calls": {"ms": r["seq_ms"], "value": mpx / (r["seq_ms"] / 1e3), "bitwise_equal": r["same"]},
+        "speedup_vs_sequential": r["seq_ms"] / r["ms"],
+        "forms": {str(k): {"form": FORMS[k], "value": v["value"], "ms_per_step": v["ms"],
+                           "sequential_value": mpx / (v["seq_ms"] / 1e3), "bitwise_equal_to_sequential": v["same"],
+                           "oracle_max_abs": worst[k][0], "oracle_max_psnr_delta_db": worst[k][1]}
+                  for k, v in res.items()},
+        "oracle_check": {"images": checked, "max_abs": worst[chosen][0], "max_psnr_delta_db": worst[chosen][1]},
+        "clocks": r["clocks"], "gpu_launches": int(r["launches"]),
+        "redo_groups": sum(st["filter_redo"] for st in r["stats"]),
+        "exact_coefs": sum(st["filter_exact"] for st in r["stats"]),
     }
     print(json.dumps(line))
     return 0
@@ -698,10 +719,6 @@ def run_reference(args):
     print(json.dumps(line))
     return 0
 
-
-FORMS = {0: "plain: FP32 certified grouping, FP32 filter with FP64 decisions in the error band",
-         1: "precision form: BF16 tensor-core grouping, FP16 tensor-core filter, FP32 decisions",
-         2: "exact groups of the plain form, FP16 tensor-core filter, FP32 decisions"}
 
 
 def run_ours(args):

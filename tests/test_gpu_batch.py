@@ -135,3 +135,15 @@ def test_per_image_parameters(hts):
     outs = hts.denoise_batch(xs, sig, hts.params(), per_image=per)
     for x, s, pi, o in zip(xs, sig, per, outs):
         np.testing.assert_array_equal(hts.denoise(x, sigma=s, p=pi).cpu().numpy(), o.cpu().numpy())
+
+
+def test_batch_tensor_core_filter_equals_single_calls(hts):
+    # precision 2 (exact groups, tensor-core filter) in the graph equals the per-image calls bit for bit
+    pg, pc = hts.params(win=11, K=8, precision=2), hts.params(win=15, precision=2)
+    imgs = _images()
+    xs = [_dev(n) for _, n, _ in imgs]
+    sig = [s for _, _, s in imgs]
+    per = [pg if C == 1 else pc for (_, _, C, _, _) in BATCH]
+    outs = hts.denoise_batch(xs, sig, hts.params(), per_image=per)
+    for x, s, pi, o in zip(xs, sig, per, outs):
+        np.testing.assert_array_equal(hts.denoise(x, sigma=s, p=pi).cpu().numpy(), o.cpu().numpy())
