@@ -1371,6 +1371,26 @@ __global__ void k_normalize(const long long *__restrict__ acc, const int *__rest
     }
 }
 
+// The same, four pixels per thread with 16-byte loads and stores (HW a multiple of 4, 16-byte aligned
+// arrays): each pixel's weight is read once for all channels.
+template <int C>
+__global__ void k_normalize4(const longlong2 *__restrict__ acc, const int4 *__restrict__ wcount, float4 *__restrict__ out,
+                             size_t HW4) {
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < HW4; q += (size_t)gridDim.x * blockDim.x) {
+        const int4 w = __ldg(wcount + q);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const longlong2 a0 = __ldg(acc + (c * HW4 + q) * 2), a1 = __ldg(acc + (c * HW4 + q) * 2 + 1);
+            float4 o;
+            o.x = __ll2float_rn(a0.x) * (1.0f / 65536.0f) / (float)w.x;
+            o.y = __ll2float_rn(a0.y) * (1.0f / 65536.0f) / (float)w.y;
+            o.z = __ll2float_rn(a1.x) * (1.0f / 65536.0f) / (float)w.z;
+            o.w = __ll2float_rn(a1.y) * (1.0f / 65536.0f) / (float)w.w;
+            out[c * HW4 + q] = o;
+        }
+    }
+}
+
 template <int C, int K>
 size_t exact_smem() {
     constexpr int NCOEF = Cfg<C>::NCOEF;
@@ -1422,9 +1442,22 @@ std::vector<int> tune_key(const Geom &g) {
 
 hts_status launch_normalize(const long long *acc, const int *wcount, float *out, size_t HW, int C, int nsm,
                             cudaStream_t s) {
-    int nb = (int)((HW * C + 255) / 256);
-    if (nb > nsm * 16) nb = nsm * 16;
-    {
+    const bool vec = HW % 4 == 0 && ((reinterpret_cast<uintptr_t>(acc) | reinterpret_cast<uintptr_t>(wcount) |
+                                      reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    if (vec) {
+        const size_t HW4 = HW / 4;
+        int nb = (int)((HW4 + 255) / 256);
+        if (nb > nsm * 8) nb = nsm * 8;
+        KTimer kt("k_normalize", s);
+        if (C == 1)
+            k_normalize4<1><<<nb, 256, 0, s>>>(reinterpret_cast<const longlong2 *>(acc),
+                                               reinterpret_cast<const int4 *>(wcount), reinterpret_cast<float4 *>(out), HW4);
+        else
+            k_normalize4<3><<<nb, 256, 0, s>>>(reinterpret_cast<const longlong2 *>(acc),
+                                               reinterpret_cast<const int4 *>(wcount), reinterpret_cast<float4 *>(out), HW4);
+    } else {
+        int nb = (int)((HW * C + 255) / 256);
+        if (nb > nsm * 16) nb = nsm * 16;
         KTimer kt("k_normalize", s);
         k_normalize<<<nb, 256, 0, s>>>(acc, wcount, out, HW, C);
     }
