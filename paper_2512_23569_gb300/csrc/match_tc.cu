@@ -3,33 +3,35 @@
 //
 // For a reference a and a candidate b of the same matching plane,
 //   ||a - b||^2 = ||a||^2 + ||b||^2 - 2 a.b,
-// and the cross terms of every candidate position of a tile's search region
-// against the tile's 64 references (8 x 8 grid positions) form one BF16 GEMM
-// with FP32 accumulation (tcgen05.mma, accumulator in TMEM):
-//   D[p][r] = sum_{u<8, v<8} plane[y_p + u][x_p + v] * A[r][8u+v].
-// No candidate matrix is materialised: the region is staged once as
-// "row-8 vectors" Q[p] = plane[y_p][x_p .. x_p+7] (16 bytes, one core-matrix
-// row), candidates are numbered p = y * Wc + x in the region, and the K slice
-// of patch rows (u, u+1) of the M = 128 candidates p0 .. p0+127 is the
-// shared-memory matrix starting at Q[p0 + u Wc] with core matrices 8 rows
-// (128 bytes) apart along M and Wc rows (16 Wc bytes) apart along K.
+// and the cross terms of a tile of 128 references (16 grid rows x 8 grid
+// columns) against the candidate positions of the tile's search region form
+// BF16 GEMMs with FP32 accumulation in tensor memory (tcgen05.mma kind::f16):
+// the references are the MMA's M = 128 rows, so reference m's distances land
+// in tensor-memory lane m.  No candidate matrix is materialised: the region is
+// staged once as "row-8 vectors" Q[p] = plane[y_p][x_p .. x_p+7] (16 bytes,
+// one core-matrix row), candidates are numbered p = y * Wc + x in the region,
+// and the K slice of patch rows (u, u+1) of the candidates p0 .. p0+63 is the
+// shared-memory matrix starting at Q[p0 + u Wc], core matrices 8 rows (128
+// bytes) apart along N and Wc rows (16 Wc bytes) apart along K.
 //
-// The candidates are the MMA's M dimension, so a warp reading 32 TMEM lanes
-// (eight warps: two per lane quarter, each taking 32 of the reference
-// columns) holds, for each reference, 32 candidates side by side: the
-// filter "inside the reference's search window and below its threshold" is a
-// warp ballot, and the passing candidates are appended to the reference's
-// list at a prefix-sum position (one shared atomic per reference and warp).
-// Four TMEM accumulators of 64 columns let the MMAs run up to three chunks
-// ahead of the warps.  A reference's threshold starts at 1.5 times the
-// (K-1)-th smallest BF16 distance to the positions around it (so its K-1
-// nearest candidates always pass) and drops to its list's 2K-th smallest
-// when the list is cut back (warp-cooperative bisection, between chunks).
-// At the end every reference's kept candidates are re-ranked with FP32
-// distances of the FP32 plane and the K-1 smallest (ties to the lower raster
-// index) follow the reference in its group.  Eq. 9 picks the plane per
-// reference: a colour tile runs once per plane that one of its references
-// uses.
+// Warp w reads lanes 32 (w % 4) .. + 31: the references of tile rows
+// 4 (w % 4) .. + 3, whose search windows cover a band of the region's rows.
+// Each run gives every lane quarter the next 64 candidates of its own band
+// (four N = 64 MMAs into 256 tensor-memory columns), so all eight warps read
+// 32 columns per run -- every warp has the same work in every run.  A thread
+// turns its reference's 32 cross terms into keys (the distance's float bits
+// with the low bits replaced by the candidate's index, so equal distances
+// keep the lower index first) and keeps the LH smallest keys below its bound
+// in a sorted register list.  The bound starts at the (K-1)-th smallest BF16
+// distance to the 24 (K = 32: 48) positions around the reference, plus a
+// margin for the MMA's different rounding, so its K-1 nearest always enter,
+// and follows the list's last entry.  Two accumulators of 256 columns let the
+// MMAs of the next run go while the current one is read.  At the end the two
+// lists of a reference (one per half of each run's columns) are merged, their
+// LH smallest keys re-ranked with FP32 distances of the FP32 plane, and the
+// K-1 smallest by (distance, raster index) follow the reference in its
+// group.  Eq. 9 picks the plane per reference: a colour tile runs once per
+// plane that one of its references uses.
 //
 // Every mbarrier wait is bounded; a wait that gives up records error code 2
 // in the call's state, and the block waits (bounded) for the MMAs it has
@@ -44,19 +46,20 @@
 namespace hts {
 namespace {
 
-constexpr int TTY = 8, TTX = 8;  // reference tile (grid rows x grid columns)
-constexpr int NR = TTY * TTX;    // references per tile = MMA N
-constexpr int MC = 128;          // candidates per chunk = MMA M
-constexpr int NBUF = 4;          // TMEM accumulators (NR columns each)
-constexpr uint32_t TMEM_COLS = 256;
+constexpr int TTY = 16, TTX = 8;  // reference tile (grid rows x grid columns)
+constexpr int NR = TTY * TTX;     // references per tile = MMA M
+constexpr int NQ = 4;             // lane quarters (tile rows 4q .. 4q+3)
+constexpr int CH = 64;            // candidates per quarter and run = MMA N
+constexpr int RUNC = NQ * CH;     // tensor-memory columns per run
+constexpr int NBUF = 2;           // accumulators
+constexpr uint32_t TMEM_COLS = NBUF * RUNC;
 constexpr long long SPIN = 1ll << 24;
 constexpr unsigned FULLM = 0xffffffffu;
-constexpr int NT = 256;  // threads: warp w reads TMEM lanes 32 (w % 4) .. +31 (its candidates) and the
-                         // columns of references 32 (w / 4) .. +31
+constexpr int NT = 256;  // warp w: lanes 32 (w % 4) .. + 31, columns 32 (w / 4) .. + 31 of its quarter's 64
 
 // Offsets (dy, dx) of the positions around a reference whose distances seed
-// its threshold, nearest first (the 7 x 7 square without its centre); the
-// first 24 fill the 5 x 5 square.
+// its bound, nearest first (the 7 x 7 square without its centre); the first
+// 24 fill the 5 x 5 square.
 constexpr int NSEED = 48;
 __constant__ signed char c_seed[NSEED][2] = {
     {0, 1},  {1, 0},   {0, -1},  {-1, 0},  {1, 1},   {1, -1},  {-1, 1},  {-1, -1}, {0, 2},   {2, 0},
@@ -75,17 +78,17 @@ struct TcArgs {
     int hc_max, wc_max;  // bounds of the candidate region over all tiles
 };
 
-// Candidates kept per reference for the FP32 re-rank (the "2K"; 48 for K =
-// 32) and the list capacity: a list is cut back to BUF once fewer than MC
-// free slots (a whole chunk) remain, so cuts are rarer the larger CAP is.
+// LH: keys each thread keeps (per half of the runs' columns) and the number
+// re-ranked in FP32 per reference; NS: seed positions.
 template <int K>
 struct ListCfg {
-    static constexpr int BUF = (2 * K < 8) ? 8 : (2 * K > 48 ? 48 : 2 * K);
-    static constexpr int CAP = BUF + MC + 48;
+    static constexpr int LH = K + (K / 2 > 8 ? K / 2 : 8);
+    static constexpr int NS = K <= 16 ? 24 : 48;
+    static_assert(NS >= K - 1, "the seeds must certify the (K-1)-th nearest");
 };
 
 struct TcLayout {
-    size_t q, a, e, ps, rn, bd, bp, ref, bar, total;
+    size_t q, a, e, ps, scr, ref, qr, bar, total;
 };
 
 __host__ __device__ inline size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -93,47 +96,45 @@ __host__ __device__ inline size_t up(size_t x, size_t a) { return (x + a - 1) / 
 // Per-reference record in shared memory.
 struct RefRec {
     int wy0, wy1, wx0, wx1;  // search window, region coordinates
-    int pself, mine, cnt, pad;
-    float a2, thr, pad1, pad2;
+    int pself, mine, pad0, pad1;
+    float a2;
+    uint32_t thrk;  // initial bound on the keys
+    int pad2, pad3;
 };
 
-// Shared memory: Q (row-8 vectors), A (references), E (squared norms), the
-// FP32 plane Ps, the row norms rn (only needed while E is formed), the lists
-// (overlaying rn), per-reference records, barriers.
+// Shared memory: Q (row-8 vectors), A (references), E (candidates' squared
+// norms), the FP32 plane Ps, a scratch area (row norms while E is formed, the
+// seed lists, then the key staging of the runs), per-reference records, the
+// quarters' candidate bands, barriers.  After the runs the final lists and
+// re-rank keys overlay Q / A / E.
 template <int K>
 __host__ __device__ inline TcLayout tc_layout(int hc_max, int wc_max) {
+    constexpr int LH = ListCfg<K>::LH;
     TcLayout L;
-    const size_t nch = ((size_t)hc_max * wc_max + MC - 1) / MC;
-    const size_t nq = nch * MC + 7 * (size_t)wc_max;
+    const size_t ncand = (size_t)hc_max * wc_max;
+    const size_t nq = ncand + CH + 7 * (size_t)wc_max;
     L.q = 0;
     L.a = up(L.q + nq * 16, 1024);
     L.e = L.a + (size_t)NR * 64 * 2;
-    L.ps = up(L.e + nch * MC * 4, 16);
-    L.rn = up(L.ps + (size_t)(hc_max + 7) * (wc_max + 7) * 4, 16);
-    L.bd = L.rn;
-    L.bp = L.bd + (size_t)NR * ListCfg<K>::CAP * 4;
-    const size_t lists_end = L.bp + (size_t)NR * ListCfg<K>::CAP * 4;
-    const size_t rn_end = L.rn + nq * 4;
-    L.ref = up(lists_end > rn_end ? lists_end : rn_end, 16);
-    L.bar = up(L.ref + (size_t)NR * sizeof(RefRec), 16);
-    L.total = L.bar + 128;
-    if (L.total < 120 * 1024) L.total = 120 * 1024;  // one block per SM
+    L.ps = up(L.e + (ncand + CH) * 4, 16);
+    const size_t fin_end = (size_t)LH * NR * 16;  // [2][LH][NR] keys + [LH][NR] re-rank keys
+    if (L.ps < fin_end) L.ps = up(fin_end, 16);
+    L.scr = up(L.ps + (size_t)(hc_max + 7) * (wc_max + 7) * 4, 16);
+    size_t scr = nq * 4;
+    if (scr < (size_t)32 * NT * 4) scr = (size_t)32 * NT * 4;
+    if (scr < (size_t)2 * (K - 1) * NR * 4) scr = (size_t)2 * (K - 1) * NR * 4;
+    L.ref = up(L.scr + scr, 16);
+    L.qr = L.ref + (size_t)NR * sizeof(RefRec);
+    L.bar = up(L.qr + NQ * sizeof(int2), 16);
+    L.total = L.bar + 64;
+    // one block per SM, and never beside a block of the other tensor-core kernels (whose tensor
+    // memory would not fit beside this block's 512 columns)
+    if (L.total < 160 * 1024) L.total = 160 * 1024;
     return L;
 }
 
-using tc::bar_init;
-using tc::mma_commit;
 using tc::sdesc;
 using tc::su32;
-using tc::tmem_ld32;
-using tc::tmem_wait_ld;
-__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) { return tc::idesc_f16(M, N, true); }
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc) {
-    tc::mma_f16(d, ad, bd, id, acc);
-}
-__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) { return tc::bar_wait(bar, parity, SPIN); }
-__device__ __forceinline__ void tc_fence_before() { tc::fence_before(); }
-__device__ __forceinline__ void tc_fence_after() { tc::fence_after(); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half)
@@ -156,93 +157,40 @@ __device__ __forceinline__ float row_dist2(uint4 x, uint4 y, float acc) {
     return acc;
 }
 
-// Warp-cooperative cut of reference j's list (n entries at j * CAP) back to
-// `keep` entries containing every entry below the returned T (the smallest
-// value, to a 12-step bisection of the list's range, with at least `keep`
-// entries <= T); the kept entries stay in list order.
-template <int CAP>
-__device__ float cut_list_warp(float *bd, int *bp, int j, int n, int keep, int lane, int *n_out) {
-    constexpr int PER = (CAP + 31) / 32;
-    float dv[PER];
-    int pv[PER];
-    float lo = __builtin_huge_valf(), hi = -__builtin_huge_valf();
-#pragma unroll
-    for (int t = 0; t < PER; ++t) {
-        const int i = t * 32 + lane;
-        dv[t] = (i < n) ? bd[j * CAP + i] : __builtin_huge_valf();
-        pv[t] = (i < n) ? bp[j * CAP + i] : 0;
-        if (i < n) {
-            lo = fminf(lo, dv[t]);
-            hi = fmaxf(hi, dv[t]);
-        }
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        lo = fminf(lo, __shfl_xor_sync(FULLM, lo, o));
-        hi = fmaxf(hi, __shfl_xor_sync(FULLM, hi, o));
-    }
-    for (int it = 0; it < 12; ++it) {  // invariant: count(<= hi) >= keep
-        const float mid = 0.5f * (lo + hi);
-        int c = 0;
-#pragma unroll
-        for (int t = 0; t < PER; ++t) c += __popc(__ballot_sync(FULLM, dv[t] <= mid));
-        if (c >= keep) hi = mid;
-        else lo = mid;
-    }
-    __syncwarp();
-    int w = 0;
-#pragma unroll
-    for (int t = 0; t < PER; ++t) {  // stable compaction: entries <= hi, at most `keep`
-        const bool k = dv[t] <= hi;
-        const uint32_t m = __ballot_sync(FULLM, k);
-        const int pos = w + __popc(m & ((1u << lane) - 1u));
-        if (k && pos < keep) {
-            bd[j * CAP + pos] = dv[t];
-            bp[j * CAP + pos] = pv[t];
-        }
-        w += __popc(m);
-    }
-    __syncwarp();
-    *n_out = w < keep ? w : keep;
-    return hi;
-}
-
 template <int K>
 __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
-    constexpr int BUF = ListCfg<K>::BUF, CAP = ListCfg<K>::CAP;
+    constexpr int LH = ListCfg<K>::LH, NS = ListCfg<K>::NS;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const TcLayout L = tc_layout<K>(a.hc_max, a.wc_max);
     uint4 *Q = reinterpret_cast<uint4 *>(smem_raw + L.q);
     unsigned char *Abuf = smem_raw + L.a;
     float *E = reinterpret_cast<float *>(smem_raw + L.e);
     float *Ps = reinterpret_cast<float *>(smem_raw + L.ps);
-    float *rn = reinterpret_cast<float *>(smem_raw + L.rn);
-    float *bd = reinterpret_cast<float *>(smem_raw + L.bd);
-    int *bp = reinterpret_cast<int *>(smem_raw + L.bp);
+    float *rn = reinterpret_cast<float *>(smem_raw + L.scr);          // row norms (E formation)
+    float *sdl = reinterpret_cast<float *>(smem_raw + L.scr);         // seed lists [2][K-1][NR]
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smem_raw + L.scr);  // key staging [32][NT] (runs)
+    uint32_t *fk = reinterpret_cast<uint32_t *>(smem_raw);             // final lists [2][LH][NR]
+    unsigned long long *fr = reinterpret_cast<unsigned long long *>(smem_raw + (size_t)2 * LH * NR * 4);
     RefRec *rec = reinterpret_cast<RefRec *>(smem_raw + L.ref);
+    int2 *qr = reinterpret_cast<int2 *>(smem_raw + L.qr);  // per quarter: first candidate, count
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + L.bar);  // [NBUF]
-    long long *issued_hi = reinterpret_cast<long long *>(full + NBUF);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(issued_hi + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(full + NBUF);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int wq4 = warp & 3, wcol = (warp >> 2) * 32;  // TMEM lane quarter, first reference column
+    const int q = warp & 3, hh = warp >> 2;  // lane quarter, half of the quarter's 64 columns
+    const int m = 32 * q + lane;            // this thread's reference slot (A row, tensor-memory lane)
     const size_t HW = (size_t)a.H * a.W;
     if (tid == 0) {
-        for (int b = 0; b < NBUF; ++b) bar_init(&full[b], 1);
-        *issued_hi = 0;
+        for (int b = 0; b < NBUF; ++b) tc::bar_init(&full[b], 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                     "r"(TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    tc_fence_before();
+    if (warp == 0) tc::tmem_alloc(tmem_slot, TMEM_COLS);
+    tc::fence_before();
     __syncthreads();
-    tc_fence_after();
+    tc::fence_after();
     const uint32_t tbase = *tmem_slot;
-    const uint32_t idesc = idesc_bf16(MC, NR);
-    long long gc = 0;  // chunks issued by this block so far (buffer = gc % NBUF, use = gc / NBUF)
+    const uint32_t idesc = tc::idesc_f16(NR, CH, true);
+    long long gc = 0;  // runs issued by this block so far (accumulator gc % NBUF, use gc / NBUF)
     bool ok = true;
 
     for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
@@ -255,11 +203,13 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
         const int cx1 = min(a.W - PS, grid_pos(gx1, a.W, a.step) + a.R);
         const int Hc = cy1 - cy0 + 1, Wc = cx1 - cx0 + 1, PSW = Wc + 7;
         const int ncand = Hc * Wc;
-        const int nch = (ncand + MC - 1) / MC;
-        const int nq = nch * MC + 7 * Wc;
+        const int nq = ncand + CH + 7 * Wc;
+        const uint32_t lowm = (1u << (32 - __clz(ncand))) - 1u;  // candidate index bits of a key
+        const uint32_t him = ~lowm;
 
         for (int pass = 0; pass < (a.C == 3 ? 2 : 1) && ok; ++pass) {
-            // ---- per-reference records (thread j < NR: reference j = row j/8, column j%8 of the tile)
+            // ---- per-reference records (thread j < NR: reference j = tile row j / 8, column j % 8),
+            //      and each quarter's band of candidate rows
             bool any = false;
             if (tid < NR) {
                 const int ry = gy0 + (tid >> 3), rx = gx0 + (tid & 7);
@@ -267,20 +217,28 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
                 const int r = valid ? ry * a.nx + rx : 0;
                 const bool mine = valid && (a.C == 1 || (int)a.green[r] == (pass == 0 ? 1 : 0));
                 const int yr = grid_pos(min(ry, gy1), a.H, a.step), xr = grid_pos(min(rx, gx1), a.W, a.step);
-                RefRec q;
-                q.wy0 = max(0, yr - a.R) - cy0;
-                q.wy1 = min(a.H - PS, yr + a.R) - cy0;
-                q.wx0 = max(0, xr - a.R) - cx0;
-                q.wx1 = min(a.W - PS, xr + a.R) - cx0;
-                q.pself = (yr - cy0) * Wc + (xr - cx0);
-                q.mine = mine ? 1 : 0;
-                q.cnt = 0;
-                q.pad = 0;
-                q.a2 = 0.f;
-                q.thr = __builtin_huge_valf();
-                q.pad1 = q.pad2 = 0.f;
-                rec[tid] = q;
+                RefRec rq;
+                rq.wy0 = max(0, yr - a.R) - cy0;
+                rq.wy1 = min(a.H - PS, yr + a.R) - cy0;
+                rq.wx0 = max(0, xr - a.R) - cx0;
+                rq.wx1 = min(a.W - PS, xr + a.R) - cx0;
+                rq.pself = (yr - cy0) * Wc + (xr - cx0);
+                rq.mine = mine ? 1 : 0;
+                rq.pad0 = rq.pad1 = rq.pad2 = rq.pad3 = 0;
+                rq.a2 = 0.f;
+                rq.thrk = 0u;
+                rec[tid] = rq;
                 any = mine;
+                int lo = mine ? rq.wy0 : 0x3fffffff, hi = mine ? rq.wy1 : -1;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    lo = min(lo, __shfl_xor_sync(FULLM, lo, o));
+                    hi = max(hi, __shfl_xor_sync(FULLM, hi, o));
+                }
+                if (lane == 0) {
+                    const int s0 = (hi < 0) ? 0 : ((lo * Wc) & ~31);
+                    qr[warp] = make_int2(s0, (hi < 0) ? 0 : (hi + 1) * Wc - s0);
+                }
             }
             if (!__syncthreads_or(any)) continue;
             // ---- stage the plane (FP32), the row-8 vectors and their norms, E, A
@@ -294,9 +252,9 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
                 Ps[e] = v;
             }
             __syncthreads();
-            for (int q = tid; q < nq; q += NT) {
-                const int y = q / Wc, x = q - y * Wc;
-                uint4 w = make_uint4(0, 0, 0, 0);
+            for (int qi = tid; qi < nq; qi += NT) {
+                const int y = qi / Wc, x = qi - y * Wc;
+                uint4 w = make_uint4(0u, 0u, 0u, 0u);
                 float n2 = 0.f;
                 if (y < Hc + 7) {
                     const float *s = Ps + y * PSW + x;
@@ -308,11 +266,11 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
                     w = make_uint4(pack_bf16(s[0], s[1]), pack_bf16(s[2], s[3]), pack_bf16(s[4], s[5]),
                                    pack_bf16(s[6], s[7]));
                 }
-                Q[q] = w;
-                rn[q] = n2;  // squared norm of the BF16 row-8 vector
+                Q[qi] = w;
+                rn[qi] = n2;  // squared norm of the BF16 row-8 vector
             }
             __syncthreads();
-            for (int p = tid; p < nch * MC; p += NT) {
+            for (int p = tid; p < ncand + CH; p += NT) {
                 float e2 = 0.f;
                 if (p < ncand) {
 #pragma unroll
@@ -323,30 +281,30 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
             // A: row j = reference j, element 8u+v; core matrix (j/8, u) at (j/8)*1024 + u*128
             for (int e = tid; e < NR * PS; e += NT) {
                 const int j = e >> 3, u = e & 7;
-                const int ty_ = gy0 + (j >> 3), tx_ = gx0 + (j & 7);
-                uint4 w = make_uint4(0, 0, 0, 0);
-                if (ty_ <= gy1 && tx_ <= gx1) w = Q[rec[j].pself + u * Wc];
+                uint4 w = make_uint4(0u, 0u, 0u, 0u);
+                if ((gy0 + (j >> 3)) <= gy1 && (gx0 + (j & 7)) <= gx1) w = Q[rec[j].pself + u * Wc];
                 *reinterpret_cast<uint4 *>(Abuf + (j >> 3) * 1024 + u * 128 + (j & 7) * 16) = w;
             }
-            __syncthreads();  // rn is dead from here: the lists overlay it
-            // ---- thresholds: 1.5 x the (K-1)-th smallest BF16 distance from the reference to the
-            //      positions around it (an upper bound of its (K-1)-th nearest candidate, so those
-            //      always pass), plus a margin for the different FP32 rounding of the MMA form
-            if (tid < NR && rec[tid].mine) {
-                constexpr int NS = (K + 8 > 24) ? ((K + 8 > NSEED) ? NSEED : K + 8) : 24;
-                const RefRec q = rec[tid];
-                const int ay = q.pself / Wc, ax = q.pself - ay * Wc;
-                const float a2 = E[q.pself];
+            __syncthreads();  // rn is dead: the seed lists overlay it
+
+            // ---- seeds: the two threads of a reference take alternate positions around it
+            RefRec rq = rec[m];
+            const bool mine = rq.mine != 0;
+            const int ay = rq.pself / Wc, ax = rq.pself - ay * Wc;
+            if (mine) {
+                uint4 ar[PS];
+#pragma unroll
+                for (int u = 0; u < PS; ++u) ar[u] = Q[rq.pself + u * Wc];
                 float best[K - 1];
 #pragma unroll
                 for (int i = 0; i < K - 1; ++i) best[i] = __builtin_huge_valf();
-                for (int sidx = 0; sidx < NS; ++sidx) {
+                for (int sidx = hh; sidx < NS; sidx += 2) {
                     const int y = ay + c_seed[sidx][0], x = ax + c_seed[sidx][1];
-                    const bool in = y >= q.wy0 && y <= q.wy1 && x >= q.wx0 && x <= q.wx1;
-                    const int pq = in ? y * Wc + x : q.pself;
+                    const bool in = y >= rq.wy0 && y <= rq.wy1 && x >= rq.wx0 && x <= rq.wx1;
+                    const int pq = in ? y * Wc + x : rq.pself;
                     float d = 0.f;
 #pragma unroll
-                    for (int u = 0; u < PS; ++u) d = row_dist2(Q[q.pself + u * Wc], Q[pq + u * Wc], d);
+                    for (int u = 0; u < PS; ++u) d = row_dist2(ar[u], Q[pq + u * Wc], d);
                     if (!in) d = __builtin_huge_valf();
 #pragma unroll
                     for (int i = 0; i < K - 1; ++i) {  // branch-free insertion into the sorted seeds
@@ -355,177 +313,228 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
                         best[i] = lo;
                     }
                 }
-                const float t = best[K - 2];
-                rec[tid].a2 = a2;
-                rec[tid].thr = (t < __builtin_huge_valf()) ? t * 1.5f + 1e-6f * (4.f * a2 + 1.f)
-                                                           : __builtin_huge_valf();
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-
-            // ---- chunks of MC candidates: MMAs (thread 0), then every warp's 32 lanes
-            auto issue = [&](int c, long long g) {
-                const uint32_t b = (uint32_t)(g % NBUF);
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint64_t cd = sdesc(su32(Q + (size_t)c * MC + (size_t)2 * kk * Wc), 16u * Wc, 128);
-                    const uint64_t rd = sdesc(su32(Abuf) + kk * 256, 128, 1024);
-                    mma_bf16(tbase + b * NR, cd, rd, idesc, kk > 0 ? 1u : 0u);
-                }
-                mma_commit(&full[b]);
-            };
-            const long long g0 = gc;
-            if (tid == 0) {
-                tc_fence_after();
-                for (int c = 0; c < nch && c < NBUF; ++c) issue(c, g0 + c);
-                *issued_hi = g0 + min(nch, NBUF);
+                for (int i = 0; i < K - 1; ++i) sdl[(hh * (K - 1) + i) * NR + m] = best[i];
             }
-            long long consumed = g0;
-            for (int c = 0; c < nch; ++c) {
+            __syncthreads();
+            uint32_t thrk = 0u;  // nothing passes for a reference of the other plane
+            float a2 = 0.f;
+            if (mine) {  // the (K-1)-th smallest of both threads' seeds, plus the rounding margin
+                int i0 = 0, i1 = 0;
+                float t = __builtin_huge_valf();
+                for (int k = 0; k < K - 1; ++k) {
+                    const float v0 = i0 < K - 1 ? sdl[i0 * NR + m] : __builtin_huge_valf();
+                    const float v1 = i1 < K - 1 ? sdl[(K - 1 + i1) * NR + m] : __builtin_huge_valf();
+                    if (v0 <= v1) {
+                        t = v0;
+                        ++i0;
+                    } else {
+                        t = v1;
+                        ++i1;
+                    }
+                }
+                a2 = E[rq.pself];
+                if (t < __builtin_huge_valf()) {
+                    const float thr = t + 1e-4f * t + 1e-5f * (4.f * a2 + 1.f);
+                    thrk = (__float_as_uint(thr) & him) + (lowm + 1u);  // every key with distance <= thr
+                } else {
+                    thrk = 0xffffffffu;
+                }
+            }
+            tc::fence_async_smem();
+            __syncthreads();  // the seed lists are dead: the key staging overlays them
+
+            // ---- runs: quarter qq's next CH candidates into columns qq*CH of the accumulator
+            int2 band[NQ];
+            int nrun = 0;
+#pragma unroll
+            for (int qq = 0; qq < NQ; ++qq) {
+                band[qq] = qr[qq];
+                nrun = max(nrun, (band[qq].y + CH - 1) / CH);
+            }
+            const long long g0 = gc;
+            auto issue = [&](int c) {
+                const uint32_t b = (uint32_t)((g0 + c) % NBUF);
+#pragma unroll
+                for (int qq = 0; qq < NQ; ++qq) {
+                    if (c * CH >= band[qq].y) continue;
+                    const uint4 *qb = Q + band[qq].x + c * CH;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ad = sdesc(su32(Abuf) + kk * 256, 128, 1024);
+                        const uint64_t bd = sdesc(su32(qb + (size_t)2 * kk * Wc), 16u * Wc, 128);
+                        tc::mma_f16(tbase + b * RUNC + qq * CH, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                    }
+                }
+                tc::mma_commit(&full[b]);
+            };
+            if (tid == 0) {
+                tc::fence_after();
+                for (int c = 0; c < nrun && c < NBUF; ++c) issue(c);
+            }
+            int issued = min(nrun, NBUF), consumed = 0;
+            uint32_t lst[LH];
+#pragma unroll
+            for (int t = 0; t < LH; ++t) lst[t] = 0xffffffffu;
+            const int start = band[q].x, len = band[q].y;
+            for (int c = 0; c < nrun; ++c) {
                 const long long g = g0 + c;
                 const uint32_t b = (uint32_t)(g % NBUF);
-                if (bar_wait(&full[b], (uint32_t)((g / NBUF) & 1))) consumed = g + 1;
+                if (tc::bar_wait(&full[b], (uint32_t)((g / NBUF) & 1), SPIN)) consumed = c + 1;
                 else ok = false;
                 ok = __all_sync(FULLM, ok);
-                if (ok) {
-                    tc_fence_after();
-                    uint32_t v0[32];
-                    tmem_ld32(tbase + ((uint32_t)(wq4 * 32) << 16) + b * NR + wcol, v0);
-                    tmem_wait_ld();
-                    // this lane's candidate
-                    const int pw = c * MC + wq4 * 32;
-                    const int p = pw + lane;
-                    const bool cval = p < ncand;
-                    const int prow = p / Wc, pcol = p - prow * Wc;
-                    const float e = cval ? E[p] : 0.f;
-                    const int rlo = pw / Wc, rhi = min(pw + 31, ncand - 1) / Wc;
-                    (void)rlo;
-                    (void)rhi;
-                    auto scan = [&](int j, uint32_t raw) {
-                        // no branch before the ballot, so the loads of consecutive references overlap
-                        const int4 wq = *reinterpret_cast<const int4 *>(&rec[j].wy0);
-                        const int4 wm = *reinterpret_cast<const int4 *>(&rec[j].pself);
-                        const float2 at = *reinterpret_cast<const float2 *>(&rec[j].a2);
-                        const float d = e + at.x - 2.f * __uint_as_float(raw);
-                        const bool pass = wm.y && cval && prow >= wq.x && prow <= wq.y && pcol >= wq.z &&
-                                          pcol <= wq.w && p != wm.x && d < at.y;
-                        const uint32_t m = __ballot_sync(FULLM, pass);
-                        if (!m) return;
-                        int base = 0;
-                        if (lane == 0) base = atomicAdd(&rec[j].cnt, __popc(m));
-                        base = __shfl_sync(FULLM, base, 0);
-                        const int pos = base + __popc(m & ((1u << lane) - 1u));
-                        if (pass && pos < CAP) {
-                            bd[j * CAP + pos] = d;
-                            bp[j * CAP + pos] = p;
+                const int off = c * CH + 32 * hh;
+                if (ok && off < len) {
+                    const int pb = start + off;  // a multiple of 32
+                    uint32_t vm = 0u;          // candidates pb .. pb+31 inside the window, without the reference
+                    if (mine) {
+                        const int y0 = max(pb / Wc, rq.wy0), y1 = min((pb + 31) / Wc, rq.wy1);
+                        for (int y = y0; y <= y1; ++y) {
+                            const int lo = max(y * Wc + rq.wx0, pb), hi = min(y * Wc + rq.wx1, pb + 31);
+                            if (lo <= hi) {
+                                const int n = hi - lo + 1;
+                                vm |= (n >= 32 ? FULLM : ((1u << n) - 1u)) << (lo - pb);
+                            }
                         }
-                    };
+                        if ((unsigned)(rq.pself - pb) < 32u) vm &= ~(1u << (rq.pself - pb));
+                    }
+                    if (__any_sync(FULLM, vm != 0u)) {
+                        tc::fence_after();
+                        uint32_t v[32];
+                        tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + b * RUNC + q * CH + 32 * hh, v);
+                        tc::tmem_wait_ld();
+                        const uint32_t bnd = min(thrk, lst[LH - 1]);
+                        const float4 *E4 = reinterpret_cast<const float4 *>(E + pb);
+                        uint32_t pm = 0u;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) scan(wcol + j, v0[j]);
-                }
-                tc_fence_before();
-                ok = !__syncthreads_or(!ok);
-                if (!ok) break;
-                // lists that the next chunk could overflow are cut back (reference j by warp j mod 4)
-                if (c + 1 < nch) {
-                    for (int j = warp; j < NR; j += NT / 32) {
-                        const int n = rec[j].cnt;
-                        if (n > CAP - MC) {
-                            int n2 = 0;
-                            const float t = cut_list_warp<CAP>(bd, bp, j, n < CAP ? n : CAP, BUF, lane, &n2);
-                            if (lane == 0) {
-                                rec[j].cnt = n2;
-                                rec[j].thr = fminf(rec[j].thr, t);
+                        for (int i4 = 0; i4 < 8; ++i4) {
+                            const float4 e4 = E4[i4];
+                            const float ev[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+                            for (int l = 0; l < 4; ++l) {
+                                const int i = 4 * i4 + l;
+                                const float d = fmaf(-2.f, __uint_as_float(v[i]), a2 + ev[l]);
+                                const uint32_t key = (__float_as_uint(fmaxf(d, 0.f)) & him) | (uint32_t)(pb + i);
+                                v[i] = key;
+                                pm |= (key < bnd ? 1u : 0u) << i;
+                            }
+                        }
+                        pm &= vm;
+                        if (__any_sync(FULLM, pm != 0u)) {
+                            if (pm) {
+#pragma unroll
+                                for (int i = 0; i < 32; ++i) stage[i * NT + tid] = v[i];
+                            }
+                            while (pm) {  // insertion into the sorted list, candidates in increasing index
+                                const int i = __ffs(pm) - 1;
+                                pm &= pm - 1u;
+                                uint32_t k = stage[i * NT + tid];
+#pragma unroll
+                                for (int t = 0; t < LH; ++t) {
+                                    const uint32_t lo = min(lst[t], k);
+                                    k = max(lst[t], k);
+                                    lst[t] = lo;
+                                }
                             }
                         }
                     }
                 }
-                __syncthreads();
-                if (tid == 0 && c + NBUF < nch) {  // the buffer of chunk c is free: chunk c + NBUF goes there
-                    tc_fence_after();
-                    issue(c + NBUF, g + NBUF);
-                    *issued_hi = g + NBUF + 1;
+                tc::fence_before();
+                ok = !__syncthreads_or(!ok);  // every thread is done with accumulator b
+                if (!ok) break;
+                if (c + NBUF < nrun) {
+                    if (tid == 0) {
+                        tc::fence_after();
+                        issue(c + NBUF);
+                    }
+                    ++issued;
                 }
             }
             if (!ok) {  // drain: wait (bounded) for the MMAs already issued before the memory is released
-                for (long long g = consumed; g < *issued_hi; ++g)
-                    bar_wait(&full[g % NBUF], (uint32_t)((g / NBUF) & 1));
+                if (tid == 0) {
+                    for (int c = consumed; c < issued; ++c)
+                        tc::bar_wait(&full[(g0 + c) % NBUF], (uint32_t)(((g0 + c) / NBUF) & 1), SPIN);
+                    atomicExch(&a.st->error, 2);
+                }
                 break;
             }
-            gc = g0 + nch;
+            gc = g0 + nrun;
 
-            // ---- per reference (one warp each): cut back to BUF, FP32 re-rank of the kept
-            //      candidates, the K-1 nearest by (distance, raster index)
-            for (int j = warp; j < NR; j += NT / 32) {
-                if (!rec[j].mine) continue;
-                int n = min(rec[j].cnt, CAP);
-                if (n > BUF) cut_list_warp<CAP>(bd, bp, j, n, BUF, lane, &n);
-                const int pself = rec[j].pself;
-                const int ay = pself / Wc, ax = pself - ay * Wc;
-                constexpr int PER = (BUF + 31) / 32;
-                float dk[PER];
-                int rk[PER];
+            // ---- both lists of every reference to shared memory (every MMA has completed: Q, A, E are free)
 #pragma unroll
-                for (int t = 0; t < PER; ++t) {
-                    const int i = t * 32 + lane;
-                    dk[t] = __builtin_huge_valf();
-                    rk[t] = 0x7fffffff;
-                    if (i < n) {
-                        const int pq = bp[j * CAP + i];
-                        const int by = pq / Wc, bx = pq - by * Wc;
+            for (int t = 0; t < LH; ++t) fk[(hh * LH + t) * NR + m] = lst[t];
+            __syncthreads();
+            // ---- merged LH smallest keys, FP32 distances of the FP32 plane in the definition's (u, v)
+            //      order (the two threads take alternate entries)
+            if (mine) {
+                float ra[PS * PS];
+#pragma unroll
+                for (int u = 0; u < PS; ++u)
+#pragma unroll
+                    for (int v = 0; v < PS; ++v) ra[u * PS + v] = Ps[(ay + u) * PSW + ax + v];
+                int i0 = 0, i1 = 0;
+                for (int t = 0; t < LH; ++t) {
+                    const uint32_t k0 = i0 < LH ? fk[i0 * NR + m] : 0xffffffffu;
+                    const uint32_t k1 = i1 < LH ? fk[(LH + i1) * NR + m] : 0xffffffffu;
+                    uint32_t k;
+                    if (k0 <= k1) {
+                        k = k0;
+                        ++i0;
+                    } else {
+                        k = k1;
+                        ++i1;
+                    }
+                    if ((t & 1) != hh) continue;
+                    unsigned long long rk = ~0ull;
+                    if (k != 0xffffffffu) {
+                        const int p = (int)(k & lowm);
+                        const int by = p / Wc, bx = p - by * Wc;
+                        const float *pbv = Ps + by * PSW + bx;
                         float d = 0.f;
-                        for (int u = 0; u < PS; ++u) {
-                            const float *ra = Ps + (ay + u) * PSW + ax, *rb = Ps + (by + u) * PSW + bx;
+#pragma unroll
+                        for (int u = 0; u < PS; ++u)
 #pragma unroll
                             for (int v = 0; v < PS; ++v) {
-                                const float df = ra[v] - rb[v];
+                                const float df = ra[u * PS + v] - pbv[u * PSW + v];
                                 d = fmaf(df, df, d);
                             }
-                        }
-                        dk[t] = d;
-                        rk[t] = (cy0 + by) * a.W + cx0 + bx;
+                        rk = ((unsigned long long)__float_as_uint(d) << 32) |
+                             (uint32_t)((cy0 + by) * a.W + cx0 + bx);
                     }
-                }
-                const int r = (gy0 + (j >> 3)) * a.nx + gx0 + (j & 7);
-                int32_t *out = a.idx + (size_t)r * K;
-                const int self = (cy0 + ay) * a.W + cx0 + ax;
-                if (lane == 0) out[0] = self;
-                for (int k = 1; k < K; ++k) {  // K-1 rounds of a warp arg-min on (distance, raster)
-                    float bdv = dk[0];
-                    int brv = rk[0];
-#pragma unroll
-                    for (int t = 1; t < PER; ++t)
-                        if (dk[t] < bdv || (dk[t] == bdv && rk[t] < brv)) {
-                            bdv = dk[t];
-                            brv = rk[t];
-                        }
-#pragma unroll
-                    for (int o = 16; o; o >>= 1) {
-                        const float od = __shfl_xor_sync(FULLM, bdv, o);
-                        const int orr = __shfl_xor_sync(FULLM, brv, o);
-                        if (od < bdv || (od == bdv && orr < brv)) {
-                            bdv = od;
-                            brv = orr;
-                        }
-                    }
-                    if (lane == 0) out[k] = (brv == 0x7fffffff) ? self : brv;
-#pragma unroll
-                    for (int t = 0; t < PER; ++t)
-                        if (rk[t] == brv) {
-                            dk[t] = __builtin_huge_valf();
-                            rk[t] = 0x7fffffff;
-                        }
+                    fr[(size_t)t * NR + m] = rk;
                 }
             }
-            tc_fence_before();
             __syncthreads();
-            tc_fence_after();
+            // ---- the K-1 smallest by (distance, raster index)
+            if (hh == 0 && mine) {
+                unsigned long long sel[K - 1];
+#pragma unroll
+                for (int i = 0; i < K - 1; ++i) sel[i] = ~0ull;
+                for (int t = 0; t < LH; ++t) {
+                    unsigned long long k = fr[(size_t)t * NR + m];
+#pragma unroll
+                    for (int i = 0; i < K - 1; ++i) {
+                        const unsigned long long lo = k < sel[i] ? k : sel[i];
+                        k = k < sel[i] ? sel[i] : k;
+                        sel[i] = lo;
+                    }
+                }
+                const int r = (gy0 + (m >> 3)) * a.nx + gx0 + (m & 7);
+                const int self = (cy0 + ay) * a.W + cx0 + ax;
+                int32_t *out = a.idx + (size_t)r * K;
+                out[0] = self;
+#pragma unroll
+                for (int i = 0; i < K - 1; ++i) out[i + 1] = (sel[i] == ~0ull) ? self : (int)(uint32_t)sel[i];
+            }
+            tc::fence_before();
+            __syncthreads();
+            tc::fence_after();
         }
     }
-    tc_fence_before();
+    tc::fence_before();
     __syncthreads();
-    tc_fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS));
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc(tbase, TMEM_COLS);
 }
 
 template <int K>
