@@ -331,7 +331,7 @@ hts_status launch_grouping(const float *img, const Geom &g, const hts_params &p,
                            int32_t *fb, DevState *st, cudaStream_t s) {
     if (p.precision != 1) return launch_match(img, g, p.gamma_gcp, idx, green, fb, st, s);
     if (g.C == 3) HTS_TRY(launch_gcp_flags(img, g, p.gamma_gcp, green, s));
-    return launch_match_tc(img, g, idx, green, st, s);
+    return launch_match_tc(img, g, p.gamma_gcp, idx, green, fb, st, s);
 }
 
 hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,

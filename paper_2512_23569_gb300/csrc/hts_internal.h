@@ -104,8 +104,10 @@ hts_status launch_gcp_flags(const float *img, const Geom &g, double gamma_gcp, u
 // Precision form of the grouping (match_tc.cu): BF16 distances on the tensor
 // cores, top-2K per reference, FP32 re-rank.  `green` must hold the Eq. 9
 // flags (colour).  HTS_EUNSUPPORTED when the window does not fit on chip.
-hts_status launch_match_tc(const float *img, const Geom &g, int32_t *idx, const uint8_t *green, DevState *st,
-                           cudaStream_t s);
+hts_status launch_match_tc(const float *img, const Geom &g, double gamma_gcp, int32_t *idx, const uint8_t *green,
+                           int32_t *fallback_list, DevState *st, cudaStream_t s);
+hts_status launch_match_rescue(const float *img, const Geom &g, int32_t *idx, const uint8_t *green,
+                               int32_t *fallback_list, DevState *st, cudaStream_t s);
 
 // The grouping step in the arithmetic p.precision selects (api.cu).
 hts_status launch_grouping(const float *img, const Geom &g, const hts_params &p, int32_t *idx, uint8_t *green,

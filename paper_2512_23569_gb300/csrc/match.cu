@@ -421,6 +421,133 @@ __global__ void __launch_bounds__(128) k_match_fallback(MatchArgs a) {
     }
 }
 
+// Exhaustive matching, in FP32, of the references the tensor-core matcher
+// listed in a.fb (count in a.st->match_fallback): one block of four warps per
+// reference, its search region staged in shared memory as FP32 plane values
+// ((R + G) + B for the channel sum), distances as FP32 fused multiply-adds
+// in the definition's (u, v) order -- the arithmetic of the tensor-core
+// matcher's re-rank -- and the K-1 nearest by (distance, raster index).  The
+// matching plane comes from a.green (Eq. 9 flags already decided).
+template <int K>
+__global__ void __launch_bounds__(128) k_match_rescue(MatchArgs a) {
+    constexpr int L = K - 1;
+    extern __shared__ float rs_plane[];  // (2R + 8)^2 region values, then the warps' lists
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int count = *(volatile int *)&a.st->match_fallback;
+    const size_t HW = (size_t)a.H * a.W;
+    const int side = 2 * a.R + PS;
+    float *wd = rs_plane + (size_t)side * side;  // [4][L]
+    int *wi = reinterpret_cast<int *>(wd + 4 * L);  // [4][L]
+    for (int f = blockIdx.x; f < count; f += gridDim.x) {
+        const int r = a.fb[f];
+        const int yr = grid_pos(r / a.nx, a.H, a.step), xr = grid_pos(r % a.nx, a.W, a.step);
+        const int green = (a.C == 3) ? (int)a.green[r] : 1;
+        const int cy0 = max(0, yr - a.R), cy1 = min(a.H - PS, yr + a.R);
+        const int cx0 = max(0, xr - a.R), cx1 = min(a.W - PS, xr + a.R);
+        const int ncol = cx1 - cx0 + 1, ncand = (cy1 - cy0 + 1) * ncol;
+        const int rw = ncol + PS - 1, rh = cy1 - cy0 + PS;  // staged rows and columns
+        __syncthreads();  // the previous reference's lists are read
+        for (int e = tid; e < rw * rh; e += 128) {
+            const int y = e / rw, x = e - y * rw;
+            const size_t o = (size_t)(cy0 + y) * a.W + cx0 + x;
+            float v;
+            if (a.C == 1) v = __ldg(a.img + o);
+            else if (green) v = __ldg(a.img + HW + o);
+            else v = (__ldg(a.img + o) + __ldg(a.img + HW + o)) + __ldg(a.img + 2 * HW + o);
+            rs_plane[e] = v;
+        }
+        __syncthreads();
+        const float *ref = rs_plane + (size_t)(yr - cy0) * rw + (xr - cx0);
+        float dl[L];
+        int il[L];
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            dl[i] = __builtin_huge_valf();
+            il[i] = 0x7fffffff;
+        }
+        for (int c = tid; c < ncand; c += 128) {
+            const int cy = c / ncol, cx = c - cy * ncol;
+            if (cy0 + cy == yr && cx0 + cx == xr) continue;
+            const float *cand = rs_plane + (size_t)cy * rw + cx;
+            float D = 0.f;
+            for (int u = 0; u < PS; ++u)
+#pragma unroll
+                for (int v = 0; v < PS; ++v) {
+                    const float d = ref[u * rw + v] - cand[u * rw + v];
+                    D = fmaf(d, d, D);
+                }
+            const int id = (cy0 + cy) * a.W + cx0 + cx;
+            if (D > dl[L - 1] || (D == dl[L - 1] && id > il[L - 1])) continue;
+#pragma unroll
+            for (int i = L - 1; i > 0; --i) {
+                const bool shift = (dl[i - 1] > D) || (dl[i - 1] == D && il[i - 1] > id);
+                const bool here = !shift && ((dl[i] > D) || (dl[i] == D && il[i] > id));
+                if (shift) {
+                    dl[i] = dl[i - 1];
+                    il[i] = il[i - 1];
+                } else if (here) {
+                    dl[i] = D;
+                    il[i] = id;
+                }
+            }
+            if ((dl[0] > D) || (dl[0] == D && il[0] > id)) {
+                dl[0] = D;
+                il[0] = id;
+            }
+        }
+        // each warp: the L smallest of its lanes' lists (L rounds of a warp arg-min over the list heads)
+        for (int j = 0; j < L; ++j) {
+            float bd = dl[0];
+            int bi = il[0];
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const float od = __shfl_xor_sync(FULL, bd, o);
+                const int oi = __shfl_xor_sync(FULL, bi, o);
+                if (od < bd || (od == bd && oi < bi)) {
+                    bd = od;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                wd[warp * L + j] = bd;
+                wi[warp * L + j] = bi;
+            }
+            if (il[0] == bi && dl[0] == bd) {
+#pragma unroll
+                for (int t = 0; t < L - 1; ++t) {
+                    dl[t] = dl[t + 1];
+                    il[t] = il[t + 1];
+                }
+                dl[L - 1] = __builtin_huge_valf();
+                il[L - 1] = 0x7fffffff;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {  // merge of the four warps' sorted lists
+            int h[4] = {0, 0, 0, 0};
+            int32_t *out = a.idx + (size_t)r * K;
+            out[0] = yr * a.W + xr;
+            for (int j = 0; j < L; ++j) {
+                int bw = -1;
+                float bd = 0.f;
+                int bi = 0x7fffffff;
+                for (int w = 0; w < 4; ++w) {
+                    if (h[w] >= L) continue;
+                    const float dv = wd[w * L + h[w]];
+                    const int iv = wi[w * L + h[w]];
+                    if (bw < 0 || dv < bd || (dv == bd && iv < bi)) {
+                        bw = w;
+                        bd = dv;
+                        bi = iv;
+                    }
+                }
+                ++h[bw];
+                out[1 + j] = (bi == 0x7fffffff) ? out[0] : bi;
+            }
+        }
+    }
+}
+
 template <int K>
 hts_status launch_k(const MatchArgs &a, cudaStream_t s) {
     const int RHM = a.step + 2 * a.R + PS;
@@ -496,6 +623,52 @@ hts_status launch_match(const float *img, const Geom &g, double gamma_gcp, int32
         case 32: return launch_k<32>(a, s);
         default: return HTS_EUNSUPPORTED;
     }
+}
+
+hts_status launch_match_rescue(const float *img, const Geom &g, int32_t *idx, const uint8_t *green,
+                               int32_t *fallback_list, DevState *st, cudaStream_t s) {
+    MatchArgs a;
+    a.img = img;
+    a.H = g.H;
+    a.W = g.W;
+    a.C = g.C;
+    a.step = g.step;
+    a.R = g.R;
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.nref = g.nref;
+    a.gamma = 0.0;
+    a.idx = idx;
+    a.green = const_cast<uint8_t *>(green);
+    a.fb = fallback_list;
+    a.st = st;
+    const size_t side = 2 * (size_t)g.R + PS;
+    const size_t smem = side * side * sizeof(float) + 4 * 32 * (sizeof(float) + sizeof(int));
+    const void *fn = nullptr;
+    switch (g.K) {
+        case 2: fn = reinterpret_cast<const void *>(k_match_rescue<2>); break;
+        case 4: fn = reinterpret_cast<const void *>(k_match_rescue<4>); break;
+        case 8: fn = reinterpret_cast<const void *>(k_match_rescue<8>); break;
+        case 16: fn = reinterpret_cast<const void *>(k_match_rescue<16>); break;
+        case 32: fn = reinterpret_cast<const void *>(k_match_rescue<32>); break;
+        default: return HTS_EUNSUPPORTED;
+    }
+    {
+        const hts_status st0 = allow_smem(fn, smem);
+        if (st0 != HTS_OK) return st0;
+    }
+    const int blocks = 4 * 152;
+    {
+        KTimer kt("k_match_rescue", s);
+        switch (g.K) {
+            case 2: k_match_rescue<2><<<blocks, 128, smem, s>>>(a); break;
+            case 4: k_match_rescue<4><<<blocks, 128, smem, s>>>(a); break;
+            case 8: k_match_rescue<8><<<blocks, 128, smem, s>>>(a); break;
+            case 16: k_match_rescue<16><<<blocks, 128, smem, s>>>(a); break;
+            default: k_match_rescue<32><<<blocks, 128, smem, s>>>(a); break;
+        }
+    }
+    return check_launch("k_match_rescue");
 }
 
 }  // namespace hts

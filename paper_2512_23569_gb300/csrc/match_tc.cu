@@ -9,29 +9,38 @@
 // the references are the MMA's M = 128 rows, so reference m's distances land
 // in tensor-memory lane m.  No candidate matrix is materialised: the region is
 // staged once as "row-8 vectors" Q[p] = plane[y_p][x_p .. x_p+7] (16 bytes,
-// one core-matrix row), candidates are numbered p = y * Wc + x in the region,
-// and the K slice of patch rows (u, u+1) of the candidates p0 .. p0+63 is the
-// shared-memory matrix starting at Q[p0 + u Wc], core matrices 8 rows (128
-// bytes) apart along N and Wc rows (16 Wc bytes) apart along K.
+// one core-matrix row), candidates are numbered p = y * Wq + x in the region
+// (Wq >= Wc, the padding columns are never valid), and the K slice of patch
+// rows (u, u+1) of the candidates p0 .. p0+63 is the shared-memory matrix
+// starting at Q[p0 + u Wq], core matrices 8 rows (128 bytes) apart along N and
+// Wq rows (16 Wq bytes) apart along K.
 //
 // Warp w reads lanes 32 (w % 4) .. + 31: the references of tile rows
 // 4 (w % 4) .. + 3, whose search windows cover a band of the region's rows.
 // Each run gives every lane quarter the next 64 candidates of its own band
 // (four N = 64 MMAs into 256 tensor-memory columns), so all eight warps read
-// 32 columns per run -- every warp has the same work in every run.  A thread
-// turns its reference's 32 cross terms into keys (the distance's float bits
-// with the low bits replaced by the candidate's index, so equal distances
-// keep the lower index first) and keeps the LH smallest keys below its bound
-// in a sorted register list.  The bound starts at the (K-1)-th smallest BF16
-// distance to the 24 (K = 32: 48) positions around the reference, plus a
-// margin for the MMA's different rounding, so its K-1 nearest always enter,
-// and follows the list's last entry.  Two accumulators of 256 columns let the
-// MMAs of the next run go while the current one is read.  At the end the two
-// lists of a reference (one per half of each run's columns) are merged, their
-// LH smallest keys re-ranked with FP32 distances of the FP32 plane, and the
-// K-1 smallest by (distance, raster index) follow the reference in its
-// group.  Eq. 9 picks the plane per reference: a colour tile runs once per
-// plane that one of its references uses.
+// 32 columns per run.  A thread turns its reference's 32 cross terms into
+// keys (the distance's float bits with the low bits replaced by the
+// candidate's index, so equal distances keep the lower index first; ~0 for a
+// candidate outside the reference's window) and drops key i into bin i (K = 32:
+// bin i mod 16), a sorted list of T slots, through a branch-free min / max network -- every
+// lane and every warp does the same work in every run.  The smallest key a
+// full bin pushed out is remembered.  A ninth warp issues the MMAs into two
+// accumulators of 256 columns: a run goes into an accumulator once all eight
+// warps have loaded the run before from it (mbarriers, no block-wide barrier
+// per run), so the warps drift apart and the loads' latency hides.  At the end each
+// thread keeps the LH smallest keys of its bins, the two threads of a
+// reference (one per half of each run's columns) merge theirs, the LH
+// smallest are re-ranked with FP32 distances of the FP32 plane, and the K-1
+// smallest by (distance, raster index) follow the reference in its group.  If
+// a pushed-out key lies below the (K+3)-th smallest kept one, the bins may
+// have lost one of the nearest candidates: the reference goes to an
+// exhaustive matcher with the re-rank's FP32 arithmetic, which rewrites its
+// group (a few references in a thousand on natural-looking images; the row
+// pitch of the candidate numbering is chosen so that the lines of equally
+// good candidates along edges and stripes spread over the bins).  Eq. 9 picks the plane
+// per reference: a colour tile runs once per plane that one of its
+// references uses.
 //
 // Every mbarrier wait is bounded; a wait that gives up records error code 2
 // in the call's state, and the block waits (bounded) for the MMAs it has
@@ -55,36 +64,29 @@ constexpr int NBUF = 2;           // accumulators
 constexpr uint32_t TMEM_COLS = NBUF * RUNC;
 constexpr long long SPIN = 1ll << 24;
 constexpr unsigned FULLM = 0xffffffffu;
-constexpr int NT = 256;  // warp w: lanes 32 (w % 4) .. + 31, columns 32 (w / 4) .. + 31 of its quarter's 64
-
-// Offsets (dy, dx) of the positions around a reference whose distances seed
-// its bound, nearest first (the 7 x 7 square without its centre); the first
-// 24 fill the 5 x 5 square.
-constexpr int NSEED = 48;
-__constant__ signed char c_seed[NSEED][2] = {
-    {0, 1},  {1, 0},   {0, -1},  {-1, 0},  {1, 1},   {1, -1},  {-1, 1},  {-1, -1}, {0, 2},   {2, 0},
-    {0, -2}, {-2, 0},  {1, 2},   {2, 1},   {-1, 2},  {2, -1},  {1, -2},  {-2, 1},  {-1, -2}, {-2, -1},
-    {2, 2},  {2, -2},  {-2, 2},  {-2, -2}, {0, 3},   {3, 0},   {0, -3},  {-3, 0},  {1, 3},   {3, 1},
-    {-1, 3}, {3, -1},  {1, -3},  {-3, 1},  {-1, -3}, {-3, -1}, {2, 3},   {3, 2},   {-2, 3},  {3, -2},
-    {2, -3}, {-3, 2},  {-2, -3}, {-3, -2}, {3, 3},   {3, -3},  {-3, 3},  {-3, -3}};
+constexpr int NWC = 8;               // reading warps: warp w takes lanes 32 (w % 4) .. + 31, columns 32 (w / 4) ..
+constexpr int NT = (NWC + 1) * 32;   // + one warp that issues the MMAs
 
 struct TcArgs {
     const float *img;
     int H, W, C, step, R, nx, ny, nref;
     int32_t *idx;
     const uint8_t *green;
+    int32_t *fb;  // references for the exhaustive matcher (count in st->match_fallback)
     DevState *st;
     int ntx, nty, ntiles;
     int hc_max, wc_max;  // bounds of the candidate region over all tiles
 };
 
-// LH: keys each thread keeps (per half of the runs' columns) and the number
-// re-ranked in FP32 per reference; NS: seed positions.
+// LH: keys each thread keeps and the number re-ranked in FP32 per reference;
+// T: slots per bin; KC: the nearest keys that must all have been kept.
 template <int K>
 struct ListCfg {
     static constexpr int LH = K + (K / 2 > 8 ? K / 2 : 8);
-    static constexpr int NS = K <= 16 ? 24 : 48;
-    static_assert(NS >= K - 1, "the seeds must certify the (K-1)-th nearest");
+    static constexpr int NBIN = K <= 16 ? 32 : 16;  // key i goes into bin i mod NBIN
+    static constexpr int T = K <= 16 ? 3 : 6;
+    static constexpr int KC = K + 3;
+    static_assert(KC <= LH, "the complete keys are re-ranked");
 };
 
 struct TcLayout {
@@ -97,36 +99,30 @@ __host__ __device__ inline size_t up(size_t x, size_t a) { return (x + a - 1) / 
 struct RefRec {
     int wy0, wy1, wx0, wx1;  // search window, region coordinates
     int pself, mine, pad0, pad1;
-    float a2;
-    uint32_t thrk;  // initial bound on the keys
-    int pad2, pad3;
 };
 
 // Shared memory: Q (row-8 vectors), A (references), E (candidates' squared
-// norms), the FP32 plane Ps, a scratch area (row norms while E is formed, the
-// seed lists, then the key staging of the runs), per-reference records, the
-// quarters' candidate bands, barriers.  After the runs the final lists and
-// re-rank keys overlay Q / A / E.
+// norms), the FP32 plane Ps, the row norms (only while E is formed),
+// per-reference records, the quarters' candidate bands, barriers.  After the
+// runs the final lists, re-rank keys and pushed-out minima overlay Q / A / E.
 template <int K>
 __host__ __device__ inline TcLayout tc_layout(int hc_max, int wc_max) {
     constexpr int LH = ListCfg<K>::LH;
     TcLayout L;
-    const size_t ncand = (size_t)hc_max * wc_max;
-    const size_t nq = ncand + CH + 7 * (size_t)wc_max;
+    const size_t wq_max = (size_t)wc_max + 7;  // largest row pitch of the candidate numbering
+    const size_t ncand = (size_t)hc_max * wq_max;
+    const size_t nq = ncand + CH + 7 * wq_max;
     L.q = 0;
     L.a = up(L.q + nq * 16, 1024);
     L.e = L.a + (size_t)NR * 64 * 2;
     L.ps = up(L.e + (ncand + CH) * 4, 16);
-    const size_t fin_end = (size_t)LH * NR * 16;  // [2][LH][NR] keys + [LH][NR] re-rank keys
+    const size_t fin_end = (size_t)LH * NR * 16 + (size_t)2 * NR * 4;  // [2][LH][NR] keys, [LH][NR] re-rank keys, [2][NR]
     if (L.ps < fin_end) L.ps = up(fin_end, 16);
     L.scr = up(L.ps + (size_t)(hc_max + 7) * (wc_max + 7) * 4, 16);
-    size_t scr = nq * 4;
-    if (scr < (size_t)32 * NT * 4) scr = (size_t)32 * NT * 4;
-    if (scr < (size_t)2 * (K - 1) * NR * 4) scr = (size_t)2 * (K - 1) * NR * 4;
-    L.ref = up(L.scr + scr, 16);
+    L.ref = up(L.scr + nq * 4, 16);
     L.qr = L.ref + (size_t)NR * sizeof(RefRec);
     L.bar = up(L.qr + NQ * sizeof(int2), 16);
-    L.total = L.bar + 64;
+    L.total = L.bar + 2 * NBUF * 8 + 16;
     // one block per SM, and never beside a block of the other tensor-core kernels (whose tensor
     // memory would not fit beside this block's 512 columns)
     if (L.total < 160 * 1024) L.total = 160 * 1024;
@@ -143,45 +139,59 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 
 __device__ __forceinline__ float bf_round(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
 
-// Squared distance of two row-8 BF16 vectors added to acc, in FP32.
-__device__ __forceinline__ float row_dist2(uint4 x, uint4 y, float acc) {
-    const uint32_t xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+// Row pitch of the candidate numbering p = y * Wq + x: the value in [Wc, Wc + 7]
+// whose key columns p mod 64 (bin and half of a thread's run) spread the
+// points of the short lattice directions (dy <= 4, |dx| <= 4) over the most
+// cells, weighted by the direction's length -- equally good candidates along
+// an edge or a stripe must not crowd into one bin.  Lanes 0..7 of every warp
+// score one pitch each.
+__device__ __forceinline__ int pick_pitch(int Wc, int lane) {
+    const int w = Wc + (lane & 7);
+    unsigned sc = 0xffffffffu;
+    for (int dy = 0; dy <= 4; ++dy)
+        for (int dx = -4; dx <= 4; ++dx) {
+            if (dy == 0 && dx <= 0) continue;
+            const int d = (dy * w + dx) & 63;
+            const int cells = d ? (64 >> (__ffs(d) - 1)) : 1;
+            sc = min(sc, (unsigned)(cells * cells) * (unsigned)(dy * dy + dx * dx));
+        }
+    unsigned key = (sc << 3) | (unsigned)(7 - (lane & 7));  // the highest score, then the smallest pitch
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float2 fa = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&xs[i]));
-        const float2 fb = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&ys[i]));
-        const float d0 = fa.x - fb.x, d1 = fa.y - fb.y;
-        acc = fmaf(d0, d0, acc);
-        acc = fmaf(d1, d1, acc);
-    }
-    return acc;
+    for (int o = 16; o; o >>= 1) key = max(key, __shfl_xor_sync(FULLM, key, o));
+    return Wc + 7 - (int)(key & 7u);
 }
 
 template <int K>
 __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
-    constexpr int LH = ListCfg<K>::LH, NS = ListCfg<K>::NS;
+    constexpr int LH = ListCfg<K>::LH, T = ListCfg<K>::T, KC = ListCfg<K>::KC, NBIN = ListCfg<K>::NBIN;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const TcLayout L = tc_layout<K>(a.hc_max, a.wc_max);
     uint4 *Q = reinterpret_cast<uint4 *>(smem_raw + L.q);
     unsigned char *Abuf = smem_raw + L.a;
     float *E = reinterpret_cast<float *>(smem_raw + L.e);
     float *Ps = reinterpret_cast<float *>(smem_raw + L.ps);
-    float *rn = reinterpret_cast<float *>(smem_raw + L.scr);          // row norms (E formation)
-    float *sdl = reinterpret_cast<float *>(smem_raw + L.scr);         // seed lists [2][K-1][NR]
-    uint32_t *stage = reinterpret_cast<uint32_t *>(smem_raw + L.scr);  // key staging [32][NT] (runs)
-    uint32_t *fk = reinterpret_cast<uint32_t *>(smem_raw);             // final lists [2][LH][NR]
+    float *rn = reinterpret_cast<float *>(smem_raw + L.scr);  // row norms (E formation)
+    uint32_t *fk = reinterpret_cast<uint32_t *>(smem_raw);     // final lists [2][LH][NR]
     unsigned long long *fr = reinterpret_cast<unsigned long long *>(smem_raw + (size_t)2 * LH * NR * 4);
+    uint32_t *fe = reinterpret_cast<uint32_t *>(smem_raw + (size_t)LH * NR * 16);  // pushed-out minima [2][NR]
     RefRec *rec = reinterpret_cast<RefRec *>(smem_raw + L.ref);
     int2 *qr = reinterpret_cast<int2 *>(smem_raw + L.qr);  // per quarter: first candidate, count
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + L.bar);  // [NBUF]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(full + NBUF);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + L.bar);  // [NBUF]: the run's MMAs completed
+    uint64_t *empty = full + NBUF;                                    // [NBUF]: every warp loaded the run
+    int *abort_flag = reinterpret_cast<int *>(empty + NBUF);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(abort_flag + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q = warp & 3, hh = warp >> 2;  // lane quarter, half of the quarter's 64 columns
+    const bool cw = warp < NWC;              // a reading warp
+    const int q = warp & 3, hh = (warp >> 2) & 1;  // lane quarter, half of the quarter's 64 columns
     const int m = 32 * q + lane;            // this thread's reference slot (A row, tensor-memory lane)
     const size_t HW = (size_t)a.H * a.W;
     if (tid == 0) {
-        for (int b = 0; b < NBUF; ++b) tc::bar_init(&full[b], 1);
+        for (int b = 0; b < NBUF; ++b) {
+            tc::bar_init(&full[b], 1);
+            tc::bar_init(&empty[b], NWC);
+        }
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) tc::tmem_alloc(tmem_slot, TMEM_COLS);
@@ -202,8 +212,9 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
         const int cx0 = max(0, grid_pos(gx0, a.W, a.step) - a.R);
         const int cx1 = min(a.W - PS, grid_pos(gx1, a.W, a.step) + a.R);
         const int Hc = cy1 - cy0 + 1, Wc = cx1 - cx0 + 1, PSW = Wc + 7;
-        const int ncand = Hc * Wc;
-        const int nq = ncand + CH + 7 * Wc;
+        const int Wq = pick_pitch(Wc, lane);  // row pitch of the candidate numbering
+        const int ncand = Hc * Wq;
+        const int nq = ncand + CH + 7 * Wq;
         const uint32_t lowm = (1u << (32 - __clz(ncand))) - 1u;  // candidate index bits of a key
         const uint32_t him = ~lowm;
 
@@ -222,11 +233,9 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
                 rq.wy1 = min(a.H - PS, yr + a.R) - cy0;
                 rq.wx0 = max(0, xr - a.R) - cx0;
                 rq.wx1 = min(a.W - PS, xr + a.R) - cx0;
-                rq.pself = (yr - cy0) * Wc + (xr - cx0);
+                rq.pself = (yr - cy0) * Wq + (xr - cx0);
                 rq.mine = mine ? 1 : 0;
-                rq.pad0 = rq.pad1 = rq.pad2 = rq.pad3 = 0;
-                rq.a2 = 0.f;
-                rq.thrk = 0u;
+                rq.pad0 = rq.pad1 = 0;
                 rec[tid] = rq;
                 any = mine;
                 int lo = mine ? rq.wy0 : 0x3fffffff, hi = mine ? rq.wy1 : -1;
@@ -236,12 +245,13 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
                     hi = max(hi, __shfl_xor_sync(FULLM, hi, o));
                 }
                 if (lane == 0) {
-                    const int s0 = (hi < 0) ? 0 : ((lo * Wc) & ~31);
-                    qr[warp] = make_int2(s0, (hi < 0) ? 0 : (hi + 1) * Wc - s0);
+                    const int s0 = (hi < 0) ? 0 : ((lo * Wq) & ~31);
+                    qr[warp] = make_int2(s0, (hi < 0) ? 0 : (hi + 1) * Wq - s0);
                 }
             }
             if (!__syncthreads_or(any)) continue;
             // ---- stage the plane (FP32), the row-8 vectors and their norms, E, A
+#pragma unroll 4
             for (int e = tid; e < (Hc + 7) * PSW; e += NT) {
                 const int y = e / PSW, x = e - y * PSW;
                 const size_t o = (size_t)(cy0 + y) * a.W + cx0 + x;
@@ -253,10 +263,10 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
             }
             __syncthreads();
             for (int qi = tid; qi < nq; qi += NT) {
-                const int y = qi / Wc, x = qi - y * Wc;
+                const int y = qi / Wq, x = qi - y * Wq;
                 uint4 w = make_uint4(0u, 0u, 0u, 0u);
                 float n2 = 0.f;
-                if (y < Hc + 7) {
+                if (y < Hc + 7 && x < Wc) {
                     const float *s = Ps + y * PSW + x;
 #pragma unroll
                     for (int v = 0; v < PS; ++v) {
@@ -274,7 +284,7 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
                 float e2 = 0.f;
                 if (p < ncand) {
 #pragma unroll
-                    for (int u = 0; u < PS; ++u) e2 += rn[p + u * Wc];
+                    for (int u = 0; u < PS; ++u) e2 += rn[p + u * Wq];
                 }
                 E[p] = e2;
             }
@@ -282,67 +292,17 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
             for (int e = tid; e < NR * PS; e += NT) {
                 const int j = e >> 3, u = e & 7;
                 uint4 w = make_uint4(0u, 0u, 0u, 0u);
-                if ((gy0 + (j >> 3)) <= gy1 && (gx0 + (j & 7)) <= gx1) w = Q[rec[j].pself + u * Wc];
+                if ((gy0 + (j >> 3)) <= gy1 && (gx0 + (j & 7)) <= gx1) w = Q[rec[j].pself + u * Wq];
                 *reinterpret_cast<uint4 *>(Abuf + (j >> 3) * 1024 + u * 128 + (j & 7) * 16) = w;
             }
-            __syncthreads();  // rn is dead: the seed lists overlay it
-
-            // ---- seeds: the two threads of a reference take alternate positions around it
-            RefRec rq = rec[m];
-            const bool mine = rq.mine != 0;
-            const int ay = rq.pself / Wc, ax = rq.pself - ay * Wc;
-            if (mine) {
-                uint4 ar[PS];
-#pragma unroll
-                for (int u = 0; u < PS; ++u) ar[u] = Q[rq.pself + u * Wc];
-                float best[K - 1];
-#pragma unroll
-                for (int i = 0; i < K - 1; ++i) best[i] = __builtin_huge_valf();
-                for (int sidx = hh; sidx < NS; sidx += 2) {
-                    const int y = ay + c_seed[sidx][0], x = ax + c_seed[sidx][1];
-                    const bool in = y >= rq.wy0 && y <= rq.wy1 && x >= rq.wx0 && x <= rq.wx1;
-                    const int pq = in ? y * Wc + x : rq.pself;
-                    float d = 0.f;
-#pragma unroll
-                    for (int u = 0; u < PS; ++u) d = row_dist2(ar[u], Q[pq + u * Wc], d);
-                    if (!in) d = __builtin_huge_valf();
-#pragma unroll
-                    for (int i = 0; i < K - 1; ++i) {  // branch-free insertion into the sorted seeds
-                        const float lo = fminf(best[i], d);
-                        d = fmaxf(best[i], d);
-                        best[i] = lo;
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < K - 1; ++i) sdl[(hh * (K - 1) + i) * NR + m] = best[i];
-            }
-            __syncthreads();
-            uint32_t thrk = 0u;  // nothing passes for a reference of the other plane
-            float a2 = 0.f;
-            if (mine) {  // the (K-1)-th smallest of both threads' seeds, plus the rounding margin
-                int i0 = 0, i1 = 0;
-                float t = __builtin_huge_valf();
-                for (int k = 0; k < K - 1; ++k) {
-                    const float v0 = i0 < K - 1 ? sdl[i0 * NR + m] : __builtin_huge_valf();
-                    const float v1 = i1 < K - 1 ? sdl[(K - 1 + i1) * NR + m] : __builtin_huge_valf();
-                    if (v0 <= v1) {
-                        t = v0;
-                        ++i0;
-                    } else {
-                        t = v1;
-                        ++i1;
-                    }
-                }
-                a2 = E[rq.pself];
-                if (t < __builtin_huge_valf()) {
-                    const float thr = t + 1e-4f * t + 1e-5f * (4.f * a2 + 1.f);
-                    thrk = (__float_as_uint(thr) & him) + (lowm + 1u);  // every key with distance <= thr
-                } else {
-                    thrk = 0xffffffffu;
-                }
-            }
             tc::fence_async_smem();
-            __syncthreads();  // the seed lists are dead: the key staging overlays them
+            __syncthreads();
+
+            // ---- this thread's reference
+            const RefRec rq = rec[m];
+            const bool mine = cw && rq.mine != 0;
+            const int ay = rq.pself / Wq, ax = rq.pself - ay * Wq;
+            const float a2 = E[rq.pself];
 
             // ---- runs: quarter qq's next CH candidates into columns qq*CH of the accumulator
             int2 band[NQ];
@@ -362,116 +322,138 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
                         const uint64_t ad = sdesc(su32(Abuf) + kk * 256, 128, 1024);
-                        const uint64_t bd = sdesc(su32(qb + (size_t)2 * kk * Wc), 16u * Wc, 128);
+                        const uint64_t bd = sdesc(su32(qb + (size_t)2 * kk * Wq), 16u * Wq, 128);
                         tc::mma_f16(tbase + b * RUNC + qq * CH, ad, bd, idesc, kk > 0 ? 1u : 0u);
                     }
                 }
                 tc::mma_commit(&full[b]);
             };
-            if (tid == 0) {
-                tc::fence_after();
-                for (int c = 0; c < nrun && c < NBUF; ++c) issue(c);
-            }
-            int issued = min(nrun, NBUF), consumed = 0;
-            uint32_t lst[LH];
+            uint32_t bn[NBIN][T];  // bin g: the T smallest keys of the columns g mod NBIN of this thread's half-runs
 #pragma unroll
-            for (int t = 0; t < LH; ++t) lst[t] = 0xffffffffu;
-            const int start = band[q].x, len = band[q].y;
-            for (int c = 0; c < nrun; ++c) {
-                const long long g = g0 + c;
-                const uint32_t b = (uint32_t)(g % NBUF);
-                if (tc::bar_wait(&full[b], (uint32_t)((g / NBUF) & 1), SPIN)) consumed = c + 1;
-                else ok = false;
-                ok = __all_sync(FULLM, ok);
-                const int off = c * CH + 32 * hh;
-                if (ok && off < len) {
-                    const int pb = start + off;  // a multiple of 32
-                    uint32_t vm = 0u;          // candidates pb .. pb+31 inside the window, without the reference
-                    if (mine) {
-                        const int y0 = max(pb / Wc, rq.wy0), y1 = min((pb + 31) / Wc, rq.wy1);
-                        for (int y = y0; y <= y1; ++y) {
-                            const int lo = max(y * Wc + rq.wx0, pb), hi = min(y * Wc + rq.wx1, pb + 31);
-                            if (lo <= hi) {
-                                const int n = hi - lo + 1;
-                                vm |= (n >= 32 ? FULLM : ((1u << n) - 1u)) << (lo - pb);
-                            }
-                        }
-                        if ((unsigned)(rq.pself - pb) < 32u) vm &= ~(1u << (rq.pself - pb));
-                    }
-                    if (__any_sync(FULLM, vm != 0u)) {
+            for (int g = 0; g < NBIN; ++g)
+#pragma unroll
+                for (int t = 0; t < T; ++t) bn[g][t] = 0xffffffffu;
+            uint32_t ev = 0xffffffffu;  // smallest key a full bin pushed out
+            volatile int *abortp = abort_flag;
+            if (!cw) {  // the issuing warp: run c goes into its accumulator once run c - NBUF was loaded by all
+                if (lane == 0) {
+                    int issued = 0;
+                    for (int c = 0; c < nrun; ++c) {
+                        const long long g = g0 + c;
+                        const uint32_t b = (uint32_t)(g % NBUF);
+                        if (g >= NBUF &&
+                            !tc::bar_wait_or_abort(&empty[b], (uint32_t)(((g / NBUF) - 1) & 1), SPIN, abortp))
+                            break;
                         tc::fence_after();
-                        uint32_t v[32];
+                        issue(c);
+                        ++issued;
+                    }
+                    if (*abortp && issued > 0) {  // drain: the last issued run completes after every earlier one
+                        const long long gl = g0 + issued - 1;
+                        tc::bar_wait(&full[gl % NBUF], (uint32_t)((gl / NBUF) & 1), SPIN);
+                    }
+                }
+                __syncwarp();
+            } else {
+                const int start = band[q].x, len = band[q].y;
+                int ry = (start + 32 * hh) / Wq, rx = start + 32 * hh - ry * Wq;  // region row / column of pb
+                for (int c = 0; c < nrun; ++c) {
+                    const long long g = g0 + c;
+                    const uint32_t b = (uint32_t)(g % NBUF);
+                    const bool got = tc::bar_wait_or_abort(&full[b], (uint32_t)((g / NBUF) & 1), SPIN, abortp);
+                    if (!__all_sync(FULLM, got)) break;
+                    const int off = c * CH + 32 * hh;
+                    const bool act = off < len;
+                    const int pb = start + off;  // a multiple of 32
+                    uint32_t v[32];
+                    uint32_t vm = 0u;  // candidates pb .. pb+31 inside the window, without the reference
+                    if (act) {
+                        tc::fence_after();
                         tc::tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + b * RUNC + q * CH + 32 * hh, v);
-                        tc::tmem_wait_ld();
-                        const uint32_t bnd = min(thrk, lst[LH - 1]);
+                        if (mine) {
+                            for (int y = ry, rs = pb - rx; rs <= pb + 31 && y <= rq.wy1; ++y, rs += Wq) {
+                                if (y < rq.wy0) continue;
+                                const int lo = max(rs + rq.wx0, pb), hi = min(rs + rq.wx1, pb + 31);
+                                if (lo <= hi) {
+                                    const int n = hi - lo + 1;
+                                    vm |= (n >= 32 ? FULLM : ((1u << n) - 1u)) << (lo - pb);
+                                }
+                            }
+                            if ((unsigned)(rq.pself - pb) < 32u) vm &= ~(1u << (rq.pself - pb));
+                        }
+                        __syncwarp();
+                        tc::tmem_wait_ld(v);
+                    }
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) tc::bar_arrive(&empty[b]);  // this warp is done with accumulator b
+                    if (act && __any_sync(FULLM, vm != 0u)) {
                         const float4 *E4 = reinterpret_cast<const float4 *>(E + pb);
-                        uint32_t pm = 0u;
 #pragma unroll
                         for (int i4 = 0; i4 < 8; ++i4) {
                             const float4 e4 = E4[i4];
-                            const float ev[4] = {e4.x, e4.y, e4.z, e4.w};
+                            const float evl[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
                             for (int l = 0; l < 4; ++l) {
                                 const int i = 4 * i4 + l;
-                                const float d = fmaf(-2.f, __uint_as_float(v[i]), a2 + ev[l]);
-                                const uint32_t key = (__float_as_uint(fmaxf(d, 0.f)) & him) | (uint32_t)(pb + i);
-                                v[i] = key;
-                                pm |= (key < bnd ? 1u : 0u) << i;
-                            }
-                        }
-                        pm &= vm;
-                        if (__any_sync(FULLM, pm != 0u)) {
-                            if (pm) {
+                                const float d = fmaf(-2.f, __uint_as_float(v[i]), a2 + evl[l]);
+                                uint32_t key = (__float_as_uint(fmaxf(d, 0.f)) & him) | (uint32_t)(pb + i);
+                                key = (vm & (1u << i)) ? key : 0xffffffffu;
+                                uint32_t *bb = bn[i % NBIN];
+                                ev = min(ev, max(bb[T - 1], key));
+                                // every slot from the old bin alone: no dependent chain
 #pragma unroll
-                                for (int i = 0; i < 32; ++i) stage[i * NT + tid] = v[i];
-                            }
-                            while (pm) {  // insertion into the sorted list, candidates in increasing index
-                                const int i = __ffs(pm) - 1;
-                                pm &= pm - 1u;
-                                uint32_t k = stage[i * NT + tid];
-#pragma unroll
-                                for (int t = 0; t < LH; ++t) {
-                                    const uint32_t lo = min(lst[t], k);
-                                    k = max(lst[t], k);
-                                    lst[t] = lo;
-                                }
+                                for (int t = T - 1; t > 0; --t) bb[t] = max(bb[t - 1], min(bb[t], key));
+                                bb[0] = min(bb[0], key);
                             }
                         }
                     }
-                }
-                tc::fence_before();
-                ok = !__syncthreads_or(!ok);  // every thread is done with accumulator b
-                if (!ok) break;
-                if (c + NBUF < nrun) {
-                    if (tid == 0) {
-                        tc::fence_after();
-                        issue(c + NBUF);
+                    rx += CH;
+                    while (rx >= Wq) {
+                        rx -= Wq;
+                        ++ry;
                     }
-                    ++issued;
                 }
             }
-            if (!ok) {  // drain: wait (bounded) for the MMAs already issued before the memory is released
-                if (tid == 0) {
-                    for (int c = consumed; c < issued; ++c)
-                        tc::bar_wait(&full[(g0 + c) % NBUF], (uint32_t)(((g0 + c) / NBUF) & 1), SPIN);
-                    atomicExch(&a.st->error, 2);
-                }
+            __syncthreads();  // every run was loaded (or the block gave up): Q, A, E are free
+            if (*abortp) {
+                if (tid == 0) atomicExch(&a.st->error, 2);
+                ok = false;
                 break;
             }
             gc = g0 + nrun;
 
-            // ---- both lists of every reference to shared memory (every MMA has completed: Q, A, E are free)
+            // ---- the LH smallest keys of this thread's bins, both threads' lists and pushed-out minima to
+            //      shared memory (every MMA has completed: Q, A, E are free)
+            if (cw) {
+                uint32_t lst[LH];
 #pragma unroll
-            for (int t = 0; t < LH; ++t) fk[(hh * LH + t) * NR + m] = lst[t];
+                for (int t = 0; t < LH; ++t) lst[t] = 0xffffffffu;
+#pragma unroll
+                for (int g = 0; g < NBIN; ++g)
+#pragma unroll
+                    for (int s = 0; s < T; ++s) {
+                        const uint32_t k = bn[g][s];
+#pragma unroll
+                        for (int t = LH - 1; t > 0; --t) lst[t] = max(lst[t - 1], min(lst[t], k));
+                        lst[0] = min(lst[0], k);
+                    }
+#pragma unroll
+                for (int t = 0; t < LH; ++t) fk[(hh * LH + t) * NR + m] = lst[t];
+                fe[hh * NR + m] = ev;
+            }
             __syncthreads();
             // ---- merged LH smallest keys, FP32 distances of the FP32 plane in the definition's (u, v)
-            //      order (the two threads take alternate entries)
+            //      order (the two threads take alternate entries); the reference goes to the exhaustive
+            //      matcher if a pushed-out key lies below the KC-th smallest kept key
+            bool lost = false;
             if (mine) {
                 float ra[PS * PS];
 #pragma unroll
                 for (int u = 0; u < PS; ++u)
 #pragma unroll
                     for (int v = 0; v < PS; ++v) ra[u * PS + v] = Ps[(ay + u) * PSW + ax + v];
+                const uint32_t evm = min(fe[m], fe[NR + m]);
                 int i0 = 0, i1 = 0;
                 for (int t = 0; t < LH; ++t) {
                     const uint32_t k0 = i0 < LH ? fk[i0 * NR + m] : 0xffffffffu;
@@ -484,11 +466,12 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
                         k = k1;
                         ++i1;
                     }
+                    if (t == KC - 1) lost = evm < k;
                     if ((t & 1) != hh) continue;
                     unsigned long long rk = ~0ull;
                     if (k != 0xffffffffu) {
                         const int p = (int)(k & lowm);
-                        const int by = p / Wc, bx = p - by * Wc;
+                        const int by = p / Wq, bx = p - by * Wq;
                         const float *pbv = Ps + by * PSW + bx;
                         float d = 0.f;
 #pragma unroll
@@ -511,13 +494,13 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
 #pragma unroll
                 for (int i = 0; i < K - 1; ++i) sel[i] = ~0ull;
                 for (int t = 0; t < LH; ++t) {
-                    unsigned long long k = fr[(size_t)t * NR + m];
+                    const unsigned long long k = fr[(size_t)t * NR + m];
 #pragma unroll
-                    for (int i = 0; i < K - 1; ++i) {
+                    for (int i = K - 2; i > 0; --i) {
                         const unsigned long long lo = k < sel[i] ? k : sel[i];
-                        k = k < sel[i] ? sel[i] : k;
-                        sel[i] = lo;
+                        sel[i] = sel[i - 1] > lo ? sel[i - 1] : lo;
                     }
+                    sel[0] = k < sel[0] ? k : sel[0];
                 }
                 const int r = (gy0 + (m >> 3)) * a.nx + gx0 + (m & 7);
                 const int self = (cy0 + ay) * a.W + cx0 + ax;
@@ -525,6 +508,7 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
                 out[0] = self;
 #pragma unroll
                 for (int i = 0; i < K - 1; ++i) out[i + 1] = (sel[i] == ~0ull) ? self : (int)(uint32_t)sel[i];
+                if (lost) a.fb[atomicAdd(&a.st->match_fallback, 1)] = r;
             }
             tc::fence_before();
             __syncthreads();
@@ -555,8 +539,8 @@ hts_status launch_tc(const TcArgs &a, cudaStream_t s) {
 
 }  // namespace
 
-hts_status launch_match_tc(const float *img, const Geom &g, int32_t *idx, const uint8_t *green, DevState *st,
-                           cudaStream_t s) {
+hts_status launch_match_tc(const float *img, const Geom &g, double gamma_gcp, int32_t *idx, const uint8_t *green,
+                           int32_t *fallback_list, DevState *st, cudaStream_t s) {
     TcArgs a;
     a.img = img;
     a.H = g.H;
@@ -569,20 +553,24 @@ hts_status launch_match_tc(const float *img, const Geom &g, int32_t *idx, const 
     a.nref = g.nref;
     a.idx = idx;
     a.green = green;
+    a.fb = fallback_list;
     a.st = st;
     a.nty = (g.ny + TTY - 1) / TTY;
     a.ntx = (g.nx + TTX - 1) / TTX;
     a.ntiles = a.nty * a.ntx;
     a.hc_max = std::min(g.H - PS + 1, (TTY - 1) * g.step + 1 + 2 * g.R);
     a.wc_max = std::min(g.W - PS + 1, (TTX - 1) * g.step + 1 + 2 * g.R);
+    hts_status st0 = HTS_EUNSUPPORTED;
     switch (g.K) {
-        case 2: return launch_tc<2>(a, s);
-        case 4: return launch_tc<4>(a, s);
-        case 8: return launch_tc<8>(a, s);
-        case 16: return launch_tc<16>(a, s);
-        case 32: return launch_tc<32>(a, s);
-        default: return HTS_EUNSUPPORTED;
+        case 2: st0 = launch_tc<2>(a, s); break;
+        case 4: st0 = launch_tc<4>(a, s); break;
+        case 8: st0 = launch_tc<8>(a, s); break;
+        case 16: st0 = launch_tc<16>(a, s); break;
+        case 32: st0 = launch_tc<32>(a, s); break;
+        default: break;
     }
+    if (st0 != HTS_OK) return st0;
+    return launch_match_rescue(img, g, idx, green, fallback_list, st, s);
 }
 
 }  // namespace hts

@@ -1,5 +1,6 @@
-"""Precision form: grouping by BF16 tensor-core distances with an FP32 re-rank of the 2K nearest,
-filtering with FP16 tensor-core projections and FP32 threshold decisions.
+"""Precision form: grouping by BF16 tensor-core distances with an FP32 re-rank of the nearest
+(references whose nearest may have been dropped by the per-thread bins are matched exhaustively in
+FP32), filtering with FP16 tensor-core projections and FP32 threshold decisions.
 
 Its groups are not bit-exact by design: BF16 rounding may reorder near
 neighbours.  What is checked: every group is valid (the reference first, K
@@ -53,6 +54,24 @@ CASES = [
 @pytest.mark.parametrize("H,W,C,win,K,sigma,seed", CASES)
 def test_groups_valid_and_close_to_exact(oracle, hts, H, W, C, win, K, sigma, seed):
     _, noisy = synth.make_config_image(H, W, C, sigma, seed)
+    _check_groups(oracle, hts, noisy, K, win)
+
+
+def test_rescue_of_crowded_bins(oracle, hts):
+    # stripes of constant x + 3y (period 16) put the equally good candidates of a reference on the lattice
+    # direction (1, -3), which the row pitch 51 of a 49-column region maps onto 4 of the 64 bins: those
+    # references are matched again exhaustively (FP32), and every group must still be valid and nearly all
+    # equal the FP64 definition's
+    H = W = 96
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    clean = 128.0 + 60.0 * np.sin(2.0 * np.pi * (xx + 3.0 * yy) / 16.0)
+    noisy = (clean + np.random.default_rng(17).normal(0.0, 5.0, clean.shape))[None].astype(np.float32)
+    _check_groups(oracle, hts, noisy, 16, 21)
+    assert hts.last_stats()["match_fallback"] >= 50
+
+
+def _check_groups(oracle, hts, noisy, K, win):
+    C, H, W = noisy.shape
     p1 = hts.params(K=K, win=win, precision=1)
     idx, green = hts.match(_dev(noisy), p1)
     idx, green = idx.cpu().numpy(), green.cpu().numpy()
