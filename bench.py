@@ -317,9 +317,23 @@ def run_batch(args):
 
 # ------------------------------------------------------------------ precision-form workload
 
+def _match_pitch(Wc):
+    """Row pitch k_match_tc numbers a Wc-column candidate region with: the value in [Wc, Wc + 7] whose
+    columns mod 64 spread the short lattice directions most (the kernel's rule, restated)."""
+    best = None
+    for w in range(Wc, Wc + 8):
+        sc = min((((64 >> ((d & -d).bit_length() - 1)) if d else 1) ** 2) * (dy * dy + dx * dx)
+                 for dy in range(5) for dx in range(-4, 5) if not (dy == 0 and dx <= 0)
+                 for d in [(dy * w + dx) & 63])
+        if best is None or sc > best[0]:
+            best = (sc, w)
+    return best[1]
+
+
 def tc_issued_flops(H, W, K, win, step, green, C):
-    """Tensor-core flops k_match_tc issues: per 8 x 8-reference tile and plane pass, ceil(Hc*Wc/128)
-    MMA groups of 128 candidates x 64 references x 64 (BF16, 2 flop per MAC)."""
+    """Tensor-core flops k_match_tc issues: per 16 x 8-reference tile, plane pass and lane quarter (four
+    tile rows), ceil(band / 64) MMA groups of 128 references x 64 candidates x 64 (BF16, 2 flop per MAC),
+    the band being the quarter's window rows (of the references of that plane) at the kernel's row pitch."""
     import numpy as np
 
     R = (win - 1) // 2
@@ -327,18 +341,44 @@ def tc_issued_flops(H, W, K, win, step, green, C):
     ny, nx = len(ys), len(xs)
     g = np.asarray(green).reshape(ny, nx) if C == 3 else None
     total = 0
-    for gy0 in range(0, ny, 8):
+    for gy0 in range(0, ny, 16):
         for gx0 in range(0, nx, 8):
-            gy1, gx1 = min(ny, gy0 + 8) - 1, min(nx, gx0 + 8) - 1
-            cy0, cy1 = max(0, ys[gy0] - R), min(H - 8, ys[gy1] + R)
+            gy1, gx1 = min(ny, gy0 + 16) - 1, min(nx, gx0 + 8) - 1
+            cy0 = max(0, ys[gy0] - R)
             cx0, cx1 = max(0, xs[gx0] - R), min(W - 8, xs[gx1] + R)
-            nch = ((cy1 - cy0 + 1) * (cx1 - cx0 + 1) + 127) // 128
-            passes = 1
-            if C == 3:
-                blk = g[gy0:gy1 + 1, gx0:gx1 + 1]
-                passes = int(blk.any()) + int((blk == 0).any())
-            total += passes * nch * 2 * 128 * 64 * 64
+            wq = _match_pitch(cx1 - cx0 + 1)
+            for plane in ((1, 0) if C == 3 else (None,)):
+                for q in range(4):
+                    rows = [ry for ry in range(gy0 + 4 * q, min(gy0 + 4 * q + 4, gy1 + 1))
+                            if plane is None or (g[ry, gx0:gx1 + 1] == plane).any()]
+                    if not rows:
+                        continue
+                    lo = max(0, ys[rows[0]] - R) - cy0
+                    hi = min(H - 8, ys[rows[-1]] + R) - cy0
+                    start = (lo * wq) & ~31
+                    total += (((hi + 1) * wq - start + 63) // 64) * 2 * 128 * 64 * 64
     return total
+
+
+def _tc_roofline(dom, ms_per_launch, H, W, C, K, win, step, green):
+    """Roofline of the dominant kernel of a tensor-core form: k_filter_tc (algorithmic transform flops
+    against the dense FP16 peak) or k_match_tc (issued BF16 MMA flops against the dense BF16 peak)."""
+    peaks = _peaks()
+    if dom == "k_filter_tc":
+        wk = algorithmic_work(H, W, C, K, win, step)["k_filter"]
+        ach = wk["flops"] / (ms_per_launch / 1e3) / 1e12
+        return {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": ach / peaks["bf16_tflops"], "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured; FP16 = BF16 rate)",
+                "algorithmic": wk["per"] + "; the Kronecker-form GEMMs issue 1.31 MFLOP per group"}
+    if dom == "k_match_tc":
+        flops = tc_issued_flops(H, W, K, win, step, green, C)
+        ach = flops / (ms_per_launch / 1e3) / 1e12
+        return {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": ach / peaks["bf16_tflops"], "traffic": None,
+                "algorithmic": "issued BF16 MMA flops (%.2f GFLOP per launch)" % (flops / 1e9),
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)"}
+    return None
 
 
 def run_precision(args):
@@ -391,16 +431,8 @@ def run_precision(args):
         want, info = o.denoise(noisy, o.Params(win=31))
         ps_o = synth.psnr(want, clean)
     same = float(np.mean([set(a) == set(b) for a, b in zip(res[1]["idx"].tolist(), res[0]["idx"].tolist())]))
-    tc_ms = res[1]["kernels"].get("k_match_tc")
-    flops = tc_issued_flops(H, W, 16, 31, 4, res[1]["green"], 3)
-    peaks = _peaks()
-    roof = None
-    if tc_ms:
-        ach = flops / (tc_ms / 1e3) / 1e12
-        roof = {"kernel": "k_match_tc", "bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"],
-                "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"], "traffic": None,
-                "algorithmic": "issued BF16 MMA flops (window-union tiles, %.2f GFLOP per launch)" % (flops / 1e9),
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)"}
+    dom = next(iter(res[1]["kernels"]))
+    roof = _tc_roofline(dom, res[1]["kernels"][dom], H, W, 3, 16, 31, 4, res[1]["green"])
     line = {
         "metric": "Mpixel/s denoised on 1 GB300, precision form (tensor-core matching and filter)",
         "value": res[1]["value"], "unit": "Mpixel/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -571,14 +603,9 @@ def run_learned(args):
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP32_PEAK_TFLOPS, "traffic": None, "algorithmic": wk["per"],
                 "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2.07 GHz"}
-    elif dom == "k_match_tc":
+    elif dom in ("k_match_tc", "k_filter_tc"):
         idx, green = hts.match(x, p)
-        flops = tc_issued_flops(H, W, p.K, p.win, p.step, green.cpu().numpy(), 3)
-        ach = flops / (kernels[dom]["ms_per_launch"] / 1e3) / 1e12
-        roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                "frac": ach / peaks["bf16_tflops"], "traffic": None,
-                "algorithmic": "issued BF16 MMA flops (%.2f GFLOP per launch)" % (flops / 1e9),
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)"}
+        roof = _tc_roofline(dom, kernels[dom]["ms_per_launch"], H, W, 3, p.K, p.win, p.step, green.cpu().numpy())
     line = {
         "metric": "Mpixel/s denoised on 1 GB300, learned form (network sigma map + BF16 matching)",
         "value": H * W / (ms / 1e3) / 1e6, "unit": "Mpixel/s", "n_gpus": 1, "steps": args.steps,
@@ -821,15 +848,11 @@ def run_ours(args):
     peaks = _peaks()
     roof = None
     wk = dict(work)
-    wk["k_filter_tc"] = work["k_filter"]
-    if dom == "k_filter_tc":
-        # a contraction on the tensor cores: the algorithmic flops against the FP16 dense peak (the measured
-        # BF16 one; FP16 and BF16 have the same nominal rate)
-        ach = wk[dom]["flops"] / (kernels[dom]["ms_per_launch"] / 1e3) / 1e12
-        roof = {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                "frac": ach / peaks["bf16_tflops"], "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured; FP16 = BF16 rate)",
-                "algorithmic": wk[dom]["per"] + "; the Kronecker-form GEMMs issue 1.31 MFLOP per group"}
+    if dom in ("k_filter_tc", "k_match_tc"):
+        # contractions on the tensor cores, against the dense FP16 / BF16 peak
+        green = hts.match(x, p)[1].cpu().numpy() if dom == "k_match_tc" else None
+        roof = _tc_roofline(dom, kernels[dom]["ms_per_launch"], w["H"], w["W"], w["C"], w["K"], w["win"],
+                            w["step"], green)
     elif dom in wk and "flops" in wk[dom]:
         ach = wk[dom]["flops"] / (kernels[dom]["ms_per_launch"] / 1e3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
