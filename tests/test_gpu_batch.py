@@ -137,9 +137,11 @@ def test_per_image_parameters(hts):
         np.testing.assert_array_equal(hts.denoise(x, sigma=s, p=pi).cpu().numpy(), o.cpu().numpy())
 
 
-def test_batch_tensor_core_filter_equals_single_calls(hts):
-    # precision 2 (exact groups, tensor-core filter) in the graph equals the per-image calls bit for bit
-    pg, pc = hts.params(win=11, K=8, precision=2), hts.params(win=15, precision=2)
+@pytest.mark.parametrize("precision", [1, 2])
+def test_batch_tensor_core_forms_equal_single_calls(hts, precision):
+    # the tensor-core forms in the graph (precision 1: BF16 tensor-core grouping with its exhaustive rescue;
+    # precision 2: exact groups) equal the per-image calls bit for bit
+    pg, pc = hts.params(win=11, K=8, precision=precision), hts.params(win=15, precision=precision)
     imgs = _images()
     xs = [_dev(n) for _, n, _ in imgs]
     sig = [s for _, _, s in imgs]
