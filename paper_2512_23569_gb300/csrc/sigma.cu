@@ -15,6 +15,8 @@
 //                FP64.  Each block adds its votes once (integer, order-free);
 // k_sigma_final: a strict majority divides sigma_est by beta (Eq. 23); then
 //                tau = tau_mult sigma sqrt(2 ln(c K ps^2)).
+#include <cooperative_groups.h>
+
 #include "hts_internal.h"
 
 namespace hts {
@@ -119,8 +121,15 @@ __device__ void lambda64_partial(const float *__restrict__ img, int H, int W, co
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const int j = ((m * k) % K) * (32 / K);
-                xr += p[k] * c_twc64[j];
-                xi += p[k] * c_tws64[j];
+                // quarter turns: the twiddle parts are exactly 0 or +-1, the same sums without the products
+                if (j == 0) xr += p[k];
+                else if (j == 8) xi -= p[k];
+                else if (j == 16) xr -= p[k];
+                else if (j == 24) xi += p[k];
+                else {
+                    xr += p[k] * c_twc64[j];
+                    xi += p[k] * c_tws64[j];
+                }
             }
             l[m] = xr * xr + xi * xi;
         }
@@ -194,8 +203,15 @@ __global__ void __launch_bounds__(128) k_vote(const float *__restrict__ img, int
 #pragma unroll
                 for (int k = 1; k < K; ++k) {
                     const int j = ((m * k) % K) * (32 / K);
-                    xr = fmaf(q[k], c_twc[j], xr);
-                    xi = fmaf(q[k], c_tws[j], xi);
+                    // quarter turns: fmaf with an exact 0 or +-1 is the plain sum (same rounding)
+                    if (j == 0) xr += q[k];
+                    else if (j == 8) xi -= q[k];
+                    else if (j == 16) xr -= q[k];
+                    else if (j == 24) xi += q[k];
+                    else {
+                        xr = fmaf(q[k], c_twc[j], xr);
+                        xi = fmaf(q[k], c_tws[j], xi);
+                    }
                 }
                 lam[m] = fmaf(xr, xr, fmaf(xi, xi, lam[m]));
             }
@@ -243,29 +259,54 @@ __global__ void __launch_bounds__(128) k_vote(const float *__restrict__ img, int
     if (threadIdx.x == 0) atomicAdd(&st->votes, s_votes);
 }
 
-// The groups k_vote could not settle, decided in FP64: one block per listed
-// group, one thread per component (c * 64 of them), fixed-order block sum.
+// The groups k_vote could not settle, decided in FP64: a cluster of VX
+// blocks per listed group, block b summing the components of slice b (one
+// thread per component, fixed-order block sum); block 0 adds the slices'
+// sums in slice order through distributed shared memory.  FP64 runs at a
+// small fraction of the FP32 rate on this part, so a group's components are
+// spread over VX SMs.
+constexpr int VX = 4;
+
+template <int C>
+__host__ __device__ constexpr int vx_threads() {
+    return ((C * NPIX + VX - 1) / VX + 31) / 32 * 32;
+}
+
 template <int C, int K>
-__global__ void __launch_bounds__(C * NPIX) k_vote_exact(const float *__restrict__ img, int H, int W,
-                                                         const int32_t *__restrict__ idx, double gamma_rank,
-                                                         const int32_t *__restrict__ list, DevState *st) {
+__global__ void __launch_bounds__(vx_threads<C>()) k_vote_exact(const float *__restrict__ img, int H, int W,
+                                                                const int32_t *__restrict__ idx, double gamma_rank,
+                                                                const int32_t *__restrict__ list, DevState *st) {
+    namespace cg = cooperative_groups;
     constexpr int NM = K / 2 + 1;
-    __shared__ double sm[(C * NPIX / 32) * NM];
+    constexpr int D = C * NPIX, SL = (D + VX - 1) / VX;
+    __shared__ double sm[(vx_threads<C>() / 32) * NM];
     __shared__ double lam[NM];
+    cg::cluster_group cl = cg::this_cluster();
+    const int b = (int)cl.block_rank();
+    const int ncl = gridDim.x / VX, cid = blockIdx.x / VX;
     const int n = *(volatile int *)&st->vote_uncertain;
-    for (int g = blockIdx.x; g < n; g += gridDim.x) {
+    for (int g = cid; g < n; g += ncl) {
         const int r = list[g];
-        lambda64_partial<C, K>(img, H, W, idx + (size_t)r * K, 0, C * NPIX, sm, lam);
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        lambda64_partial<C, K>(img, H, W, idx + (size_t)r * K, b * SL, min(D, (b + 1) * SL), sm, lam);
+        cl.sync();  // every slice's sums are in its block's shared memory
+        if (b == 0 && threadIdx.x == 0) {
+            double tot[NM];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) tot[m] = 0.0;
+            for (int q = 0; q < VX; ++q) {
+                const double *pl = cl.map_shared_rank(lam, q);
+#pragma unroll
+                for (int m = 0; m < NM; ++m) tot[m] += pl[m];
+            }
             int a = 1;  // rank of lambda_{K/2} among all K (m and K-m share a value)
+#pragma unroll
             for (int m = 0; m < K; ++m) {
                 const int mm = (m <= K / 2) ? m : K - m;
-                if (m != K / 2 && lam[mm] < lam[K / 2]) ++a;
+                if (m != K / 2 && tot[mm] < tot[K / 2]) ++a;
             }
             if ((double)a <= gamma_rank) atomicAdd(&st->votes, 1);
         }
-        __syncthreads();
+        cl.sync();  // block 0 has read every slice
     }
 }
 
@@ -306,7 +347,20 @@ hts_status launch_vote(const float *img, const Geom &g, const int32_t *idx, doub
     if (hts_status e = check_launch("k_vote"); e != HTS_OK) return e;
     {
         KTimer kt("k_vote_exact", s);
-        k_vote_exact<C, K><<<152, C * NPIX, 0, s>>>(img, g.H, g.W, idx, gamma_rank, list, st);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(152);  // 38 clusters of VX blocks
+        cfg.blockDim = dim3(vx_threads<C>());
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = VX;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, k_vote_exact<C, K>, img, g.H, g.W, idx, gamma_rank, list, st);
+        if (e != cudaSuccess) return report(HTS_ECUDA, cudaGetErrorString(e));
     }
     return check_launch("k_vote_exact");
 }
