@@ -328,9 +328,9 @@ hts_status check_basis(const hts_basis *basis, int C) {
 // image: the first chain runs on the workspace's second stream while the
 // second runs on the caller's stream; the threshold waits for both.
 hts_status launch_grouping(const float *img, const Geom &g, const hts_params &p, int32_t *idx, uint8_t *green,
-                           int32_t *fb, DevState *st, cudaStream_t s) {
+                           int32_t *fb, DevState *st, cudaStream_t s, bool flags_done) {
     if (p.precision != 1) return launch_match(img, g, p.gamma_gcp, idx, green, fb, st, s);
-    if (g.C == 3) HTS_TRY(launch_gcp_flags(img, g, p.gamma_gcp, green, s));
+    if (g.C == 3 && !flags_done) HTS_TRY(launch_gcp_flags(img, g, p.gamma_gcp, green, s));
     return launch_match_tc(img, g, p.gamma_gcp, idx, green, fb, st, s);
 }
 
@@ -349,6 +349,10 @@ hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigm
     const float *b32 = basis ? basis->b32 : w->b32;
     const double *eig = (basis && basis->has_eig) ? basis->eig : w->eig;
     const bool fork = est || need_sigma;
+    // the precision form's Eq. 9 flags go first: the basis chain is then launched beside the tensor-core
+    // matcher, whose blocks (one per SM) would otherwise wait behind the covariance's
+    const bool flags_first = p.precision == 1 && g.C == 3;
+    if (flags_first) HTS_TRY(launch_gcp_flags(noisy, g, p.gamma_gcp, w->green, s));
     if (fork) {
         HTS_TRY(cuda_ok(cudaEventRecord(w->ev_fork, s), "cudaEventRecord"));
         HTS_TRY(cuda_ok(cudaStreamWaitEvent(w->aux, w->ev_fork, 0), "cudaStreamWaitEvent"));
@@ -356,7 +360,7 @@ hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigm
         if (need_sigma) HTS_TRY(launch_sigma_floor(g, p, eig, w->st, w->aux));
         HTS_TRY(cuda_ok(cudaEventRecord(w->ev_join, w->aux), "cudaEventRecord"));
     }
-    HTS_TRY(launch_grouping(noisy, g, p, w->idx, w->green, w->fb, w->st, s));
+    HTS_TRY(launch_grouping(noisy, g, p, w->idx, w->green, w->fb, w->st, s, flags_first));
     if (need_sigma && p.adjust_rank) HTS_TRY(launch_sigma_vote(noisy, g, p, w->idx, w->redo, w->st, s));
     if (fork) HTS_TRY(cuda_ok(cudaStreamWaitEvent(s, w->ev_join, 0), "cudaStreamWaitEvent"));
     if (need_sigma) HTS_TRY(launch_sigma_final(g, p, w->st, s));

@@ -111,7 +111,7 @@ hts_status launch_match_rescue(const float *img, const Geom &g, int32_t *idx, co
 
 // The grouping step in the arithmetic p.precision selects (api.cu).
 hts_status launch_grouping(const float *img, const Geom &g, const hts_params &p, int32_t *idx, uint8_t *green,
-                           int32_t *fb, DevState *st, cudaStream_t s);
+                           int32_t *fb, DevState *st, cudaStream_t s, bool flags_done = false);
 
 // ---- global basis (basis.cu)
 size_t cov_partial_count(const Geom &g);  // doubles needed for partial sums
