@@ -456,24 +456,38 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
 
 constexpr int NSHAPES_TC = 7;
 constexpr int SHAPES_TC[NSHAPES_TC][2] = {{8, 8}, {4, 8}, {4, 4}, {2, 4}, {2, 2}, {1, 2}, {1, 1}};
+// Relative time per batch of a tile of each shape (halo staging and flushing grow as tiles shrink),
+// measured on the colour 512^2, 1024^2 and 3840x2160 workloads (8x8: 1, 4x4: 1.06, 2x4: 1.13).
+constexpr double SHAPE_WEIGHT_TC[NSHAPES_TC] = {1.0, 1.02, 1.06, 1.13, 1.3, 1.6, 2.0};
 
 template <int C, int K>
 hts_status launch_ftc(FtcArgs a, const Geom &g, cudaStream_t s, bool *used) {
     using L = FtcLayout<C>;
     const size_t budget = std::min((size_t)smem_optin(), (size_t)227 * 1024);
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // the shape that fits and minimises the rounds of tiles over the SMs x batches per tile x the
+    // shape's relative batch time (ties: the larger shape)
     size_t need = 0;
     int ty = 0, tx = 0, rh = 0, rw = 0;
+    double best = 0.0;
     for (int i = 0; i < NSHAPES_TC; ++i) {
         const int h = std::min(g.H, (SHAPES_TC[i][0] - 1) * g.step + 2 * g.R + PS);
         const int w = std::min(g.W, (SHAPES_TC[i][1] - 1) * g.step + 2 * g.R + PS);
         const size_t n = L::acc_off + (size_t)(C + 1) * h * w * 4;
-        if (n <= budget) {
+        if (n > budget) continue;
+        const long long ntiles = (long long)((g.ny + SHAPES_TC[i][0] - 1) / SHAPES_TC[i][0]) *
+                                 ((g.nx + SHAPES_TC[i][1] - 1) / SHAPES_TC[i][1]);
+        const int nb = (SHAPES_TC[i][0] * SHAPES_TC[i][1] * K + MB - 1) / MB;
+        const double cost = (double)((ntiles + nsm - 1) / nsm) * nb * SHAPE_WEIGHT_TC[i];
+        if (ty == 0 || cost < best) {
+            best = cost;
             ty = SHAPES_TC[i][0];
             tx = SHAPES_TC[i][1];
             rh = h;
             rw = w;
             need = n;
-            break;
         }
     }
     *used = false;
@@ -488,9 +502,6 @@ hts_status launch_ftc(FtcArgs a, const Geom &g, cudaStream_t s, bool *used) {
     a.ntiles = a.nty * a.ntx;
     a.rh_max = rh;
     a.rw_max = rw;
-    int dev = 0, nsm = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(a.ntiles, nsm));
     {
         KTimer kt("k_filter_tc", s);
