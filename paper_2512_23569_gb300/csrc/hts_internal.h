@@ -33,6 +33,7 @@ struct DevState {
     int filter_fixed;     // of which disagreed with FP32 and were corrected
     int xcount;           // in-band coefficients recorded by the main pass
     int error;
+    int mtc_next;         // next (tile, plane pass) item of the tensor-core matcher's work queue
     int learned;          // 1: the learned noise map was used, 0: fell back to the estimate
     double learned_ratio; // geometric mean of (learned sigma / estimated sigma)
     double learned_part[LEARNED_PARTS];  // per-block sums of log(learned sigma)

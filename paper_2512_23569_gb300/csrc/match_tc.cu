@@ -42,6 +42,9 @@
 // per reference: a colour tile runs once per plane that one of its
 // references uses.
 //
+// Blocks take (tile, plane pass) items from a queue (an atomic counter), so
+// the two passes of a colour tile run on two SMs.
+//
 // Every mbarrier wait is bounded; a wait that gives up records error code 2
 // in the call's state, and the block waits (bounded) for the MMAs it has
 // issued, releases its tensor memory and leaves.
@@ -180,6 +183,7 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
     uint64_t *empty = full + NBUF;                                    // [NBUF]: every warp loaded the run
     int *abort_flag = reinterpret_cast<int *>(empty + NBUF);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(abort_flag + 1);
+    int *item_slot = reinterpret_cast<int *>(tmem_slot + 1);  // the block's current work item
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const bool cw = warp < NWC;              // a reading warp
@@ -203,7 +207,16 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
     long long gc = 0;  // runs issued by this block so far (accumulator gc % NBUF, use gc / NBUF)
     bool ok = true;
 
-    for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+    const int npass = (a.C == 3) ? 2 : 1;
+    while (ok) {
+        // next item of the work queue: (tile, plane pass), so that the two passes of a colour tile run
+        // on two SMs and blocks that drew passes without references move on at once
+        if (tid == 0) *item_slot = atomicAdd(&a.st->mtc_next, 1);
+        __syncthreads();
+        const int item = *item_slot;
+        __syncthreads();
+        if (item >= a.ntiles * npass) break;
+        const int tile = item / npass;
         const int tyi = tile / a.ntx, txi = tile - tyi * a.ntx;
         const int gy0 = tyi * TTY, gx0 = txi * TTX;
         const int gy1 = min(a.ny, gy0 + TTY) - 1, gx1 = min(a.nx, gx0 + TTX) - 1;
@@ -218,7 +231,8 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
         const uint32_t lowm = (1u << (32 - __clz(ncand))) - 1u;  // candidate index bits of a key
         const uint32_t him = ~lowm;
 
-        for (int pass = 0; pass < (a.C == 3 ? 2 : 1) && ok; ++pass) {
+        {
+            const int pass = item - tile * npass;
             // ---- per-reference records (thread j < NR: reference j = tile row j / 8, column j % 8),
             //      and each quarter's band of candidate rows
             bool any = false;
@@ -529,7 +543,9 @@ hts_status launch_tc(const TcArgs &a, cudaStream_t s) {
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = std::max(1, std::min(a.ntiles, nsm));
+    const int items = a.ntiles * (a.C == 3 ? 2 : 1);
+    const int grid = std::max(1, std::min(items, nsm));
+    if (cudaMemsetAsync(&a.st->mtc_next, 0, sizeof(int), s) != cudaSuccess) return check_launch("cudaMemsetAsync");
     {
         KTimer kt("k_match_tc", s);
         k_match_tc<K><<<grid, NT, L.total, s>>>(a);
