@@ -197,20 +197,30 @@ __global__ void __launch_bounds__(128) k_vote(const float *__restrict__ img, int
                 a1 += fabsf(q[k]);
             }
             esq = fmaf(a1, a1, esq);
+            // k and K - k see conjugate twiddles: q_k w^{mk} + q_{K-k} w^{-mk} = (q_k + q_{K-k}) cos
+            // + i (q_k - q_{K-k}) (-sin), and w^{m K/2} = (-1)^m.  Per component this evaluation errs by
+            // at most sqrt(2) (K/2 + 5/2) u sum_k |q_k| (the subtraction, the pair sum, the twiddle, K/2
+            // accumulations), inside the bound below (sqrt(2) (K + 3) u sum_k |q_k|).
+            float sp[K / 2 + 1], dm[K / 2 + 1];
+#pragma unroll
+            for (int k = 1; k < K / 2; ++k) {
+                sp[k] = q[k] + q[K - k];
+                dm[k] = q[k] - q[K - k];
+            }
 #pragma unroll
             for (int m = 1; m < NM; ++m) {
-                float xr = 0.f, xi = 0.f;
+                float xr = (m & 1) ? -q[K / 2] : q[K / 2], xi = 0.f;
 #pragma unroll
-                for (int k = 1; k < K; ++k) {
+                for (int k = 1; k < K / 2; ++k) {
                     const int j = ((m * k) % K) * (32 / K);
                     // quarter turns: fmaf with an exact 0 or +-1 is the plain sum (same rounding)
-                    if (j == 0) xr += q[k];
-                    else if (j == 8) xi -= q[k];
-                    else if (j == 16) xr -= q[k];
-                    else if (j == 24) xi += q[k];
+                    if (j == 0) xr += sp[k];
+                    else if (j == 8) xi -= dm[k];
+                    else if (j == 16) xr -= sp[k];
+                    else if (j == 24) xi += dm[k];
                     else {
-                        xr = fmaf(q[k], c_twc[j], xr);
-                        xi = fmaf(q[k], c_tws[j], xi);
+                        xr = fmaf(sp[k], c_twc[j], xr);
+                        xi = fmaf(dm[k], c_tws[j], xi);
                     }
                 }
                 lam[m] = fmaf(xr, xr, fmaf(xi, xi, lam[m]));
