@@ -70,6 +70,23 @@ def test_rescue_of_crowded_bins(oracle, hts):
     assert hts.last_stats()["match_fallback"] >= 50
 
 
+def test_rescue_of_crowded_bins_colour(oracle, hts):
+    # colour: stripes of constant 3x + y (period 16) lie along (3, -1), which the 59-column regions of a
+    # 31x31 window map onto 4 bins; the channel gains differ between the halves of the image so that
+    # both Eq. 9 planes occur -- the rescued references must be matched on their own plane
+    H = W = 128
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    base = 120.0 + 60.0 * np.sin(2.0 * np.pi * (3.0 * xx + yy) / 16.0)
+    left = xx < W / 2
+    gains = [np.where(left, 1.3, 0.7), np.ones_like(xx), np.where(left, 0.8, 0.6)]  # R, G, B
+    rng = np.random.default_rng(23)
+    noisy = np.stack([base * g_ + rng.normal(0.0, 5.0, base.shape) for g_ in gains]).astype(np.float32)
+    _check_groups(oracle, hts, noisy, 16, 31)
+    assert hts.last_stats()["match_fallback"] >= 50
+    green = hts.match(_dev(noisy), hts.params(K=16, win=31, precision=1))[1].cpu().numpy()
+    assert 0 < int(green.sum()) < green.size  # both planes
+
+
 def _check_groups(oracle, hts, noisy, K, win):
     C, H, W = noisy.shape
     p1 = hts.params(K=K, win=win, precision=1)
