@@ -66,9 +66,11 @@ typedef struct {
                         *    definition's, ties to the lower index); FP32 transforms with FP64
                         *    threshold decisions inside the FP32 error band.
                         * 1: precision form: BF16 distances on the tensor cores (FP32
-                        *    accumulation), the 2K nearest re-ranked with FP32 distances (groups
-                        *    may differ from the FP64 definition's where BF16 rounding reorders
-                        *    near neighbours); FP16 projections on the tensor cores (FP32
+                        *    accumulation), the K + max(K/2, 8) nearest re-ranked with FP32
+                        *    distances (groups may differ from the FP64 definition's where BF16
+                        *    rounding reorders near neighbours; a reference whose candidate
+                        *    bins may have dropped one of its K + 3 nearest is matched
+                        *    exhaustively in FP32); FP16 projections on the tensor cores (FP32
                         *    accumulation) with FP32 threshold decisions.  Windows too large for
                         *    on-chip staging give HTS_EUNSUPPORTED.
                         * 2: the groups of 0 with the filter of 1. */
