@@ -63,7 +63,8 @@ def _grid(n, step, ps=8):
 
 
 def algorithmic_work(H, W, C, K, win, step):
-    """Algorithmic flops / bytes per launch of the main kernels."""
+    """Algorithmic flops / bytes per launch of the main kernels: distances 3 flop x 64 px per candidate
+    pair, the filter's projections and Haar transforms per group, the normalisation's bytes per pixel."""
     ys, xs = _grid(H, step), _grid(W, step)
     R = (win - 1) // 2
     cy = [min(H - 8, y + R) - max(0, y - R) + 1 for y in ys]
