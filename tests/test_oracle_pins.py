@@ -406,3 +406,66 @@ def test_per_reference_thresholds_reduce_to_one(oracle):
     c, info = oracle.denoise(noisy, p, sigma=sig)
     changed = np.argwhere(np.abs(c - a) > 0)
     assert len(changed) > 0
+
+
+# ------------------------------------------ Eq. 23: the vote's decision
+
+
+def _vote_image_and_groups(nref_target, voters, K=16):
+    """A gray 8 x W image, left half flat 40, right half flat 200, whose reference grid has nref_target
+    positions, with hand-made groups (Eq. 22-23 only reads the members the groups name):
+    - a "voting" group repeats one flat patch K times: lambda_0 = K^2 |p|^2 and lambda_m = 0 for m != 0,
+      so lambda_hat = lambda_{K/2} = 0 has rank position a = 1 (no lambda below it);
+    - a "non-voting" group alternates the 40-patch and the 200-patch: lambda_{K/2} = K^2 |d|^2 with
+      d = (40 - 200) / 2 per pixel, above every lambda_m (m != 0, K/2) = 0 and below lambda_0 = K^2 |c|^2,
+      c = 120 per pixel, so a = K - 1.
+    The first `voters` groups vote."""
+    W = 8 + 4 * (nref_target - 1)
+    img = np.full((1, 8, W), 40.0, dtype=np.float32)
+    img[:, :, W // 2:] = 200.0
+    left, right = 0, W - 8  # raster indices of two flat patches (row 0)
+    idx = np.empty((nref_target, K), dtype=np.int32)
+    for r in range(nref_target):
+        if r < voters:
+            idx[r] = left
+        else:
+            idx[r] = [left if k % 2 == 0 else right for k in range(K)]
+    return img, idx
+
+
+@pytest.mark.parametrize("nref,voters,adjust", [
+    (16, 9, True),    # strict majority of an even count
+    (16, 8, False),   # exact tie: no adjustment
+    (16, 7, False),   # minority
+    (15, 8, True),    # strict majority of an odd count
+    (15, 7, False),
+    (16, 16, True),   # unanimous
+    (16, 0, False),
+])
+def test_eq23_strict_majority_divides_sigma_by_beta(oracle, nref, voters, adjust):
+    K = 16
+    img, idx = _vote_image_and_groups(nref, voters, K)
+    p = oracle.Params(K=K, win=21, beta=1.5, mp_correct=0)
+    assert oracle.num_refs(img.shape[1], img.shape[2], p) == nref
+    # rank positions of the two hand-made group kinds (Eq. 22): 1 and K - 1, against gamma_K = 13 K / 32
+    votes, ranks = oracle.rank_votes(img, p, idx)
+    assert votes == voters
+    np.testing.assert_array_equal(ranks, [1] * voters + [K - 1] * (nref - voters))
+    # Eq. 12 floor from given eigenvalues (no Marchenko-Pastur edge): sigma_est^2 = lambda_min / (ps N_ref)
+    sigma0 = 10.0
+    eig = np.array([8.0 * nref * sigma0 ** 2, 5e6, 7e6])
+    s = oracle.estimate_sigma(img, p, eigvals=eig, nref=nref, idx=idx)
+    assert s["votes"] == voters and s["nref"] == nref
+    assert s["sigma_est"] == pytest.approx(sigma0, rel=1e-15)
+    assert s["adjust"] is adjust
+    # Eq. 23: divided by beta (not multiplied, not the variance divided) on a strict majority only
+    want = sigma0 / 1.5 if adjust else sigma0
+    assert s["sigma_hat"] == pytest.approx(want, rel=1e-15)
+
+
+def test_eq23_vote_off_keeps_the_floor(oracle):
+    img, idx = _vote_image_and_groups(16, 16)
+    p = oracle.Params(K=16, win=21, beta=1.5, mp_correct=0, adjust_rank=0)
+    eig = np.array([8.0 * 16 * 9.0])
+    s = oracle.estimate_sigma(img, p, eigvals=eig, nref=16, idx=idx)
+    assert not s["adjust"] and s["sigma_hat"] == pytest.approx(3.0, rel=1e-15)
