@@ -131,7 +131,8 @@ typedef struct {
  * strict majority divides by beta (Eq. 23).  basis: the covariances'
  * eigenvalues are taken from it when non-NULL (it must have been estimated,
  * not created without eigenvalues), else estimated.  Writes *sigma_out (host)
- * and *info (optional).  Synchronises on `stream`. */
+ * and *info (optional).  Synchronises on `stream`; HTS_ETIMEOUT / HTS_EINTERNAL
+ * if a kernel recorded a failure (the outputs are then invalid). */
 hts_status hts_estimate_sigma(const float *img, int H, int W, int C, const hts_basis *basis,
                               const hts_params *p, double *sigma_out, hts_sigma_info *info, void *stream);
 
@@ -152,22 +153,30 @@ hts_status hts_denoise(const float *noisy, float *out, int H, int W, int C, floa
  * the implicit device synchronisation of cudaMalloc / cudaFree.  The paper
  * has no counterpart; this is a deployment variant of hts_denoise.
  * All intermediate buffers live in one static device array of the library
- * (about 21 MB, held by every GPU that loads the library until the process
- * exits).  That bounds the image: H*W <= 262144 pixels, at most 65536
- * reference patches and N_ref*K <= 1048576; larger images return HTS_EINVAL
- * before any device work.  The caller still passes `noisy` and `out` (device);
- * every other argument and the result are as for hts_denoise.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress):
- * make that first call before any stream capture.  All calls share the one
- * array and each overwrites what the previous call left there, so calls that
- * overlap on the GPU (other streams, or host threads without ordering) race
- * and corrupt each other's results; serialise them.  Asynchronous. */
+ * (about 21 MB).  A GPU holds it from the first call on that GPU (CUDA may
+ * load the library's device code, and the array with it, only then) until
+ * the process exits, so make the first call at start-up.  That bounds the
+ * image: H*W <= 262144 pixels, at most 65536 reference patches and
+ * N_ref*K <= 1048576; larger images return HTS_EINVAL before any device work.
+ * The caller still passes `noisy` and `out` (device); every other argument
+ * (a caller's basis must live on the current device and match C) is as for
+ * hts_denoise, and the result equals hts_denoise's within 1e-3 on the
+ * [0, 255] scale.  Unlike hts_denoise, the basis estimate runs in series with
+ * the grouping on `stream` (no second stream), so a call takes a little
+ * longer.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it: make that first call before any
+ * stream capture, and do not call this entry point again after resetting the
+ * device.  All calls share the one array and each overwrites what the
+ * previous call left there, so calls that overlap on the GPU (other streams,
+ * or host threads without ordering) race and corrupt each other's results;
+ * serialise them.  Asynchronous. */
 hts_status hts_denoise_noalloc(const float *noisy, float *out, int H, int W, int C, float sigma,
                                const hts_basis *basis, const hts_params *p, void *stream);
 
 /* hts_denoise on HOST buffers: copies noisy_host to the device, denoises and
  * copies the result back into out_host, all on `stream`, then synchronises.
- * Pinned host memory is fastest but not required. */
+ * Pinned host memory is fastest but not required.  HTS_ETIMEOUT /
+ * HTS_EINTERNAL if a kernel recorded a failure (out_host is then invalid). */
 hts_status hts_denoise_host(const float *noisy_host, float *out_host, int H, int W, int C, float sigma,
                             const hts_basis *basis, const hts_params *p, void *stream);
 
@@ -176,8 +185,11 @@ typedef struct {
     const float *noisy;       /* device, CHW */
     float *out;               /* device, CHW */
     int H, W, C;
-    float sigma;              /* < 0: estimate */
+    float sigma;              /* < 0: estimate (ignored where sigma_map is given) */
     const hts_params *params; /* NULL: the batch's parameters (read at the call, not kept) */
+    const float *sigma_map;   /* NULL, or a noise level per reference patch (device, N_ref floats,
+                               * raster order of the reference grid): the image is denoised as by
+                               * hts_denoise_sigma_map (Eq. 20 with a local sigma) */
 } hts_image;
 
 /* Denoises n independent images (mixed sizes and channel counts, sigma known
@@ -273,6 +285,21 @@ hts_status hts_cnn_load(const char *path, hts_cnn **out);
 hts_status hts_denoise_learned(const float *noisy, float *out, int H, int W, int C, hts_cnn *net,
                                const hts_basis *basis, const hts_params *p, double fallback_factor, void *stream);
 
+/* The batched learned form: hts_denoise_batch in which every image's noise
+ * level per reference patch comes from the network `net` (as in
+ * hts_denoise_learned, Sec. III-C), checked against the image's eigenvalue
+ * estimate (Eq. 12, 22-23) with `fallback_factor` (> 1).  The networks'
+ * forward passes run inside the same graph launch, one image after another
+ * (largest first) on a stream of their own, into buffers the batch's plan
+ * owns; each image's filter waits only for its own map.  Every image must have
+ * net's channel count and no sigma_map; sigma is ignored.  The plan keeps
+ * `net` (its weights are read at every launch, so training between calls is
+ * seen); hts_cnn_free drops the plans that use it.  Output equals
+ * hts_denoise_learned's on each image, bit for bit.  hts_last_batch_stats
+ * reports each image's learned / learned_ratio. */
+hts_status hts_denoise_batch_learned(const hts_image *imgs, int n, hts_cnn *net, double fallback_factor,
+                                     const hts_params *p, void *stream);
+
 /* -------------------------------------- enhancement strategy (RA-Haar-tSVD) */
 
 /* RA-Haar-tSVD (Eq. 24-25): the first Haar row of every group -- sqrt(K)
@@ -357,12 +384,18 @@ typedef struct {
     int filter_fixed;      /* FP64 decisions that overturned the FP32 one (contribution corrected) */
     int learned;           /* hts_denoise_learned: 1 = learned noise map used, 0 = fell back */
     double learned_ratio;  /* hts_denoise_learned: geometric mean of learned / estimated sigma */
+    int device_error;      /* failure the kernels recorded: 0 none, 2 a bounded wait gave up, 1 a
+                            * consistency check failed */
 } hts_stats;
+/* Fills *out and returns HTS_OK, or HTS_ETIMEOUT (device_error 2) / HTS_EINTERNAL
+ * (device_error 1) when a kernel of that call recorded a failure: its result is
+ * then invalid.  This is how the asynchronous calls report device-side failures. */
 hts_status hts_last_stats(hts_stats *out, void *stream);
 
 /* Per-image counters (out[0..n-1], as hts_last_stats) and, if info is not
  * NULL, the schedule of the last hts_denoise_batch on `stream`.  HTS_EINVAL if
- * no batch ran there.  Synchronises. */
+ * no batch ran there; HTS_ETIMEOUT / HTS_EINTERNAL if a kernel recorded a
+ * failure for one of the images (its device_error says which).  Synchronises. */
 hts_status hts_last_batch_stats(hts_stats *out, int n, hts_batch_info *info, void *stream);
 
 /* Kernel timing: between hts_profile_begin() and hts_profile_end() every
@@ -377,6 +410,25 @@ typedef struct {
 } hts_kernel_time;
 hts_status hts_profile_begin(void);
 hts_status hts_profile_end(hts_kernel_time *out, int max, int *n_out);
+
+/* Host-side fault injection, for tests of the failure paths (nothing is made
+ * to fault on the GPU).  spec: comma-separated "kind:N" items, N >= 1, each arming a
+ * one-shot countdown: the N-th event of that kind from now on fails; NULL or ""
+ * disarms all.  Kinds:
+ *   alloc:N   the N-th device allocation of the library fails as out of memory
+ *             (the call returns HTS_ENOMEM; nothing is allocated);
+ *   launch:N  the N-th kernel launch is reported as failed (the call returns
+ *             HTS_ECUDA; the library stays usable);
+ *   wait:N    in the N-th launch of the tensor-core matcher (precision 1) the
+ *             thread that issues the MMAs first waits on a barrier that nothing
+ *             arrives on; the bounded wait gives up after a few thousand polls, the
+ *             kernel records the failure and gives every reference its own position
+ *             as its group (HTS_ETIMEOUT where the state is read back:
+ *             hts_last_stats, hts_denoise_host, hts_estimate_sigma).
+ * Launches inside a stream capture are never counted.  The environment variable
+ * HTS_FAULT (same syntax) arms the countdowns at the library's first event.
+ * Process-wide.  HTS_EINVAL on a malformed spec (nothing changes). */
+hts_status hts_fault_inject(const char *spec);
 
 /* Thread-local message for the last failing call on this host thread. */
 const char *hts_last_error(void);

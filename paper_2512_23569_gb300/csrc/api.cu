@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -20,6 +21,7 @@ namespace hts {
 static std::atomic<unsigned long long> g_launches{0};
 static thread_local std::string g_err;
 static thread_local unsigned long long g_captured = 0;
+static thread_local bool g_launch_fault = false;  // an injected launch failure awaits its check_launch
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -30,6 +32,67 @@ static bool capturing(cudaStream_t s) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return false;
     return cs != cudaStreamCaptureStatusNone;
+}
+
+bool stream_capturing(cudaStream_t s) { return capturing(s); }
+
+// ------------------------------------------------------- fault injection
+
+// One-shot countdowns per kind (0 = disarmed): the N-th event of the kind
+// after arming fails.  Armed by hts_fault_inject, or once, at the library's
+// first event, from the environment variable HTS_FAULT (same syntax).
+static std::atomic<long long> g_fault[FAULT_KINDS];
+static std::once_flag g_fault_env;
+
+static bool parse_fault(const char *spec, long long out[FAULT_KINDS]) {
+    for (int k = 0; k < FAULT_KINDS; ++k) out[k] = 0;
+    if (!spec) return true;
+    std::string s(spec);
+    size_t i = 0;
+    while (i < s.size()) {
+        size_t j = s.find_first_of(",|", i);
+        if (j == std::string::npos) j = s.size();
+        const std::string item = s.substr(i, j - i);
+        i = j + 1;
+        if (item.empty()) continue;
+        const size_t c = item.find(':');
+        if (c == std::string::npos) return false;
+        const std::string kind = item.substr(0, c), num = item.substr(c + 1);
+        if (num.empty() || num.size() > 12 || num.find_first_not_of("0123456789") != std::string::npos) return false;
+        const long long n = std::stoll(num);
+        if (n < 1) return false;
+        if (kind == "alloc") out[FAULT_ALLOC] = n;
+        else if (kind == "launch") out[FAULT_LAUNCH] = n;
+        else if (kind == "wait") out[FAULT_WAIT] = n;
+        else return false;
+    }
+    return true;
+}
+
+static void fault_env() {
+    std::call_once(g_fault_env, [] {
+        long long v[FAULT_KINDS];
+        if (parse_fault(std::getenv("HTS_FAULT"), v))
+            for (int k = 0; k < FAULT_KINDS; ++k)
+                if (v[k] > 0) g_fault[k].store(v[k]);
+    });
+}
+
+bool fault_take(FaultKind k) {
+    fault_env();
+    long long v = g_fault[k].load();
+    while (v > 0) {
+        if (g_fault[k].compare_exchange_weak(v, v - 1)) return v == 1;
+    }
+    return false;
+}
+
+cudaError_t dev_malloc_bytes(void **p, size_t bytes) {
+    if (fault_take(FAULT_ALLOC)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
 }
 
 hts_status allow_smem(const void *func, size_t need) {
@@ -99,6 +162,7 @@ KTimer::KTimer(const char *name, cudaStream_t s) : slot(-1), stream(s) {
         return;
     }
     count_launch();
+    if (fault_take(FAULT_LAUNCH)) g_launch_fault = true;
     std::lock_guard<std::mutex> lk(g_pmu);
     if (!g_prof) return;
     ProfRec r;
@@ -125,6 +189,11 @@ static hts_status fail(hts_status s, const std::string &msg) {
 hts_status report(hts_status s, const char *msg) { return fail(s, msg); }
 
 hts_status check_launch(const char *what) {
+    if (g_launch_fault) {
+        g_launch_fault = false;
+        cudaGetLastError();
+        return fail(HTS_ECUDA, std::string(what) + ": launch failure (injected by hts_fault_inject)");
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(HTS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
     return HTS_OK;
@@ -134,6 +203,14 @@ static hts_status cuda_ok(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return HTS_OK;
     if (e == cudaErrorMemoryAllocation) return fail(HTS_ENOMEM, std::string(what) + ": out of device memory");
     return fail(HTS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Status of a failure the kernels recorded in DevState.error (2: a bounded
+// wait gave up; 1: a consistency check failed).
+hts_status device_status(int err) {
+    if (err == 2) return fail(HTS_ETIMEOUT, "a bounded device-side wait gave up; the call's result is invalid");
+    if (err != 0) return fail(HTS_EINTERNAL, "a device-side consistency check failed; the call's result is invalid");
+    return HTS_OK;
 }
 
 #define HTS_TRY(expr)                       \
@@ -167,7 +244,7 @@ static hts_status grow(T *&ptr, size_t &cap, size_t need, const char *what) {
     ptr = nullptr;
     cap = 0;
     const size_t n = need + need / 4 + 64;
-    HTS_TRY(cuda_ok(cudaMalloc(reinterpret_cast<void **>(&ptr), n * sizeof(T)), what));
+    HTS_TRY(cuda_ok(dev_malloc(reinterpret_cast<void **>(&ptr), n * sizeof(T)), what));
     cap = n;
     return HTS_OK;
 }
@@ -185,10 +262,10 @@ static hts_status get_ws(cudaStream_t s, Workspace **out) {
     Workspace *w = new Workspace();
     w->device = dev;
     w->stream = s;
-    hts_status st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&w->st), sizeof(DevState)), "cudaMalloc(state)");
-    if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&w->b64), 2 * 256 * sizeof(double)), "cudaMalloc");
-    if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&w->b32), 2 * 256 * sizeof(float)), "cudaMalloc");
-    if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&w->eig), 4 * 8 * sizeof(double)), "cudaMalloc");
+    hts_status st = cuda_ok(dev_malloc(reinterpret_cast<void **>(&w->st), sizeof(DevState)), "cudaMalloc(state)");
+    if (st == HTS_OK) st = cuda_ok(dev_malloc(reinterpret_cast<void **>(&w->b64), 2 * 256 * sizeof(double)), "cudaMalloc");
+    if (st == HTS_OK) st = cuda_ok(dev_malloc(reinterpret_cast<void **>(&w->b32), 2 * 256 * sizeof(float)), "cudaMalloc");
+    if (st == HTS_OK) st = cuda_ok(dev_malloc(reinterpret_cast<void **>(&w->eig), 4 * 8 * sizeof(double)), "cudaMalloc");
     // The basis chain ends in a few-block eigensolver that the threshold waits
     // for: its stream gets the highest priority so that its blocks are not
     // queued behind the grouping's.
@@ -198,7 +275,13 @@ static hts_status get_ws(cudaStream_t s, Workspace **out) {
         st = cuda_ok(cudaStreamCreateWithPriority(&w->aux, cudaStreamNonBlocking, prio_hi), "cudaStreamCreate");
     if (st == HTS_OK) st = cuda_ok(cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming), "cudaEventCreate");
     if (st == HTS_OK) st = cuda_ok(cudaEventCreateWithFlags(&w->ev_join, cudaEventDisableTiming), "cudaEventCreate");
-    if (st != HTS_OK) {
+    if (st != HTS_OK) {  // release what was made before the failure
+        cudaFree(w->st);
+        cudaFree(w->b64);
+        cudaFree(w->b32);
+        cudaFree(w->eig);
+        if (w->ev_fork) cudaEventDestroy(w->ev_fork);
+        if (w->aux) cudaStreamDestroy(w->aux);
         delete w;
         return st;
     }
@@ -272,9 +355,9 @@ static hts_status alloc_basis(int C, hts_basis **out) {
     b->b64 = nullptr;
     b->b32 = nullptr;
     b->eig = nullptr;
-    hts_status st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&b->b64), basis_doubles(b->ns) * sizeof(double)), "cudaMalloc(basis)");
-    if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&b->b32), basis_doubles(b->ns) * sizeof(float)), "cudaMalloc(basis)");
-    if (st == HTS_OK) st = cuda_ok(cudaMalloc(reinterpret_cast<void **>(&b->eig), b->ns * 16 * sizeof(double)), "cudaMalloc(basis)");
+    hts_status st = cuda_ok(dev_malloc(reinterpret_cast<void **>(&b->b64), basis_doubles(b->ns) * sizeof(double)), "cudaMalloc(basis)");
+    if (st == HTS_OK) st = cuda_ok(dev_malloc(reinterpret_cast<void **>(&b->b32), basis_doubles(b->ns) * sizeof(float)), "cudaMalloc(basis)");
+    if (st == HTS_OK) st = cuda_ok(dev_malloc(reinterpret_cast<void **>(&b->eig), b->ns * 16 * sizeof(double)), "cudaMalloc(basis)");
     if (st != HTS_OK) {
         cudaFree(b->b64);
         cudaFree(b->b32);
@@ -336,7 +419,7 @@ hts_status launch_grouping(const float *img, const Geom &g, const hts_params &p,
 
 hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
                        const hts_params &p, const Bufs &b, cudaStream_t s, float *sigma_ref, double fallback_factor,
-                       hts_fcn *fcn, float *ra_buf) {
+                       hts_fcn *fcn, float *ra_buf, cudaEvent_t map_ready) {
     const Bufs *w = &b;
     const size_t hw = (size_t)g.H * g.W;
     HTS_TRY(cuda_ok(cudaMemsetAsync(w->st, 0, sizeof(DevState), s), "cudaMemsetAsync(state)"));
@@ -365,6 +448,7 @@ hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigm
     if (fork) HTS_TRY(cuda_ok(cudaStreamWaitEvent(s, w->ev_join, 0), "cudaStreamWaitEvent"));
     if (need_sigma) HTS_TRY(launch_sigma_final(g, p, w->st, s));
     else HTS_TRY(launch_set_sigma(sigma > 0 ? (double)sigma : 0.0, g, p, w->st, s));
+    if (map_ready) HTS_TRY(cuda_ok(cudaStreamWaitEvent(s, map_ready, 0), "cudaStreamWaitEvent"));
     if (sigma_ref && fallback_factor > 0) HTS_TRY(launch_learned_check(sigma_ref, g.nref, fallback_factor, w->st, s));
     float *mean_est = nullptr;
     if (fcn) {  // enhancement strategy: refined mean patch of every group (Eq. 24-25)
@@ -392,7 +476,7 @@ size_t bufs_bytes(const Geom &g) {
            align256(32 * sizeof(double)) + align256(nref * g.K * sizeof(int32_t)) + align256(nref) +
            2 * align256(nref * sizeof(int32_t)) + align256(nref * XLIST_PER_REF * sizeof(int4)) + align256(nref) +
            align256(hw * g.C * sizeof(long long)) + align256(hw * sizeof(int)) +
-           align256(cov_partial_count(g) * sizeof(double));
+           align256(cov_partial_count(g) * sizeof(double)) + align256(nref * sizeof(float));
 }
 
 void bufs_carve(const Geom &g, unsigned char *base, Bufs *b) {
@@ -416,6 +500,7 @@ void bufs_carve(const Geom &g, unsigned char *base, Bufs *b) {
     b->acc = reinterpret_cast<long long *>(take(hw * g.C * sizeof(long long)));
     b->wcount = reinterpret_cast<int *>(take(hw * sizeof(int)));
     b->cov = reinterpret_cast<double *>(take(cov_partial_count(g) * sizeof(double)));
+    b->sref = reinterpret_cast<float *>(take(nref * sizeof(float)));
 }
 
 }  // namespace hts
@@ -600,7 +685,7 @@ hts_status hts_estimate_sigma(const float *img, int H, int W, int C, const hts_b
         info->adjusted = hs.adjusted;
         info->uncertain = hs.vote_uncertain;
     }
-    return HTS_OK;
+    return device_status(hs.error);
 }
 
 hts_status hts_denoise(const float *noisy, float *out, int H, int W, int C, float sigma, const hts_basis *basis,
@@ -633,7 +718,10 @@ hts_status hts_denoise_host(const float *noisy_host, float *out_host, int H, int
     HTS_TRY(cuda_ok(cudaMemcpyAsync(w->io_in, noisy_host, n * sizeof(float), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(H2D)"));
     HTS_TRY(denoise_impl(w->io_in, w->io_out, g, sigma, basis, *p, w, s));
     HTS_TRY(cuda_ok(cudaMemcpyAsync(out_host, w->io_out, n * sizeof(float), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(D2H)"));
-    return cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    int err = 0;
+    HTS_TRY(cuda_ok(cudaMemcpyAsync(&err, &w->st->error, sizeof(int), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(D2H)"));
+    HTS_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+    return device_status(err);
 }
 
 hts_status hts_denoise_sigma_map(const float *noisy, float *out, int H, int W, int C, const float *sigma_ref,
@@ -707,7 +795,8 @@ hts_status hts_last_stats(hts_stats *out, void *stream) {
     out->filter_fixed = hs.filter_fixed;
     out->learned = hs.learned;
     out->learned_ratio = hs.learned_ratio;
-    return HTS_OK;
+    out->device_error = hs.error;
+    return device_status(hs.error);
 }
 
 hts_status hts_profile_begin(void) {
@@ -751,6 +840,14 @@ hts_status hts_profile_end(hts_kernel_time *out, int max, int *n_out) {
     }
     if (n_out) *n_out = n;
     return st;
+}
+
+hts_status hts_fault_inject(const char *spec) {
+    fault_env();  // the environment's setting, if any, is read first and then replaced
+    long long v[FAULT_KINDS];
+    if (!parse_fault(spec, v)) return fail(HTS_EINVAL, "fault spec: expected kind:N[,kind:N] with kind alloc, launch or wait, N >= 1");
+    for (int k = 0; k < FAULT_KINDS; ++k) g_fault[k].store(v[k]);
+    return HTS_OK;
 }
 
 const char *hts_last_error(void) { return g_err.c_str(); }

@@ -17,6 +17,7 @@
 // output (the aggregation is exact integer arithmetic and every group is
 // computed independently), so tuning changes only the speed.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -24,6 +25,7 @@
 #include <string>
 #include <vector>
 
+#include "cnn_internal.h"
 #include "hts_internal.h"
 
 namespace hts {
@@ -46,11 +48,17 @@ constexpr int MAX_LANES = 8;
 
 struct Sig {
     int device = 0;
-    std::vector<int> dims;          // per image: H, W, C, estimated sigma (0/1)
+    std::vector<int> dims;          // per image: H, W, C, estimated sigma (0/1), caller's sigma map (0/1)
     std::vector<unsigned char> par;  // per image: the bytes of its parameters
+    const hts_cnn *net = nullptr;    // learned form: the network, its readout window, the fallback factor
+    int window = 0;
+    double factor = 0.0;
     bool operator<(const Sig &o) const {
         if (device != o.device) return device < o.device;
         if (dims != o.dims) return dims < o.dims;
+        if (net != o.net) return net < o.net;
+        if (window != o.window) return window < o.window;
+        if (factor != o.factor) return factor < o.factor;
         return par < o.par;
     }
 };
@@ -68,6 +76,14 @@ struct Plan {
     cudaEvent_t ev_lane[MAX_LANES] = {};
     std::vector<cudaEvent_t> ev_img;  // fork and join of every image
     cudaEvent_t ev_start = nullptr, ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    // learned form: the networks' forwards run one after another on their own stream, into buffers of
+    // the plan sized for the largest image; image i's filter waits for ev_map[i]
+    hts_cnn *net = nullptr;
+    cudaStream_t cnn_stream = nullptr;
+    cudaEvent_t ev_cnn = nullptr;
+    std::vector<cudaEvent_t> ev_map;
+    __half *h16[2] = {};
+    float *cmap = nullptr, *crows = nullptr;
     int nlanes = 0;
     cudaGraphExec_t exec = nullptr;
     unsigned long long kernels = 0;
@@ -95,24 +111,31 @@ void destroy_plan(Plan *P) {
         if (P->ev_lane[l]) cudaEventDestroy(P->ev_lane[l]);
     }
     for (cudaEvent_t e : P->ev_img) cudaEventDestroy(e);
-    for (cudaEvent_t e : {P->ev_start, P->ev_in, P->ev_out, P->ev_t0, P->ev_t1})
+    for (cudaEvent_t e : P->ev_map) cudaEventDestroy(e);
+    for (cudaEvent_t e : {P->ev_start, P->ev_in, P->ev_out, P->ev_t0, P->ev_t1, P->ev_cnn})
         if (e) cudaEventDestroy(e);
     if (P->origin) cudaStreamDestroy(P->origin);
+    if (P->cnn_stream) cudaStreamDestroy(P->cnn_stream);
     cudaFree(P->arena);
+    cudaFree(P->h16[0]);
+    cudaFree(P->h16[1]);
+    cudaFree(P->cmap);
+    cudaFree(P->crows);
     cudaSetDevice(prev);
     delete P;
 }
 
 hts_status create_plan(const Sig &sig, const std::vector<Geom> &geo, const std::vector<hts_params> &par,
-                       Plan **out) {
+                       hts_cnn *net, Plan **out) {
     Plan *P = new Plan();
     P->sig = sig;
     P->geo = geo;
     P->par = par;
+    P->net = net;
     const int n = (int)geo.size();
     std::vector<size_t> off(n + 1, 0);
     for (int i = 0; i < n; ++i) off[i + 1] = off[i] + bufs_bytes(geo[i]);
-    hts_status st = cu(cudaMalloc(reinterpret_cast<void **>(&P->arena), std::max<size_t>(off[n], 256)),
+    hts_status st = cu(dev_malloc(reinterpret_cast<void **>(&P->arena), std::max<size_t>(off[n], 256)),
                        "cudaMalloc(batch arena)");
     int lo = 0, hi = 0;
     if (st == HTS_OK) st = cu(cudaDeviceGetStreamPriorityRange(&lo, &hi), "cudaDeviceGetStreamPriorityRange");
@@ -133,6 +156,24 @@ hts_status create_plan(const Sig &sig, const std::vector<Geom> &geo, const std::
         if (st == HTS_OK) st = cu(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "cudaEventCreate");
     for (cudaEvent_t *e : {&P->ev_t0, &P->ev_t1})
         if (st == HTS_OK) st = cu(cudaEventCreate(e), "cudaEventCreate");
+    if (net && st == HTS_OK) {
+        size_t px = 0, rows = 0;
+        for (const Geom &g : geo) {
+            px = std::max(px, (size_t)g.H * g.W);
+            rows = std::max(rows, (size_t)g.H * g.nx);
+        }
+        st = cu(dev_malloc(&P->h16[0], px * 32 * sizeof(__half)), "cudaMalloc(batch network buffers)");
+        if (st == HTS_OK) st = cu(dev_malloc(&P->h16[1], px * 32 * sizeof(__half)), "cudaMalloc(batch network buffers)");
+        if (st == HTS_OK) st = cu(dev_malloc(&P->cmap, px * sizeof(float)), "cudaMalloc(batch network buffers)");
+        if (st == HTS_OK) st = cu(dev_malloc(&P->crows, rows * sizeof(float)), "cudaMalloc(batch network buffers)");
+        if (st == HTS_OK) st = cu(cudaStreamCreateWithFlags(&P->cnn_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        if (st == HTS_OK) st = cu(cudaEventCreateWithFlags(&P->ev_cnn, cudaEventDisableTiming), "cudaEventCreate");
+        for (int i = 0; i < n && st == HTS_OK; ++i) {
+            cudaEvent_t e = nullptr;
+            st = cu(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+            if (st == HTS_OK) P->ev_map.push_back(e);
+        }
+    }
     if (st != HTS_OK) {
         destroy_plan(P);
         return st;
@@ -171,6 +212,26 @@ Bufs slot(const Plan &P, int i, int l) {
     return b;
 }
 
+// Image i's pipeline on stream s: as hts_denoise, hts_denoise_sigma_map (the caller's map) or
+// hts_denoise_learned (the plan's network map, ready once ev_map[i] has fired).
+hts_status run_image(Plan &P, const hts_image *imgs, int i, const Bufs &b, cudaStream_t s) {
+    if (P.net)
+        return denoise_run(imgs[i].noisy, imgs[i].out, P.geo[i], -1.f, nullptr, P.par[i], b, s, b.sref,
+                           P.sig.factor, nullptr, nullptr, P.ev_map[i]);
+    if (imgs[i].sigma_map)
+        return denoise_run(imgs[i].noisy, imgs[i].out, P.geo[i], -1.f, nullptr, P.par[i], b, s,
+                           const_cast<float *>(imgs[i].sigma_map), 0.0);
+    return denoise_run(imgs[i].noisy, imgs[i].out, P.geo[i], imgs[i].sigma, nullptr, P.par[i], b, s);
+}
+
+// Images in the order their work is dealt to lanes (largest first).
+std::vector<int> work_order(const Plan &P) {
+    std::vector<int> order(P.geo.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return P.work[a] > P.work[b]; });
+    return order;
+}
+
 // Records the whole batch on nl lanes into a new graph.
 hts_status capture(Plan &P, const hts_image *imgs, int nl, cudaGraph_t *out, unsigned long long *kernels) {
     const int n = (int)P.geo.size();
@@ -179,13 +240,22 @@ hts_status capture(Plan &P, const hts_image *imgs, int nl, cudaGraph_t *out, uns
     HTS_TRY(cu(cudaStreamBeginCapture(P.origin, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture"));
     hts_status st = cu(cudaEventRecord(P.ev_start, P.origin), "cudaEventRecord");
     for (int l = 0; l < nl && st == HTS_OK; ++l) st = cu(cudaStreamWaitEvent(P.lanes[l], P.ev_start, 0), "cudaStreamWaitEvent");
-    for (int i = 0; i < n && st == HTS_OK; ++i)
-        st = denoise_run(imgs[i].noisy, imgs[i].out, P.geo[i], imgs[i].sigma, nullptr, P.par[i],
-                         slot(P, i, lane[i]), P.lanes[lane[i]]);
+    if (P.net && st == HTS_OK) {  // the networks' maps, largest image first, into the images' slots
+        st = cu(cudaStreamWaitEvent(P.cnn_stream, P.ev_start, 0), "cudaStreamWaitEvent");
+        for (int i : work_order(P)) {
+            if (st != HTS_OK) break;
+            st = cnn_sigma_refs_into(P.net, imgs[i].noisy, P.geo[i], P.h16[0], P.h16[1], P.cmap, P.crows,
+                                     P.bufs[i].sref, P.cnn_stream);
+            if (st == HTS_OK) st = cu(cudaEventRecord(P.ev_map[i], P.cnn_stream), "cudaEventRecord");
+        }
+        if (st == HTS_OK) st = cu(cudaEventRecord(P.ev_cnn, P.cnn_stream), "cudaEventRecord");
+    }
+    for (int i = 0; i < n && st == HTS_OK; ++i) st = run_image(P, imgs, i, slot(P, i, lane[i]), P.lanes[lane[i]]);
     for (int l = 0; l < nl && st == HTS_OK; ++l) {
         st = cu(cudaEventRecord(P.ev_lane[l], P.lanes[l]), "cudaEventRecord");
         if (st == HTS_OK) st = cu(cudaStreamWaitEvent(P.origin, P.ev_lane[l], 0), "cudaStreamWaitEvent");
     }
+    if (P.net && st == HTS_OK) st = cu(cudaStreamWaitEvent(P.origin, P.ev_cnn, 0), "cudaStreamWaitEvent");
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(P.origin, &g);
     if (st != HTS_OK) {
@@ -292,7 +362,9 @@ hts_status build(Plan &P, const hts_image *imgs) {
 bool same_binding(const Plan &P, const hts_image *imgs) {
     for (size_t i = 0; i < P.bound.size(); ++i) {
         const hts_image &a = P.bound[i], &b = imgs[i];
-        if (a.noisy != b.noisy || a.out != b.out || std::memcmp(&a.sigma, &b.sigma, sizeof(float)) != 0) return false;
+        if (a.noisy != b.noisy || a.out != b.out || a.sigma_map != b.sigma_map ||
+            std::memcmp(&a.sigma, &b.sigma, sizeof(float)) != 0)
+            return false;
     }
     return true;
 }
@@ -336,12 +408,21 @@ void batch_shutdown() {
 
 using namespace hts;
 
-extern "C" hts_status hts_denoise_batch(const hts_image *imgs, int n, const hts_params *p, void *stream) {
+namespace hts {
+namespace {
+
+hts_status batch_impl(const hts_image *imgs, int n, const hts_params *p, hts_cnn *net, double factor,
+                      void *stream) {
     if (n < 0 || (n > 0 && !imgs)) return report(HTS_EINVAL, "bad batch");
     if (!p) return report(HTS_EINVAL, "params is NULL");
     std::vector<Geom> geo(n);
     std::vector<hts_params> par(n);
     Sig sig;
+    if (net) {
+        sig.net = net;
+        sig.window = hts_cnn_window(net);
+        sig.factor = factor;
+    }
     for (int i = 0; i < n; ++i) {
         const hts_params *pi = imgs[i].params ? imgs[i].params : p;
         HTS_TRY(validate(imgs[i].H, imgs[i].W, imgs[i].C, pi, &geo[i]));
@@ -363,7 +444,12 @@ extern "C" hts_status hts_denoise_batch(const hts_image *imgs, int n, const hts_
             return report(HTS_EINVAL, "bad image pointers in batch");
         if (imgs[i].sigma != imgs[i].sigma || imgs[i].sigma == __builtin_inff() || imgs[i].sigma == -__builtin_inff())
             return report(HTS_EINVAL, "sigma must be finite");
-        sig.dims.insert(sig.dims.end(), {imgs[i].H, imgs[i].W, imgs[i].C, imgs[i].sigma < 0 ? 1 : 0});
+        if (net && imgs[i].sigma_map) return report(HTS_EINVAL, "the learned batch takes no caller sigma maps");
+        if (net && hts_cnn_channels(net) != imgs[i].C)
+            return report(HTS_EINVAL, "network built for another channel count");
+        const bool est = net || imgs[i].sigma_map || imgs[i].sigma < 0;
+        sig.dims.insert(sig.dims.end(),
+                        {imgs[i].H, imgs[i].W, imgs[i].C, est ? 1 : 0, imgs[i].sigma_map ? 1 : 0});
     }
     if (n == 0) return HTS_OK;
     HTS_TRY(cu(cudaGetDevice(&sig.device), "cudaGetDevice"));
@@ -384,7 +470,7 @@ extern "C" hts_status hts_denoise_batch(const hts_image *imgs, int n, const hts_
             destroy_plan(lru->second);
             g_plans.erase(lru);
         }
-        HTS_TRY(create_plan(sig, geo, par, &P));
+        HTS_TRY(create_plan(sig, geo, par, net, &P));
         g_plans[sig] = P;
         fresh = true;
     }
@@ -402,6 +488,36 @@ extern "C" hts_status hts_denoise_batch(const hts_image *imgs, int n, const hts_
     return HTS_OK;
 }
 
+}  // namespace
+
+void batch_drop_net(const hts_cnn *net) {
+    std::lock_guard<std::mutex> lk(g_bmu);
+    for (auto it = g_plans.begin(); it != g_plans.end();) {
+        if (it->second->net != net) {
+            ++it;
+            continue;
+        }
+        Plan *P = it->second;
+        for (auto l = g_last.begin(); l != g_last.end();) l = (l->second == P) ? g_last.erase(l) : std::next(l);
+        destroy_plan(P);
+        it = g_plans.erase(it);
+    }
+}
+
+}  // namespace hts
+
+extern "C" hts_status hts_denoise_batch(const hts_image *imgs, int n, const hts_params *p, void *stream) {
+    return batch_impl(imgs, n, p, nullptr, 0.0, stream);
+}
+
+extern "C" hts_status hts_denoise_batch_learned(const hts_image *imgs, int n, hts_cnn *net, double fallback_factor,
+                                                const hts_params *p, void *stream) {
+    if (!net) return report(HTS_EINVAL, "network is NULL");
+    if (!(fallback_factor > 1.0) || !std::isfinite(fallback_factor))
+        return report(HTS_EINVAL, "fallback_factor must be > 1");
+    return batch_impl(imgs, n, p, net, fallback_factor, stream);
+}
+
 extern "C" hts_status hts_last_batch_stats(hts_stats *out, int n, hts_batch_info *info, void *stream) {
     if (n < 0 || (n > 0 && !out)) return report(HTS_EINVAL, "bad arguments");
     int dev = 0;
@@ -412,6 +528,7 @@ extern "C" hts_status hts_last_batch_stats(hts_stats *out, int n, hts_batch_info
     Plan *P = it->second;
     const int m = std::min(n, (int)P->geo.size());
     HTS_TRY(cu(cudaStreamSynchronize(P->origin), "cudaStreamSynchronize"));
+    int err = 0;
     for (int i = 0; i < m; ++i) {
         DevState hs;
         HTS_TRY(cu(cudaMemcpy(&hs, P->bufs[i].st, sizeof(DevState), cudaMemcpyDeviceToHost), "cudaMemcpy"));
@@ -426,6 +543,10 @@ extern "C" hts_status hts_last_batch_stats(hts_stats *out, int n, hts_batch_info
         o.sigma = hs.sigma_hat;
         o.tau = hs.tau;
         o.filter_fixed = hs.filter_fixed;
+        o.learned = hs.learned;
+        o.learned_ratio = hs.learned_ratio;
+        o.device_error = hs.error;
+        if (hs.error != 0 && err != 2) err = hs.error;
     }
     if (info) {
         info->images = (int)P->geo.size();
@@ -434,7 +555,7 @@ extern "C" hts_status hts_last_batch_stats(hts_stats *out, int n, hts_batch_info
         info->captures = P->captures;
         info->updates = P->updates;
     }
-    return HTS_OK;
+    return device_status(err);
 }
 
 extern "C" hts_status hts_tuned_tile(int H, int W, int C, const hts_params *p, int *ty, int *tx) {

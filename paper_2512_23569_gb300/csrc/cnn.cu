@@ -326,9 +326,9 @@ hts_status ensure_ws(hts_cnn *n, int H, int W) {
         n->d0 = n->d1 = nullptr;
         n->cap_px = 0;
         for (int l = 0; l < DEPTH; ++l)
-            HTS_TRY(cu(cudaMalloc(&n->act[l], px * (l < DEPTH - 1 ? WID : 1) * sizeof(float)), "cudaMalloc(cnn)"));
-        HTS_TRY(cu(cudaMalloc(&n->d0, px * WID * sizeof(float)), "cudaMalloc(cnn)"));
-        HTS_TRY(cu(cudaMalloc(&n->d1, px * WID * sizeof(float)), "cudaMalloc(cnn)"));
+            HTS_TRY(cu(dev_malloc(&n->act[l], px * (l < DEPTH - 1 ? WID : 1) * sizeof(float)), "cudaMalloc(cnn)"));
+        HTS_TRY(cu(dev_malloc(&n->d0, px * WID * sizeof(float)), "cudaMalloc(cnn)"));
+        HTS_TRY(cu(dev_malloc(&n->d1, px * WID * sizeof(float)), "cudaMalloc(cnn)"));
         n->cap_px = px;
     }
     const size_t ntiles = ((size_t)(H + TS - 1) / TS) * ((W + TS - 1) / TS);
@@ -337,7 +337,7 @@ hts_status ensure_ws(hts_cnn *n, int H, int W) {
         cudaFree(n->part);
         n->part = nullptr;
         n->cap_part = 0;
-        HTS_TRY(cu(cudaMalloc(&n->part, need * sizeof(float)), "cudaMalloc(cnn)"));
+        HTS_TRY(cu(dev_malloc(&n->part, need * sizeof(float)), "cudaMalloc(cnn)"));
         n->cap_part = need;
     }
     return HTS_OK;
@@ -467,13 +467,18 @@ hts_status cnn_sigma_refs(hts_cnn *n, const float *img, const Geom &g, float *si
     HTS_TRY(check_net(n, img, g.H, g.W));
     if (n->C != g.C) return report(HTS_EINVAL, "network built for another channel count");
     HTS_TRY(cnn_ensure_infer(n, g.H, g.W, g.nx));
-    HTS_TRY(cnn_forward_tc(n, img, g.H, g.W, s));
-    float *rows = n->rows;  // H x nx row sums
-    const size_t nrow = (size_t)g.H * g.nx;
+    return cnn_sigma_refs_into(n, img, g, n->h16[0], n->h16[1], n->map, n->rows, sigma_ref, s);
+}
+
+hts_status cnn_sigma_refs_into(hts_cnn *n, const float *img, const Geom &g, __half *h0, __half *h1, float *map,
+                               float *rows, float *sigma_ref, cudaStream_t s) {
+    if (n->C != g.C) return report(HTS_EINVAL, "network built for another channel count");
+    HTS_TRY(cnn_forward_tc_into(n, img, g.H, g.W, h0, h1, map, s));
+    const size_t nrow = (size_t)g.H * g.nx;  // rows: H x nx row sums
     {
         KTimer kt("k_window_rows", s);
         k_window_rows<<<(unsigned)std::min<size_t>((nrow + 255) / 256, 152 * 16), 256, 0, s>>>(
-            n->map, g.H, g.W, g.step, g.nx, n->window, rows);
+            map, g.H, g.W, g.step, g.nx, n->window, rows);
     }
     HTS_TRY(check_launch("k_window_rows"));
     {
@@ -516,11 +521,11 @@ extern "C" hts_status hts_cnn_create(int C, uint64_t seed, hts_cnn **out) {
     hts_status st = cu(cudaGetDevice(&n->device), "cudaGetDevice");
     const size_t b = n->nparams * sizeof(float);
     for (float **p : {&n->master, &n->grad, &n->m, &n->v})
-        if (st == HTS_OK) st = cu(cudaMalloc(p, b), "cudaMalloc(cnn)");
-    if (st == HTS_OK) st = cu(cudaMalloc(&n->w16, n->nparams * sizeof(__half)), "cudaMalloc(cnn)");
-    if (st == HTS_OK) st = cu(cudaMalloc(&n->loss, sizeof(double)), "cudaMalloc(cnn)");
+        if (st == HTS_OK) st = cu(dev_malloc(p, b), "cudaMalloc(cnn)");
+    if (st == HTS_OK) st = cu(dev_malloc(&n->w16, n->nparams * sizeof(__half)), "cudaMalloc(cnn)");
+    if (st == HTS_OK) st = cu(dev_malloc(&n->loss, sizeof(double)), "cudaMalloc(cnn)");
     if (st == HTS_OK) st = cu(cudaMemset(n->loss, 0, sizeof(double)), "cudaMemset");
-    if (st == HTS_OK) st = cu(cudaMalloc(&n->err, sizeof(int)), "cudaMalloc(cnn)");
+    if (st == HTS_OK) st = cu(dev_malloc(&n->err, sizeof(int)), "cudaMalloc(cnn)");
     if (st == HTS_OK) st = cu(cudaMemset(n->err, 0, sizeof(int)), "cudaMemset");
     if (st != HTS_OK) {
         free_net(n);
@@ -549,6 +554,7 @@ extern "C" hts_status hts_cnn_create(int C, uint64_t seed, hts_cnn **out) {
 }
 
 extern "C" hts_status hts_cnn_free(hts_cnn *net) {
+    if (net) batch_drop_net(net);
     free_net(net);
     return HTS_OK;
 }

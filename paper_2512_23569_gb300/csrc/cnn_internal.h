@@ -36,5 +36,14 @@ namespace hts {
 // cnn_ensure_infer sizes net->h16, net->map and net->rows first.
 hts_status cnn_forward_tc(hts_cnn *net, const float *img, int H, int W, cudaStream_t s);
 hts_status cnn_ensure_infer(hts_cnn *net, int H, int W, int nx);
+// The same forward into caller-owned buffers: h0, h1 (H * W * 32 halves each)
+// and map (H * W floats); only the weights and the error flag are the net's.
+hts_status cnn_forward_tc_into(hts_cnn *net, const float *img, int H, int W, __half *h0, __half *h1, float *map,
+                               cudaStream_t s);
+struct Geom;
+// Noise level of every reference patch (sigma_ref, device, N_ref) through the
+// readout window, from a forward into caller-owned buffers (rows: H * nx floats).
+hts_status cnn_sigma_refs_into(hts_cnn *net, const float *img, const Geom &g, __half *h0, __half *h1, float *map,
+                               float *rows, float *sigma_ref, cudaStream_t s);
 
 }  // namespace hts

@@ -218,7 +218,7 @@ hts_status grow_buf(T *&p, size_t &cap, size_t need) {
     cudaFree(p);
     p = nullptr;
     cap = 0;
-    if (cudaMalloc(&p, need * sizeof(T)) != cudaSuccess) {
+    if (dev_malloc(&p, need * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         return report(HTS_ENOMEM, "cudaMalloc(cnn inference buffers)");
     }
@@ -242,6 +242,11 @@ hts_status cnn_ensure_infer(hts_cnn *n, int H, int W, int nx) {
 }
 
 hts_status cnn_forward_tc(hts_cnn *n, const float *img, int H, int W, cudaStream_t s) {
+    return cnn_forward_tc_into(n, img, H, W, n->h16[0], n->h16[1], n->map, s);
+}
+
+hts_status cnn_forward_tc_into(hts_cnn *n, const float *img, int H, int W, __half *h0, __half *h1, float *map,
+                               cudaStream_t s) {
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -249,12 +254,11 @@ hts_status cnn_forward_tc(hts_cnn *n, const float *img, int H, int W, cudaStream
         cudaGetLastError();
         return report(HTS_ECUDA, "cudaMemsetAsync(cnn error flag)");
     }
-    float *map = n->map;
-    hts_status st = conv_tc<2, 32, true, false>(n, 0, img, nullptr, H, W, n->h16[0], nullptr, nsm, s);
-    if (st == HTS_OK) st = conv_tc<4, 32, false, false>(n, 1, nullptr, n->h16[0], H, W, n->h16[1], nullptr, nsm, s);
-    if (st == HTS_OK) st = conv_tc<4, 32, false, false>(n, 2, nullptr, n->h16[1], H, W, n->h16[0], nullptr, nsm, s);
-    if (st == HTS_OK) st = conv_tc<4, 32, false, false>(n, 3, nullptr, n->h16[0], H, W, n->h16[1], nullptr, nsm, s);
-    if (st == HTS_OK) st = conv_tc<4, 16, false, true>(n, 4, nullptr, n->h16[1], H, W, nullptr, map, nsm, s);
+    hts_status st = conv_tc<2, 32, true, false>(n, 0, img, nullptr, H, W, h0, nullptr, nsm, s);
+    if (st == HTS_OK) st = conv_tc<4, 32, false, false>(n, 1, nullptr, h0, H, W, h1, nullptr, nsm, s);
+    if (st == HTS_OK) st = conv_tc<4, 32, false, false>(n, 2, nullptr, h1, H, W, h0, nullptr, nsm, s);
+    if (st == HTS_OK) st = conv_tc<4, 32, false, false>(n, 3, nullptr, h0, H, W, h1, nullptr, nsm, s);
+    if (st == HTS_OK) st = conv_tc<4, 16, false, true>(n, 4, nullptr, h1, H, W, nullptr, map, nsm, s);
     if (st != HTS_OK) return st;
     {
         KTimer kt("k_map_poison", s);

@@ -420,11 +420,11 @@ hts_status ensure(hts_fcn *f, size_t n) {
         cudaFree(f->d1);
         f->X = f->d0 = f->d1 = nullptr;
         f->cap = 0;
-        HTS_TRY(cu(cudaMalloc(&f->X, n * f->din * sizeof(float)), "cudaMalloc(fcn)"));
-        for (int l = 0; l < NL; ++l) HTS_TRY(cu(cudaMalloc(&f->act[l], n * f->nout[l] * sizeof(float)), "cudaMalloc(fcn)"));
+        HTS_TRY(cu(dev_malloc(&f->X, n * f->din * sizeof(float)), "cudaMalloc(fcn)"));
+        for (int l = 0; l < NL; ++l) HTS_TRY(cu(dev_malloc(&f->act[l], n * f->nout[l] * sizeof(float)), "cudaMalloc(fcn)"));
         const size_t wd = std::max(HID, f->dout);
-        HTS_TRY(cu(cudaMalloc(&f->d0, n * wd * sizeof(float)), "cudaMalloc(fcn)"));
-        HTS_TRY(cu(cudaMalloc(&f->d1, n * wd * sizeof(float)), "cudaMalloc(fcn)"));
+        HTS_TRY(cu(dev_malloc(&f->d0, n * wd * sizeof(float)), "cudaMalloc(fcn)"));
+        HTS_TRY(cu(dev_malloc(&f->d1, n * wd * sizeof(float)), "cudaMalloc(fcn)"));
         f->cap = n;
     }
     return HTS_OK;
@@ -459,7 +459,7 @@ hts_status gemm_acc(hts_fcn *f, const float *A, long am, long ak, const float *B
         cudaFree(f->part);
         f->part = nullptr;
         f->cap_part = 0;
-        HTS_TRY(cu(cudaMalloc(&f->part, need * sizeof(float)), "cudaMalloc(fcn)"));
+        HTS_TRY(cu(dev_malloc(&f->part, need * sizeof(float)), "cudaMalloc(fcn)"));
         f->cap_part = need;
     }
     dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, nz);
@@ -597,11 +597,11 @@ extern "C" hts_status hts_fcn_create(int C, int K, uint64_t seed, hts_fcn **out)
     layout(f);
     hts_status st = cu(cudaGetDevice(&f->device), "cudaGetDevice");
     for (float **p : {&f->w, &f->grad, &f->m, &f->v})
-        if (st == HTS_OK) st = cu(cudaMalloc(p, f->nparams * sizeof(float)), "cudaMalloc(fcn)");
-    if (st == HTS_OK) st = cu(cudaMalloc(&f->loss, sizeof(double)), "cudaMalloc(fcn)");
+        if (st == HTS_OK) st = cu(dev_malloc(p, f->nparams * sizeof(float)), "cudaMalloc(fcn)");
+    if (st == HTS_OK) st = cu(dev_malloc(&f->loss, sizeof(double)), "cudaMalloc(fcn)");
     if (st == HTS_OK) st = cu(cudaMemset(f->loss, 0, sizeof(double)), "cudaMemset");
-    if (st == HTS_OK) st = cu(cudaMalloc(&f->lpart, LOSS_BLOCKS * sizeof(double)), "cudaMalloc(fcn)");
-    if (st == HTS_OK) st = cu(cudaMalloc(&f->sig, sizeof(float)), "cudaMalloc(fcn)");
+    if (st == HTS_OK) st = cu(dev_malloc(&f->lpart, LOSS_BLOCKS * sizeof(double)), "cudaMalloc(fcn)");
+    if (st == HTS_OK) st = cu(dev_malloc(&f->sig, sizeof(float)), "cudaMalloc(fcn)");
     if (st != HTS_OK) {
         free_fcn(f);
         return st;

@@ -72,6 +72,9 @@ __host__ __device__ __forceinline__ int grid_pos(int i, int n, int step) {
 // Argument checks and error reporting shared by the entry points (api.cu).
 hts_status validate(int H, int W, int C, const hts_params *p, Geom *g);
 hts_status report(hts_status s, const char *msg);
+// HTS_OK for DevState.error == 0, else the status of the failure it records
+// (2: HTS_ETIMEOUT, a bounded wait gave up; 1: HTS_EINTERNAL).
+hts_status device_status(int err);
 
 // Launch bookkeeping (defined in api.cu).  Every kernel launch sits inside a
 // KTimer scope: it counts the launch and, while profiling is on, records a
@@ -83,6 +86,20 @@ hts_status check_launch(const char *what);
 // reset (a captured launch is counted when its graph is launched).
 unsigned long long captured_launches();
 void reset_captured_launches();
+
+// Host-side fault injection (test support, include/hts.h: hts_fault_inject).
+// fault_take(k) is true for exactly the event of kind k that the armed
+// countdown names (and disarms it); false otherwise.
+enum FaultKind { FAULT_ALLOC = 0, FAULT_LAUNCH = 1, FAULT_WAIT = 2, FAULT_KINDS = 3 };
+bool fault_take(FaultKind k);
+// cudaMalloc through the allocation fault point.
+cudaError_t dev_malloc_bytes(void **p, size_t bytes);
+template <typename T>
+inline cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc_bytes(reinterpret_cast<void **>(p), bytes);
+}
+// True while `s` is capturing into a CUDA graph.
+bool stream_capturing(cudaStream_t s);
 
 // Largest shared memory a block may opt in to on the current device.
 int smem_optin();
@@ -190,6 +207,7 @@ struct Bufs {
     float *b32 = nullptr;
     double *eig = nullptr;
     DevState *st = nullptr;
+    float *sref = nullptr;  // a noise level per reference patch (batched learned form)
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
@@ -208,9 +226,13 @@ void batch_shutdown();
 // patch; with a fallback factor > 0 it is checked against the estimated
 // level (launch_learned_check) and the estimate is used if it fails.
 // fcn (may be nullptr) with ra_buf (2 N_ref C 64 floats): the enhancement strategy.
+// map_ready (may be nullptr): an event s waits for before the first use of sigma_ref.
 hts_status denoise_run(const float *noisy, float *out, const Geom &g, float sigma, const hts_basis *basis,
                        const hts_params &p, const Bufs &b, cudaStream_t s, float *sigma_ref = nullptr,
-                       double fallback_factor = 0.0, hts_fcn *fcn = nullptr, float *ra_buf = nullptr);
+                       double fallback_factor = 0.0, hts_fcn *fcn = nullptr, float *ra_buf = nullptr,
+                       cudaEvent_t map_ready = nullptr);
+// Destroys the batch plans that use this network (batch.cu; hts_cnn_free calls it).
+void batch_drop_net(const hts_cnn *net);
 
 }  // namespace hts
 

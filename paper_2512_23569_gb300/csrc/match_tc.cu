@@ -47,7 +47,10 @@
 //
 // Every mbarrier wait is bounded; a wait that gives up records error code 2
 // in the call's state, and the block waits (bounded) for the MMAs it has
-// issued, releases its tensor memory and leaves.
+// issued, gives the references of its item and of every item left in the
+// queue their own position as their whole group (valid positions for the
+// kernels that read the groups; the call reports HTS_ETIMEOUT where it reads
+// the state back), releases its tensor memory and leaves.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -66,6 +69,7 @@ constexpr int RUNC = NQ * CH;     // tensor-memory columns per run
 constexpr int NBUF = 2;           // accumulators
 constexpr uint32_t TMEM_COLS = NBUF * RUNC;
 constexpr long long SPIN = 1ll << 24;
+constexpr long long INJECT_SPIN = 1ll << 12;  // polls of the injected wait (hts_fault_inject "wait")
 constexpr unsigned FULLM = 0xffffffffu;
 constexpr int NWC = 8;               // reading warps: warp w takes lanes 32 (w % 4) .. + 31, columns 32 (w / 4) ..
 constexpr int NT = (NWC + 1) * 32;   // + one warp that issues the MMAs
@@ -79,6 +83,7 @@ struct TcArgs {
     DevState *st;
     int ntx, nty, ntiles;
     int hc_max, wc_max;  // bounds of the candidate region over all tiles
+    int inject_wait;     // 1: the issuing thread first waits, briefly, on a barrier nothing arrives on
 };
 
 // LH: keys each thread keeps and the number re-ranked in FP32 per reference;
@@ -125,7 +130,7 @@ __host__ __device__ inline TcLayout tc_layout(int hc_max, int wc_max) {
     L.ref = up(L.scr + nq * 4, 16);
     L.qr = L.ref + (size_t)NR * sizeof(RefRec);
     L.bar = up(L.qr + NQ * sizeof(int2), 16);
-    L.total = L.bar + 2 * NBUF * 8 + 16;
+    L.total = L.bar + (2 * NBUF + 1) * 8 + 16;
     // one block per SM, and never beside a block of the other tensor-core kernels (whose tensor
     // memory would not fit beside this block's 512 columns)
     if (L.total < 160 * 1024) L.total = 160 * 1024;
@@ -164,6 +169,15 @@ __device__ __forceinline__ int pick_pitch(int Wc, int lane) {
     return Wc + 7 - (int)(key & 7u);
 }
 
+// Group of reference r made of its own position `self` only (the failure path: valid positions for the
+// kernels that read the groups).
+template <int K>
+__device__ __forceinline__ void self_group(const TcArgs &a, int r, int self) {
+    int32_t *out = a.idx + (size_t)r * K;
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = self;
+}
+
 template <int K>
 __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
     constexpr int LH = ListCfg<K>::LH, T = ListCfg<K>::T, KC = ListCfg<K>::KC, NBIN = ListCfg<K>::NBIN;
@@ -181,7 +195,8 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
     int2 *qr = reinterpret_cast<int2 *>(smem_raw + L.qr);  // per quarter: first candidate, count
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + L.bar);  // [NBUF]: the run's MMAs completed
     uint64_t *empty = full + NBUF;                                    // [NBUF]: every warp loaded the run
-    int *abort_flag = reinterpret_cast<int *>(empty + NBUF);
+    uint64_t *never = empty + NBUF;  // no thread arrives on it (the injected wait)
+    int *abort_flag = reinterpret_cast<int *>(never + 1);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(abort_flag + 1);
     int *item_slot = reinterpret_cast<int *>(tmem_slot + 1);  // the block's current work item
 
@@ -195,6 +210,7 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
             tc::bar_init(&full[b], 1);
             tc::bar_init(&empty[b], NWC);
         }
+        tc::bar_init(never, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -208,7 +224,7 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
     bool ok = true;
 
     const int npass = (a.C == 3) ? 2 : 1;
-    while (ok) {
+    while (true) {
         // next item of the work queue: (tile, plane pass), so that the two passes of a colour tile run
         // on two SMs and blocks that drew passes without references move on at once
         if (tid == 0) *item_slot = atomicAdd(&a.st->mtc_next, 1);
@@ -264,6 +280,18 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
                 }
             }
             if (!__syncthreads_or(any)) continue;
+            // the failure path: the references of this item and of every item left in the queue get the
+            // group of the reference alone, so that the kernels after this one read valid positions only
+            auto self_groups = [&]() {
+                if (tid < NR && rec[tid].mine) {
+                    const int py = rec[tid].pself / Wq, px = rec[tid].pself - py * Wq;
+                    self_group<K>(a, (gy0 + (tid >> 3)) * a.nx + gx0 + (tid & 7), (cy0 + py) * a.W + cx0 + px);
+                }
+            };
+            if (!ok) {
+                self_groups();
+                continue;
+            }
             // ---- stage the plane (FP32), the row-8 vectors and their norms, E, A
 #pragma unroll 4
             for (int e = tid; e < (Hc + 7) * PSW; e += NT) {
@@ -352,7 +380,11 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
             if (!cw) {  // the issuing warp: run c goes into its accumulator once run c - NBUF was loaded by all
                 if (lane == 0) {
                     int issued = 0;
-                    for (int c = 0; c < nrun; ++c) {
+                    // fault injection: before issuing anything the thread waits on a barrier nothing
+                    // arrives on; the bounded wait gives up and sets the abort flag (no MMA in flight)
+                    const bool injected =
+                        a.inject_wait && g0 == 0 && !tc::bar_wait_or_abort(never, 0u, INJECT_SPIN, abortp);
+                    for (int c = 0; c < nrun && !injected; ++c) {
                         const long long g = g0 + c;
                         const uint32_t b = (uint32_t)(g % NBUF);
                         if (g >= NBUF &&
@@ -433,7 +465,8 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
             if (*abortp) {
                 if (tid == 0) atomicExch(&a.st->error, 2);
                 ok = false;
-                break;
+                self_groups();
+                continue;
             }
             gc = g0 + nrun;
 
@@ -576,6 +609,7 @@ hts_status launch_match_tc(const float *img, const Geom &g, double gamma_gcp, in
     a.ntiles = a.nty * a.ntx;
     a.hc_max = std::min(g.H - PS + 1, (TTY - 1) * g.step + 1 + 2 * g.R);
     a.wc_max = std::min(g.W - PS + 1, (TTX - 1) * g.step + 1 + 2 * g.R);
+    a.inject_wait = (!stream_capturing(s) && fault_take(FAULT_WAIT)) ? 1 : 0;
     hts_status st0 = HTS_EUNSUPPORTED;
     switch (g.K) {
         case 2: st0 = launch_tc<2>(a, s); break;

@@ -6,8 +6,13 @@
 // not acceptable.  All intermediate buffers of the call live in one static
 // device array of this file, sized for images of at most 512 x 512 pixels
 // (any channel count the library supports), at most 65536 reference patches
-// and at most 2^20 group slots (N_ref * K).  Every GPU that loads the library
-// holds this array (about 21 MB) until the process exits.
+// and at most 2^20 group slots (N_ref * K).  A GPU holds this array (about
+// 21 MB) from the first call on it (with CUDA's lazy module loading the
+// library's module, and the array with it, may be loaded only then) until the
+// process exits.  The basis and noise-floor chain runs in series with the
+// grouping on the caller's stream (hts_denoise overlaps them on a second
+// stream), so a call takes somewhat longer; the result equals hts_denoise's
+// up to 1e-3 on the [0, 255] scale (the same kernels run).
 #include <mutex>
 
 #include "hts_internal.h"
@@ -53,7 +58,9 @@ std::mutex g_na_mu;
 unsigned char *g_na_base[NA_MAX_DEVICES] = {nullptr};
 
 // Device address of the scratch on the current device (looked up on the
-// first call on that device).
+// first call on that device and kept: after a reset of the device, e.g.
+// cudaDeviceReset, the kept address is stale and the entry point must not be
+// called again in this process).
 hts_status scratch_base(unsigned char **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return report(HTS_ECUDA, "cudaGetDevice failed");
@@ -126,7 +133,7 @@ extern "C" hts_status hts_denoise_noalloc(const float *noisy, float *out, int H,
     st = launch_grouping(noisy, g, *p, idx, green, fb, ds, s);
     if (st != HTS_OK) return st;
     if (sigma < 0) st = launch_sigma(noisy, g, *p, ueig, idx, redo, ds, s);
-    else st = launch_set_sigma((double)sigma, g, *p, ds, s);
+    else st = launch_set_sigma(sigma > 0 ? (double)sigma : 0.0, g, *p, ds, s);
     if (st != HTS_OK) return st;
     return launch_filter(noisy, g, idx, ub64, ub32, acc, wcount, redo, xlist, xskip, ds, out,
                          p->precision == 0 ? 1 : 0, nullptr, 0, tau_scale(g, *p), s);

@@ -36,7 +36,7 @@ EXPORTS = [
     "hts_fcn_num_params", "hts_fcn_channels", "hts_fcn_create", "hts_fcn_free", "hts_fcn_get_params",
     "hts_fcn_set_params", "hts_group_means", "hts_fcn_refine", "hts_fcn_zero_grad", "hts_fcn_accumulate_grad",
     "hts_fcn_take_loss", "hts_fcn_get_grad", "hts_fcn_adam_step", "hts_denoise_ra", "hts_mean_coefs",
-    "hts_fcn_group_size",
+    "hts_fcn_group_size", "hts_fault_inject", "hts_denoise_batch_learned",
 ]
 
 
@@ -64,7 +64,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("nref", ctypes.c_int), ("match_reranked", ctypes.c_int), ("match_fallback", ctypes.c_int),
                 ("filter_redo", ctypes.c_int), ("filter_exact", ctypes.c_int), ("vote_uncertain", ctypes.c_int),
                 ("sigma", ctypes.c_double), ("tau", ctypes.c_double), ("filter_fixed", ctypes.c_int),
-                ("learned", ctypes.c_int), ("learned_ratio", ctypes.c_double)]
+                ("learned", ctypes.c_int), ("learned_ratio", ctypes.c_double), ("device_error", ctypes.c_int)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -78,7 +78,8 @@ class KernelTime(ctypes.Structure):
 
 class Image(ctypes.Structure):
     _fields_ = [("noisy", ctypes.c_void_p), ("out", ctypes.c_void_p), ("H", ctypes.c_int), ("W", ctypes.c_int),
-                ("C", ctypes.c_int), ("sigma", ctypes.c_float), ("params", ctypes.c_void_p)]
+                ("C", ctypes.c_int), ("sigma", ctypes.c_float), ("params", ctypes.c_void_p),
+                ("sigma_map", ctypes.c_void_p)]
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -104,6 +105,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.hts_denoise_host.argtypes = [P, P, I, I, I, F, P, PP, P]
         lib.hts_denoise_noalloc.argtypes = [P, P, I, I, I, F, P, PP, P]
         lib.hts_denoise_batch.argtypes = [ctypes.POINTER(Image), I, PP, P]
+        lib.hts_denoise_batch_learned.argtypes = [ctypes.POINTER(Image), I, P, D, PP, P]
         lib.hts_last_batch_stats.argtypes = [ctypes.POINTER(Stats), I, ctypes.POINTER(BatchInfo), P]
         lib.hts_tuned_tile.argtypes = [I, I, I, PP, ctypes.POINTER(I), ctypes.POINTER(I)]
         lib.hts_match.argtypes = [P, I, I, I, PP, P, P, P]
@@ -155,6 +157,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.hts_fcn_adam_step.argtypes = [P, F, P]
         lib.hts_denoise_ra.argtypes = [P, P, I, I, I, F, P, P, PP, P]
         lib.hts_mean_coefs.argtypes = [P, I, I, P, I, P, P]
+        lib.hts_fault_inject.argtypes = [ctypes.c_char_p]
         for name in EXPORTS:  # fail loudly on a library that lacks a declared entry point
             getattr(lib, name)
         _LIB = lib
@@ -609,24 +612,42 @@ def denoise_host(noisy: np.ndarray, sigma: float | None = None, basis: Basis | N
     return out
 
 
-def denoise_batch(noisy: list, sigmas: list, p: Params | None = None, outs: list | None = None, stream=None,
-                  per_image: list | None = None):
-    """One graph launch over CUDA CHW tensors; sigma None -> estimated; per_image: Params or None each."""
+def _batch_images(noisy, sigmas, outs, per_image, sigma_maps):
     import torch
 
-    p = p or params()
     imgs = (Image * max(1, len(noisy)))()
     outs = outs or [torch.empty_like(_chw(x)) for x in noisy]
-    keep = []  # per-image parameter structs stay alive through the call
     for i, (x, s) in enumerate(zip(noisy, sigmas)):
         x = _chw(x)
         C, H, W = x.shape
         pi = per_image[i] if per_image else None
-        if pi is not None:
-            keep.append(pi)
+        m = sigma_maps[i] if sigma_maps else None
+        if m is not None:
+            _cuda_f32(m, "sigma_map")
+            if m.numel() != num_refs(H, W, pi or params()):
+                raise ValueError("sigma_map: expected N_ref values")
         imgs[i] = Image(x.data_ptr(), outs[i].data_ptr(), H, W, C, -1.0 if s is None else float(s),
-                        ctypes.addressof(pi) if pi is not None else None)
+                        ctypes.addressof(pi) if pi is not None else None, m.data_ptr() if m is not None else None)
+    return imgs, outs
+
+
+def denoise_batch(noisy: list, sigmas: list, p: Params | None = None, outs: list | None = None, stream=None,
+                  per_image: list | None = None, sigma_maps: list | None = None):
+    """One graph launch over CUDA CHW tensors; sigma None -> estimated; per_image: Params or None each;
+    sigma_maps: None, or per image None or a CUDA float32 tensor of N_ref noise levels."""
+    p = p or params()
+    imgs, outs = _batch_images(noisy, sigmas, outs, per_image, sigma_maps)  # per_image structs stay alive here
     _check(load().hts_denoise_batch(imgs, len(noisy), ctypes.byref(p), _stream(stream)))
+    return outs
+
+
+def denoise_batch_learned(noisy: list, net: "Cnn", p: Params | None = None, fallback_factor: float = 2.0,
+                          outs: list | None = None, stream=None, per_image: list | None = None):
+    """hts_denoise_batch_learned: one graph launch in which the network maps every image's noise level."""
+    p = p or params()
+    imgs, outs = _batch_images(noisy, [None] * len(noisy), outs, per_image, None)
+    _check(load().hts_denoise_batch_learned(imgs, len(noisy), net.handle, float(fallback_factor), ctypes.byref(p),
+                                            _stream(stream)))
     return outs
 
 
@@ -648,9 +669,16 @@ def tuned_tile(H: int, W: int, C: int, p: Params | None = None):
 
 
 def last_stats(stream=None) -> dict:
+    """Counters of the last call on the stream; raises HtsError (HTS_ETIMEOUT / HTS_EINTERNAL) if a kernel of
+    that call recorded a failure."""
     st = Stats()
     _check(load().hts_last_stats(ctypes.byref(st), _stream(stream)))
     return {f: getattr(st, f) for f, _ in Stats._fields_}
+
+
+def fault_inject(spec: str | None) -> None:
+    """hts_fault_inject: arm one-shot host-side failures ("alloc:N", "launch:N", "wait:N"; None disarms)."""
+    _check(load().hts_fault_inject(None if spec is None else spec.encode()))
 
 
 def launch_count() -> int:

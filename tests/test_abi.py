@@ -112,3 +112,16 @@ def test_product_path_has_no_oracle_and_no_fallback():
             if f.endswith((".py", ".cu", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in src.replace("the oracle", "").lower() or f == "synth.py", f
+
+
+def test_fault_spec_parsing(lib):
+    # host-side fault injection: well-formed specs arm (and "" disarms); malformed ones are refused
+    for spec in (b"alloc:1", b"launch:3,wait:2", b"alloc:2|launch:1", b"", None):
+        assert lib.hts_fault_inject(spec) == 0, spec
+    for spec in (b"alloc", b"alloc:0", b"alloc:-1", b"boom:1", b"launch:x", b"wait:1,", b"wait:99999999999999"):
+        st = lib.hts_fault_inject(spec)
+        if spec == b"wait:1,":  # a trailing separator is allowed
+            assert st == 0
+        else:
+            assert st == 1, spec  # HTS_EINVAL
+    assert lib.hts_fault_inject(None) == 0

@@ -149,3 +149,70 @@ def test_batch_tensor_core_forms_equal_single_calls(hts, precision):
     outs = hts.denoise_batch(xs, sig, hts.params(), per_image=per)
     for x, s, pi, o in zip(xs, sig, per, outs):
         np.testing.assert_array_equal(hts.denoise(x, sigma=s, p=pi).cpu().numpy(), o.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_sigma_maps_equal_single_calls(oracle, hts, precision):
+    # a caller's noise level per reference patch (hts_image.sigma_map) in the graph: per image equal to
+    # hts_denoise_sigma_map bit for bit, mixed with images that have none; against the oracle fed the
+    # same levels (plain form: <= 1e-3 max-abs)
+    pg, pc = hts.params(win=11, K=8, precision=precision), hts.params(win=15, precision=precision)
+    imgs = _images()
+    xs = [_dev(n) for _, n, _ in imgs]
+    sig = [s for _, _, s in imgs]
+    per = [pg if C == 1 else pc for (_, _, C, _, _) in BATCH]
+    rng = np.random.default_rng(77)
+    maps = []
+    for i, ((H, W, C, _, _), pi) in enumerate(zip(BATCH, per)):
+        if i % 3 == 1:
+            maps.append(None)
+            continue
+        n = hts.num_refs(H, W, pi)
+        maps.append(_dev(rng.uniform(8.0, 40.0, size=n)))
+    outs = hts.denoise_batch(xs, sig, hts.params(), per_image=per, sigma_maps=maps)
+    for x, s, pi, m, o in zip(xs, sig, per, maps, outs):
+        want = (hts.denoise(x, sigma=s, p=pi) if m is None else hts.denoise_sigma_map(x, m, p=pi)).cpu().numpy()
+        np.testing.assert_array_equal(want, o.cpu().numpy())
+    if precision == 0:
+        for (clean, noisy, s), (H, W, C, _, _), m, o in zip(imgs, BATCH, maps, outs):
+            if m is None:
+                continue
+            po = oracle.Params(win=11, K=8) if C == 1 else oracle.Params(win=15)
+            basis = hts.estimate_basis(_dev(noisy), hts.params(win=11, K=8) if C == 1 else hts.params(win=15))
+            b, _ = basis.read()
+            want, _ = oracle.denoise(noisy, po, sigma=m.cpu().numpy().astype(np.float64), basis=b)
+            got = o.cpu().numpy().astype(np.float64)
+            assert np.max(np.abs(got - want)) <= 1e-3
+
+
+def test_batch_learned_equals_single_calls(hts):
+    # the network's maps inside the graph launch (its forwards on a stream of their own): per image equal
+    # to hts_denoise_learned bit for bit, the fallback decisions included; training between calls is seen
+    imgs = [(c, n, s) for (c, n, s), (_, _, C, _, _) in zip(_images(), BATCH) if C == 3]
+    xs = [_dev(n) for _, n, _ in imgs]
+    net = hts.Cnn(3, seed=5)
+    net.window = 16
+    for prec in (1, 2):
+        p = hts.params(win=15, precision=prec)
+        for factor in (2.0, 50.0):  # 2: the untrained map may be judged off and fall back; 50: used
+            outs = hts.denoise_batch_learned(xs, net, p, fallback_factor=factor)
+            per, _ = hts.last_batch_stats(len(xs))
+            for x, o, st in zip(xs, outs, per):
+                want = hts.denoise_learned(x, net, p, fallback_factor=factor).cpu().numpy()
+                single = hts.last_stats()
+                np.testing.assert_array_equal(want, o.cpu().numpy())
+                assert st["learned"] == single["learned"]
+                assert st["learned_ratio"] == pytest.approx(single["learned_ratio"], rel=1e-12)
+            if factor == 50.0:
+                assert all(st["learned"] == 1 for st in per)
+    # new weights: the same plan reads them at its next launch
+    theta = net.get_params()
+    theta[-1] += 0.5  # the output bias: log sigma + 0.5 everywhere
+    net.set_params(theta)
+    p = hts.params(win=15, precision=1)
+    outs = hts.denoise_batch_learned(xs, net, p, fallback_factor=50.0)
+    for x, o in zip(xs, outs):
+        np.testing.assert_array_equal(hts.denoise_learned(x, net, p, fallback_factor=50.0).cpu().numpy(),
+                                      o.cpu().numpy())
+    with pytest.raises(hts.HtsError):  # a gray image with a colour network
+        hts.denoise_batch_learned([_dev(_images()[0][1])], net, p)

@@ -32,31 +32,48 @@ def hts():
     return h
 
 
-def _noalloc(hts, x, sigma, p):
+def _noalloc(hts, x, sigma, p, basis=None):
     lib = hts.load()
     out = torch.empty_like(x)
     C, H, W = x.shape
     s = -1.0 if sigma is None else float(sigma)
     r = lib.hts_denoise_noalloc(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), H, W, C,
-                                ctypes.c_float(s), None, ctypes.byref(p),
+                                ctypes.c_float(s), basis.handle if basis else None, ctypes.byref(p),
                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert r == 0, lib.hts_last_error()
     return out
 
 
-def test_noalloc_matches_denoise_on_two_calls_in_a_row(hts):
-    cases = [
-        ((96, 112, 3), 40.0, None, dict(win=21)),   # colour, sigma and basis estimated
-        ((128, 128, 1), 25.0, 25.0, dict(win=21)),  # gray, known sigma
-    ]
-    for (H, W, C), sig, known, kw in cases:
+def _check_cases(hts, cases):
+    for (H, W, C), sig, known, kw, own_basis in cases:
         clean, noisy = synth.make_config_image(H, W, C, sig, 500 + C)
         x = torch.from_numpy(noisy).cuda()
         p = hts.params(**kw)
-        want = hts.denoise(x, sigma=known, p=p).cpu().numpy()
-        got = _noalloc(hts, x, known, p).cpu().numpy()
+        basis = hts.estimate_basis(x, p) if own_basis else None
+        want = hts.denoise(x, sigma=known, p=p, basis=basis).cpu().numpy()
+        got = _noalloc(hts, x, known, p, basis).cpu().numpy()
         err = float(np.max(np.abs(got.astype(np.float64) - want)))
-        assert err <= MAX_ABS, (H, W, C, err)
+        assert err <= MAX_ABS, (H, W, C, kw, own_basis, err)
+
+
+def test_noalloc_matches_denoise_on_two_calls_in_a_row(hts):
+    _check_cases(hts, [
+        ((96, 112, 3), 40.0, None, dict(win=21), False),   # colour, sigma and basis estimated
+        ((128, 128, 1), 25.0, 25.0, dict(win=21), False),  # gray, known sigma
+    ])
+
+
+def test_noalloc_tensor_core_forms_and_caller_basis(hts):
+    # the tensor-core grouping (Eq. 9 flags, rescue list) and filter inside the shared array, and a basis
+    # (with eigenvalues) passed by the caller
+    _check_cases(hts, [
+        ((96, 112, 3), 40.0, None, dict(win=31, precision=1), False),
+        ((128, 128, 1), 25.0, None, dict(win=21, precision=1), False),
+        ((96, 112, 3), 40.0, 40.0, dict(win=31, precision=2), False),
+        ((128, 128, 1), 25.0, None, dict(win=21, precision=2), False),
+        ((96, 112, 3), 40.0, None, dict(win=21), True),
+        ((128, 128, 1), 25.0, None, dict(win=21, precision=1), True),
+    ])
 
 
 def test_noalloc_rejects_images_beyond_its_scratch(hts):
