@@ -285,6 +285,14 @@ hts_status hts_cnn_load(const char *path, hts_cnn **out);
 hts_status hts_denoise_learned(const float *noisy, float *out, int H, int W, int C, hts_cnn *net,
                                const hts_basis *basis, const hts_params *p, double fallback_factor, void *stream);
 
+/* hts_denoise_learned on HOST buffers (the host-to-device copy, the call and
+ * the device-to-host copy on `stream`, then a synchronisation), as
+ * hts_denoise_host is to hts_denoise.  HTS_ETIMEOUT / HTS_EINTERNAL if a
+ * kernel recorded a failure (out_host is then invalid). */
+hts_status hts_denoise_learned_host(const float *noisy_host, float *out_host, int H, int W, int C, hts_cnn *net,
+                                    const hts_basis *basis, const hts_params *p, double fallback_factor,
+                                    void *stream);
+
 /* The batched learned form: hts_denoise_batch in which every image's noise
  * level per reference patch comes from the network `net` (as in
  * hts_denoise_learned, Sec. III-C), checked against the image's eigenvalue

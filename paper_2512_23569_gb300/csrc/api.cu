@@ -757,6 +757,31 @@ hts_status hts_denoise_learned(const float *noisy, float *out, int H, int W, int
     return denoise_run(noisy, out, g, -1.f, basis, *p, *w, s, w->sref, fallback_factor);
 }
 
+hts_status hts_denoise_learned_host(const float *noisy_host, float *out_host, int H, int W, int C, hts_cnn *net,
+                                    const hts_basis *basis, const hts_params *p, double fallback_factor,
+                                    void *stream) {
+    Geom g;
+    HTS_TRY(validate(H, W, C, p, &g));
+    if (!noisy_host || !out_host || !net) return fail(HTS_EINVAL, "NULL pointer");
+    if (!(fallback_factor > 1.0) || !std::isfinite(fallback_factor))
+        return fail(HTS_EINVAL, "fallback_factor must be > 1");
+    if (hts_cnn_channels(net) != C) return fail(HTS_EINVAL, "network built for another channel count");
+    HTS_TRY(check_basis(basis, C));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Workspace *w;
+    HTS_TRY(get_ws(s, &w));
+    const size_t n = (size_t)H * W * C;
+    HTS_TRY(grow(w->io_in, w->cap_in, n, "cudaMalloc(io)"));
+    HTS_TRY(grow(w->io_out, w->cap_out, n, "cudaMalloc(io)"));
+    HTS_TRY(cuda_ok(cudaMemcpyAsync(w->io_in, noisy_host, n * sizeof(float), cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(H2D)"));
+    HTS_TRY(hts_denoise_learned(w->io_in, w->io_out, H, W, C, net, basis, p, fallback_factor, stream));
+    HTS_TRY(cuda_ok(cudaMemcpyAsync(out_host, w->io_out, n * sizeof(float), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(D2H)"));
+    int err = 0;
+    HTS_TRY(cuda_ok(cudaMemcpyAsync(&err, &w->st->error, sizeof(int), cudaMemcpyDeviceToHost, s), "cudaMemcpyAsync(D2H)"));
+    HTS_TRY(cuda_ok(cudaStreamSynchronize(s), "cudaStreamSynchronize"));
+    return device_status(err);
+}
+
 hts_status hts_denoise_ra(const float *noisy, float *out, int H, int W, int C, float sigma, hts_fcn *fcn,
                           const hts_basis *basis, const hts_params *p, void *stream) {
     Geom g;

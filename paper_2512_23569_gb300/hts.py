@@ -37,6 +37,7 @@ EXPORTS = [
     "hts_fcn_set_params", "hts_group_means", "hts_fcn_refine", "hts_fcn_zero_grad", "hts_fcn_accumulate_grad",
     "hts_fcn_take_loss", "hts_fcn_get_grad", "hts_fcn_adam_step", "hts_denoise_ra", "hts_mean_coefs",
     "hts_fcn_group_size", "hts_fault_inject", "hts_denoise_batch_learned",
+    "hts_denoise_learned_host",
 ]
 
 
@@ -118,6 +119,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.hts_profile_end.argtypes = [ctypes.POINTER(KernelTime), I, ctypes.POINTER(I)]
         lib.hts_denoise_sigma_map.argtypes = [P, P, I, I, I, P, P, PP, P]
         lib.hts_denoise_learned.argtypes = [P, P, I, I, I, P, P, PP, D, P]
+        lib.hts_denoise_learned_host.argtypes = [P, P, I, I, I, P, P, PP, D, P]
         lib.hts_cnn_num_params.argtypes = [I]
         lib.hts_cnn_num_params.restype = I
         lib.hts_cnn_channels.argtypes = [P]
@@ -473,6 +475,22 @@ def denoise_learned(noisy, net: Cnn, p: Params | None = None, basis: Basis | Non
     _check(load().hts_denoise_learned(ctypes.c_void_p(noisy.data_ptr()), ctypes.c_void_p(out.data_ptr()), H, W, C,
                                       net.handle, basis.handle if basis else None, ctypes.byref(p),
                                       float(fallback_factor), _stream(stream)))
+    return out
+
+
+def denoise_learned_host(noisy: np.ndarray, net: Cnn, p: Params | None = None, basis: Basis | None = None,
+                         fallback_factor: float = 2.0, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+    """hts_denoise_learned_host: host (numpy) in, host out; the copies happen inside the call."""
+    a = noisy if noisy.ndim == 3 else noisy[None]
+    if a.dtype != np.float32 or not a.flags.c_contiguous:
+        raise TypeError("expected a C-contiguous float32 CHW array")
+    C, H, W = a.shape
+    if out is None:
+        out = np.empty_like(a)
+    p = p or params()
+    _check(load().hts_denoise_learned_host(ctypes.c_void_p(a.ctypes.data), ctypes.c_void_p(out.ctypes.data), H, W,
+                                           C, net.handle, basis.handle if basis else None, ctypes.byref(p),
+                                           float(fallback_factor), _stream(stream)))
     return out
 
 

@@ -166,19 +166,25 @@ def make_pg_correlated_image(H: int, W: int, C: int, seed: int, a: float = 0.01,
 
 
 def add_varying_noise(clean: np.ndarray, seed: int, a_max: float = 0.02, sb_max: float = 30.0,
-                      sb_min: float = 0.0):
+                      sb_min: float = 0.0, gain: float | None = None, levels: tuple | None = None):
     """(noisy, sigma_px): Poisson-Gaussian noise on `clean` whose read-noise level varies across it.
 
     Gain a ~ U[0, a_max]; sigma_b ramps linearly between two levels drawn from
     U[sb_min, sb_max] along a direction drawn from U[0, 2 pi) (all from seed's
-    generator); the noise itself uses seed + 1.  sigma_px (H, W) is the true
-    per-pixel standard deviation, the root mean over channels of
+    generator); the noise itself uses seed + 1.  `gain` and `levels` (the
+    ramp's two ends), when given, replace the drawn a and levels (the
+    generator still draws them, so the direction is the same).  sigma_px (H, W)
+    is the true per-pixel standard deviation, the root mean over channels of
     a * clean + sigma_b^2.
     """
     C, H, W = clean.shape
     rng = _rng(seed)
     a = float(rng.uniform(0.0, a_max))
     s0, s1 = rng.uniform(sb_min, sb_max, size=2)
+    if gain is not None:
+        a = float(gain)
+    if levels is not None:
+        s0, s1 = float(levels[0]), float(levels[1])
     th = rng.uniform(0.0, 2.0 * np.pi)
     yy, xx = np.meshgrid(np.arange(H, dtype=np.float64), np.arange(W, dtype=np.float64), indexing="ij")
     proj = np.cos(th) * yy + np.sin(th) * xx
@@ -190,10 +196,10 @@ def add_varying_noise(clean: np.ndarray, seed: int, a_max: float = 0.02, sb_max:
 
 
 def make_varying_noise_image(H: int, W: int, C: int, seed: int, a_max: float = 0.02, sb_max: float = 30.0,
-                             sb_min: float = 0.0):
-    """(clean, noisy, sigma_px): clean_image(seed) with add_varying_noise(clean, seed + 1)."""
+                             sb_min: float = 0.0, gain: float | None = None, levels: tuple | None = None):
+    """(clean, noisy, sigma_px): clean_image(seed) with add_varying_noise(clean, seed + 1, ...)."""
     clean = clean_image(H, W, C, seed)
-    noisy, sigma_px = add_varying_noise(clean, seed + 1, a_max, sb_max, sb_min)
+    noisy, sigma_px = add_varying_noise(clean, seed + 1, a_max, sb_max, sb_min, gain, levels)
     return clean, noisy, sigma_px
 
 

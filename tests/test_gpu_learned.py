@@ -175,3 +175,14 @@ def test_network_save_load_roundtrip(hts, tmp_path):
     back = hts.Cnn.load_file(path)
     assert back.C == 3 and back.window == 40
     np.testing.assert_array_equal(back.get_params(), net.get_params())
+
+
+def test_learned_host_buffers_equal_device_call(hts):
+    # hts_denoise_learned_host: copies in, the learned call, copies out -- the device call's result
+    p = hts.params(win=15, precision=1)
+    net = hts.Cnn(3, seed=4)
+    net.window = 32
+    clean, noisy, _ = synth.make_varying_noise_image(80, 96, 3, 321, sb_min=2.0)
+    want = hts.denoise_learned(_dev(noisy), net, p, fallback_factor=50.0).cpu().numpy()
+    got = hts.denoise_learned_host(noisy, net, p, fallback_factor=50.0)
+    np.testing.assert_array_equal(want, got)
