@@ -1391,6 +1391,45 @@ __global__ void k_normalize4(const longlong2 *__restrict__ acc, const int4 *__re
     }
 }
 
+// Weights from patch-origin counts (the tensor-core filter's aggregation): the weight of pixel (y, x)
+// is the sum of the counts of the origins (y - u, x - v), 0 <= u, v < 8, formed per 32 x 32 block of
+// pixels from the counts staged in shared memory (row sums over 8 columns, then 8 rows); then
+// out = sum / (2^16 weight) as in k_normalize.
+constexpr int NB_T = 32;
+template <int C>
+__global__ void __launch_bounds__(256) k_normalize_box(const long long *__restrict__ acc, const int *__restrict__ cnt,
+                                                       float *__restrict__ out, int H, int W) {
+    __shared__ int sc[NB_T + PS - 1][NB_T + PS - 1];
+    __shared__ int sr[NB_T + PS - 1][NB_T];
+    const int by = blockIdx.y * NB_T, bx = blockIdx.x * NB_T;
+    const size_t HW = (size_t)H * W;
+    for (int e = threadIdx.x; e < (NB_T + PS - 1) * (NB_T + PS - 1); e += blockDim.x) {
+        const int yy = e / (NB_T + PS - 1), xx = e - yy * (NB_T + PS - 1);
+        const int y = by + yy - (PS - 1), x = bx + xx - (PS - 1);
+        sc[yy][xx] = (y >= 0 && y < H && x >= 0 && x < W) ? __ldg(cnt + (size_t)y * W + x) : 0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < (NB_T + PS - 1) * NB_T; e += blockDim.x) {
+        const int yy = e / NB_T, xx = e - yy * NB_T;
+        int t = 0;
+#pragma unroll
+        for (int v = 0; v < PS; ++v) t += sc[yy][xx + v];
+        sr[yy][xx] = t;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB_T * NB_T; e += blockDim.x) {
+        const int yy = e / NB_T, xx = e - yy * NB_T;
+        const int y = by + yy, x = bx + xx;
+        if (y >= H || x >= W) continue;
+        int w = 0;
+#pragma unroll
+        for (int u = 0; u < PS; ++u) w += sr[yy + u][xx];
+        const size_t p = (size_t)y * W + x;
+#pragma unroll
+        for (int c = 0; c < C; ++c) out[c * HW + p] = __ll2float_rn(acc[c * HW + p]) * (1.0f / 65536.0f) / (float)w;
+    }
+}
+
 template <int C, int K>
 size_t exact_smem() {
     constexpr int NCOEF = Cfg<C>::NCOEF;
@@ -1438,6 +1477,17 @@ std::vector<int> tune_key(const Geom &g) {
     int dev = 0;
     cudaGetDevice(&dev);
     return {dev, g.H, g.W, g.C, g.K, g.R, g.step};
+}
+
+// Normalisation when wcount holds patch-origin counts (the tensor-core filter).
+hts_status launch_normalize_box(const long long *acc, const int *cnt, float *out, int H, int W, int C, cudaStream_t s) {
+    const dim3 grid((W + NB_T - 1) / NB_T, (H + NB_T - 1) / NB_T);
+    {
+        KTimer kt("k_normalize_box", s);
+        if (C == 1) k_normalize_box<1><<<grid, 256, 0, s>>>(acc, cnt, out, H, W);
+        else k_normalize_box<3><<<grid, 256, 0, s>>>(acc, cnt, out, H, W);
+    }
+    return check_launch("k_normalize_box");
 }
 
 hts_status launch_normalize(const long long *acc, const int *wcount, float *out, size_t HW, int C, int nsm,
@@ -1585,12 +1635,7 @@ hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, co
             launch_filter_tc(img, g, idx, b32, acc, wcount, st, sigma_ref, map_judged, tau_scale, mean_est, s, &used);
         if (st0 != HTS_OK) return st0;
         if (!used && mean_est) return report(HTS_EUNSUPPORTED, "the enhancement strategy needs the tensor-core filter");
-        if (used) {
-            int dev = 0, nsm = 152;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-            return launch_normalize(acc, wcount, out, (size_t)g.H * g.W, g.C, nsm, s);
-        }
+        if (used) return launch_normalize_box(acc, wcount, out, g.H, g.W, g.C, s);
     }
 #define HTS_FILTER_CASE(CC, KK) \
     if (g.C == CC && g.K == KK) return launch_ck<CC, KK>(a, g, out, s);

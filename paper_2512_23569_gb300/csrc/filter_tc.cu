@@ -26,7 +26,11 @@
 // estimates in 32-bit shared-memory accumulators over the tile's region
 // (at most 2^10 members of a tile cover a pixel: no overflow), flushed to
 // the image-wide int64 sums (2^16 scale) once per tile; integer sums do not
-// depend on the order of the additions, so the result is deterministic.  The MMA waits
+// depend on the order of the additions, so the result is deterministic.
+// Weights: every member adds 1 to the count of its patch origin (top-left
+// pixel) instead of 1 to each of its 64 pixels; a pixel's weight is the sum of
+// the origin counts over the 8 x 8 origins whose patch covers it, formed by
+// k_normalize_box.  The MMA waits
 // are bounded: a wait that gives up records DevState.error = 2, waits
 // (bounded) for the MMAs, frees the tensor memory and leaves.
 #include <cuda_fp16.h>
@@ -40,10 +44,55 @@
 namespace hts {
 namespace {
 
-using fc::haar_fwd;
-using fc::haar_inv;
 using fc::K3F;
 using fc::S3H;
+
+// The Haar transform of Eq. 8 without its 1/sqrt(2) factors: sums and differences only.  In the row
+// order of Eq. 8 (row 0 the sum, then the difference rows coarse to fine) coefficient k has passed
+// l_k butterflies, l_0 = log2 K and l_k = log2 K - floor(log2 k) for k >= 1, and equals 2^(l_k / 2)
+// times the orthonormal one.  A coefficient is kept iff the orthonormal value reaches tau, i.e. iff
+// |x_k| >= tau 2^(l_k / 2); kept ones are scaled by 2^(-l_k) (exact), after which the unnormalised
+// inverse butterflies give the orthonormal inverse.
+template <int K>
+__device__ __forceinline__ void haar_fwd_u(float (&x)[K]) {
+#pragma unroll
+    for (int n = K; n >= 2; n >>= 1) {
+        float t[K];
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            t[i] = x[2 * i] + x[2 * i + 1];
+            t[n / 2 + i] = x[2 * i] - x[2 * i + 1];
+        }
+#pragma unroll
+        for (int i = 0; i < n; ++i) x[i] = t[i];
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void haar_inv_u(float (&x)[K]) {
+#pragma unroll
+    for (int n = 2; n <= K; n <<= 1) {
+        float t[K];
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            t[2 * i] = x[i] + x[n / 2 + i];
+            t[2 * i + 1] = x[i] - x[n / 2 + i];
+        }
+#pragma unroll
+        for (int i = 0; i < n; ++i) x[i] = t[i];
+    }
+}
+
+// Butterflies coefficient k of a K-long unnormalised Haar transform has passed.
+template <int K>
+__host__ __device__ constexpr int haar_level(int k) {
+    int L = 0;
+    while ((1 << L) < K) ++L;
+    if (k == 0) return L;
+    int f = 0;
+    while ((2 << f) <= k) ++f;
+    return L - f;
+}
 
 constexpr int NT = 512;   // 16 warps: warp w reads tensor-memory lanes 32 (w % 4) .. + 31, column quarter w / 4
 constexpr int MB = 128;   // group members per batch = MMA M
@@ -106,7 +155,7 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
     uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
     int *accs = reinterpret_cast<int *>(smem + L::acc_off);
     const int RA = a.rh_max * a.rw_max;
-    int *acc_v = accs, *acc_w = accs + C * RA;  // [C][RA] sums of value * 2^8, [RA] counts
+    int *acc_v = accs, *acc_w = accs + C * RA;  // [C][RA] sums of value * 2^8, [RA] patch-origin counts
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const size_t HW = (size_t)a.H * a.W;
     const bool use_map = a.sigma_ref && (!a.map_judged || a.st->learned);
@@ -333,23 +382,32 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
                         x[k + 2] = t4.z;
                         x[k + 3] = t4.w;
                     }
-                    haar_fwd<K>(x);
+                    haar_fwd_u<K>(x);
                     if (!cplx) {
 #pragma unroll
-                        for (int k = 0; k < K; ++k)
-                            if (!(fabsf(x[k]) >= tau)) x[k] = 0.f;
+                        for (int k = 0; k < K; ++k) {
+                            const int l = haar_level<K>(k);
+                            // |x| >= tau 2^(l/2): tau times sqrt(2) for odd l, times 2^(l/2) exactly
+                            const float tl = (l & 1) ? tau * (float)(1 << (l >> 1)) * 1.41421356237309505f
+                                                     : tau * (float)(1 << (l >> 1));
+                            x[k] = (fabsf(x[k]) >= tl) ? x[k] * (1.f / (float)(1 << l)) : 0.f;
+                        }
                     } else {
+                        // modulus test on squares: re^2 + im^2 >= tau^2 2^l (lanes 2i, 2i + 1 hold the real and
+                        // imaginary stream of one coefficient; the sum is formed in one order on both)
                         const bool im = s2 & 1;
+                        const float tau2 = tau * tau;
 #pragma unroll
                         for (int k = 0; k < K; ++k) {
+                            const int l = haar_level<K>(k);
                             const float sq = x[k] * x[k];
                             const float other = __shfl_xor_sync(0xffffffffu, sq, 1);
-                            const float mag = im ? sqrtf(other + sq) : sqrtf(sq + other);  // re^2 + im^2, one order
-                            if (!(mag >= tau)) x[k] = 0.f;
+                            const float m2 = im ? (other + sq) : (sq + other);
+                            x[k] = (m2 >= tau2 * (float)(1 << l)) ? x[k] * (1.f / (float)(1 << l)) : 0.f;
                         }
                     }
                     if (ra) x[0] = 0.f;  // Haar row 0 (Eq. 8 order): its refined value is added after the inverse
-                    haar_inv<K>(x);
+                    haar_inv_u<K>(x);
 #pragma unroll
                     for (int k = 0; k < K; k += 4)
                         *reinterpret_cast<float4 *>(p + k) = make_float4(x[k], x[k + 1], x[k + 2], x[k + 3]);
@@ -423,8 +481,8 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
                         for (int v = 0; v < 8; ++v) {
 #pragma unroll
                             for (int c = 0; c < C; ++c) atomicAdd(acc_v + c * RA + o + v, __float2int_rn(out[c][v] * 256.f));
-                            atomicAdd(acc_w + o + v, 1);
                         }
+                        if (row == 0) atomicAdd(acc_w + o, 1);  // the patch's origin: its 64 pixels' weight
                     } else {
                         atomicExch(&a.st->error, 1);
                     }
@@ -434,18 +492,20 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
             __syncthreads();
         }
         if (!ok) break;
-        // flush the tile's sums to the image-wide int64 sums
+        // flush the tile's sums to the image-wide int64 sums and its origin counts to the image-wide ones
+        // (k_normalize_box turns those into pixel weights)
         for (int e = tid; e < rh * rw; e += NT) {
             const int w = acc_w[e];
-            if (w == 0) continue;
             const int yy = e / rw, xx = e - yy * rw;
             const size_t gpix = (size_t)(ry0 + yy) * a.W + (rx0 + xx);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                const long long s = (long long)acc_v[c * RA + e] * 256ll;  // to the image-wide 2^16 scale
+                const int v = acc_v[c * RA + e];
+                if (v == 0) continue;
+                const long long s = (long long)v * 256ll;  // to the image-wide 2^16 scale
                 atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + c * HW + gpix), (unsigned long long)s);
             }
-            atomicAdd(a.wcount + gpix, w);
+            if (w != 0) atomicAdd(a.wcount + gpix, w);
         }
         __syncthreads();
     }
