@@ -1,23 +1,27 @@
 // Globally-learned t-SVD basis (Sec. III-B2, Eq. 11) on sm_103a, in FP64.
 //
-// k_cov      : every block takes a run of reference patches, forms their
-//              unitary DFT along channels (slice 0 real, slice 1 complex;
-//              slice 2 is the conjugate of slice 1) and accumulates the upper
-//              triangles of C_row^(j) = sum P P^H and C_col^(j) = sum P^H P,
-//              one thread per matrix entry, into per-block partial sums;
+// k_cov      : the channel-pair sums behind C_row and C_col as sums along
+//              image lines: every row (column) pair of a grid row (column) of
+//              patches is summed once over the whole line, each position
+//              weighted by the number of reference patches that cover it, in
+//              exact products and double-float sums (see below), one thread
+//              per matrix entry, per-block partial sums;
 // k_cov_sum  : adds the partial sums in block order (deterministic) and
 //              fills the Hermitian matrices;
 // k_jacobi   : one warp per 8x8 Hermitian matrix, parallel cyclic Jacobi
 //              (4 disjoint complex rotations per round, 7 rounds per sweep),
 //              first in FP32, then refined in FP64; eigenvalues sorted
 //              ascending, eigenvectors as columns.
+#include <algorithm>
+
 #include "hts_internal.h"
 
 namespace hts {
 namespace {
 
-constexpr int COV_REFS = 64;   // reference patches per block
-constexpr int COV_BATCH = 16;  // staged at once
+constexpr int COV_CH = 128;     // line positions staged per step
+constexpr int COV_BLOCKS = 608;  // blocks per side at most (a constant: the partial sums' layout and order
+                                 // do not depend on the device)
 constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ void pair_of(int p, int &a, int &b) {
@@ -33,13 +37,19 @@ __device__ __forceinline__ void pair_of(int p, int &a, int &b) {
 
 // Raw channel products of the reference patches, exactly: every product of
 // two floats is split into p + e (p = fl(x y), e = fma(x, y, -p)) and
-// accumulated in a double-float (hi, lo) pair; |error| <= n u^2 sum|terms| for
-// n terms (u = 2^-24), i.e. FP64-grade without the FP64 pipes.
+// accumulated in a double-float (hi, lo) pair over at most COV_CH terms, then
+// added to an FP64 sum; |error| <= n u^2 sum|terms| per pair (u = 2^-24,
+// n <= 128), i.e. FP64-grade without the FP64 pipes.
 //   row sums  M_tt'[a][b] = sum_i sum_k P_i^(t)[a][k] P_i^(t')[b][k]
 //   col sums  N_tt'[a][b] = sum_i sum_k P_i^(t)[k][a] P_i^(t')[k][b]
-// for channel pairs t <= t' (upper triangles when t = t').  k_cov_sum adds
-// the blocks' partial sums in FP64 in block order and forms the Fourier-slice
-// covariances C_row^(j) = (1/c) sum_{t,t'} w^{j(t-t')} M_tt',
+// for channel pairs t <= t' (upper triangles when t = t').  With the patches
+// on the grid Y x X, M_tt'[a][b] = sum_{y in Y} sum_col m_X(col)
+// I_t(y + a, col) I_t'(y + b, col), m_X(col) = number of grid positions x
+// with x <= col <= x + 7 (1 or 2 at step 4): one weighted dot product of two
+// image rows per grid row instead of one 8-term product per patch (and the
+// same along columns for N).  Multiplying by m_X (an integer <= 8) is exact.
+// k_cov_sum adds the blocks' partial sums in FP64 in block order and forms
+// the Fourier-slice covariances C_row^(j) = (1/c) sum_{t,t'} w^{j(t-t')} M_tt',
 // C_col^(j) = (1/c) sum_{t,t'} w^{j(t'-t)} N_tt', w = exp(-2 pi i / c).
 template <int C>
 struct CovCfg {
@@ -47,7 +57,7 @@ struct CovCfg {
     static constexpr int NASY = C * (C - 1) / 2;     // channel pairs t < t'
     static constexpr int PER = NSYM * 36 + NASY * 64;  // entries per side
     static constexpr int NT = 2 * PER;               // row + col
-    static constexpr int THREADS = (NT + 31) / 32 * 32;
+    static constexpr int THREADS = (PER + 31) / 32 * 32 < 64 ? 64 : (PER + 31) / 32 * 32;
 };
 
 __device__ __forceinline__ void task_of(int t, int per, int nsym, int &m, int &t0, int &t1, int &a, int &b) {
@@ -77,59 +87,91 @@ __device__ __forceinline__ void df_add(float &hi, float &lo, float x, float y) {
     lo = __fadd_rn(lo, __fadd_rn(err, e));
 }
 
+// Reference patches (grid 0, step, 2 step, ... plus n - 8) that cover index i of an axis of length n.
+__device__ __forceinline__ int cover_count(int i, int n, int step) {
+    const int last = n - PS;
+    const int lo = max(0, i - (PS - 1)), hi = min(i, last);
+    if (hi < lo) return 0;
+    int c = hi / step - (lo + step - 1) / step + 1;
+    if (c < 0) c = 0;
+    if (last % step != 0 && last >= lo && last <= hi) c += 1;
+    return c;
+}
+
+// blockIdx.y = side (0: row sums along image rows, 1: column sums along image columns); block b of a
+// side takes grid lines b, b + nb, ... (nb = nb_r or nb_c); thread t < PER takes entry t of its side.
 template <int C>
 __global__ void __launch_bounds__(CovCfg<C>::THREADS) k_cov(const float *__restrict__ img, int H, int W, int step,
-                                                            int nx, int nref, double *__restrict__ partials) {
-    constexpr int NT = CovCfg<C>::NT;
-    __shared__ float sp[COV_BATCH][C * 64];
+                                                            int ny, int nx, int nb_r, int nb_c,
+                                                            double *__restrict__ partials) {
+    constexpr int PER = CovCfg<C>::PER;
+    constexpr int NL = C * PS;  // staged lines: channel * 8 + offset
+    constexpr int LS = COV_CH + 4;
+    __shared__ __align__(16) float sl[NL][LS];
+    __shared__ __align__(16) float sw[COV_CH];
+    const int side = blockIdx.y;
+    const int nb = side == 0 ? nb_r : nb_c;
+    if ((int)blockIdx.x >= nb) return;  // the whole block
     const int t = threadIdx.x;
-    const size_t HW = (size_t)H * W;
+    const bool valid = t < PER;
     int m = 0, t0 = 0, t1 = 0, a = 0, b = 0;
-    if (t < NT) task_of(t, CovCfg<C>::PER, CovCfg<C>::NSYM, m, t0, t1, a, b);
-    float hi = 0.f, lo = 0.f;
-    const int r0 = blockIdx.x * COV_REFS;
-    const int r1 = min(nref, r0 + COV_REFS);
-    for (int rb = r0; rb < r1; rb += COV_BATCH) {
-        const int nb = min(COV_BATCH, r1 - rb);
-        for (int w = t; w < nb * C * 64; w += blockDim.x) {
-            const int rr = w / (C * 64), ce = w - rr * (C * 64);
-            const int c = ce >> 6, e = ce & 63;
-            const int r = rb + rr;
-            const int y = grid_pos(r / nx, H, step) + (e >> 3), x = grid_pos(r % nx, W, step) + (e & 7);
-            sp[rr][ce] = __ldg(img + (size_t)c * HW + (size_t)y * W + x);
-        }
-        __syncthreads();
-        if (t < NT) {
-            for (int rr = 0; rr < nb; ++rr) {
-                const float *X = sp[rr] + t0 * 64, *Y = sp[rr] + t1 * 64;
-                if (m == 0) {
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) df_add(hi, lo, X[a * 8 + k], Y[b * 8 + k]);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) df_add(hi, lo, X[k * 8 + a], Y[k * 8 + b]);
+    if (valid) task_of(side * PER + t, PER, CovCfg<C>::NSYM, m, t0, t1, a, b);
+    const size_t HW = (size_t)H * W;
+    const int nlines = side == 0 ? ny : nx;
+    const int len = side == 0 ? W : H;
+    double acc = 0.0;
+    for (int gl = blockIdx.x; gl < nlines; gl += nb) {
+        const int base = grid_pos(gl, side == 0 ? H : W, step);  // first image row (column) of the patches
+        for (int p0 = 0; p0 < len; p0 += COV_CH) {
+            const int np = min(COV_CH, len - p0);
+            if (side == 0) {  // rows base .. base + 7 of every channel, columns p0 .. p0 + np - 1
+                for (int e = t; e < NL * COV_CH; e += blockDim.x) {
+                    const int ln = e / COV_CH, q = e - ln * COV_CH;
+                    const int c = ln >> 3, off = ln & 7;
+                    sl[ln][q] = q < np ? __ldg(img + c * HW + (size_t)(base + off) * W + p0 + q) : 0.f;
+                }
+            } else {  // columns base .. base + 7 of every channel, rows p0 .. p0 + np - 1
+                for (int e = t; e < NL * COV_CH; e += blockDim.x) {
+                    const int q = e / NL, ln = e - q * NL;
+                    const int c = ln >> 3, off = ln & 7;
+                    sl[ln][q] = q < np ? __ldg(img + c * HW + (size_t)(p0 + q) * W + base + off) : 0.f;
                 }
             }
-            // renormalise so that lo stays below an ulp of hi
-            const float s = __fadd_rn(hi, lo);
-            lo = __fsub_rn(lo, __fsub_rn(s, hi));
-            hi = s;
+            for (int q = t; q < COV_CH; q += blockDim.x) sw[q] = q < np ? (float)cover_count(p0 + q, len, step) : 0.f;
+            __syncthreads();
+            if (valid) {
+                const float4 *X = reinterpret_cast<const float4 *>(sl[t0 * PS + a]);
+                const float4 *Y = reinterpret_cast<const float4 *>(sl[t1 * PS + b]);
+                const float4 *Wt = reinterpret_cast<const float4 *>(sw);
+                float hi = 0.f, lo = 0.f;
+                for (int q4 = 0; q4 < (np + 3) / 4; ++q4) {
+                    const float4 x = X[q4], y = Y[q4], w = Wt[q4];
+                    df_add(hi, lo, __fmul_rn(x.x, w.x), y.x);
+                    df_add(hi, lo, __fmul_rn(x.y, w.y), y.y);
+                    df_add(hi, lo, __fmul_rn(x.z, w.z), y.z);
+                    df_add(hi, lo, __fmul_rn(x.w, w.w), y.w);
+                }
+                acc += (double)hi + (double)lo;
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
-    if (t < NT) partials[(size_t)blockIdx.x * NT + t] = (double)hi + (double)lo;
+    if (valid) partials[((size_t)(side == 0 ? 0 : nb_r) + blockIdx.x) * PER + t] = acc;
 }
 
 // Sum of the blocks' partial sums, one warp per entry, fixed reduction tree.
 template <int C>
-__global__ void __launch_bounds__(256) k_cov_sum(const double *__restrict__ partials, int nblocks,
+__global__ void __launch_bounds__(256) k_cov_sum(const double *__restrict__ partials, int nb_r, int nb_c,
                                                  double *__restrict__ totals) {
-    constexpr int NT = CovCfg<C>::NT;
+    constexpr int NT = CovCfg<C>::NT, PER = CovCfg<C>::PER;
     const int lane = threadIdx.x & 31;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (t >= NT) return;
+    const int side = t / PER, e = t - side * PER;
+    const int nblocks = side == 0 ? nb_r : nb_c;
+    const double *part = partials + (size_t)(side == 0 ? 0 : nb_r) * PER + e;
     double sum = 0.0;
-    for (int bl = lane; bl < nblocks; bl += 32) sum += partials[(size_t)bl * NT + t];
+    for (int bl = lane; bl < nblocks; bl += 32) sum += part[(size_t)bl * PER];
 #pragma unroll
     for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
     if (lane == 0) totals[t] = sum;
@@ -548,26 +590,27 @@ __global__ void __launch_bounds__(32) k_jacobi(const double *__restrict__ totals
 }  // namespace
 
 size_t cov_partial_count(const Geom &g) {
-    const int nb = (g.nref + COV_REFS - 1) / COV_REFS;
-    const int nt = (g.C == 3) ? CovCfg<3>::NT : CovCfg<1>::NT;
-    return (size_t)nb * nt + nt;  // per-block partial sums, then the totals
+    const int nb = std::min(g.ny, COV_BLOCKS) + std::min(g.nx, COV_BLOCKS);
+    const int per = (g.C == 3) ? CovCfg<3>::PER : CovCfg<1>::PER;
+    return (size_t)nb * per + 2 * per;  // per-block partial sums of both sides, then the totals
 }
 
 template <int C>
 hts_status launch_basis_c(const float *img, const Geom &g, double *partials, double *b64, float *b32, double *eig,
                           cudaStream_t s) {
-    constexpr int NT = CovCfg<C>::NT;
-    const int nb = (g.nref + COV_REFS - 1) / COV_REFS;
+    constexpr int NT = CovCfg<C>::NT, PER = CovCfg<C>::PER;
+    const int nb_r = std::min(g.ny, COV_BLOCKS), nb_c = std::min(g.nx, COV_BLOCKS);
     const int ns = C / 2 + 1;
-    double *totals = partials + (size_t)nb * NT;
+    double *totals = partials + (size_t)(nb_r + nb_c) * PER;
     {
         KTimer kt("k_cov", s);
-        k_cov<C><<<nb, CovCfg<C>::THREADS, 0, s>>>(img, g.H, g.W, g.step, g.nx, g.nref, partials);
+        k_cov<C><<<dim3(std::max(nb_r, nb_c), 2), CovCfg<C>::THREADS, 0, s>>>(img, g.H, g.W, g.step, g.ny, g.nx,
+                                                                              nb_r, nb_c, partials);
     }
     if (hts_status st = check_launch("k_cov"); st != HTS_OK) return st;
     {
         KTimer kt("k_cov_sum", s);
-        k_cov_sum<C><<<(NT * 32 + 255) / 256, 256, 0, s>>>(partials, nb, totals);
+        k_cov_sum<C><<<(NT * 32 + 255) / 256, 256, 0, s>>>(partials, nb_r, nb_c, totals);
     }
     if (hts_status st = check_launch("k_cov_sum"); st != HTS_OK) return st;
     {

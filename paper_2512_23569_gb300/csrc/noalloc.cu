@@ -33,7 +33,8 @@ constexpr size_t OFF_B64 = OFF_STATE + align256(sizeof(DevState));
 constexpr size_t OFF_B32 = OFF_B64 + align256(2 * 256 * sizeof(double));
 constexpr size_t OFF_EIG = OFF_B32 + align256(2 * 256 * sizeof(float));
 constexpr size_t OFF_COV = OFF_EIG + align256(32 * sizeof(double));
-// covariance sums: (N_ref / 64 blocks) x 600 channel-pair entries, then the 600 totals
+// covariance sums (at most 2 x 608 blocks of 300 channel-pair entries, then the 600 totals; the
+// launch checks cov_partial_count against this)
 constexpr size_t COV_DOUBLES = (size_t)((NA_MAX_NREF + 63) / 64) * 600 + 600;
 constexpr size_t OFF_IDX = OFF_COV + align256(COV_DOUBLES * sizeof(double));
 constexpr size_t OFF_GREEN = OFF_IDX + align256(NA_MAX_SLOTS * sizeof(int32_t));
