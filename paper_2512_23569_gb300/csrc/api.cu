@@ -13,6 +13,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hts_internal.h"
 
 
@@ -35,6 +37,22 @@ static bool capturing(cudaStream_t s) {
 }
 
 bool stream_capturing(cudaStream_t s) { return capturing(s); }
+
+void *tensor_map_encoder() {
+    static void *fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = p;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
 
 // ------------------------------------------------------- fault injection
 
@@ -156,12 +174,14 @@ static cudaEvent_t take_event() {
     return e;
 }
 
-KTimer::KTimer(const char *name, cudaStream_t s) : slot(-1), stream(s) {
+KTimer::KTimer(const char *name, cudaStream_t s) : slot(-1), range(false), stream(s) {
     if (capturing(s)) {  // counted when the graph launches; no profiling events in graphs
         ++g_captured;
         return;
     }
     count_launch();
+    nvtxRangePushA(name);
+    range = true;
     if (fault_take(FAULT_LAUNCH)) g_launch_fault = true;
     std::lock_guard<std::mutex> lk(g_pmu);
     if (!g_prof) return;
@@ -176,6 +196,7 @@ KTimer::KTimer(const char *name, cudaStream_t s) : slot(-1), stream(s) {
 }
 
 KTimer::~KTimer() {
+    if (range) nvtxRangePop();
     if (slot < 0) return;
     std::lock_guard<std::mutex> lk(g_pmu);
     cudaEventRecord(g_recs[slot].e1, stream);

@@ -24,6 +24,8 @@
 // gives up sets the network's error flag, the block waits (bounded) for its
 // MMAs and releases its tensor memory, and the map is then filled with NaN
 // so that the learned-map check falls back to the estimate.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -186,6 +188,153 @@ __global__ void __launch_bounds__(NTH, 1)
     if (warp == 0) tc::tmem_dealloc(tbase, L::tcols);
 }
 
+// Hidden layers (1..4: four planes of 8 FP16 channels in), with the input staged by TMA: a block runs
+// its strips in turn with two staging buffers; while strip i's MMAs and epilogue run, the tensor-memory
+// accumulators being read and the outputs written, the TMA copy of strip i + 1's input (the same
+// 4 x 18 x 66 box of 16-byte pixel vectors, zero outside the image) lands in the other buffer.  One
+// block per SM (two 76 KB buffers).  Waits bounded as in k_conv_tc; a block that gives up waits
+// (bounded) for its copy in flight and its MMAs before it releases its tensor memory.
+constexpr int CING_H = 4;
+constexpr size_t TMA_BOX_BYTES = (size_t)CING_H * PY * PX * 16;
+constexpr size_t TMA_BUF = (TMA_BOX_BYTES + 1023) / 1024 * 1024;
+
+template <int NOUT>
+struct ConvTmaLayout {
+    static constexpr size_t buf0 = 0, buf1 = TMA_BUF;
+    static constexpr size_t b_off = 2 * TMA_BUF;
+    static constexpr size_t b_bytes = (size_t)9 * CING_H * NOUT * 16;
+    static constexpr size_t bias_off = b_off + b_bytes;
+    static constexpr size_t bar_off = (bias_off + (size_t)NOUT * 4 + 15) / 16 * 16;
+    static constexpr size_t total = bar_off + 4 * 8 + 16;
+    static constexpr uint32_t tcols = MT * NOUT;
+};
+
+template <int NOUT, bool OUT_MAP>
+__global__ void __launch_bounds__(NTH, 1)
+    k_conv_tma(const __grid_constant__ CUtensorMap tmap, int H, int W, const __half *__restrict__ wt, int cin, int cout,
+               __half *__restrict__ hout, float *__restrict__ map, int *err) {
+    using L = ConvTmaLayout<NOUT>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __half *sB = reinterpret_cast<__half *>(smem + L::b_off);
+    float *sBias = reinterpret_cast<float *>(smem + L::bias_off);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::bar_off);  // [2]: a staging buffer's copy landed
+    uint64_t *mbar = full + 2;                                         // the strip's MMAs completed
+    uint32_t *slot = reinterpret_cast<uint32_t *>(full + 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    for (int e = tid; e < 9 * CING_H * NOUT * 8; e += NTH) {
+        const int k = e & 7, rest = e >> 3;
+        const int n = rest % NOUT, g = (rest / NOUT) % CING_H, tap = rest / (NOUT * CING_H);
+        const int ci = g * 8 + k;
+        sB[e] = (n < cout && ci < cin) ? wt[(n * cin + ci) * 9 + tap] : __float2half_rn(0.f);
+    }
+    for (int n = tid; n < NOUT; n += NTH) sBias[n] = n < cout ? __half2float(wt[cout * cin * 9 + n]) : 0.f;
+    const int nsx = (W + SX - 1) / SX, nstrip = ((H + SY - 1) / SY) * nsx;
+    if (tid == 0) {
+        tc::bar_init(&full[0], 1);
+        tc::bar_init(&full[1], 1);
+        tc::bar_init(mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) tc::tmem_alloc(slot, L::tcols);
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = *slot;
+    const uint32_t idesc = tc::idesc_f16(128, NOUT, false);
+    auto issue_copy = [&](int strip, int b) {  // thread 0: the strip's input box into buffer b
+        const int y0 = (strip / nsx) * SY, x0 = (strip % nsx) * SX;
+        tc::bar_arrive_expect_tx(&full[b], (uint32_t)TMA_BOX_BYTES);
+        tc::tma_load_3d(smem + (b ? L::buf1 : L::buf0), &tmap, &full[b], 2 * (x0 - 1), y0 - 1, 0);
+    };
+    // copies issued into / waited for from each buffer (the same on every thread: the decisions are uniform)
+    int issued[2] = {0, 0}, waited[2] = {0, 0};
+    if ((int)blockIdx.x < nstrip) {
+        if (tid == 0) issue_copy(blockIdx.x, 0);
+        issued[0] = 1;
+    }
+    bool failed = false;
+    int i = 0;
+    for (int strip = blockIdx.x; strip < nstrip; strip += gridDim.x, ++i) {
+        const int b = i & 1;
+        const int y0 = (strip / nsx) * SY, x0 = (strip % nsx) * SX;
+        // the next strip's copy goes out now (its buffer's last reader, strip i - 1's MMAs, has completed)
+        const int next = strip + gridDim.x;
+        if (next < nstrip) {
+            if (tid == 0) issue_copy(next, b ^ 1);
+            ++issued[b ^ 1];
+        }
+        const bool landed = tc::bar_wait(&full[b], (uint32_t)(waited[b] & 1), SPIN);
+        if (__syncthreads_or(!landed)) {
+            failed = true;
+            break;
+        }
+        ++waited[b];
+        if (tid == 0) {
+            tc::fence_after();
+            const uint32_t a0 = tc::su32(smem + (b ? L::buf1 : L::buf0)), b0 = tc::su32(sB);
+            for (int j = 0; j < MT; ++j)
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ky = tap / 3, kx = tap - 3 * ky;
+#pragma unroll
+                    for (int ss = 0; ss < CING_H / 2; ++ss) {
+                        const uint32_t aoff = (uint32_t)((((2 * ss) * PY + ky) * PX + 8 * j + kx) * 16);
+                        const uint32_t boff = (uint32_t)((tap * CING_H + 2 * ss) * NOUT * 16);
+                        const uint64_t ad = tc::sdesc(a0 + aoff, PY * PX * 16, PX * 16);
+                        const uint64_t bd = tc::sdesc(b0 + boff, NOUT * 16, 128);
+                        tc::mma_f16(tbase + j * NOUT, ad, bd, idesc, (tap | ss) ? 1u : 0u);
+                    }
+                }
+            tc::mma_commit(mbar);
+        }
+        const bool done = tc::bar_wait(mbar, (uint32_t)(i & 1), SPIN);
+        if (__syncthreads_or(!done)) {
+            if (tid == 0) tc::bar_wait(mbar, (uint32_t)(i & 1), SPIN);  // the MMAs end before the memory is released
+            failed = true;
+            break;
+        }
+        tc::fence_after();
+        const int q = warp & 3, m = 32 * q + lane;
+        const int oy = y0 + (m >> 3);
+        for (int j = warp >> 2; j < MT; j += 2) {
+            const int ox = x0 + 8 * j + (m & 7);
+            const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(j * NOUT);
+            if (OUT_MAP) {
+                const float v = __uint_as_float(tc::tmem_ld1(taddr));
+                tc::tmem_wait_ld();
+                if (oy < H && ox < W) map[(size_t)oy * W + ox] = v + sBias[0];
+            } else {
+                uint32_t r[32];
+                tc::tmem_ld32(taddr, r);
+                tc::tmem_wait_ld();
+                if (oy < H && ox < W) {
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        __align__(16) __half h[8];
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)
+                            h[c] = __float2half_rn(fmaxf(__uint_as_float(r[8 * g + c]) + sBias[8 * g + c], 0.f));
+                        reinterpret_cast<uint4 *>(hout)[((size_t)g * H + oy) * W + ox] =
+                            *reinterpret_cast<const uint4 *>(h);
+                    }
+                }
+            }
+        }
+        tc::fence_before();
+        __syncthreads();  // tensor memory is free for the next strip
+    }
+    if (failed && tid == 0) {
+        atomicExch(err, 1);
+        // copies still in flight must land before the block's shared memory is released
+        for (int pb = 0; pb < 2; ++pb)
+            for (int w = waited[pb]; w < issued[pb]; ++w) tc::bar_wait(&full[pb], (uint32_t)(w & 1), SPIN);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, L::tcols);
+}
+
 // After a forward whose wait gave up: the whole map becomes NaN.
 __global__ void k_map_poison(float *map, size_t n, const int *err) {
     if (*err == 0) return;
@@ -208,6 +357,37 @@ hts_status conv_tc(const hts_cnn *n, int l, const float *img, const __half *hin,
             img, n->C, hin, H, W, n->w16 + n->off[l], n->cin[l], n->cout[l], hout, map, n->err);
     }
     return check_launch("k_conv_tc");
+}
+
+// A hidden layer with the TMA-staged input: the tensor map describes hin as [plane][y][x][8 halves], read
+// as 8-byte elements (3-D, innermost first: 2 W, H, 4 planes) with the box of one strip's staged input.
+template <int NOUT, bool OUT_MAP>
+hts_status conv_tma(const hts_cnn *n, int l, const __half *hin, int H, int W, __half *hout, float *map, int nsm,
+                    cudaStream_t s) {
+    using L = ConvTmaLayout<NOUT>;
+    const auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
+    if (!enc) return report(HTS_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    // 8-byte elements, two per pixel vector: each box row is one contiguous run of 2 PX elements
+    CUtensorMap tmap;
+    const cuuint64_t dims[3] = {(cuuint64_t)W * 2, (cuuint64_t)H, (cuuint64_t)CING_H};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * 16, (cuuint64_t)H * W * 16};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * PX), (cuuint32_t)PY, (cuuint32_t)CING_H};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<__half *>(hin), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return report(HTS_ECUDA, "cuTensorMapEncodeTiled failed for a network layer");
+    const void *k = reinterpret_cast<const void *>(k_conv_tma<NOUT, OUT_MAP>);
+    const hts_status st = allow_smem(k, L::total);
+    if (st != HTS_OK) return st;
+    const int nstrip = ((H + SY - 1) / SY) * ((W + SX - 1) / SX);
+    const int grid = std::max(1, std::min(nstrip, nsm));
+    {
+        KTimer kt("k_conv_tma", s);
+        k_conv_tma<NOUT, OUT_MAP><<<grid, NTH, L::total, s>>>(tmap, H, W, n->w16 + n->off[l], n->cin[l], n->cout[l],
+                                                               hout, map, n->err);
+    }
+    return check_launch("k_conv_tma");
 }
 
 }  // namespace
@@ -255,10 +435,10 @@ hts_status cnn_forward_tc_into(hts_cnn *n, const float *img, int H, int W, __hal
         return report(HTS_ECUDA, "cudaMemsetAsync(cnn error flag)");
     }
     hts_status st = conv_tc<2, 32, true, false>(n, 0, img, nullptr, H, W, h0, nullptr, nsm, s);
-    if (st == HTS_OK) st = conv_tc<4, 32, false, false>(n, 1, nullptr, h0, H, W, h1, nullptr, nsm, s);
-    if (st == HTS_OK) st = conv_tc<4, 32, false, false>(n, 2, nullptr, h1, H, W, h0, nullptr, nsm, s);
-    if (st == HTS_OK) st = conv_tc<4, 32, false, false>(n, 3, nullptr, h0, H, W, h1, nullptr, nsm, s);
-    if (st == HTS_OK) st = conv_tc<4, 16, false, true>(n, 4, nullptr, h1, H, W, nullptr, map, nsm, s);
+    if (st == HTS_OK) st = conv_tma<32, false>(n, 1, h0, H, W, h1, nullptr, nsm, s);
+    if (st == HTS_OK) st = conv_tma<32, false>(n, 2, h1, H, W, h0, nullptr, nsm, s);
+    if (st == HTS_OK) st = conv_tma<32, false>(n, 3, h0, H, W, h1, nullptr, nsm, s);
+    if (st == HTS_OK) st = conv_tma<16, true>(n, 4, h1, H, W, nullptr, map, nsm, s);
     if (st != HTS_OK) return st;
     {
         KTimer kt("k_map_poison", s);

@@ -1,22 +1,22 @@
 // Collaborative filtering of the precision form on the sm_103a tensor cores
 // (Eq. 19-21, Alg. 1 steps 2-3), FP32 threshold decisions.
 //
-// The separable projection Shat = U^H Phat V of one Fourier slice (Eq. 19) is
-// one 64 x 64 matrix applied to the patch read as a vector:
-//   vec(S)[(a,b)] = sum_(i,j) conj(U[i][a]) V[j][b] vec(Phat)[(i,j)],
-// so a batch of 128 group members (8 groups of K = 16) is one GEMM per slice
-// with the members as the MMA's M = 128 rows: D[m][coefficient] =
-// sum_pixel A[m][pixel] B[coefficient][pixel], FP16 operands, FP32
-// accumulation in tensor memory (tcgen05.mma kind::f16).  Slice 0 is real
-// (N = 64); slice 1 is complex and runs as two real GEMMs with N = 128,
-// [Re S | Im S] = Re Phat [Mr | Mi]^T + Im Phat [-Mi | Mr]^T.  The inverse
-// (Eq. 21) is the conjugate transpose, the same shape of GEMM.  Between the
-// two, the coefficients go through shared memory (transposed, FP32) so that
-// one thread holds a coefficient stream of a group: Haar along the group axis
-// (Eq. 8), hard threshold (Eq. 20, modulus for the complex slice, the group's
-// tau), inverse Haar; then FP16 again as the inverse GEMM's A operand.  The
-// channel DFT (before) and its inverse (after, with the aggregation) run on
-// the CUDA cores.
+// The unitary DFT along the channels (Eq. 4-5) and the separable projection
+// Shat = U^H Phat V of every Fourier slice (Eq. 19) are linear in the patch's
+// raw pixels, so together they are one real orthogonal matrix F (192 x 192
+// for colour, 64 x 64 for gray) applied to the patch read as a vector of its
+// R, G, B pixels, giving [S^(1) | sqrt2 Re S^(2) | sqrt2 Im S^(2)] (slice 3 is
+// the conjugate of slice 2).  A batch of 128 group members (8 groups of K =
+// 16) is one GEMM with the members as the MMA's M = 128 rows: D[m][coefficient]
+// = sum_pixel A[m][pixel] F[coefficient][pixel], FP16 operands, FP32
+// accumulation in tensor memory (tcgen05.mma kind::f16, N = 192).  The
+// inverse (Eq. 21 and the inverse channel DFT) is F^T: the same shared-memory
+// matrix read with the transpose bit (MN-major), giving the R, G, B pixels of
+// every member directly.  Between the two, the coefficients go through shared
+// memory (transposed, FP32) so that one thread holds a coefficient stream of a
+// group: Haar along the group axis (Eq. 8), hard threshold (Eq. 20, modulus
+// for the complex slice, the group's tau), inverse Haar; then FP16 again as
+// the inverse GEMM's A operand.
 //
 // FP16 rather than BF16: pixels lie in a bounded range and the bases are
 // orthonormal, so FP16's 11-bit significand fits the data, where BF16's 8
@@ -45,7 +45,6 @@ namespace hts {
 namespace {
 
 using fc::K3F;
-using fc::S3H;
 
 // The Haar transform of Eq. 8 without its 1/sqrt(2) factors: sums and differences only.  In the row
 // order of Eq. 8 (row 0 the sum, then the difference rows coarse to fine) coefficient k has passed
@@ -107,14 +106,11 @@ __device__ __forceinline__ int cm_off(int r, int k) { return (((r >> 3) << 3) + 
 template <int C>
 struct FtcLayout {
     static constexpr int NBLK = (C == 3) ? 3 : 1;  // 64-column blocks of the member operand
-    // FP16 Kronecker matrices (halves): B0 [coefficient][pixel] and B0I [pixel][coefficient] of slice 0;
-    // C == 3: BF = [Mr; Mi; -Mi] [coefficient][pixel] and BI = [Mr^T; Mi^T; -Mi^T] [pixel][coefficient]
-    // of slice 1 (192 rows each)
-    static constexpr int B0 = 0;
-    static constexpr int BF = 64 * 64;
-    static constexpr int B0I = (C == 3) ? BF + 192 * 64 : 64 * 64;
-    static constexpr int BI = B0I + 64 * 64;
-    static constexpr int B_HALVES = (C == 3) ? BI + 192 * 64 : 2 * 64 * 64;
+    // The FP16 transform F [coefficient][pixel] (CK x CK, CK = 64 C), K-major, core matrices of 8 rows x 8
+    // columns, 8-column groups 128 B apart along K and 8-row groups CK * 16 B apart: the forward GEMM's B
+    // operand, and with the transpose bit (K = coefficients, N = pixels, MN-major) the inverse's.
+    static constexpr int CK = 64 * C;
+    static constexpr int B_HALVES = CK * CK;
     static constexpr size_t a_off = 0;                               // [NBLK][128][64] FP16
     static constexpr size_t b_off = a_off + (size_t)NBLK * MB * 64 * 2;
     static constexpr size_t t_off = b_off + (size_t)B_HALVES * 2;    // [64][TS] FP32
@@ -173,22 +169,28 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
         }
     }
     __syncthreads();
-    for (int e = tid; e < 64 * 64; e += NT) {
-        const int n = e >> 6, k = e & 63;  // n = coefficient (a, b), k = pixel (i, j)
-        const int ia = (k >> 3) * 8 + (n >> 3), jb = (k & 7) * 8 + (n & 7);
-        const float m0 = sBas[ia] * sBas[64 + jb];  // U0[i][a] V0[j][b]
-        sB[L::B0 + cm_off(n, k)] = __float2half_rn(m0);
-        sB[L::B0I + cm_off(k, n)] = __float2half_rn(m0);
-        if (C == 3) {
+    // F: the unitary DFT along the channels (Eq. 4-5) followed by the slices' projections (Eq. 19), as one real
+    // orthogonal map of the raw R, G, B pixels (column t * 64 + (i, j)) to [S^(1) | sqrt2 Re S^(2) |
+    // sqrt2 Im S^(2)] (row (a, b), 64 + (a, b), 128 + (a, b)); its inverse (Eq. 21) is its transpose.
+    // Slice 1: P^(1) = (R + w G + w^2 B) / sqrt3, w = exp(-2 pi i / 3), projected by conj(U1[i][a]) V1[j][b].
+    constexpr int CK = L::CK;
+    for (int e = tid; e < CK * CK; e += NT) {
+        const int n = e / CK, k = e - n * CK;  // n: coefficient row, k: channel t = k / 64, pixel (i, j)
+        const int t = k >> 6, px = k & 63, nc = n & 63, sl = n >> 6;
+        const int ia = (px >> 3) * 8 + (nc >> 3), jb = (px & 7) * 8 + (nc & 7);
+        float f;
+        if (sl == 0) {
+            f = sBas[ia] * sBas[64 + jb];  // U0[i][a] V0[j][b]
+            if (C == 3) f *= K3F;
+        } else {
             const float ur = sBas[128 + ia], ui = sBas[192 + ia], vr = sBas[256 + jb], vi = sBas[320 + jb];
             const float mr = ur * vr + ui * vi, mi = ur * vi - ui * vr;  // conj(U1[i][a]) V1[j][b]
-            sB[L::BF + cm_off(n, k)] = __float2half_rn(mr);
-            sB[L::BF + cm_off(64 + n, k)] = __float2half_rn(mi);
-            sB[L::BF + cm_off(128 + n, k)] = __float2half_rn(-mi);
-            sB[L::BI + cm_off(k, n)] = __float2half_rn(mr);
-            sB[L::BI + cm_off(64 + k, n)] = __float2half_rn(mi);
-            sB[L::BI + cm_off(128 + k, n)] = __float2half_rn(-mi);
+            // channel weights of Re and Im of P^(1): (1, -1/2, -1/2) / sqrt3 and (0, -1/2, 1/2)
+            const float cr = (t == 0) ? K3F : -0.5f * K3F, ci = (t == 0) ? 0.f : (t == 1 ? -0.5f : 0.5f);
+            const float v = (sl == 1) ? (mr * cr - mi * ci) : (mr * ci + mi * cr);
+            f = v * 1.41421356237309505f;
         }
+        sB[(((n >> 3) * (CK / 8) + (k >> 3)) << 6) + ((n & 7) << 3) + (k & 7)] = __float2half_rn(f);
     }
     if (tid == 0) {
         tc::bar_init(bar, 1);
@@ -199,7 +201,8 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = *slot;
-    const uint32_t id64 = tc::idesc_f16(MB, 64, false);
+    const uint32_t idf = tc::idesc_f16(MB, L::CK, false);                 // forward: B K-major
+    const uint32_t idi = tc::idesc_f16(MB, L::CK, false) | (1u << 16);    // inverse: B transposed (MN-major)
     const int q = warp & 3, wq = warp >> 2;  // tensor-memory lane quarter, column quarter
     const uint32_t tlane = (uint32_t)(32 * q) << 16;
     uint32_t phase = 0;
@@ -213,30 +216,16 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
         if (tid == 0) {
             tc::fence_after();
             const uint32_t a0 = tc::su32(sA), b0 = tc::su32(sB);
-            const int bs = inverse ? L::B0I : L::B0;
+            // A: [NBLK][128][64] K-major (K step kk: block kk / 4, two core matrices at (kk % 4) * 256 B).
+            // Forward B = F: K = pixels, core matrices 128 B apart along K, CK * 16 B along N (coefficients).
+            // Inverse B = F^T read in place: K = coefficients (core matrices CK * 16 B apart: LBO), N = pixels
+            // (128 B apart: SBO), the MN-major convention.
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)
-                tc::mma_f16(tbase, tc::sdesc(a0 + kk * 256, 128, 1024), tc::sdesc(b0 + bs * 2 + kk * 256, 128, 1024),
-                            id64, kk > 0 ? 1u : 0u);
-            if (C == 3) {
-                // rows 0, 64, 128 of BF / BI hold Mr, Mi, -Mi (resp. their transposes); A blocks 1 and 2 hold
-                // Re, Im of slice 1 (pixels forward, coefficients inverse).  Forward:
-                //   Re S = Re P Mr^T + Im P (-Mi)^T,  Im S = Re P Mi^T + Im P Mr^T;
-                // inverse: Re P = Re S Mr + Im S Mi,  Im P = Re S (-Mi) + Im S Mr.
-                const int bb = inverse ? L::BI : L::BF;
-                const int re_a = 0, re_b = inverse ? 64 : 128, im_a = inverse ? 128 : 64, im_b = 0;
-                auto chain = [&](uint32_t dcol, int r1, int r2) {
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        tc::mma_f16(tbase + dcol, tc::sdesc(a0 + MB * 64 * 2 + kk * 256, 128, 1024),
-                                    tc::sdesc(b0 + (bb + r1 * 64) * 2 + kk * 256, 128, 1024), id64, kk > 0 ? 1u : 0u);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        tc::mma_f16(tbase + dcol, tc::sdesc(a0 + 2 * MB * 64 * 2 + kk * 256, 128, 1024),
-                                    tc::sdesc(b0 + (bb + r2 * 64) * 2 + kk * 256, 128, 1024), id64, 1u);
-                };
-                chain(64, re_a, re_b);
-                chain(128, im_a, im_b);
+            for (int kk = 0; kk < CK / 16; ++kk) {
+                const uint64_t ad = tc::sdesc(a0 + (kk >> 2) * (MB * 64 * 2) + (kk & 3) * 256, 128, 1024);
+                const uint64_t bd = inverse ? tc::sdesc(b0 + kk * 2 * (CK * 16), CK * 16, 128)
+                                            : tc::sdesc(b0 + kk * 256, 128, CK * 16);
+                tc::mma_f16(tbase, ad, bd, inverse ? idi : idf, kk > 0 ? 1u : 0u);
             }
             tc::mma_commit(bar);
         }
@@ -300,20 +289,14 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
                 for (int c = 0; c < C; ++c) pf[it][c] = pos >= 0 ? __ldg(src + c * HW) : 0.f;
             }
         };
-        // registers -> Fourier slices of the channel axis (unitary DFT), FP16, member rows of the operand
+        // registers -> FP16, member rows of the operand (channel c in block c; F applies the channel DFT)
         auto commit = [&]() {
 #pragma unroll
             for (int it = 0; it < NPF; ++it) {
                 const int m = 4 * (2 * it + g_mh) + g_ml;
                 const int o = cm_off(m, g_row * 8 + g_px);
-                if constexpr (C == 1) {
-                    sA[o] = __float2half_rn(pf[it][0]);
-                } else {
-                    const float R = pf[it][0], G = pf[it][C - 2], B = pf[it][C - 1];
-                    sA[o] = __float2half_rn(((R + G) + B) * K3F);
-                    sA[MB * 64 + o] = __float2half_rn((R - 0.5f * (G + B)) * K3F);
-                    sA[2 * MB * 64 + o] = __float2half_rn((B - G) * 0.5f);
-                }
+#pragma unroll
+                for (int c = 0; c < C; ++c) sA[c * MB * 64 + o] = __float2half_rn(pf[it][c]);
             }
         };
         setup(0, 0);
@@ -332,7 +315,7 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
             commit();
             if (b + 1 < nbatch) setup(b + 1, cur ^ 1);  // read after the next batch's first barrier
             if (b >= 1 && b + 1 < nbatch && tid < MB) sPos[MB * (cur ^ 1) + tid] = posreg;  // batch b + 1
-            // ---- forward projection (Eq. 19): D[m] = [S0 | Re S1 | Im S1]
+            // ---- forward transform (Eq. 4-5, 19): D[m] = [S0 | sqrt2 Re S1 | sqrt2 Im S1]
             if (!run_stage(false)) {
                 ok = false;
                 break;
@@ -393,10 +376,11 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
                             x[k] = (fabsf(x[k]) >= tl) ? x[k] * (1.f / (float)(1 << l)) : 0.f;
                         }
                     } else {
-                        // modulus test on squares: re^2 + im^2 >= tau^2 2^l (lanes 2i, 2i + 1 hold the real and
-                        // imaginary stream of one coefficient; the sum is formed in one order on both)
+                        // modulus test on squares: the streams hold sqrt2 Re and sqrt2 Im (F's rows), so
+                        // |S| >= tau iff re^2 + im^2 >= 2 tau^2 2^l (lanes 2i, 2i + 1 hold the real and imaginary
+                        // stream of one coefficient; the sum is formed in one order on both)
                         const bool im = s2 & 1;
-                        const float tau2 = tau * tau;
+                        const float tau2 = 2.f * tau * tau;
 #pragma unroll
                         for (int k = 0; k < K; ++k) {
                             const int l = haar_level<K>(k);
@@ -428,12 +412,12 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
                 tc::fence_before();
                 __syncthreads();
             }
-            // ---- inverse projection (Eq. 21): D[m] = [Phat0 | Re Phat1 | Im Phat1]
+            // ---- inverse transform (Eq. 21 and the inverse channel DFT): D[m] = [R | G | B] pixels
             if (!run_stage(true)) {
                 ok = false;
                 break;
             }
-            // ---- inverse DFT along the channels and aggregation: member m = 32 q + lane, patch rows
+            // ---- aggregation: member m = 32 q + lane, patch rows
             //      2 wq, 2 wq + 1
             {
                 const int m = 32 * q + lane;
@@ -455,17 +439,13 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
                     }
                     tc::tmem_wait_ld();
                     if (pos < 0) continue;
-                    float out[C][8];
+                    float out[C][8];  // the inverse transform (F^T) gives the channels' pixels directly
 #pragma unroll
                     for (int v = 0; v < 8; ++v) {
-                        const float f0 = __uint_as_float(p0[v]);
-                        if constexpr (C == 1) {
-                            out[0][v] = f0;
-                        } else {
-                            const float fr = __uint_as_float(p1[v]), fi = __uint_as_float(p2[v]);
-                            out[0][v] = (f0 + 2.f * fr) * K3F;
-                            out[1][v] = (f0 - fr - 2.f * S3H * fi) * K3F;
-                            out[2][v] = (f0 - fr + 2.f * S3H * fi) * K3F;
+                        out[0][v] = __uint_as_float(p0[v]);
+                        if constexpr (C == 3) {
+                            out[1][v] = __uint_as_float(p1[v]);
+                            out[2][v] = __uint_as_float(p2[v]);
                         }
                     }
                     if (mrow) {  // first Haar row replaced (Eq. 24-25): the refined mean joins every member

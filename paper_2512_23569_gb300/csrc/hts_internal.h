@@ -77,8 +77,9 @@ hts_status report(hts_status s, const char *msg);
 hts_status device_status(int err);
 
 // Launch bookkeeping (defined in api.cu).  Every kernel launch sits inside a
-// KTimer scope: it counts the launch and, while profiling is on, records a
-// CUDA event before and after it on the launch stream.
+// KTimer scope: it counts the launch, opens an NVTX range named after the
+// kernel (seen by profilers; a no-op without one) and, while profiling is on,
+// records a CUDA event before and after it on the launch stream.
 void count_launch();
 void count_launches(unsigned long long n);
 hts_status check_launch(const char *what);
@@ -100,6 +101,9 @@ inline cudaError_t dev_malloc(T **p, size_t bytes) {
 }
 // True while `s` is capturing into a CUDA graph.
 bool stream_capturing(cudaStream_t s);
+// cuTensorMapEncodeTiled of the driver (the library links only the runtime), as a
+// PFN_cuTensorMapEncodeTiled_v12000; nullptr if the driver does not provide it.
+void *tensor_map_encoder();
 
 // Largest shared memory a block may opt in to on the current device.
 int smem_optin();
@@ -108,6 +112,7 @@ int smem_optin();
 hts_status allow_smem(const void *func, size_t need);
 struct KTimer {
     int slot;
+    bool range;  // an NVTX range was opened (launches outside stream captures)
     cudaStream_t stream;
     KTimer(const char *name, cudaStream_t s);
     ~KTimer();

@@ -51,9 +51,12 @@
 // queue their own position as their whole group (valid positions for the
 // kernels that read the groups; the call reports HTS_ETIMEOUT where it reads
 // the state back), releases its tensor memory and leaves.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "hts_internal.h"
 #include "tc_ptx.h"
@@ -75,6 +78,7 @@ constexpr int NWC = 8;               // reading warps: warp w takes lanes 32 (w 
 constexpr int NT = (NWC + 1) * 32;   // + one warp that issues the MMAs
 
 struct TcArgs {
+    CUtensorMap tmap;  // the image as [C][H][W] FP32, box (tma_bw, tma_bh, 1): one channel's candidate region
     const float *img;
     int H, W, C, step, R, nx, ny, nref;
     int32_t *idx;
@@ -84,6 +88,8 @@ struct TcArgs {
     int ntx, nty, ntiles;
     int hc_max, wc_max;  // bounds of the candidate region over all tiles
     int inject_wait;     // 1: the issuing thread first waits, briefly, on a barrier nothing arrives on
+    int use_tma;         // 1: the candidate region is staged by TMA (else by loads)
+    int tma_bw, tma_bh;  // the TMA box: columns (a multiple of 4, from a column multiple of 4) and rows
 };
 
 // LH: keys each thread keeps and the number re-ranked in FP32 per reference;
@@ -130,7 +136,7 @@ __host__ __device__ inline TcLayout tc_layout(int hc_max, int wc_max) {
     L.ref = up(L.scr + nq * 4, 16);
     L.qr = L.ref + (size_t)NR * sizeof(RefRec);
     L.bar = up(L.qr + NQ * sizeof(int2), 16);
-    L.total = L.bar + (2 * NBUF + 1) * 8 + 16;
+    L.total = L.bar + (2 * NBUF + 2) * 8 + 16;
     // one block per SM, and never beside a block of the other tensor-core kernels (whose tensor
     // memory would not fit beside this block's 512 columns)
     if (L.total < 160 * 1024) L.total = 160 * 1024;
@@ -179,7 +185,7 @@ __device__ __forceinline__ void self_group(const TcArgs &a, int r, int self) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
+__global__ void __launch_bounds__(NT, 1) k_match_tc(const __grid_constant__ TcArgs a) {
     constexpr int LH = ListCfg<K>::LH, T = ListCfg<K>::T, KC = ListCfg<K>::KC, NBIN = ListCfg<K>::NBIN;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const TcLayout L = tc_layout<K>(a.hc_max, a.wc_max);
@@ -196,7 +202,8 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + L.bar);  // [NBUF]: the run's MMAs completed
     uint64_t *empty = full + NBUF;                                    // [NBUF]: every warp loaded the run
     uint64_t *never = empty + NBUF;  // no thread arrives on it (the injected wait)
-    int *abort_flag = reinterpret_cast<int *>(never + 1);
+    uint64_t *tbar = never + 1;      // the TMA copies of an item's region landed
+    int *abort_flag = reinterpret_cast<int *>(tbar + 1);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(abort_flag + 1);
     int *item_slot = reinterpret_cast<int *>(tmem_slot + 1);  // the block's current work item
 
@@ -211,6 +218,7 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
             tc::bar_init(&empty[b], NWC);
         }
         tc::bar_init(never, 1);
+        tc::bar_init(tbar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -221,12 +229,16 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
     const uint32_t tbase = *tmem_slot;
     const uint32_t idesc = tc::idesc_f16(NR, CH, true);
     long long gc = 0;  // runs issued by this block so far (accumulator gc % NBUF, use gc / NBUF)
+    uint32_t tphase = 0;  // TMA stagings so far (the parity of tbar's next phase)
+    volatile int *abortp = abort_flag;
     bool ok = true;
 
     const int npass = (a.C == 3) ? 2 : 1;
     while (true) {
         // next item of the work queue: (tile, plane pass), so that the two passes of a colour tile run
-        // on two SMs and blocks that drew passes without references move on at once
+        // on two SMs and blocks that drew passes without references move on at once.  The fence orders this
+        // thread's earlier shared-memory accesses before the next item's TMA writes into the same area.
+        tc::fence_async_smem();
         if (tid == 0) *item_slot = atomicAdd(&a.st->mtc_next, 1);
         __syncthreads();
         const int item = *item_slot;
@@ -293,15 +305,47 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
                 continue;
             }
             // ---- stage the plane (FP32), the row-8 vectors and their norms, E, A
+            if (a.use_tma) {
+                // the channels the plane needs, each a box of the image from column cx0 rounded down to a
+                // multiple of 4 (16 bytes), into the free area of Q; zero outside the image
+                const int nch = (a.C == 3 && pass == 1) ? 3 : 1;  // pass 1: R + G + B
+                const int ch0 = (a.C == 3 && pass == 0) ? 1 : 0;
+                const int xs = cx0 & 3, bsz = (a.tma_bw * a.tma_bh + 31) & ~31;  // 128-byte aligned boxes
+                float *stg = reinterpret_cast<float *>(smem_raw + L.q);
+                if (tid == 0) {
+                    tc::bar_arrive_expect_tx(tbar, (uint32_t)(nch * a.tma_bw * a.tma_bh * 4));  // the boxes' bytes
+                    for (int c = 0; c < nch; ++c)
+                        tc::tma_load_3d(stg + c * bsz, &a.tmap, tbar, cx0 - xs, cy0, ch0 + c);
+                }
+                const bool landed = tc::bar_wait_or_abort(tbar, (uint32_t)(tphase & 1), SPIN, abortp);
+                ++tphase;
+                if (!__all_sync(FULLM, landed)) {
+                    // the copy must land before the area is used again; the item fails as a bounded wait does
+                    if (tid == 0) tc::bar_wait(tbar, (uint32_t)((tphase - 1) & 1), SPIN);
+                }
+                if (__syncthreads_or(*abortp)) {
+                    if (tid == 0) atomicExch(&a.st->error, 2);
+                    ok = false;
+                    self_groups();
+                    continue;
+                }
 #pragma unroll 4
-            for (int e = tid; e < (Hc + 7) * PSW; e += NT) {
-                const int y = e / PSW, x = e - y * PSW;
-                const size_t o = (size_t)(cy0 + y) * a.W + cx0 + x;
-                float v;
-                if (a.C == 1) v = __ldg(a.img + o);
-                else if (pass == 0) v = __ldg(a.img + HW + o);
-                else v = (__ldg(a.img + o) + __ldg(a.img + HW + o)) + __ldg(a.img + 2 * HW + o);
-                Ps[e] = v;
+                for (int e = tid; e < (Hc + 7) * PSW; e += NT) {
+                    const int y = e / PSW, x = e - y * PSW;
+                    const int o = y * a.tma_bw + x + xs;
+                    Ps[e] = (nch == 1) ? stg[o] : (stg[o] + stg[bsz + o]) + stg[2 * bsz + o];
+                }
+            } else {
+#pragma unroll 4
+                for (int e = tid; e < (Hc + 7) * PSW; e += NT) {
+                    const int y = e / PSW, x = e - y * PSW;
+                    const size_t o = (size_t)(cy0 + y) * a.W + cx0 + x;
+                    float v;
+                    if (a.C == 1) v = __ldg(a.img + o);
+                    else if (pass == 0) v = __ldg(a.img + HW + o);
+                    else v = (__ldg(a.img + o) + __ldg(a.img + HW + o)) + __ldg(a.img + 2 * HW + o);
+                    Ps[e] = v;
+                }
             }
             __syncthreads();
             for (int qi = tid; qi < nq; qi += NT) {
@@ -376,7 +420,6 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(TcArgs a) {
 #pragma unroll
                 for (int t = 0; t < T; ++t) bn[g][t] = 0xffffffffu;
             uint32_t ev = 0xffffffffu;  // smallest key a full bin pushed out
-            volatile int *abortp = abort_flag;
             if (!cw) {  // the issuing warp: run c goes into its accumulator once run c - NBUF was loaded by all
                 if (lane == 0) {
                     int issued = 0;
@@ -610,6 +653,36 @@ hts_status launch_match_tc(const float *img, const Geom &g, double gamma_gcp, in
     a.hc_max = std::min(g.H - PS + 1, (TTY - 1) * g.step + 1 + 2 * g.R);
     a.wc_max = std::min(g.W - PS + 1, (TTX - 1) * g.step + 1 + 2 * g.R);
     a.inject_wait = (!stream_capturing(s) && fault_take(FAULT_WAIT)) ? 1 : 0;
+    // TMA staging of the candidate regions: one channel's region is a box of the image tensor [C][H][W]
+    // starting at a column multiple of 4 (16 bytes), so the box is 3 columns wider than the widest region;
+    // used where the rows are 16-byte multiples and the boxes of all channels fit in the area of Q
+    a.use_tma = 0;
+    a.tma_bw = ((a.wc_max + 7 + 3) + 3) & ~3;
+    a.tma_bh = a.hc_max + 7;
+    std::memset(&a.tmap, 0, sizeof(a.tmap));
+    {
+        size_t qarea = 0;
+        switch (g.K) {
+            case 2: qarea = tc_layout<2>(a.hc_max, a.wc_max).a; break;
+            case 4: qarea = tc_layout<4>(a.hc_max, a.wc_max).a; break;
+            case 8: qarea = tc_layout<8>(a.hc_max, a.wc_max).a; break;
+            case 16: qarea = tc_layout<16>(a.hc_max, a.wc_max).a; break;
+            default: qarea = tc_layout<32>(a.hc_max, a.wc_max).a; break;
+        }
+        const size_t box = (size_t)((a.tma_bw * a.tma_bh + 31) & ~31) * 4;
+        const auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
+        if (enc && g.W % 4 == 0 && (reinterpret_cast<uintptr_t>(img) & 15) == 0 && a.tma_bw <= 256 &&
+            a.tma_bh <= 256 && (size_t)g.C * box <= qarea) {
+            const cuuint64_t dims[3] = {(cuuint64_t)g.W, (cuuint64_t)g.H, (cuuint64_t)g.C};
+            const cuuint64_t strides[2] = {(cuuint64_t)g.W * 4, (cuuint64_t)g.H * g.W * 4};
+            const cuuint32_t boxd[3] = {(cuuint32_t)a.tma_bw, (cuuint32_t)a.tma_bh, 1};
+            const cuuint32_t estr[3] = {1, 1, 1};
+            if (enc(&a.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(img), dims, strides, boxd, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+                a.use_tma = 1;
+        }
+    }
     hts_status st0 = HTS_EUNSUPPORTED;
     switch (g.K) {
         case 2: st0 = launch_tc<2>(a, s); break;

@@ -82,6 +82,22 @@ __device__ __forceinline__ bool bar_wait_or_abort(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// One arrival on the mbarrier that also announces `bytes` of asynchronous copies (TMA) completing on it.
+__device__ __forceinline__ void bar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+
+// TMA: a 3-D box of the tensor described by *tmap (a CUtensorMap kernel parameter) at coordinates
+// (c0, c1, c2), innermost first, into shared memory at dst (128-byte aligned); the bytes complete on the
+// mbarrier.  Out-of-range elements read as zero.
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, uint64_t *bar, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(c2), "r"(su32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 // Generic-proxy writes to shared memory made visible to the tensor cores (before a barrier).
