@@ -581,10 +581,11 @@ def pixel_errors(got, want, clean):
             "psnr_db": ps, "psnr_oracle_db": po, "psnr_delta_db": ps - po}
 
 
-def _timed(fn, args, stream, flush, local, world):
+def _timed(fn, args, stream, flush, local, world, label="timed"):
     """W warm-up and K timed calls of fn (barrier + synchronize on both sides, CUDA events on the launching
     stream, L2 flushed between steps outside the events, kernels bracketed by the library's events); the step
-    time is the max over ranks."""
+    time is the max over ranks.  The timed calls sit in an NVTX range named `label` (profilers can select
+    them: ncu --nvtx --nvtx-include "<label>/")."""
     import torch
 
     from paper_2512_23569_gb300 import dist as hd
@@ -601,11 +602,16 @@ def _timed(fn, args, stream, flush, local, world):
     clocks.start()
     l0 = hts.launch_count()
     hts.profile_begin()
+    torch.cuda.nvtx.range_push(label)
+    host_ms = []
     for i in range(args.steps):
         flush.zero_()
         evs[i][0].record(stream)
+        t0 = time.perf_counter()
         fn()
+        host_ms.append(1e3 * (time.perf_counter() - t0))
         evs[i][1].record(stream)
+    torch.cuda.nvtx.range_pop()
     prof = hts.profile_end()
     torch.cuda.synchronize()
     launches = hts.launch_count() - l0
@@ -617,7 +623,8 @@ def _timed(fn, args, stream, flush, local, world):
     tot = sum(v[0] for v in prof.values()) or 1e-9
     kernels = {k: {"ms_per_launch": v[0] / max(v[1], 1), "launches_per_step": v[1] / args.steps,
                    "share": v[0] / tot} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
-    return {"ms": max_ms / args.steps, "kernels": kernels, "launches": int(launches), "clocks": clk}
+    return {"ms": max_ms / args.steps, "kernels": kernels, "launches": int(launches), "clocks": clk,
+            "host_call_ms": {"median": statistics.median(host_ms), "max": max(host_ms)}}
 
 
 def _kernel_rooflines(kernels, H, W, C, K, win, step, green):
@@ -668,7 +675,7 @@ def run_learned4k(args):
     stream = torch.cuda.current_stream()
     t_start = time.perf_counter()
     p1 = hts.params(K=w["K"], win=w["win"], step=w["step"], precision=1)
-    net, train_info = train_network(p1, ncrop=w["train_crops"],
+    net, train_info = train_network(p1, ncrop=args.train_crops,
                                     workers=max(1, min(16, (os.cpu_count() or 1) // max(1, world))))
     clean, noisy, spx = learned_image(rank)
     truth = synth.ref_log_sigma(spx)
@@ -680,13 +687,14 @@ def run_learned4k(args):
     for prec in (1, 2):
         p = hts.params(K=w["K"], win=w["win"], step=w["step"], precision=prec)
         r = _timed(lambda: hts.denoise_learned(x, net, p, fallback_factor=factor, out=out), args, stream, flush,
-                   local, world)
+                   local, world, label="timed_learned_p%d" % prec)
         r["stats"] = hts.last_stats()
         r["out"] = out.cpu().numpy()
         r["p"] = p
         forms["learned_p%d" % prec] = r
     p0 = hts.params(K=w["K"], win=w["win"], step=w["step"], precision=0)
-    plain = _timed(lambda: hts.denoise(x, sigma=None, p=p0, out=out), args, stream, flush, local, world)
+    plain = _timed(lambda: hts.denoise(x, sigma=None, p=p0, out=out), args, stream, flush, local, world,
+                   label="timed_plain")
     plain["stats"] = hts.last_stats()
     plain["out"] = out.cpu().numpy()
     # the noise levels the learned forms used (the map, or the estimate where the judge fell back)
@@ -745,7 +753,8 @@ def run_learned4k(args):
         "dtype": "bf16 matching / f16 filter / f16 network (f32 accumulate)" if chosen == "learned_p1"
                  else "f32 matching / f16 filter / f16 network (f32 accumulate)",
         "data": "synthetic",
-        "config": dict(w, parallelism="replicas: one image per rank" if world > 1 else "single GPU"),
+        "config": dict(w, train_crops=args.train_crops,
+                       parallelism="replicas: one image per rank" if world > 1 else "single GPU"),
         "chosen_form": chosen, "chosen_precision": pc.precision,
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -759,7 +768,10 @@ def run_learned4k(args):
                       "learned_ratio": v["stats"]["learned_ratio"], "gpu_launches": v["launches"],
                       "clocks_sm_mhz": v["clocks"]["sm_mhz"],
                       "stats": {q: v["stats"][q] for q in ("match_reranked", "match_fallback", "vote_uncertain",
-                                                           "filter_redo", "filter_exact", "sigma")}}
+                                                           "filter_redo", "filter_exact", "sigma")},
+                      "kernels_ms": {kk: vv["ms_per_launch"] * vv["launches_per_step"]
+                                     for kk, vv in list(v["kernels"].items())[:8]},
+                      "host_call_ms": v["host_call_ms"]}
                   for k, v in forms.items()},
         "plain": {"form": FORMS[0] + ", one estimated sigma", "value": world * H * W / (plain["ms"] / 1e3) / 1e6,
                   "ms_per_step": plain["ms"], "psnr_db": synth.psnr(plain["out"], clean),
@@ -1107,6 +1119,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="leave the other workloads out of the default line")
+    ap.add_argument("--train-crops", type=int, default=WORKLOAD["train_crops"],
+                    help="training crops of the learned workload's network (the workload's configuration: 4096)")
     ap.add_argument("--workload", choices=["learned4k", "colour512", "batch64", "precision1024", "cnn"],
                     default="learned4k",
                     help="learned4k (default): the learned form on 3840x2160x3; colour512: the colour 512x512x3 "

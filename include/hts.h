@@ -215,6 +215,10 @@ typedef struct {
     int kernels;   /* kernel launches per graph launch */
     int captures;  /* graph captures made for this signature so far */
     int updates;   /* in-place graph updates (new pointers / sigma) so far */
+    int phased;    /* 1: every image is in a tensor-core form (precision 1 or 2), and the tensor-core
+                    * matcher and filter each run as one persistent launch per group of images (same K;
+                    * filter: same C and K) over a device work queue of (image, tile) items, between
+                    * the per-image steps on the lanes; 0: one pipeline per image on the lanes */
 } hts_batch_info;
 
 /* Filter tile shape chosen by the autotuner for this geometry (*ty x *tx

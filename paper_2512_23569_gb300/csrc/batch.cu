@@ -78,6 +78,19 @@ struct Plan {
     cudaEvent_t ev_start = nullptr, ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
     // learned form: the networks' forwards run one after another on their own stream, into buffers of
     // the plan sized for the largest image; image i's filter waits for ev_map[i]
+    // phased form (every image on the tensor-core filter): the matcher and the filter run as one launch
+    // per group of images (matcher: same K; filter: same C and K) over a job table in device memory
+    bool phased = false;
+    struct Group {
+        int K = 0, C = 0, first = 0, njobs = 0, nitems = 0, start_off = 0, queue_off = 0;
+    };
+    std::vector<Group> mgroups, fgroups;
+    std::vector<int> mjob_of, fjob_of;            // image -> row of the job tables (-1: none)
+    std::vector<unsigned char> mjob_h, fjob_h;    // the job tables (host copies, uploaded at each capture)
+    std::vector<int> starts_h;                    // every group's item / tile prefix sums, then queue counters
+    unsigned char *mjob_d = nullptr, *fjob_d = nullptr;
+    int *starts_d = nullptr;
+    cudaEvent_t ev_phase[4] = {};
     hts_cnn *net = nullptr;
     cudaStream_t cnn_stream = nullptr;
     cudaEvent_t ev_cnn = nullptr;
@@ -121,6 +134,11 @@ void destroy_plan(Plan *P) {
     cudaFree(P->h16[1]);
     cudaFree(P->cmap);
     cudaFree(P->crows);
+    cudaFree(P->mjob_d);
+    cudaFree(P->fjob_d);
+    cudaFree(P->starts_d);
+    for (cudaEvent_t e : P->ev_phase)
+        if (e) cudaEventDestroy(e);
     cudaSetDevice(prev);
     delete P;
 }
@@ -184,8 +202,96 @@ hts_status create_plan(const Sig &sig, const std::vector<Geom> &geo, const std::
         bufs_carve(geo[i], P->arena + off[i], &P->bufs[i]);
         P->work[i] = (double)geo[i].nref * (geo[i].C == 3 ? 4.0 : 1.0) * geo[i].K;
     }
+    // the phased form: every image in a tensor-core form whose filter takes its geometry
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, sig.device);
+    bool phased = n > 0;
+    std::vector<unsigned char> probe(std::max(filter_tc_job_size(), match_tc_job_size()));
+    for (int i = 0; i < n && phased; ++i)
+        phased = par[i].precision >= 1 &&
+                 filter_tc_job(nullptr, geo[i], nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0.0, nsm,
+                               probe.data()) >= 0;
+    if (phased) {
+        P->phased = true;
+        P->mjob_of.assign(n, -1);
+        P->fjob_of.assign(n, -1);
+        // groups: matcher by K (precision 1 images), filter by (C, K); jobs of a group contiguous
+        for (int pass = 0; pass < 2; ++pass) {
+            auto &groups = pass == 0 ? P->mgroups : P->fgroups;
+            auto &job_of = pass == 0 ? P->mjob_of : P->fjob_of;
+            int row = 0;
+            for (int i = 0; i < n; ++i) {
+                if (job_of[i] >= 0 || (pass == 0 && par[i].precision != 1)) continue;
+                Plan::Group gr;
+                gr.K = geo[i].K;
+                gr.C = pass == 0 ? 0 : geo[i].C;
+                gr.first = row;
+                for (int j = i; j < n; ++j)
+                    if (job_of[j] < 0 && geo[j].K == gr.K && (pass == 0 ? par[j].precision == 1 : geo[j].C == gr.C)) {
+                        job_of[j] = row++;
+                        ++gr.njobs;
+                    }
+                groups.push_back(gr);
+            }
+        }
+        int off2 = 0;
+        for (auto *gs : {&P->mgroups, &P->fgroups})
+            for (auto &gr : *gs) {
+                gr.start_off = off2;
+                off2 += gr.njobs + 1;
+            }
+        for (auto &gr : P->mgroups) gr.queue_off = off2++;
+        P->starts_h.assign(off2, 0);
+        P->mjob_h.assign(std::max<size_t>(1, P->mgroups.empty() ? 0 : n) * match_tc_job_size(), 0);
+        P->fjob_h.assign((size_t)n * filter_tc_job_size(), 0);
+        st = cu(dev_malloc(&P->mjob_d, P->mjob_h.size()), "cudaMalloc(batch job tables)");
+        if (st == HTS_OK) st = cu(dev_malloc(&P->fjob_d, P->fjob_h.size()), "cudaMalloc(batch job tables)");
+        if (st == HTS_OK) st = cu(dev_malloc(&P->starts_d, P->starts_h.size() * sizeof(int)), "cudaMalloc(batch job tables)");
+        for (cudaEvent_t &e : P->ev_phase)
+            if (st == HTS_OK) st = cu(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+        if (st != HTS_OK) {
+            destroy_plan(P);
+            return st;
+        }
+    }
     *out = P;
     return HTS_OK;
+}
+
+// The job tables of the phased form for these image pointers, uploaded to the plan's device copies.
+hts_status upload_jobs(Plan &P, const hts_image *imgs) {
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P.sig.device);
+    const int n = (int)P.geo.size();
+    const size_t ms = match_tc_job_size(), fs = filter_tc_job_size();
+    std::vector<int> items_m(n, 0), items_f(n, 0);  // work items per job-table row
+    for (int i = 0; i < n; ++i) {
+        const Bufs &b = P.bufs[i];
+        const Geom &g = P.geo[i];
+        if (P.mjob_of[i] >= 0)
+            items_m[P.mjob_of[i]] =
+                match_tc_job(imgs[i].noisy, g, b.idx, b.green, b.fb, b.st, P.mjob_h.data() + P.mjob_of[i] * ms);
+        const float *sref = P.net ? b.sref : imgs[i].sigma_map;
+        items_f[P.fjob_of[i]] = filter_tc_job(imgs[i].noisy, g, b.idx, b.b32, b.acc, b.wcount, b.st, sref,
+                                              P.net ? 1 : 0, tau_scale(g, P.par[i]), nsm,
+                                              P.fjob_h.data() + P.fjob_of[i] * fs);
+    }
+    // every group's prefix sums of work items (rows in job-table order)
+    for (int pass = 0; pass < 2; ++pass)
+        for (auto &gr : pass == 0 ? P.mgroups : P.fgroups) {
+            const auto &items = pass == 0 ? items_m : items_f;
+            int acc = 0;
+            for (int j = 0; j < gr.njobs; ++j) {
+                P.starts_h[gr.start_off + j] = acc;
+                acc += items[gr.first + j];
+            }
+            P.starts_h[gr.start_off + gr.njobs] = acc;
+            gr.nitems = acc;
+        }
+    HTS_TRY(cu(cudaMemcpy(P.mjob_d, P.mjob_h.data(), P.mjob_h.size(), cudaMemcpyHostToDevice), "cudaMemcpy(jobs)"));
+    HTS_TRY(cu(cudaMemcpy(P.fjob_d, P.fjob_h.data(), P.fjob_h.size(), cudaMemcpyHostToDevice), "cudaMemcpy(jobs)"));
+    return cu(cudaMemcpy(P.starts_d, P.starts_h.data(), P.starts_h.size() * sizeof(int), cudaMemcpyHostToDevice),
+              "cudaMemcpy(jobs)");
 }
 
 // Lane of every image: largest first, each to the least-loaded lane.
@@ -232,10 +338,100 @@ std::vector<int> work_order(const Plan &P) {
     return order;
 }
 
+// The phased form of the batch on nl lanes: per image on its lane the small steps, and between them the
+// two heavy kernels as single launches over all images (one per group), on the plan's stream:
+//   A  state and sums cleared, Eq. 9 flags, the basis chain and noise floor on the lane's second stream;
+//   B  the tensor-core matcher over every (image, tile, plane pass) of the precision-1 images;
+//   C  rescue (precision 1) or the exact grouping (precision 2), the rank vote, the noise level, the
+//      learned map's check;
+//   D  the tensor-core filter over every (image, tile);
+//   E  the normalisation.
+// Every image's result equals its per-image call, bit for bit (the same kernels on the same work items;
+// integer aggregation).
+hts_status capture_phases(Plan &P, const hts_image *imgs, const std::vector<int> &lane, int nl) {
+    const int n = (int)P.geo.size();
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P.sig.device);
+    auto join_lanes = [&](cudaEvent_t ev) -> hts_status {  // origin waits for every lane, then the lanes for it
+        for (int l = 0; l < nl; ++l) {
+            HTS_TRY(cu(cudaEventRecord(P.ev_lane[l], P.lanes[l]), "cudaEventRecord"));
+            HTS_TRY(cu(cudaStreamWaitEvent(P.origin, P.ev_lane[l], 0), "cudaStreamWaitEvent"));
+        }
+        return cu(cudaEventRecord(ev, P.origin), "cudaEventRecord");
+    };
+    auto lanes_wait = [&](cudaEvent_t ev) -> hts_status {
+        for (int l = 0; l < nl; ++l) HTS_TRY(cu(cudaStreamWaitEvent(P.lanes[l], ev, 0), "cudaStreamWaitEvent"));
+        return HTS_OK;
+    };
+    // A
+    for (int i = 0; i < n; ++i) {
+        const Bufs b = slot(P, i, lane[i]);
+        const Geom &g = P.geo[i];
+        const hts_params &p = P.par[i];
+        cudaStream_t s = P.lanes[lane[i]];
+        const size_t hw = (size_t)g.H * g.W;
+        // as run_image: a map (the network's or the caller's) stands for sigma; only a checked map needs the estimate
+        const float sig = (P.net || imgs[i].sigma_map) ? -1.f : imgs[i].sigma;
+        const bool need_sigma = sig < 0 && (imgs[i].sigma_map == nullptr || P.net);
+        HTS_TRY(cu(cudaMemsetAsync(b.st, 0, sizeof(DevState), s), "cudaMemsetAsync(state)"));
+        HTS_TRY(cu(cudaMemsetAsync(b.acc, 0, hw * g.C * sizeof(long long), s), "cudaMemsetAsync(acc)"));
+        HTS_TRY(cu(cudaMemsetAsync(b.wcount, 0, hw * sizeof(int), s), "cudaMemsetAsync(weights)"));
+        if (p.precision == 1 && g.C == 3) HTS_TRY(launch_gcp_flags(imgs[i].noisy, g, p.gamma_gcp, b.green, s));
+        HTS_TRY(cu(cudaEventRecord(b.ev_fork, s), "cudaEventRecord"));
+        HTS_TRY(cu(cudaStreamWaitEvent(b.aux, b.ev_fork, 0), "cudaStreamWaitEvent"));
+        HTS_TRY(launch_basis(imgs[i].noisy, g, b.cov, b.b64, b.b32, b.eig, b.aux));
+        if (need_sigma) HTS_TRY(launch_sigma_floor(g, p, b.eig, b.st, b.aux));
+        HTS_TRY(cu(cudaEventRecord(b.ev_join, b.aux), "cudaEventRecord"));
+    }
+    HTS_TRY(join_lanes(P.ev_phase[0]));
+    // B
+    for (const auto &gr : P.mgroups)
+        HTS_TRY(launch_match_tc_batch(gr.K, P.mjob_h.data() + gr.first * match_tc_job_size(),
+                                      P.mjob_d + gr.first * match_tc_job_size(), P.starts_d + gr.start_off,
+                                      gr.njobs, gr.nitems, P.starts_d + gr.queue_off, nsm, P.origin));
+    HTS_TRY(cu(cudaEventRecord(P.ev_phase[1], P.origin), "cudaEventRecord"));
+    HTS_TRY(lanes_wait(P.ev_phase[1]));
+    // C
+    for (int i = 0; i < n; ++i) {
+        const Bufs b = slot(P, i, lane[i]);
+        const Geom &g = P.geo[i];
+        const hts_params &p = P.par[i];
+        cudaStream_t s = P.lanes[lane[i]];
+        const float sig = (P.net || imgs[i].sigma_map) ? -1.f : imgs[i].sigma;
+        const bool need_sigma = sig < 0 && (imgs[i].sigma_map == nullptr || P.net);
+        if (p.precision == 1) HTS_TRY(launch_match_rescue(imgs[i].noisy, g, b.idx, b.green, b.fb, b.st, s));
+        else HTS_TRY(launch_match(imgs[i].noisy, g, p.gamma_gcp, b.idx, b.green, b.fb, b.st, s));
+        if (need_sigma && p.adjust_rank) HTS_TRY(launch_sigma_vote(imgs[i].noisy, g, p, b.idx, b.redo, b.st, s));
+        HTS_TRY(cu(cudaStreamWaitEvent(s, b.ev_join, 0), "cudaStreamWaitEvent"));
+        if (need_sigma) HTS_TRY(launch_sigma_final(g, p, b.st, s));
+        else HTS_TRY(launch_set_sigma(sig > 0 ? (double)sig : 0.0, g, p, b.st, s));
+        if (P.net) {
+            HTS_TRY(cu(cudaStreamWaitEvent(s, P.ev_map[i], 0), "cudaStreamWaitEvent"));
+            HTS_TRY(launch_learned_check(b.sref, g.nref, P.sig.factor, b.st, s));
+        }
+    }
+    HTS_TRY(join_lanes(P.ev_phase[2]));
+    // D
+    for (const auto &gr : P.fgroups)
+        HTS_TRY(launch_filter_tc_batch(gr.C, gr.K, P.fjob_h.data() + gr.first * filter_tc_job_size(),
+                                       P.fjob_d + gr.first * filter_tc_job_size(), P.starts_d + gr.start_off,
+                                       gr.njobs, gr.nitems, nsm, P.origin));
+    HTS_TRY(cu(cudaEventRecord(P.ev_phase[3], P.origin), "cudaEventRecord"));
+    HTS_TRY(lanes_wait(P.ev_phase[3]));
+    // E
+    for (int i = 0; i < n; ++i) {
+        const Bufs b = slot(P, i, lane[i]);
+        const Geom &g = P.geo[i];
+        HTS_TRY(launch_normalize_box(b.acc, b.wcount, imgs[i].out, g.H, g.W, g.C, P.lanes[lane[i]]));
+    }
+    return HTS_OK;
+}
+
 // Records the whole batch on nl lanes into a new graph.
 hts_status capture(Plan &P, const hts_image *imgs, int nl, cudaGraph_t *out, unsigned long long *kernels) {
     const int n = (int)P.geo.size();
     const std::vector<int> lane = assign_lanes(P, nl);
+    if (P.phased) HTS_TRY(upload_jobs(P, imgs));
     reset_captured_launches();
     HTS_TRY(cu(cudaStreamBeginCapture(P.origin, cudaStreamCaptureModeRelaxed), "cudaStreamBeginCapture"));
     hts_status st = cu(cudaEventRecord(P.ev_start, P.origin), "cudaEventRecord");
@@ -250,7 +446,11 @@ hts_status capture(Plan &P, const hts_image *imgs, int nl, cudaGraph_t *out, uns
         }
         if (st == HTS_OK) st = cu(cudaEventRecord(P.ev_cnn, P.cnn_stream), "cudaEventRecord");
     }
-    for (int i = 0; i < n && st == HTS_OK; ++i) st = run_image(P, imgs, i, slot(P, i, lane[i]), P.lanes[lane[i]]);
+    if (P.phased) {
+        if (st == HTS_OK) st = capture_phases(P, imgs, lane, nl);
+    } else {
+        for (int i = 0; i < n && st == HTS_OK; ++i) st = run_image(P, imgs, i, slot(P, i, lane[i]), P.lanes[lane[i]]);
+    }
     for (int l = 0; l < nl && st == HTS_OK; ++l) {
         st = cu(cudaEventRecord(P.ev_lane[l], P.lanes[l]), "cudaEventRecord");
         if (st == HTS_OK) st = cu(cudaStreamWaitEvent(P.origin, P.ev_lane[l], 0), "cudaStreamWaitEvent");
@@ -554,6 +754,7 @@ extern "C" hts_status hts_last_batch_stats(hts_stats *out, int n, hts_batch_info
         info->kernels = (int)P->kernels;
         info->captures = P->captures;
         info->updates = P->updates;
+        info->phased = P->phased ? 1 : 0;
     }
     return device_status(err);
 }

@@ -1480,7 +1480,7 @@ std::vector<int> tune_key(const Geom &g) {
 }
 
 // Normalisation when wcount holds patch-origin counts (the tensor-core filter).
-hts_status launch_normalize_box(const long long *acc, const int *cnt, float *out, int H, int W, int C, cudaStream_t s) {
+hts_status normalize_box(const long long *acc, const int *cnt, float *out, int H, int W, int C, cudaStream_t s) {
     const dim3 grid((W + NB_T - 1) / NB_T, (H + NB_T - 1) / NB_T);
     {
         KTimer kt("k_normalize_box", s);
@@ -1635,7 +1635,7 @@ hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, co
             launch_filter_tc(img, g, idx, b32, acc, wcount, st, sigma_ref, map_judged, tau_scale, mean_est, s, &used);
         if (st0 != HTS_OK) return st0;
         if (!used && mean_est) return report(HTS_EUNSUPPORTED, "the enhancement strategy needs the tensor-core filter");
-        if (used) return launch_normalize_box(acc, wcount, out, g.H, g.W, g.C, s);
+        if (used) return normalize_box(acc, wcount, out, g.H, g.W, g.C, s);
     }
 #define HTS_FILTER_CASE(CC, KK) \
     if (g.C == CC && g.K == KK) return launch_ck<CC, KK>(a, g, out, s);
@@ -1643,6 +1643,11 @@ hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, co
     HTS_FILTER_CASE(3, 2) HTS_FILTER_CASE(3, 4) HTS_FILTER_CASE(3, 8) HTS_FILTER_CASE(3, 16) HTS_FILTER_CASE(3, 32)
 #undef HTS_FILTER_CASE
     return HTS_EUNSUPPORTED;
+}
+
+hts_status launch_normalize_box(const long long *acc, const int *cnt, float *out, int H, int W, int C,
+                                cudaStream_t s) {
+    return normalize_box(acc, cnt, out, H, W, C, s);
 }
 
 }  // namespace hts

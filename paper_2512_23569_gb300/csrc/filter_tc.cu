@@ -36,6 +36,7 @@
 #include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "filter_common.h"
 #include "hts_internal.h"
@@ -117,7 +118,8 @@ struct FtcLayout {
     static constexpr size_t basis_off = t_off + (size_t)64 * TS * 4;  // 6 x 64 FP32
     static constexpr size_t misc_off = basis_off + (size_t)6 * 64 * 4;
     // misc, two buffers each: pos[MB] int, tau[32] float; 2 mbarrier words, tensor-memory slot
-    static constexpr size_t acc_off = misc_off + (size_t)2 * (MB * 4 + 32 * 4) + 16 + 16;
+    static constexpr size_t job_off = misc_off + (size_t)2 * (MB * 4 + 32 * 4) + 16 + 16;  // the current job
+    static constexpr size_t acc_off = job_off + 256;
     static constexpr uint32_t tcols = (C == 3) ? 256 : 64;
 };
 
@@ -136,9 +138,21 @@ struct FtcArgs {
     int ty, tx, nty, ntx, ntiles, rh_max, rw_max;
 };
 
-template <int C, int K>
-__global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
+// A launch over the images of a batch (same C and K): jobs (device array of every image's arguments with
+// its tile shape) and their tiles taken in turn; job j owns tiles tile_start[j] .. tile_start[j+1]-1.
+struct FtcBatch {
+    const FtcArgs *jobs;
+    const int *tile_start;
+    int njobs, ntiles;
+    int rh_max, rw_max;  // the largest tile region over the jobs
+};
+
+// BATCH: the tiles of every job of `bt` (a0 unused); else the tiles of the one image a0 (bt unused).
+template <int C, int K, bool BATCH>
+__global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ FtcArgs a0,
+                                                     const __grid_constant__ FtcBatch bt) {
     using L = FtcLayout<C>;
+    static_assert(sizeof(FtcArgs) <= 256, "the job fits its shared-memory slot");
     constexpr int GPB = MB / K;  // groups per batch
     extern __shared__ __align__(1024) unsigned char smem[];
     __half *sA = reinterpret_cast<__half *>(smem + L::a_off);
@@ -150,48 +164,49 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
     uint64_t *bar = reinterpret_cast<uint64_t *>(sTau + 64);  // 8-byte aligned: misc_off + 1280
     uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
     int *accs = reinterpret_cast<int *>(smem + L::acc_off);
-    const int RA = a.rh_max * a.rw_max;
+    FtcArgs *sjob = reinterpret_cast<FtcArgs *>(smem + L::job_off);
+    const FtcArgs &a = BATCH ? *sjob : a0;  // the current job's arguments
+    const int RA = BATCH ? bt.rh_max * bt.rw_max : a0.rh_max * a0.rw_max;
     int *acc_v = accs, *acc_w = accs + C * RA;  // [C][RA] sums of value * 2^8, [RA] patch-origin counts
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const size_t HW = (size_t)a.H * a.W;
-    const bool use_map = a.sigma_ref && (!a.map_judged || a.st->learned);
-    const bool ra = a.mean_est != nullptr;
-
-    // ---- bases (row-major 8x8, element (r, c) at r * 8 + c) and the Kronecker matrices
-    for (int t = tid; t < 64; t += NT) {
-        sBas[t] = a.b32[(0 * 64 + t) * 2];        // U0
-        sBas[64 + t] = a.b32[(1 * 64 + t) * 2];   // V0
-        if (C == 3) {
-            sBas[128 + t] = a.b32[(2 * 64 + t) * 2];      // U1 re
-            sBas[192 + t] = a.b32[(2 * 64 + t) * 2 + 1];  // U1 im
-            sBas[256 + t] = a.b32[(3 * 64 + t) * 2];      // V1 re
-            sBas[320 + t] = a.b32[(3 * 64 + t) * 2 + 1];  // V1 im
-        }
-    }
-    __syncthreads();
-    // F: the unitary DFT along the channels (Eq. 4-5) followed by the slices' projections (Eq. 19), as one real
-    // orthogonal map of the raw R, G, B pixels (column t * 64 + (i, j)) to [S^(1) | sqrt2 Re S^(2) |
-    // sqrt2 Im S^(2)] (row (a, b), 64 + (a, b), 128 + (a, b)); its inverse (Eq. 21) is its transpose.
-    // Slice 1: P^(1) = (R + w G + w^2 B) / sqrt3, w = exp(-2 pi i / 3), projected by conj(U1[i][a]) V1[j][b].
+    // ---- bases (row-major 8x8, element (r, c) at r * 8 + c) and the transform F of the current job
     constexpr int CK = L::CK;
-    for (int e = tid; e < CK * CK; e += NT) {
-        const int n = e / CK, k = e - n * CK;  // n: coefficient row, k: channel t = k / 64, pixel (i, j)
-        const int t = k >> 6, px = k & 63, nc = n & 63, sl = n >> 6;
-        const int ia = (px >> 3) * 8 + (nc >> 3), jb = (px & 7) * 8 + (nc & 7);
-        float f;
-        if (sl == 0) {
-            f = sBas[ia] * sBas[64 + jb];  // U0[i][a] V0[j][b]
-            if (C == 3) f *= K3F;
-        } else {
-            const float ur = sBas[128 + ia], ui = sBas[192 + ia], vr = sBas[256 + jb], vi = sBas[320 + jb];
-            const float mr = ur * vr + ui * vi, mi = ur * vi - ui * vr;  // conj(U1[i][a]) V1[j][b]
-            // channel weights of Re and Im of P^(1): (1, -1/2, -1/2) / sqrt3 and (0, -1/2, 1/2)
-            const float cr = (t == 0) ? K3F : -0.5f * K3F, ci = (t == 0) ? 0.f : (t == 1 ? -0.5f : 0.5f);
-            const float v = (sl == 1) ? (mr * cr - mi * ci) : (mr * ci + mi * cr);
-            f = v * 1.41421356237309505f;
+    auto build_f = [&]() {
+        for (int t = tid; t < 64; t += NT) {
+            sBas[t] = a.b32[(0 * 64 + t) * 2];        // U0
+            sBas[64 + t] = a.b32[(1 * 64 + t) * 2];   // V0
+            if (C == 3) {
+                sBas[128 + t] = a.b32[(2 * 64 + t) * 2];      // U1 re
+                sBas[192 + t] = a.b32[(2 * 64 + t) * 2 + 1];  // U1 im
+                sBas[256 + t] = a.b32[(3 * 64 + t) * 2];      // V1 re
+                sBas[320 + t] = a.b32[(3 * 64 + t) * 2 + 1];  // V1 im
+            }
         }
-        sB[(((n >> 3) * (CK / 8) + (k >> 3)) << 6) + ((n & 7) << 3) + (k & 7)] = __float2half_rn(f);
-    }
+        __syncthreads();
+        // F: the unitary DFT along the channels (Eq. 4-5) followed by the slices' projections (Eq. 19), as one real
+        // orthogonal map of the raw R, G, B pixels (column t * 64 + (i, j)) to [S^(1) | sqrt2 Re S^(2) |
+        // sqrt2 Im S^(2)] (row (a, b), 64 + (a, b), 128 + (a, b)); its inverse (Eq. 21) is its transpose.
+        // Slice 1: P^(1) = (R + w G + w^2 B) / sqrt3, w = exp(-2 pi i / 3), projected by conj(U1[i][a]) V1[j][b].
+        for (int e = tid; e < CK * CK; e += NT) {
+            const int n = e / CK, k = e - n * CK;  // n: coefficient row, k: channel t = k / 64, pixel (i, j)
+            const int t = k >> 6, px = k & 63, nc = n & 63, sl = n >> 6;
+            const int ia = (px >> 3) * 8 + (nc >> 3), jb = (px & 7) * 8 + (nc & 7);
+            float f;
+            if (sl == 0) {
+                f = sBas[ia] * sBas[64 + jb];  // U0[i][a] V0[j][b]
+                if (C == 3) f *= K3F;
+            } else {
+                const float ur = sBas[128 + ia], ui = sBas[192 + ia], vr = sBas[256 + jb], vi = sBas[320 + jb];
+                const float mr = ur * vr + ui * vi, mi = ur * vi - ui * vr;  // conj(U1[i][a]) V1[j][b]
+                // channel weights of Re and Im of P^(1): (1, -1/2, -1/2) / sqrt3 and (0, -1/2, 1/2)
+                const float cr = (t == 0) ? K3F : -0.5f * K3F, ci = (t == 0) ? 0.f : (t == 1 ? -0.5f : 0.5f);
+                const float v = (sl == 1) ? (mr * cr - mi * ci) : (mr * ci + mi * cr);
+                f = v * 1.41421356237309505f;
+            }
+            sB[(((n >> 3) * (CK / 8) + (k >> 3)) << 6) + ((n & 7) << 3) + (k & 7)] = __float2half_rn(f);
+        }
+    };
+    if (!BATCH) build_f();
     if (tid == 0) {
         tc::bar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -242,13 +257,38 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(FtcArgs a) {
         return true;
     };
 
-    const int gpt = a.ty * a.tx;
-    const int nbatch = (gpt + GPB - 1) / GPB;
     // gather mapping: per step it, thread tid loads pixel (row, px) of member m(it); a warp covers one
     // patch row of 4 consecutive members (4 coalesced 32-byte segments)
     const int g_px = tid & 7, g_ml = (tid >> 3) & 3, g_row = (tid >> 5) & 7, g_mh = tid >> 8;
     constexpr int NPF = MB * 64 / NT;  // pixels per thread per batch
-    for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+    int cur_job = -1;
+    const int total = BATCH ? bt.ntiles : a0.ntiles;
+    for (int gt = blockIdx.x; gt < total && ok; gt += gridDim.x) {
+        int tile = gt;
+        if (BATCH) {
+            int lo = 0, hi = bt.njobs - 1;  // the job owning the tile: the last j with tile_start[j] <= gt
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (bt.tile_start[mid] <= gt) lo = mid;
+                else hi = mid - 1;
+            }
+            tile = gt - bt.tile_start[lo];
+            if (lo != cur_job) {  // the job's arguments and its transform F (the previous MMAs have completed)
+                const int *src = reinterpret_cast<const int *>(bt.jobs + lo);
+                int *dst = reinterpret_cast<int *>(sjob);
+                for (int w = tid; w < (int)(sizeof(FtcArgs) / 4); w += NT) dst[w] = src[w];
+                cur_job = lo;
+                __syncthreads();
+                build_f();
+                tc::fence_async_smem();
+                __syncthreads();
+            }
+        }
+        const size_t HW = (size_t)a.H * a.W;
+        const bool use_map = a.sigma_ref && (!a.map_judged || a.st->learned);
+        const bool ra = a.mean_est != nullptr;
+        const int gpt = a.ty * a.tx;
+        const int nbatch = (gpt + GPB - 1) / GPB;
         const int tyi = tile / a.ntx, txi = tile - tyi * a.ntx;
         const int gy0 = tyi * a.ty, gx0 = txi * a.tx;
         const int gy1 = min(a.ny, gy0 + a.ty) - 1, gx1 = min(a.nx, gx0 + a.tx) - 1;
@@ -500,17 +540,14 @@ constexpr int SHAPES_TC[NSHAPES_TC][2] = {{8, 8}, {4, 8}, {4, 4}, {2, 4}, {2, 2}
 // measured on the colour 512^2, 1024^2 and 3840x2160 workloads (8x8: 1, 4x4: 1.06, 2x4: 1.13).
 constexpr double SHAPE_WEIGHT_TC[NSHAPES_TC] = {1.0, 1.02, 1.06, 1.13, 1.3, 1.6, 2.0};
 
+// The tile shape of geometry g: among the shapes that fit, the one that minimises the rounds of tiles over
+// the SMs x batches per tile x the shape's relative batch time (ties: the larger shape); ty = 0 if none fits.
 template <int C, int K>
-hts_status launch_ftc(FtcArgs a, const Geom &g, cudaStream_t s, bool *used) {
+void ftc_shape(const Geom &g, int nsm, int &ty, int &tx, int &rh, int &rw, size_t &need) {
     using L = FtcLayout<C>;
     const size_t budget = std::min((size_t)smem_optin(), (size_t)227 * 1024);
-    int dev = 0, nsm = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    // the shape that fits and minimises the rounds of tiles over the SMs x batches per tile x the
-    // shape's relative batch time (ties: the larger shape)
-    size_t need = 0;
-    int ty = 0, tx = 0, rh = 0, rw = 0;
+    need = 0;
+    ty = tx = rh = rw = 0;
     double best = 0.0;
     for (int i = 0; i < NSHAPES_TC; ++i) {
         const int h = std::min(g.H, (SHAPES_TC[i][0] - 1) * g.step + 2 * g.R + PS);
@@ -530,9 +567,19 @@ hts_status launch_ftc(FtcArgs a, const Geom &g, cudaStream_t s, bool *used) {
             need = n;
         }
     }
+}
+
+template <int C, int K>
+hts_status launch_ftc(FtcArgs a, const Geom &g, cudaStream_t s, bool *used) {
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    size_t need = 0;
+    int ty = 0, tx = 0, rh = 0, rw = 0;
+    ftc_shape<C, K>(g, nsm, ty, tx, rh, rw, need);
     *used = false;
     if (ty == 0) return HTS_OK;  // the window is too large for a tile: the SIMT filter takes it
-    const void *k = reinterpret_cast<const void *>(k_filter_tc<C, K>);
+    const void *k = reinterpret_cast<const void *>(k_filter_tc<C, K, false>);
     const hts_status st = allow_smem(k, need);
     if (st != HTS_OK) return st;
     a.ty = ty;
@@ -543,15 +590,95 @@ hts_status launch_ftc(FtcArgs a, const Geom &g, cudaStream_t s, bool *used) {
     a.rh_max = rh;
     a.rw_max = rw;
     const int grid = std::max(1, std::min(a.ntiles, nsm));
+    const FtcBatch none{};
     {
         KTimer kt("k_filter_tc", s);
-        k_filter_tc<C, K><<<grid, NT, need, s>>>(a);
+        k_filter_tc<C, K, false><<<grid, NT, need, s>>>(a, none);
     }
     *used = true;
     return check_launch("k_filter_tc");
 }
 
+template <int C, int K>
+hts_status launch_ftc_batch(const FtcBatch &bt, int grid, cudaStream_t s) {
+    using L = FtcLayout<C>;
+    const size_t need = L::acc_off + (size_t)(C + 1) * bt.rh_max * bt.rw_max * 4;
+    const void *k = reinterpret_cast<const void *>(k_filter_tc<C, K, true>);
+    const hts_status st = allow_smem(k, need);
+    if (st != HTS_OK) return st;
+    const FtcArgs none{};
+    {
+        KTimer kt("k_filter_tc", s);
+        k_filter_tc<C, K, true><<<grid, NT, need, s>>>(none, bt);
+    }
+    return check_launch("k_filter_tc");
+}
+
 }  // namespace
+
+size_t filter_tc_job_size() { return sizeof(FtcArgs); }
+
+int filter_tc_job(const float *img, const Geom &g, const int32_t *idx, const float *b32, long long *acc, int *wcount,
+                  DevState *st, const float *sigma_ref, int map_judged, double tau_scale, int nsm, void *job) {
+    FtcArgs a{};
+    a.img = img;
+    a.H = g.H;
+    a.W = g.W;
+    a.step = g.step;
+    a.R = g.R;
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.idx = idx;
+    a.b32 = b32;
+    a.acc = acc;
+    a.wcount = wcount;
+    a.sigma_ref = sigma_ref;
+    a.map_judged = map_judged;
+    a.tau_scale = tau_scale;
+    a.mean_est = nullptr;
+    a.st = st;
+    size_t need = 0;
+    int ty = 0, tx = 0, rh = 0, rw = 0;
+#define HTS_FTC_SHAPE(CC, KK) \
+    if (g.C == CC && g.K == KK) ftc_shape<CC, KK>(g, nsm, ty, tx, rh, rw, need);
+    HTS_FTC_SHAPE(1, 8) HTS_FTC_SHAPE(1, 16) HTS_FTC_SHAPE(1, 32) HTS_FTC_SHAPE(3, 8) HTS_FTC_SHAPE(3, 16)
+    HTS_FTC_SHAPE(3, 32)
+#undef HTS_FTC_SHAPE
+    if (ty == 0) return -1;  // not for the tensor-core filter
+    a.ty = ty;
+    a.tx = tx;
+    a.nty = (g.ny + ty - 1) / ty;
+    a.ntx = (g.nx + tx - 1) / tx;
+    a.ntiles = a.nty * a.ntx;
+    a.rh_max = rh;
+    a.rw_max = rw;
+    std::memcpy(job, &a, sizeof(FtcArgs));
+    return a.ntiles;
+}
+
+hts_status launch_filter_tc_batch(int C, int K, const void *jobs_host, const void *jobs_dev, const int *tile_start_dev,
+                                  int njobs, int ntiles, int grid, cudaStream_t s) {
+    FtcBatch bt{};
+    bt.jobs = static_cast<const FtcArgs *>(jobs_dev);
+    bt.tile_start = tile_start_dev;
+    bt.njobs = njobs;
+    bt.ntiles = ntiles;
+    const FtcArgs *jh = static_cast<const FtcArgs *>(jobs_host);
+    int area = 0;
+    for (int j = 0; j < njobs; ++j)
+        if (jh[j].rh_max * jh[j].rw_max > area) {
+            area = jh[j].rh_max * jh[j].rw_max;
+            bt.rh_max = jh[j].rh_max;
+            bt.rw_max = jh[j].rw_max;
+        }
+    grid = std::max(1, std::min(grid, ntiles));
+#define HTS_FTC_BATCH(CC, KK) \
+    if (C == CC && K == KK) return launch_ftc_batch<CC, KK>(bt, grid, s);
+    HTS_FTC_BATCH(1, 8) HTS_FTC_BATCH(1, 16) HTS_FTC_BATCH(1, 32) HTS_FTC_BATCH(3, 8) HTS_FTC_BATCH(3, 16)
+    HTS_FTC_BATCH(3, 32)
+#undef HTS_FTC_BATCH
+    return HTS_EUNSUPPORTED;
+}
 
 hts_status launch_filter_tc(const float *img, const Geom &g, const int32_t *idx, const float *b32, long long *acc,
                             int *wcount, DevState *st, const float *sigma_ref, int map_judged, double tau_scale,

@@ -224,6 +224,23 @@ void bufs_carve(const Geom &g, unsigned char *base, Bufs *b);  // device pointer
 hts_status launch_learned_check(const float *sigma_ref, int nref, double factor, DevState *st, cudaStream_t s);
 // Noise level of every reference patch from the learned network (device, N_ref; cnn.cu).
 hts_status cnn_sigma_refs(hts_cnn *n, const float *img, const Geom &g, float *sigma_ref, cudaStream_t s);
+// Batched launches of the tensor-core kernels over the images of a batch (match_tc.cu, filter_tc.cu):
+// *_job writes an image's arguments (job_size bytes, host memory) and returns its work items (matcher:
+// tiles x plane passes; filter: tiles, -1 if the tensor-core filter does not take the geometry); the
+// launches read the job table and the prefix sums of the items from device memory.
+size_t match_tc_job_size();
+int match_tc_job(const float *img, const Geom &g, int32_t *idx, const uint8_t *green, int32_t *fallback_list,
+                 DevState *st, void *job);
+hts_status launch_match_tc_batch(int K, const void *jobs_host, const void *jobs_dev, const int *item_start_dev,
+                                 int njobs, int nitems, int *queue_dev, int grid, cudaStream_t s);
+size_t filter_tc_job_size();
+int filter_tc_job(const float *img, const Geom &g, const int32_t *idx, const float *b32, long long *acc, int *wcount,
+                  DevState *st, const float *sigma_ref, int map_judged, double tau_scale, int nsm, void *job);
+hts_status launch_filter_tc_batch(int C, int K, const void *jobs_host, const void *jobs_dev, const int *tile_start_dev,
+                                  int njobs, int ntiles, int grid, cudaStream_t s);
+// Pixel weights from the tensor-core filter's patch-origin counts, and the normalisation (filter.cu).
+hts_status launch_normalize_box(const long long *acc, const int *cnt, float *out, int H, int W, int C, cudaStream_t s);
+
 // Releases every batch plan (batch.cu).
 void batch_shutdown();
 // The whole method for one image on stream s with the buffers of b (api.cu).

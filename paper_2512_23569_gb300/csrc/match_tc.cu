@@ -92,6 +92,16 @@ struct TcArgs {
     int tma_bw, tma_bh;  // the TMA box: columns (a multiple of 4, from a column multiple of 4) and rows
 };
 
+// A launch over the images of a batch: jobs (device array of every image's arguments, staged by loads)
+// and one work queue of (job, tile, plane pass) items; job j owns items item_start[j] .. item_start[j+1]-1.
+struct TcBatch {
+    const TcArgs *jobs;
+    const int *item_start;
+    int njobs, nitems;
+    int *queue;          // the queue's counter (zero at the launch)
+    int hc_max, wc_max;  // bounds of the candidate regions over the jobs
+};
+
 // LH: keys each thread keeps and the number re-ranked in FP32 per reference;
 // T: slots per bin; KC: the nearest keys that must all have been kept.
 template <int K>
@@ -104,7 +114,7 @@ struct ListCfg {
 };
 
 struct TcLayout {
-    size_t q, a, e, ps, scr, ref, qr, bar, total;
+    size_t q, a, e, ps, scr, ref, qr, bar, job, total;
 };
 
 __host__ __device__ inline size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -136,7 +146,8 @@ __host__ __device__ inline TcLayout tc_layout(int hc_max, int wc_max) {
     L.ref = up(L.scr + nq * 4, 16);
     L.qr = L.ref + (size_t)NR * sizeof(RefRec);
     L.bar = up(L.qr + NQ * sizeof(int2), 16);
-    L.total = L.bar + (2 * NBUF + 2) * 8 + 16;
+    L.job = up(L.bar + (2 * NBUF + 2) * 8 + 16, 64);  // the current job's arguments (batched launches)
+    L.total = L.job + sizeof(TcArgs);
     // one block per SM, and never beside a block of the other tensor-core kernels (whose tensor
     // memory would not fit beside this block's 512 columns)
     if (L.total < 160 * 1024) L.total = 160 * 1024;
@@ -184,11 +195,14 @@ __device__ __forceinline__ void self_group(const TcArgs &a, int r, int self) {
     for (int k = 0; k < K; ++k) out[k] = self;
 }
 
-template <int K>
-__global__ void __launch_bounds__(NT, 1) k_match_tc(const __grid_constant__ TcArgs a) {
+// BATCH: the items of every job of `bt` (a0 unused); else the items of the one image a0 (bt unused).
+template <int K, bool BATCH>
+__global__ void __launch_bounds__(NT, 1) k_match_tc(const __grid_constant__ TcArgs a0,
+                                                    const __grid_constant__ TcBatch bt) {
     constexpr int LH = ListCfg<K>::LH, T = ListCfg<K>::T, KC = ListCfg<K>::KC, NBIN = ListCfg<K>::NBIN;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const TcLayout L = tc_layout<K>(a.hc_max, a.wc_max);
+    const TcLayout L = tc_layout<K>(BATCH ? bt.hc_max : a0.hc_max, BATCH ? bt.wc_max : a0.wc_max);
+    TcArgs *sjob = reinterpret_cast<TcArgs *>(smem_raw + L.job);
     uint4 *Q = reinterpret_cast<uint4 *>(smem_raw + L.q);
     unsigned char *Abuf = smem_raw + L.a;
     float *E = reinterpret_cast<float *>(smem_raw + L.e);
@@ -211,7 +225,6 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(const __grid_constant__ TcAr
     const bool cw = warp < NWC;              // a reading warp
     const int q = warp & 3, hh = (warp >> 2) & 1;  // lane quarter, half of the quarter's 64 columns
     const int m = 32 * q + lane;            // this thread's reference slot (A row, tensor-memory lane)
-    const size_t HW = (size_t)a.H * a.W;
     if (tid == 0) {
         for (int b = 0; b < NBUF; ++b) {
             tc::bar_init(&full[b], 1);
@@ -233,17 +246,37 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(const __grid_constant__ TcAr
     volatile int *abortp = abort_flag;
     bool ok = true;
 
-    const int npass = (a.C == 3) ? 2 : 1;
+    int cur_job = -1;
     while (true) {
         // next item of the work queue: (tile, plane pass), so that the two passes of a colour tile run
         // on two SMs and blocks that drew passes without references move on at once.  The fence orders this
         // thread's earlier shared-memory accesses before the next item's TMA writes into the same area.
         tc::fence_async_smem();
-        if (tid == 0) *item_slot = atomicAdd(&a.st->mtc_next, 1);
+        if (tid == 0) *item_slot = atomicAdd(BATCH ? bt.queue : &a0.st->mtc_next, 1);
         __syncthreads();
-        const int item = *item_slot;
+        int item = *item_slot;
         __syncthreads();
-        if (item >= a.ntiles * npass) break;
+        if (BATCH) {
+            if (item >= bt.nitems) break;
+            int lo = 0, hi = bt.njobs - 1;  // the job owning the item: the last j with item_start[j] <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (bt.item_start[mid] <= item) lo = mid;
+                else hi = mid - 1;
+            }
+            item -= bt.item_start[lo];
+            if (lo != cur_job) {  // the job's arguments into shared memory (every thread reads them below)
+                const int *src = reinterpret_cast<const int *>(bt.jobs + lo);
+                int *dst = reinterpret_cast<int *>(sjob);
+                for (int w = tid; w < (int)(sizeof(TcArgs) / 4); w += NT) dst[w] = src[w];
+                cur_job = lo;
+                __syncthreads();
+            }
+        }
+        const TcArgs &a = BATCH ? *sjob : a0;
+        const int npass = (a.C == 3) ? 2 : 1;
+        const size_t HW = (size_t)a.H * a.W;
+        if (!BATCH && item >= a.ntiles * npass) break;
         const int tile = item / npass;
         const int tyi = tile / a.ntx, txi = tile - tyi * a.ntx;
         const int gy0 = tyi * TTY, gx0 = txi * TTX;
@@ -614,7 +647,7 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(const __grid_constant__ TcAr
 template <int K>
 hts_status launch_tc(const TcArgs &a, cudaStream_t s) {
     const TcLayout L = tc_layout<K>(a.hc_max, a.wc_max);
-    const hts_status st0 = allow_smem(reinterpret_cast<const void *>(k_match_tc<K>), L.total);
+    const hts_status st0 = allow_smem(reinterpret_cast<const void *>(k_match_tc<K, false>), L.total);
     if (st0 != HTS_OK) return st0;
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
@@ -622,14 +655,81 @@ hts_status launch_tc(const TcArgs &a, cudaStream_t s) {
     const int items = a.ntiles * (a.C == 3 ? 2 : 1);
     const int grid = std::max(1, std::min(items, nsm));
     if (cudaMemsetAsync(&a.st->mtc_next, 0, sizeof(int), s) != cudaSuccess) return check_launch("cudaMemsetAsync");
+    TcBatch none{};
     {
         KTimer kt("k_match_tc", s);
-        k_match_tc<K><<<grid, NT, L.total, s>>>(a);
+        k_match_tc<K, false><<<grid, NT, L.total, s>>>(a, none);
+    }
+    return check_launch("k_match_tc");
+}
+
+template <int K>
+hts_status launch_tc_batch(const TcBatch &bt, int grid, cudaStream_t s) {
+    const TcLayout L = tc_layout<K>(bt.hc_max, bt.wc_max);
+    const hts_status st0 = allow_smem(reinterpret_cast<const void *>(k_match_tc<K, true>), L.total);
+    if (st0 != HTS_OK) return st0;
+    if (cudaMemsetAsync(bt.queue, 0, sizeof(int), s) != cudaSuccess) return check_launch("cudaMemsetAsync");
+    TcArgs none{};
+    {
+        KTimer kt("k_match_tc", s);
+        k_match_tc<K, true><<<grid, NT, L.total, s>>>(none, bt);
     }
     return check_launch("k_match_tc");
 }
 
 }  // namespace
+
+size_t match_tc_job_size() { return sizeof(TcArgs); }
+
+int match_tc_job(const float *img, const Geom &g, int32_t *idx, const uint8_t *green, int32_t *fallback_list,
+                 DevState *st, void *job) {
+    TcArgs a{};
+    a.img = img;
+    a.H = g.H;
+    a.W = g.W;
+    a.C = g.C;
+    a.step = g.step;
+    a.R = g.R;
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.nref = g.nref;
+    a.idx = idx;
+    a.green = green;
+    a.fb = fallback_list;
+    a.st = st;
+    a.nty = (g.ny + TTY - 1) / TTY;
+    a.ntx = (g.nx + TTX - 1) / TTX;
+    a.ntiles = a.nty * a.ntx;
+    a.hc_max = std::min(g.H - PS + 1, (TTY - 1) * g.step + 1 + 2 * g.R);
+    a.wc_max = std::min(g.W - PS + 1, (TTX - 1) * g.step + 1 + 2 * g.R);
+    a.use_tma = 0;  // the job table lives in global memory: regions staged by loads
+    std::memcpy(job, &a, sizeof(TcArgs));
+    return a.ntiles * (g.C == 3 ? 2 : 1);
+}
+
+hts_status launch_match_tc_batch(int K, const void *jobs_host, const void *jobs_dev, const int *item_start_dev,
+                                 int njobs, int nitems, int *queue_dev, int grid, cudaStream_t s) {
+    TcBatch bt{};
+    bt.jobs = static_cast<const TcArgs *>(jobs_dev);
+    bt.item_start = item_start_dev;
+    bt.njobs = njobs;
+    bt.nitems = nitems;
+    bt.queue = queue_dev;
+    const TcArgs *jh = static_cast<const TcArgs *>(jobs_host);
+    for (int j = 0; j < njobs; ++j) {
+        bt.hc_max = std::max(bt.hc_max, jh[j].hc_max);
+        bt.wc_max = std::max(bt.wc_max, jh[j].wc_max);
+    }
+    grid = std::max(1, std::min(grid, nitems));
+    switch (K) {
+        case 2: return launch_tc_batch<2>(bt, grid, s);
+        case 4: return launch_tc_batch<4>(bt, grid, s);
+        case 8: return launch_tc_batch<8>(bt, grid, s);
+        case 16: return launch_tc_batch<16>(bt, grid, s);
+        case 32: return launch_tc_batch<32>(bt, grid, s);
+        default: return HTS_EUNSUPPORTED;
+    }
+}
 
 hts_status launch_match_tc(const float *img, const Geom &g, double gamma_gcp, int32_t *idx, const uint8_t *green,
                            int32_t *fallback_list, DevState *st, cudaStream_t s) {

@@ -70,7 +70,7 @@ class Stats(ctypes.Structure):
 
 class BatchInfo(ctypes.Structure):
     _fields_ = [("images", ctypes.c_int), ("lanes", ctypes.c_int), ("kernels", ctypes.c_int),
-                ("captures", ctypes.c_int), ("updates", ctypes.c_int)]
+                ("captures", ctypes.c_int), ("updates", ctypes.c_int), ("phased", ctypes.c_int)]
 
 
 class KernelTime(ctypes.Structure):

@@ -216,3 +216,29 @@ def test_batch_learned_equals_single_calls(hts):
                                       o.cpu().numpy())
     with pytest.raises(hts.HtsError):  # a gray image with a colour network
         hts.denoise_batch_learned([_dev(_images()[0][1])], net, p)
+
+
+def test_phased_batch_uses_single_launches_over_all_images(oracle, hts):
+    # every image in a tensor-core form: the matcher and the filter run once per group of images over a work
+    # queue of (image, tile) items; mixed sizes, gray and colour, K 8 and 16, precision 1 and 2 together
+    imgs = _images()
+    xs = [_dev(n) for _, n, _ in imgs]
+    sig = [s for _, _, s in imgs]
+    per = []
+    for i, (_, _, C, _, _) in enumerate(BATCH):
+        per.append(hts.params(win=11, K=8, precision=1 + (i % 2)) if C == 1 else hts.params(win=15, precision=1))
+    outs = hts.denoise_batch(xs, sig, hts.params(), per_image=per)
+    per_stats, info = hts.last_batch_stats(len(xs))
+    assert info["phased"] == 1
+    for x, s, pi, o in zip(xs, sig, per, outs):
+        np.testing.assert_array_equal(hts.denoise(x, sigma=s, p=pi).cpu().numpy(), o.cpu().numpy())
+    # the graph holds far fewer heavy launches than one pipeline per image would
+    n0 = hts.launch_count()
+    hts.denoise_batch(xs, sig, hts.params(), per_image=per)
+    torch.cuda.synchronize()
+    assert hts.launch_count() - n0 == info["kernels"]
+    # a plain-form image in the batch: one pipeline per image
+    per2 = list(per)
+    per2[0] = hts.params(win=11, K=8)
+    hts.denoise_batch(xs, sig, hts.params(), per_image=per2)
+    assert hts.last_batch_stats(len(xs))[1]["phased"] == 0
