@@ -91,6 +91,8 @@ struct Plan {
     unsigned char *mjob_d = nullptr, *fjob_d = nullptr;
     int *starts_d = nullptr;
     cudaEvent_t ev_phase[4] = {};
+    int fshape = -1;         // autotuned: the filter's tile shape for every image (-1: each geometry's model)
+    bool largest_first = false;  // autotuned: the matcher's queue takes the largest images first
     hts_cnn *net = nullptr;
     cudaStream_t cnn_stream = nullptr;
     cudaEvent_t ev_cnn = nullptr;
@@ -274,8 +276,24 @@ hts_status upload_jobs(Plan &P, const hts_image *imgs) {
         const float *sref = P.net ? b.sref : imgs[i].sigma_map;
         items_f[P.fjob_of[i]] = filter_tc_job(imgs[i].noisy, g, b.idx, b.b32, b.acc, b.wcount, b.st, sref,
                                               P.net ? 1 : 0, tau_scale(g, P.par[i]), nsm,
-                                              P.fjob_h.data() + P.fjob_of[i] * fs);
+                                              P.fjob_h.data() + P.fjob_of[i] * fs, P.fshape);
     }
+    // the matcher's queue order within each group: as given, or the largest images first (rows swapped
+    // together with their item counts; the results do not depend on the order)
+    if (P.largest_first)
+        for (auto &gr : P.mgroups) {
+            std::vector<int> rows(gr.njobs);
+            std::iota(rows.begin(), rows.end(), gr.first);
+            std::stable_sort(rows.begin(), rows.end(), [&](int a, int b) { return items_m[a] > items_m[b]; });
+            std::vector<unsigned char> tab((size_t)gr.njobs * ms);
+            std::vector<int> it(gr.njobs);
+            for (int j = 0; j < gr.njobs; ++j) {
+                std::memcpy(tab.data() + (size_t)j * ms, P.mjob_h.data() + (size_t)rows[j] * ms, ms);
+                it[j] = items_m[rows[j]];
+            }
+            std::memcpy(P.mjob_h.data() + (size_t)gr.first * ms, tab.data(), tab.size());
+            for (int j = 0; j < gr.njobs; ++j) items_m[gr.first + j] = it[j];
+        }
     // every group's prefix sums of work items (rows in job-table order)
     for (int pass = 0; pass < 2; ++pass)
         for (auto &gr : pass == 0 ? P.mgroups : P.fgroups) {
@@ -554,6 +572,45 @@ hts_status build(Plan &P, const hts_image *imgs) {
         } else {
             cudaGraphExecDestroy(ex);
         }
+    }
+    if (P.phased) {
+        // the search schedule of the phased form: the filter's tile shape (each geometry's model, or one
+        // shape for all: 8x8, 4x8, 4x4, 2x4 groups) and the matcher's queue order, each kept if faster
+        auto trial = [&](int fshape, bool lf) -> hts_status {
+            const int f0 = P.fshape;
+            const bool l0 = P.largest_first;
+            P.fshape = fshape;
+            P.largest_first = lf;
+            cudaGraph_t g = nullptr;
+            unsigned long long k = 0;
+            HTS_TRY(capture(P, imgs, P.nlanes, &g, &k));
+            cudaGraphExec_t ex = nullptr;
+            hts_status st = instantiate(g, &ex);
+            cudaGraphDestroy(g);
+            HTS_TRY(st);
+            ++P.captures;
+            float ms = 0.f;
+            st = time_exec(P, ex, &ms);
+            if (st != HTS_OK) {
+                cudaGraphExecDestroy(ex);
+                return st;
+            }
+            count_launches(2 * k);
+            if (ms < best_ms) {
+                best_ms = ms;
+                cudaGraphExecDestroy(P.exec);
+                P.exec = ex;
+                P.kernels = k;
+            } else {
+                cudaGraphExecDestroy(ex);
+                P.fshape = f0;
+                P.largest_first = l0;
+            }
+            return HTS_OK;
+        };
+        for (int fsh : {0, 1, 2, 3}) HTS_TRY(trial(fsh, P.largest_first));
+        HTS_TRY(trial(P.fshape, !P.largest_first));
+        HTS_TRY(upload_jobs(P, imgs));  // the device tables of the kept schedule
     }
     P.bound.assign(imgs, imgs + n);
     return HTS_OK;

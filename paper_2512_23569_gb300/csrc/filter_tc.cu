@@ -542,13 +542,27 @@ constexpr double SHAPE_WEIGHT_TC[NSHAPES_TC] = {1.0, 1.02, 1.06, 1.13, 1.3, 1.6,
 
 // The tile shape of geometry g: among the shapes that fit, the one that minimises the rounds of tiles over
 // the SMs x batches per tile x the shape's relative batch time (ties: the larger shape); ty = 0 if none fits.
+// force >= 0: shape SHAPES_TC[force] where it fits (else the model's choice).
 template <int C, int K>
-void ftc_shape(const Geom &g, int nsm, int &ty, int &tx, int &rh, int &rw, size_t &need) {
+void ftc_shape(const Geom &g, int nsm, int &ty, int &tx, int &rh, int &rw, size_t &need, int force = -1) {
     using L = FtcLayout<C>;
     const size_t budget = std::min((size_t)smem_optin(), (size_t)227 * 1024);
     need = 0;
     ty = tx = rh = rw = 0;
     double best = 0.0;
+    if (force >= 0 && force < NSHAPES_TC) {
+        const int h = std::min(g.H, (SHAPES_TC[force][0] - 1) * g.step + 2 * g.R + PS);
+        const int w = std::min(g.W, (SHAPES_TC[force][1] - 1) * g.step + 2 * g.R + PS);
+        const size_t n = L::acc_off + (size_t)(C + 1) * h * w * 4;
+        if (n <= budget) {
+            ty = SHAPES_TC[force][0];
+            tx = SHAPES_TC[force][1];
+            rh = h;
+            rw = w;
+            need = n;
+            return;
+        }
+    }
     for (int i = 0; i < NSHAPES_TC; ++i) {
         const int h = std::min(g.H, (SHAPES_TC[i][0] - 1) * g.step + 2 * g.R + PS);
         const int w = std::min(g.W, (SHAPES_TC[i][1] - 1) * g.step + 2 * g.R + PS);
@@ -619,7 +633,8 @@ hts_status launch_ftc_batch(const FtcBatch &bt, int grid, cudaStream_t s) {
 size_t filter_tc_job_size() { return sizeof(FtcArgs); }
 
 int filter_tc_job(const float *img, const Geom &g, const int32_t *idx, const float *b32, long long *acc, int *wcount,
-                  DevState *st, const float *sigma_ref, int map_judged, double tau_scale, int nsm, void *job) {
+                  DevState *st, const float *sigma_ref, int map_judged, double tau_scale, int nsm, void *job,
+                  int force_shape) {
     FtcArgs a{};
     a.img = img;
     a.H = g.H;
@@ -640,7 +655,7 @@ int filter_tc_job(const float *img, const Geom &g, const int32_t *idx, const flo
     size_t need = 0;
     int ty = 0, tx = 0, rh = 0, rw = 0;
 #define HTS_FTC_SHAPE(CC, KK) \
-    if (g.C == CC && g.K == KK) ftc_shape<CC, KK>(g, nsm, ty, tx, rh, rw, need);
+    if (g.C == CC && g.K == KK) ftc_shape<CC, KK>(g, nsm, ty, tx, rh, rw, need, force_shape);
     HTS_FTC_SHAPE(1, 8) HTS_FTC_SHAPE(1, 16) HTS_FTC_SHAPE(1, 32) HTS_FTC_SHAPE(3, 8) HTS_FTC_SHAPE(3, 16)
     HTS_FTC_SHAPE(3, 32)
 #undef HTS_FTC_SHAPE

@@ -234,8 +234,10 @@ int match_tc_job(const float *img, const Geom &g, int32_t *idx, const uint8_t *g
 hts_status launch_match_tc_batch(int K, const void *jobs_host, const void *jobs_dev, const int *item_start_dev,
                                  int njobs, int nitems, int *queue_dev, int grid, cudaStream_t s);
 size_t filter_tc_job_size();
+// force_shape >= 0: the filter's tile shape number force_shape (8x8, 4x8, 4x4, 2x4, ...) where it fits.
 int filter_tc_job(const float *img, const Geom &g, const int32_t *idx, const float *b32, long long *acc, int *wcount,
-                  DevState *st, const float *sigma_ref, int map_judged, double tau_scale, int nsm, void *job);
+                  DevState *st, const float *sigma_ref, int map_judged, double tau_scale, int nsm, void *job,
+                  int force_shape = -1);
 hts_status launch_filter_tc_batch(int C, int K, const void *jobs_host, const void *jobs_dev, const int *tile_start_dev,
                                   int njobs, int ntiles, int grid, cudaStream_t s);
 // Pixel weights from the tensor-core filter's patch-origin counts, and the normalisation (filter.cu).

@@ -139,14 +139,22 @@ def test_training_beats_one_global_sigma(hts):
     hist = train.fit(net, [d[0] for d in data], [d[1] for d in data], p, steps=1200, batch=8, lr0=2e-3)
     assert hist[-1] < 0.5 * hist[0], hist
     net.window = 64
-    gains = []
-    for clean, noisy, _ in _images(6, 192, 9000):
+    gains, err_net, err_est = [], [], []
+    for clean, noisy, spx in _images(6, 192, 9000):
         x = _dev(noisy)
         a = hts.denoise_learned(x, net, p, fallback_factor=3.0).cpu().numpy()
         assert hts.last_stats()["learned"] == 1
         b = hts.denoise(x, p=p).cpu().numpy()
         gains.append(synth.psnr(a, clean) - synth.psnr(b, clean))
-    assert np.mean(gains) > 0.0, gains
+        # the map's noise levels against the generator's, beside the one eigenvalue estimate's
+        truth = synth.ref_log_sigma(spx, 8, 4).astype(np.float64)
+        lmap = np.log(net.sigma_refs(x, p).cpu().numpy().astype(np.float64))
+        est, _ = hts.estimate_sigma(x, p)
+        err_net.append(np.sqrt(np.mean((lmap - truth) ** 2)))
+        err_est.append(np.sqrt(np.mean((np.log(est) - truth) ** 2)))
+    # measured: about +1 dB and a map several times closer to the true levels than one global estimate
+    assert np.mean(gains) > 0.3, gains
+    assert np.mean(err_net) < np.mean(err_est), (err_net, err_est)
 
 
 def test_far_map_falls_back_to_the_estimate(hts):
