@@ -6,17 +6,21 @@
 // raw pixels, so together they are one real orthogonal matrix F (192 x 192
 // for colour, 64 x 64 for gray) applied to the patch read as a vector of its
 // R, G, B pixels, giving [S^(1) | sqrt2 Re S^(2) | sqrt2 Im S^(2)] (slice 3 is
-// the conjugate of slice 2).  A batch of 128 group members (8 groups of K =
-// 16) is one GEMM with the members as the MMA's M = 128 rows: D[m][coefficient]
-// = sum_pixel A[m][pixel] F[coefficient][pixel], FP16 operands, FP32
-// accumulation in tensor memory (tcgen05.mma kind::f16, N = 192).  The
-// inverse (Eq. 21 and the inverse channel DFT) is F^T: the same shared-memory
-// matrix read with the transpose bit (MN-major), giving the R, G, B pixels of
-// every member directly.  Between the two, the coefficients go through shared
-// memory (transposed, FP32) so that one thread holds a coefficient stream of a
-// group: Haar along the group axis (Eq. 8), hard threshold (Eq. 20, modulus
-// for the complex slice, the group's tau), inverse Haar; then FP16 again as
-// the inverse GEMM's A operand.
+// the conjugate of slice 2).  The Haar transform along the group axis (Eq. 8)
+// acts on the members, F on each member's pixels: the two commute, so the
+// kernel applies Haar first, to the gathered pixels in FP32 registers (a
+// thread holds one pixel of all the group's members), and one GEMM then
+// gives the 3-D coefficients: with the 128 Haar rows of a batch (8 groups of
+// K = 16) as the MMA's M, D[row][coefficient] = sum_pixel A[row][pixel]
+// F[coefficient][pixel], FP16 operands, FP32 accumulation in tensor memory
+// (tcgen05.mma kind::f16, N = 192).  A thread per row thresholds its
+// coefficients in place (Eq. 20; the complex slice's real and imaginary
+// parts lie in the same row) and writes them as the inverse GEMM's operand;
+// the inverse (Eq. 21 and the inverse channel DFT) is F^T, the same
+// shared-memory matrix read with the transpose bit (MN-major), giving each
+// Haar row's pixels.  One transposed pass per channel hands a (group, pixel)
+// pair to a thread, which applies the inverse Haar along the group and adds
+// the members' estimates to the tile's sums.
 //
 // FP16 rather than BF16: pixels lie in a bounded range and the bases are
 // orthonormal, so FP16's 11-bit significand fits the data, where BF16's 8
@@ -26,13 +30,14 @@
 // estimates in 32-bit shared-memory accumulators over the tile's region
 // (at most 2^10 members of a tile cover a pixel: no overflow), flushed to
 // the image-wide int64 sums (2^16 scale) once per tile; integer sums do not
-// depend on the order of the additions, so the result is deterministic.
-// Weights: every member adds 1 to the count of its patch origin (top-left
-// pixel) instead of 1 to each of its 64 pixels; a pixel's weight is the sum of
-// the origin counts over the 8 x 8 origins whose patch covers it, formed by
-// k_normalize_box.  The MMA waits
-// are bounded: a wait that gives up records DevState.error = 2, waits
-// (bounded) for the MMAs, frees the tensor memory and leaves.
+// depend on the order of the additions, so the result is deterministic.  A
+// warp adds 4 rows x 8 pixels of one member's patch, in 32 distinct banks
+// (row stride 8 mod 32).  Weights: every member adds 1 to the count of its
+// patch origin (top-left pixel) instead of 1 to each of its 64 pixels; a
+// pixel's weight is the sum of the origin counts over the 8 x 8 origins whose
+// patch covers it, formed by k_normalize_box.  The MMA waits are bounded: a
+// wait that gives up records DevState.error = 2, waits (bounded) for the
+// MMAs, frees the tensor memory and leaves.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -83,43 +88,58 @@ __device__ __forceinline__ void haar_inv_u(float (&x)[K]) {
     }
 }
 
-// Butterflies coefficient k of a K-long unnormalised Haar transform has passed.
-template <int K>
-__host__ __device__ constexpr int haar_level(int k) {
-    int L = 0;
-    while ((1 << L) < K) ++L;
-    if (k == 0) return L;
-    int f = 0;
-    while ((2 << f) <= k) ++f;
-    return L - f;
-}
-
 constexpr int NT = 512;   // 16 warps: warp w reads tensor-memory lanes 32 (w % 4) .. + 31, column quarter w / 4
-constexpr int MB = 128;   // group members per batch = MMA M
-constexpr int TS = MB + 4;  // row stride (floats) of the transpose buffer: conflict-free float4 reads
+constexpr int MB = 128;   // Haar rows per batch (8 groups of K = 16) = MMA M
+constexpr int TS = MB + 4;  // row stride (floats) of the transposed buffer: conflict-free float4 reads
 constexpr long long SPIN = 1ll << 24;
 
-// Offset (in halves) of element (r, k) of a K-major FP16 operand block of 64
-// columns, no swizzle: core matrices of 8 rows x 8 columns (128 B), 8-column
-// groups 128 B apart (LBO), 8-row groups 1024 B apart (SBO).
-__device__ __forceinline__ int cm_off(int r, int k) { return (((r >> 3) << 3) + (k >> 3)) * 64 + ((r & 7) << 3) + (k & 7); }
+// The row operands of the two GEMMs (forward: the groups' Haar rows of raw pixels, inverse: the thresholded
+// coefficients), FP16, K-major without swizzle: core matrices of 8 rows x 8 columns (128 B); adjacent core
+// matrices along K 144 B apart (16 B of padding, so that the four core matrices a warp's 32 consecutive
+// columns touch fall in distinct banks), 8-row groups 8 x 144 B apart, 64-column blocks of 128 rows.
+constexpr int LBO_A = 144;
+constexpr int SBO_A = 8 * LBO_A;
+constexpr int BLK_A = 16 * SBO_A;
+
+// Byte offset of element (row r, column k) of a row operand.
+__device__ __forceinline__ int a_off(int r, int k) {
+    return (k >> 6) * BLK_A + (r >> 3) * SBO_A + ((k & 63) >> 3) * LBO_A + ((r & 7) << 4) + ((k & 7) << 1);
+}
+
+// Row stride (elements) of the tile's staged region (FP16) and shared sums (int32): the region width rounded
+// up to 8 mod 64.  A warp reads or adds to 4 rows x 8 pixels of one patch: in the region four 16-byte row
+// pieces whose starts are 16 B apart modulo the banks' 128 bytes, in the sums four 32-byte row pieces 32 B
+// apart: distinct banks.
+__host__ __device__ constexpr int acc_stride(int rw) { return rw + ((8 - rw) & 63); }
+
+// Fixed-point value * 2^8 rounded to the nearest integer (ties to even), as __float2int_rn(v * 256), for the
+// range the tile's 32-bit sums hold (|v| < 2^13; values beyond it are clamped): v * 256 + 1.5 * 2^23 lies in
+// [2^23, 2^24), where FP32 spacing is 1, so the fused multiply-add rounds once to the integer and leaves it in
+// the low mantissa bits.
+__device__ __forceinline__ int fix8(float v) {
+    v = fminf(fmaxf(v, -8191.f), 8191.f);
+    return __float_as_int(fmaf(v, 256.f, 12582912.f)) - 0x4B400000;
+}
 
 template <int C>
 struct FtcLayout {
-    static constexpr int NBLK = (C == 3) ? 3 : 1;  // 64-column blocks of the member operand
     // The FP16 transform F [coefficient][pixel] (CK x CK, CK = 64 C), K-major, core matrices of 8 rows x 8
     // columns, 8-column groups 128 B apart along K and 8-row groups CK * 16 B apart: the forward GEMM's B
     // operand, and with the transpose bit (K = coefficients, N = pixels, MN-major) the inverse's.
     static constexpr int CK = 64 * C;
     static constexpr int B_HALVES = CK * CK;
-    static constexpr size_t a_off = 0;                               // [NBLK][128][64] FP16
-    static constexpr size_t b_off = a_off + (size_t)NBLK * MB * 64 * 2;
-    static constexpr size_t t_off = b_off + (size_t)B_HALVES * 2;    // [64][TS] FP32
-    static constexpr size_t basis_off = t_off + (size_t)64 * TS * 4;  // 6 x 64 FP32
+    // the row operand, and between the inverse GEMM and the next batch's commit the transposed FP32 buffer
+    // [64][TS] of one 64-column chunk
+    static constexpr size_t a_bytes = (size_t)C * BLK_A > (size_t)64 * TS * 4 ? (size_t)C * BLK_A : (size_t)64 * TS * 4;
+    static constexpr size_t a_off = 0;
+    static constexpr size_t b_off = a_off + a_bytes;
+    static constexpr size_t basis_off = b_off + (size_t)B_HALVES * 2;  // 6 x 64 FP32
     static constexpr size_t misc_off = basis_off + (size_t)6 * 64 * 4;
-    // misc, two buffers each: pos[MB] int, tau[32] float; 2 mbarrier words, tensor-memory slot
-    static constexpr size_t job_off = misc_off + (size_t)2 * (MB * 4 + 32 * 4) + 16 + 16;  // the current job
+    // misc: tau[2][32] float, off[2][MB] int, 2 mbarrier words, tensor-memory slot
+    static constexpr size_t job_off = misc_off + (size_t)2 * 32 * 4 + 2 * MB * 4 + 16 + 16;
+    // then the tile's sums [C][RA] int32 and its staged region [C][RA] FP16 (RA = rows x acc_stride(width))
     static constexpr size_t acc_off = job_off + 256;
+    static constexpr size_t bytes(int rh, int rw) { return acc_off + (size_t)C * rh * acc_stride(rw) * 6; }
     static constexpr uint32_t tcols = (C == 3) ? 256 : 64;
 };
 
@@ -148,26 +168,45 @@ struct FtcBatch {
 };
 
 // BATCH: the tiles of every job of `bt` (a0 unused); else the tiles of the one image a0 (bt unused).
+//
+// Per batch of MB Haar rows (GPB = MB / K groups):
+//  1. gather: a thread holds, for one (group, pixel) pair, that pixel of the group's K members (for K = 32
+//     two threads hold 16 members each), applies the unnormalised Haar transform along the group axis in
+//     FP32 registers and writes the K Haar rows' pixel to the row operand (FP16); Haar along the group and the
+//     per-patch transform F commute, so the forward GEMM then gives the 3-D coefficients directly;
+//  2. forward GEMM: D[row][coefficient] = sum_pixel A[row][pixel] F[coefficient][pixel] (tensor memory);
+//  3. threshold: a thread per row (tensor-memory lane) keeps or drops its coefficients against the level's
+//     threshold (modulus for the complex slice, both parts in the same lane), rescales the kept ones by
+//     2^-l and writes them as the inverse GEMM's row operand (FP16);
+//  4. inverse GEMM with F^T: the rows' pixels, still in the Haar domain along the group;
+//  5. per channel: tensor memory -> transposed FP32 buffer; a thread per (group, pixel) pair applies the
+//     unnormalised inverse Haar and adds the K members' estimates of that pixel to the tile's sums.
 template <int C, int K, bool BATCH>
 __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ FtcArgs a0,
                                                      const __grid_constant__ FtcBatch bt) {
     using L = FtcLayout<C>;
     static_assert(sizeof(FtcArgs) <= 256, "the job fits its shared-memory slot");
-    constexpr int GPB = MB / K;  // groups per batch
+    constexpr int GPB = MB / K;                 // groups per batch
+    constexpr int KM = K < 16 ? K : 16;         // members a thread holds per (group, pixel) pair
+    constexpr int TPP = K / KM;                 // threads per pair
+    constexpr int PPT = GPB * 64 * TPP / NT;    // pairs per thread
+    static_assert(PPT * NT == GPB * 64 * TPP && TPP <= 2, "pairs cover the threads");
+    constexpr int LOGK = (K == 8) ? 3 : (K == 16) ? 4 : 5;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __half *sA = reinterpret_cast<__half *>(smem + L::a_off);
+    unsigned char *sA = smem + L::a_off;
+    float *sT = reinterpret_cast<float *>(smem + L::a_off);
     __half *sB = reinterpret_cast<__half *>(smem + L::b_off);
-    float *sT = reinterpret_cast<float *>(smem + L::t_off);
     float *sBas = reinterpret_cast<float *>(smem + L::basis_off);
-    int *sPos = reinterpret_cast<int *>(smem + L::misc_off);  // [2][MB] members' top-left pixels
-    float *sTau = reinterpret_cast<float *>(sPos + 2 * MB);    // [2][32] groups' thresholds
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sTau + 64);  // 8-byte aligned: misc_off + 1280
+    float *sTau = reinterpret_cast<float *>(smem + L::misc_off);  // [2][32] groups' thresholds
+    int *sOff = reinterpret_cast<int *>(sTau + 64);  // [2][MB] members' patch origins in the tile region (-1: none)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sOff + 2 * MB);  // 8-byte aligned
     uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
     int *accs = reinterpret_cast<int *>(smem + L::acc_off);
     FtcArgs *sjob = reinterpret_cast<FtcArgs *>(smem + L::job_off);
     const FtcArgs &a = BATCH ? *sjob : a0;  // the current job's arguments
-    const int RA = BATCH ? bt.rh_max * bt.rw_max : a0.rh_max * a0.rw_max;
-    int *acc_v = accs, *acc_w = accs + C * RA;  // [C][RA] sums of value * 2^8, [RA] patch-origin counts
+    const int RA = BATCH ? bt.rh_max * acc_stride(bt.rw_max) : a0.rh_max * acc_stride(a0.rw_max);
+    int *acc_v = accs;                                         // [C][RA] the tile's sums of value * 2^8
+    __half *sReg = reinterpret_cast<__half *>(accs + C * RA);  // [C][RA] the tile's region, FP16
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // ---- bases (row-major 8x8, element (r, c) at r * 8 + c) and the transform F of the current job
     constexpr int CK = L::CK;
@@ -231,13 +270,13 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
         if (tid == 0) {
             tc::fence_after();
             const uint32_t a0 = tc::su32(sA), b0 = tc::su32(sB);
-            // A: [NBLK][128][64] K-major (K step kk: block kk / 4, two core matrices at (kk % 4) * 256 B).
+            // A: the row operand, K step kk = block kk / 4, two core matrices at (kk % 4) * 2 * LBO_A.
             // Forward B = F: K = pixels, core matrices 128 B apart along K, CK * 16 B along N (coefficients).
             // Inverse B = F^T read in place: K = coefficients (core matrices CK * 16 B apart: LBO), N = pixels
             // (128 B apart: SBO), the MN-major convention.
 #pragma unroll
             for (int kk = 0; kk < CK / 16; ++kk) {
-                const uint64_t ad = tc::sdesc(a0 + (kk >> 2) * (MB * 64 * 2) + (kk & 3) * 256, 128, 1024);
+                const uint64_t ad = tc::sdesc(a0 + (kk >> 2) * BLK_A + (kk & 3) * 2 * LBO_A, LBO_A, SBO_A);
                 const uint64_t bd = inverse ? tc::sdesc(b0 + kk * 2 * (CK * 16), CK * 16, 128)
                                             : tc::sdesc(b0 + kk * 256, 128, CK * 16);
                 tc::mma_f16(tbase, ad, bd, inverse ? idi : idf, kk > 0 ? 1u : 0u);
@@ -257,10 +296,32 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
         return true;
     };
 
-    // gather mapping: per step it, thread tid loads pixel (row, px) of member m(it); a warp covers one
-    // patch row of 4 consecutive members (4 coalesced 32-byte segments)
-    const int g_px = tid & 7, g_ml = (tid >> 3) & 3, g_row = (tid >> 5) & 7, g_mh = tid >> 8;
-    constexpr int NPF = MB * 64 / NT;  // pixels per thread per batch
+    // pair slot i of this thread: group g, pixel p (patch row p >> 3, column p & 7), half h of the group's
+    // members (K = 32).  A warp covers 32 consecutive pixels of one group (4 patch rows: 4 coalesced 32-byte
+    // segments per member); for K = 32 16 pixels of both halves, the partner half in lane ^ 16.
+    auto slot_of = [&](int i, int &g, int &p, int &h) {
+        const int s = tid + i * NT;
+        int pair;
+        if (TPP == 1) {
+            pair = s;
+            h = 0;
+        } else {
+            h = (s >> 4) & 1;
+            pair = ((s >> 5) << 4) | (s & 15);
+        }
+        g = pair >> 6;
+        p = pair & 63;
+    };
+    // Haar row (Eq. 8 order) of local row r of half h when two threads share a group (K = 32): after the
+    // exchange of the halves' sums row 0 of half 0 is global row 0, of half 1 global row 1; local detail rows
+    // of level size n (r in [n, 2n)) go to global rows 2n + h n + (r - n).
+    auto grow = [](int r, int h) -> int {
+        if (TPP == 1) return r;
+        if (r == 0) return h;
+        const int n = r >= 8 ? 8 : r >= 4 ? 4 : r >= 2 ? 2 : 1;
+        return 2 * n + h * n + (r - n);
+    };
+
     int cur_job = -1;
     const int total = BATCH ? bt.ntiles : a0.ntiles;
     for (int gt = blockIdx.x; gt < total && ok; gt += gridDim.x) {
@@ -296,236 +357,290 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
         const int X0 = grid_pos(gx0, a.W, a.step), X1 = grid_pos(gx1, a.W, a.step);
         const int ry0 = max(0, Y0 - a.R), ry1 = min(a.H - 1, Y1 + a.R + PS - 1);
         const int rx0 = max(0, X0 - a.R), rx1 = min(a.W - 1, X1 + a.R + PS - 1);
-        const int rh = ry1 - ry0 + 1, rw = rx1 - rx0 + 1;
-        for (int e = tid; e < (C + 1) * RA; e += NT) accs[e] = 0;
-        // the thresholds of batch bb's groups into buffer buf
-        auto setup = [&](int bb, int buf) {
-            if (tid < GPB) {
-                const int lg = bb * GPB + tid;
-                const int gy = gy0 + lg / a.tx, gx = gx0 + lg % a.tx;
-                const bool valid = lg < gpt && gy <= gy1 && gx <= gx1;
-                sTau[32 * buf + tid] = !valid ? 0.f
-                                       : use_map ? (float)(a.tau_scale * (double)a.sigma_ref[gy * a.nx + gx])
-                                                 : a.st->tau32;
+        const int rh = ry1 - ry0 + 1, rw = rx1 - rx0 + 1, rwp = acc_stride(rw);
+        const int RP = rh * rwp;  // elements per channel plane of the region and of the sums
+        for (int e = tid; e < C * RP; e += NT) acc_v[e] = 0;
+        // the tile's region, FP16: row y of channel c at (c * rh + y) * rwp; consecutive threads take consecutive
+        // pixels of a row, eight loads in flight per thread
+        {
+            // element e = tid + i NT: column x, region row `row` = channel c, row y; advanced by NT per step
+            const int dq = NT / rw, dr = NT - dq * rw;
+            int row = tid / rw, x = tid - row * rw;
+            int c = row / rh, y = row - c * rh;
+            for (int e0 = 0; e0 < C * rh * rw; e0 += 8 * NT) {
+                float v[8];
+                int d[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const bool in = c < C;
+                    d[i] = in ? row * rwp + x : -1;
+                    v[i] = in ? __ldg(a.img + c * HW + (size_t)(ry0 + y) * a.W + rx0 + x) : 0.f;
+                    x += dr;
+                    row += dq;
+                    y += dq;
+                    if (x >= rw) {
+                        x -= rw;
+                        ++row;
+                        ++y;
+                    }
+                    while (y >= rh) {
+                        y -= rh;
+                        ++c;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (d[i] >= 0) sReg[d[i]] = __float2half_rn(v[i]);
             }
+        }
+        // group tid (< GPB) of batch bb: its noise level (the map's, else 1), loaded a batch ahead of its use
+        // (nothing reads the loaded value until then: no wait), and whether the slot holds a group
+        const float tau_all = use_map ? 0.f : a.st->tau32;
+        auto sig_of = [&](int bb, bool &valid) -> float {
+            const int lg = bb * GPB + tid;
+            const int gy = gy0 + lg / a.tx, gx = gx0 + lg % a.tx;
+            valid = lg < gpt && gy <= gy1 && gx <= gx1;
+            return use_map ? __ldg(a.sigma_ref + (valid ? gy * a.nx + gx : 0)) : 1.f;
         };
-        // member m (= tid < MB) of batch bb: its patch's top-left pixel, -1 for an empty group slot
-        auto member_pos = [&](int bb) -> int {
+        auto tau_from = [&](float sig, bool valid) -> float {
+            return !valid ? 0.f : use_map ? (float)(a.tau_scale * (double)sig) : tau_all;
+        };
+        // member m (= tid < MB) of batch bb: its patch's top-left pixel (loaded; read a batch later) and
+        // whether the slot holds a group
+        auto member_pos = [&](int bb, bool &valid) -> int {
             const int g = tid / K, k = tid - g * K;
             const int lg = bb * GPB + g;
             const int gy = gy0 + lg / a.tx, gx = gx0 + lg % a.tx;
-            const bool valid = lg < gpt && gy <= gy1 && gx <= gx1;
-            return valid ? __ldg(a.idx + (size_t)(gy * a.nx + gx) * K + k) : -1;
+            valid = lg < gpt && gy <= gy1 && gx <= gx1;
+            return __ldg(a.idx + (size_t)(valid ? gy * a.nx + gx : 0) * K + k);
         };
-        // this thread's pixels of the batch whose positions are in buffer buf, into registers
-        float pf[NPF][C];
-        auto prefetch = [&](int buf) {
+        // member tid (< MB) at pixel pos into buffer buf: its patch origin in the region (-1: empty slot), and
+        // its origin count (the weight of the patch's 64 pixels, formed by k_normalize_box)
+        auto member_off = [&](int pos, int buf) {
+            int o = -1;
+            if (pos >= 0) {
+                const int py = pos / a.W, px = pos - py * a.W;
+                const int ly = py - ry0, lx = px - rx0;
+                if (ly >= 0 && ly + PS <= rh && lx >= 0 && lx + PS <= rw) {
+                    o = ly * rwp + lx;
+                    atomicAdd(a.wcount + pos, 1);
+                } else {
+                    atomicExch(&a.st->error, 1);
+                }
+            }
+            sOff[MB * buf + tid] = o;
+        };
+        // the batch's pixels (offsets in buffer buf) from the staged region, Haar along the group axis (Eq. 8,
+        // unnormalised) in FP32, FP16 rows of the operand
+        auto commit = [&](int buf) {
 #pragma unroll
-            for (int it = 0; it < NPF; ++it) {
-                const int m = 4 * (2 * it + g_mh) + g_ml;
-                const int pos = sPos[MB * buf + m];
-                const float *src = a.img + (pos >= 0 ? pos : 0) + g_row * a.W + g_px;  // a valid address either way
+            for (int i = 0; i < PPT; ++i) {
+                int g, p, h;
+                slot_of(i, g, p, h);
+                const int *offs = sOff + MB * buf + g * K + h * KM;
+                const __half *src = sReg + (p >> 3) * rwp + (p & 7);
+                float v[KM][C];
 #pragma unroll
-                for (int c = 0; c < C; ++c) pf[it][c] = pos >= 0 ? __ldg(src + c * HW) : 0.f;
+                for (int j = 0; j < KM; ++j) {
+                    const int o = offs[j];
+#pragma unroll
+                    for (int c = 0; c < C; ++c) v[j][c] = o >= 0 ? __half2float(src[c * RP + o]) : 0.f;
+                }
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    float x[KM];
+#pragma unroll
+                    for (int j = 0; j < KM; ++j) x[j] = v[j][c];
+                    haar_fwd_u<KM>(x);
+                    if (TPP == 2) {  // the top level across the halves: sum and difference of their sums
+                        const float o = __shfl_xor_sync(0xffffffffu, x[0], 16);
+                        x[0] = h ? (o - x[0]) : (x[0] + o);
+                    }
+                    unsigned char *col = sA + a_off(g * K, c * 64 + p);
+#pragma unroll
+                    for (int r = 0; r < KM; ++r) {
+                        const int row = grow(r, h);  // within the group: g * K + row, whose 8-row groups are SBO_A apart
+                        *reinterpret_cast<__half *>(col + (row >> 3) * SBO_A + ((row & 7) << 4)) = __float2half_rn(x[r]);
+                    }
+                }
             }
         };
-        // registers -> FP16, member rows of the operand (channel c in block c; F applies the channel DFT)
-        auto commit = [&]() {
-#pragma unroll
-            for (int it = 0; it < NPF; ++it) {
-                const int m = 4 * (2 * it + g_mh) + g_ml;
-                const int o = cm_off(m, g_row * 8 + g_px);
-#pragma unroll
-                for (int c = 0; c < C; ++c) sA[c * MB * 64 + o] = __float2half_rn(pf[it][c]);
-            }
-        };
-        setup(0, 0);
         int posreg = -1;
+        float sigreg = 0.f;
+        bool pvalid = false, svalid = false;
+        if (tid < GPB) {
+            const float s0 = sig_of(0, svalid);
+            sTau[tid] = tau_from(s0, svalid);
+            if (nbatch > 1) sigreg = sig_of(1, svalid);
+        }
         if (tid < MB) {
-            sPos[tid] = member_pos(0);
-            sPos[MB + tid] = nbatch > 1 ? member_pos(1) : -1;
-            posreg = nbatch > 2 ? member_pos(2) : -1;
+            const int p0 = member_pos(0, pvalid);
+            member_off(pvalid ? p0 : -1, 0);
+            if (nbatch > 1) posreg = member_pos(1, pvalid);
         }
         __syncthreads();
-        prefetch(0);
         for (int b = 0; b < nbatch; ++b) {
             const int cur = b & 1;
             const float *bTau = sTau + 32 * cur;
-            const int *bPos = sPos + MB * cur;
-            commit();
-            if (b + 1 < nbatch) setup(b + 1, cur ^ 1);  // read after the next batch's first barrier
-            if (b >= 1 && b + 1 < nbatch && tid < MB) sPos[MB * (cur ^ 1) + tid] = posreg;  // batch b + 1
-            // ---- forward transform (Eq. 4-5, 19): D[m] = [S0 | sqrt2 Re S1 | sqrt2 Im S1]
+            commit(cur);
+            if (b + 1 < nbatch) {  // the next batch's thresholds and member offsets (read after the next barrier)
+                if (tid < GPB) sTau[32 * (cur ^ 1) + tid] = tau_from(sigreg, svalid);
+                if (tid < MB) member_off(pvalid ? posreg : -1, cur ^ 1);
+            }
+            // ---- forward transform (Eq. 4-5, 19) of the Haar rows: D[row] = [S0 | sqrt2 Re S1 | sqrt2 Im S1]
             if (!run_stage(false)) {
                 ok = false;
                 break;
             }
-            if (b + 1 < nbatch) {  // the next batch's pixel loads go out now, and the positions of the one after
-                prefetch(cur ^ 1);
-                if (tid < MB && b + 2 < nbatch) posreg = member_pos(b + 2);
+            if (b + 2 < nbatch) {  // the positions and noise levels of the batch after next
+                if (tid < MB) posreg = member_pos(b + 2, pvalid);
+                if (tid < GPB) sigreg = sig_of(b + 2, svalid);
             }
-            // ---- per 64-column chunk: tensor memory -> transposed FP32 buffer, Haar + threshold +
-            //      inverse Haar per (group, coefficient) stream, FP16 into the inverse's operand.
-            //      Chunk 0: S0 (columns 0..63); chunks 1, 2: complex coefficients c0 = 32 (ch - 1) .. + 31,
-            //      real parts (columns 64 + c) as local columns 0..31, imaginary parts (128 + c) as 32..63.
-            constexpr int NCHUNK = (C == 3) ? 3 : 1;
-#pragma unroll 1
-            for (int ch = 0; ch < NCHUNK; ++ch) {
-                const bool cplx = ch >= 1;
-                const int c0 = 32 * (ch - 1);
-                const int col0 = !cplx ? 16 * wq : (wq < 2 ? 64 + c0 + 16 * wq : 128 + c0 + 16 * (wq - 2));
+            // ---- hard threshold (Eq. 20) of row m = 32 q + lane: Haar row k of group m / K, level l_k.  The
+            //      unnormalised coefficient is 2^(l/2) times the orthonormal one, so it is kept iff x^2 >= tau^2 2^l
+            //      (complex: (sqrt2 Re)^2 + (sqrt2 Im)^2 >= 2 tau^2 2^l); kept ones are scaled by 2^-l (exact).
+            {
+                const int m = 32 * q + lane;
+                const int k = m & (K - 1);
+                const int l = k == 0 ? LOGK : LOGK - (31 - __clz(k));
+                const float tau = bTau[m / K];  // 0 for an empty slot: its zeros stay zeros
+                const float t2 = tau * tau * (float)(1 << l);
+                const float sc = (ra && k == 0) ? 0.f : __int_as_float((127 - l) << 23);  // 2^-l; RA: row 0 replaced
+                unsigned char *rowp = sA + (m >> 3) * SBO_A + ((m & 7) << 4);
                 {
                     uint32_t v[16];
-                    tc::tmem_ld16(tbase + tlane + (uint32_t)col0, v);
+                    tc::tmem_ld16(tbase + tlane + (uint32_t)(16 * wq), v);
+                    tc::tmem_wait_ld();
+                    __align__(16) __half2 hv[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float x0 = __uint_as_float(v[2 * j]), x1 = __uint_as_float(v[2 * j + 1]);
+                        hv[j] = __floats2half2_rn(x0 * x0 >= t2 ? x0 * sc : 0.f, x1 * x1 >= t2 ? x1 * sc : 0.f);
+                    }
+                    const uint4 *hp = reinterpret_cast<const uint4 *>(hv);
+                    *reinterpret_cast<uint4 *>(rowp + (2 * wq) * LBO_A) = hp[0];
+                    *reinterpret_cast<uint4 *>(rowp + (2 * wq + 1) * LBO_A) = hp[1];
+                }
+                if constexpr (C == 3) {
+                    uint32_t vr[16], vi[16];
+                    tc::tmem_ld16(tbase + tlane + (uint32_t)(64 + 16 * wq), vr);
+                    tc::tmem_ld16(tbase + tlane + (uint32_t)(128 + 16 * wq), vi);
+                    tc::tmem_wait_ld();
+                    const float t2c = 2.f * t2;
+                    __align__(16) __half2 hr[8], hi[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        float o[2][2];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const float re = __uint_as_float(vr[2 * j + e]), im = __uint_as_float(vi[2 * j + e]);
+                            const bool keep = fmaf(re, re, im * im) >= t2c;
+                            o[0][e] = keep ? re * sc : 0.f;
+                            o[1][e] = keep ? im * sc : 0.f;
+                        }
+                        hr[j] = __floats2half2_rn(o[0][0], o[0][1]);
+                        hi[j] = __floats2half2_rn(o[1][0], o[1][1]);
+                    }
+                    const uint4 *rp = reinterpret_cast<const uint4 *>(hr);
+                    const uint4 *ip = reinterpret_cast<const uint4 *>(hi);
+                    *reinterpret_cast<uint4 *>(rowp + BLK_A + (2 * wq) * LBO_A) = rp[0];
+                    *reinterpret_cast<uint4 *>(rowp + BLK_A + (2 * wq + 1) * LBO_A) = rp[1];
+                    *reinterpret_cast<uint4 *>(rowp + 2 * BLK_A + (2 * wq) * LBO_A) = ip[0];
+                    *reinterpret_cast<uint4 *>(rowp + 2 * BLK_A + (2 * wq + 1) * LBO_A) = ip[1];
+                }
+            }
+            // ---- inverse transform (Eq. 21 and the inverse channel DFT): E[row] = [R | G | B] pixels of the
+            //      group's thresholded Haar rows
+            if (!run_stage(true)) {
+                ok = false;
+                break;
+            }
+            // ---- per channel: inverse Haar along the group axis and aggregation of the members' estimates
+            int offs[PPT][KM];  // this thread's members' patch origins in the region (-1: empty slot)
+#pragma unroll
+            for (int i = 0; i < PPT; ++i) {
+                int g, p, h;
+                slot_of(i, g, p, h);
+#pragma unroll
+                for (int j = 0; j < KM; ++j) {
+                    const int o = sOff[MB * cur + g * K + h * KM + j];
+                    offs[i][j] = o >= 0 ? o + (p >> 3) * rwp + (p & 7) : -1;
+                }
+            }
+#pragma unroll 1
+            for (int c = 0; c < C; ++c) {
+                {
+                    uint32_t v[16];
+                    tc::tmem_ld16(tbase + tlane + (uint32_t)(64 * c + 16 * wq), v);
                     tc::tmem_wait_ld();
                     const int m = 32 * q + lane;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) sT[(16 * wq + j) * TS + m] = __uint_as_float(v[j]);
                 }
                 __syncthreads();
-                // 64 GPB streams (real) or half-streams (complex: lanes 2i, 2i + 1 hold the real and
-                // imaginary part of one coefficient and exchange squares); whole warps take part
-                for (int s2 = tid; s2 < 64 * GPB; s2 += NT) {
-                    int col, g;
-                    if (!cplx) {
-                        col = s2 & 63;
-                        g = s2 >> 6;
-                    } else {
-                        col = ((s2 >> 1) & 31) + 32 * (s2 & 1);
-                        g = s2 >> 6;
-                    }
-                    const float tau = bTau[g];  // 0 for an empty slot: its zeros stay zeros
-                    float *p = sT + col * TS + g * K;
-                    float x[K];
 #pragma unroll
-                    for (int k = 0; k < K; k += 4) {
-                        const float4 t4 = *reinterpret_cast<const float4 *>(p + k);
-                        x[k] = t4.x;
-                        x[k + 1] = t4.y;
-                        x[k + 2] = t4.z;
-                        x[k + 3] = t4.w;
-                    }
-                    haar_fwd_u<K>(x);
-                    if (!cplx) {
+                for (int i = 0; i < PPT; ++i) {
+                    int g, p, h;
+                    slot_of(i, g, p, h);
+                    const float *colp = sT + p * TS + g * K;
+                    float x[KM];
+                    if (TPP == 1) {
 #pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            const int l = haar_level<K>(k);
-                            // |x| >= tau 2^(l/2): tau times sqrt(2) for odd l, times 2^(l/2) exactly
-                            const float tl = (l & 1) ? tau * (float)(1 << (l >> 1)) * 1.41421356237309505f
-                                                     : tau * (float)(1 << (l >> 1));
-                            x[k] = (fabsf(x[k]) >= tl) ? x[k] * (1.f / (float)(1 << l)) : 0.f;
+                        for (int r = 0; r < KM; r += 4) {
+                            const float4 t4 = *reinterpret_cast<const float4 *>(colp + r);
+                            x[r] = t4.x;
+                            x[r + 1] = t4.y;
+                            x[r + 2] = t4.z;
+                            x[r + 3] = t4.w;
                         }
                     } else {
-                        // modulus test on squares: the streams hold sqrt2 Re and sqrt2 Im (F's rows), so
-                        // |S| >= tau iff re^2 + im^2 >= 2 tau^2 2^l (lanes 2i, 2i + 1 hold the real and imaginary
-                        // stream of one coefficient; the sum is formed in one order on both)
-                        const bool im = s2 & 1;
-                        const float tau2 = 2.f * tau * tau;
+                        const float2 z = *reinterpret_cast<const float2 *>(colp);
+                        x[0] = h ? (z.x - z.y) : (z.x + z.y);  // the top level: this half's sum
+                        x[1] = colp[grow(1, h)];
+                        const float2 u = *reinterpret_cast<const float2 *>(colp + grow(2, h));
+                        x[2] = u.x;
+                        x[3] = u.y;
 #pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            const int l = haar_level<K>(k);
-                            const float sq = x[k] * x[k];
-                            const float other = __shfl_xor_sync(0xffffffffu, sq, 1);
-                            const float m2 = im ? (other + sq) : (sq + other);
-                            x[k] = (m2 >= tau2 * (float)(1 << l)) ? x[k] * (1.f / (float)(1 << l)) : 0.f;
+                        for (int r = 4; r < KM; r += 4) {
+                            const float4 t4 = *reinterpret_cast<const float4 *>(colp + grow(r, h));
+                            x[r] = t4.x;
+                            x[r + 1] = t4.y;
+                            x[r + 2] = t4.z;
+                            x[r + 3] = t4.w;
                         }
                     }
-                    if (ra) x[0] = 0.f;  // Haar row 0 (Eq. 8 order): its refined value is added after the inverse
-                    haar_inv_u<K>(x);
+                    haar_inv_u<KM>(x);
+                    if (ra) {  // first Haar row replaced (Eq. 24-25): the refined mean joins every member
+                        const int lg = b * GPB + g;
+                        const int gy = gy0 + lg / a.tx, gx = gx0 + lg % a.tx;
+                        if (lg < gpt && gy <= gy1 && gx <= gx1) {
+                            const float mu = __ldg(a.mean_est + (size_t)(gy * a.nx + gx) * (C * 64) + c * 64 + p);
 #pragma unroll
-                    for (int k = 0; k < K; k += 4)
-                        *reinterpret_cast<float4 *>(p + k) = make_float4(x[k], x[k + 1], x[k + 2], x[k + 3]);
-                }
-                __syncthreads();
-                // FP16 into the inverse GEMM's operand: member m, 8 consecutive local columns 8 jg ..
+                            for (int j = 0; j < KM; ++j) x[j] += mu;
+                        }
+                    }
+                    int *dst = acc_v + c * RP;
 #pragma unroll
-                for (int it = 0; it < MB * 8 / NT; ++it) {
-                    const int e2 = it * NT + tid;
-                    const int m = e2 & (MB - 1), jg = e2 >> 7;
-                    const int gc = !cplx ? 8 * jg : (jg < 4 ? 64 + c0 + 8 * jg : 128 + c0 + 8 * (jg - 4));
-                    __align__(16) __half hv[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) hv[e] = __float2half_rn(sT[(8 * jg + e) * TS + m]);
-                    *reinterpret_cast<uint4 *>(sA + (gc >> 6) * (MB * 64) + cm_off(m, gc & 63)) =
-                        *reinterpret_cast<const uint4 *>(hv);
+                    for (int j = 0; j < KM; ++j)
+                        if (offs[i][j] >= 0) atomicAdd(dst + offs[i][j], fix8(x[j]));
                 }
                 tc::fence_before();
                 __syncthreads();
             }
-            // ---- inverse transform (Eq. 21 and the inverse channel DFT): D[m] = [R | G | B] pixels
-            if (!run_stage(true)) {
-                ok = false;
-                break;
-            }
-            // ---- aggregation: member m = 32 q + lane, patch rows
-            //      2 wq, 2 wq + 1
-            {
-                const int m = 32 * q + lane;
-                const int pos = bPos[m];
-                const int py = pos >= 0 ? pos / a.W : 0, px = pos >= 0 ? pos - py * a.W : 0;
-                const float *mrow = nullptr;  // the member's group's refined mean patch (enhancement strategy)
-                if (ra && pos >= 0) {
-                    const int lg = b * GPB + m / K;
-                    mrow = a.mean_est + (size_t)((gy0 + lg / a.tx) * a.nx + gx0 + lg % a.tx) * (C * 64);
-                }
-#pragma unroll 1
-                for (int rr = 0; rr < 2; ++rr) {
-                    const int row = 2 * wq + rr;
-                    uint32_t p0[8], p1[8] = {}, p2[8] = {};
-                    tc::tmem_ld8(tbase + tlane + (uint32_t)(row * 8), p0);
-                    if constexpr (C == 3) {
-                        tc::tmem_ld8(tbase + tlane + (uint32_t)(64 + row * 8), p1);
-                        tc::tmem_ld8(tbase + tlane + (uint32_t)(128 + row * 8), p2);
-                    }
-                    tc::tmem_wait_ld();
-                    if (pos < 0) continue;
-                    float out[C][8];  // the inverse transform (F^T) gives the channels' pixels directly
-#pragma unroll
-                    for (int v = 0; v < 8; ++v) {
-                        out[0][v] = __uint_as_float(p0[v]);
-                        if constexpr (C == 3) {
-                            out[1][v] = __uint_as_float(p1[v]);
-                            out[2][v] = __uint_as_float(p2[v]);
-                        }
-                    }
-                    if (mrow) {  // first Haar row replaced (Eq. 24-25): the refined mean joins every member
-#pragma unroll
-                        for (int c = 0; c < C; ++c)
-#pragma unroll
-                            for (int v = 0; v < 8; ++v) out[c][v] += __ldg(mrow + c * 64 + row * 8 + v);
-                    }
-                    const int ly = py + row - ry0, lx = px - rx0;
-                    if (ly >= 0 && ly < rh && lx >= 0 && lx + 7 < rw) {
-                        const int o = ly * rw + lx;
-#pragma unroll
-                        for (int v = 0; v < 8; ++v) {
-#pragma unroll
-                            for (int c = 0; c < C; ++c) atomicAdd(acc_v + c * RA + o + v, __float2int_rn(out[c][v] * 256.f));
-                        }
-                        if (row == 0) atomicAdd(acc_w + o, 1);  // the patch's origin: its 64 pixels' weight
-                    } else {
-                        atomicExch(&a.st->error, 1);
-                    }
-                }
-            }
-            tc::fence_before();
-            __syncthreads();
         }
         if (!ok) break;
-        // flush the tile's sums to the image-wide int64 sums and its origin counts to the image-wide ones
-        // (k_normalize_box turns those into pixel weights)
+        // flush the tile's sums to the image-wide int64 sums
         for (int e = tid; e < rh * rw; e += NT) {
-            const int w = acc_w[e];
             const int yy = e / rw, xx = e - yy * rw;
+            const int le = yy * rwp + xx;
             const size_t gpix = (size_t)(ry0 + yy) * a.W + (rx0 + xx);
 #pragma unroll
             for (int c = 0; c < C; ++c) {
-                const int v = acc_v[c * RA + e];
+                const int v = acc_v[c * RP + le];
                 if (v == 0) continue;
                 const long long s = (long long)v * 256ll;  // to the image-wide 2^16 scale
                 atomicAdd(reinterpret_cast<unsigned long long *>(a.acc + c * HW + gpix), (unsigned long long)s);
             }
-            if (w != 0) atomicAdd(a.wcount + gpix, w);
         }
         __syncthreads();
     }
@@ -553,7 +668,7 @@ void ftc_shape(const Geom &g, int nsm, int &ty, int &tx, int &rh, int &rw, size_
     if (force >= 0 && force < NSHAPES_TC) {
         const int h = std::min(g.H, (SHAPES_TC[force][0] - 1) * g.step + 2 * g.R + PS);
         const int w = std::min(g.W, (SHAPES_TC[force][1] - 1) * g.step + 2 * g.R + PS);
-        const size_t n = L::acc_off + (size_t)(C + 1) * h * w * 4;
+        const size_t n = L::bytes(h, w);
         if (n <= budget) {
             ty = SHAPES_TC[force][0];
             tx = SHAPES_TC[force][1];
@@ -566,7 +681,7 @@ void ftc_shape(const Geom &g, int nsm, int &ty, int &tx, int &rh, int &rw, size_
     for (int i = 0; i < NSHAPES_TC; ++i) {
         const int h = std::min(g.H, (SHAPES_TC[i][0] - 1) * g.step + 2 * g.R + PS);
         const int w = std::min(g.W, (SHAPES_TC[i][1] - 1) * g.step + 2 * g.R + PS);
-        const size_t n = L::acc_off + (size_t)(C + 1) * h * w * 4;
+        const size_t n = L::bytes(h, w);
         if (n > budget) continue;
         const long long ntiles = (long long)((g.ny + SHAPES_TC[i][0] - 1) / SHAPES_TC[i][0]) *
                                  ((g.nx + SHAPES_TC[i][1] - 1) / SHAPES_TC[i][1]);
@@ -616,7 +731,7 @@ hts_status launch_ftc(FtcArgs a, const Geom &g, cudaStream_t s, bool *used) {
 template <int C, int K>
 hts_status launch_ftc_batch(const FtcBatch &bt, int grid, cudaStream_t s) {
     using L = FtcLayout<C>;
-    const size_t need = L::acc_off + (size_t)(C + 1) * bt.rh_max * bt.rw_max * 4;
+    const size_t need = L::bytes(bt.rh_max, bt.rw_max);
     const void *k = reinterpret_cast<const void *>(k_filter_tc<C, K, true>);
     const hts_status st = allow_smem(k, need);
     if (st != HTS_OK) return st;
@@ -679,10 +794,10 @@ hts_status launch_filter_tc_batch(int C, int K, const void *jobs_host, const voi
     bt.njobs = njobs;
     bt.ntiles = ntiles;
     const FtcArgs *jh = static_cast<const FtcArgs *>(jobs_host);
-    int area = 0;
+    int area = 0;  // the kernel's sums hold rh_max x acc_stride(rw_max) per plane: the largest over the jobs
     for (int j = 0; j < njobs; ++j)
-        if (jh[j].rh_max * jh[j].rw_max > area) {
-            area = jh[j].rh_max * jh[j].rw_max;
+        if (jh[j].rh_max * acc_stride(jh[j].rw_max) > area) {
+            area = jh[j].rh_max * acc_stride(jh[j].rw_max);
             bt.rh_max = jh[j].rh_max;
             bt.rw_max = jh[j].rw_max;
         }
