@@ -102,11 +102,11 @@ struct TcBatch {
     int hc_max, wc_max;  // bounds of the candidate regions over the jobs
 };
 
-// LH: keys each thread keeps and the number re-ranked in FP32 per reference;
+// LH: keys each thread keeps and the number re-ranked in FP32 per reference: the top 2K (at least K + 8);
 // T: slots per bin; KC: the nearest keys that must all have been kept.
 template <int K>
 struct ListCfg {
-    static constexpr int LH = K + (K / 2 > 8 ? K / 2 : 8);
+    static constexpr int LH = 2 * K > K + 8 ? 2 * K : K + 8;
     static constexpr int NBIN = K <= 16 ? 32 : 16;  // key i goes into bin i mod NBIN
     static constexpr int T = K <= 16 ? 3 : 6;
     static constexpr int KC = K + 3;
