@@ -554,7 +554,9 @@ def train_network(p, ncrop=4096, cs=256, workers=None):
     info = {"crops": ncrop, "epochs": 3, "crop": "%dx%dx3" % (cs, cs), "seconds": train_s,
             "crops_per_s": 3 * ncrop / train_s, "loss_every_1024_crops": hist, "pairs_seconds": pairs_s,
             "crop_generation_seconds": gen_s, "crop_generation_workers": workers,
-            "best_multiplier_mean": float(np.mean([q[2] for q in pairs])), "readout_window": net.window}
+            "best_multiplier_mean": float(np.mean([q[2] for q in pairs])), "readout_window": net.window,
+            "arithmetic": ("tensor cores: FP16 activations and input gradients, FP32 weight-gradient accumulation, "
+                           "FP32 Adam" if net.train_fp16 else "FP32 kernels")}
     return net, info
 
 

@@ -66,13 +66,16 @@ typedef struct {
                         *    definition's, ties to the lower index); FP32 transforms with FP64
                         *    threshold decisions inside the FP32 error band.
                         * 1: precision form: BF16 distances on the tensor cores (FP32
-                        *    accumulation), the K + max(K/2, 8) nearest re-ranked with FP32
+                        *    accumulation), the 2K nearest (at least K + 8) re-ranked with FP32
                         *    distances (groups may differ from the FP64 definition's where BF16
                         *    rounding reorders near neighbours; a reference whose candidate
                         *    bins may have dropped one of its K + 3 nearest is matched
                         *    exhaustively in FP32); FP16 projections on the tensor cores (FP32
                         *    accumulation) with FP32 threshold decisions.  Windows too large for
-                        *    on-chip staging give HTS_EUNSUPPORTED.
+                        *    on-chip staging give HTS_EUNSUPPORTED.  The FP16 operands and the
+                        *    filter's 32-bit tile sums assume pixel values of magnitude below
+                        *    2^11 (the [0, 255] scale has ample room); estimates beyond 2^13 are
+                        *    clamped.
                         * 2: the groups of 0 with the filter of 1. */
 } hts_params;
 
@@ -259,7 +262,7 @@ hts_status hts_cnn_get_params(const hts_cnn *net, float *host_params);
 hts_status hts_cnn_set_params(hts_cnn *net, const float *host_params);
 /* Forward pass used for denoising: log-sigma map (device, H x W) of a device
  * CHW image, on the tensor cores with the network input and the hidden
- * activations rounded to FP16 (training's forward keeps them in FP32). */
+ * activations rounded to FP16 (the same forward as tensor-core training). */
 hts_status hts_cnn_log_sigma_map(hts_cnn *net, const float *img, int H, int W, float *map_out, void *stream);
 /* Readout window S (1 <= S <= 4096) of hts_cnn_sigma_refs / hts_denoise_learned. */
 hts_status hts_cnn_set_window(hts_cnn *net, int S);
@@ -269,7 +272,18 @@ hts_status hts_cnn_sigma_refs(hts_cnn *net, const float *img, int H, int W, cons
                               float *sigma_ref, void *stream);
 /* Training: gradients accumulate over images until hts_cnn_zero_grad; the
  * loss (mean squared error of log sigma against target_log_sigma, device,
- * N_ref) accumulates until hts_cnn_take_loss (synchronises). */
+ * N_ref) accumulates until hts_cnn_take_loss (synchronises).  By default a
+ * training step runs on the tensor cores: the forward of
+ * hts_cnn_log_sigma_map keeping every layer's FP16 activations, the
+ * gradients of the layer inputs in FP16 (the loss gradient scaled by
+ * 2^(floor(log2 N_ref) + 2), the scale divided out of the weight
+ * gradients), the weight and bias
+ * gradients accumulated in FP32.  hts_cnn_set_train_fp16(net, 0) selects
+ * the FP32 kernels instead (FP32 activations and gradients); either setting
+ * keeps FP32 master parameters and FP32 Adam state.  If a bounded wait of a
+ * training kernel gives up, the layer's gradient becomes NaN. */
+hts_status hts_cnn_set_train_fp16(hts_cnn *net, int on);
+int hts_cnn_train_fp16(const hts_cnn *net); /* 1: tensor-core training (default), 0: FP32, -1 for NULL */
 hts_status hts_cnn_zero_grad(hts_cnn *net, void *stream);
 hts_status hts_cnn_accumulate_grad(hts_cnn *net, const float *img, int H, int W, const hts_params *p,
                                    const float *target_log_sigma, void *stream);

@@ -132,6 +132,63 @@ def backward(theta: np.ndarray, cache, dout: np.ndarray) -> np.ndarray:
     return np.concatenate(out)
 
 
+def loss_scale(nref: int) -> float:
+    """The loss scale of the tensor-core training step: 2^(floor(log2 N_ref) + 2), so that the scaled loss
+    gradient 2 (out - target) / N_ref * scale lies within (4, 8] times the error."""
+    return float(2 ** (int(np.floor(np.log2(nref))) + 2))
+
+
+def grad_act16(theta: np.ndarray, img: np.ndarray, centres: np.ndarray, target_log_sigma: np.ndarray,
+               scale: float | None = None, rnd=fp16):
+    """Loss and gradient as the tensor-core training step forms them: the forward of forward_act16 (network
+    input and hidden activations rounded by `rnd`), the loss gradient map times `scale` (loss_scale by
+    default) rounded, and going back through each layer the gradient of its input (correlation with the
+    flipped kernels, times the ReLU mask of the stored activation) rounded; the weight and bias gradients are
+    exact sums of those rounded values, divided by `scale`.  With rnd = identity this is the FP64 gradient of
+    backward()."""
+    if scale is None:
+        scale = loss_scale(len(centres))
+    C = img.shape[0]
+    layers = unpack(theta, C)
+    a = rnd(np.asarray(img, dtype=np.float64) / 255.0)
+    acts = [a]
+    for li, (w, b) in enumerate(layers):
+        z = conv3x3(a, w, b)
+        a = rnd(np.maximum(z, 0.0)) if li < DEPTH - 1 else z
+        acts.append(a)
+    loss, dout = loss_and_dout(acts[-1][0], centres, target_log_sigma)
+    d = rnd(dout * scale)[None, :, :]
+    grads = []
+    for li in range(DEPTH - 1, -1, -1):
+        w, _ = layers[li]
+        x = acts[li]
+        ci, H, W = x.shape
+        xp = np.zeros((ci, H + 2, W + 2))
+        xp[:, 1:-1, 1:-1] = x
+        dw = np.empty_like(w)
+        for co in range(w.shape[0]):
+            for c in range(ci):
+                for ky in range(3):
+                    for kx in range(3):
+                        dw[co, c, ky, kx] = np.sum(d[co] * xp[c, ky:ky + H, kx:kx + W])
+        grads.append((dw / scale, d.sum(axis=(1, 2)) / scale))
+        if li > 0:
+            dp = np.zeros((w.shape[0], H + 2, W + 2))
+            dp[:, 1:-1, 1:-1] = d
+            dx = np.zeros((ci, H, W))
+            for c in range(ci):
+                for co in range(w.shape[0]):
+                    for ky in range(3):
+                        for kx in range(3):
+                            dx[c] += w[co, c, ky, kx] * dp[co, 2 - ky:2 - ky + H, 2 - kx:2 - kx + W]
+            d = rnd(dx * (acts[li] > 0))  # the ReLU of layer li - 1's output
+    out = []
+    for dw, db in reversed(grads):
+        out.append(dw.reshape(-1))
+        out.append(db)
+    return loss, np.concatenate(out)
+
+
 def ref_centres(H: int, W: int, ps: int = 8, step: int = 4):
     """(y + 4, x + 4) of every reference patch, raster order (Alg. 1 grid)."""
     def grid(n):

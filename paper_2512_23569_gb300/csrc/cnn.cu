@@ -3,7 +3,8 @@
 // global value (Sec. III-C), trained here by the library's own kernels.
 // This file holds the FP32 training path (forward with FP32 activations,
 // backward, Adam), the readout and the host interface; the forward pass used
-// for denoising runs on the tensor cores (cnn_tc.cu).
+// for denoising and the default (FP16) training step run on the tensor cores
+// (cnn_tc.cu).
 //
 // Network: the noisy image scaled by 1/255 goes through five 3x3
 // convolutions with zero padding (widths C -> 32 -> 32 -> 32 -> 32 -> 1,
@@ -303,6 +304,22 @@ __global__ void k_learned_final(int nref, double factor, DevState *st) {
     st->learned = (ratio > 0.0 && ratio >= 1.0 / factor && ratio <= factor) ? 1 : 0;
 }
 
+}  // namespace
+
+// The training loss over the reference patches and its gradient map (dout: H x W, zeroed here), for the
+// tensor-core training path (cnn_tc.cu).
+hts_status cnn_loss(const float *map, int H, int W, const Geom &g, const float *target, float *dout, double *loss,
+                    cudaStream_t s) {
+    HTS_TRY(cu(cudaMemsetAsync(dout, 0, (size_t)H * W * sizeof(float), s), "cudaMemsetAsync"));
+    {
+        KTimer kt("k_loss", s);
+        k_loss<<<1, 1024, 0, s>>>(map, H, W, g.step, g.nx, g.nref, target, dout, loss);
+    }
+    return check_launch("k_loss");
+}
+
+namespace {
+
 size_t fwd_smem(int cin, int cout) { return ((size_t)cin * HALO * HALO + (size_t)cout * cin * 9) * 4; }
 
 uint64_t splitmix64(uint64_t &x) {
@@ -444,6 +461,12 @@ void free_net(hts_cnn *n) {
     cudaFree(n->map);
     cudaFree(n->rows);
     cudaFree(n->err);
+    for (int i = 0; i < 4; ++i) cudaFree(n->tr_act[i]);
+    for (int i = 0; i < 2; ++i) cudaFree(n->tr_dy[i]);
+    cudaFree(n->tr_wt);
+    cudaFree(n->tr_map);
+    cudaFree(n->tr_d0);
+    cudaFree(n->tr_part);
     delete n;
 }
 
@@ -590,6 +613,14 @@ extern "C" hts_status hts_cnn_sigma_refs(hts_cnn *net, const float *img, int H, 
     return cnn_sigma_refs(net, img, g, sigma_ref, static_cast<cudaStream_t>(stream));
 }
 
+extern "C" hts_status hts_cnn_set_train_fp16(hts_cnn *net, int on) {
+    if (!net) return report(HTS_EINVAL, "NULL pointer");
+    net->train_tc = on ? 1 : 0;
+    return HTS_OK;
+}
+
+extern "C" int hts_cnn_train_fp16(const hts_cnn *net) { return net ? net->train_tc : -1; }
+
 extern "C" hts_status hts_cnn_zero_grad(hts_cnn *net, void *stream) {
     if (!net) return report(HTS_EINVAL, "NULL pointer");
     return cu(cudaMemsetAsync(net->grad, 0, net->nparams * sizeof(float), static_cast<cudaStream_t>(stream)),
@@ -603,6 +634,7 @@ extern "C" hts_status hts_cnn_accumulate_grad(hts_cnn *net, const float *img, in
     Geom g;
     HTS_TRY(validate(H, W, net->C, p, &g));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (net->train_tc) return cnn_grad_tc(net, img, H, W, g, target_log_sigma, s);
     HTS_TRY(ensure_ws(net, H, W));
     HTS_TRY(forward(net, img, H, W, s));
     const size_t px = (size_t)H * W;

@@ -25,6 +25,12 @@ struct hts_cnn {
     float *map = nullptr;   // its log-sigma map (H x W)
     float *rows = nullptr;  // row sums of the readout window (H x reference columns)
     int *err = nullptr;     // set by a tensor-core forward whose wait gave up (the map is then NaN)
+    // tensor-core training (cnn_tc.cu): per-layer FP16 activations, FP16 input gradients (ping-pong), the
+    // map and its loss gradient, per-block weight-gradient sums, the flipped weights of the backward passes
+    int train_tc = 1;  // 1: hts_cnn_accumulate_grad runs on the tensor cores (FP16); 0: the FP32 kernels
+    size_t tr_cap_px = 0, tr_cap_part = 0, tr_cap_wt = 0;
+    __half *tr_act[4] = {}, *tr_dy[2] = {}, *tr_wt = nullptr;
+    float *tr_map = nullptr, *tr_d0 = nullptr, *tr_part = nullptr;
 };
 
 namespace hts {
@@ -41,6 +47,13 @@ hts_status cnn_ensure_infer(hts_cnn *net, int H, int W, int nx);
 hts_status cnn_forward_tc_into(hts_cnn *net, const float *img, int H, int W, __half *h0, __half *h1, float *map,
                                cudaStream_t s);
 struct Geom;
+// Training loss (added to *loss) and its gradient map (dout, zeroed first) over the reference patches.
+hts_status cnn_loss(const float *map, int H, int W, const Geom &g, const float *target, float *dout, double *loss,
+                    cudaStream_t s);
+// One image's loss and gradient (added to net->grad) on the tensor cores: FP16 activations and input
+// gradients (loss scale 2^(floor(log2 N_ref) + 2)), FP32 accumulation of the weight gradients.
+hts_status cnn_grad_tc(hts_cnn *net, const float *img, int H, int W, const Geom &g, const float *target,
+                       cudaStream_t s);
 // Noise level of every reference patch (sigma_ref, device, N_ref) through the
 // readout window, from a forward into caller-owned buffers (rows: H * nx floats).
 hts_status cnn_sigma_refs_into(hts_cnn *net, const float *img, const Geom &g, __half *h0, __half *h1, float *map,

@@ -47,6 +47,41 @@ constexpr long long SPIN = 1ll << 22;
 // their tensor memory (at most 2 x 256 columns) is always free to allocate.
 constexpr size_t MIN_SMEM = 80 * 1024;
 
+// Epilogues: bias and ReLU to FP16 planes (forward, hidden layers), column 0 plus bias to the FP32 map
+// (forward, last layer), or the accumulated value times the ReLU mask of a stored activation to FP16 planes
+// (backward: the gradient of a layer's input, zero where the activation is zero).
+constexpr int EPI_RELU = 0, EPI_MAP = 1, EPI_MASK = 2;
+
+// One tile row of the epilogue: thread m of lane quarter q holds output pixel (oy, ox); r: its NOUT
+// accumulator columns (read by the caller).
+template <int NOUT, int EPI>
+__device__ __forceinline__ void epilogue_store(const uint32_t *r, const float *sBias, int H, int W, int oy, int ox,
+                                               __half *hout, float *map, const __half *hmask) {
+    if (oy >= H || ox >= W) return;
+    const size_t HW = (size_t)H * W;
+    if constexpr (EPI == EPI_MAP) {
+        map[(size_t)oy * W + ox] = __uint_as_float(r[0]) + sBias[0];
+    } else {
+#pragma unroll
+        for (int g = 0; g < NOUT / 8; ++g) {
+            const size_t pix = (size_t)g * HW + (size_t)oy * W + ox;
+            __align__(16) __half h[8];
+            if (EPI == EPI_RELU) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    h[c] = __float2half_rn(fmaxf(__uint_as_float(r[8 * g + c]) + sBias[8 * g + c], 0.f));
+            } else {
+                const uint4 mv = reinterpret_cast<const uint4 *>(hmask)[pix];
+                const __half *mk = reinterpret_cast<const __half *>(&mv);
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    h[c] = __float2half_rn(__hgt(mk[c], __float2half_rn(0.f)) ? __uint_as_float(r[8 * g + c]) : 0.f);
+            }
+            reinterpret_cast<uint4 *>(hout)[pix] = *reinterpret_cast<const uint4 *>(h);
+        }
+    }
+}
+
 template <int CING, int NOUT>
 struct ConvTcLayout {
     static constexpr size_t a_bytes = (size_t)CING * PY * PX * 16;  // staged input planes
@@ -62,14 +97,14 @@ struct ConvTcLayout {
 
 // CING: input planes of 8 channels (2 for layer 0, whose C <= 3 channels
 // occupy plane 0 and plane 1 is zero; 4 otherwise).  NOUT: MMA N.
-// IN_F32: the input is the FP32 image (planar C x H x W, scaled by 1/255);
-// otherwise FP16 planes hin[g][y][x][8].  OUT_MAP: write column 0 plus bias
-// to the FP32 map; otherwise ReLU, FP16 planes hout[g][y][x][8].
-template <int CING, int NOUT, bool IN_F32, bool OUT_MAP>
+// IN_F32: the input is an FP32 planar C x H x W array (the image) times
+// in_scale (1/255); otherwise FP16 planes hin[g][y][x][8].  EPI: the
+// epilogue (EPI_RELU, EPI_MAP, EPI_MASK with the activation planes hmask).
+template <int CING, int NOUT, bool IN_F32, int EPI>
 __global__ void __launch_bounds__(NTH, 1)
-    k_conv_tc(const float *__restrict__ img, int C, const __half *__restrict__ hin, int H, int W,
+    k_conv_tc(const float *__restrict__ img, int C, float in_scale, const __half *__restrict__ hin, int H, int W,
               const __half *__restrict__ wt, int cin, int cout, __half *__restrict__ hout, float *__restrict__ map,
-              int *err) {
+              const __half *__restrict__ hmask, int *err) {
     using L = ConvTcLayout<CING, NOUT>;
     extern __shared__ __align__(1024) unsigned char smem[];
     uint4 *sA = reinterpret_cast<uint4 *>(smem);
@@ -114,7 +149,7 @@ __global__ void __launch_bounds__(NTH, 1)
                         __align__(16) __half h[8];
 #pragma unroll
                         for (int c = 0; c < 8; ++c)
-                            h[c] = __float2half_rn(c < C ? img[c * HW + (size_t)y * W + x] * (1.f / 255.f) : 0.f);
+                            h[c] = __float2half_rn(c < C ? img[c * HW + (size_t)y * W + x] * in_scale : 0.f);
                         v = *reinterpret_cast<const uint4 *>(h);
                     }
                 } else {
@@ -159,26 +194,14 @@ __global__ void __launch_bounds__(NTH, 1)
         for (int j = warp >> 2; j < MT; j += 2) {
             const int ox = x0 + 8 * j + (m & 7);
             const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(j * NOUT);
-            if (OUT_MAP) {
-                const float v = __uint_as_float(tc::tmem_ld1(taddr));
-                tc::tmem_wait_ld();
-                if (oy < H && ox < W) map[(size_t)oy * W + ox] = v + sBias[0];
+            uint32_t r[32];
+            if (EPI == EPI_MAP) {
+                r[0] = tc::tmem_ld1(taddr);
             } else {
-                uint32_t r[32];
                 tc::tmem_ld32(taddr, r);
-                tc::tmem_wait_ld();
-                if (oy < H && ox < W) {
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        __align__(16) __half h[8];
-#pragma unroll
-                        for (int c = 0; c < 8; ++c)
-                            h[c] = __float2half_rn(fmaxf(__uint_as_float(r[8 * g + c]) + sBias[8 * g + c], 0.f));
-                        reinterpret_cast<uint4 *>(hout)[((size_t)g * H + oy) * W + ox] =
-                            *reinterpret_cast<const uint4 *>(h);
-                    }
-                }
             }
+            tc::tmem_wait_ld();
+            epilogue_store<NOUT, EPI>(r, sBias, H, W, oy, ox, hout, map, hmask);
         }
         tc::fence_before();
         __syncthreads();  // tensor memory and the staged planes are free for the next strip
@@ -209,10 +232,10 @@ struct ConvTmaLayout {
     static constexpr uint32_t tcols = MT * NOUT;
 };
 
-template <int NOUT, bool OUT_MAP>
+template <int NOUT, int EPI>
 __global__ void __launch_bounds__(NTH, 1)
     k_conv_tma(const __grid_constant__ CUtensorMap tmap, int H, int W, const __half *__restrict__ wt, int cin, int cout,
-               __half *__restrict__ hout, float *__restrict__ map, int *err) {
+               __half *__restrict__ hout, float *__restrict__ map, const __half *__restrict__ hmask, int *err) {
     using L = ConvTmaLayout<NOUT>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __half *sB = reinterpret_cast<__half *>(smem + L::b_off);
@@ -300,26 +323,14 @@ __global__ void __launch_bounds__(NTH, 1)
         for (int j = warp >> 2; j < MT; j += 2) {
             const int ox = x0 + 8 * j + (m & 7);
             const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(j * NOUT);
-            if (OUT_MAP) {
-                const float v = __uint_as_float(tc::tmem_ld1(taddr));
-                tc::tmem_wait_ld();
-                if (oy < H && ox < W) map[(size_t)oy * W + ox] = v + sBias[0];
+            uint32_t r[32];
+            if (EPI == EPI_MAP) {
+                r[0] = tc::tmem_ld1(taddr);
             } else {
-                uint32_t r[32];
                 tc::tmem_ld32(taddr, r);
-                tc::tmem_wait_ld();
-                if (oy < H && ox < W) {
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        __align__(16) __half h[8];
-#pragma unroll
-                        for (int c = 0; c < 8; ++c)
-                            h[c] = __float2half_rn(fmaxf(__uint_as_float(r[8 * g + c]) + sBias[8 * g + c], 0.f));
-                        reinterpret_cast<uint4 *>(hout)[((size_t)g * H + oy) * W + ox] =
-                            *reinterpret_cast<const uint4 *>(h);
-                    }
-                }
             }
+            tc::tmem_wait_ld();
+            epilogue_store<NOUT, EPI>(r, sBias, H, W, oy, ox, hout, map, hmask);
         }
         tc::fence_before();
         __syncthreads();  // tensor memory is free for the next strip
@@ -335,6 +346,9 @@ __global__ void __launch_bounds__(NTH, 1)
     if (warp == 0) tc::tmem_dealloc(tbase, L::tcols);
 }
 
+// The network's FP16 weights of layer l with its channel counts, as conv_tc / conv_tma take them.
+#define LW(n, l) (n)->w16 + (n)->off[l], (n)->cin[l], (n)->cout[l]
+
 // After a forward whose wait gave up: the whole map becomes NaN.
 __global__ void k_map_poison(float *map, size_t n, const int *err) {
     if (*err == 0) return;
@@ -342,28 +356,30 @@ __global__ void k_map_poison(float *map, size_t n, const int *err) {
         map[i] = __int_as_float(0x7fc00000);
 }
 
-template <int CING, int NOUT, bool IN_F32, bool OUT_MAP>
-hts_status conv_tc(const hts_cnn *n, int l, const float *img, const __half *hin, int H, int W, __half *hout,
-                   float *map, int nsm, cudaStream_t s) {
+// wt: FP16 weights [cout][cin][3][3] then cout biases (the network's, or the flipped ones of a backward pass).
+template <int CING, int NOUT, bool IN_F32, int EPI>
+hts_status conv_tc(const hts_cnn *n, const __half *wt, int cin, int cout, const float *img, int C, float in_scale,
+                   const __half *hin, int H, int W, __half *hout, float *map, const __half *hmask, int nsm,
+                   cudaStream_t s) {
     using L = ConvTcLayout<CING, NOUT>;
-    const void *k = reinterpret_cast<const void *>(k_conv_tc<CING, NOUT, IN_F32, OUT_MAP>);
+    const void *k = reinterpret_cast<const void *>(k_conv_tc<CING, NOUT, IN_F32, EPI>);
     const hts_status st = allow_smem(k, L::total);
     if (st != HTS_OK) return st;
     const int nstrip = ((H + SY - 1) / SY) * ((W + SX - 1) / SX);
     const int grid = std::max(1, std::min(nstrip, 2 * nsm));
     {
         KTimer kt("k_conv_tc", s);
-        k_conv_tc<CING, NOUT, IN_F32, OUT_MAP><<<grid, NTH, L::total, s>>>(
-            img, n->C, hin, H, W, n->w16 + n->off[l], n->cin[l], n->cout[l], hout, map, n->err);
+        k_conv_tc<CING, NOUT, IN_F32, EPI><<<grid, NTH, L::total, s>>>(img, C, in_scale, hin, H, W, wt, cin, cout,
+                                                                      hout, map, hmask, n->err);
     }
     return check_launch("k_conv_tc");
 }
 
 // A hidden layer with the TMA-staged input: the tensor map describes hin as [plane][y][x][8 halves], read
 // as 8-byte elements (3-D, innermost first: 2 W, H, 4 planes) with the box of one strip's staged input.
-template <int NOUT, bool OUT_MAP>
-hts_status conv_tma(const hts_cnn *n, int l, const __half *hin, int H, int W, __half *hout, float *map, int nsm,
-                    cudaStream_t s) {
+template <int NOUT, int EPI>
+hts_status conv_tma(const hts_cnn *n, const __half *wt, int cin, int cout, const __half *hin, int H, int W,
+                    __half *hout, float *map, const __half *hmask, int nsm, cudaStream_t s) {
     using L = ConvTmaLayout<NOUT>;
     const auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
     if (!enc) return report(HTS_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
@@ -377,17 +393,252 @@ hts_status conv_tma(const hts_cnn *n, int l, const __half *hin, int H, int W, __
                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return report(HTS_ECUDA, "cuTensorMapEncodeTiled failed for a network layer");
-    const void *k = reinterpret_cast<const void *>(k_conv_tma<NOUT, OUT_MAP>);
+    const void *k = reinterpret_cast<const void *>(k_conv_tma<NOUT, EPI>);
     const hts_status st = allow_smem(k, L::total);
     if (st != HTS_OK) return st;
     const int nstrip = ((H + SY - 1) / SY) * ((W + SX - 1) / SX);
     const int grid = std::max(1, std::min(nstrip, nsm));
     {
         KTimer kt("k_conv_tma", s);
-        k_conv_tma<NOUT, OUT_MAP><<<grid, NTH, L::total, s>>>(tmap, H, W, n->w16 + n->off[l], n->cin[l], n->cout[l],
-                                                               hout, map, n->err);
+        k_conv_tma<NOUT, EPI><<<grid, NTH, L::total, s>>>(tmap, H, W, wt, cin, cout, hout, map, hmask, n->err);
     }
     return check_launch("k_conv_tma");
+}
+
+// ------------------------------------------------------------------ training (backward) on the tensor cores
+
+// Weight and bias gradient of one 3x3 layer: dW[co][ci][ky][kx] = sum_p dY[co](p) X[ci](p + (ky - 1, kx - 1)),
+// db[co] = sum_p dY[co](p), a contraction over the pixels: D[(tap, ci)][co] = sum_p A[(tap, ci)][p] B[co][p]
+// with the pixels as the MMA's K.  A block takes strips of 8 x 64 pixels, stages X with a one-pixel halo and
+// dY as planes of 8 FP16 channels, and per strip row (64 pixels, four K steps) copies the 64 pixel vectors of
+// every (tap, plane) into a 1 KB group of a chunk buffer, so that the 8-row groups of A (8 channels of one
+// plane at one tap) lie 1 KB apart: A is MN-major (8 channels per 16-byte pixel vector), M = 128 rows = 16
+// groups per tile; one extra group holds ones (its rows give the bias gradient).  B is the staged dY row,
+// MN-major as well (core matrices of 8 pixels, planes 8 KB apart).  The block accumulates every strip it
+// takes in tensor memory and writes its sums once; k_wgrad_reduce adds the blocks' sums in block order.
+constexpr int WSY = 8;            // strip rows
+constexpr int WPY = WSY + 2;      // staged X rows
+constexpr int WCH = SX;           // pixels per chunk (one strip row)
+
+template <int CINX, int NPLY>
+struct WgradLayout {
+    static constexpr int NG = 9 * CINX + 1;        // (tap, plane) groups and the ones group
+    static constexpr int NTILE = (NG + 15) / 16;   // M tiles of 16 groups
+    static constexpr int N = NPLY * 8;             // MMA N: the output channels
+    static constexpr int ROWS = 9 * CINX * 8 + 1;  // rows written per block: (tap, ci), then the bias row
+    static constexpr size_t x_bytes = (size_t)CINX * WPY * PX * 16;
+    static constexpr size_t y_off = (x_bytes + 1023) / 1024 * 1024;
+    static constexpr size_t y_plane = (size_t)WSY * WCH * 16;
+    static constexpr size_t i_off = y_off + (size_t)NPLY * y_plane;
+    static constexpr size_t bar_off = i_off + (size_t)NTILE * 16 * 1024;
+    static constexpr size_t used = bar_off + 32;
+    static constexpr size_t total = used > MIN_SMEM ? used : MIN_SMEM;
+    static constexpr uint32_t tcols = NTILE * N <= 32 ? 32 : NTILE * N <= 64 ? 64 : NTILE * N <= 128 ? 128 : 256;
+};
+
+// X_F32: X is the FP32 image (planar, C channels) times 1/255, else FP16 planes xin[CINX][H][W][8].
+// Y_F32: dY is the FP32 gradient map (one channel) times y_scale, else FP16 planes yin[NPLY][H][W][8].
+template <int CINX, int NPLY, bool X_F32, bool Y_F32>
+__global__ void __launch_bounds__(NTH, 1)
+    k_conv_wgrad(const float *__restrict__ img, int C, const __half *__restrict__ xin, const float *__restrict__ ymap,
+                 float y_scale, const __half *__restrict__ yin, int H, int W, float *__restrict__ part,
+                 int *err) {
+    using L = WgradLayout<CINX, NPLY>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint4 *sX = reinterpret_cast<uint4 *>(smem);
+    uint4 *sY = reinterpret_cast<uint4 *>(smem + L::y_off);
+    uint4 *sI = reinterpret_cast<uint4 *>(smem + L::i_off);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L::bar_off);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const size_t HW = (size_t)H * W;
+    // chunk buffer: groups past the (tap, plane) ones: the ones group, then zeros
+    for (int e = tid; e < (L::NTILE * 16 - 9 * CINX) * WCH; e += NTH) {
+        const int gr = 9 * CINX + e / WCH;
+        const __half one = __float2half_rn(gr == 9 * CINX ? 1.f : 0.f);
+        const __half2 h2 = __halves2half2(one, one);
+        uint4 v;
+        v.x = v.y = v.z = v.w = *reinterpret_cast<const uint32_t *>(&h2);
+        sI[gr * WCH + (e % WCH)] = v;
+    }
+    if (tid == 0) {
+        tc::bar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) tc::tmem_alloc(slot, L::tcols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = *slot;
+    const uint32_t idesc = tc::idesc_f16(128, L::N, false) | (1u << 15) | (1u << 16);  // A and B MN-major
+    const int nsx = (W + WCH - 1) / WCH, nstrip = ((H + WSY - 1) / WSY) * nsx;
+    uint32_t phase = 0;
+    bool first = true, failed = false;
+    for (int strip = blockIdx.x; strip < nstrip && !failed; strip += gridDim.x) {
+        const int y0 = (strip / nsx) * WSY, x0 = (strip % nsx) * WCH;
+        // ---- stage X (halo, zero outside the image) and dY (zero outside)
+        for (int e = tid; e < CINX * WPY * PX; e += NTH) {
+            const int gp = e / (WPY * PX), r = e - gp * (WPY * PX), py = r / PX, px = r - py * PX;
+            const int y = y0 - 1 + py, x = x0 - 1 + px;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (y >= 0 && y < H && x >= 0 && x < W) {
+                if (X_F32) {
+                    __align__(16) __half h[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        h[c] = __float2half_rn(c < C ? img[c * HW + (size_t)y * W + x] * (1.f / 255.f) : 0.f);
+                    v = *reinterpret_cast<const uint4 *>(h);
+                } else {
+                    v = reinterpret_cast<const uint4 *>(xin)[((size_t)gp * H + y) * W + x];
+                }
+            }
+            sX[e] = v;
+        }
+        for (int e = tid; e < NPLY * WSY * WCH; e += NTH) {
+            const int gp = e / (WSY * WCH), r = e - gp * (WSY * WCH), py = r / WCH, px = r - py * WCH;
+            const int y = y0 + py, x = x0 + px;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (y < H && x < W) {
+                if (Y_F32) {
+                    if (gp == 0) {
+                        __align__(16) __half h[8];
+                        h[0] = __float2half_rn(ymap[(size_t)y * W + x] * y_scale);
+#pragma unroll
+                        for (int c = 1; c < 8; ++c) h[c] = __float2half_rn(0.f);
+                        v = *reinterpret_cast<const uint4 *>(h);
+                    }
+                } else {
+                    v = reinterpret_cast<const uint4 *>(yin)[((size_t)gp * H + y) * W + x];
+                }
+            }
+            sY[e] = v;
+        }
+        __syncthreads();
+        for (int r = 0; r < WSY; ++r) {
+            // ---- the chunk (strip row r): group (tap, plane) = the 64 staged X vectors of that tap's shift
+            for (int e = tid; e < 9 * CINX * WCH; e += NTH) {
+                const int gr = e / WCH, px = e - gr * WCH;
+                const int tap = gr / CINX, gp = gr - tap * CINX, ky = tap / 3, kx = tap - 3 * ky;
+                sI[gr * WCH + px] = sX[(gp * WPY + r + ky) * PX + px + kx];
+            }
+            tc::fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after();
+                const uint32_t a0 = tc::su32(sI), b0 = tc::su32(sY) + (uint32_t)(r * WCH * 16);
+#pragma unroll
+                for (int t = 0; t < L::NTILE; ++t)
+#pragma unroll
+                    for (int kk = 0; kk < WCH / 16; ++kk) {
+                        const uint64_t ad = tc::sdesc(a0 + t * 16 * 1024 + kk * 256, 128, 1024);
+                        const uint64_t bd = tc::sdesc(b0 + kk * 256, 128, (uint32_t)L::y_plane);
+                        tc::mma_f16(tbase + t * L::N, ad, bd, idesc, (first && kk == 0) ? 0u : 1u);
+                    }
+                tc::mma_commit(bar);
+            }
+            const bool done = tc::bar_wait(bar, phase, SPIN);
+            if (__syncthreads_or(!done)) {
+                if (tid == 0) {
+                    tc::bar_wait(bar, phase, SPIN);  // the MMAs must end before the memory is released
+                    atomicExch(err, 1);
+                }
+                failed = true;
+                break;
+            }
+            phase ^= 1u;
+            tc::fence_after();
+            first = false;
+        }
+    }
+    // ---- the block's sums: row (tap, ci) or the bias row, N output channels
+    if (!failed && !first) {
+        const int q = warp & 3;
+        for (int t = warp >> 2; t < L::NTILE; t += NTH / 128) {
+            const int row = t * 128 + 32 * q + lane, gr = row >> 3, ch = row & 7;
+            uint32_t v[32];
+            const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(t * L::N);
+            if constexpr (L::N == 32) {
+                tc::tmem_ld32(taddr, v);
+            } else {
+                tc::tmem_ld16(taddr, *reinterpret_cast<uint32_t(*)[16]>(v));
+            }
+            tc::tmem_wait_ld();
+            int orow = -1;
+            if (gr < 9 * CINX) orow = gr * 8 + ch;                  // (tap, plane, channel) = tap * 8 CINX + ci
+            else if (gr == 9 * CINX && ch == 0) orow = L::ROWS - 1;  // the bias
+            if (orow >= 0) {
+                float *dst = part + ((size_t)blockIdx.x * L::ROWS + orow) * L::N;
+#pragma unroll
+                for (int n = 0; n < L::N; ++n) dst[n] = __uint_as_float(v[n]);
+            }
+        }
+    } else if (!failed) {  // a block without strips adds zeros
+        for (int e = tid; e < L::ROWS * L::N; e += NTH) part[(size_t)blockIdx.x * L::ROWS * L::N + e] = 0.f;
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, L::tcols);
+}
+
+// grad[e] += (sum over the blocks, in block order, of their sums) / scale for every parameter of the layer
+// (cout x cin x 9 weights, then cout biases); NaN everywhere after a wait that gave up.
+__global__ void k_wgrad_reduce(const float *__restrict__ part, int nblk, int rows, int N, int cin, int cout,
+                               int cin_pad, float inv_scale, const int *err, float *__restrict__ grad) {
+    const int ne = cout * cin * 9 + cout;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+        int row, co;
+        if (e < cout * cin * 9) {
+            co = e / (cin * 9);
+            const int rem = e - co * cin * 9, ci = rem / 9, tap = rem - ci * 9;
+            row = tap * cin_pad + ci;
+        } else {
+            co = e - cout * cin * 9;
+            row = rows - 1;
+        }
+        float s = 0.f;
+        for (int b = 0; b < nblk; ++b) s += part[((size_t)b * rows + row) * N + co];
+        grad[e] = *err ? __int_as_float(0x7fc00000) : grad[e] + s * inv_scale;
+    }
+}
+
+// The flipped, transposed weights of a backward pass through layer l: out channel n = the layer's input
+// channel, input channel c = its output channel, tap 8 - t; biases zero.
+__global__ void k_wflip(const __half *__restrict__ w, int cout, int cin, __half *__restrict__ wt) {
+    const int ne = cin * cout * 9;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne + cin; e += gridDim.x * blockDim.x) {
+        if (e >= ne) {
+            wt[e] = __float2half_rn(0.f);
+            continue;
+        }
+        const int n = e / (cout * 9), rem = e - n * cout * 9, c = rem / 9, tap = rem - c * 9;
+        wt[e] = w[(c * cin + n) * 9 + (8 - tap)];
+    }
+}
+
+// y_scale: the loss scale dY carries (applied here when dY is the FP32 map, by the caller otherwise); the
+// reduction divides it out.
+template <int CINX, int NPLY, bool X_F32, bool Y_F32>
+hts_status conv_wgrad(hts_cnn *n, int l, const float *img, const __half *xin, const float *ymap, float y_scale,
+                      const __half *yin, int H, int W, int nsm, cudaStream_t s) {
+    using L = WgradLayout<CINX, NPLY>;
+    const void *k = reinterpret_cast<const void *>(k_conv_wgrad<CINX, NPLY, X_F32, Y_F32>);
+    hts_status st = allow_smem(k, L::total);
+    if (st != HTS_OK) return st;
+    const int nstrip = ((H + WSY - 1) / WSY) * ((W + WCH - 1) / WCH);
+    const int grid = std::max(1, std::min(nstrip, nsm));
+    {
+        KTimer kt("k_conv_wgrad", s);
+        k_conv_wgrad<CINX, NPLY, X_F32, Y_F32><<<grid, NTH, L::total, s>>>(img, n->C, xin, ymap, y_scale, yin, H, W,
+                                                                          n->tr_part, n->err);
+    }
+    st = check_launch("k_conv_wgrad");
+    if (st != HTS_OK) return st;
+    {
+        KTimer kt("k_wgrad_reduce", s);
+        k_wgrad_reduce<<<64, 256, 0, s>>>(n->tr_part, grid, L::ROWS, L::N, n->cin[l], n->cout[l], CINX * 8,
+                                          1.f / y_scale, n->err, n->grad + n->off[l]);
+    }
+    return check_launch("k_wgrad_reduce");
 }
 
 }  // namespace
@@ -434,17 +685,114 @@ hts_status cnn_forward_tc_into(hts_cnn *n, const float *img, int H, int W, __hal
         cudaGetLastError();
         return report(HTS_ECUDA, "cudaMemsetAsync(cnn error flag)");
     }
-    hts_status st = conv_tc<2, 32, true, false>(n, 0, img, nullptr, H, W, h0, nullptr, nsm, s);
-    if (st == HTS_OK) st = conv_tma<32, false>(n, 1, h0, H, W, h1, nullptr, nsm, s);
-    if (st == HTS_OK) st = conv_tma<32, false>(n, 2, h1, H, W, h0, nullptr, nsm, s);
-    if (st == HTS_OK) st = conv_tma<32, false>(n, 3, h0, H, W, h1, nullptr, nsm, s);
-    if (st == HTS_OK) st = conv_tma<16, true>(n, 4, h1, H, W, nullptr, map, nsm, s);
+    hts_status st = conv_tc<2, 32, true, EPI_RELU>(n, LW(n, 0), img, n->C, 1.f / 255.f, nullptr, H, W, h0, nullptr,
+                                                   nullptr, nsm, s);
+    if (st == HTS_OK) st = conv_tma<32, EPI_RELU>(n, LW(n, 1), h0, H, W, h1, nullptr, nullptr, nsm, s);
+    if (st == HTS_OK) st = conv_tma<32, EPI_RELU>(n, LW(n, 2), h1, H, W, h0, nullptr, nullptr, nsm, s);
+    if (st == HTS_OK) st = conv_tma<32, EPI_RELU>(n, LW(n, 3), h0, H, W, h1, nullptr, nullptr, nsm, s);
+    if (st == HTS_OK) st = conv_tma<16, EPI_MAP>(n, LW(n, 4), h1, H, W, nullptr, map, nullptr, nsm, s);
     if (st != HTS_OK) return st;
     {
         KTimer kt("k_map_poison", s);
         k_map_poison<<<nsm, 256, 0, s>>>(map, (size_t)H * W, n->err);
     }
     return check_launch("k_map_poison");
+}
+
+
+// ------------------------------------------------------------------ tensor-core training step
+
+namespace {
+constexpr int WG_ROWS_MAX = 9 * 4 * 8 + 1;
+}  // namespace
+
+hts_status cnn_train_ensure(hts_cnn *n, int H, int W, int nsm) {
+    const size_t px = (size_t)H * W;
+    if (px > n->tr_cap_px) {
+        for (int i = 0; i < 4; ++i) {
+            cudaFree(n->tr_act[i]);
+            n->tr_act[i] = nullptr;
+        }
+        for (int i = 0; i < 2; ++i) {
+            cudaFree(n->tr_dy[i]);
+            n->tr_dy[i] = nullptr;
+        }
+        cudaFree(n->tr_map);
+        cudaFree(n->tr_d0);
+        n->tr_map = n->tr_d0 = nullptr;
+        n->tr_cap_px = 0;
+        size_t cap = 0;
+        for (int i = 0; i < 4; ++i) {
+            cap = 0;
+            if (grow_buf(n->tr_act[i], cap, px * 32) != HTS_OK) return HTS_ENOMEM;
+        }
+        for (int i = 0; i < 2; ++i) {
+            cap = 0;
+            if (grow_buf(n->tr_dy[i], cap, px * 32) != HTS_OK) return HTS_ENOMEM;
+        }
+        cap = 0;
+        if (grow_buf(n->tr_map, cap, px) != HTS_OK) return HTS_ENOMEM;
+        cap = 0;
+        if (grow_buf(n->tr_d0, cap, px) != HTS_OK) return HTS_ENOMEM;
+        n->tr_cap_px = px;
+    }
+    hts_status st = grow_buf(n->tr_part, n->tr_cap_part, (size_t)nsm * WG_ROWS_MAX * 32);
+    if (st != HTS_OK) return st;
+    return grow_buf(n->tr_wt, n->tr_cap_wt, (size_t)n->nparams + 5 * 32);
+}
+
+// One image's loss and gradient on the tensor cores: the forward of cnn_forward_tc keeping every layer's
+// FP16 activations, the loss gradient map 2 (out - target) / N_ref times the loss scale 2^(floor(log2 N_ref)
+// + 2) (so (4, 8] times the error, well inside FP16's range) rounded to FP16, then per layer from the last:
+// the weight and bias gradients (k_conv_wgrad, FP32 accumulation, the scale divided out) and the gradient of
+// the layer input (the forward kernels with the flipped, transposed weights, times the ReLU mask of the
+// stored activation, FP16).
+hts_status cnn_grad_tc(hts_cnn *n, const float *img, int H, int W, const Geom &g, const float *target,
+                       cudaStream_t s) {
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    hts_status st = cnn_train_ensure(n, H, W, nsm);
+    if (st != HTS_OK) return st;
+    if (cudaMemsetAsync(n->err, 0, sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        return report(HTS_ECUDA, "cudaMemsetAsync(cnn error flag)");
+    }
+    __half **a = n->tr_act;
+    const float S = ldexpf(1.f, ilogb((double)g.nref) + 2);
+    st = conv_tc<2, 32, true, EPI_RELU>(n, LW(n, 0), img, n->C, 1.f / 255.f, nullptr, H, W, a[0], nullptr, nullptr,
+                                        nsm, s);
+    for (int l = 1; l < 4 && st == HTS_OK; ++l)
+        st = conv_tma<32, EPI_RELU>(n, LW(n, l), a[l - 1], H, W, a[l], nullptr, nullptr, nsm, s);
+    if (st == HTS_OK) st = conv_tma<16, EPI_MAP>(n, LW(n, 4), a[3], H, W, nullptr, n->tr_map, nullptr, nsm, s);
+    if (st == HTS_OK) st = cnn_loss(n->tr_map, H, W, g, target, n->tr_d0, n->loss, s);
+    if (st != HTS_OK) return st;
+    // flipped weights of layers 1..4 (layer l's at n->off[l] + 32 l: its cin biases follow its weights)
+    for (int l = 1; l < 5; ++l) {
+        {
+            KTimer kt("k_wflip", s);
+            k_wflip<<<64, 256, 0, s>>>(n->w16 + n->off[l], n->cout[l], n->cin[l], n->tr_wt + n->off[l] + 32 * l);
+        }
+        st = check_launch("k_wflip");
+        if (st != HTS_OK) return st;
+    }
+    auto wf = [&](int l) { return n->tr_wt + n->off[l] + 32 * l; };
+    // layer 4 (linear): its gradients from the loss map, then the gradient of its input
+    st = conv_wgrad<4, 2, false, true>(n, 4, nullptr, a[3], n->tr_d0, S, nullptr, H, W, nsm, s);
+    if (st == HTS_OK)
+        st = conv_tc<2, 32, true, EPI_MASK>(n, wf(4), n->cout[4], n->cin[4], n->tr_d0, 1, S, nullptr, H, W,
+                                            n->tr_dy[0], nullptr, a[3], nsm, s);
+    int cur = 0;
+    for (int l = 3; l >= 1 && st == HTS_OK; --l) {
+        st = conv_wgrad<4, 4, false, false>(n, l, nullptr, a[l - 1], nullptr, S, n->tr_dy[cur], H, W, nsm, s);
+        if (st == HTS_OK)
+            st = conv_tma<32, EPI_MASK>(n, wf(l), n->cout[l], n->cin[l], n->tr_dy[cur], H, W, n->tr_dy[cur ^ 1],
+                                        nullptr, a[l - 1], nsm, s);
+        cur ^= 1;
+    }
+    if (st == HTS_OK)
+        st = conv_wgrad<1, 4, true, false>(n, 0, img, nullptr, nullptr, S, n->tr_dy[cur], H, W, nsm, s);
+    return st;
 }
 
 }  // namespace hts

@@ -32,7 +32,8 @@ EXPORTS = [
     "hts_denoise_sigma_map", "hts_denoise_learned", "hts_cnn_num_params", "hts_cnn_channels", "hts_cnn_create",
     "hts_cnn_free", "hts_cnn_get_params", "hts_cnn_set_params", "hts_cnn_log_sigma_map", "hts_cnn_sigma_refs",
     "hts_cnn_zero_grad", "hts_cnn_accumulate_grad", "hts_cnn_take_loss", "hts_cnn_get_grad", "hts_cnn_adam_step",
-    "hts_cnn_save", "hts_cnn_load", "hts_cnn_set_window", "hts_cnn_window",
+    "hts_cnn_save", "hts_cnn_load", "hts_cnn_set_window", "hts_cnn_window", "hts_cnn_set_train_fp16",
+    "hts_cnn_train_fp16",
     "hts_fcn_num_params", "hts_fcn_channels", "hts_fcn_create", "hts_fcn_free", "hts_fcn_get_params",
     "hts_fcn_set_params", "hts_group_means", "hts_fcn_refine", "hts_fcn_zero_grad", "hts_fcn_accumulate_grad",
     "hts_fcn_take_loss", "hts_fcn_get_grad", "hts_fcn_adam_step", "hts_denoise_ra", "hts_mean_coefs",
@@ -140,6 +141,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.hts_cnn_set_window.argtypes = [P, I]
         lib.hts_cnn_window.argtypes = [P]
         lib.hts_cnn_window.restype = I
+        lib.hts_cnn_set_train_fp16.argtypes = [P, I]
+        lib.hts_cnn_train_fp16.argtypes = [P]
+        lib.hts_cnn_train_fp16.restype = I
         lib.hts_fcn_num_params.argtypes = [I]
         lib.hts_fcn_num_params.restype = I
         lib.hts_fcn_channels.argtypes = [P]
@@ -378,6 +382,15 @@ class Cnn:
     def window(self, S: int) -> None:
         _check(load().hts_cnn_set_window(self._h, int(S)))
 
+    @property
+    def train_fp16(self) -> bool:
+        """True: training steps run on the tensor cores (FP16 activations and gradients); False: FP32 kernels."""
+        return bool(load().hts_cnn_train_fp16(self._h))
+
+    @train_fp16.setter
+    def train_fp16(self, on: bool) -> None:
+        _check(load().hts_cnn_set_train_fp16(self._h, 1 if on else 0))
+
     def get_params(self) -> np.ndarray:
         a = np.empty(self.nparams, dtype=np.float32)
         _check(load().hts_cnn_get_params(self._h, ctypes.c_void_p(a.ctypes.data)))
@@ -517,6 +530,15 @@ class Fcn:
     @property
     def handle(self):
         return self._h
+
+    @property
+    def train_fp16(self) -> bool:
+        """True: training steps run on the tensor cores (FP16 activations and gradients); False: FP32 kernels."""
+        return bool(load().hts_cnn_train_fp16(self._h))
+
+    @train_fp16.setter
+    def train_fp16(self, on: bool) -> None:
+        _check(load().hts_cnn_set_train_fp16(self._h, 1 if on else 0))
 
     def get_params(self) -> np.ndarray:
         a = np.empty(self.nparams, dtype=np.float32)

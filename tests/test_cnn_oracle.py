@@ -125,3 +125,36 @@ def test_fp16_activation_forward():
     a, b = co.forward_act16(theta, img), co.forward(theta, img)[0]
     assert np.max(np.abs(a - b)) > 0
     assert np.max(np.abs(a - b)) <= 50 * 2.0 ** -11 * (1.0 + np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("C", [1, 3])
+def test_fp16_training_gradient(C):
+    # structure: with the rounding replaced by the identity, the tensor-core training step's gradient is
+    # the FP64 gradient of backward() (pinned above by finite differences) at any loss scale
+    rng = np.random.default_rng(20 + C)
+    theta = co.fp16(rng.standard_normal(co.num_params(C)) * 0.2)
+    img = rng.uniform(0, 255, size=(C, 12, 16))
+    cen = co.ref_centres(12, 16)
+    tgt = rng.standard_normal(len(cen))
+    out, cache = co.forward(theta, img)
+    L, dout = co.loss_and_dout(out, cen, tgt)
+    want = co.backward(theta, cache, dout)
+    for scale in (1.0, 16384.0):
+        L2, got = co.grad_act16(theta, img, cen, tgt, scale=scale, rnd=lambda v: v)
+        assert abs(L2 - L) <= 1e-12 * (1 + L)
+        np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-12 * np.max(np.abs(want)))
+    # with FP16 rounding (He-scaled weights, as the library initialises them) every layer's gradient stays
+    # within a few FP16 roundoffs of the exact one
+    theta = np.concatenate([np.concatenate([rng.standard_normal(co_ * ci * 9) * np.sqrt(2.0 / (9 * ci)),
+                                            np.zeros(co_)]) for co_, ci in co.layer_shapes(C)])
+    theta = co.fp16(theta)
+    out, cache = co.forward(theta, img)
+    want = co.backward(theta, cache, co.loss_and_dout(out, cen, tgt)[1])
+    L3, g16 = co.grad_act16(theta, img, cen, tgt)
+    assert len(cen) == 6 and co.loss_scale(len(cen)) == 16.0  # 2 x 3 references: 2^(2 + 2)
+    o = 0
+    for cout, cin in co.layer_shapes(C):
+        n = cout * cin * 9 + cout
+        a, b = g16[o:o + n], want[o:o + n]
+        assert np.linalg.norm(a - b) <= 0.02 * np.linalg.norm(b), (cout, cin)
+        o += n

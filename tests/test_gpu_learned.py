@@ -87,10 +87,11 @@ def test_network_matches_oracle(hts, C, H, W):
         net.window = S
         np.testing.assert_allclose(net.sigma_refs(_dev(img), p).cpu().numpy(), co.window_sigma(out16, cen, S),
                                    rtol=2 * tol)
-    # loss and gradient
+    # loss and gradient of the FP32 training kernels
     tgt = rng.uniform(1.0, 3.5, size=len(cen)).astype(np.float32)
     L, dout = co.loss_and_dout(out, cen, tgt)
     g = co.backward(th16, cache, dout)
+    net.train_fp16 = False
     net.zero_grad()
     net.accumulate_grad(_dev(img), _dev(tgt), p)
     assert net.take_loss() == pytest.approx(L, rel=1e-4)
@@ -102,6 +103,59 @@ def test_network_matches_oracle(hts, C, H, W):
     net.adam_step(1e-2)
     want, _, _ = co.adam_step(theta.astype(np.float64), 0.0, 0.0, gg.astype(np.float64), 1, 1e-2)
     np.testing.assert_allclose(net.get_params(), want, rtol=1e-5, atol=1e-7)
+
+
+def _he_params(co, C, rng):
+    # He-scaled weights (the library's initialisation) and small biases: activations stay O(1)
+    parts = []
+    for cout, cin in co.layer_shapes(C):
+        parts.append(rng.standard_normal(cout * cin * 9) * np.sqrt(2.0 / (9 * cin)))
+        parts.append(rng.standard_normal(cout) * 0.05)
+    return np.concatenate(parts).astype(np.float32)
+
+
+@pytest.mark.parametrize("C,H,W", [(1, 24, 28), (3, 24, 28), (3, 45, 150)])
+def test_fp16_training_step_matches_oracle(hts, C, H, W):
+    # the tensor-core training step (the default): FP16 activations and input gradients, FP32 weight
+    # gradients; against the oracle that rounds the same values (grad_act16), and near the exact FP64
+    # gradient.  45 x 150 spans 6 x 3 strips of 8 x 64 pixels of the weight-gradient kernel, ragged ones last
+    from oracle import cnn_oracle as co
+
+    p = hts.params()
+    rng = np.random.default_rng(200 + C)
+    net = hts.Cnn(C, seed=5)
+    assert net.train_fp16
+    theta = _he_params(co, C, rng)
+    net.set_params(theta)
+    th16 = co.fp16(theta)
+    cen = co.ref_centres(H, W)
+    imgs = [rng.uniform(0, 255, size=(C, H, W)).astype(np.float32) for _ in range(2)]
+    tgts = [rng.uniform(1.0, 3.5, size=len(cen)).astype(np.float32) for _ in range(2)]
+    net.zero_grad()
+    L16, g16, gex = 0.0, 0.0, 0.0
+    for img, tgt in zip(imgs, tgts):  # two images: the gradients add up
+        net.accumulate_grad(_dev(img), _dev(tgt), p)
+        l16, gi = co.grad_act16(th16, img, cen, tgt)
+        out, cache = co.forward(th16, img)
+        L16 += l16
+        g16 = g16 + gi
+        gex = gex + co.backward(th16, cache, co.loss_and_dout(out, cen, tgt)[1])
+    assert net.take_loss() == pytest.approx(L16, rel=1e-4)
+    gg = net.get_grad()
+    assert np.all(np.isfinite(gg))
+    for sl in _layer_slices(co, C):
+        # FP32 against FP64 accumulation can move a stored FP16 value by one unit (2^-11) now and then
+        assert np.linalg.norm(gg[sl] - g16[sl]) <= 2e-3 * np.linalg.norm(g16[sl]) + 1e-9
+        assert np.linalg.norm(gg[sl] - gex[sl]) <= 3e-2 * np.linalg.norm(gex[sl]) + 1e-9
+    # the same step on the FP32 kernels agrees with the exact gradient; both settings train the same net
+    net.train_fp16 = False
+    net.zero_grad()
+    for img, tgt in zip(imgs, tgts):
+        net.accumulate_grad(_dev(img), _dev(tgt), p)
+    net.take_loss()
+    g32 = net.get_grad()
+    for sl in _layer_slices(co, C):
+        assert np.linalg.norm(g32[sl] - gex[sl]) <= 1e-3 * np.linalg.norm(gex[sl]) + 1e-9
 
 
 def test_denoising_forward_full_size_samples(hts):
@@ -146,13 +200,15 @@ def test_training_beats_one_global_sigma(hts):
         assert hts.last_stats()["learned"] == 1
         b = hts.denoise(x, p=p).cpu().numpy()
         gains.append(synth.psnr(a, clean) - synth.psnr(b, clean))
-        # the map's noise levels against the generator's, beside the one eigenvalue estimate's
+        # the map's shape against the generator's per-patch levels: the network learns log(m* sigma) with the
+        # best-PSNR multiplier m*, so both are compared up to a constant; one global level (any constant)
+        # leaves at best the spread of the true levels about their mean
         truth = synth.ref_log_sigma(spx, 8, 4).astype(np.float64)
         lmap = np.log(net.sigma_refs(x, p).cpu().numpy().astype(np.float64))
-        est, _ = hts.estimate_sigma(x, p)
-        err_net.append(np.sqrt(np.mean((lmap - truth) ** 2)))
-        err_est.append(np.sqrt(np.mean((np.log(est) - truth) ** 2)))
-    # measured: about +1 dB and a map several times closer to the true levels than one global estimate
+        d = lmap - truth
+        err_net.append(np.sqrt(np.mean((d - d.mean()) ** 2)))
+        err_est.append(np.sqrt(np.mean((truth - truth.mean()) ** 2)))
+    # measured: about +1 dB, and a map that follows the per-patch levels
     assert np.mean(gains) > 0.3, gains
     assert np.mean(err_net) < np.mean(err_est), (err_net, err_est)
 
