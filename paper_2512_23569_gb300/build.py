@@ -19,6 +19,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhts.so")
+# the check build: every translation unit with -DHTS_CHECK (device-side bounds checks, error code 3)
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(HERE, "libhts_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-warn-spills"]
 
@@ -37,8 +40,12 @@ def _stale(out: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, check: bool = False) -> str:
+    """Compile csrc/*.cu for sm_103a and link libhts.so (check=True: libhts_check.so with the bounds checks)."""
     nvcc = _nvcc()
+    BUILD = BUILD_CHECK if check else globals()["BUILD"]
+    LIB = LIB_CHECK if check else globals()["LIB"]
+    extra = list(extra or []) + (["-DHTS_CHECK"] if check else [])
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(CSRC, "*.h"))) + [os.path.join(os.path.dirname(HERE), "include", "hts.h")]
@@ -67,10 +74,10 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
-            raise RuntimeError("link of libhts.so failed")
+            raise RuntimeError("link of %s failed" % os.path.basename(LIB))
         os.replace(tmp, LIB)
     return LIB
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, check="--check" in sys.argv))

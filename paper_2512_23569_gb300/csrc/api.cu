@@ -227,9 +227,11 @@ static hts_status cuda_ok(cudaError_t e, const char *what) {
 }
 
 // Status of a failure the kernels recorded in DevState.error (2: a bounded
-// wait gave up; 1: a consistency check failed).
+// wait gave up; 1: a consistency check failed; 3: a bounds check of the check
+// build failed).
 hts_status device_status(int err) {
     if (err == 2) return fail(HTS_ETIMEOUT, "a bounded device-side wait gave up; the call's result is invalid");
+    if (err == 3) return fail(HTS_EINTERNAL, "a device-side bounds check failed; the call's result is invalid");
     if (err != 0) return fail(HTS_EINTERNAL, "a device-side consistency check failed; the call's result is invalid");
     return HTS_OK;
 }

@@ -212,13 +212,16 @@ __global__ void __launch_bounds__(NTH, 1)
 }
 
 // Hidden layers (1..4: four planes of 8 FP16 channels in), with the input staged by TMA: a block runs
-// its strips in turn with two staging buffers; while strip i's MMAs and epilogue run, the tensor-memory
-// accumulators being read and the outputs written, the TMA copy of strip i + 1's input (the same
-// 4 x 18 x 66 box of 16-byte pixel vectors, zero outside the image) lands in the other buffer.  One
-// block per SM (two 76 KB buffers).  Waits bounded as in k_conv_tc; a block that gives up waits
+// its strips (16 x 32 output pixels: four 16 x 8 tiles) in turn with two staging buffers; while strip i's
+// MMAs and epilogue run, the tensor-memory accumulators being read and the outputs written, the TMA copy of
+// strip i + 1's input (the same 4 x 18 x 34 box of 16-byte pixel vectors, zero outside the image) lands in
+// the other buffer.  Two blocks per SM (two 39 KB buffers each, 128 tensor-memory columns): the second
+// block's warps hide the first's latencies.  Waits bounded as in k_conv_tc; a block that gives up waits
 // (bounded) for its copy in flight and its MMAs before it releases its tensor memory.
 constexpr int CING_H = 4;
-constexpr size_t TMA_BOX_BYTES = (size_t)CING_H * PY * PX * 16;
+constexpr int MTH = 4;                 // tiles per strip of the hidden layers
+constexpr int SXH = 8 * MTH, PXH = SXH + 2;
+constexpr size_t TMA_BOX_BYTES = (size_t)CING_H * PY * PXH * 16;
 constexpr size_t TMA_BUF = (TMA_BOX_BYTES + 1023) / 1024 * 1024;
 
 template <int NOUT>
@@ -229,7 +232,7 @@ struct ConvTmaLayout {
     static constexpr size_t bias_off = b_off + b_bytes;
     static constexpr size_t bar_off = (bias_off + (size_t)NOUT * 4 + 15) / 16 * 16;
     static constexpr size_t total = bar_off + 4 * 8 + 16;
-    static constexpr uint32_t tcols = MT * NOUT;
+    static constexpr uint32_t tcols = MTH * NOUT;
 };
 
 template <int NOUT, int EPI>
@@ -252,7 +255,7 @@ __global__ void __launch_bounds__(NTH, 1)
         sB[e] = (n < cout && ci < cin) ? wt[(n * cin + ci) * 9 + tap] : __float2half_rn(0.f);
     }
     for (int n = tid; n < NOUT; n += NTH) sBias[n] = n < cout ? __half2float(wt[cout * cin * 9 + n]) : 0.f;
-    const int nsx = (W + SX - 1) / SX, nstrip = ((H + SY - 1) / SY) * nsx;
+    const int nsx = (W + SXH - 1) / SXH, nstrip = ((H + SY - 1) / SY) * nsx;
     if (tid == 0) {
         tc::bar_init(&full[0], 1);
         tc::bar_init(&full[1], 1);
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(NTH, 1)
     const uint32_t tbase = *slot;
     const uint32_t idesc = tc::idesc_f16(128, NOUT, false);
     auto issue_copy = [&](int strip, int b) {  // thread 0: the strip's input box into buffer b
-        const int y0 = (strip / nsx) * SY, x0 = (strip % nsx) * SX;
+        const int y0 = (strip / nsx) * SY, x0 = (strip % nsx) * SXH;
         tc::bar_arrive_expect_tx(&full[b], (uint32_t)TMA_BOX_BYTES);
         tc::tma_load_3d(smem + (b ? L::buf1 : L::buf0), &tmap, &full[b], 2 * (x0 - 1), y0 - 1, 0);
     };
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(NTH, 1)
     int i = 0;
     for (int strip = blockIdx.x; strip < nstrip; strip += gridDim.x, ++i) {
         const int b = i & 1;
-        const int y0 = (strip / nsx) * SY, x0 = (strip % nsx) * SX;
+        const int y0 = (strip / nsx) * SY, x0 = (strip % nsx) * SXH;
         // the next strip's copy goes out now (its buffer's last reader, strip i - 1's MMAs, has completed)
         const int next = strip + gridDim.x;
         if (next < nstrip) {
@@ -297,14 +300,14 @@ __global__ void __launch_bounds__(NTH, 1)
         if (tid == 0) {
             tc::fence_after();
             const uint32_t a0 = tc::su32(smem + (b ? L::buf1 : L::buf0)), b0 = tc::su32(sB);
-            for (int j = 0; j < MT; ++j)
+            for (int j = 0; j < MTH; ++j)
                 for (int tap = 0; tap < 9; ++tap) {
                     const int ky = tap / 3, kx = tap - 3 * ky;
 #pragma unroll
                     for (int ss = 0; ss < CING_H / 2; ++ss) {
-                        const uint32_t aoff = (uint32_t)((((2 * ss) * PY + ky) * PX + 8 * j + kx) * 16);
+                        const uint32_t aoff = (uint32_t)((((2 * ss) * PY + ky) * PXH + 8 * j + kx) * 16);
                         const uint32_t boff = (uint32_t)((tap * CING_H + 2 * ss) * NOUT * 16);
-                        const uint64_t ad = tc::sdesc(a0 + aoff, PY * PX * 16, PX * 16);
+                        const uint64_t ad = tc::sdesc(a0 + aoff, PY * PXH * 16, PXH * 16);
                         const uint64_t bd = tc::sdesc(b0 + boff, NOUT * 16, 128);
                         tc::mma_f16(tbase + j * NOUT, ad, bd, idesc, (tap | ss) ? 1u : 0u);
                     }
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(NTH, 1)
         tc::fence_after();
         const int q = warp & 3, m = 32 * q + lane;
         const int oy = y0 + (m >> 3);
-        for (int j = warp >> 2; j < MT; j += 2) {
+        for (int j = warp >> 2; j < MTH; j += 2) {
             const int ox = x0 + 8 * j + (m & 7);
             const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(j * NOUT);
             uint32_t r[32];
@@ -383,11 +386,11 @@ hts_status conv_tma(const hts_cnn *n, const __half *wt, int cin, int cout, const
     using L = ConvTmaLayout<NOUT>;
     const auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(tensor_map_encoder());
     if (!enc) return report(HTS_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    // 8-byte elements, two per pixel vector: each box row is one contiguous run of 2 PX elements
+    // 8-byte elements, two per pixel vector: each box row is one contiguous run of 2 PXH elements
     CUtensorMap tmap;
     const cuuint64_t dims[3] = {(cuuint64_t)W * 2, (cuuint64_t)H, (cuuint64_t)CING_H};
     const cuuint64_t strides[2] = {(cuuint64_t)W * 16, (cuuint64_t)H * W * 16};
-    const cuuint32_t box[3] = {(cuuint32_t)(2 * PX), (cuuint32_t)PY, (cuuint32_t)CING_H};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * PXH), (cuuint32_t)PY, (cuuint32_t)CING_H};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<__half *>(hin), dims, strides, box,
                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -396,8 +399,8 @@ hts_status conv_tma(const hts_cnn *n, const __half *wt, int cin, int cout, const
     const void *k = reinterpret_cast<const void *>(k_conv_tma<NOUT, EPI>);
     const hts_status st = allow_smem(k, L::total);
     if (st != HTS_OK) return st;
-    const int nstrip = ((H + SY - 1) / SY) * ((W + SX - 1) / SX);
-    const int grid = std::max(1, std::min(nstrip, nsm));
+    const int nstrip = ((H + SY - 1) / SY) * ((W + SXH - 1) / SXH);
+    const int grid = std::max(1, std::min(nstrip, 2 * nsm));
     {
         KTimer kt("k_conv_tma", s);
         k_conv_tma<NOUT, EPI><<<grid, NTH, L::total, s>>>(tmap, H, W, wt, cin, cout, hout, map, hmask, n->err);

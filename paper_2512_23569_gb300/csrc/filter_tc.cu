@@ -443,8 +443,9 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
 #pragma unroll
                 for (int j = 0; j < KM; ++j) {
                     const int o = offs[j];
+                    const bool in = o >= 0 && HTS_IN_BOUNDS(o + (p >> 3) * rwp + (p & 7) < RP, &a.st->error);
 #pragma unroll
-                    for (int c = 0; c < C; ++c) v[j][c] = o >= 0 ? __half2float(src[c * RP + o]) : 0.f;
+                    for (int c = 0; c < C; ++c) v[j][c] = in ? __half2float(src[c * RP + o]) : 0.f;
                 }
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
@@ -622,7 +623,8 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
                     int *dst = acc_v + c * RP;
 #pragma unroll
                     for (int j = 0; j < KM; ++j)
-                        if (offs[i][j] >= 0) atomicAdd(dst + offs[i][j], fix8(x[j]));
+                        if (offs[i][j] >= 0 && HTS_IN_BOUNDS(offs[i][j] < RP, &a.st->error))
+                            atomicAdd(dst + offs[i][j], fix8(x[j]));
                 }
                 tc::fence_before();
                 __syncthreads();

@@ -17,6 +17,15 @@ constexpr double FIX_SCALE = 65536.0;  // 2^16: fixed-point scale of the aggrega
 constexpr int LEARNED_PARTS = 160;  // blocks of the learned-map check
 
 // Device-resident state of one call: noise level, threshold and counters.
+// Bounds checks of the check build (compiled with -DHTS_CHECK, library libhts_check.so): a failed check
+// records error code 3 in *errp and the guarded access is skipped; in the normal build the condition is not
+// evaluated and the access always runs.
+#ifdef HTS_CHECK
+#define HTS_IN_BOUNDS(cond, errp) ((cond) ? true : (atomicExch((errp), 3), false))
+#else
+#define HTS_IN_BOUNDS(cond, errp) true
+#endif
+
 struct DevState {
     double sigma_est;
     double sigma_hat;

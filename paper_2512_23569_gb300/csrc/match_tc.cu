@@ -411,7 +411,9 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(const __grid_constant__ TcAr
             for (int e = tid; e < NR * PS; e += NT) {
                 const int j = e >> 3, u = e & 7;
                 uint4 w = make_uint4(0u, 0u, 0u, 0u);
-                if ((gy0 + (j >> 3)) <= gy1 && (gx0 + (j & 7)) <= gx1) w = Q[rec[j].pself + u * Wq];
+                if ((gy0 + (j >> 3)) <= gy1 && (gx0 + (j & 7)) <= gx1 &&
+                    HTS_IN_BOUNDS(rec[j].pself + u * Wq < nq, &a.st->error))
+                    w = Q[rec[j].pself + u * Wq];
                 *reinterpret_cast<uint4 *>(Abuf + (j >> 3) * 1024 + u * 128 + (j & 7) * 16) = w;
             }
             tc::fence_async_smem();
@@ -595,6 +597,7 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(const __grid_constant__ TcAr
                     if (k != 0xffffffffu) {
                         const int p = (int)(k & lowm);
                         const int by = p / Wq, bx = p - by * Wq;
+                        if (!HTS_IN_BOUNDS(by < Hc && bx < Wc, &a.st->error)) continue;
                         const float *pbv = Ps + by * PSW + bx;
                         float d = 0.f;
 #pragma unroll

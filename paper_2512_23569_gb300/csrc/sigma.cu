@@ -15,6 +15,7 @@
 //                FP64.  Each block adds its votes once (integer, order-free);
 // k_sigma_final: a strict majority divides sigma_est by beta (Eq. 23); then
 //                tau = tau_mult sigma sqrt(2 ln(c K ps^2)).
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "hts_internal.h"
@@ -150,123 +151,192 @@ __device__ void lambda64_partial(const float *__restrict__ img, int H, int W, co
     }
 }
 
+// The vote of one group (one warp): lambda_m of its members' patches, components read from src at
+// c * plane + (e >> 3) * rstride + (e & 7) + off[k] for member k; returns 1 for a vote, 0 otherwise (a group
+// the FP32 bound cannot settle is listed for k_vote_exact and counts 0 here).
 template <int C, int K>
-__global__ void __launch_bounds__(128) k_vote(const float *__restrict__ img, int H, int W,
-                                              const int32_t *__restrict__ idx, int nref, double gamma_rank,
-                                              int32_t *__restrict__ list, DevState *st) {
+__device__ __forceinline__ int vote_group(const float *__restrict__ src, size_t plane, int rstride,
+                                          const int (&off)[K], double gamma_rank, int r, int32_t *__restrict__ list,
+                                          DevState *st) {
     constexpr int D = C * NPIX;
     constexpr int NM = K / 2 + 1;
-    __shared__ int s_votes;
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) s_votes = 0;
-    __syncthreads();
-    const size_t HW = (size_t)H * W;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    int my_votes = 0;
-    for (int r = gw; r < nref; r += nw) {
-        int off[K];
-        {
-            const int mine = (lane < K) ? idx[(size_t)r * K + lane] : 0;
+    float lam[NM];
 #pragma unroll
-            for (int k = 0; k < K; ++k) off[k] = __shfl_sync(FULL, mine, k);
-        }
-        float lam[NM];
-#pragma unroll
-        for (int m = 0; m < NM; ++m) lam[m] = 0.f;
-        float e0sq = 0.f, esq = 0.f;
+    for (int m = 0; m < NM; ++m) lam[m] = 0.f;
+    float e0sq = 0.f, esq = 0.f;
 #pragma unroll 1
-        for (int d = lane; d < D; d += 32) {
-            const int c = d / NPIX, e = d - c * NPIX;
-            const size_t base = (size_t)c * HW + (size_t)(e >> 3) * W + (e & 7);
-            float p[K];
+    for (int d = lane; d < D; d += 32) {
+        const int c = d / NPIX, e = d - c * NPIX;
+        const size_t base = (size_t)c * plane + (size_t)(e >> 3) * rstride + (e & 7);
+        float p[K];
 #pragma unroll
-            for (int k = 0; k < K; ++k) p[k] = __ldg(img + base + off[k]);
-            float x0 = 0.f, a0 = 0.f, a1 = 0.f;
+        for (int k = 0; k < K; ++k) p[k] = src[base + off[k]];
+        float x0 = 0.f, a0 = 0.f, a1 = 0.f;
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                x0 += p[k];
-                a0 += fabsf(p[k]);
-            }
-            lam[0] = fmaf(x0, x0, lam[0]);
-            e0sq = fmaf(a0, a0, e0sq);
-            float q[K];
+        for (int k = 0; k < K; ++k) {
+            x0 += p[k];
+            a0 += fabsf(p[k]);
+        }
+        lam[0] = fmaf(x0, x0, lam[0]);
+        e0sq = fmaf(a0, a0, e0sq);
+        float q[K];
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                q[k] = p[k] - p[0];
-                a1 += fabsf(q[k]);
-            }
-            esq = fmaf(a1, a1, esq);
-            // k and K - k see conjugate twiddles: q_k w^{mk} + q_{K-k} w^{-mk} = (q_k + q_{K-k}) cos
-            // + i (q_k - q_{K-k}) (-sin), and w^{m K/2} = (-1)^m.  Per component this evaluation errs by
-            // at most sqrt(2) (K/2 + 5/2) u sum_k |q_k| (the subtraction, the pair sum, the twiddle, K/2
-            // accumulations), inside the bound below (sqrt(2) (K + 3) u sum_k |q_k|).
-            float sp[K / 2 + 1], dm[K / 2 + 1];
+        for (int k = 0; k < K; ++k) {
+            q[k] = p[k] - p[0];
+            a1 += fabsf(q[k]);
+        }
+        esq = fmaf(a1, a1, esq);
+        // k and K - k see conjugate twiddles: q_k w^{mk} + q_{K-k} w^{-mk} = (q_k + q_{K-k}) cos
+        // + i (q_k - q_{K-k}) (-sin), and w^{m K/2} = (-1)^m.  Per component this evaluation errs by
+        // at most sqrt(2) (K/2 + 5/2) u sum_k |q_k| (the subtraction, the pair sum, the twiddle, K/2
+        // accumulations), inside the bound below (sqrt(2) (K + 3) u sum_k |q_k|).
+        float sp[K / 2 + 1], dm[K / 2 + 1];
+#pragma unroll
+        for (int k = 1; k < K / 2; ++k) {
+            sp[k] = q[k] + q[K - k];
+            dm[k] = q[k] - q[K - k];
+        }
+#pragma unroll
+        for (int m = 1; m < NM; ++m) {
+            float xr = (m & 1) ? -q[K / 2] : q[K / 2], xi = 0.f;
 #pragma unroll
             for (int k = 1; k < K / 2; ++k) {
-                sp[k] = q[k] + q[K - k];
-                dm[k] = q[k] - q[K - k];
+                const int j = ((m * k) % K) * (32 / K);
+                // quarter turns: fmaf with an exact 0 or +-1 is the plain sum (same rounding)
+                if (j == 0) xr += sp[k];
+                else if (j == 8) xi -= dm[k];
+                else if (j == 16) xr -= sp[k];
+                else if (j == 24) xi += dm[k];
+                else {
+                    xr = fmaf(sp[k], c_twc[j], xr);
+                    xi = fmaf(dm[k], c_tws[j], xi);
+                }
             }
+            lam[m] = fmaf(xr, xr, fmaf(xi, xi, lam[m]));
+        }
+    }
 #pragma unroll
-            for (int m = 1; m < NM; ++m) {
-                float xr = (m & 1) ? -q[K / 2] : q[K / 2], xi = 0.f;
+    for (int o = 16; o; o >>= 1) {
 #pragma unroll
-                for (int k = 1; k < K / 2; ++k) {
-                    const int j = ((m * k) % K) * (32 / K);
-                    // quarter turns: fmaf with an exact 0 or +-1 is the plain sum (same rounding)
-                    if (j == 0) xr += sp[k];
-                    else if (j == 8) xi -= dm[k];
-                    else if (j == 16) xr -= sp[k];
-                    else if (j == 24) xi += dm[k];
-                    else {
-                        xr = fmaf(sp[k], c_twc[j], xr);
-                        xi = fmaf(dm[k], c_tws[j], xi);
+        for (int m = 0; m < NM; ++m) lam[m] += __shfl_xor_sync(FULL, lam[m], o);
+        e0sq += __shfl_xor_sync(FULL, e0sq, o);
+        esq += __shfl_xor_sync(FULL, esq, o);
+    }
+    // rigorous bound on |lambda32 - lambda|
+    const float dx0 = 1.4143f * (float)(K + 3) * U32 * sqrtf(e0sq) * 1.01f;
+    const float dx = 1.4143f * (float)(K + 3) * U32 * sqrtf(esq) * 1.01f;
+    float bnd[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        const float dd = (m == 0) ? dx0 : dx;
+        const float sl = sqrtf(fmaxf(lam[m], 0.f) * 1.02f);
+        bnd[m] = (2.f * sl * dd + dd * dd) * 1.01f + 16.f * U32 * lam[m] + 1e-30f;
+    }
+    const float lh = lam[K / 2], bh = bnd[K / 2];
+    int sure = 0, unc = 0;
+#pragma unroll
+    for (int m = 0; m < K / 2; ++m) {
+        const int mult = (m == 0) ? 1 : 2;
+        if (lam[m] + bnd[m] < lh - bh) sure += mult;
+        else if (lam[m] - bnd[m] >= lh + bh) {
+        } else unc += mult;
+    }
+    if ((double)(1 + sure + unc) <= gamma_rank) return 1;
+    if ((double)(1 + sure) > gamma_rank) return 0;
+    if (lane == 0) {  // decided in FP64 by k_vote_exact
+        const int pos = atomicAdd(&st->vote_uncertain, 1);
+        list[pos] = r;
+    }
+    return 0;
+}
+
+// Row stride (floats) of the vote's staged region: the width rounded up to 8 mod 32, so that a warp's 32
+// components (4 rows x 8 pixels of a patch) fall in 32 distinct banks.
+__host__ __device__ constexpr int vote_stride(int w) { return w + ((8 - w) & 31); }
+constexpr int VT = 8;        // reference tile: VT x VT references
+constexpr int VNT = 256;     // threads per block (8 warps)
+
+// The rank vote over tiles of VT x VT references: a block stages the tile's search region (every channel,
+// FP32, exactly the image's values) in shared memory and its warps take the tile's groups in turn; the
+// arithmetic of a group is vote_group's, on the staged values (a group with a member outside the region,
+// which no matcher produces, reads the image instead).  Each block adds its votes once (integer, order-free).
+template <int C, int K>
+__global__ void __launch_bounds__(VNT) k_vote(const float *__restrict__ img, int H, int W,
+                                              const int32_t *__restrict__ idx, int nx, int ny, int step, int R,
+                                              double gamma_rank, int32_t *__restrict__ list, DevState *st) {
+    extern __shared__ float vreg[];
+    __shared__ int s_votes;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_votes = 0;
+    const size_t HW = (size_t)H * W;
+    const int ntx = (nx + VT - 1) / VT, ntiles = ntx * ((ny + VT - 1) / VT);
+    int my_votes = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int gy0 = (tile / ntx) * VT, gx0 = (tile % ntx) * VT;
+        const int gy1 = min(ny, gy0 + VT) - 1, gx1 = min(nx, gx0 + VT) - 1;
+        const int ry0 = max(0, grid_pos(gy0, H, step) - R), ry1 = min(H - 1, grid_pos(gy1, H, step) + R + PS - 1);
+        const int rx0 = max(0, grid_pos(gx0, W, step) - R), rx1 = min(W - 1, grid_pos(gx1, W, step) + R + PS - 1);
+        const int rh = ry1 - ry0 + 1, rw = rx1 - rx0 + 1, rs = vote_stride(rw);
+        const size_t plane = (size_t)rh * rs;
+        __syncthreads();  // the previous tile's groups are done with the region
+        {
+            // element e = tid + i VNT: column x, region row `row` = channel c, row y; advanced by VNT per step
+            const int dq = VNT / rw, dr = VNT - dq * rw;
+            int row = tid / rw, x = tid - row * rw;
+            int c = row / rh, y = row - c * rh;
+            for (int e0 = 0; e0 < C * rh * rw; e0 += 8 * VNT) {
+                float v[8];
+                int dst[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const bool in = c < C;
+                    dst[i] = in ? (c * rh + y) * rs + x : -1;
+                    v[i] = in ? __ldg(img + c * HW + (size_t)(ry0 + y) * W + rx0 + x) : 0.f;
+                    x += dr;
+                    row += dq;
+                    y += dq;
+                    if (x >= rw) {
+                        x -= rw;
+                        ++row;
+                        ++y;
+                    }
+                    while (y >= rh) {
+                        y -= rh;
+                        ++c;
                     }
                 }
-                lam[m] = fmaf(xr, xr, fmaf(xi, xi, lam[m]));
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (dst[i] >= 0) vreg[dst[i]] = v[i];
             }
         }
+        __syncthreads();
+        const int tw = gx1 - gx0 + 1, ng = (gy1 - gy0 + 1) * tw;
+        for (int t = warp; t < ng; t += VNT / 32) {
+            const int gy = gy0 + t / tw, gx = gx0 + t % tw, r = gy * nx + gx;
+            const int pos = (lane < K) ? idx[(size_t)r * K + lane] : 0;
+            const int py = pos / W, px = pos - py * W;
+            const bool inside = lane >= K || (py >= ry0 && py + PS - 1 <= ry1 && px >= rx0 && px + PS - 1 <= rx1);
+            int off[K];
+            if (__all_sync(FULL, inside)) {
+                const int mine = (py - ry0) * rs + (px - rx0);
+                if (!HTS_IN_BOUNDS(lane >= K || mine + (C - 1) * (int)plane + (PS - 1) * rs + PS - 1 < C * (int)plane,
+                                   &st->error))
+                    continue;  // (the check build: the staged region would be overrun)
 #pragma unroll
-        for (int o = 16; o; o >>= 1) {
+                for (int k = 0; k < K; ++k) off[k] = __shfl_sync(FULL, mine, k);
+                my_votes += vote_group<C, K>(vreg, plane, rs, off, gamma_rank, r, list, st);
+            } else {
 #pragma unroll
-            for (int m = 0; m < NM; ++m) lam[m] += __shfl_xor_sync(FULL, lam[m], o);
-            e0sq += __shfl_xor_sync(FULL, e0sq, o);
-            esq += __shfl_xor_sync(FULL, esq, o);
-        }
-        // rigorous bound on |lambda32 - lambda|
-        const float dx0 = 1.4143f * (float)(K + 3) * U32 * sqrtf(e0sq) * 1.01f;
-        const float dx = 1.4143f * (float)(K + 3) * U32 * sqrtf(esq) * 1.01f;
-        float bnd[NM];
-#pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            const float dd = (m == 0) ? dx0 : dx;
-            const float sl = sqrtf(fmaxf(lam[m], 0.f) * 1.02f);
-            bnd[m] = (2.f * sl * dd + dd * dd) * 1.01f + 16.f * U32 * lam[m] + 1e-30f;
-        }
-        const float lh = lam[K / 2], bh = bnd[K / 2];
-        int sure = 0, unc = 0;
-#pragma unroll
-        for (int m = 0; m < K / 2; ++m) {
-            const int mult = (m == 0) ? 1 : 2;
-            if (lam[m] + bnd[m] < lh - bh) sure += mult;
-            else if (lam[m] - bnd[m] >= lh + bh) {
-            } else unc += mult;
-        }
-        int vote;
-        if ((double)(1 + sure + unc) <= gamma_rank) vote = 1;
-        else if ((double)(1 + sure) > gamma_rank) vote = 0;
-        else {
-            vote = 0;  // decided in FP64 by k_vote_exact
-            if (lane == 0) {
-                const int pos = atomicAdd(&st->vote_uncertain, 1);
-                list[pos] = r;
+                for (int k = 0; k < K; ++k) off[k] = __shfl_sync(FULL, pos, k);
+                my_votes += vote_group<C, K>(img, HW, W, off, gamma_rank, r, list, st);
             }
         }
-        my_votes += vote;
     }
     if (lane == 0) atomicAdd(&s_votes, my_votes);
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(&st->votes, s_votes);
+    if (tid == 0) atomicAdd(&st->votes, s_votes);
 }
 
 // The groups k_vote could not settle, decided in FP64: a cluster of VX
@@ -348,11 +418,20 @@ __global__ void k_set_sigma(DevState *st, double sigma, int nref, double tau_sca
 template <int C, int K>
 hts_status launch_vote(const float *img, const Geom &g, const int32_t *idx, double gamma_rank, int32_t *list,
                        DevState *st, cudaStream_t s) {
-    int blocks = (g.nref + 3) / 4;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    // the largest tile region: VT x VT references, their windows and patches, cut to the image
+    const int rh = std::min(g.H, (VT - 1) * g.step + 2 * g.R + PS), rw = std::min(g.W, (VT - 1) * g.step + 2 * g.R + PS);
+    const size_t smem = (size_t)C * rh * vote_stride(rw) * sizeof(float);
+    const void *fn = reinterpret_cast<const void *>(k_vote<C, K>);
+    if (hts_status e = allow_smem(fn, smem); e != HTS_OK) return e;
+    int dev = 0, nsm = 152, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, VNT, smem);
+    const int ntiles = ((g.nx + VT - 1) / VT) * ((g.ny + VT - 1) / VT);
+    const int blocks = std::max(1, std::min(ntiles, nsm * std::max(per_sm, 1)));
     {
         KTimer kt("k_vote", s);
-        k_vote<C, K><<<blocks, 128, 0, s>>>(img, g.H, g.W, idx, g.nref, gamma_rank, list, st);
+        k_vote<C, K><<<blocks, VNT, smem, s>>>(img, g.H, g.W, idx, g.nx, g.ny, g.step, g.R, gamma_rank, list, st);
     }
     if (hts_status e = check_launch("k_vote"); e != HTS_OK) return e;
     {

@@ -14,7 +14,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libhts.so")
+# HTS_LIBRARY=check selects the check build (libhts_check.so: device-side bounds checks)
+LIB_PATH = os.path.join(_HERE, "libhts_check.so" if os.environ.get("HTS_LIBRARY") == "check" else "libhts.so")
 _LOCK = threading.Lock()
 _LIB = None
 
