@@ -14,7 +14,7 @@ the plain FP32 path ("plain vs chosen").  The line also carries short runs of th
 (colour 512x512x3, precision 1024x1024x3, the 64-image batch) under "other_workloads".
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload learned4k|colour512|precision1024|batch64|cnn] [--no-extras]
+                       [--workload learned4k|colour512|precision1024|precision4k|batch64|cnn] [--no-extras]
 Under torchrun every rank denoises its own seeded image (weak scaling, no collective in the data
 path); rank 0 prints one JSON line.
 """
@@ -396,6 +396,43 @@ def _tc_roofline(dom, ms_per_launch, H, W, C, K, win, step, green):
                 "algorithmic": "issued BF16 MMA flops (%.2f GFLOP per launch)" % (flops / 1e9),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)"}
     return None
+
+
+def run_precision4k(args):
+    """The default line's image (colour 3840x2160x3, Poisson-Gaussian a = 0.01, read noise ramping 2 to 28)
+    through the precision form with the eigenvalue noise estimate (no network, no training): the full-size
+    kernels of the default step on their own, for profiling (it holds well under a GB of device memory and
+    runs few launches before the timed ones)."""
+    import torch
+
+    from paper_2512_23569_gb300 import build, hts, synth
+
+    build.build()
+    hts.load()
+    w = WORKLOAD
+    H, W, C = w["H"], w["W"], w["C"]
+    clean, noisy, _ = learned_image()
+    x = torch.from_numpy(noisy).cuda()
+    p = hts.params(win=w["win"], precision=1, K=w["K"], step=w["step"])
+    out = torch.empty_like(x)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    r = _timed(lambda: hts.denoise(x, sigma=None, p=p, out=out), args, torch.cuda.current_stream(), flush, 0, 1,
+               label="timed_precision4k")
+    green = hts.match(x, p)[1].cpu().numpy()
+    rooflines = _kernel_rooflines(r["kernels"], H, W, C, w["K"], w["win"], w["step"], green)
+    dom = _dominant(r["kernels"])
+    roof = dict(rooflines.get(dom) or {"kernel": dom, "bound": None})
+    roof["traffic"] = _committed_traffic(dom, "precision4k")
+    return {
+        "metric": "Mpixel/s denoised on 1 GB300, precision form, eigenvalue noise estimate",
+        "value": H * W / (r["ms"] / 1e3) / 1e6, "unit": "Mpixel/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 matching / f16 filter (f32 accumulate)", "data": "synthetic",
+        "config": dict(w, workload="colour 3840x2160x3 of the default line, precision form, sigma estimated"),
+        "roofline": roof, "psnr_db": synth.psnr(out.cpu().numpy(), clean), "clocks": r["clocks"],
+        "gpu_launches": r["launches"], "kernels": r["kernels"], "kernel_rooflines": rooflines,
+        "kernels_note": AUX_NOTE,
+    }
 
 
 def run_precision(args):
@@ -1142,10 +1179,12 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="leave the other workloads out of the default line")
     ap.add_argument("--train-crops", type=int, default=WORKLOAD["train_crops"],
                     help="training crops of the learned workload's network (the workload's configuration: 4096)")
-    ap.add_argument("--workload", choices=["learned4k", "colour512", "batch64", "precision1024", "cnn"],
+    ap.add_argument("--workload", choices=["learned4k", "colour512", "batch64", "precision1024", "precision4k",
+                                           "cnn"],
                     default="learned4k",
                     help="learned4k (default): the learned form on 3840x2160x3; colour512: the colour 512x512x3 "
                          "workload; batch64: the 64-image batched form; precision1024: the BF16 precision form; "
+                         "precision4k: the default image through the precision form without the network (profiling); "
                          "cnn: the noise-level network's forward alone (each prints one JSON line of its own)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -1170,6 +1209,8 @@ def main():
             line = run_batch(args)
         elif args.workload == "precision1024":
             line = run_precision(args)
+        elif args.workload == "precision4k":
+            line = run_precision4k(args)
         else:
             line = run_cnn(args)
         if line is not None and rank == 0:

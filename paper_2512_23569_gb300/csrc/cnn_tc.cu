@@ -215,8 +215,8 @@ __global__ void __launch_bounds__(NTH, 1)
 // its strips (16 x 32 output pixels: four 16 x 8 tiles) in turn with two staging buffers; while strip i's
 // MMAs and epilogue run, the tensor-memory accumulators being read and the outputs written, the TMA copy of
 // strip i + 1's input (the same 4 x 18 x 34 box of 16-byte pixel vectors, zero outside the image) lands in
-// the other buffer.  Two blocks per SM (two 39 KB buffers each, 128 tensor-memory columns): the second
-// block's warps hide the first's latencies.  Waits bounded as in k_conv_tc; a block that gives up waits
+// the other buffer.  Two blocks per SM (two 39 KB buffers each, 128 tensor-memory columns, at most 128
+// registers a thread): the second block's warps hide the first's latencies.  Waits bounded as in k_conv_tc; a block that gives up waits
 // (bounded) for its copy in flight and its MMAs before it releases its tensor memory.
 constexpr int CING_H = 4;
 constexpr int MTH = 4;                 // tiles per strip of the hidden layers
@@ -236,7 +236,7 @@ struct ConvTmaLayout {
 };
 
 template <int NOUT, int EPI>
-__global__ void __launch_bounds__(NTH, 1)
+__global__ void __launch_bounds__(NTH, 2)
     k_conv_tma(const __grid_constant__ CUtensorMap tmap, int H, int W, const __half *__restrict__ wt, int cin, int cout,
                __half *__restrict__ hout, float *__restrict__ map, const __half *__restrict__ hmask, int *err) {
     using L = ConvTmaLayout<NOUT>;

@@ -315,6 +315,89 @@ __device__ __forceinline__ int decide(float mag, float tau, float band) {
 
 // FP64 value of Haar coefficient (h, slice j, element e = i*8+jj) of group
 // r, evaluated from the input pixels and the FP64 basis by the whole warp.
+// A Haar detail row h >= 1 sums to zero over its members (Eq. 8), so its coefficient is unchanged when one
+// member's patch (kref, the first of the row's support) is subtracted from every member: the FP32 value
+// computed from those differences errs only in proportion to them, which at low noise are far smaller
+// than the patches.  One (member k, patch row arow) unit: its FP32 contribution (sr, si) to the
+// coefficient (slice j, position (i, jj)) and the sum sa of the absolute values of every product in it,
+// sum_b |h_k| |U[arow][i]| |d[arow][b]| |V[b][jj]|, which bounds the evaluation error (diff_bound).
+template <int C>
+__device__ __forceinline__ void diff_unit32(const FilterArgs &a, const int32_t *grp, int K, int h, int j, int i,
+                                            int jj, int kref, int k, int arow, float &sr, float &si, float &sa) {
+    const size_t HW = (size_t)a.H * a.W;
+    const float *U = a.b32 + (size_t)((j * 2 + 0) * 64) * 2;
+    const float *V = a.b32 + (size_t)((j * 2 + 1) * 64) * 2;
+    const int pos = grp[k], pref = grp[kref];
+    const int y = pos / a.W, x = pos - y * a.W, yr = pref / a.W, xr = pref - yr * a.W;
+    float tr = 0.f, ti = 0.f, ta = 0.f;
+    for (int b = 0; b < 8; ++b) {
+        const size_t o = (size_t)(y + arow) * a.W + x + b, orf = (size_t)(yr + arow) * a.W + xr + b;
+        float pr, pi = 0.f, pa;
+        if (C == 1) {
+            pr = __ldg(a.img + o) - __ldg(a.img + orf);
+            pa = fabsf(pr);
+        } else {
+            const float dR = __ldg(a.img + o) - __ldg(a.img + orf);
+            const float dG = __ldg(a.img + HW + o) - __ldg(a.img + HW + orf);
+            const float dB = __ldg(a.img + 2 * HW + o) - __ldg(a.img + 2 * HW + orf);
+            if (j == 0) {
+                pr = ((dR + dG) + dB) * K3F;
+                pa = (fabsf(dR) + fabsf(dG) + fabsf(dB)) * K3F;
+            } else {
+                pr = (dR - 0.5f * (dG + dB)) * K3F;
+                pi = (dB - dG) * (S3H * K3F);
+                pa = (fabsf(dR) + 0.5f * (fabsf(dG) + fabsf(dB))) * K3F + (fabsf(dB) + fabsf(dG)) * (S3H * K3F);
+            }
+        }
+        const float vr = V[(b * 8 + jj) * 2], vi = V[(b * 8 + jj) * 2 + 1];
+        tr = fmaf(pr, vr, fmaf(-pi, vi, tr));
+        ti = fmaf(pr, vi, fmaf(pi, vr, ti));
+        ta = fmaf(pa, fabsf(vr) + fabsf(vi), ta);
+    }
+    const float ur = U[(arow * 8 + i) * 2], ui = U[(arow * 8 + i) * 2 + 1];
+    const float hv = (float)haar_entry(K, h, k);
+    sr = hv * fmaf(ur, tr, ui * ti);  // conj(u) * t
+    si = hv * fmaf(ur, ti, -ui * tr);
+    sa = fabsf(hv) * (fabsf(ur) + fabsf(ui)) * ta;
+}
+
+// The keep / drop decision of a coefficient from its FP32 difference evaluation (re, im, the absolute sum
+// A of its products over at most 1024 of them): every product carries at most a few FP32 roundings of the
+// differences, the basis and its own, and the summation (a thread's run of units, then a 7-level tree)
+// adds at most about 20 u relative to A; 128 u A bounds the total with room to spare, and 4 u |value| the
+// modulus.  1 keep, 0 drop, -1 undecided (the FP64 evaluation decides).
+__device__ __forceinline__ int diff_decide(int j, float re, float im, float A, double tau64) {
+    const float mag = (j == 0) ? fabsf(re) : sqrtf(re * re + im * im);
+    const double bnd = 128.0 * (double)U32 * (double)A * 1.01 + 4.0 * (double)U32 * (double)mag + 1e-30;
+    if ((double)mag - bnd >= tau64) return 1;
+    if ((double)mag + bnd < tau64) return 0;
+    return -1;
+}
+
+// The decision of coefficient (Haar row h >= 1, slice j, position e) of group grp by one warp from the FP32
+// differences (diff_unit32 over the row's support, units spread over the lanes, a shuffle tree); -1 when the
+// bound cannot decide it.
+template <int C>
+__device__ int diff_decide_warp(const FilterArgs &a, const int32_t *grp, int K, int h, int j, int e, int lane,
+                                double tau64) {
+    const int l = 31 - __clz(h), L = K >> l, k0 = (h - (1 << l)) * L;
+    float fr = 0.f, fi = 0.f, fa = 0.f;
+    for (int u = lane; u < L * 8; u += 32) {
+        float ur, ui, ua;
+        diff_unit32<C>(a, grp, K, h, j, e >> 3, e & 7, k0, k0 + (u >> 3), u & 7, ur, ui, ua);
+        fr += ur;
+        fi += ui;
+        fa += ua;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        fr += __shfl_xor_sync(FULL, fr, o);
+        fi += __shfl_xor_sync(FULL, fi, o);
+        fa += __shfl_xor_sync(FULL, fa, o);
+    }
+    return diff_decide(j, fr, fi, fa, tau64);
+}
+
 template <int C>
 __device__ void exact_coef(const FilterArgs &a, const int32_t *grp, int K, int h, int j, int e, int lane,
                            double &re, double &im) {
@@ -529,17 +612,22 @@ __global__ void __launch_bounds__(64) k_filter_exact(FilterArgs a) {
                 const int it = t / K, q = t - it * K;
                 const int j = it < 64 ? 0 : 1;
                 const int e = it < 64 ? it : it - 64;
-                double re, im;
-                exact_coef<C>(a, grp, K, q, j, e, lane, re, im);
-                const double mag = (j == 0) ? fabs(re) : sqrt(re * re + im * im);
+                // Haar detail rows: first the certified FP32 evaluation on the members' differences
+                int keep = (q > 0) ? diff_decide_warp<C>(a, grp, K, q, j, e, lane, tau64) : -1;
+                if (keep < 0) {
+                    double re, im;
+                    exact_coef<C>(a, grp, K, q, j, e, lane, re, im);
+                    const double mag = (j == 0) ? fabs(re) : sqrt(re * re + im * im);
+                    keep = (mag >= tau64) ? 1 : 0;
+                    if (lane == 0) atomicAdd(&a.st->filter_exact, 1);
+                }
                 if (lane == 0) {
                     const int bit = it * K + q;
                     mask[bit >> 5] |= (1u << (bit & 31));
-                    if (!(mag >= tau64)) {
+                    if (!keep) {
                         coef[it * ROW + q] = 0.f;
                         if (it >= 64) coef[(it + 64) * ROW + q] = 0.f;
                     }
-                    atomicAdd(&a.st->filter_exact, 1);
                 }
                 __syncwarp();
             }
@@ -1279,6 +1367,7 @@ __device__ __forceinline__ void exact_unit(const FilterArgs &a, const int32_t *g
 template <int C, int K>
 __global__ void __launch_bounds__(128) k_filter_fix(FilterArgs a) {
     __shared__ double red[2][4];
+    __shared__ float red32[3][4];
     __shared__ int dec;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = min(*(volatile int *)&a.st->xcount, a.xcap);
@@ -1296,31 +1385,66 @@ __global__ void __launch_bounds__(128) k_filter_fix(FilterArgs a) {
             k0 = ii * L;
             k1 = k0 + L;
         }
-        double sr = 0.0, si = 0.0;
-        for (int u = tid; u < (k1 - k0) * 8; u += 128) {
-            double ur, ui;
-            exact_unit<C>(a, grp, K, h, j, i, jj, k0 + (u >> 3), u & 7, ur, ui);
-            sr += ur;
-            si += ui;
-        }
+        // Haar detail rows: first the certified FP32 evaluation on the members' differences
+        if (h > 0) {
+            float fr = 0.f, fi = 0.f, fa = 0.f;
+            for (int u = tid; u < (k1 - k0) * 8; u += 128) {
+                float ur, ui, ua;
+                diff_unit32<C>(a, grp, K, h, j, i, jj, k0, k0 + (u >> 3), u & 7, ur, ui, ua);
+                fr += ur;
+                fi += ui;
+                fa += ua;
+            }
 #pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            sr += __shfl_xor_sync(FULL, sr, o);
-            si += __shfl_xor_sync(FULL, si, o);
-        }
-        if (lane == 0) {
-            red[0][warp] = sr;
-            red[1][warp] = si;
+            for (int o = 16; o; o >>= 1) {
+                fr += __shfl_xor_sync(FULL, fr, o);
+                fi += __shfl_xor_sync(FULL, fi, o);
+                fa += __shfl_xor_sync(FULL, fa, o);
+            }
+            if (lane == 0) {
+                red32[0][warp] = fr;
+                red32[1][warp] = fi;
+                red32[2][warp] = fa;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                const float re = (red32[0][0] + red32[0][1]) + (red32[0][2] + red32[0][3]);
+                const float im = (red32[1][0] + red32[1][1]) + (red32[1][2] + red32[1][3]);
+                const float A = (red32[2][0] + red32[2][1]) + (red32[2][2] + red32[2][3]);
+                dec = diff_decide(j, re, im, A, group_tau64(a, r));
+            }
+            __syncthreads();
+        } else if (tid == 0) {
+            dec = -1;
         }
         __syncthreads();
-        if (tid == 0) {
-            const double re = (red[0][0] + red[0][1]) + (red[0][2] + red[0][3]);
-            const double im = (red[1][0] + red[1][1]) + (red[1][2] + red[1][3]);
-            const int keep64 = (((j == 0) ? fabs(re) : sqrt(re * re + im * im)) >= group_tau64(a, r)) ? 1 : 0;
-            atomicAdd(&a.st->filter_exact, 1);
-            if (keep64 != keep32) atomicAdd(&a.st->filter_fixed, 1);
-            dec = keep64;
+        if (dec < 0) {  // FP64 from the pixels and the FP64 basis
+            double sr = 0.0, si = 0.0;
+            for (int u = tid; u < (k1 - k0) * 8; u += 128) {
+                double ur, ui;
+                exact_unit<C>(a, grp, K, h, j, i, jj, k0 + (u >> 3), u & 7, ur, ui);
+                sr += ur;
+                si += ui;
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                sr += __shfl_xor_sync(FULL, sr, o);
+                si += __shfl_xor_sync(FULL, si, o);
+            }
+            if (lane == 0) {
+                red[0][warp] = sr;
+                red[1][warp] = si;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                const double re = (red[0][0] + red[0][1]) + (red[0][2] + red[0][3]);
+                const double im = (red[1][0] + red[1][1]) + (red[1][2] + red[1][3]);
+                dec = (((j == 0) ? fabs(re) : sqrt(re * re + im * im)) >= group_tau64(a, r)) ? 1 : 0;
+                atomicAdd(&a.st->filter_exact, 1);
+            }
+            __syncthreads();
         }
+        if (tid == 0 && dec != keep32) atomicAdd(&a.st->filter_fixed, 1);
         __syncthreads();
         const int keep64 = dec;
         __syncthreads();  // dec and red are reused by the next entry
@@ -1553,15 +1677,20 @@ hts_status launch_ck(const FilterArgs &a, const Geom &g, float *out, cudaStream_
     hts_status st = check_launch("k_filter");
     if (st != HTS_OK) return st;
     if (a.exact) {
+        // the FP64 passes' work lists live on the device: as many blocks as fit on the SMs, each taking
+        // entries in turn (their integer additions do not depend on the order)
+        int per_sm_x = 1, per_sm_f = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_x, k_filter_exact<C, K>, 64, sm_exact);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_filter_fix<C, K>, 128, 0);
         {
             KTimer kt("k_filter_exact", s);
-            k_filter_exact<C, K><<<nsm, 64, sm_exact, s>>>(a);
+            k_filter_exact<C, K><<<nsm * std::max(per_sm_x, 1), 64, sm_exact, s>>>(a);
         }
         st = check_launch("k_filter_exact");
         if (st != HTS_OK) return st;
         {
             KTimer kt("k_filter_fix", s);
-            k_filter_fix<C, K><<<nsm, 128, 0, s>>>(a);
+            k_filter_fix<C, K><<<nsm * std::max(per_sm_f, 1), 128, 0, s>>>(a);
         }
         st = check_launch("k_filter_fix");
         if (st != HTS_OK) return st;

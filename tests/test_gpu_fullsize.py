@@ -135,6 +135,17 @@ def test_precision_colour1024_full_size(oracle, hts):
     print("precision 1024 end-to-end: max %.4g p99.9 %.4g mean %.4g dPSNR %.3g dB, sigma %.6g vs %.6g"
           % (mx, p999, mean, dp, st["sigma"], info["sigma"]))
     assert abs(dp) <= 0.05 and p999 <= E2E_P999, (dp, mx, p999, mean)
+    # the plain form on the same low-noise image (sigma-hat about 0.86: most coefficients lie near the
+    # threshold, the certified FP32 difference evaluation and the FP64 passes decide them): the oracle's
+    # groups bit for bit, its noise level, pixels within 1e-3
+    p0 = hts.params(K=16, win=31)
+    out0 = hts.denoise(x, sigma=None, p=p0).cpu().numpy()
+    st0 = hts.last_stats()
+    np.testing.assert_array_equal(hts.match(x, p0)[0].cpu().numpy(), want_idx)
+    assert abs(st0["sigma"] / info["sigma"] - 1) < 1e-9, (st0["sigma"], info["sigma"])
+    mx, p999, mean = _errors(out0, want)
+    print("plain 1024 low noise: max %.4g p99.9 %.4g mean %.4g" % (mx, p999, mean))
+    assert mx <= 1e-3, (mx, p999, mean)
 
 
 def test_learned_map_precision_filter_per_pixel(oracle, hts):
