@@ -532,15 +532,6 @@ class Fcn:
     def handle(self):
         return self._h
 
-    @property
-    def train_fp16(self) -> bool:
-        """True: training steps run on the tensor cores (FP16 activations and gradients); False: FP32 kernels."""
-        return bool(load().hts_cnn_train_fp16(self._h))
-
-    @train_fp16.setter
-    def train_fp16(self, on: bool) -> None:
-        _check(load().hts_cnn_set_train_fp16(self._h, 1 if on else 0))
-
     def get_params(self) -> np.ndarray:
         a = np.empty(self.nparams, dtype=np.float32)
         _check(load().hts_fcn_get_params(self._h, ctypes.c_void_p(a.ctypes.data)))
