@@ -151,6 +151,60 @@ __device__ void lambda64_partial(const float *__restrict__ img, int H, int W, co
     }
 }
 
+// Half spectrum X_m, m = 0..N/2, of N real values x (N a power of two, 2..32), into re[m OS], im[m OS]:
+// one radix-2 split per level (a_k = x_k + x_{k+N/2} carries the even outputs, d_k = x_k - x_{k+N/2} the
+// odd ones), the odd outputs X_{2j+1} = sum_k d_k w^{(2j+1) k} evaluated directly, pairing d_k with
+// d_{N/2-k} (their twiddles are minus each other's conjugates):
+//   X_{2j+1} = d_0 + sum_{0<k<N/4} [(d_k - d_{N/2-k}) cos t - i (d_k + d_{N/2-k}) sin t] + (-i)^{2j+1} d_{N/4},
+// t = 2 pi (2j+1) k / N.  Every input reaches a real or imaginary output part along one path, whose
+// constants are at most 1 in modulus: for an odd output split off after L levels, L sums, the
+// difference d, the pair, the twiddle's own rounding and at most N / 2^(L+2) - 1 steps of the chain,
+// i.e. at most N/4 + 2 roundings (N >= 4); for X_0, log2 N.  So |Re, Im error| <= gamma_(N/4 + 2)
+// sum_k |x_k|.
+template <int N, int OS, int NO>
+__device__ __forceinline__ void rdft_half(const float *x, float (&re)[NO], float (&im)[NO]) {
+    if constexpr (N == 2) {
+        re[0] = x[0] + x[1];
+        im[0] = 0.f;
+        re[OS] = x[0] - x[1];
+        im[OS] = 0.f;
+    } else {
+        constexpr int n = N / 2;
+        float a[n], d[n];
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            a[k] = x[k] + x[k + n];
+            d[k] = x[k] - x[k + n];
+        }
+        rdft_half<n, 2 * OS, NO>(a, re, im);
+        float dd[n / 2 > 0 ? n / 2 : 1], ss[n / 2 > 0 ? n / 2 : 1];
+#pragma unroll
+        for (int k = 1; k < n / 2; ++k) {
+            dd[k] = d[k] - d[n - k];
+            ss[k] = d[k] + d[n - k];
+        }
+#pragma unroll
+        for (int j = 0; j < n / 2; ++j) {
+            float r = d[0], i = (j & 1) ? d[n / 2] : -d[n / 2];
+#pragma unroll
+            for (int k = 1; k < n / 2; ++k) {
+                const int t = ((2 * j + 1) * k * (32 / N)) & 31;
+                // quarter turns: the twiddle parts are exactly 0 or +-1, the same sums without the products
+                if (t == 0) r += dd[k];
+                else if (t == 8) i -= ss[k];
+                else if (t == 16) r -= dd[k];
+                else if (t == 24) i += ss[k];
+                else {
+                    r = fmaf(dd[k], c_twc[t], r);
+                    i = fmaf(ss[k], c_tws[t], i);
+                }
+            }
+            re[(2 * j + 1) * OS] = r;
+            im[(2 * j + 1) * OS] = i;
+        }
+    }
+}
+
 // The vote of one group (one warp): lambda_m of its members' patches, components read from src at
 // c * plane + (e >> 3) * rstride + (e & 7) + off[k] for member k; returns 1 for a vote, 0 otherwise (a group
 // the FP32 bound cannot settle is listed for k_vote_exact and counts 0 here).
@@ -172,49 +226,26 @@ __device__ __forceinline__ int vote_group(const float *__restrict__ src, size_t 
         float p[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) p[k] = src[base + off[k]];
-        float x0 = 0.f, a0 = 0.f, a1 = 0.f;
+        // q_k = p_k - p_0: X_m(q) = X_m(p) for m != 0, and X_0(p) = X_0(q) + K p_0
+        float q[K], a1 = 0.f;
+        q[0] = 0.f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            x0 += p[k];
-            a0 += fabsf(p[k]);
-        }
-        lam[0] = fmaf(x0, x0, lam[0]);
-        e0sq = fmaf(a0, a0, e0sq);
-        float q[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
+        for (int k = 1; k < K; ++k) {
             q[k] = p[k] - p[0];
             a1 += fabsf(q[k]);
         }
+        float xr[NM], xi[NM];
+        rdft_half<K, 1, NM>(q, xr, xi);
+        const float x0 = fmaf((float)K, p[0], xr[0]);
+        lam[0] = fmaf(x0, x0, lam[0]);
+#pragma unroll
+        for (int m = 1; m < NM; ++m) lam[m] = fmaf(xr[m], xr[m], fmaf(xi[m], xi[m], lam[m]));
+        // error bounds: X_m, m != 0, errs by at most sqrt(2) gamma_(K/4 + 3) sum_k |q_k| (the subtraction's
+        // rounding added), X_0(p) by gamma_(log2 K + 2) (sum_k |q_k| + K |p_0|); both inside sqrt(2) (K + 3) u
+        // times these sums, the bounds below
+        const float a0 = fmaf((float)K, fabsf(p[0]), a1);
+        e0sq = fmaf(a0, a0, e0sq);
         esq = fmaf(a1, a1, esq);
-        // k and K - k see conjugate twiddles: q_k w^{mk} + q_{K-k} w^{-mk} = (q_k + q_{K-k}) cos
-        // + i (q_k - q_{K-k}) (-sin), and w^{m K/2} = (-1)^m.  Per component this evaluation errs by
-        // at most sqrt(2) (K/2 + 5/2) u sum_k |q_k| (the subtraction, the pair sum, the twiddle, K/2
-        // accumulations), inside the bound below (sqrt(2) (K + 3) u sum_k |q_k|).
-        float sp[K / 2 + 1], dm[K / 2 + 1];
-#pragma unroll
-        for (int k = 1; k < K / 2; ++k) {
-            sp[k] = q[k] + q[K - k];
-            dm[k] = q[k] - q[K - k];
-        }
-#pragma unroll
-        for (int m = 1; m < NM; ++m) {
-            float xr = (m & 1) ? -q[K / 2] : q[K / 2], xi = 0.f;
-#pragma unroll
-            for (int k = 1; k < K / 2; ++k) {
-                const int j = ((m * k) % K) * (32 / K);
-                // quarter turns: fmaf with an exact 0 or +-1 is the plain sum (same rounding)
-                if (j == 0) xr += sp[k];
-                else if (j == 8) xi -= dm[k];
-                else if (j == 16) xr -= sp[k];
-                else if (j == 24) xi += dm[k];
-                else {
-                    xr = fmaf(sp[k], c_twc[j], xr);
-                    xi = fmaf(dm[k], c_tws[j], xi);
-                }
-            }
-            lam[m] = fmaf(xr, xr, fmaf(xi, xi, lam[m]));
-        }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
