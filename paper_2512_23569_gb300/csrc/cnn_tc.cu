@@ -101,7 +101,7 @@ struct ConvTcLayout {
 // in_scale (1/255); otherwise FP16 planes hin[g][y][x][8].  EPI: the
 // epilogue (EPI_RELU, EPI_MAP, EPI_MASK with the activation planes hmask).
 template <int CING, int NOUT, bool IN_F32, int EPI>
-__global__ void __launch_bounds__(NTH, 1)
+__global__ void __launch_bounds__(NTH, 2)
     k_conv_tc(const float *__restrict__ img, int C, float in_scale, const __half *__restrict__ hin, int H, int W,
               const __half *__restrict__ wt, int cin, int cout, __half *__restrict__ hout, float *__restrict__ map,
               const __half *__restrict__ hmask, int *err) {
@@ -139,24 +139,39 @@ __global__ void __launch_bounds__(NTH, 1)
     for (int strip = blockIdx.x; strip < nstrip; strip += gridDim.x) {
         const int y0 = (strip / nsx) * SY, x0 = (strip % nsx) * SX;
         // ---- stage the input planes with the halo (zero outside the image)
-        for (int e = tid; e < CING * PY * PX; e += NTH) {
-            const int g = e / (PY * PX), r = e - g * (PY * PX), py = r / PX, px = r - py * PX;
-            const int y = y0 - 1 + py, x = x0 - 1 + px;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (y >= 0 && y < H && x >= 0 && x < W) {
-                if (IN_F32) {
-                    if (g == 0) {
-                        __align__(16) __half h[8];
+        if constexpr (IN_F32) {
+            // plane 0 only (the others stay zero from the first strip): every load of the thread's pixels
+            // issued before the first conversion
+            constexpr int NE = (PY * PX + NTH - 1) / NTH;
+            float v[NE][3];
 #pragma unroll
-                        for (int c = 0; c < 8; ++c)
-                            h[c] = __float2half_rn(c < C ? img[c * HW + (size_t)y * W + x] * in_scale : 0.f);
-                        v = *reinterpret_cast<const uint4 *>(h);
-                    }
-                } else {
-                    v = reinterpret_cast<const uint4 *>(hin)[((size_t)g * H + y) * W + x];
+            for (int i = 0; i < NE; ++i) {
+                const int e = tid + i * NTH, py = e / PX, px = e - py * PX;
+                const int y = y0 - 1 + py, x = x0 - 1 + px;
+                const bool in = e < PY * PX && y >= 0 && y < H && x >= 0 && x < W;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[i][c] = (in && c < C) ? __ldg(img + c * HW + (size_t)y * W + x) : 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < NE; ++i) {
+                const int e = tid + i * NTH;
+                if (e < PY * PX) {
+                    __align__(16) __half h[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) h[c] = __float2half_rn(c < 3 ? v[i][c] * in_scale : 0.f);
+                    sA[e] = *reinterpret_cast<const uint4 *>(h);
                 }
             }
-            sA[e] = v;
+            if (strip == (int)blockIdx.x)
+                for (int e = PY * PX + tid; e < CING * PY * PX; e += NTH) sA[e] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+            for (int e = tid; e < CING * PY * PX; e += NTH) {
+                const int g = e / (PY * PX), r = e - g * (PY * PX), py = r / PX, px = r - py * PX;
+                const int y = y0 - 1 + py, x = x0 - 1 + px;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (y >= 0 && y < H && x >= 0 && x < W) v = reinterpret_cast<const uint4 *>(hin)[((size_t)g * H + y) * W + x];
+                sA[e] = v;
+            }
         }
         tc::fence_async_smem();
         __syncthreads();

@@ -393,6 +393,24 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
                     if (d[i] >= 0) sReg[d[i]] = __float2half_rn(v[i]);
             }
         }
+        // the block's next tile's region into L2 while this tile runs (its staging then reads L2, not HBM):
+        // per channel and row, one address every 128 bytes from the first column, and the last column
+        if (!BATCH && gt + (int)gridDim.x < total) {
+            const int nt = gt + (int)gridDim.x;
+            const int nyi = nt / a.ntx, nxi = nt - nyi * a.ntx;
+            const int ngy0 = nyi * a.ty, ngx0 = nxi * a.tx;
+            const int ngy1 = min(a.ny, ngy0 + a.ty) - 1, ngx1 = min(a.nx, ngx0 + a.tx) - 1;
+            const int py0 = max(0, grid_pos(ngy0, a.H, a.step) - a.R);
+            const int py1 = min(a.H - 1, grid_pos(ngy1, a.H, a.step) + a.R + PS - 1);
+            const int px0 = max(0, grid_pos(ngx0, a.W, a.step) - a.R);
+            const int px1 = min(a.W - 1, grid_pos(ngx1, a.W, a.step) + a.R + PS - 1);
+            const int nl = (px1 - px0) / 32 + 2, prow = py1 - py0 + 1;
+            for (int e = tid; e < C * prow * nl; e += NT) {
+                const int c = e / (prow * nl), rem = e - c * (prow * nl), y = rem / nl, l = rem - y * nl;
+                const int x = min(px0 + 32 * l, px1);
+                tc::prefetch_l2(a.img + c * HW + (size_t)(py0 + y) * a.W + x);
+            }
+        }
         // group tid (< GPB) of batch bb: its noise level (the map's, else 1), loaded a batch ahead of its use
         // (nothing reads the loaded value until then: no wait), and whether the slot holds a group
         const float tau_all = use_map ? 0.f : a.st->tau32;

@@ -158,5 +158,8 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
                  : "memory");
 }
 
+// Brings the 128-byte line holding p (a valid global address) into L2; no register waits on it.
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 }  // namespace tc
 }  // namespace hts
