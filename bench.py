@@ -387,7 +387,7 @@ def _tc_roofline(dom, ms_per_launch, H, W, C, K, win, step, green):
         return {"kernel": dom, "bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                 "frac": ach / peaks["bf16_tflops"], "traffic": None,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured; FP16 = BF16 rate)",
-                "algorithmic": wk["per"] + "; the Kronecker-form GEMMs issue 1.31 MFLOP per group"}
+                "algorithmic": wk["per"] + "; the slice GEMMs (64x64 and 128x128 per Haar row, forward and inverse) issue 1.31 MFLOP per group"}
     if dom == "k_match_tc":
         flops = tc_issued_flops(H, W, K, win, step, green, C)
         ach = flops / (ms_per_launch / 1e3) / 1e12

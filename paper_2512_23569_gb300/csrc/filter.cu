@@ -1518,7 +1518,8 @@ __global__ void k_normalize4(const longlong2 *__restrict__ acc, const int4 *__re
 // Weights from patch-origin counts (the tensor-core filter's aggregation): the weight of pixel (y, x)
 // is the sum of the counts of the origins (y - u, x - v), 0 <= u, v < 8, formed per 32 x 32 block of
 // pixels from the counts staged in shared memory (row sums over 8 columns, then 8 rows); then
-// out = sum / (2^16 weight) as in k_normalize.
+// out = sum / (2^16 weight) as in k_normalize.  Colour: the tensor-core filter sums the slices of the
+// channel DFT (P^(1), sqrt2 Re P^(2), sqrt2 Im P^(2), orthonormal), turned back into R, G, B here.
 constexpr int NB_T = 32;
 template <int C>
 __global__ void __launch_bounds__(256) k_normalize_box(const long long *__restrict__ acc, const int *__restrict__ cnt,
@@ -1549,8 +1550,17 @@ __global__ void __launch_bounds__(256) k_normalize_box(const long long *__restri
 #pragma unroll
         for (int u = 0; u < PS; ++u) w += sr[yy + u][xx];
         const size_t p = (size_t)y * W + x;
-#pragma unroll
-        for (int c = 0; c < C; ++c) out[c * HW + p] = __ll2float_rn(acc[c * HW + p]) * (1.0f / 65536.0f) / (float)w;
+        if constexpr (C == 1) {
+            out[p] = __ll2float_rn(acc[p]) * (1.0f / 65536.0f) / (float)w;
+        } else {  // the sums are per slice [P^(1) | sqrt2 Re P^(2) | sqrt2 Im P^(2)]: the inverse channel DFT
+            const float sc = (1.0f / 65536.0f) / (float)w;
+            const float s0 = __ll2float_rn(acc[p]) * sc, s1 = __ll2float_rn(acc[HW + p]) * sc,
+                        s2 = __ll2float_rn(acc[2 * HW + p]) * sc;
+            const float t = fc::K3F * s0 - 0.5f * fc::K23F * s1;
+            out[p] = fmaf(fc::K23F, s1, fc::K3F * s0);
+            out[HW + p] = t - fc::R2F * s2;
+            out[2 * HW + p] = t + fc::R2F * s2;
+        }
     }
 }
 

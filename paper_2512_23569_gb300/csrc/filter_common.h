@@ -9,6 +9,7 @@ namespace fc {
 constexpr float R2F = 0.70710678118654752f;  // 1/sqrt(2)
 constexpr float K3F = 0.57735026918962576f;  // 1/sqrt(3)
 constexpr float S3H = 0.86602540378443865f;  // sqrt(3)/2
+constexpr float K23F = 0.81649658092772604f;  // sqrt(2/3)
 
 // --------------------------------------------------------- Haar (Eq. 8)
 

@@ -1,26 +1,32 @@
 // Collaborative filtering of the precision form on the sm_103a tensor cores
 // (Eq. 19-21, Alg. 1 steps 2-3), FP32 threshold decisions.
 //
-// The unitary DFT along the channels (Eq. 4-5) and the separable projection
-// Shat = U^H Phat V of every Fourier slice (Eq. 19) are linear in the patch's
-// raw pixels, so together they are one real orthogonal matrix F (192 x 192
-// for colour, 64 x 64 for gray) applied to the patch read as a vector of its
-// R, G, B pixels, giving [S^(1) | sqrt2 Re S^(2) | sqrt2 Im S^(2)] (slice 3 is
-// the conjugate of slice 2).  The Haar transform along the group axis (Eq. 8)
-// acts on the members, F on each member's pixels: the two commute, so the
-// kernel applies Haar first, to the gathered pixels in FP32 registers (a
-// thread holds one pixel of all the group's members), and one GEMM then
-// gives the 3-D coefficients: with the 128 Haar rows of a batch (8 groups of
-// K = 16) as the MMA's M, D[row][coefficient] = sum_pixel A[row][pixel]
-// F[coefficient][pixel], FP16 operands, FP32 accumulation in tensor memory
-// (tcgen05.mma kind::f16, N = 192).  A thread per row thresholds its
-// coefficients in place (Eq. 20; the complex slice's real and imaginary
-// parts lie in the same row) and writes them as the inverse GEMM's operand;
-// the inverse (Eq. 21 and the inverse channel DFT) is F^T, the same
-// shared-memory matrix read with the transpose bit (MN-major), giving each
-// Haar row's pixels.  One transposed pass per channel hands a (group, pixel)
-// pair to a thread, which applies the inverse Haar along the group and adds
-// the members' estimates to the tile's sums.
+// The unitary DFT along the channels (Eq. 4-5), in its real orthonormal form
+// [P^(1) | sqrt2 Re P^(2) | sqrt2 Im P^(2)] (slice 3 is the conjugate of
+// slice 2), is applied to the gathered pixels in FP32 registers.  The
+// separable projection Shat = U^H Phat V of each slice (Eq. 19) is then one
+// real orthogonal matrix per slice: F0 (64 x 64) for the real slice 1 and,
+// for colour, F1 (128 x 128, the real form [[Re M, -Im M], [Im M, Re M]] of
+// the unitary M = conj(U) (x) V of the complex slice 2), giving
+// [S^(1) | sqrt2 Re S^(2) | sqrt2 Im S^(2)].  The Haar transform along the
+// group axis (Eq. 8) acts on the members, the DFT and F on each member's
+// pixels: they commute, so the kernel applies the DFT and Haar first, in
+// FP32 registers (a thread holds one pixel of all the group's members), and
+// two GEMMs then give the 3-D coefficients: with the 128 Haar rows of a
+// batch (8 groups of K = 16) as the MMA's M, D[row][coefficient] =
+// sum_pixel A[row][pixel] F[coefficient][pixel] per slice, FP16 operands,
+// FP32 accumulation in tensor memory (tcgen05.mma kind::f16, N = 64 and
+// 128).  A thread per row thresholds its coefficients in place (Eq. 20; the
+// complex slice's real and imaginary parts lie in the same row) and writes
+// them as the inverse GEMMs' operand; the inverse (Eq. 21) is F0^T and F1^T,
+// the same shared-memory matrices read with the transpose bit (MN-major),
+// giving each Haar row's slice values.  One transposed pass per slice hands
+// a (group, pixel) pair to a thread, which applies the inverse Haar along
+// the group and adds the members' estimates to the tile's sums of that
+// slice; slice 1's pass runs while the tensor cores compute slice 2's
+// inverse.  The sums are kept per slice, and the inverse channel DFT is
+// applied once per pixel when they are normalised (k_normalize_box): the
+// aggregation and the DFT are both linear.
 //
 // FP16 rather than BF16: pixels lie in a bounded range and the bases are
 // orthonormal, so FP16's 11-bit significand fits the data, where BF16's 8
@@ -51,6 +57,8 @@ namespace hts {
 namespace {
 
 using fc::K3F;
+using fc::K23F;
+constexpr float K12F = fc::R2F;
 
 // The Haar transform of Eq. 8 without its 1/sqrt(2) factors: sums and differences only.  In the row
 // order of Eq. 8 (row 0 the sum, then the difference rows coarse to fine) coefficient k has passed
@@ -123,21 +131,23 @@ __device__ __forceinline__ int fix8(float v) {
 
 template <int C>
 struct FtcLayout {
-    // The FP16 transform F [coefficient][pixel] (CK x CK, CK = 64 C), K-major, core matrices of 8 rows x 8
-    // columns, 8-column groups 128 B apart along K and 8-row groups CK * 16 B apart: the forward GEMM's B
-    // operand, and with the transpose bit (K = coefficients, N = pixels, MN-major) the inverse's.
-    static constexpr int CK = 64 * C;
-    static constexpr int B_HALVES = CK * CK;
-    // the row operand, and between the inverse GEMM and the next batch's commit the transposed FP32 buffer
-    // [64][TS] of one 64-column chunk
-    static constexpr size_t a_bytes = (size_t)C * BLK_A > (size_t)64 * TS * 4 ? (size_t)C * BLK_A : (size_t)64 * TS * 4;
+    // The FP16 transforms F0 [coefficient][pixel] (64 x 64) and, for colour, F1 (128 x 128) right after it,
+    // K-major, core matrices of 8 rows x 8 columns, 8-column groups 128 B apart along K and 8-row groups
+    // (64 or 128) * 16 B apart: the forward GEMMs' B operands, and with the transpose bit (K = coefficients,
+    // N = pixels, MN-major) the inverse's.
+    static constexpr int F0_HALVES = 64 * 64;
+    static constexpr int B_HALVES = (C == 3) ? F0_HALVES + 128 * 128 : F0_HALVES;
+    static constexpr size_t a_bytes = (size_t)C * BLK_A;  // the row operand
     static constexpr size_t a_off = 0;
-    static constexpr size_t b_off = a_off + a_bytes;
+    static constexpr size_t t_off = a_off + a_bytes;  // the transposed FP32 buffer [64][TS] of one slice
+    static constexpr size_t b_off = t_off + (size_t)64 * TS * 4;
     static constexpr size_t basis_off = b_off + (size_t)B_HALVES * 2;  // 6 x 64 FP32
     static constexpr size_t misc_off = basis_off + (size_t)6 * 64 * 4;
-    // misc: tau[2][32] float, off[2][MB] int, 2 mbarrier words, tensor-memory slot
-    static constexpr size_t job_off = misc_off + (size_t)2 * 32 * 4 + 2 * MB * 4 + 16 + 16;
-    // then the tile's sums [C][RA] int32 and its staged region [C][RA] FP16 (RA = rows x acc_stride(width))
+    // misc: tau[2][32] float, off[2][MB] int, 4 mbarrier words (forward; inverse of slice 1; inverse of
+    // slices 2-3), tensor-memory slot
+    static constexpr size_t job_off = misc_off + (size_t)2 * 32 * 4 + 2 * MB * 4 + 32 + 16;
+    // then the tile's sums [C][RA] int32 (per slice) and its staged region [C][RA] FP16 (per channel; RA =
+    // rows x acc_stride(width))
     static constexpr size_t acc_off = job_off + 256;
     static constexpr size_t bytes(int rh, int rw) { return acc_off + (size_t)C * rh * acc_stride(rw) * 6; }
     static constexpr uint32_t tcols = (C == 3) ? 256 : 64;
@@ -171,16 +181,17 @@ struct FtcBatch {
 //
 // Per batch of MB Haar rows (GPB = MB / K groups):
 //  1. gather: a thread holds, for one (group, pixel) pair, that pixel of the group's K members (for K = 32
-//     two threads hold 16 members each), applies the unnormalised Haar transform along the group axis in
-//     FP32 registers and writes the K Haar rows' pixel to the row operand (FP16); Haar along the group and the
-//     per-patch transform F commute, so the forward GEMM then gives the 3-D coefficients directly;
-//  2. forward GEMM: D[row][coefficient] = sum_pixel A[row][pixel] F[coefficient][pixel] (tensor memory);
+//     two threads hold 16 members each), applies the channel DFT and the unnormalised Haar transform along
+//     the group axis in FP32 registers and writes the K Haar rows' slice values to the row operand (FP16);
+//  2. forward GEMMs: D[row][coefficient] = sum_pixel A[row][pixel] F[coefficient][pixel] per slice
+//     (tensor memory);
 //  3. threshold: a thread per row (tensor-memory lane) keeps or drops its coefficients against the level's
 //     threshold (modulus for the complex slice, both parts in the same lane), rescales the kept ones by
-//     2^-l and writes them as the inverse GEMM's row operand (FP16);
-//  4. inverse GEMM with F^T: the rows' pixels, still in the Haar domain along the group;
-//  5. per channel: tensor memory -> transposed FP32 buffer; a thread per (group, pixel) pair applies the
-//     unnormalised inverse Haar and adds the K members' estimates of that pixel to the tile's sums.
+//     2^-l and writes them as the inverse GEMMs' row operand (FP16);
+//  4. inverse GEMMs with F0^T, then F1^T (two commits): the rows' slice values, still in the Haar domain;
+//  5. per slice, once its inverse has completed: tensor memory -> transposed FP32 buffer; a thread per
+//     (group, pixel) pair applies the unnormalised inverse Haar and adds the K members' estimates of that
+//     pixel to the tile's sums of the slice.
 template <int C, int K, bool BATCH>
 __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ FtcArgs a0,
                                                      const __grid_constant__ FtcBatch bt) {
@@ -194,13 +205,13 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
     constexpr int LOGK = (K == 8) ? 3 : (K == 16) ? 4 : 5;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sA = smem + L::a_off;
-    float *sT = reinterpret_cast<float *>(smem + L::a_off);
+    float *sT = reinterpret_cast<float *>(smem + L::t_off);
     __half *sB = reinterpret_cast<__half *>(smem + L::b_off);
     float *sBas = reinterpret_cast<float *>(smem + L::basis_off);
     float *sTau = reinterpret_cast<float *>(smem + L::misc_off);  // [2][32] groups' thresholds
     int *sOff = reinterpret_cast<int *>(sTau + 64);  // [2][MB] members' patch origins in the tile region (-1: none)
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sOff + 2 * MB);  // 8-byte aligned
-    uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sOff + 2 * MB);  // [3], 8-byte aligned
+    uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 4);
     int *accs = reinterpret_cast<int *>(smem + L::acc_off);
     FtcArgs *sjob = reinterpret_cast<FtcArgs *>(smem + L::job_off);
     const FtcArgs &a = BATCH ? *sjob : a0;  // the current job's arguments
@@ -209,7 +220,6 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
     __half *sReg = reinterpret_cast<__half *>(accs + C * RA);  // [C][RA] the tile's region, FP16
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // ---- bases (row-major 8x8, element (r, c) at r * 8 + c) and the transform F of the current job
-    constexpr int CK = L::CK;
     auto build_f = [&]() {
         for (int t = tid; t < 64; t += NT) {
             sBas[t] = a.b32[(0 * 64 + t) * 2];        // U0
@@ -222,32 +232,34 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
             }
         }
         __syncthreads();
-        // F: the unitary DFT along the channels (Eq. 4-5) followed by the slices' projections (Eq. 19), as one real
-        // orthogonal map of the raw R, G, B pixels (column t * 64 + (i, j)) to [S^(1) | sqrt2 Re S^(2) |
-        // sqrt2 Im S^(2)] (row (a, b), 64 + (a, b), 128 + (a, b)); its inverse (Eq. 21) is its transpose.
-        // Slice 1: P^(1) = (R + w G + w^2 B) / sqrt3, w = exp(-2 pi i / 3), projected by conj(U1[i][a]) V1[j][b].
-        for (int e = tid; e < CK * CK; e += NT) {
-            const int n = e / CK, k = e - n * CK;  // n: coefficient row, k: channel t = k / 64, pixel (i, j)
-            const int t = k >> 6, px = k & 63, nc = n & 63, sl = n >> 6;
-            const int ia = (px >> 3) * 8 + (nc >> 3), jb = (px & 7) * 8 + (nc & 7);
+        // F0[(a, b)][(i, j)] = U0[i][a] V0[j][b] (S^(1) = U0^T P^(1) V0, Eq. 19).  Colour, F1: with M = conj(U1[i][a])
+        // V1[j][b] = Mr + i Mi, rows Re S^(2) then Im S^(2), columns Re P^(2) then Im P^(2) (both sides times
+        // sqrt2): F1 = [[Mr, -Mi], [Mi, Mr]].
+        for (int e = tid; e < L::B_HALVES; e += NT) {
+            int n, k, idx;
             float f;
-            if (sl == 0) {
-                f = sBas[ia] * sBas[64 + jb];  // U0[i][a] V0[j][b]
-                if (C == 3) f *= K3F;
+            if (e < L::F0_HALVES) {
+                n = e >> 6;
+                k = e & 63;
+                f = sBas[(k >> 3) * 8 + (n >> 3)] * sBas[64 + (k & 7) * 8 + (n & 7)];
+                idx = (((n >> 3) * 8 + (k >> 3)) << 6) + ((n & 7) << 3) + (k & 7);
             } else {
+                const int e1 = e - L::F0_HALVES;
+                n = e1 >> 7;
+                k = e1 & 127;
+                const int nc = n & 63, px = k & 63;
+                const int ia = (px >> 3) * 8 + (nc >> 3), jb = (px & 7) * 8 + (nc & 7);
                 const float ur = sBas[128 + ia], ui = sBas[192 + ia], vr = sBas[256 + jb], vi = sBas[320 + jb];
-                const float mr = ur * vr + ui * vi, mi = ur * vi - ui * vr;  // conj(U1[i][a]) V1[j][b]
-                // channel weights of Re and Im of P^(1): (1, -1/2, -1/2) / sqrt3 and (0, -1/2, 1/2)
-                const float cr = (t == 0) ? K3F : -0.5f * K3F, ci = (t == 0) ? 0.f : (t == 1 ? -0.5f : 0.5f);
-                const float v = (sl == 1) ? (mr * cr - mi * ci) : (mr * ci + mi * cr);
-                f = v * 1.41421356237309505f;
+                const float mr = ur * vr + ui * vi, mi = ur * vi - ui * vr;
+                f = (n < 64) ? ((k < 64) ? mr : -mi) : ((k < 64) ? mi : mr);
+                idx = L::F0_HALVES + (((n >> 3) * 16 + (k >> 3)) << 6) + ((n & 7) << 3) + (k & 7);
             }
-            sB[(((n >> 3) * (CK / 8) + (k >> 3)) << 6) + ((n & 7) << 3) + (k & 7)] = __float2half_rn(f);
+            sB[idx] = __float2half_rn(f);
         }
     };
     if (!BATCH) build_f();
     if (tid == 0) {
-        tc::bar_init(bar, 1);
+        for (int i = 0; i < 3; ++i) tc::bar_init(&bar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) tc::tmem_alloc(slot, L::tcols);
@@ -255,43 +267,59 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = *slot;
-    const uint32_t idf = tc::idesc_f16(MB, L::CK, false);                 // forward: B K-major
-    const uint32_t idi = tc::idesc_f16(MB, L::CK, false) | (1u << 16);    // inverse: B transposed (MN-major)
+    const uint32_t idf0 = tc::idesc_f16(MB, 64, false), idf1 = tc::idesc_f16(MB, 128, false);  // B K-major
+    const uint32_t idi0 = idf0 | (1u << 16), idi1 = idf1 | (1u << 16);  // inverse: B transposed (MN-major)
     const int q = warp & 3, wq = warp >> 2;  // tensor-memory lane quarter, column quarter
     const uint32_t tlane = (uint32_t)(32 * q) << 16;
-    uint32_t phase = 0;
+    uint32_t phase = 0;  // parity of the batches done: every barrier completes once per batch
     bool ok = true;
 
-    // issue the MMAs of one GEMM stage and wait for them; false if the wait gave up
-    auto run_stage = [&](bool inverse) -> bool {
+    // A K step kk of the row operand: columns 16 kk .. 16 kk + 15, two core matrices at (kk % 4) * 2 * LBO_A
+    // in 64-column block kk / 4.
+    auto a_desc = [&](uint32_t a0, int kk) { return tc::sdesc(a0 + (kk >> 2) * BLK_A + (kk & 3) * 2 * LBO_A, LBO_A, SBO_A); };
+    // Issues the MMAs of the forward GEMMs (commit on bar[0]) or of the inverse ones (slice 1's commit on
+    // bar[1], then slices 2-3's on bar[2]), after every thread's shared-memory writes; thread 0 only.
+    // Forward B = F: K = pixels, core matrices 128 B apart along K, (64 or 128) * 16 B along N (coefficients).
+    // Inverse B = F^T read in place: K = coefficients ((64 or 128) * 16 B apart: LBO), N = pixels (128 B
+    // apart: SBO), the MN-major convention.
+    auto issue = [&](bool inverse) {
+        tc::fence_after();
+        const uint32_t a0 = tc::su32(sA), f0 = tc::su32(sB), f1 = f0 + L::F0_HALVES * 2;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t bd = inverse ? tc::sdesc(f0 + kk * 2 * 1024, 1024, 128) : tc::sdesc(f0 + kk * 256, 128, 1024);
+            tc::mma_f16(tbase, a_desc(a0, kk), bd, inverse ? idi0 : idf0, kk > 0 ? 1u : 0u);
+        }
+        if (inverse) tc::mma_commit(&bar[1]);
+        if constexpr (C == 3) {
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const uint64_t bd =
+                    inverse ? tc::sdesc(f1 + kk * 2 * 2048, 2048, 128) : tc::sdesc(f1 + kk * 256, 128, 2048);
+                tc::mma_f16(tbase + 64, a_desc(a0, 4 + kk), bd, inverse ? idi1 : idf1, kk > 0 ? 1u : 0u);
+            }
+            if (inverse) tc::mma_commit(&bar[2]);
+        }
+        if (!inverse) tc::mma_commit(&bar[0]);
+    };
+    // Every thread: the row operand written, then thread 0 issues the GEMMs.
+    auto launch_stage = [&](bool inverse) {
         tc::fence_async_smem();
         tc::fence_before();
         __syncthreads();
-        if (tid == 0) {
-            tc::fence_after();
-            const uint32_t a0 = tc::su32(sA), b0 = tc::su32(sB);
-            // A: the row operand, K step kk = block kk / 4, two core matrices at (kk % 4) * 2 * LBO_A.
-            // Forward B = F: K = pixels, core matrices 128 B apart along K, CK * 16 B along N (coefficients).
-            // Inverse B = F^T read in place: K = coefficients (core matrices CK * 16 B apart: LBO), N = pixels
-            // (128 B apart: SBO), the MN-major convention.
-#pragma unroll
-            for (int kk = 0; kk < CK / 16; ++kk) {
-                const uint64_t ad = tc::sdesc(a0 + (kk >> 2) * BLK_A + (kk & 3) * 2 * LBO_A, LBO_A, SBO_A);
-                const uint64_t bd = inverse ? tc::sdesc(b0 + kk * 2 * (CK * 16), CK * 16, 128)
-                                            : tc::sdesc(b0 + kk * 256, 128, CK * 16);
-                tc::mma_f16(tbase, ad, bd, inverse ? idi : idf, kk > 0 ? 1u : 0u);
-            }
-            tc::mma_commit(bar);
-        }
-        const bool done = tc::bar_wait(bar, phase, SPIN);
+        if (tid == 0) issue(inverse);
+    };
+    // Waits for barrier i of this batch; false (error 2 recorded) if the wait gave up, after thread 0 has
+    // waited (bounded) for every MMA this batch issued, so that the memory can be released.
+    auto wait_bar = [&](int i) -> bool {
+        const bool done = tc::bar_wait(&bar[i], phase, SPIN);
         if (__syncthreads_or(!done)) {
             if (tid == 0) {
-                tc::bar_wait(bar, phase, SPIN);  // the MMAs must end before the memory is released
+                for (int j = i; j < (i == 0 ? 1 : (C == 3 ? 3 : 2)); ++j) tc::bar_wait(&bar[j], phase, SPIN);
                 atomicExch(&a.st->error, 2);
             }
             return false;
         }
-        phase ^= 1u;
         tc::fence_after();
         return true;
     };
@@ -465,6 +493,15 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
 #pragma unroll
                     for (int c = 0; c < C; ++c) v[j][c] = in ? __half2float(src[c * RP + o]) : 0.f;
                 }
+                if constexpr (C == 3) {  // the channel DFT (Eq. 4-5), real orthonormal form: v[j][s] = slice value s
+#pragma unroll
+                    for (int j = 0; j < KM; ++j) {
+                        const float r = v[j][0], gb = v[j][1] + v[j][2], d = v[j][2] - v[j][1];
+                        v[j][0] = K3F * (r + gb);
+                        v[j][1] = K23F * fmaf(-0.5f, gb, r);
+                        v[j][2] = K12F * d;
+                    }
+                }
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     float x[KM];
@@ -506,8 +543,9 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
                 if (tid < GPB) sTau[32 * (cur ^ 1) + tid] = tau_from(sigreg, svalid);
                 if (tid < MB) member_off(pvalid ? posreg : -1, cur ^ 1);
             }
-            // ---- forward transform (Eq. 4-5, 19) of the Haar rows: D[row] = [S0 | sqrt2 Re S1 | sqrt2 Im S1]
-            if (!run_stage(false)) {
+            // ---- forward transform (Eq. 19) of the Haar rows: D[row] = [S0 | sqrt2 Re S1 | sqrt2 Im S1]
+            launch_stage(false);
+            if (!wait_bar(0)) {
                 ok = false;
                 break;
             }
@@ -568,13 +606,10 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
                     *reinterpret_cast<uint4 *>(rowp + 2 * BLK_A + (2 * wq + 1) * LBO_A) = ip[1];
                 }
             }
-            // ---- inverse transform (Eq. 21 and the inverse channel DFT): E[row] = [R | G | B] pixels of the
-            //      group's thresholded Haar rows
-            if (!run_stage(true)) {
-                ok = false;
-                break;
-            }
-            // ---- per channel: inverse Haar along the group axis and aggregation of the members' estimates
+            // ---- inverse transform (Eq. 21): E[row] = the slices' values of the group's thresholded Haar rows,
+            //      slice 1 first (its own commit), so that its aggregation overlaps the rest
+            launch_stage(true);
+            // ---- per slice: inverse Haar along the group axis and aggregation of the members' estimates
             int offs[PPT][KM];  // this thread's members' patch origins in the region (-1: empty slot)
 #pragma unroll
             for (int i = 0; i < PPT; ++i) {
@@ -588,6 +623,10 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
             }
 #pragma unroll 1
             for (int c = 0; c < C; ++c) {
+                if (c < 2 && !wait_bar(1 + c)) {  // slice c's inverse has completed (slices 2 and 3 together)
+                    ok = false;
+                    break;
+                }
                 {
                     uint32_t v[16];
                     tc::tmem_ld16(tbase + tlane + (uint32_t)(64 * c + 16 * wq), v);
@@ -633,7 +672,14 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
                         const int lg = b * GPB + g;
                         const int gy = gy0 + lg / a.tx, gx = gx0 + lg % a.tx;
                         if (lg < gpt && gy <= gy1 && gx <= gx1) {
-                            const float mu = __ldg(a.mean_est + (size_t)(gy * a.nx + gx) * (C * 64) + c * 64 + p);
+                            const float *mp = a.mean_est + (size_t)(gy * a.nx + gx) * (C * 64) + p;
+                            float mu;  // slice c of the refined mean's pixel p
+                            if (C == 1) {
+                                mu = __ldg(mp);
+                            } else {
+                                const float r = __ldg(mp), gg = __ldg(mp + 64), bl = __ldg(mp + 128);
+                                mu = c == 0 ? K3F * (r + (gg + bl)) : c == 1 ? K23F * fmaf(-0.5f, gg + bl, r) : K12F * (bl - gg);
+                            }
 #pragma unroll
                             for (int j = 0; j < KM; ++j) x[j] += mu;
                         }
@@ -647,9 +693,11 @@ __global__ void __launch_bounds__(NT, 1) k_filter_tc(const __grid_constant__ Ftc
                 tc::fence_before();
                 __syncthreads();
             }
+            if (!ok) break;
+            phase ^= 1u;
         }
         if (!ok) break;
-        // flush the tile's sums to the image-wide int64 sums
+        // flush the tile's sums (per slice) to the image-wide int64 sums
         for (int e = tid; e < rh * rw; e += NT) {
             const int yy = e / rw, xx = e - yy * rw;
             const int le = yy * rwp + xx;
