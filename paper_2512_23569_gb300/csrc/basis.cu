@@ -37,10 +37,9 @@ __device__ __forceinline__ void pair_of(int p, int &a, int &b) {
 
 // Raw channel products of the reference patches, exactly: every product of
 // two floats is split into p + e (p = fl(x y), e = fma(x, y, -p)) and
-// accumulated in four double-float (hi, lo) pairs (positions q mod 4) over at
-// most COV_CH / 4 terms each, then added to an FP64 sum; |error| <= n u^2
-// sum|terms| per pair (u = 2^-24, n <= 32), i.e. FP64-grade without the FP64
-// pipes.
+// accumulated in a double-float (hi, lo) pair over at most COV_CH terms, then
+// added to an FP64 sum; |error| <= n u^2 sum|terms| per pair (u = 2^-24,
+// n <= 128), i.e. FP64-grade without the FP64 pipes.
 //   row sums  M_tt'[a][b] = sum_i sum_k P_i^(t)[a][k] P_i^(t')[b][k]
 //   col sums  N_tt'[a][b] = sum_i sum_k P_i^(t)[k][a] P_i^(t')[k][b]
 // for channel pairs t <= t' (upper triangles when t = t').  With the patches
@@ -144,17 +143,15 @@ __global__ void __launch_bounds__(CovCfg<C>::THREADS) k_cov(const float *__restr
                 const float4 *X = reinterpret_cast<const float4 *>(sl[t0 * PS + a]);
                 const float4 *Y = reinterpret_cast<const float4 *>(sl[t1 * PS + b]);
                 const float4 *Wt = reinterpret_cast<const float4 *>(sw);
-                // four independent double-float sums (positions q mod 4): four chains in flight per thread
-                float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+                float hi = 0.f, lo = 0.f;
                 for (int q4 = 0; q4 < (np + 3) / 4; ++q4) {
                     const float4 x = X[q4], y = Y[q4], w = Wt[q4];
-                    df_add(hi[0], lo[0], __fmul_rn(x.x, w.x), y.x);
-                    df_add(hi[1], lo[1], __fmul_rn(x.y, w.y), y.y);
-                    df_add(hi[2], lo[2], __fmul_rn(x.z, w.z), y.z);
-                    df_add(hi[3], lo[3], __fmul_rn(x.w, w.w), y.w);
+                    df_add(hi, lo, __fmul_rn(x.x, w.x), y.x);
+                    df_add(hi, lo, __fmul_rn(x.y, w.y), y.y);
+                    df_add(hi, lo, __fmul_rn(x.z, w.z), y.z);
+                    df_add(hi, lo, __fmul_rn(x.w, w.w), y.w);
                 }
-                acc += ((double)hi[0] + (double)lo[0]) + ((double)hi[1] + (double)lo[1]) +
-                       ((double)hi[2] + (double)lo[2]) + ((double)hi[3] + (double)lo[3]);
+                acc += (double)hi + (double)lo;
             }
             __syncthreads();
         }
