@@ -164,6 +164,64 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 
 __device__ __forceinline__ float bf_round(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
 
+// Compare-exchange into ascending order.
+__device__ __forceinline__ void cmpx(uint32_t &a, uint32_t &b) {
+    const uint32_t lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+}
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+// Bitonic sequence v[B .. B + N) into ascending order.
+template <int B, int N, int NP>
+__device__ __forceinline__ void bitonic_clean(uint32_t (&v)[NP]) {
+    constexpr int LN = ilog2c(N);
+#pragma unroll
+    for (int e = LN - 1; e >= 0; --e)
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if ((i & (1 << e)) == 0) cmpx(v[B + i], v[B + i + (1 << e)]);
+}
+// One merge level: the ascending runs of length 2^L of v merged pairwise (the second reversed against the
+// first makes both halves bitonic, then both are cleaned) into runs of length 2^(L+1).
+template <int NP, int L>
+__device__ __forceinline__ void merge_level(uint32_t (&v)[NP]) {
+#pragma unroll
+    for (int base = 0; base < NP; base += 2 << L) {
+#pragma unroll
+        for (int i = 0; i < (1 << L); ++i) cmpx(v[base + i], v[base + (2 << L) - 1 - i]);
+#pragma unroll
+        for (int e = L - 1; e >= 0; --e)
+#pragma unroll
+            for (int i = 0; i < (2 << L); ++i)
+                if ((i & (1 << e)) == 0) cmpx(v[base + i], v[base + i + (1 << e)]);
+    }
+}
+template <int NP, int L, int LE>
+struct MergeLevels {
+    static __device__ __forceinline__ void run(uint32_t (&v)[NP]) {
+        merge_level<NP, L>(v);
+        MergeLevels<NP, L + 1, LE>::run(v);
+    }
+};
+template <int NP, int LE>
+struct MergeLevels<NP, LE, LE> {
+    static __device__ __forceinline__ void run(uint32_t (&)[NP]) {}
+};
+// The S smallest of v[NP] (NP / R ascending runs of length R, powers of two, S >= R) into v[0 .. S),
+// ascending: runs merged up to length S, then the chunks of S folded into the first (element i against
+// element S - 1 - i of the next chunk keeps the S smallest, as a bitonic sequence).  Only compile-time
+// indices: the array stays in registers.
+template <int NP, int R, int S>
+__device__ __forceinline__ void smallest_sorted(uint32_t (&v)[NP]) {
+    MergeLevels<NP, ilog2c(R), ilog2c(S)>::run(v);
+#pragma unroll
+    for (int c = 1; c < NP / S; ++c) {
+#pragma unroll
+        for (int i = 0; i < S; ++i) v[i] = min(v[i], v[c * S + S - 1 - i]);
+        bitonic_clean<0, S, NP>(v);
+    }
+}
+
 // Row pitch of the candidate numbering p = y * Wq + x: the value in [Wc, Wc + 7]
 // whose key columns p mod 64 (bin and half of a thread's run) spread the
 // points of the short lattice directions (dy <= 4, |dx| <= 4) over the most
@@ -200,6 +258,9 @@ template <int K, bool BATCH>
 __global__ void __launch_bounds__(NT, 1) k_match_tc(const __grid_constant__ TcArgs a0,
                                                     const __grid_constant__ TcBatch bt) {
     constexpr int LH = ListCfg<K>::LH, T = ListCfg<K>::T, KC = ListCfg<K>::KC, NBIN = ListCfg<K>::NBIN;
+    constexpr int TP = T <= 1 ? 1 : T <= 2 ? 2 : T <= 4 ? 4 : 8;                   // slots per bin, padded
+    constexpr int LS = LH <= 8 ? 8 : LH <= 16 ? 16 : LH <= 32 ? 32 : 64;           // sorted list length >= LH
+    static_assert(T <= 8 && LH <= 64 && LS >= TP && (NBIN * TP) % LS == 0, "top-list network shape");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const TcLayout L = tc_layout<K>(BATCH ? bt.hc_max : a0.hc_max, BATCH ? bt.wc_max : a0.wc_max);
     TcArgs *sjob = reinterpret_cast<TcArgs *>(smem_raw + L.job);
@@ -551,20 +612,14 @@ __global__ void __launch_bounds__(NT, 1) k_match_tc(const __grid_constant__ TcAr
             // ---- the LH smallest keys of this thread's bins, both threads' lists and pushed-out minima to
             //      shared memory (every MMA has completed: Q, A, E are free)
             if (cw) {
-                uint32_t lst[LH];
-#pragma unroll
-                for (int t = 0; t < LH; ++t) lst[t] = 0xffffffffu;
+                uint32_t v[NBIN * TP];  // bin g's slots ascending at g * TP, padded with ~0
 #pragma unroll
                 for (int g = 0; g < NBIN; ++g)
 #pragma unroll
-                    for (int s = 0; s < T; ++s) {
-                        const uint32_t k = bn[g][s];
+                    for (int s = 0; s < TP; ++s) v[g * TP + s] = s < T ? bn[g][s] : 0xffffffffu;
+                smallest_sorted<NBIN * TP, TP, LS>(v);
 #pragma unroll
-                        for (int t = LH - 1; t > 0; --t) lst[t] = max(lst[t - 1], min(lst[t], k));
-                        lst[0] = min(lst[0], k);
-                    }
-#pragma unroll
-                for (int t = 0; t < LH; ++t) fk[(hh * LH + t) * NR + m] = lst[t];
+                for (int t = 0; t < LH; ++t) fk[(hh * LH + t) * NR + m] = v[t];
                 fe[hh * NR + m] = ev;
             }
             __syncthreads();
