@@ -227,27 +227,28 @@ __global__ void __launch_bounds__(NTH, 2)
 }
 
 // Hidden layers (1..4: four planes of 8 FP16 channels in), with the input staged by TMA: a block runs
-// its strips (16 x 32 output pixels: four 16 x 8 tiles) in turn with two staging buffers; while strip i's
-// MMAs and epilogue run, the tensor-memory accumulators being read and the outputs written, the TMA copy of
-// strip i + 1's input (the same 4 x 18 x 34 box of 16-byte pixel vectors, zero outside the image) lands in
-// the other buffer.  Two blocks per SM (two 39 KB buffers each, 128 tensor-memory columns, at most 128
-// registers a thread): the second block's warps hide the first's latencies.  Waits bounded as in k_conv_tc; a block that gives up waits
-// (bounded) for its copy in flight and its MMAs before it releases its tensor memory.
+// its strips (16 x 16 output pixels: two 16 x 8 tiles) in turn through a ring of NBH staging buffers.  The
+// copies of the block's next NBH - 1 strips (4 x 18 x 18 boxes of 16-byte pixel vectors, zero outside the
+// image) are in flight while a strip's MMAs and epilogue run; once a strip's MMAs have completed its buffer
+// takes the copy of the strip NBH ahead.  Two blocks per SM (four 21 KB buffers each, 64 tensor-memory
+// columns, at most 128 registers a thread): six input boxes in flight per SM keep enough reads outstanding
+// for the memory's latency.  Waits bounded as in k_conv_tc; a block that gives up waits (bounded) for its
+// copies in flight and its MMAs before it releases its shared and tensor memory.
 constexpr int CING_H = 4;
-constexpr int MTH = 4;                 // tiles per strip of the hidden layers
+constexpr int MTH = 2;                 // tiles per strip of the hidden layers
+constexpr int NBH = 4;                 // staging buffers (ring)
 constexpr int SXH = 8 * MTH, PXH = SXH + 2;
 constexpr size_t TMA_BOX_BYTES = (size_t)CING_H * PY * PXH * 16;
 constexpr size_t TMA_BUF = (TMA_BOX_BYTES + 1023) / 1024 * 1024;
 
 template <int NOUT>
 struct ConvTmaLayout {
-    static constexpr size_t buf0 = 0, buf1 = TMA_BUF;
-    static constexpr size_t b_off = 2 * TMA_BUF;
+    static constexpr size_t b_off = NBH * TMA_BUF;  // buffer k at k * TMA_BUF
     static constexpr size_t b_bytes = (size_t)9 * CING_H * NOUT * 16;
     static constexpr size_t bias_off = b_off + b_bytes;
     static constexpr size_t bar_off = (bias_off + (size_t)NOUT * 4 + 15) / 16 * 16;
-    static constexpr size_t total = bar_off + 4 * 8 + 16;
-    static constexpr uint32_t tcols = MTH * NOUT;
+    static constexpr size_t total = bar_off + (NBH + 1) * 8 + 16;  // NBH copy barriers, the MMA barrier, slot
+    static constexpr uint32_t tcols = MTH * NOUT < 32 ? 32 : MTH * NOUT;
 };
 
 template <int NOUT, int EPI>
@@ -258,9 +259,9 @@ __global__ void __launch_bounds__(NTH, 2)
     extern __shared__ __align__(1024) unsigned char smem[];
     __half *sB = reinterpret_cast<__half *>(smem + L::b_off);
     float *sBias = reinterpret_cast<float *>(smem + L::bias_off);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::bar_off);  // [2]: a staging buffer's copy landed
-    uint64_t *mbar = full + 2;                                         // the strip's MMAs completed
-    uint32_t *slot = reinterpret_cast<uint32_t *>(full + 4);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::bar_off);  // [NBH]: a staging buffer's copy landed
+    uint64_t *mbar = full + NBH;                                       // the strip's MMAs completed
+    uint32_t *slot = reinterpret_cast<uint32_t *>(full + NBH + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     for (int e = tid; e < 9 * CING_H * NOUT * 8; e += NTH) {
@@ -272,9 +273,7 @@ __global__ void __launch_bounds__(NTH, 2)
     for (int n = tid; n < NOUT; n += NTH) sBias[n] = n < cout ? __half2float(wt[cout * cin * 9 + n]) : 0.f;
     const int nsx = (W + SXH - 1) / SXH, nstrip = ((H + SY - 1) / SY) * nsx;
     if (tid == 0) {
-        tc::bar_init(&full[0], 1);
-        tc::bar_init(&full[1], 1);
-        tc::bar_init(mbar, 1);
+        for (int k = 0; k <= NBH; ++k) tc::bar_init(&full[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 0) tc::tmem_alloc(slot, L::tcols);
@@ -287,34 +286,29 @@ __global__ void __launch_bounds__(NTH, 2)
     auto issue_copy = [&](int strip, int b) {  // thread 0: the strip's input box into buffer b
         const int y0 = (strip / nsx) * SY, x0 = (strip % nsx) * SXH;
         tc::bar_arrive_expect_tx(&full[b], (uint32_t)TMA_BOX_BYTES);
-        tc::tma_load_3d(smem + (b ? L::buf1 : L::buf0), &tmap, &full[b], 2 * (x0 - 1), y0 - 1, 0);
+        tc::tma_load_3d(smem + (size_t)b * TMA_BUF, &tmap, &full[b], 2 * (x0 - 1), y0 - 1, 0);
     };
-    // copies issued into / waited for from each buffer (the same on every thread: the decisions are uniform)
-    int issued[2] = {0, 0}, waited[2] = {0, 0};
-    if ((int)blockIdx.x < nstrip) {
-        if (tid == 0) issue_copy(blockIdx.x, 0);
-        issued[0] = 1;
+    // The block's k-th strip goes through buffer k % NBH; copies issued (and waited for) in order, so copy k
+    // lands on the (k / NBH)-th phase of its buffer's barrier.  The counts are the same on every thread.
+    int issued = 0, waited = 0;
+    for (int k = 0; k < NBH && (int)blockIdx.x + k * (int)gridDim.x < nstrip; ++k) {
+        if (tid == 0) issue_copy(blockIdx.x + k * gridDim.x, k);
+        ++issued;
     }
     bool failed = false;
     int i = 0;
     for (int strip = blockIdx.x; strip < nstrip; strip += gridDim.x, ++i) {
-        const int b = i & 1;
+        const int b = i % NBH;
         const int y0 = (strip / nsx) * SY, x0 = (strip % nsx) * SXH;
-        // the next strip's copy goes out now (its buffer's last reader, strip i - 1's MMAs, has completed)
-        const int next = strip + gridDim.x;
-        if (next < nstrip) {
-            if (tid == 0) issue_copy(next, b ^ 1);
-            ++issued[b ^ 1];
-        }
-        const bool landed = tc::bar_wait(&full[b], (uint32_t)(waited[b] & 1), SPIN);
+        const bool landed = tc::bar_wait(&full[b], (uint32_t)((i / NBH) & 1), SPIN);
         if (__syncthreads_or(!landed)) {
             failed = true;
             break;
         }
-        ++waited[b];
+        ++waited;
         if (tid == 0) {
             tc::fence_after();
-            const uint32_t a0 = tc::su32(smem + (b ? L::buf1 : L::buf0)), b0 = tc::su32(sB);
+            const uint32_t a0 = tc::su32(smem + (size_t)b * TMA_BUF), b0 = tc::su32(sB);
             for (int j = 0; j < MTH; ++j)
                 for (int tap = 0; tap < 9; ++tap) {
                     const int ky = tap / 3, kx = tap - 3 * ky;
@@ -336,6 +330,12 @@ __global__ void __launch_bounds__(NTH, 2)
             break;
         }
         tc::fence_after();
+        // buffer b is free (this strip's MMAs have read it): the copy of the strip NBH ahead
+        const int ahead = strip + NBH * (int)gridDim.x;
+        if (ahead < nstrip) {
+            if (tid == 0) issue_copy(ahead, b);
+            ++issued;
+        }
         const int q = warp & 3, m = 32 * q + lane;
         const int oy = y0 + (m >> 3);
         for (int j = warp >> 2; j < MTH; j += 2) {
@@ -356,8 +356,7 @@ __global__ void __launch_bounds__(NTH, 2)
     if (failed && tid == 0) {
         atomicExch(err, 1);
         // copies still in flight must land before the block's shared memory is released
-        for (int pb = 0; pb < 2; ++pb)
-            for (int w = waited[pb]; w < issued[pb]; ++w) tc::bar_wait(&full[pb], (uint32_t)(w & 1), SPIN);
+        for (int w = waited; w < issued; ++w) tc::bar_wait(&full[w % NBH], (uint32_t)((w / NBH) & 1), SPIN);
     }
     tc::fence_before();
     __syncthreads();
