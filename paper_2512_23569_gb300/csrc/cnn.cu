@@ -253,9 +253,19 @@ __global__ void k_window_rows(const float *__restrict__ outm, int H, int W, int 
         int lo, hi;
         window_span(grid_pos(gx, W, step) + PS / 2, S, W, lo, hi);
         const float *row = outm + (size_t)y * W;
-        float acc = 0.f;
-        for (int x = lo; x < hi; ++x) acc += row[x];
-        rows[e] = acc;
+        // four partial sums over 16-byte loads (the windows of grid columns start on multiples of 4 pixels)
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int x = lo;
+        for (; x < hi && (reinterpret_cast<uintptr_t>(row + x) & 15) != 0; ++x) a0 += row[x];
+        for (; x + 4 <= hi; x += 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(row + x));
+            a0 += v.x;
+            a1 += v.y;
+            a2 += v.z;
+            a3 += v.w;
+        }
+        for (; x < hi; ++x) a0 += row[x];
+        rows[e] = (a0 + a1) + (a2 + a3);
     }
 }
 
