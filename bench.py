@@ -754,7 +754,7 @@ def run_learned4k(args):
                    label="timed_plain")
     plain["stats"] = hts.last_stats()
     plain["out"] = out.cpu().numpy()
-    # the noise levels the learned forms used (the map, or the estimate where the judge fell back)
+    # the noise levels the learned forms used (the map, or the estimate where the eigenvalue check fell back)
     st1 = forms["learned_p1"]["stats"]
     sref = net.sigma_refs(x, p1).cpu().numpy().astype(np.float64)
     est, est_info = hts.estimate_sigma(x, p1)
@@ -933,7 +933,7 @@ def run_cnn(args):
 def run_reference(args):
     """The reference arm: the FP64 oracle, as it stands, on the host cores, on the default workload's config.
     Each step is a bounded sample of that workload: the oracle's Haar-tSVD with its eigenvalue noise estimate
-    (Eq. 12 floor, Eq. 22-23 vote; the judge and fallback of the learned form) on one 512x512x3 crop of the
+    (Eq. 12 floor, Eq. 22-23 vote; the check and fallback of the learned form) on one 512x512x3 crop of the
     3840x2160x3 image, the crops taken in raster order over the image.  Under torchrun rank 0 alone runs."""
     rank, world, _ = _dist()
     if rank != 0:
