@@ -247,32 +247,65 @@ __device__ __forceinline__ int vote_group(const float *__restrict__ src, size_t 
         e0sq = fmaf(a0, a0, e0sq);
         esq = fmaf(a1, a1, esq);
     }
+    // warp sums of the NM eigenvalues and the two bound sums by a reduce-scatter: at each level a lane keeps
+    // the half of its values that its lane bit selects and adds the partner's copy of that half, so that
+    // after log2(NV) levels it holds the full sum of one value (index vidx); the addition depth per value
+    // is the same as a butterfly's (five levels), inside the bound's 16 u lambda
+    constexpr int NV = NM + 2 <= 8 ? 8 : NM + 2 <= 16 ? 16 : 32;
+    float val[NV];
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
+    for (int m = 0; m < NV; ++m) val[m] = m < NM ? lam[m] : m == NM ? e0sq : m == NM + 1 ? esq : 0.f;
+    int vidx = 0;
 #pragma unroll
-        for (int m = 0; m < NM; ++m) lam[m] += __shfl_xor_sync(FULL, lam[m], o);
-        e0sq += __shfl_xor_sync(FULL, e0sq, o);
-        esq += __shfl_xor_sync(FULL, esq, o);
+    for (int lv = 0, o = 16, nv = NV; lv < 5; ++lv, o >>= 1) {
+        if (nv > 1) {
+            const int half = nv / 2;
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < half; ++i) {
+                const float send = up ? val[i] : val[half + i];
+                const float keep = up ? val[half + i] : val[i];
+                val[i] = keep + __shfl_xor_sync(FULL, send, o);
+            }
+            vidx += up ? half : 0;
+            nv = half;
+        } else {
+            val[0] += __shfl_xor_sync(FULL, val[0], o);
+        }
     }
+    // the bound terms and lambda_hat = lambda_{K/2} from the lanes holding them (value v sits in lane 2 v' where
+    // v' has v's bits in lane bits 4..(5 - log2 NV), read from the first such lane)
+    auto lane_of = [&](int v) {
+        int l = 0;
+#pragma unroll
+        for (int lv = 0, o = 16, nv = NV; lv < 5 && nv > 1; ++lv, o >>= 1) {
+            const int half = nv / 2;
+            if (v >= half) {
+                l |= o;
+                v -= half;
+            }
+            nv = half;
+        }
+        return l;
+    };
+    const float e0s = __shfl_sync(FULL, val[0], lane_of(NM)), es = __shfl_sync(FULL, val[0], lane_of(NM + 1));
     // rigorous bound on |lambda32 - lambda|
-    const float dx0 = 1.4143f * (float)(K + 3) * U32 * sqrtf(e0sq) * 1.01f;
-    const float dx = 1.4143f * (float)(K + 3) * U32 * sqrtf(esq) * 1.01f;
-    float bnd[NM];
-#pragma unroll
-    for (int m = 0; m < NM; ++m) {
-        const float dd = (m == 0) ? dx0 : dx;
-        const float sl = sqrtf(fmaxf(lam[m], 0.f) * 1.02f);
-        bnd[m] = (2.f * sl * dd + dd * dd) * 1.01f + 16.f * U32 * lam[m] + 1e-30f;
-    }
-    const float lh = lam[K / 2], bh = bnd[K / 2];
-    int sure = 0, unc = 0;
-#pragma unroll
-    for (int m = 0; m < K / 2; ++m) {
-        const int mult = (m == 0) ? 1 : 2;
-        if (lam[m] + bnd[m] < lh - bh) sure += mult;
-        else if (lam[m] - bnd[m] >= lh + bh) {
-        } else unc += mult;
-    }
+    const float dx0 = 1.4143f * (float)(K + 3) * U32 * sqrtf(e0s) * 1.01f;
+    const float dx = 1.4143f * (float)(K + 3) * U32 * sqrtf(es) * 1.01f;
+    const float lm = val[0];
+    const float dd = (vidx == 0) ? dx0 : dx;
+    const float sl = sqrtf(fmaxf(lm, 0.f) * 1.02f);
+    const float bm = (2.f * sl * dd + dd * dd) * 1.01f + 16.f * U32 * lm + 1e-30f;
+    const float lh = __shfl_sync(FULL, lm, lane_of(K / 2)), bh = __shfl_sync(FULL, bm, lane_of(K / 2));
+    // classification of lambda_m, m < K/2, one lane each (the first lane holding it), counted by ballots;
+    // m and K - m give the same eigenvalue, so m >= 1 counts twice
+    const bool mine_m = vidx < K / 2 && lane == lane_of(vidx);
+    const bool s_below = mine_m && (lm + bm < lh - bh);
+    const bool s_unc = mine_m && !(lm + bm < lh - bh) && !(lm - bm >= lh + bh);
+    const unsigned bs = __ballot_sync(FULL, s_below), bu = __ballot_sync(FULL, s_unc);
+    const unsigned l0 = 1u << lane_of(0);
+    const int sure = 2 * __popc(bs) - ((bs & l0) ? 1 : 0);
+    const int unc = 2 * __popc(bu) - ((bu & l0) ? 1 : 0);
     if ((double)(1 + sure + unc) <= gamma_rank) return 1;
     if ((double)(1 + sure) > gamma_rank) return 0;
     if (lane == 0) {  // decided in FP64 by k_vote_exact
