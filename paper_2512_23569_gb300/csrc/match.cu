@@ -572,24 +572,57 @@ hts_status launch_k(const MatchArgs &a, cudaStream_t s) {
     return check_launch("k_match_fallback");
 }
 
-// Eq. 9 flag of every reference patch (one warp each), for the tensor-core
-// matching path, which reads the flags instead of deciding them itself.
+// Eq. 9 flag of every reference patch, for the tensor-core matching path, which reads the flags instead of
+// deciding them itself: two references per warp (a half-warp each, four pixels of the 8 x 8 patch per lane),
+// the FP32 screen of gcp_green_fast (the same sums in another order, inside the same margin), and the FP64
+// decision by the whole warp for a reference the screen leaves open.
 __global__ void __launch_bounds__(128) k_gcp_flags(const float *__restrict__ img, int H, int W, int step, int nx,
                                                    int nref, double gamma, uint8_t *__restrict__ green) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
     const size_t HW = (size_t)H * W;
-    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nref; r += (gridDim.x * blockDim.x) >> 5) {
+    const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    for (int r0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 2; r0 < nref; r0 += 2 * nwarp) {
+        const int r = min(r0 + half, nref - 1);  // the last odd reference is decided twice, identically
         const int gy = r / nx, gx = r - gy * nx;
         const int yr = grid_pos(gy, H, step), xr = grid_pos(gx, W, step);
-        const int gflag = gcp_green_fast(img, W, HW, yr, xr, gamma, lane);
-        if (lane == 0) green[r] = (uint8_t)gflag;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = hl + 16 * q;
+            const size_t o = (size_t)(yr + (e >> 3)) * W + xr + (e & 7);
+            const float rv = __ldg(img + o), gv = __ldg(img + HW + o), bv = __ldg(img + 2 * HW + o);
+            s0 = fmaf(rv, rv, s0);
+            s1 = fmaf(gv, gv, s1);
+            s2 = fmaf(bv, bv, s2);
+        }
+#pragma unroll
+        for (int o = 8; o; o >>= 1) {
+            s0 += __shfl_xor_sync(FULL, s0, o);
+            s1 += __shfl_xor_sync(FULL, s1, o);
+            s2 += __shfl_xor_sync(FULL, s2, o);
+        }
+        const float lhs = s1 * (float)(gamma * gamma), rhs = fmaxf(s0, s2);
+        int flag = -1;  // -1: open
+        if (lhs > rhs * (1.f + 1e-5f) && lhs > 0.f) flag = 1;
+        else if (lhs < rhs * (1.f - 1e-5f)) flag = 0;
+        const unsigned open = __ballot_sync(FULL, flag < 0);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (open & (1u << (16 * h))) {  // the whole warp decides reference r0 + h in FP64
+                const int rh = min(r0 + h, nref - 1);
+                const int gyh = rh / nx, gxh = rh - gyh * nx;
+                const int f = gcp_green(img, W, HW, grid_pos(gyh, H, step), grid_pos(gxh, W, step), gamma, lane);
+                if (half == h) flag = f;
+            }
+        }
+        if (hl == 0 && r0 + half < nref) green[r] = (uint8_t)flag;
     }
 }
 
 }  // namespace
 
 hts_status launch_gcp_flags(const float *img, const Geom &g, double gamma_gcp, uint8_t *green, cudaStream_t s) {
-    int blocks = (g.nref + 3) / 4;
+    int blocks = (g.nref + 7) / 8;  // four warps of two references
     if (blocks > 152 * 16) blocks = 152 * 16;
     {
         KTimer kt("k_gcp_flags", s);
