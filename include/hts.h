@@ -74,8 +74,8 @@ typedef struct {
                         *    accumulation) with FP32 threshold decisions.  Windows too large for
                         *    on-chip staging give HTS_EUNSUPPORTED.  The FP16 operands and the
                         *    filter's 32-bit tile sums assume pixel values of magnitude below
-                        *    2^11 (the [0, 255] scale has ample room); estimates beyond 2^13 are
-                        *    clamped.
+                        *    2^11 (the [0, 255] scale has ample room); estimates beyond 2^13 (of a
+                        *    channel-DFT slice, summed before the inverse DFT) are clamped.
                         * 2: the groups of 0 with the filter of 1. */
 } hts_params;
 

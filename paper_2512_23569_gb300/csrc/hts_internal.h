@@ -177,9 +177,10 @@ hts_status launch_filter(const float *img, const Geom &g, const int32_t *idx, co
                          DevState *st, float *out, int exact, const float *sigma_ref, int map_judged,
                          double tau_scale, cudaStream_t s, const float *mean_est = nullptr);
 double tau_scale(const Geom &g, const hts_params &p);  // sigma -> tau factor (sigma.cu)
-// Tensor-core filter of the precision form (filter_tc.cu): FP16 Kronecker
-// projections on tcgen05, FP32 decisions, tile aggregation into acc / wcount
-// (no normalisation).  *used = false (and nothing launched) where the group
+// Tensor-core filter of the precision form (filter_tc.cu): FP16 projections of
+// each Fourier slice on tcgen05, FP32 decisions, tile aggregation into acc /
+// wcount (per slice for colour; no normalisation: normalize_box forms the
+// weights and turns the slice sums into R, G, B).  *used = false (and nothing launched) where the group
 // size or the window does not fit it.
 hts_status launch_filter_tc(const float *img, const Geom &g, const int32_t *idx, const float *b32, long long *acc,
                             int *wcount, DevState *st, const float *sigma_ref, int map_judged, double tau_scale,
